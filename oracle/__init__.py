@@ -1,0 +1,22 @@
+"""Oracle for the orbital minimization method (OMM) of Corsetti (arXiv:1312.1549).
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product (the CUDA library and its
+Python binding) may import, call or link anything in this package; only the
+tests, `__graft_entry__.smoke()` and the bench's CPU-baseline leg use it.
+
+Contents (all plain float64 CPU code, written from the paper):
+
+* `exact`  -- the result the OMM converges to, by its plain definition: the n
+  lowest generalised eigenpairs of H x = eps S x (Sec. 2.1, Eqs. 1 and 7-8).
+* `jacobi` -- a self-contained cyclic Jacobi eigensolver with Cholesky
+  reduction, used to pin `exact` on tiny inputs without any library solver.
+* `omm`    -- the OMM itself, step by step: eigenspectrum shift (Sec. 2.2),
+  CG with Polak-Ribiere directions, the gradient (Eq. 9), the quartic line
+  search with directly computed coefficients (Eq. 10-12), the state update
+  (Eq. 13), the kinetic preconditioner (Eq. 14) and the outputs.
+
+Parity status: every function here is pinned by a test in
+tests/test_oracle_pins.py against brute force, closed forms, finite
+differences or invariants; none is "parity unpinned" except the CG iteration
+count, which the paper does not fix.
+"""
