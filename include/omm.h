@@ -1,0 +1,154 @@
+/*
+ * omm.h -- C ABI of the GB300 orbital minimization method (OMM) library.
+ *
+ * The library minimises the OMM functional of Corsetti, "The orbital
+ * minimization method for electronic structure calculations with finite-range
+ * atomic basis sets" (arXiv:1312.1549):
+ *
+ *     E~[C] = 2 Tr[(2I - S_W) H_W] = 4 Tr H_W - 2 Tr(S_W H_W)      (Sec. 2.1, Eq. 8)
+ *     H_W = C^T H~ C,  S_W = C^T S C                                 (Eqs. 5-6)
+ *     H~  = H - eta S  (eigenspectrum shift)                         (Sec. 2.2, Eq. 9)
+ *
+ * by conjugate gradients with Polak-Ribiere directions, the exact quartic line
+ * search with directly computed coefficients (Sec. 2.3, Eqs. 12-16) and the
+ * kinetic preconditioner P = (S + T/tau)^-1 (Sec. 2.4, Eq. 17), on one GPU.
+ * The converged point gives the band energy E = 2 sum_{i<=n} eps_i of the
+ * generalised eigenproblem H c = eps S c (Eq. 1), the density matrix
+ * D = 2 C (2I - S_W) C^T = dE/dH and the energy-density matrix EDM, with
+ * dE/dS = -EDM.
+ *
+ * Conventions shared by every entry point
+ *  - Numbers are IEEE float64.
+ *  - H, S, T, D, EDM are m x m, symmetric, row-major (row-major and
+ *    column-major coincide for symmetric matrices).
+ *  - C0 and C are n x m row-major: row j holds Wannier function j over the m
+ *    basis functions. These are the same bytes as the paper's m x n matrix C
+ *    stored column-major.
+ *  - Every matrix pointer may point to host memory (pageable or pinned) or to
+ *    device memory of the current device; the library copies with
+ *    cudaMemcpyDefault (unified addressing) and never keeps a caller pointer
+ *    after a call returns. Scalar outputs (E, info) are host pointers.
+ *  - All GPU work is ordered on the stream given to omm_create (NULL = the
+ *    legacy default stream). Calls return after their results are written.
+ *  - Errors: every call returns an omm_status and never aborts, traps or
+ *    exits. omm_last_error() gives a human-readable message for the last
+ *    failing call on the calling thread. After a non-OK status the outputs are
+ *    unspecified, except that omm_solve leaves the last iterate in C on
+ *    OMM_ERR_NO_CONVERGENCE.
+ *  - Units: eta in the units of H (hartree in the bundled workloads), tau in
+ *    the units of T (tau = 10 Ry is 5 Ha).
+ *  - Thread safety: a context may be used by one thread at a time; distinct
+ *    contexts are independent.
+ */
+#ifndef OMM_GB300_OMM_H
+#define OMM_GB300_OMM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct omm_ctx omm_ctx; /* opaque; owned by the library */
+
+typedef enum {
+  OMM_OK = 0,
+  OMM_ERR_ARG = 1,            /* invalid argument (sizes, NULL pointers, tau <= 0, n >= m) */
+  OMM_ERR_NOT_SPD = 2,        /* S + T/tau (or S) is not positive definite (Cholesky failed) */
+  OMM_ERR_UNBOUNDED = 3,      /* the quartic along the search line has no minimum: the shifted
+                                 functional is unbounded below (Sec. 2.2 footnote; eta too high) */
+  OMM_ERR_NO_CONVERGENCE = 4, /* max_iter line searches without meeting the tolerance */
+  OMM_ERR_NONFINITE = 5,      /* a NaN or Inf appeared in a reduction */
+  OMM_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  OMM_ERR_CUDA = 7,           /* a CUDA runtime call failed */
+  OMM_ERR_OOM = 8,            /* device memory allocation failed */
+  OMM_ERR_STATE = 9           /* call out of order (e.g. omm_backward before a solve) */
+} omm_status;
+
+typedef enum {
+  OMM_PREC_FP64 = 0,   /* every contraction in float64 */
+  OMM_PREC_MIXED = 1   /* bulk contractions on the BF16 tensor cores as 3-term split products
+                          with FP32 accumulation, state in float64, float64 refinement and a
+                          float64 certificate of the final point */
+} omm_precision;
+
+/* Options. A zero-filled struct (or NULL) selects every default. */
+typedef struct {
+  int precision;        /* omm_precision; default OMM_PREC_FP64 */
+  int max_iter;         /* line searches per solve; 0 -> 10000 */
+  int no_precondition;  /* 0 -> use P = (S + T/tau)^-1 (default); 1 -> plain gradient */
+  int check_every;      /* line searches between host convergence polls; 0 -> 8 */
+  double tol_grad;      /* stop when max|G| < tol_grad, G the exact gradient of Eq. 12; 0 -> 1e-9 */
+  double e_tol;         /* also stop when |2(E_new-E)/(E_new+E)| <= e_tol (Eq. 18); 0 -> off */
+  double refine_ratio;  /* mixed: refine in float64 once max|G| fell by this factor since
+                           the last float64 refinement; 0 -> 1e-4 */
+} omm_opts;
+
+/* Per-solve report. */
+typedef struct {
+  int status;           /* omm_status of the solve */
+  int iterations;       /* line searches in total */
+  int iterations_fp64;  /* line searches run with float64 contractions */
+  int refinements;      /* float64 recomputations of the state (mixed precision) */
+  double E;             /* band energy 2 sum eps_i = E~ + 2 n eta (certified in float64) */
+  double Etilde;        /* the shifted functional E~ at the returned C */
+  double gmax;          /* max|G| of the certified gradient at the returned C */
+  double ms_setup;      /* omm_create GPU time (shift, Cholesky, inverse, splits) */
+  double ms_iterate;    /* CG line searches */
+  double ms_refine;     /* float64 refinements and the final certificate */
+  double ms_outputs;    /* density matrix */
+  double gemm_flop;     /* logical contraction flops of the solve (FP64-equivalent) */
+  double gemm_flop_tc;  /* flops issued to the BF16 tensor cores (3 per logical in split form) */
+} omm_info;
+
+/* Create a solver context for one (H, S, T) and do the per-geometry setup:
+ * H~ = H - eta S (Eq. 9) and the preconditioner P = (S + T/tau)^-1 (Eq. 17) by a
+ * float64 Cholesky factorisation and inverse (Sec. 2.4: once per geometry).
+ *   m      number of basis functions, n number of Wannier functions, 0 < n < m.
+ *   H,S,T  m x m symmetric float64 (host or device). T may be NULL when
+ *          opts->no_precondition == 1. They are copied; the caller keeps ownership.
+ *   eta    eigenspectrum shift; the solve finds the n lowest states only if
+ *          eta lies above the n-th eigenvalue (Sec. 2.2).
+ *   tau    kinetic-energy scale, > 0; +infinity gives P = S^-1.
+ *   stream cudaStream_t (as void*) for every GPU operation of this context.
+ *   out    receives the context; *out is NULL on failure.
+ * Errors: OMM_ERR_ARG, OMM_ERR_NOT_SPD, OMM_ERR_OOM, OMM_ERR_CUDA. */
+omm_status omm_create(int m, int n, const double* H, const double* S, const double* T,
+                      double eta, double tau, const omm_opts* opts, void* stream,
+                      omm_ctx** out);
+
+/* Minimise E~ from the starting coefficients C0 (n x m, host or device; may alias C).
+ * Writes the converged C (n x m), the band energy *E (host) and, if D != NULL,
+ * the density matrix D = 2 C (2I - S_W) C^T (m x m) = dE/dH. info may be NULL.
+ * Stops when max|G| < tol_grad (G of Eq. 12, certified in float64), or by the
+ * relative energy change of Eq. 18 when e_tol > 0.
+ * Errors: OMM_ERR_ARG, OMM_ERR_UNBOUNDED, OMM_ERR_NO_CONVERGENCE,
+ * OMM_ERR_NONFINITE, OMM_ERR_CUDA. */
+omm_status omm_solve(omm_ctx* ctx, const double* C0, double* C, double* E, double* D,
+                     omm_info* info);
+
+/* Gradients of E with respect to H and S at the last converged solve (m x m
+ * each, host or device, either may be NULL):
+ *   dEdH = D = 2 C (2I - S_W) C^T,
+ *   dEdS = -EDM = -(2 C H~_W C^T + eta D).
+ * By the envelope theorem these are exact at the minimum (derived from Eq. 8
+ * with H~ = H - eta S). Errors: OMM_ERR_STATE (no converged solve), OMM_ERR_CUDA. */
+omm_status omm_backward(omm_ctx* ctx, double* dEdH, double* dEdS);
+
+/* Replace H (SCF warm start: S, T and P are kept; Sec. 2.5.2). */
+omm_status omm_update_H(omm_ctx* ctx, const double* H);
+
+/* Release every resource of the context (NULL is ignored). */
+void omm_free(omm_ctx* ctx);
+
+/* Static description of a status code. */
+const char* omm_status_str(omm_status s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* omm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OMM_GB300_OMM_H */

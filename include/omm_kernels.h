@@ -1,0 +1,55 @@
+/*
+ * omm_kernels.h -- step-level entry points of the OMM library.
+ *
+ * Each function runs one step of the OMM hot path on the GPU, exactly as the
+ * solver of omm.h runs it, so that the steps can be checked one by one.
+ * Pointers are device pointers (float64 unless stated) unless marked
+ * "host"; all work is ordered on `stream` (cudaStream_t as void*, NULL = legacy
+ * default stream) and the call returns after it completes. Errors are
+ * returned as omm_status (see omm.h), never raised; the library never
+ * traps or aborts.
+ */
+#ifndef OMM_GB300_OMM_KERNELS_H
+#define OMM_GB300_OMM_KERNELS_H
+
+#include "omm.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Float64 GEMM, row-major: C = alpha op(A) op(B) + beta C, op(A) M x K and
+ * op(B) K x N. transA = 0: A is M x K (ld lda); 1: A is K x M. transB likewise.
+ * This is the contraction of every float64 step (Sec. 2.3, Table 1: the
+ * m x m by m x n, m x n by n x n and n x m by m x n products).
+ * Errors: OMM_ERR_ARG (negative sizes, NULL pointers), OMM_ERR_CUDA. */
+omm_status omm_kernel_dgemm(int transA, int transB, int M, int N, int K, double alpha,
+                            const double* A, long lda, const double* B, long ldb, double beta,
+                            double* C, long ldc, void* stream);
+
+/* P = A^-1 for a symmetric positive definite m x m A, by a float64 Cholesky
+ * factorisation and triangular inverse (the preconditioner of Sec. 2.4,
+ * Eq. 17, applied to A = S + T/tau). A is not modified. *info (host) receives
+ * 0, or the 1-based column of the first non-positive pivot, in which case the
+ * call returns OMM_ERR_NOT_SPD and P is unspecified. */
+omm_status omm_kernel_spd_inverse(int m, const double* A, double* P, int* info, void* stream);
+
+/* Line minimum of the quartic a0 + a1 x + a2 x^2 + a3 x^3 + a4 x^4 (Sec. 2.3,
+ * Eq. 13) as the solver takes it on the device: the first local minimum along
+ * x > 0 (a1 < 0). alpha (host, 5 values), x (host) receives the step.
+ * Returns OMM_OK, or OMM_ERR_UNBOUNDED when the quartic has no minimum on
+ * x > 0 (the functional is unbounded along the line, Sec. 2.2 footnote). */
+omm_status omm_kernel_line_minimum(const double* alpha, double* x);
+
+/* Quartic coefficients alpha_0..alpha_4 (Eq. 13) of one line search from the
+ * n x n matrices SWHW = [S_W | H_W] (n x 2n, row-major) and
+ * Proj = [H' | S' | H'' | S''] (n x 4n, row-major) with H' = Delta^T H C and
+ * H'' = Delta^T H Delta (Eqs. 14-15); E is alpha_0. alpha (host, 5 values). */
+omm_status omm_kernel_quartic_coefficients(int n, const double* SWHW, const double* Proj, double E,
+                                           double* alpha, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OMM_GB300_OMM_KERNELS_H */

@@ -1,0 +1,128 @@
+// Step-level C entry points of include/omm_kernels.h.
+#include "../../include/omm_kernels.h"
+#include "omm_internal.cuh"
+
+#include <cstring>
+#include <string>
+
+using namespace omm;
+
+namespace {
+
+omm_status cuda_fail(const char* where, const CudaError& e) {
+  set_last_error(std::string(where) + ": " + e.what + ": " + cudaGetErrorString(e.err));
+  return OMM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+omm_status omm_kernel_dgemm(int transA, int transB, int M, int N, int K, double alpha, const double* A,
+                            long lda, const double* B, long ldb, double beta, double* C, long ldc,
+                            void* stream) {
+  if (M < 0 || N < 0 || K < 0 || !C || (K > 0 && (!A || !B))) {
+    set_last_error("omm_kernel_dgemm: invalid argument");
+    return OMM_ERR_ARG;
+  }
+  try {
+    cudaStream_t st = (cudaStream_t)stream;
+    dgemm(st, transA, transB, M, N, K, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0);
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
+  } catch (const CudaError& e) {
+    return cuda_fail("omm_kernel_dgemm", e);
+  }
+  return OMM_OK;
+}
+
+omm_status omm_kernel_spd_inverse(int m, const double* A, double* P, int* info, void* stream) {
+  if (m <= 0 || !A || !P) {
+    set_last_error("omm_kernel_spd_inverse: invalid argument");
+    return OMM_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double* W = nullptr;
+  double* work = nullptr;
+  int* info_dev = nullptr;
+  omm_status rc = OMM_OK;
+  try {
+    const size_t mm = (size_t)m * m;
+    OMM_CUDA_TRY(cudaMalloc((void**)&W, mm * sizeof(double)));
+    OMM_CUDA_TRY(cudaMalloc((void**)&work, spd_inverse_workspace(m) * sizeof(double)));
+    OMM_CUDA_TRY(cudaMalloc((void**)&info_dev, sizeof(int)));
+    OMM_CUDA_TRY(cudaMemcpyAsync(W, A, mm * sizeof(double), cudaMemcpyDefault, st));
+    spd_inverse(st, m, W, P, work, info_dev);
+    int h = 0;
+    OMM_CUDA_TRY(cudaMemcpyAsync(&h, info_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (info) *info = h;
+    if (h != 0) {
+      set_last_error("omm_kernel_spd_inverse: not positive definite");
+      rc = OMM_ERR_NOT_SPD;
+    }
+  } catch (const CudaError& e) {
+    rc = cuda_fail("omm_kernel_spd_inverse", e);
+  }
+  if (W) cudaFree(W);
+  if (work) cudaFree(work);
+  if (info_dev) cudaFree(info_dev);
+  return rc;
+}
+
+omm_status omm_kernel_line_minimum(const double* alpha, double* x) {
+  if (!alpha || !x) {
+    set_last_error("omm_kernel_line_minimum: NULL argument");
+    return OMM_ERR_ARG;
+  }
+  double* d = nullptr;
+  omm_status rc = OMM_OK;
+  try {
+    OMM_CUDA_TRY(cudaMalloc((void**)&d, 8 * sizeof(double)));
+    OMM_CUDA_TRY(cudaMemcpy(d, alpha, 5 * sizeof(double), cudaMemcpyHostToDevice));
+    int* st = (int*)(d + 6);
+    launch_line_minimum(nullptr, d, d + 5, st);
+    double out[2];
+    int s = 0;
+    OMM_CUDA_TRY(cudaMemcpy(out, d + 5, sizeof(double), cudaMemcpyDeviceToHost));
+    OMM_CUDA_TRY(cudaMemcpy(&s, st, sizeof(int), cudaMemcpyDeviceToHost));
+    *x = out[0];
+    rc = (s == 0) ? OMM_OK : OMM_ERR_UNBOUNDED;
+  } catch (const CudaError& e) {
+    rc = cuda_fail("omm_kernel_line_minimum", e);
+  }
+  if (d) cudaFree(d);
+  return rc;
+}
+
+omm_status omm_kernel_quartic_coefficients(int n, const double* SWHW, const double* Proj, double E,
+                                           double* alpha, void* stream) {
+  if (n <= 0 || !SWHW || !Proj || !alpha) {
+    set_last_error("omm_kernel_quartic_coefficients: invalid argument");
+    return OMM_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Scalars* sc = nullptr;
+  double* part = nullptr;
+  omm_status rc = OMM_OK;
+  try {
+    OMM_CUDA_TRY(cudaMalloc((void**)&sc, sizeof(Scalars)));
+    OMM_CUDA_TRY(cudaMalloc((void**)&part, (size_t)traces_blocks(n) * kNumTraces * sizeof(double)));
+    Scalars h;
+    std::memset(&h, 0, sizeof(h));
+    h.E = E;
+    h.max_iter = 1;
+    OMM_CUDA_TRY(cudaMemcpyAsync(sc, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+    launch_traces(st, n, SWHW, Proj, part, sc);
+    launch_control_linesearch(st, sc, part, traces_blocks(n));
+    OMM_CUDA_TRY(cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int q = 0; q < 5; ++q) alpha[q] = h.alpha[q];
+  } catch (const CudaError& e) {
+    rc = cuda_fail("omm_kernel_quartic_coefficients", e);
+  }
+  if (sc) cudaFree(sc);
+  if (part) cudaFree(part);
+  return rc;
+}
+
+}  // extern "C"

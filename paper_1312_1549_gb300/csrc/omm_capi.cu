@@ -1,0 +1,506 @@
+// The C ABI of include/omm.h: solver context, setup, the CG loop and outputs.
+//
+// Data layout in device memory (m basis functions, n Wannier functions,
+// all float64, row-major; "_nm" arrays hold one Wannier function per row):
+//   HS    2m x m   [H~ ; S]        H~ = H - eta S (Sec. 2.2, Eq. 9)
+//   P     m x m    (S + T/tau)^-1  (Sec. 2.4, Eq. 17)
+//   C, Dir, G, Gold, PG   n x m
+//   Y4    4n x m   [HC ; SC ; HD ; SD]   (the reused products of the Sec. 2.3 footnote)
+//   SWHW  n x 2n   [S_W | H_W]
+//   Proj  n x 4n   [H' | S' | H'' | S'']  (Eqs. 14-15)
+// With this layout every contraction of a line search is one GEMM:
+//   HD,SD = Dir [H~;S]^T, Proj = Dir Y4^T, G = 8 HC - 4 SWHW [HC;SC], PG = G P.
+#include "../../include/omm.h"
+#include "omm_internal.cuh"
+#include "omm_mixed.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+namespace omm {
+namespace {
+thread_local std::string g_last_error;
+}
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+const char* last_error_cstr() { return g_last_error.c_str(); }
+}  // namespace omm
+
+using namespace omm;
+
+struct omm_ctx {
+  int m = 0, n = 0;
+  double eta = 0.0, tau = 0.0;
+  omm_opts opts{};
+  cudaStream_t st = nullptr;
+  bool precond = true;
+  bool solved = false;
+  double* HS = nullptr;
+  double* P = nullptr;
+  double* C = nullptr;
+  double* Dir = nullptr;
+  double* G = nullptr;
+  double* Gold = nullptr;
+  double* PG = nullptr;
+  double* Y4 = nullptr;
+  double* SWHW = nullptr;
+  double* Proj = nullptr;
+  double* nn = nullptr;      // n x n scratch
+  double* part = nullptr;    // reduction partials
+  double* part2 = nullptr;   // trace partials
+  double* mm = nullptr;      // m x m output scratch (lazy)
+  Scalars* sc = nullptr;
+  Scalars* sc_host = nullptr;  // pinned
+  int* info_dev = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double ms_setup = 0.0;
+  MixedState* mixed = nullptr;
+};
+
+namespace {
+
+struct Status {
+  omm_status s;
+  std::string msg;
+};
+
+omm_status fail(omm_status s, const std::string& msg) {
+  set_last_error(msg);
+  return s;
+}
+
+template <typename T>
+void dev_alloc(T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    throw std::bad_alloc();
+  }
+}
+
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void copy_in(double* dst, const double* src, size_t count, cudaStream_t st) {
+  OMM_CUDA_TRY(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, st));
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms;
+}
+
+// HC, SC = C [H~;S]^T; S_W, H_W; E~; G = 8 HC - 4 [S_W|H_W][HC;SC]  (all float64)
+void recompute_state_fp64(omm_ctx* c) {
+  const int m = c->m, n = c->n;
+  const long nm = (long)n * m, mm = (long)m * m;
+  dgemm(c->st, 0, 1, n, m, m, 1.0, c->C, m, 0, c->HS, m, mm, 0.0, c->Y4, m, nm, 2);
+  dgemm(c->st, 0, 1, n, n, m, 1.0, c->C, m, 0, c->Y4 + nm, m, 0, 0.0, c->SWHW, 2L * n, 0);
+  dgemm(c->st, 0, 1, n, n, m, 1.0, c->C, m, 0, c->Y4, m, 0, 0.0, c->SWHW + n, 2L * n, 0);
+  launch_functional(c->st, n, c->SWHW, c->part2);
+  launch_finish_functional(c->st, c->sc, c->part2, traces_blocks(n));
+  launch_scale_copy(c->st, nm, c->Y4, 8.0, c->G, nullptr);
+  dgemm(c->st, 0, 0, n, m, 2 * n, -4.0, c->SWHW, 2L * n, 0, c->Y4, m, 0, 1.0, c->G, m, 0);
+  launch_gmax(c->st, nm, c->G, c->part);
+  launch_finish_gmax(c->st, c->sc, c->part);
+}
+
+// One line search with float64 contractions (Sec. 2.3).
+void iterate_fp64(omm_ctx* c) {
+  const int m = c->m, n = c->n;
+  const long nm = (long)n * m, mm = (long)m * m;
+  const int* skip = &c->sc->done;
+  if (c->precond)
+    dgemm(c->st, 0, 1, n, m, m, 1.0, c->G, m, 0, c->P, m, 0, 0.0, c->PG, m, 0, 1, 0, skip);
+  else
+    launch_scale_copy(c->st, nm, c->G, 1.0, c->PG, c->sc);
+  launch_grad_reduce(c->st, nm, c->G, c->PG, c->Gold, c->Dir, c->part, c->sc);
+  launch_control_direction(c->st, c->sc, c->part, 0);
+  launch_direction(c->st, nm, c->PG, c->Dir, c->sc);
+  dgemm(c->st, 0, 1, n, m, m, 1.0, c->Dir, m, 0, c->HS, m, mm, 0.0, c->Y4 + 2 * nm, m, nm, 2, 0, skip);
+  dgemm(c->st, 0, 1, n, 4 * n, m, 1.0, c->Dir, m, 0, c->Y4, m, 0, 0.0, c->Proj, 4L * n, 0, 1, 0, skip);
+  launch_traces(c->st, n, c->SWHW, c->Proj, c->part2, c->sc);
+  launch_control_linesearch(c->st, c->sc, c->part2, traces_blocks(n));
+  launch_update_state(c->st, n, m, c->C, c->Y4, c->Dir, c->G, c->Gold, c->sc);
+  launch_update_subspace(c->st, n, c->SWHW, c->Proj, c->sc);
+  dgemm(c->st, 0, 0, n, m, 2 * n, -4.0, c->SWHW, 2L * n, 0, c->Y4, m, 0, 1.0, c->G, m, 0, 1, 0, skip);
+}
+
+void read_scalars(omm_ctx* c) {
+  OMM_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->st));
+  OMM_CUDA_TRY(cudaStreamSynchronize(c->st));
+}
+
+void reset_loop_flags(omm_ctx* c, bool full) {
+  Scalars& h = *c->sc_host;
+  if (full) {
+    std::memset(&h, 0, sizeof(Scalars));
+  }
+  h.done = 0;
+  h.halt = 0;
+  h.status = 0;
+  h.have_dir = 0;
+  h.restart = 1;
+  h.stop_pending = 0;
+  h.stop_reason = 0;
+  h.max_iter = c->opts.max_iter;
+  h.tol_grad = c->opts.tol_grad;
+  h.e_tol = c->opts.e_tol;
+}
+
+void write_scalars(omm_ctx* c) {
+  OMM_CUDA_TRY(cudaMemcpyAsync(c->sc, c->sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, c->st));
+}
+
+// D = 2 C^T (2I - S_W) C  (n x m layout) into out (m x m, device)
+void density_into(omm_ctx* c, double* out) {
+  const int m = c->m, n = c->n;
+  launch_two_i_minus(c->st, n, c->SWHW, 2L * n, c->nn);
+  dgemm(c->st, 0, 0, n, m, n, 1.0, c->nn, n, 0, c->C, m, 0, 0.0, c->PG, m, 0);
+  dgemm(c->st, 1, 0, m, m, n, 2.0, c->C, m, 0, c->PG, m, 0, 0.0, out, m, 0, 1, kTriLower);
+  launch_symmetrize_lower(c->st, m, out);
+}
+
+// out = -(2 C^T H~_W C + eta D), with D already in out
+void minus_edm_into(omm_ctx* c, double* out) {
+  const int m = c->m, n = c->n;
+  dgemm(c->st, 0, 0, n, m, n, 1.0, c->SWHW + n, 2L * n, 0, c->C, m, 0, 0.0, c->PG, m, 0);
+  dgemm(c->st, 1, 0, m, m, n, -2.0, c->C, m, 0, c->PG, m, 0, -c->eta, out, m, 0, 1, kTriLower);
+  launch_symmetrize_lower(c->st, m, out);
+}
+
+void ensure_mm(omm_ctx* c) {
+  if (!c->mm) dev_alloc(&c->mm, (size_t)c->m * c->m);
+}
+
+void destroy(omm_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  dev_free(c->HS);
+  dev_free(c->P);
+  dev_free(c->C);
+  dev_free(c->Dir);
+  dev_free(c->G);
+  dev_free(c->Gold);
+  dev_free(c->PG);
+  dev_free(c->Y4);
+  dev_free(c->SWHW);
+  dev_free(c->Proj);
+  dev_free(c->nn);
+  dev_free(c->part);
+  dev_free(c->part2);
+  dev_free(c->mm);
+  dev_free(c->sc);
+  dev_free(c->info_dev);
+  if (c->sc_host) cudaFreeHost(c->sc_host);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->mixed) mixed_destroy(c->mixed);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* omm_status_str(omm_status s) {
+  switch (s) {
+    case OMM_OK: return "ok";
+    case OMM_ERR_ARG: return "invalid argument";
+    case OMM_ERR_NOT_SPD: return "matrix is not positive definite";
+    case OMM_ERR_UNBOUNDED: return "functional unbounded along the search line (eta too high?)";
+    case OMM_ERR_NO_CONVERGENCE: return "no convergence within max_iter";
+    case OMM_ERR_NONFINITE: return "non-finite value";
+    case OMM_ERR_TIMEOUT: return "device wait timed out";
+    case OMM_ERR_CUDA: return "CUDA error";
+    case OMM_ERR_OOM: return "out of device memory";
+    case OMM_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* omm_last_error(void) { return last_error_cstr(); }
+
+omm_status omm_create(int m, int n, const double* H, const double* S, const double* T, double eta,
+                      double tau, const omm_opts* opts, void* stream, omm_ctx** out) {
+  if (out) *out = nullptr;
+  if (!out || !H || !S) return fail(OMM_ERR_ARG, "omm_create: NULL argument");
+  if (m <= 0 || n <= 0 || n >= m) return fail(OMM_ERR_ARG, "omm_create: need 0 < n < m");
+  omm_opts o{};
+  if (opts) o = *opts;
+  if (o.max_iter <= 0) o.max_iter = 10000;
+  if (o.check_every <= 0) o.check_every = 8;
+  if (!(o.tol_grad > 0.0)) o.tol_grad = 1e-9;
+  if (!(o.e_tol >= 0.0)) o.e_tol = 0.0;
+  if (!(o.refine_ratio > 0.0)) o.refine_ratio = 1e-4;
+  if (o.precision != OMM_PREC_FP64 && o.precision != OMM_PREC_MIXED)
+    return fail(OMM_ERR_ARG, "omm_create: unknown precision");
+  const bool precond = (o.no_precondition == 0);
+  if (precond && !(tau > 0.0)) return fail(OMM_ERR_ARG, "omm_create: tau must be > 0");
+  if (precond && !T && std::isfinite(tau)) return fail(OMM_ERR_ARG, "omm_create: T is NULL");
+  if (!std::isfinite(eta)) return fail(OMM_ERR_ARG, "omm_create: eta is not finite");
+
+  omm_ctx* c = new (std::nothrow) omm_ctx();
+  if (!c) return fail(OMM_ERR_OOM, "omm_create: host allocation");
+  c->m = m;
+  c->n = n;
+  c->eta = eta;
+  c->tau = tau;
+  c->opts = o;
+  c->st = (cudaStream_t)stream;
+  c->precond = precond;
+  double* A = nullptr;
+  double* work = nullptr;
+  try {
+    const long mm = (long)m * m, nm = (long)n * m;
+    for (auto& e : c->ev) OMM_CUDA_TRY(cudaEventCreate(&e));
+    OMM_CUDA_TRY(cudaMallocHost((void**)&c->sc_host, sizeof(Scalars)));
+    dev_alloc(&c->sc, 1);
+    dev_alloc(&c->info_dev, 1);
+    dev_alloc(&c->HS, 2 * mm);
+    OMM_CUDA_TRY(cudaEventRecord(c->ev[0], c->st));
+    copy_in(c->HS, H, mm, c->st);
+    copy_in(c->HS + mm, S, mm, c->st);
+    launch_axpby_shift(c->st, mm, c->HS, c->HS + mm, eta, c->HS);
+    if (precond) {
+      dev_alloc(&c->P, mm);
+      dev_alloc(&A, mm);
+      dev_alloc(&work, spd_inverse_workspace(m));
+      if (std::isfinite(tau)) {
+        copy_in(A, T, mm, c->st);
+        launch_add_scaled(c->st, mm, c->HS + mm, A, 1.0 / tau, A);
+      } else {
+        OMM_CUDA_TRY(cudaMemcpyAsync(A, c->HS + mm, mm * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+      }
+      spd_inverse(c->st, m, A, c->P, work, c->info_dev);
+    }
+    dev_alloc(&c->C, nm);
+    dev_alloc(&c->Dir, nm);
+    dev_alloc(&c->G, nm);
+    dev_alloc(&c->Gold, nm);
+    dev_alloc(&c->PG, nm);
+    dev_alloc(&c->Y4, 4 * nm);
+    dev_alloc(&c->SWHW, 2L * n * n);
+    dev_alloc(&c->Proj, 4L * n * n);
+    dev_alloc(&c->nn, (size_t)n * n);
+    dev_alloc(&c->part, (size_t)kReduceBlocks * 4);
+    dev_alloc(&c->part2, (size_t)traces_blocks(n) * kNumTraces);
+    if (o.precision == OMM_PREC_MIXED) c->mixed = mixed_create(c->st, m, n, c->HS, c->P);
+    OMM_CUDA_TRY(cudaEventRecord(c->ev[1], c->st));
+    int info = 0;
+    OMM_CUDA_TRY(cudaMemcpyAsync(&info, c->info_dev, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(c->st));
+    c->ms_setup = elapsed(c->ev[0], c->ev[1]);
+    dev_free(A);
+    dev_free(work);
+    A = work = nullptr;
+    if (info != 0) {
+      destroy(c);
+      return fail(OMM_ERR_NOT_SPD, "omm_create: S + T/tau is not positive definite (pivot " +
+                                       std::to_string(info) + ")");
+    }
+  } catch (const std::bad_alloc&) {
+    dev_free(A);
+    dev_free(work);
+    destroy(c);
+    return fail(OMM_ERR_OOM, "omm_create: device allocation failed");
+  } catch (const CudaError& e) {
+    dev_free(A);
+    dev_free(work);
+    destroy(c);
+    return fail(OMM_ERR_CUDA, std::string("omm_create: ") + e.what + ": " + cudaGetErrorString(e.err));
+  }
+  *out = c;
+  return OMM_OK;
+}
+
+omm_status omm_update_H(omm_ctx* c, const double* H) {
+  if (!c || !H) return fail(OMM_ERR_ARG, "omm_update_H: NULL argument");
+  try {
+    const long mm = (long)c->m * c->m;
+    copy_in(c->HS, H, mm, c->st);
+    launch_axpby_shift(c->st, mm, c->HS, c->HS + mm, c->eta, c->HS);
+    if (c->mixed) mixed_update_H(c->mixed, c->st, c->HS);
+    OMM_CUDA_TRY(cudaStreamSynchronize(c->st));
+    c->solved = false;
+  } catch (const CudaError& e) {
+    return fail(OMM_ERR_CUDA, std::string("omm_update_H: ") + e.what + ": " + cudaGetErrorString(e.err));
+  }
+  return OMM_OK;
+}
+
+omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, double* D, omm_info* info) {
+  if (!c || !C0) return fail(OMM_ERR_ARG, "omm_solve: NULL argument");
+  omm_info inf{};
+  omm_status result = OMM_OK;
+  const int m = c->m, n = c->n;
+  const long nm = (long)n * m;
+  c->solved = false;
+  try {
+    copy_in(c->C, C0, nm, c->st);
+    reset_loop_flags(c, true);
+    write_scalars(c);
+    const bool mixed = c->mixed != nullptr;
+    double flop = 0.0, flop_tc = 0.0;
+    const double per_it = 6.0 * m * (double)m * n + 12.0 * (double)m * n * n;
+    const double per_state = 4.0 * m * (double)m * n + 8.0 * (double)m * n * n;
+    double ms_iter = 0.0, ms_ref = 0.0;
+    int fp64_iters = 0, refinements = 0;
+    int iter_total = 0;
+    double g_ref = -1.0;  // max|G| at the last float64 recompute
+    bool energy_stop = false;
+    // Outer loop: float64 recompute of the state (refinement / certificate),
+    // then line searches until converged, halted or capped.
+    for (int round = 0;; ++round) {
+      OMM_CUDA_TRY(cudaEventRecord(c->ev[0], c->st));
+      recompute_state_fp64(c);
+      flop += per_state;
+      OMM_CUDA_TRY(cudaEventRecord(c->ev[1], c->st));
+      read_scalars(c);
+      ms_ref += elapsed(c->ev[0], c->ev[1]);
+      Scalars& h = *c->sc_host;
+      if (!std::isfinite(h.gmax) || !std::isfinite(h.E)) {
+        result = OMM_ERR_NONFINITE;
+        break;
+      }
+      if (h.gmax < c->opts.tol_grad || energy_stop) break;  // certified (or Eq. 18 met)
+      if (round > 0) ++refinements;
+      if (iter_total >= c->opts.max_iter) {
+        result = OMM_ERR_NO_CONVERGENCE;
+        break;
+      }
+      if (round > 64) {
+        result = OMM_ERR_NO_CONVERGENCE;
+        break;
+      }
+      g_ref = h.gmax;
+      const double E_keep = h.E, g_keep = h.gmax;
+      reset_loop_flags(c, false);
+      h.E = E_keep;
+      h.gmax = g_keep;
+      h.iter = iter_total;
+      h.halt_gmax = mixed ? std::max(c->opts.tol_grad * 0.5, g_ref * c->opts.refine_ratio) : 0.0;
+      write_scalars(c);
+      OMM_CUDA_TRY(cudaEventRecord(c->ev[2], c->st));
+      int prev_iter = iter_total;
+      for (;;) {
+        for (int k = 0; k < c->opts.check_every; ++k) {
+          if (mixed) mixed_iterate(c->mixed, c->st, c->sc, c->C, c->Dir, c->G, c->Gold, c->PG,
+                                   c->Y4, c->SWHW, c->Proj, c->part, c->part2, c->HS, c->P,
+                                   c->precond);
+          else iterate_fp64(c);
+        }
+        read_scalars(c);
+        if (h.done || h.halt) break;
+      }
+      OMM_CUDA_TRY(cudaEventRecord(c->ev[3], c->st));
+      OMM_CUDA_TRY(cudaEventSynchronize(c->ev[3]));
+      ms_iter += elapsed(c->ev[2], c->ev[3]);
+      const int did = h.iter - prev_iter;
+      iter_total = h.iter;
+      if (mixed) flop_tc += 3.0 * per_it * did; else { flop += per_it * did; fp64_iters += did; }
+      if (mixed) flop += per_it * did;
+      if (h.status != 0) {
+        result = (omm_status)h.status;
+        if (result != OMM_ERR_NO_CONVERGENCE) break;
+        // iteration cap: certify what we have, report no convergence
+        recompute_state_fp64(c);
+        read_scalars(c);
+        break;
+      }
+      // done (device-side convergence) or a refinement request: recompute and test
+      if (h.done && h.stop_reason == 2) energy_stop = true;
+    }
+    Scalars& h = *c->sc_host;
+    inf.iterations = iter_total;
+    inf.iterations_fp64 = fp64_iters;
+    inf.refinements = refinements;
+    inf.Etilde = h.E;
+    inf.E = h.E + 2.0 * n * c->eta;
+    inf.gmax = h.gmax;
+    inf.ms_setup = c->ms_setup;
+    inf.ms_iterate = ms_iter;
+    inf.ms_refine = ms_ref;
+    if (result == OMM_OK || result == OMM_ERR_NO_CONVERGENCE) {
+      if (Cout) OMM_CUDA_TRY(cudaMemcpyAsync(Cout, c->C, nm * sizeof(double), cudaMemcpyDefault, c->st));
+      if (E) *E = inf.E;
+    }
+    if (result == OMM_OK) {
+      c->solved = true;
+      if (D) {
+        OMM_CUDA_TRY(cudaEventRecord(c->ev[0], c->st));
+        double* tgt = D;
+        if (!is_device_ptr(D)) {
+          ensure_mm(c);
+          tgt = c->mm;
+        }
+        density_into(c, tgt);
+        if (tgt != D)
+          OMM_CUDA_TRY(cudaMemcpyAsync(D, tgt, (size_t)m * m * sizeof(double), cudaMemcpyDefault, c->st));
+        flop += 2.0 * n * (double)n * m + 2.0 * m * (double)m * n;
+        OMM_CUDA_TRY(cudaEventRecord(c->ev[1], c->st));
+        OMM_CUDA_TRY(cudaEventSynchronize(c->ev[1]));
+        inf.ms_outputs = elapsed(c->ev[0], c->ev[1]);
+      }
+    }
+    OMM_CUDA_TRY(cudaStreamSynchronize(c->st));
+    inf.gemm_flop = flop;
+    inf.gemm_flop_tc = flop_tc;
+  } catch (const std::bad_alloc&) {
+    result = OMM_ERR_OOM;
+    set_last_error("omm_solve: device allocation failed");
+  } catch (const CudaError& e) {
+    result = OMM_ERR_CUDA;
+    set_last_error(std::string("omm_solve: ") + e.what + ": " + cudaGetErrorString(e.err));
+  }
+  inf.status = result;
+  if (info) *info = inf;
+  if (result != OMM_OK && result != OMM_ERR_CUDA && result != OMM_ERR_OOM)
+    set_last_error(std::string("omm_solve: ") + omm_status_str(result));
+  return result;
+}
+
+omm_status omm_backward(omm_ctx* c, double* dEdH, double* dEdS) {
+  if (!c) return fail(OMM_ERR_ARG, "omm_backward: NULL context");
+  if (!c->solved) return fail(OMM_ERR_STATE, "omm_backward: no converged solve");
+  try {
+    const size_t bytes = (size_t)c->m * c->m * sizeof(double);
+    double* tH = dEdH;
+    double* tS = dEdS;
+    if (dEdH && !is_device_ptr(dEdH)) { ensure_mm(c); tH = c->mm; }
+    if (dEdH) {
+      density_into(c, tH);
+      if (tH != dEdH) OMM_CUDA_TRY(cudaMemcpyAsync(dEdH, tH, bytes, cudaMemcpyDefault, c->st));
+    }
+    if (dEdS) {
+      if (!is_device_ptr(dEdS)) { ensure_mm(c); tS = c->mm; }
+      density_into(c, tS);
+      minus_edm_into(c, tS);
+      if (tS != dEdS) OMM_CUDA_TRY(cudaMemcpyAsync(dEdS, tS, bytes, cudaMemcpyDefault, c->st));
+    }
+    OMM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  } catch (const std::bad_alloc&) {
+    return fail(OMM_ERR_OOM, "omm_backward: device allocation failed");
+  } catch (const CudaError& e) {
+    return fail(OMM_ERR_CUDA, std::string("omm_backward: ") + e.what + ": " + cudaGetErrorString(e.err));
+  }
+  return OMM_OK;
+}
+
+void omm_free(omm_ctx* c) { destroy(c); }
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// Internal declarations shared by the translation units of the OMM library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+namespace omm {
+
+// Device-resident control block of one solve. Every iteration kernel reads
+// the flags first and returns at once when `done` or `halt` is set, so a
+// batch of line searches enqueued ahead of a host poll (or replayed from a
+// CUDA graph) turns into no-ops after convergence.
+struct Scalars {
+  int done;          // converged: remaining iteration kernels are no-ops
+  int halt;          // stop for the host (error, iteration cap, refinement request)
+  int status;        // omm_status set by the device (0 = ok)
+  int iter;          // line searches completed
+  int have_dir;      // a previous search direction exists
+  int restart;       // next direction is the preconditioned steepest descent
+  int stop_pending;  // Eq. 18 met at the last line search: stop at the next check
+  int max_iter;
+  int stop_reason;   // 1: gradient test met, 2: energy test (Eq. 18) met
+  int pad_;
+  double E;          // current shifted functional E~
+  double gmax;       // max |G| of the current gradient
+  double gpg;        // <G, P G>
+  double gpg_old;    // <G_old, P G_old>
+  double gopg;       // <G_old, P G>
+  double gdo;        // <G, Delta_old>
+  double beta;       // Polak-Ribiere coefficient of the current direction
+  double x;          // line-search step
+  double alpha[5];   // quartic coefficients of the last line search
+  double tol_grad;
+  double e_tol;
+  double halt_gmax;  // mixed precision: request a float64 refinement below this max|G|
+  double trace[12];  // last trace products (debug / tests)
+};
+
+constexpr int kReduceBlocks = 512;   // fixed grid of the gradient reductions (deterministic sums)
+constexpr int kNumTraces = 11;
+
+// ------------------------------------------------------------------ error handling
+struct CudaError {
+  cudaError_t err;
+  const char* what;
+};
+
+void set_last_error(const std::string& msg);
+const char* last_error_cstr();
+
+#define OMM_CUDA_TRY(call)                                                   \
+  do {                                                                       \
+    cudaError_t e__ = (call);                                                \
+    if (e__ != cudaSuccess) throw ::omm::CudaError{e__, #call};              \
+  } while (0)
+
+// ------------------------------------------------------------------ float64 GEMM
+// C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b], row-major, for b < batch.
+// op(A) is M x K: A[i*lda + k] (transA = 0) or A[k*lda + i] (transA = 1).
+// op(B) is K x N: B[k*ldb + j] (transB = 0) or B[j*ldb + k] (transB = 1).
+// tri bit 0: compute only tiles that touch the lower triangle (i >= j);
+// tri bit 1: start the K loop at max(tile row, tile col) (both operands lower-
+// triangular in the contracted index, as in L^-T L^-1).
+// `skip`: device flag pair (done, halt); when either is set the kernel returns.
+enum { kTriLower = 1, kTriKStart = 2 };
+void dgemm(cudaStream_t st, int transA, int transB, int M, int N, int K, double alpha,
+           const double* A, long lda, long strideA, const double* B, long ldb, long strideB,
+           double beta, double* C, long ldc, long strideC, int batch = 1, int tri = 0,
+           const int* skip = nullptr);
+
+// ------------------------------------------------------------------ Cholesky inverse
+// P = A^-1 for symmetric positive definite A (m x m, row-major, device). A is
+// overwritten. `work` needs m*m + m*64*... doubles (see cholesky.cu). info_dev
+// receives 0 or the 1-based column of the first non-positive pivot.
+size_t spd_inverse_workspace(int m);
+void spd_inverse(cudaStream_t st, int m, double* A, double* P, double* work, int* info_dev);
+
+// ------------------------------------------------------------------ iteration kernels
+void launch_axpby_shift(cudaStream_t st, long count, const double* H, const double* S, double eta,
+                        double* Ht);                      // Ht = H - eta S
+void launch_add_scaled(cudaStream_t st, long count, const double* S, const double* T, double inv_tau,
+                       double* A);                       // A = S + T*inv_tau
+void launch_grad_reduce(cudaStream_t st, long count, const double* G, const double* PG,
+                        const double* Gold, const double* Dir, double* part, const Scalars* sc);
+void launch_control_direction(cudaStream_t st, Scalars* sc, const double* part, int mixed);
+void launch_direction(cudaStream_t st, long count, const double* PG, double* Dir, const Scalars* sc);
+void launch_traces(cudaStream_t st, int n, const double* SWHW, const double* Proj, double* part,
+                   const Scalars* sc);
+int traces_blocks(int n);
+void launch_control_linesearch(cudaStream_t st, Scalars* sc, const double* part, int nblocks);
+void launch_update_state(cudaStream_t st, int n, long m, double* C, double* Y4, const double* Dir,
+                         double* G, double* Gold, const Scalars* sc);
+void launch_update_subspace(cudaStream_t st, int n, double* SWHW, const double* Proj,
+                            const Scalars* sc);
+void launch_scale_copy(cudaStream_t st, long count, const double* src, double a, double* dst,
+                       const Scalars* sc);              // dst = a*src (skipped when done/halt)
+void launch_functional(cudaStream_t st, int n, const double* SWHW, double* part);  // E~ partials
+void launch_finish_functional(cudaStream_t st, Scalars* sc, const double* part, int nblocks);
+void launch_gmax(cudaStream_t st, long count, const double* G, double* part);
+void launch_finish_gmax(cudaStream_t st, Scalars* sc, const double* part);
+void launch_two_i_minus(cudaStream_t st, int n, const double* SW, long ldsw, double* out);  // 2I - S_W
+void launch_symmetrize_lower(cudaStream_t st, int m, double* A);  // A[j,i] = A[i,j], i > j
+void launch_fill(cudaStream_t st, long count, double v, double* dst);
+
+// Device-side line minimum (first local minimum of the quartic along x > 0).
+__host__ __device__ int quartic_first_minimum(const double a[5], double* x_out);
+void launch_line_minimum(cudaStream_t st, const double* a, double* x, int* status);
+
+}  // namespace omm

@@ -1,0 +1,319 @@
+// BF16 tensor-core GEMM for sm_103a: tcgen05.mma with the accumulator in
+// tensor memory (TMEM), operands moved global -> shared by TMA
+// (cp.async.bulk.tensor, 128-byte swizzle), a 4-stage mbarrier pipeline and
+// warp specialisation:
+//   warp 0      TMA producer (one lane)
+//   warp 1      TMEM allocation and the MMA issuer (one lane)
+//   warps 2-5   epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator,
+//               C = alpha * acc + beta * C written in float64
+// Each CTA computes one 128 x 256 tile of C = A B^T with A (M x K) and
+// B (N x K) both K-major bf16. "Split" operands x = x_hi + x_lo are
+// contracted as A_hi B_hi + A_hi B_lo + A_lo B_hi (three passes over K into
+// the same accumulator), which keeps about 16 significant bits.
+//
+// Every wait on an mbarrier is bounded (globaltimer, 2 s): on expiry the
+// kernel records an error code, stops issuing work and frees its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "omm_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace omm {
+namespace tc {
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 256;
+constexpr int NTHREADS = 192;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: false after WAIT_NS without completion
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 0 && globaltimer() - t0 > WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)(16 >> 4) << 16;                 // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset
+  d |= (uint64_t)1 << 46;                         // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                         // layout: SWIZZLE_128B
+  return d;
+}
+
+// instruction descriptor, kind::f16: D f32, A/B bf16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
+                       const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
+                       int K, int npass, Epilogue ep) {
+  if (ep.skip != nullptr && (ep.skip[0] | ep.skip[1])) return;  // uniform: before any resource use
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  // bars[0..S) full, bars[S..2S) empty, bars[2S] accumulator ready
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int nkb = (K + BK - 1) / BK;
+  const int total = npass * nkb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[STAGES + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[2 * STAGES]), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    prefetch_tmap(&mA_hi);
+    prefetch_tmap(&mB_hi);
+    if (npass > 1) {
+      prefetch_tmap(&mA_lo);
+      prefetch_tmap(&mB_lo);
+    }
+    for (int t = 0; t < total; ++t) {
+      const int s = t % STAGES, r = t / STAGES;
+      if (!mbar_wait(smem_u32(&bars[STAGES + s]), (r & 1) ^ 1)) {
+        *abort_flag = 1;
+        atomicCAS(ep.err, 0, 1);
+        break;
+      }
+      if (*abort_flag) break;
+      const int pass = t / nkb, kb = t % nkb;
+      const CUtensorMap* a = (pass == 2) ? &mA_lo : &mA_hi;
+      const CUtensorMap* b = (pass == 1) ? &mB_lo : &mB_hi;
+      const uint32_t full = smem_u32(&bars[s]);
+      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+      mbar_expect_tx(full, STAGE_BYTES);
+      tma_load_2d(sa, a, full, kb * BK, m0);
+      tma_load_2d(sa + A_BYTES, b, full, kb * BK, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    int t = 0;
+    for (; t < total; ++t) {
+      const int s = t % STAGES, r = t / STAGES;
+      if (!mbar_wait(smem_u32(&bars[s]), r & 1)) {
+        *abort_flag = 1;
+        atomicCAS(ep.err, 0, 2);
+        break;
+      }
+      if (*abort_flag) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k) {
+        umma_bf16(tmem, smem_desc(sa + k * 32), smem_desc(sb + k * 32), idesc, (t > 0 || k > 0) ? 1u : 0u);
+      }
+      umma_commit(smem_u32(&bars[STAGES + s]));  // stage s is free once these MMAs have read it
+    }
+    umma_commit(smem_u32(&bars[2 * STAGES]));    // accumulator complete (also on abort: drains MMAs)
+  } else if (warp >= 2) {
+    // ---------------- epilogue
+    const bool ok = mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
+    if (!ok) atomicCAS(ep.err, 0, 3);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int lane_base = (warp & 3) * 32;
+    const int row = m0 + lane_base + lane;
+    const bool write = ok && !*abort_flag;
+#pragma unroll 1
+    for (int c = 0; c < BN / 32; ++c) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(c * 32), v);
+      if (!write || row >= ep.M) continue;
+      const int col0 = n0 + c * 32;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = col0 + j;
+        if (col >= ep.N) break;
+        const long blk = col / ep.split_cols;
+        double* p = ep.C + blk * ep.split_stride + (long)row * ep.ldc + (col - blk * ep.split_cols);
+        const double a = ep.alpha * (double)v[j];
+        *p = (ep.beta == 0.0) ? a : fma(ep.beta, *p, a);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  if (!g_encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    OMM_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) throw CudaError{cudaErrorNotSupported, "cuTensorMapEncodeTiled"};
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  return g_encode;
+}
+
+}  // namespace
+
+// Row-major bf16 matrix rows x cols (leading dimension ld elements, ld*2 a
+// multiple of 16 bytes, base 16-byte aligned) as a TMA map with box
+// {BK, box_rows} and 128-byte swizzle.
+TensorMap make_map(const __nv_bfloat16* base, long rows, long cols, long ld, int box_rows) {
+  TensorMap tm;
+  static_assert(sizeof(TensorMap) == sizeof(CUtensorMap), "TensorMap must hold a CUtensorMap");
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15))
+    throw CudaError{cudaErrorInvalidValue, "make_map: operand not 16-byte aligned"};
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encoder()(reinterpret_cast<CUtensorMap*>(&tm), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                         const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled"};
+  return tm;
+}
+
+Operand make_operand(const __nv_bfloat16* hi, const __nv_bfloat16* lo, long rows, long cols, long ld, bool is_a) {
+  Operand o;
+  const int box = is_a ? BM : BN;
+  o.hi = make_map(hi, rows, cols, ld, box);
+  o.lo = make_map(lo ? lo : hi, rows, cols, ld, box);
+  o.rows = rows;
+  o.cols = cols;
+  return o;
+}
+
+void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, int npass, const Epilogue& ep) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      SMEM_BYTES));
+    attr_set = true;
+  }
+  dim3 grid((unsigned)((ep.N + BN - 1) / BN), (unsigned)((ep.M + BM - 1) / BM));
+  const CUtensorMap* a_hi = reinterpret_cast<const CUtensorMap*>(&A.hi);
+  const CUtensorMap* a_lo = reinterpret_cast<const CUtensorMap*>(&A.lo);
+  const CUtensorMap* b_hi = reinterpret_cast<const CUtensorMap*>(&B.hi);
+  const CUtensorMap* b_lo = reinterpret_cast<const CUtensorMap*>(&B.lo);
+  gemm_bf16_split_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(*a_hi, *a_lo, *b_hi, *b_lo, K, npass, ep);
+  OMM_CUDA_TRY(cudaGetLastError());
+}
+
+int tile_m() { return BM; }
+int tile_n() { return BN; }
+
+}  // namespace tc
+}  // namespace omm

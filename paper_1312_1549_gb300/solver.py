@@ -1,0 +1,152 @@
+"""Python binding of the OMM library: argument marshalling only.
+
+Tensors are passed to the C ABI as raw pointers; every step of the solve runs
+in the CUDA library. torch supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import math
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("expected a contiguous float64 tensor")
+        return ct.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a C-contiguous float64 array")
+        return ct.c_void_p(x.ctypes.data)
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, torch.cuda.Stream):
+        return ct.c_void_p(stream.cuda_stream)
+    return ct.c_void_p(int(stream))
+
+
+class OMMSolver:
+    """One (H, S, T, eta, tau) problem: omm_create / omm_solve / omm_backward / omm_free.
+
+    H, S, T: m x m float64 (torch CUDA/CPU tensors or numpy arrays).
+    n: number of Wannier functions. precision: "fp64" or "mixed".
+    """
+
+    def __init__(self, H, S, T, n, eta, tau, precision="fp64", stream=None, max_iter=0,
+                 tol_grad=1e-9, e_tol=0.0, refine_ratio=0.0, precondition=True, check_every=0):
+        lib = N.lib()
+        m = int(H.shape[0])
+        self.m, self.n, self.eta, self.tau = m, int(n), float(eta), float(tau)
+        self.stream = stream
+        opts = N.OmmOpts(precision=N.PREC_MIXED if precision == "mixed" else N.PREC_FP64,
+                         max_iter=int(max_iter), no_precondition=0 if precondition else 1,
+                         check_every=int(check_every), tol_grad=float(tol_grad),
+                         e_tol=float(e_tol), refine_ratio=float(refine_ratio))
+        self._keep = (H, S, T)
+        h = ct.c_void_p()
+        tau_arg = math.inf if tau is None else float(tau)
+        N.check(lib.omm_create(m, self.n, _ptr(H), _ptr(S), _ptr(T), self.eta, tau_arg,
+                               ct.byref(opts), _stream_handle(stream), ct.byref(h)), "omm_create")
+        self._keep = None
+        self._h = h
+        self.info = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().omm_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, C0, want_D=False, C_out=None, D_out=None, raise_on_error=True):
+        """Minimise from C0 (n x m). Returns (C, E, D or None, info dict)."""
+        like_cuda = isinstance(C0, torch.Tensor) and C0.is_cuda
+        if C_out is None:
+            if isinstance(C0, torch.Tensor):
+                C_out = torch.empty_like(C0)
+            else:
+                C_out = np.empty_like(C0)
+        if want_D and D_out is None:
+            if like_cuda:
+                D_out = torch.empty((self.m, self.m), dtype=torch.float64, device=C0.device)
+            else:
+                D_out = np.empty((self.m, self.m))
+        E = ct.c_double(0.0)
+        info = N.OmmInfo()
+        rc = N.lib().omm_solve(self._h, _ptr(C0), _ptr(C_out), ct.byref(E),
+                               _ptr(D_out) if want_D else None, ct.byref(info))
+        self.info = info.as_dict()
+        if raise_on_error:
+            N.check(rc, "omm_solve")
+        return C_out, E.value, (D_out if want_D else None), self.info
+
+    def backward(self, dEdH=None, dEdS=None, device=None):
+        """(dE/dH, dE/dS) = (D, -EDM) at the last converged solve (m x m)."""
+        dev = device if device is not None else torch.device("cuda")
+        if dEdH is None:
+            dEdH = torch.empty((self.m, self.m), dtype=torch.float64, device=dev)
+        if dEdS is None:
+            dEdS = torch.empty((self.m, self.m), dtype=torch.float64, device=dev)
+        N.check(N.lib().omm_backward(self._h, _ptr(dEdH), _ptr(dEdS)), "omm_backward")
+        return dEdH, dEdS
+
+    def update_H(self, H):
+        N.check(N.lib().omm_update_H(self._h, _ptr(H)), "omm_update_H")
+
+
+# ------------------------------------------------------------------ step-level entry points
+def dgemm(transA, transB, A, B, C, alpha=1.0, beta=0.0, stream=None):
+    M = C.shape[0]
+    Ncols = C.shape[1]
+    K = A.shape[0] if transA else A.shape[1]
+    N.check(N.lib().omm_kernel_dgemm(int(transA), int(transB), M, Ncols, K, float(alpha), _ptr(A),
+                                     A.stride(0), _ptr(B), B.stride(0), float(beta), _ptr(C),
+                                     C.stride(0), _stream_handle(stream)), "omm_kernel_dgemm")
+    return C
+
+
+def spd_inverse(A, P=None, stream=None):
+    m = A.shape[0]
+    if P is None:
+        P = torch.empty_like(A)
+    info = ct.c_int(0)
+    N.check(N.lib().omm_kernel_spd_inverse(m, _ptr(A), _ptr(P), ct.byref(info), _stream_handle(stream)),
+            "omm_kernel_spd_inverse")
+    return P
+
+
+def line_minimum(alpha):
+    a = (ct.c_double * 5)(*[float(v) for v in alpha])
+    x = ct.c_double(0.0)
+    rc = N.lib().omm_kernel_line_minimum(a, ct.byref(x))
+    return x.value, rc
+
+
+def quartic_coefficients(SWHW, Proj, E, stream=None):
+    n = SWHW.shape[0]
+    out = (ct.c_double * 5)()
+    N.check(N.lib().omm_kernel_quartic_coefficients(n, _ptr(SWHW), _ptr(Proj), float(E), out,
+                                                    _stream_handle(stream)),
+            "omm_kernel_quartic_coefficients")
+    return np.array(list(out))
