@@ -1,0 +1,300 @@
+#!/usr/bin/env python
+"""Time-to-solution of the OMM solve on GB300 (and its oracle on the host cores).
+
+One step = one whole solve of the Si512 DZP-like workload (m = 6656 basis
+functions, n = 1024 Wannier functions): omm_create (shift, float64 Cholesky
+inverse of S + T/tau, operand splits) + omm_solve to max|G| < 1e-9
+(certified in float64) + the density matrix D. Inputs are resident in HBM
+when the timed region starts; H, S, T (354 MB each) are larger than L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config 2] [--precision mixed|fp64]
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "OMM time-to-solution & GEMM TFLOP/s, mixed vs FP64 GPU at |ΔE|/|E|≤1e-9"
+WORKLOADS = {
+    1: "si64_sz: Si 64-atom diamond, sp single-zeta, m=256, n=128, tau=5 Ha, eta=HOMO+0.1 Ha, |G|inf<1e-9",
+    2: "si512_dzp: Si 512-atom diamond, DZP-like 13 orbitals/atom, m=6656, n=1024, tau=5 Ha, "
+       "eta=HOMO+0.1 Ha, |G|inf<1e-9",
+    3: "water256_dzp: 256 H2O at 1 g/cm3, DZP-like 23 orbitals/molecule, m=5888, n=1024, tau=5 Ha, "
+       "eta=HOMO+0.1 Ha, |G|inf<1e-9",
+}
+# Line searches the float64 solve takes on each workload from its seeded C0
+# (measured with the float64 GPU path); used to extrapolate bounded oracle samples.
+FP64_LINE_SEARCHES = {1: 43, 2: 160, 3: 160}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if gpus > 1 and world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return rank, world, local, dist
+    return rank, world, local, None
+
+
+def build_problem(config):
+    from synth import configs
+    return configs.CONFIGS[config]()
+
+
+def cpu_oracle_sample(p, config, n_iter=2):
+    """Oracle (plain float64 numpy OMM) on the host cores: setup + n_iter line searches."""
+    from oracle import omm as oomm
+    t0 = time.perf_counter()
+    oomm.solve(p.H, p.S, p.T, p.eta, p.tau, p.C0, tol_grad=0.0, max_iter=0, want_matrices=False)
+    t_base = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oomm.solve(p.H, p.S, p.T, p.eta, p.tau, p.C0, tol_grad=0.0, max_iter=n_iter, want_matrices=False)
+    t_iter = (time.perf_counter() - t0 - t_base) / n_iter
+    return t_base, max(t_iter, 0.0)
+
+
+def run_reference(args):
+    """--impl reference: the oracle as it stands on the host cores, bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p = build_problem(args.config)
+    iters = FP64_LINE_SEARCHES[args.config]
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are not repeated
+    times = []
+    for _ in range(args.steps):
+        t_base, t_iter = cpu_oracle_sample(p, args.config)
+        times.append(t_base + iters * t_iter)
+    value = statistics.mean(times)
+    cores = os.cpu_count()
+    sample = (f"per step: oracle setup + initial state + certificate, plus 2 line searches, timed; "
+              f"extrapolated to {iters} line searches")
+    out = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": 0, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": WORKLOADS[args.config], "l2": "inputs larger than L2"},
+           "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-exact-check", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    from paper_1312_1549_gb300 import build as _build
+    _build.build()
+    from paper_1312_1549_gb300 import solver as S
+
+    rank, world, local, dist = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = build_problem(args.config)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    H, Sm, T, C0 = t(p.H), t(p.S), t(p.T), t(p.C0)
+    stream = torch.cuda.Stream(device=dev)
+    Cbuf = torch.empty_like(C0)
+    Dbuf = torch.empty((p.m, p.m), dtype=torch.float64, device=dev)
+
+    def step(precision=args.precision, profile=True):
+        with S.OMMSolver(H, Sm, T, p.n, p.eta, p.tau, precision=precision, stream=stream,
+                         profile=profile) as s:
+            _, E, _, info = s.solve(C0, want_D=True, C_out=Cbuf, D_out=Dbuf)
+        return E, info
+
+    for _ in range(args.warmup):
+        step()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    energies = []
+    launches0 = S.launch_count()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            E, info = step()
+            infos.append(info)
+            energies.append(E)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = S.launch_count() - launches0
+    clocks = clk.summary()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+        dist.barrier()
+    if rank != 0:
+        return 0
+
+    peaks, peak_kind = load_peaks()
+    main_ms = sum(i["ms_main_gemm"] for i in infos)
+    main_flop = sum(i["main_gemm_flop"] for i in infos)
+    main_launches = sum(i["main_gemm_launches"] for i in infos)
+    iters = infos[-1]["iterations"]
+    logical = statistics.mean(i["gemm_flop"] for i in infos)
+    it_ms = statistics.mean(i["ms_iterate"] for i in infos)
+    mixed = args.precision == "mixed"
+    achieved = main_flop / (main_ms * 1e-3) / 1e12 if main_ms > 0 else None
+    peak = peaks["bf16_tflops_sustained"] if mixed else None
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+                "kernel": "gemm_bf16_split_kernel (tcgen05, 3-term split)" if mixed else "dgemm_kernel (DFMA)",
+                "peak_source": f"bf16_tflops_sustained of {peak_kind} MEASURED_PEAKS" if mixed else
+                "float64 DFMA (no measured peak; see fp64 fields)",
+                "launches": main_launches, "avg_launch_ms": main_ms / max(main_launches, 1)}
+    out = {"metric": METRIC, "value": ms * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "bf16x3+f64" if mixed else "f64", "data": "synthetic",
+           "config": {"workload": WORKLOADS[args.config], "precision": args.precision,
+                      "l2": "inputs larger than L2 (H, S, T are m*m*8 bytes each)",
+                      "parallelism": "replicas only" if world > 1 else "1 GPU"},
+           "line_searches": iters, "refinements": infos[-1]["refinements"],
+           "E": energies[-1], "gmax": infos[-1]["gmax"],
+           "ms_setup": statistics.mean(i["ms_setup"] for i in infos),
+           "ms_iterate": it_ms, "ms_refine": statistics.mean(i["ms_refine"] for i in infos),
+           "gemm_tflops_logical": logical / (ms * 1e-3) / 1e12,
+           "gemm_tflops_logical_in_iterations": (infos[-1]["gemm_flop"] and
+                                                 (iters * (6.0 * p.m * p.m * p.n + 12.0 * p.m * p.n * p.n))
+                                                 / (it_ms * 1e-3) / 1e12),
+           "roofline": roofline, "gpu_launches": launches, "clocks": clocks}
+    if not args.no_exact_check and args.config in (1, 2, 3):
+        from oracle import exact
+        ex = exact.exact_minimum(p.H, p.S, p.n, want_matrices=False)
+        out["rel_err_E_vs_exact"] = abs(energies[-1] - ex["E"]) / abs(ex["E"])
+    if not args.no_fp64_compare and mixed:
+        E64, i64 = step(precision="fp64", profile=True)
+        out["fp64_gpu"] = {"time_to_solution_s": (i64["ms_setup"] + i64["ms_iterate"] + i64["ms_refine"] +
+                                                  i64["ms_outputs"]) * 1e-3,
+                           "line_searches": i64["iterations"],
+                           "dgemm_tflops": (i64["main_gemm_flop"] / (i64["ms_main_gemm"] * 1e-3) / 1e12
+                                            if i64["ms_main_gemm"] > 0 else None),
+                           "E": E64, "speedup_mixed_over_fp64": None}
+        out["fp64_gpu"]["speedup_mixed_over_fp64"] = out["fp64_gpu"]["time_to_solution_s"] / (ms * 1e-3)
+    if not args.no_e2e:
+        Hh, Sh, Th, C0h = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (p.H, p.S, p.T, p.C0))
+        Ch = torch.empty_like(C0h).pin_memory()
+        Dh = torch.empty((p.m, p.m), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with S.OMMSolver(Hh, Sh, Th, p.n, p.eta, p.tau, precision=args.precision, stream=stream) as s:
+            _, Ee, _, _ = s.solve(C0h, want_D=True, C_out=Ch, D_out=Dh)
+        te = time.perf_counter() - t0
+        out["e2e"] = {"value": te, "unit": "s", "h2d_bytes_per_step": (3 * p.m * p.m + p.n * p.m) * 8,
+                      "d2h_bytes_per_step": (p.n * p.m + p.m * p.m + 1) * 8,
+                      "api": "omm_create + omm_solve with pinned host H, S, T, C0 and host C, D, E"}
+    if not args.no_cpu_baseline and world == 1:
+        t_base, t_iter = cpu_oracle_sample(p, args.config)
+        n_ls = FP64_LINE_SEARCHES[args.config]
+        out["cpu_baseline"] = {"value": t_base + n_ls * t_iter, "unit": "s", "cores": os.cpu_count(),
+                               "kind": "oracle",
+                               "sample": f"oracle setup + initial state + certificate ({t_base:.1f} s) and 2 "
+                                         f"line searches ({t_iter:.2f} s each) on this workload, "
+                                         f"extrapolated to {n_ls} line searches"}
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -82,6 +82,8 @@ typedef struct {
   double e_tol;         /* also stop when |2(E_new-E)/(E_new+E)| <= e_tol (Eq. 18); 0 -> off */
   double refine_ratio;  /* mixed: refine in float64 once max|G| fell by this factor since
                            the last float64 refinement; 0 -> 1e-4 */
+  int profile;          /* 1 -> time every launch of the line-search GEMM with CUDA events on
+                           the context's stream (omm_info.ms_main_gemm and friends) */
 } omm_opts;
 
 /* Per-solve report. */
@@ -99,6 +101,10 @@ typedef struct {
   double ms_outputs;    /* density matrix */
   double gemm_flop;     /* logical contraction flops of the solve (FP64-equivalent) */
   double gemm_flop_tc;  /* flops issued to the BF16 tensor cores (3 per logical in split form) */
+  double kernel_launches;    /* kernels launched by the library during the solve */
+  double ms_main_gemm;       /* with opts.profile: summed duration of the line-search GEMM launches */
+  double main_gemm_launches; /* with opts.profile: number of those launches */
+  double main_gemm_flop;     /* with opts.profile: flops they issued (tensor-core flops when mixed) */
 } omm_info;
 
 /* Create a solver context for one (H, S, T) and do the per-geometry setup:
@@ -146,6 +152,9 @@ const char* omm_status_str(omm_status s);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* omm_last_error(void);
+
+/* Number of GPU kernels this library has launched in the process so far. */
+unsigned long long omm_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -48,6 +48,18 @@ omm_status omm_kernel_line_minimum(const double* alpha, double* x);
 omm_status omm_kernel_quartic_coefficients(int n, const double* SWHW, const double* Proj, double E,
                                            double* alpha, void* stream);
 
+/* Tensor-core contraction of the mixed-precision path (Sec. 2.3, Table 1
+ * products, run on the BF16 tensor cores): C = alpha A B^T + beta C with A
+ * M x K and B N x K (row-major float64, contracted over their rows' K
+ * entries) and C M x N float64. A and B are split into bf16 pairs
+ * x = hi + lo (hi = bf16(x), lo = bf16(x - hi)); npass = 3 accumulates
+ * A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32 (about 2^-16 relative error per
+ * product), npass = 1 only A_hi B_hi. Scratch for the splits is allocated and
+ * freed inside the call. Errors: OMM_ERR_ARG, OMM_ERR_OOM, OMM_ERR_TIMEOUT
+ * (a bounded device wait expired), OMM_ERR_CUDA. */
+omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double* B, double alpha,
+                              double beta, double* C, int npass, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,7 @@ PREC_MIXED = 1
 class OmmOpts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("max_iter", ct.c_int), ("no_precondition", ct.c_int),
                 ("check_every", ct.c_int), ("tol_grad", ct.c_double), ("e_tol", ct.c_double),
-                ("refine_ratio", ct.c_double)]
+                ("refine_ratio", ct.c_double), ("profile", ct.c_int)]
 
 
 class OmmInfo(ct.Structure):
@@ -30,7 +30,9 @@ class OmmInfo(ct.Structure):
                 ("refinements", ct.c_int), ("E", ct.c_double), ("Etilde", ct.c_double),
                 ("gmax", ct.c_double), ("ms_setup", ct.c_double), ("ms_iterate", ct.c_double),
                 ("ms_refine", ct.c_double), ("ms_outputs", ct.c_double), ("gemm_flop", ct.c_double),
-                ("gemm_flop_tc", ct.c_double)]
+                ("gemm_flop_tc", ct.c_double), ("kernel_launches", ct.c_double),
+                ("ms_main_gemm", ct.c_double), ("main_gemm_launches", ct.c_double),
+                ("main_gemm_flop", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -57,10 +59,12 @@ _SIGNATURES = {
     "omm_free": (None, [_P]),
     "omm_status_str": (ct.c_char_p, [_I]),
     "omm_last_error": (ct.c_char_p, []),
+    "omm_launch_count": (ct.c_ulonglong, []),
     "omm_kernel_dgemm": (_I, [_I, _I, _I, _I, _I, _D, _P, _L, _P, _L, _D, _P, _L, _P]),
     "omm_kernel_spd_inverse": (_I, [_I, _P, _P, ct.POINTER(_I), _P]),
     "omm_kernel_line_minimum": (_I, [ct.POINTER(_D), ct.POINTER(_D)]),
     "omm_kernel_quartic_coefficients": (_I, [_I, _P, _P, _D, ct.POINTER(_D), _P]),
+    "omm_kernel_gemm_tc": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _P]),
 }
 
 # entry points declared in include/*.h, for the export check

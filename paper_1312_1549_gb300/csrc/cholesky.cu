@@ -101,7 +101,7 @@ void trtri_rec(cudaStream_t st, int m, double* Y, const Work& w, int r0, int r1)
     const int b = r1 - r0;
     copy_block_kernel<<<16, 256, 0, st>>>(b, w.Dinv + (long)(r0 / NB) * NB * NB, NB,
                                           Y + (long)r0 * m + r0, m);
-    OMM_CUDA_TRY(cudaGetLastError());
+    OMM_LAUNCH_CHECK();
     return;
   }
   const int mid = r0 + (nb_blocks / 2) * NB;
@@ -135,7 +135,7 @@ void spd_inverse(cudaStream_t st, int m, double* A, double* P, double* work, int
     const int b = (m - k < NB) ? (m - k) : NB;
     double* Akk = A + (long)k * m + k;
     potf2_inv_kernel<<<1, 256, 0, st>>>(Akk, m, b, w.Dinv + (long)kb * NB * NB, info_dev, k);
-    OMM_CUDA_TRY(cudaGetLastError());
+    OMM_LAUNCH_CHECK();
     const int r = m - k - b;
     if (r > 0) {
       double* A21 = A + (long)(k + b) * m + k;
@@ -149,7 +149,7 @@ void spd_inverse(cudaStream_t st, int m, double* A, double* P, double* work, int
     }
   }
   zero_upper_kernel<<<1024, 256, 0, st>>>(m, A);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
   // 2. Y = L^-1 in place
   trtri_rec(st, m, A, w, 0, m);
   // 3. P = Y^T Y (lower), mirrored

@@ -107,7 +107,7 @@ void dgemm(cudaStream_t st, int transA, int transB, int M, int N, int K, double 
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
   dgemm_kernel<<<grid, NT, 0, st>>>(transA, transB, M, N, K, alpha, A, lda, strideA, B, ldb,
                                      strideB, beta, C, ldc, strideC, tri, skip);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 
 }  // namespace omm

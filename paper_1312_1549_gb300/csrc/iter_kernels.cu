@@ -136,9 +136,20 @@ control_direction_kernel(Scalars* sc, const double* part, int mixed) {
     sc->done = 1;
     return;
   }
-  if (mixed && gmax < sc->halt_gmax) {
-    sc->halt = 1;  // refinement request; status stays 0
-    return;
+  if (mixed) {
+    // refinement request (status stays 0): the target of the round is met, or
+    // max|G| has stopped falling (the split-product noise floor is reached)
+    if (gmax < sc->halt_gmax) {
+      sc->halt = 1;
+      return;
+    }
+    if (gmax < 0.5 * sc->best_g) {
+      sc->best_g = gmax;
+      sc->best_it = sc->iter_round;
+    } else if (sc->iter_round - sc->best_it > sc->stall_window) {
+      sc->halt = 1;
+      return;
+    }
   }
   if (sc->iter >= sc->max_iter) {
     set_error(sc, 4 /* OMM_ERR_NO_CONVERGENCE */);
@@ -151,6 +162,7 @@ control_direction_kernel(Scalars* sc, const double* part, int mixed) {
     if (-gpg + beta * gdo >= 0.0) beta = 0.0;   // not a descent direction: restart
   }
   sc->beta = beta;
+  sc->gd = -gpg + beta * gdo;
   sc->gpg_old = gpg;
   sc->restart = 0;
 }
@@ -325,6 +337,11 @@ control_linesearch_kernel(Scalars* sc, const double* part, int nblocks) {
   double a[5];
   a[0] = sc->E;
   a[1] = 8.0 * t[0] - 4.0 * t[1] - 4.0 * t[2];
+  // Mixed precision: the slope alpha_1 = <G, Delta> (the exact directional
+  // derivative of Eq. 8 along Delta) is taken from the float64 reduction over
+  // G and Delta instead of the tensor-core traces, whose absolute error would
+  // hide its sign once |G| is small.
+  if (sc->mixed) a[1] = sc->gd;
   a[2] = 4.0 * t[3] - 2.0 * t[4] - 2.0 * t[5] - 4.0 * t[6] - 4.0 * t[7];
   a[3] = -4.0 * t[8] - 4.0 * t[9];
   a[4] = -2.0 * t[10];
@@ -336,6 +353,10 @@ control_linesearch_kernel(Scalars* sc, const double* part, int nblocks) {
   double x;
   if (quartic_first_minimum(a, &x) != 0) {
     sc->x = 0.0;
+    if (sc->mixed && sc->iter_round > 0) {
+      sc->halt = 1;  // split-product noise: refresh the state in float64 and retry
+      return;
+    }
     set_error(sc, 3 /* OMM_ERR_UNBOUNDED */);
     return;
   }
@@ -344,6 +365,7 @@ control_linesearch_kernel(Scalars* sc, const double* part, int nblocks) {
   sc->x = x;
   sc->E = Enew;
   sc->iter += 1;
+  sc->iter_round += 1;
   sc->have_dir = 1;
 }
 
@@ -365,6 +387,30 @@ __global__ void update_state_kernel(int n, long m, double* C, double* Y4, const 
     SC[i] = fma(x, SD[i], SC[i]);
     Gold[i] = G[i];
     G[i] = 8.0 * hc;
+  }
+}
+
+__global__ void update_state_mixed_kernel(int n, long m, double* C, double* Y4, const double* Dir, double* G,
+                                          double* Gold, double* dY, const double* Gref, const Scalars* sc) {
+  if (stopped(sc)) return;
+  const double x = sc->x;
+  const long count = (long)n * m;
+  double* HC = Y4;
+  double* SC = Y4 + count;
+  const double* HD = Y4 + 2 * count;
+  const double* SD = Y4 + 3 * count;
+  double* dHC = dY;
+  double* dSC = dY + count;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+    C[i] = fma(x, Dir[i], C[i]);
+    const double hd = x * HD[i], sd = x * SD[i];
+    HC[i] += hd;
+    SC[i] += sd;
+    const double dh = dHC[i] + hd;
+    dHC[i] = dh;
+    dSC[i] += sd;
+    Gold[i] = G[i];
+    G[i] = fma(8.0, dh, Gref[i]);
   }
 }
 
@@ -510,28 +556,28 @@ inline int grid_for(long count) {
 
 void launch_axpby_shift(cudaStream_t st, long count, const double* H, const double* S, double eta, double* Ht) {
   shift_kernel<<<grid_for(count), TB, 0, st>>>(count, H, S, eta, Ht);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_add_scaled(cudaStream_t st, long count, const double* S, const double* T, double s, double* A) {
   add_scaled_kernel<<<grid_for(count), TB, 0, st>>>(count, S, T, s, A);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_fill(cudaStream_t st, long count, double v, double* d) {
   fill_kernel<<<grid_for(count), TB, 0, st>>>(count, v, d);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_grad_reduce(cudaStream_t st, long count, const double* G, const double* PG, const double* Gold,
                         const double* Dir, double* part, const Scalars* sc) {
   grad_reduce_kernel<<<kReduceBlocks, TB, 0, st>>>(count, G, PG, Gold, Dir, part, sc);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_control_direction(cudaStream_t st, Scalars* sc, const double* part, int mixed) {
   control_direction_kernel<<<1, TB, 0, st>>>(sc, part, mixed);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_direction(cudaStream_t st, long count, const double* PG, double* Dir, const Scalars* sc) {
   direction_kernel<<<grid_for(count), TB, 0, st>>>(count, PG, Dir, sc);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 int traces_blocks(int n) {
   const int t = (n + 31) / 32;
@@ -540,52 +586,57 @@ int traces_blocks(int n) {
 void launch_traces(cudaStream_t st, int n, const double* SWHW, const double* Proj, double* part,
                    const Scalars* sc) {
   traces_kernel<<<traces_blocks(n), TB, 0, st>>>(n, SWHW, Proj, part, sc);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_control_linesearch(cudaStream_t st, Scalars* sc, const double* part, int nblocks) {
   control_linesearch_kernel<<<1, TB, 0, st>>>(sc, part, nblocks);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_update_state(cudaStream_t st, int n, long m, double* C, double* Y4, const double* Dir,
                          double* G, double* Gold, const Scalars* sc) {
   update_state_kernel<<<grid_for((long)n * m), TB, 0, st>>>(n, m, C, Y4, Dir, G, Gold, sc);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
+}
+void launch_update_state_mixed(cudaStream_t st, int n, long m, double* C, double* Y4, const double* Dir,
+                               double* G, double* Gold, double* dY, const double* Gref, const Scalars* sc) {
+  update_state_mixed_kernel<<<grid_for((long)n * m), TB, 0, st>>>(n, m, C, Y4, Dir, G, Gold, dY, Gref, sc);
+  OMM_LAUNCH_CHECK();
 }
 void launch_update_subspace(cudaStream_t st, int n, double* SWHW, const double* Proj, const Scalars* sc) {
   update_subspace_kernel<<<traces_blocks(n), TB, 0, st>>>(n, SWHW, Proj, sc);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_scale_copy(cudaStream_t st, long count, const double* src, double a, double* dst, const Scalars* sc) {
   scale_copy_kernel<<<grid_for(count), TB, 0, st>>>(count, src, a, dst, sc);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_functional(cudaStream_t st, int n, const double* SWHW, double* part) {
   functional_kernel<<<traces_blocks(n), TB, 0, st>>>(n, SWHW, part);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_finish_functional(cudaStream_t st, Scalars* sc, const double* part, int nblocks) {
   finish_functional_kernel<<<1, TB, 0, st>>>(sc, part, nblocks);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_gmax(cudaStream_t st, long count, const double* G, double* part) {
   gmax_kernel<<<kReduceBlocks, TB, 0, st>>>(count, G, part);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_finish_gmax(cudaStream_t st, Scalars* sc, const double* part) {
   finish_gmax_kernel<<<1, TB, 0, st>>>(sc, part);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_two_i_minus(cudaStream_t st, int n, const double* SW, long ldsw, double* out) {
   two_i_minus_kernel<<<grid_for((long)n * n), TB, 0, st>>>(n, SW, ldsw, out);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_line_minimum(cudaStream_t st, const double* a, double* x, int* status) {
   line_minimum_kernel<<<1, 32, 0, st>>>(a, x, status);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 void launch_symmetrize_lower(cudaStream_t st, int m, double* A) {
   symmetrize_lower_kernel<<<grid_for((long)m * m), TB, 0, st>>>(m, A);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 
 }  // namespace omm

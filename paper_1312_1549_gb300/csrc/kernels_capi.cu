@@ -1,6 +1,7 @@
 // Step-level C entry points of include/omm_kernels.h.
 #include "../../include/omm_kernels.h"
 #include "omm_internal.cuh"
+#include "tc_gemm.cuh"
 
 #include <cstring>
 #include <string>
@@ -122,6 +123,48 @@ omm_status omm_kernel_quartic_coefficients(int n, const double* SWHW, const doub
   }
   if (sc) cudaFree(sc);
   if (part) cudaFree(part);
+  return rc;
+}
+
+omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double* B, double alpha,
+                              double beta, double* C, int npass, void* stream) {
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || (npass != 1 && npass != 3)) {
+    set_last_error("omm_kernel_gemm_tc: invalid argument");
+    return OMM_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const long ld = (K + 7) / 8 * 8;
+  __nv_bfloat16* buf = nullptr;
+  int* err = nullptr;
+  omm_status rc = OMM_OK;
+  try {
+    const size_t na = (size_t)M * ld, nb = (size_t)N * ld;
+    if (cudaMalloc((void**)&buf, 2 * (na + nb) * sizeof(__nv_bfloat16)) != cudaSuccess ||
+        cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      if (buf) cudaFree(buf);
+      set_last_error("omm_kernel_gemm_tc: device allocation failed");
+      return OMM_ERR_OOM;
+    }
+    __nv_bfloat16 *a_hi = buf, *a_lo = buf + na, *b_hi = buf + 2 * na, *b_lo = buf + 2 * na + nb;
+    OMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    tc::split(st, A, M, K, K, a_hi, a_lo, ld, nullptr);
+    tc::split(st, B, N, K, K, b_hi, b_lo, ld, nullptr);
+    tc::Operand oa = tc::make_operand(a_hi, a_lo, M, K, ld, true);
+    tc::Operand ob = tc::make_operand(b_hi, b_lo, N, K, ld, false);
+    tc::gemm(st, oa, ob, K, npass, tc::Epilogue{C, N, N, 0, alpha, beta, M, N, nullptr, err});
+    int h = 0;
+    OMM_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h != 0) {
+      set_last_error("omm_kernel_gemm_tc: a bounded device wait expired (code " + std::to_string(h) + ")");
+      rc = OMM_ERR_TIMEOUT;
+    }
+  } catch (const CudaError& e) {
+    rc = cuda_fail("omm_kernel_gemm_tc", e);
+  }
+  if (buf) cudaFree(buf);
+  if (err) cudaFree(err);
   return rc;
 }
 

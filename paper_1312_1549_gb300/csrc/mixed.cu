@@ -1,20 +1,190 @@
-// Mixed-precision line searches (tensor-core contractions with float64 state).
+// Mixed-precision line searches: every contraction of a line search runs on
+// the BF16 tensor cores in 3-term split form (tc_gemm.cu) with FP32
+// accumulation, while the state C, HC, SC, H_W, S_W and every scalar stay in
+// float64. Each tensor-core product carries a factor that shrinks with the
+// step, so its error does too (iterative refinement):
+//   HD, SD = [H~; S] Delta                 (Delta -> 0)
+//   H', S', H'', S'' = Delta^T [HC SC HD SD]
+//   P G                                     (G -> 0)
+//   G = G_ref + 8 dHC - 4 (dS_W HC + dH_W SC + S_W,ref dHC + H_W,ref dSC)
+// where _ref is the state at the last float64 refresh and d = now - ref
+// (Eq. 12 expanded around the refresh point). Computing Eq. 12 directly on
+// the tensor cores would leave an absolute error of about 2^-17 |HC| in G,
+// a floor the line searches cannot get below. The host loop refreshes the
+// state in float64 when max|G| has dropped by refine_ratio (or stalls) and
+// certifies the final point in float64.
 #include "omm_mixed.cuh"
+#include "tc_gemm.cuh"
 
-#include <stdexcept>
+#include <new>
 
 namespace omm {
 
 struct MixedState {
-  int m, n;
+  int m = 0, n = 0;
+  long ldm = 0, ld2n = 0;
+  bool precond = false;
+  int npass = 3;
+  __nv_bfloat16 *HS_hi = nullptr, *HS_lo = nullptr;   // [H~; S]   2m x m
+  __nv_bfloat16 *P_hi = nullptr, *P_lo = nullptr;     // P         m x m
+  __nv_bfloat16 *G_hi = nullptr, *G_lo = nullptr;     // G         n x m
+  __nv_bfloat16 *D_hi = nullptr, *D_lo = nullptr;     // Delta     n x m
+  __nv_bfloat16 *Y_hi = nullptr, *Y_lo = nullptr;     // [HC;SC;HD;SD]  4n x m
+  __nv_bfloat16 *YT_hi = nullptr, *YT_lo = nullptr;   // [HC_mn | SC_mn | dHC_mn | dSC_mn] m x 4n
+  __nv_bfloat16 *W_hi = nullptr, *W_lo = nullptr;     // [dS_W | dH_W | S_W,ref | H_W,ref] n x 4n
+  double* Gref = nullptr;                              // G at the last refresh, n x m
+  double* dY = nullptr;                                // [HC - HC_ref; SC - SC_ref], 2n x m
+  double* Wref = nullptr;                              // [S_W | H_W] at the last refresh, n x 2n
+  tc::Operand opHS, opP, opG, opD, opY, opYT, opW;
+  int* err = nullptr;
 };
 
-MixedState* mixed_create(cudaStream_t, int, int, const double*, const double*) {
-  throw CudaError{cudaErrorNotSupported, "mixed precision is not built in this version"};
+namespace {
+
+long round8(long x) { return (x + 7) / 8 * 8; }
+
+template <typename T>
+void alloc(T** p, size_t count) {
+  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    throw std::bad_alloc();
+  }
 }
-void mixed_update_H(MixedState*, cudaStream_t, const double*) {}
-void mixed_destroy(MixedState* ms) { delete ms; }
-void mixed_iterate(MixedState*, cudaStream_t, Scalars*, double*, double*, double*, double*, double*,
-                   double*, double*, double*, double*, double*, const double*, const double*, bool) {}
+
+}  // namespace
+
+MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const double* P) {
+  MixedState* ms = new MixedState();
+  try {
+    ms->m = m;
+    ms->n = n;
+    ms->ldm = round8(m);
+    ms->ld2n = round8(4L * n);  // leading dimension of the 4n-wide gradient operands
+    ms->precond = (P != nullptr);
+    const long ldm = ms->ldm, ld2n = ms->ld2n;
+    alloc(&ms->HS_hi, 2L * m * ldm);
+    alloc(&ms->HS_lo, 2L * m * ldm);
+    if (ms->precond) {
+      alloc(&ms->P_hi, (size_t)m * ldm);
+      alloc(&ms->P_lo, (size_t)m * ldm);
+    }
+    alloc(&ms->G_hi, (size_t)n * ldm);
+    alloc(&ms->G_lo, (size_t)n * ldm);
+    alloc(&ms->D_hi, (size_t)n * ldm);
+    alloc(&ms->D_lo, (size_t)n * ldm);
+    alloc(&ms->Y_hi, 4L * n * ldm);
+    alloc(&ms->Y_lo, 4L * n * ldm);
+    alloc(&ms->YT_hi, (size_t)m * ld2n);
+    alloc(&ms->YT_lo, (size_t)m * ld2n);
+    alloc(&ms->W_hi, (size_t)n * ld2n);
+    alloc(&ms->W_lo, (size_t)n * ld2n);
+    alloc(&ms->Gref, (size_t)n * m);
+    alloc(&ms->dY, 2L * n * m);
+    alloc(&ms->Wref, 2L * n * n);
+    alloc(&ms->err, 1);
+    OMM_CUDA_TRY(cudaMemsetAsync(ms->err, 0, sizeof(int), st));
+    // padding columns stay zero (the tensor maps never read them, but keep them defined)
+    OMM_CUDA_TRY(cudaMemsetAsync(ms->YT_hi, 0, (size_t)m * ld2n * 2, st));
+    OMM_CUDA_TRY(cudaMemsetAsync(ms->YT_lo, 0, (size_t)m * ld2n * 2, st));
+    tc::split(st, HS, 2L * m, m, m, ms->HS_hi, ms->HS_lo, ldm, nullptr);
+    if (ms->precond) tc::split(st, P, m, m, m, ms->P_hi, ms->P_lo, ldm, nullptr);
+    ms->opHS = tc::make_operand(ms->HS_hi, ms->HS_lo, 2L * m, m, ldm, false);
+    if (ms->precond) ms->opP = tc::make_operand(ms->P_hi, ms->P_lo, m, m, ldm, false);
+    ms->opG = tc::make_operand(ms->G_hi, ms->G_lo, n, m, ldm, true);
+    ms->opD = tc::make_operand(ms->D_hi, ms->D_lo, n, m, ldm, true);
+    ms->opY = tc::make_operand(ms->Y_hi, ms->Y_lo, 4L * n, m, ldm, false);
+    ms->opYT = tc::make_operand(ms->YT_hi, ms->YT_lo, m, 4L * n, ld2n, false);
+    ms->opW = tc::make_operand(ms->W_hi, ms->W_lo, n, 4L * n, ld2n, true);
+  } catch (...) {
+    mixed_destroy(ms);
+    throw;
+  }
+  return ms;
+}
+
+void mixed_update_H(MixedState* ms, cudaStream_t st, const double* HS) {
+  tc::split(st, HS, ms->m, ms->m, ms->m, ms->HS_hi, ms->HS_lo, ms->ldm, nullptr);
+}
+
+void mixed_destroy(MixedState* ms) {
+  if (!ms) return;
+  __nv_bfloat16* bufs[] = {ms->HS_hi, ms->HS_lo, ms->P_hi, ms->P_lo, ms->G_hi, ms->G_lo, ms->D_hi,
+                           ms->D_lo, ms->Y_hi, ms->Y_lo, ms->YT_hi, ms->YT_lo, ms->W_hi, ms->W_lo};
+  for (auto* b : bufs)
+    if (b) cudaFree(b);
+  if (ms->err) cudaFree(ms->err);
+  if (ms->Gref) cudaFree(ms->Gref);
+  if (ms->dY) cudaFree(ms->dY);
+  if (ms->Wref) cudaFree(ms->Wref);
+  delete ms;
+}
+
+int mixed_error(MixedState* ms, cudaStream_t st) {
+  int e = 0;
+  OMM_CUDA_TRY(cudaMemcpyAsync(&e, ms->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  OMM_CUDA_TRY(cudaStreamSynchronize(st));
+  return e;
+}
+
+// after a float64 recompute: the new reference point of the incremental gradient
+void mixed_sync_state(MixedState* ms, cudaStream_t st, const double* Y4, const double* SWHW, const double* G) {
+  const int m = ms->m, n = ms->n;
+  const long ld4 = ms->ld2n;
+  OMM_CUDA_TRY(cudaMemcpyAsync(ms->Gref, G, (size_t)n * m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  OMM_CUDA_TRY(cudaMemcpyAsync(ms->Wref, SWHW, 2L * n * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  OMM_CUDA_TRY(cudaMemsetAsync(ms->dY, 0, 2L * n * m * sizeof(double), st));
+  tc::split(st, Y4, 2L * n, m, m, ms->Y_hi, ms->Y_lo, ms->ldm, nullptr);
+  tc::split_transposed(st, Y4, 2L * n, m, m, ms->YT_hi, ms->YT_lo, ld4, nullptr);
+  tc::split_transposed(st, ms->dY, 2L * n, m, m, ms->YT_hi + 2L * n, ms->YT_lo + 2L * n, ld4, nullptr);
+  tc::split_diff(st, SWHW, ms->Wref, n, 2L * n, 2L * n, ms->W_hi, ms->W_lo, ld4, nullptr);
+  tc::split(st, ms->Wref, n, 2L * n, 2L * n, ms->W_hi + 2L * n, ms->W_lo + 2L * n, ld4, nullptr);
+}
+
+void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, double* Dir, double* G,
+                   double* Gold, double* PG, double* Y4, double* SWHW, double* Proj, double* part,
+                   double* part2, const double* HS, const double* P, bool precond, Profiler& pf) {
+  (void)HS;
+  (void)P;
+  const int m = ms->m, n = ms->n;
+  const long nm = (long)n * m;
+  const int* skip = &sc->done;
+  const int np = ms->npass;
+  // P G (Sec. 2.4)
+  if (precond) {
+    tc::split(st, G, n, m, m, ms->G_hi, ms->G_lo, ms->ldm, sc);
+    pf.begin(st);
+    tc::gemm(st, ms->opG, ms->opP, m, np, tc::Epilogue{PG, m, m, 0, 1.0, 0.0, n, m, skip, ms->err});
+    pf.end(st, 2.0 * np * n * (double)m * m);
+  } else {
+    launch_scale_copy(st, nm, G, 1.0, PG, sc);
+  }
+  launch_grad_reduce(st, nm, G, PG, Gold, Dir, part, sc);
+  launch_control_direction(st, sc, part, 1);
+  launch_direction(st, nm, PG, Dir, sc);
+  tc::split(st, Dir, n, m, m, ms->D_hi, ms->D_lo, ms->ldm, sc);
+  // [H~ D ; S D] (n x m layout): one GEMM over the stacked [H~; S]
+  pf.begin(st);
+  tc::gemm(st, ms->opD, ms->opHS, m, np, tc::Epilogue{Y4 + 2 * nm, m, m, nm, 1.0, 0.0, n, 2 * m, skip, ms->err});
+  pf.end(st, 4.0 * np * n * (double)m * m);
+  tc::split(st, Y4 + 2 * nm, 2L * n, m, m, ms->Y_hi + 2L * n * ms->ldm, ms->Y_lo + 2L * n * ms->ldm, ms->ldm, sc);
+  // [H' | S' | H'' | S''] = D [HC; SC; HD; SD]^T (Eqs. 14-15)
+  pf.begin(st);
+  tc::gemm(st, ms->opD, ms->opY, m, np, tc::Epilogue{Proj, 4L * n, 4L * n, 0, 1.0, 0.0, n, 4 * n, skip, ms->err});
+  pf.end(st, 8.0 * np * n * (double)n * m);
+  launch_traces(st, n, SWHW, Proj, part2, sc);
+  launch_control_linesearch(st, sc, part2, traces_blocks(n));
+  launch_update_state_mixed(st, n, m, C, Y4, Dir, G, Gold, ms->dY, ms->Gref, sc);
+  tc::split(st, Y4, 2L * n, m, m, ms->Y_hi, ms->Y_lo, ms->ldm, sc);
+  tc::split_transposed(st, Y4, 2L * n, m, m, ms->YT_hi, ms->YT_lo, ms->ld2n, sc);
+  tc::split_transposed(st, ms->dY, 2L * n, m, m, ms->YT_hi + 2L * n, ms->YT_lo + 2L * n, ms->ld2n, sc);
+  launch_update_subspace(st, n, SWHW, Proj, sc);
+  tc::split_diff(st, SWHW, ms->Wref, n, 2L * n, 2L * n, ms->W_hi, ms->W_lo, ms->ld2n, sc);
+  // G = Gref + 8 dHC - 4 [dS_W | dH_W | S_W,ref | H_W,ref] [HC; SC; dHC; dSC] (Eq. 12 about
+  // the refresh point); the update preset G = Gref + 8 dHC
+  pf.begin(st);
+  tc::gemm(st, ms->opW, ms->opYT, 4 * n, np, tc::Epilogue{G, m, m, 0, -4.0, 1.0, n, m, skip, ms->err});
+  pf.end(st, 8.0 * np * n * (double)n * m);
+}
 
 }  // namespace omm

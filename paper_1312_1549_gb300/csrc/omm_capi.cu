@@ -15,6 +15,7 @@
 #include "omm_mixed.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -26,6 +27,49 @@ thread_local std::string g_last_error;
 }
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 const char* last_error_cstr() { return g_last_error.c_str(); }
+
+std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void Profiler::begin(cudaStream_t st) {
+  if (!on) return;
+  if (used_ == cap_) {
+    const int ncap = cap_ ? 2 * cap_ : 64;
+    Pair* np = new Pair[ncap];
+    for (int i = 0; i < cap_; ++i) np[i] = pairs_[i];
+    for (int i = cap_; i < ncap; ++i) {
+      cudaEventCreate(&np[i].a);
+      cudaEventCreate(&np[i].b);
+    }
+    delete[] pairs_;
+    pairs_ = np;
+    cap_ = ncap;
+  }
+  cudaEventRecord(pairs_[used_].a, st);
+}
+void Profiler::end(cudaStream_t st, double f) {
+  if (!on) return;
+  cudaEventRecord(pairs_[used_].b, st);
+  pairs_[used_].flop = f;
+  ++used_;
+}
+void Profiler::collect() {
+  for (int i = 0; i < used_; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pairs_[i].a, pairs_[i].b) == cudaSuccess) ms += t;
+    flop += pairs_[i].flop;
+    ++launches;
+  }
+  cudaGetLastError();
+  used_ = 0;
+}
+Profiler::~Profiler() {
+  for (int i = 0; i < cap_; ++i) {
+    cudaEventDestroy(pairs_[i].a);
+    cudaEventDestroy(pairs_[i].b);
+  }
+  delete[] pairs_;
+}
 }  // namespace omm
 
 using namespace omm;
@@ -57,9 +101,12 @@ struct omm_ctx {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double ms_setup = 0.0;
   MixedState* mixed = nullptr;
+  Profiler prof;  // main contraction kernel of the iteration (tensor-core or float64 GEMM)
 };
 
 namespace {
+
+constexpr int kMixedRoundCap = 400;
 
 struct Status {
   omm_status s;
@@ -124,20 +171,31 @@ void iterate_fp64(omm_ctx* c) {
   const int m = c->m, n = c->n;
   const long nm = (long)n * m, mm = (long)m * m;
   const int* skip = &c->sc->done;
-  if (c->precond)
+  Profiler& pf = c->prof;
+  const double fPG = 2.0 * n * (double)m * m, fHD = 4.0 * n * (double)m * m;
+  const double fPr = 8.0 * n * (double)n * m, fG = 4.0 * n * (double)n * m;
+  if (c->precond) {
+    pf.begin(c->st);
     dgemm(c->st, 0, 1, n, m, m, 1.0, c->G, m, 0, c->P, m, 0, 0.0, c->PG, m, 0, 1, 0, skip);
-  else
+    pf.end(c->st, fPG);
+  } else
     launch_scale_copy(c->st, nm, c->G, 1.0, c->PG, c->sc);
   launch_grad_reduce(c->st, nm, c->G, c->PG, c->Gold, c->Dir, c->part, c->sc);
   launch_control_direction(c->st, c->sc, c->part, 0);
   launch_direction(c->st, nm, c->PG, c->Dir, c->sc);
+  pf.begin(c->st);
   dgemm(c->st, 0, 1, n, m, m, 1.0, c->Dir, m, 0, c->HS, m, mm, 0.0, c->Y4 + 2 * nm, m, nm, 2, 0, skip);
+  pf.end(c->st, fHD);
+  pf.begin(c->st);
   dgemm(c->st, 0, 1, n, 4 * n, m, 1.0, c->Dir, m, 0, c->Y4, m, 0, 0.0, c->Proj, 4L * n, 0, 1, 0, skip);
+  pf.end(c->st, fPr);
   launch_traces(c->st, n, c->SWHW, c->Proj, c->part2, c->sc);
   launch_control_linesearch(c->st, c->sc, c->part2, traces_blocks(n));
   launch_update_state(c->st, n, m, c->C, c->Y4, c->Dir, c->G, c->Gold, c->sc);
   launch_update_subspace(c->st, n, c->SWHW, c->Proj, c->sc);
+  pf.begin(c->st);
   dgemm(c->st, 0, 0, n, m, 2 * n, -4.0, c->SWHW, 2L * n, 0, c->Y4, m, 0, 1.0, c->G, m, 0, 1, 0, skip);
+  pf.end(c->st, fG);
 }
 
 void read_scalars(omm_ctx* c) {
@@ -157,6 +215,11 @@ void reset_loop_flags(omm_ctx* c, bool full) {
   h.restart = 1;
   h.stop_pending = 0;
   h.stop_reason = 0;
+  h.iter_round = 0;
+  h.mixed = c->mixed != nullptr;
+  h.best_g = 1e300;
+  h.best_it = 0;
+  h.stall_window = 40;
   h.max_iter = c->opts.max_iter;
   h.tol_grad = c->opts.tol_grad;
   h.e_tol = c->opts.e_tol;
@@ -234,6 +297,8 @@ const char* omm_status_str(omm_status s) {
 }
 
 const char* omm_last_error(void) { return last_error_cstr(); }
+
+unsigned long long omm_launch_count(void) { return g_launches.load(); }
 
 omm_status omm_create(int m, int n, const double* H, const double* S, const double* T, double eta,
                       double tau, const omm_opts* opts, void* stream, omm_ctx** out) {
@@ -351,12 +416,15 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
   const long nm = (long)n * m;
   c->solved = false;
   try {
+    const unsigned long long launches0 = g_launches.load();
+    c->prof.on = c->opts.profile != 0;
+    c->prof.reset();
     copy_in(c->C, C0, nm, c->st);
     reset_loop_flags(c, true);
     write_scalars(c);
     const bool mixed = c->mixed != nullptr;
     double flop = 0.0, flop_tc = 0.0;
-    const double per_it = 6.0 * m * (double)m * n + 12.0 * (double)m * n * n;
+    const double per_it = 6.0 * m * (double)m * n + (c->mixed ? 16.0 : 12.0) * (double)m * n * n;
     const double per_state = 4.0 * m * (double)m * n + 8.0 * (double)m * n * n;
     double ms_iter = 0.0, ms_ref = 0.0;
     int fp64_iters = 0, refinements = 0;
@@ -395,17 +463,25 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
       h.iter = iter_total;
       h.halt_gmax = mixed ? std::max(c->opts.tol_grad * 0.5, g_ref * c->opts.refine_ratio) : 0.0;
       write_scalars(c);
+      if (mixed) mixed_sync_state(c->mixed, c->st, c->Y4, c->SWHW, c->G);
       OMM_CUDA_TRY(cudaEventRecord(c->ev[2], c->st));
       int prev_iter = iter_total;
       for (;;) {
         for (int k = 0; k < c->opts.check_every; ++k) {
           if (mixed) mixed_iterate(c->mixed, c->st, c->sc, c->C, c->Dir, c->G, c->Gold, c->PG,
                                    c->Y4, c->SWHW, c->Proj, c->part, c->part2, c->HS, c->P,
-                                   c->precond);
+                                   c->precond, c->prof);
           else iterate_fp64(c);
         }
         read_scalars(c);
+        c->prof.collect();
         if (h.done || h.halt) break;
+        // a mixed round that stalls above its refinement threshold is refreshed in float64
+        if (mixed && h.iter - prev_iter >= kMixedRoundCap) break;
+      }
+      if (mixed && mixed_error(c->mixed, c->st) != 0) {
+        result = OMM_ERR_TIMEOUT;
+        break;
       }
       OMM_CUDA_TRY(cudaEventRecord(c->ev[3], c->st));
       OMM_CUDA_TRY(cudaEventSynchronize(c->ev[3]));
@@ -460,6 +536,10 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     OMM_CUDA_TRY(cudaStreamSynchronize(c->st));
     inf.gemm_flop = flop;
     inf.gemm_flop_tc = flop_tc;
+    inf.kernel_launches = (double)(g_launches.load() - launches0);
+    inf.ms_main_gemm = c->prof.ms;
+    inf.main_gemm_launches = (double)c->prof.launches;
+    inf.main_gemm_flop = c->prof.flop;
   } catch (const std::bad_alloc&) {
     result = OMM_ERR_OOM;
     set_last_error("omm_solve: device allocation failed");

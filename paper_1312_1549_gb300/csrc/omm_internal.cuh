@@ -22,19 +22,24 @@ struct Scalars {
   int stop_pending;  // Eq. 18 met at the last line search: stop at the next check
   int max_iter;
   int stop_reason;   // 1: gradient test met, 2: energy test (Eq. 18) met
-  int pad_;
+  int mixed;         // line searches run on the tensor cores
+  int iter_round;    // line searches since the last float64 recompute
   double E;          // current shifted functional E~
   double gmax;       // max |G| of the current gradient
   double gpg;        // <G, P G>
   double gpg_old;    // <G_old, P G_old>
   double gopg;       // <G_old, P G>
   double gdo;        // <G, Delta_old>
+  double gd;         // <G, Delta> of the current direction (= alpha_1, the slope at x = 0)
   double beta;       // Polak-Ribiere coefficient of the current direction
   double x;          // line-search step
   double alpha[5];   // quartic coefficients of the last line search
   double tol_grad;
   double e_tol;
   double halt_gmax;  // mixed precision: request a float64 refinement below this max|G|
+  double best_g;     // mixed precision: smallest max|G| of the current round
+  int best_it;       // line search of the round where best_g was reached
+  int stall_window;  // refine when best_g has not halved for this many line searches
   double trace[12];  // last trace products (debug / tests)
 };
 
@@ -50,11 +55,40 @@ struct CudaError {
 void set_last_error(const std::string& msg);
 const char* last_error_cstr();
 
+// every kernel launch of the library is counted (omm_launch_count)
+void count_launch();
+#define OMM_LAUNCH_CHECK()                   \
+  do {                                       \
+    ::omm::count_launch();                   \
+    OMM_CUDA_TRY(cudaGetLastError());        \
+  } while (0)
+
 #define OMM_CUDA_TRY(call)                                                   \
   do {                                                                       \
     cudaError_t e__ = (call);                                                \
     if (e__ != cudaSuccess) throw ::omm::CudaError{e__, #call};              \
   } while (0)
+
+// ------------------------------------------------------------------ kernel timing
+// CUDA-event timing of selected launches on their own stream (enabled by
+// omm_opts.profile): begin()/end() bracket a launch, collect() after a stream
+// synchronisation adds the elapsed times.
+class Profiler {
+ public:
+  bool on = false;
+  double ms = 0.0, flop = 0.0;
+  long launches = 0;
+  void begin(cudaStream_t st);
+  void end(cudaStream_t st, double flop_of_launch);
+  void collect();  // the stream must have been synchronised
+  void reset() { ms = 0.0; flop = 0.0; launches = 0; }
+  ~Profiler();
+
+ private:
+  struct Pair { cudaEvent_t a, b; double flop; };
+  Pair* pairs_ = nullptr;
+  int used_ = 0, cap_ = 0;
+};
 
 // ------------------------------------------------------------------ float64 GEMM
 // C[b] = alpha * op(A[b]) op(B[b]) + beta * C[b], row-major, for b < batch.
@@ -92,6 +126,10 @@ int traces_blocks(int n);
 void launch_control_linesearch(cudaStream_t st, Scalars* sc, const double* part, int nblocks);
 void launch_update_state(cudaStream_t st, int n, long m, double* C, double* Y4, const double* Dir,
                          double* G, double* Gold, const Scalars* sc);
+// mixed precision: as launch_update_state, plus dY = [dHC; dSC] += x [HD; SD] and
+// G = Gref + 8 (HC - HC_ref) as the base of the incremental gradient GEMM
+void launch_update_state_mixed(cudaStream_t st, int n, long m, double* C, double* Y4, const double* Dir,
+                               double* G, double* Gold, double* dY, const double* Gref, const Scalars* sc);
 void launch_update_subspace(cudaStream_t st, int n, double* SWHW, const double* Proj,
                             const Scalars* sc);
 void launch_scale_copy(cudaStream_t st, long count, const double* src, double a, double* dst,

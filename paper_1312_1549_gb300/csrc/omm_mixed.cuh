@@ -11,8 +11,13 @@ struct MixedState;
 MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const double* P);
 void mixed_update_H(MixedState* ms, cudaStream_t st, const double* HS);
 void mixed_destroy(MixedState* ms);
+// after a float64 recompute: take (G, HC, SC, S_W, H_W) as the new reference
+// point of the incremental gradient and refresh the bf16 copies
+void mixed_sync_state(MixedState* ms, cudaStream_t st, const double* Y4, const double* SWHW, const double* G);
+// nonzero if a tensor-core kernel gave up a bounded wait (synchronises the stream)
+int mixed_error(MixedState* ms, cudaStream_t st);
 void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, double* Dir, double* G,
                    double* Gold, double* PG, double* Y4, double* SWHW, double* Proj, double* part,
-                   double* part2, const double* HS, const double* P, bool precond);
+                   double* part2, const double* HS, const double* P, bool precond, Profiler& prof);
 
 }  // namespace omm

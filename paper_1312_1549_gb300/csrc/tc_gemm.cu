@@ -309,7 +309,7 @@ void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, int npass,
   const CUtensorMap* b_hi = reinterpret_cast<const CUtensorMap*>(&B.hi);
   const CUtensorMap* b_lo = reinterpret_cast<const CUtensorMap*>(&B.lo);
   gemm_bf16_split_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(*a_hi, *a_lo, *b_hi, *b_lo, K, npass, ep);
-  OMM_CUDA_TRY(cudaGetLastError());
+  OMM_LAUNCH_CHECK();
 }
 
 int tile_m() { return BM; }

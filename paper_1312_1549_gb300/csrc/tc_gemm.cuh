@@ -45,6 +45,9 @@ int tile_n();
 // transposed variants write dst[j][i]. Skipped when sc's done/halt is set.
 void split(cudaStream_t st, const double* src, long rows, long cols, long ld_src, __nv_bfloat16* hi,
            __nv_bfloat16* lo, long ld_dst, const Scalars* sc);
+// hi/lo of (src - sub), both float64 with the same layout
+void split_diff(cudaStream_t st, const double* src, const double* sub, long rows, long cols, long ld_src,
+                __nv_bfloat16* hi, __nv_bfloat16* lo, long ld_dst, const Scalars* sc);
 void split_transposed(cudaStream_t st, const double* src, long rows, long cols, long ld_src,
                       __nv_bfloat16* hi_t, __nv_bfloat16* lo_t, long ld_dst, const Scalars* sc);
 

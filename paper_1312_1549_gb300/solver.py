@@ -44,7 +44,8 @@ class OMMSolver:
     """
 
     def __init__(self, H, S, T, n, eta, tau, precision="fp64", stream=None, max_iter=0,
-                 tol_grad=1e-9, e_tol=0.0, refine_ratio=0.0, precondition=True, check_every=0):
+                 tol_grad=1e-9, e_tol=0.0, refine_ratio=0.0, precondition=True, check_every=0,
+                 profile=False):
         lib = N.lib()
         m = int(H.shape[0])
         self.m, self.n, self.eta, self.tau = m, int(n), float(eta), float(tau)
@@ -52,7 +53,8 @@ class OMMSolver:
         opts = N.OmmOpts(precision=N.PREC_MIXED if precision == "mixed" else N.PREC_FP64,
                          max_iter=int(max_iter), no_precondition=0 if precondition else 1,
                          check_every=int(check_every), tol_grad=float(tol_grad),
-                         e_tol=float(e_tol), refine_ratio=float(refine_ratio))
+                         e_tol=float(e_tol), refine_ratio=float(refine_ratio),
+                         profile=1 if profile else 0)
         self._keep = (H, S, T)
         h = ct.c_void_p()
         tau_arg = math.inf if tau is None else float(tau)
@@ -150,3 +152,17 @@ def quartic_coefficients(SWHW, Proj, E, stream=None):
                                                     _stream_handle(stream)),
             "omm_kernel_quartic_coefficients")
     return np.array(list(out))
+
+
+def gemm_tc(A, B, C, alpha=1.0, beta=0.0, npass=3, stream=None):
+    """C = alpha A B^T + beta C on the BF16 tensor cores (split operands)."""
+    M, K = A.shape
+    Nn = B.shape[0]
+    N.check(N.lib().omm_kernel_gemm_tc(M, Nn, K, _ptr(A), _ptr(B), float(alpha), float(beta), _ptr(C),
+                                       int(npass), _stream_handle(stream)), "omm_kernel_gemm_tc")
+    return C
+
+
+def launch_count():
+    """Kernels launched by the library in this process."""
+    return int(N.lib().omm_launch_count())

@@ -1,0 +1,92 @@
+"""GPU parity of the tensor-core (tcgen05) contraction and of the mixed-precision solve."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_1312_1549_gb300 import build
+    build.build()
+    from paper_1312_1549_gb300 import solver
+    return solver
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def bf16_round(x):
+    """float64 -> nearest bf16 (8 significant bits, ties to even), rounded once."""
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (130, 257, 70), (256, 512, 1000), (1, 1, 1), (384, 96, 200)])
+def test_gemm_tc_single_pass_is_exact_bf16_product(S, M, N, K):
+    """npass = 1: the product of the bf16-rounded operands up to FP32 accumulation (K * 2^-23)."""
+    rng = np.random.default_rng(M + N + K)
+    A = rng.normal(size=(M, K)); B = rng.normal(size=(N, K))
+    C = dev(np.zeros((M, N)))
+    S.gemm_tc(dev(A), dev(B), C, npass=1)
+    ref = bf16_round(A) @ bf16_round(B).T
+    scale = np.abs(bf16_round(A)) @ np.abs(bf16_round(B)).T
+    assert np.all(np.abs(C.cpu().numpy() - ref) <= K * 2.0 ** -23 * scale + 1e-30)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (200, 300, 100), (256, 512, 1024), (129, 700, 333)])
+def test_gemm_tc_split_error_bound(S, M, N, K):
+    """npass = 3: error of the 3-term split product within 2^-14 |A||B|^T elementwise."""
+    rng = np.random.default_rng(7 * M + N + K)
+    A = rng.normal(size=(M, K)); B = rng.normal(size=(N, K))
+    C0 = rng.normal(size=(M, N))
+    C = dev(C0)
+    S.gemm_tc(dev(A), dev(B), C, alpha=2.0, beta=-1.0, npass=3)
+    ref = 2.0 * A @ B.T - C0
+    scale = 2.0 * np.abs(A) @ np.abs(B).T
+    err = np.abs(C.cpu().numpy() - ref)
+    assert np.all(err <= 2.0 ** -14 * scale + 1e-12)
+    # and far better than the single pass
+    C1 = dev(np.zeros((M, N)))
+    S.gemm_tc(dev(A), dev(B), C1, npass=1)
+    e1 = np.abs(C1.cpu().numpy() - A @ B.T).max()
+    assert err.max() < e1 / 50
+
+
+@pytest.fixture(scope="module")
+def si64():
+    from synth import config1
+    from oracle import exact, omm
+    p = config1()
+    ref = omm.solve(p.H, p.S, p.T, p.eta, p.tau, p.C0, tol_grad=1e-9)
+    ex = exact.exact_minimum(p.H, p.S, p.n)
+    return p, ref, ex
+
+
+def test_mixed_solve_si64_matches_oracle(S, si64):
+    p, ref, ex = si64
+    with S.OMMSolver(dev(p.H), dev(p.S), dev(p.T), p.n, p.eta, p.tau, precision="mixed") as s:
+        C, E, D, info = s.solve(dev(p.C0), want_D=True)
+        dH, dS = s.backward()
+    D = D.cpu().numpy()
+    assert info["status"] == 0 and info["gmax"] < 1e-9
+    assert info["gemm_flop_tc"] > 0
+    assert abs(E - ref["E"]) / abs(ref["E"]) <= 1e-9
+    assert abs(E - ex["E"]) / abs(ex["E"]) <= 1e-9
+    assert np.abs(D - ex["D"]).max() <= 1e-7
+    Cm = C.cpu().numpy().T
+    assert np.abs(Cm.T @ p.S @ Cm - np.eye(p.n)).max() < 1e-8
+    assert np.abs(dS.cpu().numpy() + ex["EDM"]).max() <= 1e-7
+
+
+def test_mixed_solve_without_preconditioner(S, si64):
+    p, ref, ex = si64
+    with S.OMMSolver(dev(p.H), dev(p.S), dev(p.T), p.n, p.eta, p.tau, precision="mixed",
+                     precondition=False) as s:
+        C, E, D, info = s.solve(dev(p.C0), want_D=True)
+    assert info["status"] == 0
+    assert abs(E - ex["E"]) / abs(ex["E"]) <= 1e-9
+    assert np.abs(D.cpu().numpy() - ex["D"]).max() <= 1e-7

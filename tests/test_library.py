@@ -14,7 +14,7 @@ def declared_functions():
             continue
         text = open(os.path.join(ROOT, "include", hdr)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(omm_\w+)\s*\(", text, flags=re.M)
+        names += re.findall(r"^[A-Za-z_][\w \t\*]*?\b(omm_[A-Za-z0-9_]+)\s*\(", text, flags=re.M)
     return sorted(set(names))
 
 
