@@ -36,7 +36,7 @@ WORKLOADS = {
 }
 # Line searches the float64 solve takes on each workload from its seeded C0
 # (measured with the float64 GPU path); used to extrapolate bounded oracle samples.
-FP64_LINE_SEARCHES = {1: 43, 2: 160, 3: 160}
+FP64_LINE_SEARCHES = {1: 43, 2: 63, 3: 160}
 
 
 def load_peaks():

@@ -1,0 +1,67 @@
+"""Full-size parity (Si512 DZP-like and water256), in the bench's launch configuration.
+
+The oracle's plain definition of the minimum (the n lowest generalised eigenpairs, LAPACK) gives
+E*, D* = 2 X X^T and EDM*; D and dE/dS are compared on sampled rows, S_W and Tr(DS) in full.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module", params=[2, 3], ids=["si512_dzp", "water256_dzp"])
+def solved(request):
+    from paper_1312_1549_gb300 import build
+    build.build()
+    from paper_1312_1549_gb300.solver import OMMSolver
+    from synth import configs
+    from oracle import exact
+    p = configs.CONFIGS[request.param]()
+    with OMMSolver(dev(p.H), dev(p.S), dev(p.T), p.n, p.eta, p.tau, precision="mixed") as s:
+        C, E, D, info = s.solve(dev(p.C0), want_D=True)
+        dH, dS = s.backward()
+    rows = np.random.default_rng(0).choice(p.m, size=192, replace=False)
+    rows.sort()
+    out = {"p": p, "C": C.cpu().numpy(), "E": E, "info": info, "rows": rows,
+           "D_rows": D[rows].cpu().numpy(), "dS_rows": dS[rows].cpu().numpy(),
+           "dH_equals_D": bool(torch.equal(dH, D)), "D_trace_DS": float((D * dev(p.S)).sum())}
+    del D, dH, dS
+    ex = exact.exact_minimum(p.H, p.S, p.n, want_matrices=False)
+    import scipy.linalg
+    w, X = scipy.linalg.eigh(p.H, p.S, subset_by_index=[0, p.n - 1])
+    out["E_exact"] = ex["E"]
+    out["Dstar_rows"] = 2.0 * X[rows] @ X.T
+    out["EDMstar_rows"] = 2.0 * (X[rows] * w[None, :]) @ X.T
+    return out
+
+
+def test_energy_matches_exact(solved):
+    r = solved
+    assert r["info"]["status"] == 0 and r["info"]["gmax"] < 1e-9
+    assert abs(r["E"] - r["E_exact"]) / abs(r["E_exact"]) <= 1e-9
+
+
+def test_density_matrix_matches_eigenvectors(solved):
+    r = solved
+    assert np.abs(r["D_rows"] - r["Dstar_rows"]).max() <= 1e-7
+    assert r["D_trace_DS"] == pytest.approx(2 * r["p"].n, abs=1e-6)
+
+
+def test_overlap_is_identity_at_minimum(solved):
+    r = solved
+    p = r["p"]
+    Cm = r["C"].T
+    SW = Cm.T @ (p.S @ Cm)
+    assert np.abs(SW - np.eye(p.n)).max() < 1e-8
+
+
+def test_backward_matches_energy_density_matrix(solved):
+    r = solved
+    assert r["dH_equals_D"]
+    assert np.abs(r["dS_rows"] + r["EDMstar_rows"]).max() <= 1e-7
