@@ -111,10 +111,10 @@ void trtri_rec(cudaStream_t st, int m, double* Y, const Work& w, int r0, int r1)
   double* L21 = Y + (long)mid * m + r0;
   const double* Y11 = Y + (long)r0 * m + r0;
   const double* Y22 = Y + (long)mid * m + mid;
-  // W = L21 * Y11  (n2 x n1)
-  dgemm(st, 0, 0, n2, n1, n1, 1.0, L21, m, 0, Y11, m, 0, 0.0, w.tmp, n1, 0);
-  // Y21 = -Y22 * W
-  dgemm(st, 0, 0, n2, n1, n2, -1.0, Y22, m, 0, w.tmp, n1, 0, 0.0, L21, m, 0);
+  // W = L21 * Y11  (n2 x n1); Y11 is lower triangular
+  dgemm(st, 0, 0, n2, n1, n1, 1.0, L21, m, 0, Y11, m, 0, 0.0, w.tmp, n1, 0, 1, kTriKFromCol);
+  // Y21 = -Y22 * W; Y22 is lower triangular
+  dgemm(st, 0, 0, n2, n1, n2, -1.0, Y22, m, 0, w.tmp, n1, 0, 0.0, L21, m, 0, 1, kTriKToRow);
 }
 
 }  // namespace

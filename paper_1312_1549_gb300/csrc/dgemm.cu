@@ -33,9 +33,11 @@ dgemm_kernel(int transA, int transB, int M, int N, int K, double alpha,
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
 
-  int kbeg = 0;
+  int kbeg = 0, kend = K;
   if (tri & kTriKStart) kbeg = (max(row0, col0) / BK) * BK;
-  for (int k0 = kbeg; k0 < K; k0 += BK) {
+  if (tri & kTriKFromCol) kbeg = max(kbeg, (col0 / BK) * BK);
+  if (tri & kTriKToRow) kend = min(K, row0 + BM);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int t = 0; t < (BM * BK) / NT; ++t) {
       const int idx = tid + t * NT;

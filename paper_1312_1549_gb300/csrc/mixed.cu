@@ -141,6 +141,35 @@ void mixed_sync_state(MixedState* ms, cudaStream_t st, const double* Y4, const d
   tc::split(st, ms->Wref, n, 2L * n, 2L * n, ms->W_hi + 2L * n, ms->W_lo + 2L * n, ld4, nullptr);
 }
 
+// The initial state (HC, SC, S_W, H_W, E~, G and max|G|) on the tensor cores.
+// Its split-product error only has to stay below the first round's target
+// (refine_ratio of the starting gradient); every later refresh and the
+// certificate are float64.
+void mixed_recompute_state(MixedState* ms, cudaStream_t st, Scalars* sc, const double* C, double* Y4,
+                           double* SWHW, double* G, double* part, double* part2) {
+  const int m = ms->m, n = ms->n;
+  const long nm = (long)n * m, ld4 = ms->ld2n;
+  tc::split(st, C, n, m, m, ms->D_hi, ms->D_lo, ms->ldm, nullptr);
+  tc::gemm(st, ms->opD, ms->opHS, m, ms->npass, tc::Epilogue{Y4, m, m, nm, 1.0, 0.0, n, 2 * m, nullptr, ms->err});
+  tc::split(st, Y4, 2L * n, m, m, ms->Y_hi, ms->Y_lo, ms->ldm, nullptr);
+  // [H_W | S_W] = C [HC; SC]^T written as SWHW = [S_W | H_W]
+  tc::gemm(st, ms->opD, ms->opY, m, ms->npass,
+           tc::Epilogue{SWHW + n, 2L * n, n, -(long)n, 1.0, 0.0, n, 2 * n, nullptr, ms->err});
+  launch_functional(st, n, SWHW, part2);
+  launch_finish_functional(st, sc, part2, traces_blocks(n));
+  // G = 8 HC - 4 [S_W | H_W] [HC; SC]: the incremental GEMM about a zero reference
+  OMM_CUDA_TRY(cudaMemsetAsync(ms->Wref, 0, 2L * n * n * sizeof(double), st));
+  OMM_CUDA_TRY(cudaMemcpyAsync(ms->dY, Y4, 2L * nm * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_scale_copy(st, nm, Y4, 8.0, G, nullptr);
+  tc::split_transposed(st, Y4, 2L * n, m, m, ms->YT_hi, ms->YT_lo, ld4, nullptr);
+  tc::split_transposed(st, ms->dY, 2L * n, m, m, ms->YT_hi + 2L * n, ms->YT_lo + 2L * n, ld4, nullptr);
+  tc::split(st, SWHW, n, 2L * n, 2L * n, ms->W_hi, ms->W_lo, ld4, nullptr);
+  tc::split(st, ms->Wref, n, 2L * n, 2L * n, ms->W_hi + 2L * n, ms->W_lo + 2L * n, ld4, nullptr);
+  tc::gemm(st, ms->opW, ms->opYT, 4 * n, ms->npass, tc::Epilogue{G, m, m, 0, -4.0, 1.0, n, m, nullptr, ms->err});
+  launch_gmax(st, nm, G, part);
+  launch_finish_gmax(st, sc, part);
+}
+
 void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, double* Dir, double* G,
                    double* Gold, double* PG, double* Y4, double* SWHW, double* Proj, double* part,
                    double* part2, const double* HS, const double* P, bool precond, Profiler& pf) {

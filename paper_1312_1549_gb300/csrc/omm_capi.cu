@@ -434,18 +434,27 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     // Outer loop: float64 recompute of the state (refinement / certificate),
     // then line searches until converged, halted or capped.
     for (int round = 0;; ++round) {
+      // the mixed path starts from a tensor-core state; every later state is float64
+      const bool tc_state = mixed && round == 0;
       OMM_CUDA_TRY(cudaEventRecord(c->ev[0], c->st));
-      recompute_state_fp64(c);
+      if (tc_state) {
+        mixed_recompute_state(c->mixed, c->st, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
+        flop_tc += 3.0 * per_state;
+      } else {
+        recompute_state_fp64(c);
+      }
       flop += per_state;
       OMM_CUDA_TRY(cudaEventRecord(c->ev[1], c->st));
       read_scalars(c);
-      ms_ref += elapsed(c->ev[0], c->ev[1]);
+      if (tc_state) ms_iter += elapsed(c->ev[0], c->ev[1]);
+      else ms_ref += elapsed(c->ev[0], c->ev[1]);
       Scalars& h = *c->sc_host;
       if (!std::isfinite(h.gmax) || !std::isfinite(h.E)) {
         result = OMM_ERR_NONFINITE;
         break;
       }
-      if (h.gmax < c->opts.tol_grad || energy_stop) break;  // certified (or Eq. 18 met)
+      // only a float64 state certifies (or Eq. 18 met)
+      if (!tc_state && (h.gmax < c->opts.tol_grad || energy_stop)) break;
       if (round > 0) ++refinements;
       if (iter_total >= c->opts.max_iter) {
         result = OMM_ERR_NO_CONVERGENCE;

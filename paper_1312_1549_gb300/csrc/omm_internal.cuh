@@ -96,9 +96,12 @@ class Profiler {
 // op(B) is K x N: B[k*ldb + j] (transB = 0) or B[j*ldb + k] (transB = 1).
 // tri bit 0: compute only tiles that touch the lower triangle (i >= j);
 // tri bit 1: start the K loop at max(tile row, tile col) (both operands lower-
-// triangular in the contracted index, as in L^-T L^-1).
+// triangular in the contracted index, as in L^-T L^-1);
+// tri bit 2: start the K loop at the tile's first column (op(B) lower triangular:
+// B[k][j] = 0 for k < j); tri bit 3: end it after the tile's last row (op(A)
+// lower triangular: A[i][k] = 0 for k > i).
 // `skip`: device flag pair (done, halt); when either is set the kernel returns.
-enum { kTriLower = 1, kTriKStart = 2 };
+enum { kTriLower = 1, kTriKStart = 2, kTriKFromCol = 4, kTriKToRow = 8 };
 void dgemm(cudaStream_t st, int transA, int transB, int M, int N, int K, double alpha,
            const double* A, long lda, long strideA, const double* B, long ldb, long strideB,
            double beta, double* C, long ldc, long strideC, int batch = 1, int tri = 0,

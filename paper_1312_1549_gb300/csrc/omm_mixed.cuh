@@ -14,6 +14,9 @@ void mixed_destroy(MixedState* ms);
 // after a float64 recompute: take (G, HC, SC, S_W, H_W) as the new reference
 // point of the incremental gradient and refresh the bf16 copies
 void mixed_sync_state(MixedState* ms, cudaStream_t st, const double* Y4, const double* SWHW, const double* G);
+// initial state on the tensor cores (not a certificate)
+void mixed_recompute_state(MixedState* ms, cudaStream_t st, Scalars* sc, const double* C, double* Y4,
+                           double* SWHW, double* G, double* part, double* part2);
 // nonzero if a tensor-core kernel gave up a bounded wait (synchronises the stream)
 int mixed_error(MixedState* ms, cudaStream_t st);
 void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, double* Dir, double* G,

@@ -145,7 +145,10 @@ gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_c
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  // M-fastest rasterisation: CTAs that run together share one B tile (read
+  // from DRAM once, then from L2) and sweep the small A operand
+  const int tiles_m = (ep.M + BM - 1) / BM;
+  const int m0 = (blockIdx.x % tiles_m) * BM, n0 = (blockIdx.x / tiles_m) * BN;
   const int nkb = (K + BK - 1) / BK;
   const int total = npass * nkb;
 
@@ -303,7 +306,7 @@ void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, int npass,
                                       SMEM_BYTES));
     attr_set = true;
   }
-  dim3 grid((unsigned)((ep.N + BN - 1) / BN), (unsigned)((ep.M + BM - 1) / BM));
+  dim3 grid((unsigned)(((ep.N + BN - 1) / BN) * ((ep.M + BM - 1) / BM)));
   const CUtensorMap* a_hi = reinterpret_cast<const CUtensorMap*>(&A.hi);
   const CUtensorMap* a_lo = reinterpret_cast<const CUtensorMap*>(&A.lo);
   const CUtensorMap* b_hi = reinterpret_cast<const CUtensorMap*>(&B.hi);
