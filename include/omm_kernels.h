@@ -60,6 +60,23 @@ omm_status omm_kernel_quartic_coefficients(int n, const double* SWHW, const doub
 omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double* B, double alpha,
                               double beta, double* C, int npass, void* stream);
 
+/* omm_kernel_quartic_coefficients for callers that cannot allocate device
+ * memory (a runtime whose memory pool owns the whole device, a path that must
+ * not let cudaMalloc/cudaFree synchronise the device, an embedding that must
+ * not grow its footprint after start-up). The paper has no counterpart: this
+ * is a deployment variant of the step above with the same arguments and
+ * results. It calls no cudaMalloc, cudaFree or allocating library routine;
+ * its scratch (trace partial sums and a control block) is one static device
+ * array of about 361 KB that every GPU loading the library keeps until the
+ * process exits. Limit: n <= 2048 (larger n returns OMM_ERR_ARG and leaves
+ * alpha untouched). The first call on each device, made with that device
+ * current, looks the array's device address up (cudaGetSymbolAddress); make
+ * that first call before any stream capture. All calls share the array:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller. Errors: OMM_ERR_ARG, OMM_ERR_CUDA. */
+omm_status omm_kernel_quartic_coefficients_noalloc(int n, const double* SWHW, const double* Proj,
+                                                   double E, double* alpha, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
