@@ -60,6 +60,20 @@ omm_status omm_kernel_quartic_coefficients(int n, const double* SWHW, const doub
 omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double* B, double alpha,
                               double beta, double* C, int npass, void* stream);
 
+/* Float64-class contraction on the BF16 tensor cores, as the mixed path
+ * refreshes its state (float64 emulation by error-free fixed-point slicing:
+ * Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59, 2012): C = alpha A B^T +
+ * beta C with A M x K, B N x K, C M x N row-major float64. Every row of A and
+ * of B is cut into `slices` (1..10) bf16 slices of 5 bits each below a
+ * power-of-two row scale; the slice products of one level are exact in the
+ * FP32 accumulator for K <= 16384 and are summed in float64. Each slice adds
+ * 5 bits: with s slices the error is about 2^-5s times (row maximum of A) x
+ * (row maximum of B) x K. Scratch is allocated and freed inside
+ * the call. Errors: OMM_ERR_ARG (including K > 16384), OMM_ERR_OOM,
+ * OMM_ERR_TIMEOUT, OMM_ERR_CUDA. */
+omm_status omm_kernel_gemm_emu(int M, int N, int K, const double* A, const double* B, double alpha,
+                               double beta, double* C, int slices, void* stream);
+
 /* omm_kernel_quartic_coefficients for callers that cannot allocate device
  * memory (a runtime whose memory pool owns the whole device, a path that must
  * not let cudaMalloc/cudaFree synchronise the device, an embedding that must

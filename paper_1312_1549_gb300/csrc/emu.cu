@@ -1,0 +1,221 @@
+// Float64-class contractions on the BF16 tensor cores by error-free
+// fixed-point slicing (the Ozaki scheme: K. Ozaki, T. Ogita, S. Oishi,
+// S. M. Rump, "Error-free transformations of matrix multiplication by using
+// fast routines of matrix multiplication and its applications", Numerical
+// Algorithms 59 (2012)), used by the mixed path to refresh its state.
+//
+// Slicing: every row r of an operand gets a power of two sigma_r > 2 max|x|
+// over the row, and x = sigma_r * sum_i a_i 2^-5(i+1) + O(sigma_r 2^-5s) with
+// integers |a_i| <= 16 (bf16 holds a_i * 2^k exactly). For a pair of slices
+// (i, j) every product a b <= 256 units of 2^(e_r + f_c - 5(i+j+2)), so all
+// products of one level d = i + j share one unit per output element and a
+// level of (d+1) pairs summed over K stays an integer below (d+1) K 256
+// units: exact in the FP32 accumulator while that is <= 2^24. Each launch
+// therefore takes at most 2^24 / (256 K) pairs of one level (all pairs of a
+// level for K <= 1638, nine for the Si512 contraction K = 6656), so every
+// launch is exact and the float64 epilogue sums the launches. (Lumping
+// several levels into one FP32 accumulator is not exact: the tensor cores'
+// FP32 adder truncates, and those errors grow linearly with K — measured
+// 1e-10 of |A||B| at K = 1000.) With s = 10 slices the result carries about
+// 50 bits of each row-scaled operand.
+#include "emu.cuh"
+#include "tc_gemm.cuh"
+
+#include <new>
+
+namespace omm {
+namespace {
+
+constexpr int kSliceBits = 5;
+
+__device__ __forceinline__ bool stopped(const Scalars* sc) { return sc != nullptr && (sc->done | sc->halt); }
+
+// one warp per row
+__global__ void slice_rows_kernel(const double* __restrict__ src, long rows, long cols, long ld_src, int s,
+                                  __nv_bfloat16* __restrict__ dst, long ld_dst, long slice_stride,
+                                  const Scalars* sc) {
+  if (stopped(sc)) return;
+  const long row = (long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const double* x = src + row * ld_src;
+  double mx = 0.0;
+  for (long c = lane; c < cols; c += 32) mx = fmax(mx, fabs(x[c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);  // mx < 2^e
+  const int esig = e + 1;        // sigma = 2^(e+1) > 2 max|x|
+  __nv_bfloat16* out = dst + row * ld_dst;
+  for (long c = lane; c < cols; c += 32) {
+    double r = ldexp(x[c], -esig);  // |r| < 1/2, exact
+    for (int i = 0; i < s; ++i) {
+      const double t = r * 32.0;
+      const double a = rint(t);
+      r = t - a;
+      out[i * slice_stride + c] = __double2bfloat16(ldexp(a, esig - kSliceBits * (i + 1)));
+    }
+  }
+}
+
+// dst (cols x rows) = src^T, 32 x 32 shared-memory tiles
+__global__ void transpose_kernel(const double* __restrict__ src, long rows, long cols, long ld_src,
+                                 double* __restrict__ dst, long ld_dst) {
+  __shared__ double tile[32][33];
+  const long tiles_c = (cols + 31) / 32;
+  const long r0 = (blockIdx.x / tiles_c) * 32, c0 = (blockIdx.x % tiles_c) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int k = ty; k < 32; k += 8) {
+    const long r = r0 + k, c = c0 + tx;
+    tile[k][tx] = (r < rows && c < cols) ? src[r * ld_src + c] : 0.0;
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const long c = c0 + k, r = r0 + tx;
+    if (c < cols && r < rows) dst[c * ld_dst + r] = tile[tx][k];
+  }
+}
+
+long round8(long x) { return (x + 7) / 8 * 8; }
+
+template <typename T>
+void alloc(T** p, size_t count) {
+  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    throw std::bad_alloc();
+  }
+}
+
+}  // namespace
+
+namespace emu {
+
+void slice_rows(cudaStream_t st, const double* src, long rows, long cols, long ld_src, int s,
+                __nv_bfloat16* dst, long ld_dst, const Scalars* sc) {
+  if (rows <= 0) return;
+  const int warps = 8;
+  const long blocks = (rows + warps - 1) / warps;
+  slice_rows_kernel<<<(unsigned)blocks, warps * 32, 0, st>>>(src, rows, cols, ld_src, s, dst, ld_dst,
+                                                               rows * ld_dst, sc);
+  OMM_LAUNCH_CHECK();
+}
+
+void transpose(cudaStream_t st, const double* src, long rows, long cols, long ld_src, double* dst, long ld_dst) {
+  const long blocks = ((rows + 31) / 32) * ((cols + 31) / 32);
+  transpose_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, rows, cols, ld_src, dst, ld_dst);
+  OMM_LAUNCH_CHECK();
+}
+
+void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep) {
+  // Every launch accumulates at most g slice pairs of one level, so that its
+  // FP32 sum of integer units stays below 2^24 and is exact; the float64
+  // epilogue adds the launches, smallest level first.
+  const long g_max = (1L << 24) / (256L * (K > 0 ? K : 1));
+  const int g = (int)(g_max < 1 ? 1 : (g_max > tc::kMaxPairs ? tc::kMaxPairs : g_max));
+  tc::Epilogue e = ep;
+  bool first = true;
+  for (int d = s - 1; d >= 0; --d) {
+    for (int i0 = 0; i0 <= d; i0 += g) {
+      tc::PairList pl{};
+      for (int i = i0; i <= d && i < i0 + g; ++i) {
+        pl.a[pl.n] = (unsigned char)i;
+        pl.b[pl.n] = (unsigned char)(d - i);
+        ++pl.n;
+      }
+      e.beta = first ? ep.beta : 1.0;
+      tc::gemm(st, A, B, K, pl, e);
+      first = false;
+    }
+  }
+}
+
+}  // namespace emu
+
+struct EmuState {
+  int m = 0, n = 0, s = 0;
+  long ldm = 0, ld2n = 0;
+  __nv_bfloat16* HSs = nullptr;  // s slices of [H~; S]     2m x m
+  __nv_bfloat16* Cs = nullptr;   // s slices of C           n x m
+  __nv_bfloat16* Ys = nullptr;   // s slices of [HC; SC]    2n x m
+  __nv_bfloat16* Ws = nullptr;   // s slices of [S_W | H_W] n x 2n
+  __nv_bfloat16* YTs = nullptr;  // s slices of [HC | SC]^T m x 2n
+  double* T64 = nullptr;         // [HC; SC]^T in float64  m x 2n
+  tc::Operand opHS, opC, opY, opW, opYT;
+  int* err = nullptr;
+};
+
+EmuState* emu_create(cudaStream_t st, int m, int n, int slices, const double* HS) {
+  EmuState* es = new EmuState();
+  try {
+    es->m = m;
+    es->n = n;
+    es->s = slices;
+    es->ldm = round8(m);
+    es->ld2n = round8(2L * n);
+    const long s = slices, ldm = es->ldm, ld2n = es->ld2n;
+    alloc(&es->HSs, (size_t)s * 2 * m * ldm);
+    alloc(&es->Cs, (size_t)s * n * ldm);
+    alloc(&es->Ys, (size_t)s * 2 * n * ldm);
+    alloc(&es->Ws, (size_t)s * n * ld2n);
+    alloc(&es->YTs, (size_t)s * m * ld2n);
+    alloc(&es->T64, (size_t)m * 2 * n);
+    alloc(&es->err, 1);
+    OMM_CUDA_TRY(cudaMemsetAsync(es->err, 0, sizeof(int), st));
+    emu::slice_rows(st, HS, 2L * m, m, m, slices, es->HSs, ldm, nullptr);
+    es->opHS = tc::make_operand(es->HSs, 2L * m, m, ldm, slices, false);
+    es->opC = tc::make_operand(es->Cs, n, m, ldm, slices, true);
+    es->opY = tc::make_operand(es->Ys, 2L * n, m, ldm, slices, false);
+    es->opW = tc::make_operand(es->Ws, n, 2L * n, ld2n, slices, true);
+    es->opYT = tc::make_operand(es->YTs, m, 2L * n, ld2n, slices, false);
+  } catch (...) {
+    emu_destroy(es);
+    throw;
+  }
+  return es;
+}
+
+void emu_update_H(EmuState* es, cudaStream_t st, const double* HS) {
+  emu::slice_rows(st, HS, 2L * es->m, es->m, es->m, es->s, es->HSs, es->ldm, nullptr);
+}
+
+void emu_destroy(EmuState* es) {
+  if (!es) return;
+  void* bufs[] = {es->HSs, es->Cs, es->Ys, es->Ws, es->YTs, es->T64, es->err};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete es;
+}
+
+int emu_error(EmuState* es, cudaStream_t st) {
+  int e = 0;
+  OMM_CUDA_TRY(cudaMemcpyAsync(&e, es->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  OMM_CUDA_TRY(cudaStreamSynchronize(st));
+  return e;
+}
+
+// HC, SC, S_W, H_W, E~, G and max|G| from C with float64-class tensor-core products.
+void emu_recompute_state(EmuState* es, cudaStream_t st, Scalars* sc, const double* C, double* Y4,
+                         double* SWHW, double* G, double* part, double* part2) {
+  const int m = es->m, n = es->n, s = es->s;
+  const long nm = (long)n * m;
+  emu::slice_rows(st, C, n, m, m, s, es->Cs, es->ldm, nullptr);
+  // [HC; SC] (n x m layout) = C [H~; S]^T
+  emu::gemm(st, es->opC, es->opHS, m, s, tc::Epilogue{Y4, m, m, nm, 1.0, 0.0, n, 2 * m, nullptr, es->err});
+  emu::slice_rows(st, Y4, 2L * n, m, m, s, es->Ys, es->ldm, nullptr);
+  // [S_W | H_W] = C [SC; HC]^T
+  emu::gemm(st, es->opC, es->opY, m, s,
+            tc::Epilogue{SWHW + n, 2L * n, n, -(long)n, 1.0, 0.0, n, 2 * n, nullptr, es->err});
+  launch_functional(st, n, SWHW, part2);
+  launch_finish_functional(st, sc, part2, traces_blocks(n));
+  // G = 8 HC - 4 [S_W | H_W] [HC; SC]
+  emu::slice_rows(st, SWHW, n, 2L * n, 2L * n, s, es->Ws, es->ld2n, nullptr);
+  emu::transpose(st, Y4, 2L * n, m, m, es->T64, 2L * n);
+  emu::slice_rows(st, es->T64, m, 2L * n, 2L * n, s, es->YTs, es->ld2n, nullptr);
+  launch_scale_copy(st, nm, Y4, 8.0, G, nullptr);
+  emu::gemm(st, es->opW, es->opYT, 2 * n, s, tc::Epilogue{G, m, m, 0, -4.0, 1.0, n, m, nullptr, es->err});
+  launch_gmax(st, nm, G, part);
+  launch_finish_gmax(st, sc, part);
+}
+
+}  // namespace omm

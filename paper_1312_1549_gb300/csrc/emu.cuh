@@ -1,0 +1,25 @@
+// Float64-class contractions on the BF16 tensor cores (fixed-point slicing).
+#pragma once
+#include <cuda_bf16.h>
+#include "omm_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace omm {
+namespace emu {
+// s fixed-point bf16 slices of each row of src (rows x cols), stacked: slice i at dst + i*rows*ld_dst
+void slice_rows(cudaStream_t st, const double* src, long rows, long cols, long ld_src, int s,
+                __nv_bfloat16* dst, long ld_dst, const Scalars* sc);
+void transpose(cudaStream_t st, const double* src, long rows, long cols, long ld_src, double* dst, long ld_dst);
+// C = alpha A B^T + beta C from s-slice operands (A, B made by slice_rows)
+void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep);
+}  // namespace emu
+
+struct EmuState;
+EmuState* emu_create(cudaStream_t st, int m, int n, int slices, const double* HS);
+void emu_update_H(EmuState* es, cudaStream_t st, const double* HS);
+void emu_destroy(EmuState* es);
+int emu_error(EmuState* es, cudaStream_t st);
+void emu_recompute_state(EmuState* es, cudaStream_t st, Scalars* sc, const double* C, double* Y4,
+                         double* SWHW, double* G, double* part, double* part2);
+
+}  // namespace omm

@@ -2,6 +2,7 @@
 #include "../../include/omm_kernels.h"
 #include "omm_internal.cuh"
 #include "tc_gemm.cuh"
+#include "emu.cuh"
 
 #include <cstring>
 #include <string>
@@ -150,8 +151,8 @@ omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double
     OMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     tc::split(st, A, M, K, K, a_hi, a_lo, ld, nullptr);
     tc::split(st, B, N, K, K, b_hi, b_lo, ld, nullptr);
-    tc::Operand oa = tc::make_operand(a_hi, a_lo, M, K, ld, true);
-    tc::Operand ob = tc::make_operand(b_hi, b_lo, N, K, ld, false);
+    tc::Operand oa = tc::make_operand(a_hi, M, K, ld, 2, true);
+    tc::Operand ob = tc::make_operand(b_hi, N, K, ld, 2, false);
     tc::gemm(st, oa, ob, K, npass, tc::Epilogue{C, N, N, 0, alpha, beta, M, N, nullptr, err});
     int h = 0;
     OMM_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -162,6 +163,47 @@ omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double
     }
   } catch (const CudaError& e) {
     rc = cuda_fail("omm_kernel_gemm_tc", e);
+  }
+  if (buf) cudaFree(buf);
+  if (err) cudaFree(err);
+  return rc;
+}
+
+omm_status omm_kernel_gemm_emu(int M, int N, int K, const double* A, const double* B, double alpha,
+                               double beta, double* C, int slices, void* stream) {
+  if (M <= 0 || N <= 0 || K <= 0 || K > 16384 || !A || !B || !C || slices < 1 || slices > 10) {
+    set_last_error("omm_kernel_gemm_emu: invalid argument");
+    return OMM_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const long ld = (K + 7) / 8 * 8;
+  __nv_bfloat16* buf = nullptr;
+  int* err = nullptr;
+  omm_status rc = OMM_OK;
+  try {
+    const size_t na = (size_t)slices * M * ld, nb = (size_t)slices * N * ld;
+    if (cudaMalloc((void**)&buf, (na + nb) * sizeof(__nv_bfloat16)) != cudaSuccess ||
+        cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      if (buf) cudaFree(buf);
+      set_last_error("omm_kernel_gemm_emu: device allocation failed");
+      return OMM_ERR_OOM;
+    }
+    OMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    emu::slice_rows(st, A, M, K, K, slices, buf, ld, nullptr);
+    emu::slice_rows(st, B, N, K, K, slices, buf + na, ld, nullptr);
+    tc::Operand oa = tc::make_operand(buf, M, K, ld, slices, true);
+    tc::Operand ob = tc::make_operand(buf + na, N, K, ld, slices, false);
+    emu::gemm(st, oa, ob, K, slices, tc::Epilogue{C, N, N, 0, alpha, beta, M, N, nullptr, err});
+    int h = 0;
+    OMM_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h != 0) {
+      set_last_error("omm_kernel_gemm_emu: a bounded device wait expired");
+      rc = OMM_ERR_TIMEOUT;
+    }
+  } catch (const CudaError& e) {
+    rc = cuda_fail("omm_kernel_gemm_emu", e);
   }
   if (buf) cudaFree(buf);
   if (err) cudaFree(err);

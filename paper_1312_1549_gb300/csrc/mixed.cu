@@ -63,39 +63,34 @@ MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const 
     ms->ld2n = round8(4L * n);  // leading dimension of the 4n-wide gradient operands
     ms->precond = (P != nullptr);
     const long ldm = ms->ldm, ld2n = ms->ld2n;
-    alloc(&ms->HS_hi, 2L * m * ldm);
-    alloc(&ms->HS_lo, 2L * m * ldm);
-    if (ms->precond) {
-      alloc(&ms->P_hi, (size_t)m * ldm);
-      alloc(&ms->P_lo, (size_t)m * ldm);
-    }
-    alloc(&ms->G_hi, (size_t)n * ldm);
-    alloc(&ms->G_lo, (size_t)n * ldm);
-    alloc(&ms->D_hi, (size_t)n * ldm);
-    alloc(&ms->D_lo, (size_t)n * ldm);
-    alloc(&ms->Y_hi, 4L * n * ldm);
-    alloc(&ms->Y_lo, 4L * n * ldm);
-    alloc(&ms->YT_hi, (size_t)m * ld2n);
-    alloc(&ms->YT_lo, (size_t)m * ld2n);
-    alloc(&ms->W_hi, (size_t)n * ld2n);
-    alloc(&ms->W_lo, (size_t)n * ld2n);
+    // each split operand is one allocation holding the stack [hi; lo]
+    auto pair = [](__nv_bfloat16** hi, __nv_bfloat16** lo, long rows, long ld) {
+      alloc(hi, 2 * (size_t)rows * ld);
+      *lo = *hi + rows * ld;
+    };
+    pair(&ms->HS_hi, &ms->HS_lo, 2L * m, ldm);
+    if (ms->precond) pair(&ms->P_hi, &ms->P_lo, m, ldm);
+    pair(&ms->G_hi, &ms->G_lo, n, ldm);
+    pair(&ms->D_hi, &ms->D_lo, n, ldm);
+    pair(&ms->Y_hi, &ms->Y_lo, 4L * n, ldm);
+    pair(&ms->YT_hi, &ms->YT_lo, m, ld2n);
+    pair(&ms->W_hi, &ms->W_lo, n, ld2n);
     alloc(&ms->Gref, (size_t)n * m);
     alloc(&ms->dY, 2L * n * m);
     alloc(&ms->Wref, 2L * n * n);
     alloc(&ms->err, 1);
     OMM_CUDA_TRY(cudaMemsetAsync(ms->err, 0, sizeof(int), st));
     // padding columns stay zero (the tensor maps never read them, but keep them defined)
-    OMM_CUDA_TRY(cudaMemsetAsync(ms->YT_hi, 0, (size_t)m * ld2n * 2, st));
-    OMM_CUDA_TRY(cudaMemsetAsync(ms->YT_lo, 0, (size_t)m * ld2n * 2, st));
+    OMM_CUDA_TRY(cudaMemsetAsync(ms->YT_hi, 0, 2 * (size_t)m * ld2n * 2, st));
     tc::split(st, HS, 2L * m, m, m, ms->HS_hi, ms->HS_lo, ldm, nullptr);
     if (ms->precond) tc::split(st, P, m, m, m, ms->P_hi, ms->P_lo, ldm, nullptr);
-    ms->opHS = tc::make_operand(ms->HS_hi, ms->HS_lo, 2L * m, m, ldm, false);
-    if (ms->precond) ms->opP = tc::make_operand(ms->P_hi, ms->P_lo, m, m, ldm, false);
-    ms->opG = tc::make_operand(ms->G_hi, ms->G_lo, n, m, ldm, true);
-    ms->opD = tc::make_operand(ms->D_hi, ms->D_lo, n, m, ldm, true);
-    ms->opY = tc::make_operand(ms->Y_hi, ms->Y_lo, 4L * n, m, ldm, false);
-    ms->opYT = tc::make_operand(ms->YT_hi, ms->YT_lo, m, 4L * n, ld2n, false);
-    ms->opW = tc::make_operand(ms->W_hi, ms->W_lo, n, 4L * n, ld2n, true);
+    ms->opHS = tc::make_operand(ms->HS_hi, 2L * m, m, ldm, 2, false);
+    if (ms->precond) ms->opP = tc::make_operand(ms->P_hi, m, m, ldm, 2, false);
+    ms->opG = tc::make_operand(ms->G_hi, n, m, ldm, 2, true);
+    ms->opD = tc::make_operand(ms->D_hi, n, m, ldm, 2, true);
+    ms->opY = tc::make_operand(ms->Y_hi, 4L * n, m, ldm, 2, false);
+    ms->opYT = tc::make_operand(ms->YT_hi, m, 4L * n, ld2n, 2, false);
+    ms->opW = tc::make_operand(ms->W_hi, n, 4L * n, ld2n, 2, true);
   } catch (...) {
     mixed_destroy(ms);
     throw;
@@ -109,8 +104,7 @@ void mixed_update_H(MixedState* ms, cudaStream_t st, const double* HS) {
 
 void mixed_destroy(MixedState* ms) {
   if (!ms) return;
-  __nv_bfloat16* bufs[] = {ms->HS_hi, ms->HS_lo, ms->P_hi, ms->P_lo, ms->G_hi, ms->G_lo, ms->D_hi,
-                           ms->D_lo, ms->Y_hi, ms->Y_lo, ms->YT_hi, ms->YT_lo, ms->W_hi, ms->W_lo};
+  __nv_bfloat16* bufs[] = {ms->HS_hi, ms->P_hi, ms->G_hi, ms->D_hi, ms->Y_hi, ms->YT_hi, ms->W_hi};
   for (auto* b : bufs)
     if (b) cudaFree(b);
   if (ms->err) cudaFree(ms->err);

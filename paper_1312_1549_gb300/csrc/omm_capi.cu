@@ -13,6 +13,7 @@
 #include "../../include/omm.h"
 #include "omm_internal.cuh"
 #include "omm_mixed.cuh"
+#include "emu.cuh"
 
 #include <algorithm>
 #include <atomic>
@@ -101,12 +102,14 @@ struct omm_ctx {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double ms_setup = 0.0;
   MixedState* mixed = nullptr;
+  EmuState* emu = nullptr;  // float64-class tensor-core refresh of the mixed path
   Profiler prof;  // main contraction kernel of the iteration (tensor-core or float64 GEMM)
 };
 
 namespace {
 
 constexpr int kMixedRoundCap = 400;
+constexpr int kEmuSlices = 10;  // fixed-point slices of the float64-class refresh (about 50 bits)
 
 struct Status {
   omm_status s;
@@ -273,6 +276,7 @@ void destroy(omm_ctx* c) {
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->mixed) mixed_destroy(c->mixed);
+  if (c->emu) emu_destroy(c->emu);
   delete c;
 }
 
@@ -364,7 +368,10 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     dev_alloc(&c->nn, (size_t)n * n);
     dev_alloc(&c->part, (size_t)kReduceBlocks * 4);
     dev_alloc(&c->part2, (size_t)traces_blocks(n) * kNumTraces);
-    if (o.precision == OMM_PREC_MIXED) c->mixed = mixed_create(c->st, m, n, c->HS, c->P);
+    if (o.precision == OMM_PREC_MIXED) {
+      c->mixed = mixed_create(c->st, m, n, c->HS, c->P);
+      c->emu = emu_create(c->st, m, n, kEmuSlices, c->HS);
+    }
     OMM_CUDA_TRY(cudaEventRecord(c->ev[1], c->st));
     int info = 0;
     OMM_CUDA_TRY(cudaMemcpyAsync(&info, c->info_dev, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -400,6 +407,7 @@ omm_status omm_update_H(omm_ctx* c, const double* H) {
     copy_in(c->HS, H, mm, c->st);
     launch_axpby_shift(c->st, mm, c->HS, c->HS + mm, c->eta, c->HS);
     if (c->mixed) mixed_update_H(c->mixed, c->st, c->HS);
+    if (c->emu) emu_update_H(c->emu, c->st, c->HS);
     OMM_CUDA_TRY(cudaStreamSynchronize(c->st));
     c->solved = false;
   } catch (const CudaError& e) {
@@ -431,15 +439,26 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     int iter_total = 0;
     double g_ref = -1.0;  // max|G| at the last float64 recompute
     bool energy_stop = false;
+    bool last_round_done = false;  // the last mixed round ended on the device's convergence test
     // Outer loop: float64 recompute of the state (refinement / certificate),
     // then line searches until converged, halted or capped.
     for (int round = 0;; ++round) {
       // the mixed path starts from a tensor-core state; every later state is float64
+      // mixed path: a tensor-core first state, float64-class (sliced) refreshes while the
+      // device asks for them, and a native float64 state once it reports convergence
       const bool tc_state = mixed && round == 0;
+      const bool emu_state = mixed && round > 0 && !last_round_done;
       OMM_CUDA_TRY(cudaEventRecord(c->ev[0], c->st));
       if (tc_state) {
         mixed_recompute_state(c->mixed, c->st, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
         flop_tc += 3.0 * per_state;
+      } else if (emu_state) {
+        emu_recompute_state(c->emu, c->st, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
+        flop_tc += 0.5 * kEmuSlices * (kEmuSlices + 1) * per_state;
+        if (emu_error(c->emu, c->st) != 0) {
+          result = OMM_ERR_TIMEOUT;
+          break;
+        }
       } else {
         recompute_state_fp64(c);
       }
@@ -453,8 +472,8 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
         result = OMM_ERR_NONFINITE;
         break;
       }
-      // only a float64 state certifies (or Eq. 18 met)
-      if (!tc_state && (h.gmax < c->opts.tol_grad || energy_stop)) break;
+      // only a native float64 state certifies (or Eq. 18 met)
+      if (!tc_state && !emu_state && (h.gmax < c->opts.tol_grad || energy_stop)) break;
       if (round > 0) ++refinements;
       if (iter_total >= c->opts.max_iter) {
         result = OMM_ERR_NO_CONVERGENCE;
@@ -509,6 +528,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
       }
       // done (device-side convergence) or a refinement request: recompute and test
       if (h.done && h.stop_reason == 2) energy_stop = true;
+      last_round_done = h.done != 0;
     }
     Scalars& h = *c->sc_host;
     inf.iterations = iter_total;

@@ -7,9 +7,11 @@
 //   warps 2-5   epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator,
 //               C = alpha * acc + beta * C written in float64
 // Each CTA computes one 128 x 256 tile of C = A B^T with A (M x K) and
-// B (N x K) both K-major bf16. "Split" operands x = x_hi + x_lo are
-// contracted as A_hi B_hi + A_hi B_lo + A_lo B_hi (three passes over K into
-// the same accumulator), which keeps about 16 significant bits.
+// B (N x K) both K-major bf16. Operands are stacks of slices; a pair list
+// says which slice products are accumulated (passes over K into the same
+// accumulator). "Split" operands x = x_hi + x_lo use the three pairs
+// A_hi B_hi + A_hi B_lo + A_lo B_hi, which keep about 16 significant bits;
+// the float64 emulation (emu_gemm.cu) uses fixed-point slices.
 //
 // Every wait on an mbarrier is bounded (globaltimer, 2 s): on expiry the
 // kernel records an error code, stops issuing work and frees its TMEM.
@@ -133,9 +135,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1)
-gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
-                       const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
-                       int K, int npass, Epilogue ep) {
+gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+                       int K, int rowsA, int rowsB, const __grid_constant__ PairList pl, Epilogue ep) {
   if (ep.skip != nullptr && (ep.skip[0] | ep.skip[1])) return;  // uniform: before any resource use
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -150,7 +151,7 @@ gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_c
   const int tiles_m = (ep.M + BM - 1) / BM;
   const int m0 = (blockIdx.x % tiles_m) * BM, n0 = (blockIdx.x / tiles_m) * BN;
   const int nkb = (K + BK - 1) / BK;
-  const int total = npass * nkb;
+  const int total = pl.n * nkb;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -175,12 +176,8 @@ gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_c
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    prefetch_tmap(&mA_hi);
-    prefetch_tmap(&mB_hi);
-    if (npass > 1) {
-      prefetch_tmap(&mA_lo);
-      prefetch_tmap(&mB_lo);
-    }
+    prefetch_tmap(&mA);
+    prefetch_tmap(&mB);
     for (int t = 0; t < total; ++t) {
       const int s = t % STAGES, r = t / STAGES;
       if (!mbar_wait(smem_u32(&bars[STAGES + s]), (r & 1) ^ 1)) {
@@ -189,14 +186,12 @@ gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_c
         break;
       }
       if (*abort_flag) break;
-      const int pass = t / nkb, kb = t % nkb;
-      const CUtensorMap* a = (pass == 2) ? &mA_lo : &mA_hi;
-      const CUtensorMap* b = (pass == 1) ? &mB_lo : &mB_hi;
+      const int p = t / nkb, kb = t % nkb;
       const uint32_t full = smem_u32(&bars[s]);
       const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
       mbar_expect_tx(full, STAGE_BYTES);
-      tma_load_2d(sa, a, full, kb * BK, m0);
-      tma_load_2d(sa + A_BYTES, b, full, kb * BK, n0);
+      tma_load_2d(sa, &mA, full, kb * BK, (int)pl.a[p] * rowsA + m0);
+      tma_load_2d(sa + A_BYTES, &mB, full, kb * BK, (int)pl.b[p] * rowsB + n0);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
@@ -289,29 +284,44 @@ TensorMap make_map(const __nv_bfloat16* base, long rows, long cols, long ld, int
   return tm;
 }
 
-Operand make_operand(const __nv_bfloat16* hi, const __nv_bfloat16* lo, long rows, long cols, long ld, bool is_a) {
+Operand make_operand(const __nv_bfloat16* base, long rows, long cols, long ld, int slices, bool is_a) {
   Operand o;
-  const int box = is_a ? BM : BN;
-  o.hi = make_map(hi, rows, cols, ld, box);
-  o.lo = make_map(lo ? lo : hi, rows, cols, ld, box);
+  o.map = make_map(base, rows * slices, cols, ld, is_a ? BM : BN);
   o.rows = rows;
   o.cols = cols;
+  o.slices = slices;
   return o;
 }
 
-void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, int npass, const Epilogue& ep) {
+PairList pairs_split3() {
+  PairList p{};
+  p.n = 3;
+  p.a[0] = 0; p.b[0] = 0;
+  p.a[1] = 0; p.b[1] = 1;
+  p.a[2] = 1; p.b[2] = 0;
+  return p;
+}
+
+PairList pairs_single() {
+  PairList p{};
+  p.n = 1;
+  return p;
+}
+
+void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const PairList& pl, const Epilogue& ep) {
   static bool attr_set = false;
   if (!attr_set) {
     OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       SMEM_BYTES));
     attr_set = true;
   }
+  if (pl.n <= 0 || pl.n > kMaxPairs) throw CudaError{cudaErrorInvalidValue, "tc::gemm: pair list"};
+  for (int p = 0; p < pl.n; ++p)
+    if (pl.a[p] >= A.slices || pl.b[p] >= B.slices) throw CudaError{cudaErrorInvalidValue, "tc::gemm: slice index"};
   dim3 grid((unsigned)(((ep.N + BN - 1) / BN) * ((ep.M + BM - 1) / BM)));
-  const CUtensorMap* a_hi = reinterpret_cast<const CUtensorMap*>(&A.hi);
-  const CUtensorMap* a_lo = reinterpret_cast<const CUtensorMap*>(&A.lo);
-  const CUtensorMap* b_hi = reinterpret_cast<const CUtensorMap*>(&B.hi);
-  const CUtensorMap* b_lo = reinterpret_cast<const CUtensorMap*>(&B.lo);
-  gemm_bf16_split_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(*a_hi, *a_lo, *b_hi, *b_lo, K, npass, ep);
+  const CUtensorMap* a = reinterpret_cast<const CUtensorMap*>(&A.map);
+  const CUtensorMap* b = reinterpret_cast<const CUtensorMap*>(&B.map);
+  gemm_bf16_split_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(*a, *b, K, (int)A.rows, (int)B.rows, pl, ep);
   OMM_LAUNCH_CHECK();
 }
 

@@ -11,11 +11,25 @@ struct alignas(64) TensorMap {
   unsigned char bytes[128];
 };
 
-// A bf16 operand x = hi + lo, row-major rows x cols (contracted dimension = cols).
+// A bf16 operand made of `slices` row-major matrices (rows x cols each, the
+// contracted dimension is cols) stacked vertically in one allocation with
+// leading dimension ld: slice i starts at row i * rows. A split pair
+// x = hi + lo is the 2-slice stack [hi; lo].
 struct Operand {
-  TensorMap hi, lo;
+  TensorMap map;
   long rows = 0, cols = 0;
+  int slices = 1;
 };
+
+// Which slice products one GEMM accumulates into its FP32 accumulator.
+constexpr int kMaxPairs = 64;
+struct PairList {
+  int n;
+  unsigned char a[kMaxPairs];
+  unsigned char b[kMaxPairs];
+};
+PairList pairs_split3();   // A_hi B_hi + A_hi B_lo + A_lo B_hi
+PairList pairs_single();   // A_0 B_0
 
 // C (float64) = alpha * acc + beta * C over the valid M x N block. Output
 // column j goes to C + (j / split_cols) * split_stride + row * ldc + j % split_cols
@@ -35,9 +49,14 @@ struct Epilogue {
   int* err;
 };
 
-Operand make_operand(const __nv_bfloat16* hi, const __nv_bfloat16* lo, long rows, long cols, long ld, bool is_a);
-// npass = 3: A_hi B_hi + A_hi B_lo + A_lo B_hi; npass = 1: A_hi B_hi.
-void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, int npass, const Epilogue& ep);
+// base: 16-byte aligned; ld * 2 bytes a multiple of 16.
+Operand make_operand(const __nv_bfloat16* base, long rows, long cols, long ld, int slices, bool is_a);
+// C = alpha * sum_p A_{pl.a[p]} B_{pl.b[p]}^T + beta * C (FP32 accumulation, float64 epilogue)
+void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const PairList& pl, const Epilogue& ep);
+// the npass convention of the split form: 3 -> pairs_split3(), 1 -> pairs_single()
+inline void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, int npass, const Epilogue& ep) {
+  gemm(st, A, B, K, npass == 3 ? pairs_split3() : pairs_single(), ep);
+}
 int tile_m();
 int tile_n();
 

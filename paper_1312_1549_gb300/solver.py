@@ -163,6 +163,15 @@ def gemm_tc(A, B, C, alpha=1.0, beta=0.0, npass=3, stream=None):
     return C
 
 
+def gemm_emu(A, B, C, alpha=1.0, beta=0.0, slices=10, stream=None):
+    """C = alpha A B^T + beta C, float64-class, on the BF16 tensor cores (fixed-point slices)."""
+    M, K = A.shape
+    Nn = B.shape[0]
+    N.check(N.lib().omm_kernel_gemm_emu(M, Nn, K, _ptr(A), _ptr(B), float(alpha), float(beta), _ptr(C),
+                                        int(slices), _stream_handle(stream)), "omm_kernel_gemm_emu")
+    return C
+
+
 def launch_count():
     """Kernels launched by the library in this process."""
     return int(N.lib().omm_launch_count())

@@ -90,3 +90,29 @@ def test_mixed_solve_without_preconditioner(S, si64):
     assert info["status"] == 0
     assert abs(E - ex["E"]) / abs(ex["E"]) <= 1e-9
     assert np.abs(D.cpu().numpy() - ex["D"]).max() <= 1e-7
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (200, 300, 1000), (64, 1000, 6656), (130, 70, 16384)])
+def test_gemm_emu_is_float64_class(S, M, N, K):
+    """10 fixed-point slices: error within 2^-44 of |alpha||A||B|^T + |beta C| elementwise."""
+    rng = np.random.default_rng(M * N + K)
+    A = rng.normal(size=(M, K)) * np.exp(rng.normal(size=(M, 1)))   # rows of different scales
+    B = rng.normal(size=(N, K))
+    C0 = rng.normal(size=(M, N))
+    C = dev(C0)
+    S.gemm_emu(dev(A), dev(B), C, alpha=-4.0, beta=1.0, slices=10)
+    ref = -4.0 * A @ B.T + C0
+    scale = 4.0 * np.abs(A) @ np.abs(B).T + np.abs(C0)
+    assert np.all(np.abs(C.cpu().numpy() - ref) <= 2.0 ** -44 * scale)
+
+
+def test_gemm_emu_error_falls_with_slices(S):
+    rng = np.random.default_rng(5)
+    A = rng.normal(size=(128, 512)); B = rng.normal(size=(256, 512))
+    ref = A @ B.T
+    errs = []
+    for s in (2, 4, 6, 8):
+        C = dev(np.zeros((128, 256)))
+        S.gemm_emu(dev(A), dev(B), C, slices=s)
+        errs.append(np.abs(C.cpu().numpy() - ref).max())
+    assert all(errs[i + 1] < errs[i] / 100 for i in range(3)), errs
