@@ -84,6 +84,9 @@ typedef struct {
                            the last float64 refinement; 0 -> 1e-4 */
   int profile;          /* 1 -> time every launch of the line-search GEMM with CUDA events on
                            the context's stream (omm_info.ms_main_gemm and friends) */
+  int emulated_certificate; /* mixed: 1 -> certify the final point with float64-class
+                           tensor-core products (fixed-point slices, about 2^-50 of each
+                           row-scaled operand) instead of native float64 (0, default) */
 } omm_opts;
 
 /* Per-solve report. */
@@ -146,6 +149,35 @@ omm_status omm_update_H(omm_ctx* ctx, const double* H);
 
 /* Release every resource of the context (NULL is ignored). */
 void omm_free(omm_ctx* ctx);
+
+/* ---- batches of independent problems (k-points, spins, snapshots) ---- */
+typedef struct omm_batch omm_batch; /* opaque; owned by the library */
+
+/* Create `count` independent problems in one batch: per instance i the same
+ * arguments as omm_create (m[i], n[i], H[i], S[i], T[i] (T may be NULL when
+ * opts->no_precondition), eta[i], tau[i]), one opts and one stream for all.
+ * With opts->precision == OMM_PREC_MIXED the line searches of all instances
+ * run in lockstep: each phase is one launch over the whole batch (grouped
+ * tensor-core GEMMs, batched vector kernels), captured once in a CUDA graph
+ * and replayed; with OMM_PREC_FP64 the instances are solved one after the
+ * other. Errors: as omm_create, reported for the first failing instance. */
+omm_status omm_create_batched(int count, const int* m, const int* n, const double* const* H,
+                              const double* const* S, const double* const* T, const double* eta,
+                              const double* tau, const omm_opts* opts, void* stream, omm_batch** out);
+
+/* Solve every instance from C0[i] (n[i] x m[i], host or device). Writes C[i]
+ * (if C and C[i] are non-NULL), E[i] (host array, count entries, may be NULL)
+ * and info[i] (host array, may be NULL; ms_iterate is the time of the whole
+ * batched solve). Returns OMM_OK when every instance converged, else the
+ * status of the first failing instance (its info[i].status says which). */
+omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* const* C, double* E,
+                             omm_info* info);
+
+/* The context of instance i (for omm_backward after a batched solve), or NULL. */
+omm_ctx* omm_batch_instance(omm_batch* b, int i);
+
+/* Release the batch and its instances (NULL is ignored). */
+void omm_free_batched(omm_batch* b);
 
 /* Static description of a status code. */
 const char* omm_status_str(omm_status s);

@@ -22,7 +22,8 @@ PREC_MIXED = 1
 class OmmOpts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("max_iter", ct.c_int), ("no_precondition", ct.c_int),
                 ("check_every", ct.c_int), ("tol_grad", ct.c_double), ("e_tol", ct.c_double),
-                ("refine_ratio", ct.c_double), ("profile", ct.c_int)]
+                ("refine_ratio", ct.c_double), ("profile", ct.c_int),
+                ("emulated_certificate", ct.c_int)]
 
 
 class OmmInfo(ct.Structure):
@@ -60,6 +61,10 @@ _SIGNATURES = {
     "omm_status_str": (ct.c_char_p, [_I]),
     "omm_last_error": (ct.c_char_p, []),
     "omm_launch_count": (ct.c_ulonglong, []),
+    "omm_create_batched": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, ct.POINTER(OmmOpts), _P, ct.POINTER(_P)]),
+    "omm_solve_batched": (_I, [_P, _P, _P, _P, _P]),
+    "omm_batch_instance": (_P, [_P, _I]),
+    "omm_free_batched": (None, [_P]),
     "omm_kernel_dgemm": (_I, [_I, _I, _I, _I, _I, _D, _P, _L, _P, _L, _D, _P, _L, _P]),
     "omm_kernel_spd_inverse": (_I, [_I, _P, _P, ct.POINTER(_I), _P]),
     "omm_kernel_line_minimum": (_I, [ct.POINTER(_D), ct.POINTER(_D)]),

@@ -1,0 +1,514 @@
+// Batched OMM: many independent (H, S) instances of uneven size (k-points,
+// spins, snapshots) minimised together on one GPU.
+//
+// Each instance owns an ordinary mixed-precision context (setup, buffers,
+// refresh and certificate code of omm_capi.cu / mixed.cu / emu.cu). The line
+// searches of all instances advance in lockstep: every phase of a line search
+// is ONE launch over the whole batch -- the four contractions are grouped
+// tcgen05 GEMMs over the union of the instances' tiles, the vector and
+// control work runs as batched kernels with the instance in blockIdx.y -- and
+// the ~20 launches of one line search are captured once in a CUDA graph that
+// is replayed. An instance that has converged, or waits for a refresh, masks
+// itself out through its device flags, so the graph never changes. The host
+// polls all status words with one copy every `check_every` replays and runs
+// the per-instance refreshes (float64-class) and certificates (float64).
+#include "iter_device.cuh"
+#include "omm_ctx.cuh"
+#include "split_device.cuh"
+#include "tc_gemm.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace omm {
+namespace {
+
+constexpr int kBatchReduceBlocks = 64;  // gradient-reduction partials per instance (<= kReduceBlocks)
+
+struct IterArgs {
+  int n, m;
+  long nm;
+  int tiles;  // 32 x 32 tiles of an n x n matrix
+  int precond;
+  Scalars* sc;
+  double *C, *Dir, *G, *Gold, *PG, *Y4, *SWHW, *Proj, *part, *part2, *dY, *Gref, *Wref;
+  __nv_bfloat16 *G_hi, *D_hi, *Y_hi, *YT_hi, *W_hi;
+  long ldm, ld4;
+};
+
+enum SplitJob { kSplitG = 0, kSplitD, kSplitHDSD, kSplitHCSC, kSplitW };
+
+__global__ void __launch_bounds__(256) b_split_kernel(const IterArgs* __restrict__ A, int job) {
+  const IterArgs& a = A[blockIdx.y];
+  if (dev::stopped(a.sc)) return;
+  const long n = a.n, m = a.m;
+  switch (job) {
+    case kSplitG:
+      dev::split_body(a.G, nullptr, n, m, m, a.G_hi, a.G_hi + n * a.ldm, a.ldm, blockIdx.x, gridDim.x);
+      break;
+    case kSplitD:
+      dev::split_body(a.Dir, nullptr, n, m, m, a.D_hi, a.D_hi + n * a.ldm, a.ldm, blockIdx.x, gridDim.x);
+      break;
+    case kSplitHDSD:
+      dev::split_body(a.Y4 + 2 * a.nm, nullptr, 2 * n, m, m, a.Y_hi + 2 * n * a.ldm, a.Y_hi + 6 * n * a.ldm,
+                      a.ldm, blockIdx.x, gridDim.x);
+      break;
+    case kSplitHCSC:
+      dev::split_body(a.Y4, nullptr, 2 * n, m, m, a.Y_hi, a.Y_hi + 4 * n * a.ldm, a.ldm, blockIdx.x, gridDim.x);
+      break;
+    default:
+      dev::split_body(a.SWHW, a.Wref, n, 2 * n, 2 * n, a.W_hi, a.W_hi + n * a.ld4, a.ld4, blockIdx.x, gridDim.x);
+      break;
+  }
+}
+
+// job 0: [HC; SC] -> columns [0, 2n) of YT; job 1: [dHC; dSC] -> columns [2n, 4n)
+__global__ void __launch_bounds__(256) b_split_t_kernel(const IterArgs* __restrict__ A, int job) {
+  const IterArgs& a = A[blockIdx.y];
+  if (dev::stopped(a.sc)) return;
+  const long rows = 2L * a.n, cols = a.m;
+  const long tiles = ((rows + 31) / 32) * ((cols + 31) / 32);
+  if ((long)blockIdx.x >= tiles) return;
+  const double* src = job == 0 ? a.Y4 : a.dY;
+  __nv_bfloat16* hi = a.YT_hi + (job == 0 ? 0 : 2L * a.n);
+  dev::split_t_body(src, rows, cols, cols, hi, hi + (long)a.m * a.ld4, a.ld4, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(dev::TB) b_grad_reduce_kernel(const IterArgs* __restrict__ A) {
+  const IterArgs& a = A[blockIdx.y];
+  dev::grad_reduce_body(a.nm, a.G, a.PG, a.Gold, a.Dir, a.part, a.sc, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(dev::TB) b_control_direction_kernel(const IterArgs* __restrict__ A) {
+  const IterArgs& a = A[blockIdx.y];
+  dev::control_direction_body(a.sc, a.part, 1, kBatchReduceBlocks, 0, 1);
+}
+
+__global__ void __launch_bounds__(256) b_direction_kernel(const IterArgs* __restrict__ A) {
+  const IterArgs& a = A[blockIdx.y];
+  dev::direction_body(a.nm, a.PG, a.Dir, a.sc, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) b_copy_gradient_kernel(const IterArgs* __restrict__ A) {
+  const IterArgs& a = A[blockIdx.y];
+  dev::scale_copy_body(a.nm, a.G, 1.0, a.PG, a.sc, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(dev::TB) b_traces_kernel(const IterArgs* __restrict__ A) {
+  const IterArgs& a = A[blockIdx.y];
+  if ((int)blockIdx.x >= a.tiles) return;
+  dev::traces_body(a.n, a.SWHW, a.Proj, a.part2, a.sc, blockIdx.x, a.tiles);
+}
+
+__global__ void __launch_bounds__(dev::TB) b_control_linesearch_kernel(const IterArgs* __restrict__ A) {
+  const IterArgs& a = A[blockIdx.y];
+  dev::control_linesearch_body(a.sc, a.part2, a.tiles, 0, 1);
+}
+
+__global__ void __launch_bounds__(256) b_update_state_kernel(const IterArgs* __restrict__ A) {
+  const IterArgs& a = A[blockIdx.y];
+  dev::update_state_mixed_body(a.n, a.m, a.C, a.Y4, a.Dir, a.G, a.Gold, a.dY, a.Gref, a.sc, blockIdx.x,
+                               gridDim.x);
+}
+
+__global__ void __launch_bounds__(dev::TB) b_update_subspace_kernel(const IterArgs* __restrict__ A) {
+  const IterArgs& a = A[blockIdx.y];
+  if ((int)blockIdx.x >= a.tiles) return;
+  dev::update_subspace_body(a.n, a.SWHW, a.Proj, a.sc, blockIdx.x, a.tiles);
+}
+
+struct Grouped {
+  tc::GroupDesc* dev = nullptr;
+  int ngroups = 0, tiles = 0;
+};
+
+template <typename T>
+void alloc(T** p, size_t count) {
+  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    throw std::bad_alloc();
+  }
+}
+
+}  // namespace
+}  // namespace omm
+
+using namespace omm;
+
+struct omm_batch {
+  int count = 0;
+  cudaStream_t st = nullptr;
+  omm_opts opts{};
+  std::vector<omm_ctx*> ctx;
+  Scalars* sc_all = nullptr;       // device, count entries (each context's sc points here)
+  Scalars* sc_host_all = nullptr;  // pinned
+  IterArgs* args = nullptr;        // device
+  Grouped gPG, gHD, gPr, gG;
+  int max_rows = 0;        // largest 2n (split grid)
+  int max_tiles = 0;       // largest n x n tile count
+  int max_ttiles = 0;      // largest transposed-split tile count
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool precond = true;
+};
+
+namespace {
+
+void batch_destroy(omm_batch* b) {
+  if (!b) return;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (omm_ctx* c : b->ctx) {
+    if (c && b->sc_all && c->sc >= b->sc_all && c->sc < b->sc_all + b->count) {
+      c->sc = nullptr;  // the status words belong to the batch
+      c->sc_host = nullptr;
+    }
+    destroy(c);
+  }
+  for (Grouped* g : {&b->gPG, &b->gHD, &b->gPr, &b->gG})
+    if (g->dev) cudaFree(g->dev);
+  if (b->args) cudaFree(b->args);
+  if (b->sc_all) cudaFree(b->sc_all);
+  if (b->sc_host_all) cudaFreeHost(b->sc_host_all);
+  delete b;
+}
+
+void upload_groups(cudaStream_t st, Grouped* g, const std::vector<tc::GroupDesc>& v) {
+  g->ngroups = (int)v.size();
+  if (v.empty()) return;
+  g->tiles = v.back().tile_begin + tc::tiles_of(v.back().ep);
+  alloc(&g->dev, v.size());
+  OMM_CUDA_TRY(cudaMemcpyAsync(g->dev, v.data(), v.size() * sizeof(tc::GroupDesc), cudaMemcpyHostToDevice, st));
+}
+
+// one line search of every instance (captured into the graph)
+void enqueue_line_search(omm_batch* b) {
+  cudaStream_t st = b->st;
+  const unsigned cnt = (unsigned)b->count;
+  const dim3 rows_grid((unsigned)std::min(b->max_rows, 1024), cnt);
+  const dim3 vec_grid(256, cnt);
+  const tc::PairList pl = tc::pairs_split3();
+  if (b->precond) {
+    b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitG);
+    OMM_LAUNCH_CHECK();
+    tc::gemm_grouped(st, b->gPG.dev, b->gPG.ngroups, b->gPG.tiles, pl);
+  } else {
+    b_copy_gradient_kernel<<<vec_grid, 256, 0, st>>>(b->args);
+    OMM_LAUNCH_CHECK();
+  }
+  b_grad_reduce_kernel<<<dim3(kBatchReduceBlocks, cnt), dev::TB, 0, st>>>(b->args);
+  OMM_LAUNCH_CHECK();
+  b_control_direction_kernel<<<dim3(1, cnt), dev::TB, 0, st>>>(b->args);
+  OMM_LAUNCH_CHECK();
+  b_direction_kernel<<<vec_grid, 256, 0, st>>>(b->args);
+  OMM_LAUNCH_CHECK();
+  b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitD);
+  OMM_LAUNCH_CHECK();
+  tc::gemm_grouped(st, b->gHD.dev, b->gHD.ngroups, b->gHD.tiles, pl);
+  b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitHDSD);
+  OMM_LAUNCH_CHECK();
+  tc::gemm_grouped(st, b->gPr.dev, b->gPr.ngroups, b->gPr.tiles, pl);
+  b_traces_kernel<<<dim3(b->max_tiles, cnt), dev::TB, 0, st>>>(b->args);
+  OMM_LAUNCH_CHECK();
+  b_control_linesearch_kernel<<<dim3(1, cnt), dev::TB, 0, st>>>(b->args);
+  OMM_LAUNCH_CHECK();
+  b_update_state_kernel<<<vec_grid, 256, 0, st>>>(b->args);
+  OMM_LAUNCH_CHECK();
+  b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitHCSC);
+  OMM_LAUNCH_CHECK();
+  b_split_t_kernel<<<dim3(b->max_ttiles, cnt), 256, 0, st>>>(b->args, 0);
+  OMM_LAUNCH_CHECK();
+  b_split_t_kernel<<<dim3(b->max_ttiles, cnt), 256, 0, st>>>(b->args, 1);
+  OMM_LAUNCH_CHECK();
+  b_update_subspace_kernel<<<dim3(b->max_tiles, cnt), dev::TB, 0, st>>>(b->args);
+  OMM_LAUNCH_CHECK();
+  b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitW);
+  OMM_LAUNCH_CHECK();
+  tc::gemm_grouped(st, b->gG.dev, b->gG.ngroups, b->gG.tiles, pl);
+}
+
+// start a mixed round of instance i from its current (just recomputed) state
+void begin_round(omm_batch* b, int i, double g_ref, int iter_total) {
+  omm_ctx* c = b->ctx[i];
+  Scalars& h = *c->sc_host;
+  const double E_keep = h.E, g_keep = h.gmax;
+  reset_loop_flags(c, false);
+  h.E = E_keep;
+  h.gmax = g_keep;
+  h.iter = iter_total;
+  h.halt_gmax = std::max(c->opts.tol_grad * 0.5, g_ref * c->opts.refine_ratio);
+  write_scalars(c);
+  mixed_sync_state(c->mixed, c->st, c->Y4, c->SWHW, c->G);
+}
+
+}  // namespace
+
+extern "C" {
+
+omm_status omm_create_batched(int count, const int* m, const int* n, const double* const* H,
+                              const double* const* S, const double* const* T, const double* eta,
+                              const double* tau, const omm_opts* opts, void* stream, omm_batch** out) {
+  if (out) *out = nullptr;
+  if (!out || count <= 0 || !m || !n || !H || !S || !eta || !tau)
+    return fail(OMM_ERR_ARG, "omm_create_batched: invalid argument");
+  omm_batch* b = new (std::nothrow) omm_batch();
+  if (!b) return fail(OMM_ERR_OOM, "omm_create_batched: host allocation");
+  b->count = count;
+  b->st = (cudaStream_t)stream;
+  omm_opts o{};
+  if (opts) o = *opts;
+  b->opts = o;
+  b->precond = o.no_precondition == 0;
+  b->ctx.assign(count, nullptr);
+  for (int i = 0; i < count; ++i) {
+    omm_status rc = omm_create(m[i], n[i], H[i], S[i], T ? T[i] : nullptr, eta[i], tau[i], &o, stream, &b->ctx[i]);
+    if (rc != OMM_OK) {
+      const std::string msg = std::string("omm_create_batched: instance ") + std::to_string(i) + ": " +
+                              omm_last_error();
+      batch_destroy(b);
+      return fail(rc, msg);
+    }
+  }
+  if (o.precision != OMM_PREC_MIXED) {
+    *out = b;  // float64 batches solve instance by instance
+    return OMM_OK;
+  }
+  try {
+    alloc(&b->sc_all, count);
+    OMM_CUDA_TRY(cudaMallocHost((void**)&b->sc_host_all, count * sizeof(Scalars)));
+    std::vector<IterArgs> args(count);
+    std::vector<tc::GroupDesc> gpg, ghd, gpr, gg;
+    int tpg = 0, thd = 0, tpr = 0, tgg = 0;
+    for (int i = 0; i < count; ++i) {
+      omm_ctx* c = b->ctx[i];
+      cudaFree(c->sc);
+      c->sc = b->sc_all + i;
+      cudaFreeHost(c->sc_host);
+      c->sc_host = b->sc_host_all + i;
+      const MixedView v = mixed_view(c->mixed);
+      const int mi = c->m, ni = c->n;
+      const long nm = (long)ni * mi;
+      IterArgs& a = args[i];
+      a.n = ni;
+      a.m = mi;
+      a.nm = nm;
+      a.tiles = traces_blocks(ni);
+      a.precond = b->precond;
+      a.sc = c->sc;
+      a.C = c->C; a.Dir = c->Dir; a.G = c->G; a.Gold = c->Gold; a.PG = c->PG; a.Y4 = c->Y4;
+      a.SWHW = c->SWHW; a.Proj = c->Proj; a.part = c->part; a.part2 = c->part2;
+      a.dY = v.dY; a.Gref = v.Gref; a.Wref = v.Wref;
+      a.G_hi = v.G_hi; a.D_hi = v.D_hi; a.Y_hi = v.Y_hi; a.YT_hi = v.YT_hi; a.W_hi = v.W_hi;
+      a.ldm = v.ldm;
+      a.ld4 = v.ld4;
+      const int* skip = &c->sc->done;
+      if (b->precond) {
+        tc::Epilogue e{c->PG, mi, mi, 0, 1.0, 0.0, ni, mi, skip, v.err};
+        gpg.push_back(tc::make_group(*v.opG, *v.opP, mi, e, tpg));
+        tpg += tc::tiles_of(e);
+      }
+      tc::Epilogue ehd{c->Y4 + 2 * nm, mi, mi, nm, 1.0, 0.0, ni, 2 * mi, skip, v.err};
+      ghd.push_back(tc::make_group(*v.opD, *v.opHS, mi, ehd, thd));
+      thd += tc::tiles_of(ehd);
+      tc::Epilogue epr{c->Proj, 4L * ni, 4L * ni, 0, 1.0, 0.0, ni, 4 * ni, skip, v.err};
+      gpr.push_back(tc::make_group(*v.opD, *v.opY, mi, epr, tpr));
+      tpr += tc::tiles_of(epr);
+      tc::Epilogue eg{c->G, mi, mi, 0, -4.0, 1.0, ni, mi, skip, v.err};
+      gg.push_back(tc::make_group(*v.opW, *v.opYT, 4 * ni, eg, tgg));
+      tgg += tc::tiles_of(eg);
+      b->max_rows = std::max(b->max_rows, 2 * ni);
+      b->max_tiles = std::max(b->max_tiles, a.tiles);
+      b->max_ttiles = std::max(b->max_ttiles, (int)(((2L * ni + 31) / 32) * ((mi + 31) / 32)));
+    }
+    alloc(&b->args, count);
+    OMM_CUDA_TRY(cudaMemcpyAsync(b->args, args.data(), count * sizeof(IterArgs), cudaMemcpyHostToDevice, b->st));
+    upload_groups(b->st, &b->gPG, gpg);
+    upload_groups(b->st, &b->gHD, ghd);
+    upload_groups(b->st, &b->gPr, gpr);
+    upload_groups(b->st, &b->gG, gg);
+    OMM_CUDA_TRY(cudaStreamSynchronize(b->st));
+    // capture one line search of the whole batch
+    tc::prepare_grouped();
+    cudaStream_t cap = nullptr;
+    OMM_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t saved = b->st;
+    b->st = cap;
+    OMM_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    try {
+      enqueue_line_search(b);
+    } catch (...) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(cap, &g);
+      if (g) cudaGraphDestroy(g);
+      b->st = saved;
+      cudaStreamDestroy(cap);
+      throw;
+    }
+    OMM_CUDA_TRY(cudaStreamEndCapture(cap, &b->graph));
+    b->st = saved;
+    OMM_CUDA_TRY(cudaStreamDestroy(cap));
+    OMM_CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  } catch (const std::bad_alloc&) {
+    batch_destroy(b);
+    return fail(OMM_ERR_OOM, "omm_create_batched: device allocation failed");
+  } catch (const CudaError& e) {
+    batch_destroy(b);
+    return fail(OMM_ERR_CUDA, std::string("omm_create_batched: ") + e.what + ": " + cudaGetErrorString(e.err));
+  }
+  *out = b;
+  return OMM_OK;
+}
+
+omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* const* C, double* E, omm_info* info) {
+  if (!b || !C0) return fail(OMM_ERR_ARG, "omm_solve_batched: NULL argument");
+  const int cnt = b->count;
+  if (b->opts.precision != OMM_PREC_MIXED) {
+    // float64: instance after instance through the single-instance path
+    omm_status worst = OMM_OK;
+    for (int i = 0; i < cnt; ++i) {
+      double e = 0.0;
+      omm_info inf{};
+      const omm_status rc = omm_solve(b->ctx[i], C0[i], C ? C[i] : nullptr, &e, nullptr, &inf);
+      if (E) E[i] = e;
+      if (info) info[i] = inf;
+      if (rc != OMM_OK && worst == OMM_OK) worst = rc;
+    }
+    return worst == OMM_OK ? OMM_OK : fail(worst, "omm_solve_batched: at least one instance failed");
+  }
+  std::vector<int> finished(cnt, 0), rounds(cnt, 0), refinements(cnt, 0), energy_stop(cnt, 0);
+  std::vector<int> iter_total(cnt, 0), last_done(cnt, 0), round_start(cnt, 0);
+  std::vector<omm_status> result(cnt, OMM_OK);
+  std::vector<double> ms_ref(cnt, 0.0);
+  omm_status worst = OMM_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms_total = 0.f;
+  try {
+    OMM_CUDA_TRY(cudaEventCreate(&e0));
+    OMM_CUDA_TRY(cudaEventCreate(&e1));
+    OMM_CUDA_TRY(cudaEventRecord(e0, b->st));
+    for (int i = 0; i < cnt; ++i) {
+      omm_ctx* c = b->ctx[i];
+      c->solved = false;
+      copy_in(c->C, C0[i], (size_t)c->n * c->m, b->st);
+      reset_loop_flags(c, true);
+      write_scalars(c);
+      mixed_recompute_state(c->mixed, b->st, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
+    }
+    OMM_CUDA_TRY(cudaMemcpyAsync(b->sc_host_all, b->sc_all, cnt * sizeof(Scalars), cudaMemcpyDeviceToHost, b->st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(b->st));
+    for (int i = 0; i < cnt; ++i) {
+      const Scalars& h = b->sc_host_all[i];
+      if (!std::isfinite(h.gmax) || !std::isfinite(h.E)) {
+        finished[i] = 1;
+        result[i] = OMM_ERR_NONFINITE;
+        b->sc_host_all[i].done = 1;
+        write_scalars(b->ctx[i]);
+        continue;
+      }
+      begin_round(b, i, h.gmax, 0);
+    }
+    const int check = b->ctx[0]->opts.check_every;
+    for (int poll = 0;; ++poll) {
+      int active = 0;
+      for (int i = 0; i < cnt; ++i) active += !finished[i];
+      if (active == 0) break;
+      for (int k = 0; k < check; ++k) OMM_CUDA_TRY(cudaGraphLaunch(b->exec, b->st));
+      OMM_CUDA_TRY(cudaMemcpyAsync(b->sc_host_all, b->sc_all, cnt * sizeof(Scalars), cudaMemcpyDeviceToHost, b->st));
+      OMM_CUDA_TRY(cudaStreamSynchronize(b->st));
+      for (int i = 0; i < cnt; ++i) {
+        if (finished[i]) continue;
+        omm_ctx* c = b->ctx[i];
+        Scalars& h = *c->sc_host;
+        const bool capped = h.iter - round_start[i] >= kMixedRound;
+        if (!(h.done || h.halt || h.status || capped)) continue;
+        iter_total[i] = h.iter;
+        if (h.status != 0) {
+          result[i] = (omm_status)h.status;
+          finished[i] = 1;
+          if (result[i] == OMM_ERR_NO_CONVERGENCE) recompute_state_fp64(c);
+          h.done = 1;
+          write_scalars(c);
+          continue;
+        }
+        if (h.done && h.stop_reason == 2) energy_stop[i] = 1;
+        last_done[i] = h.done != 0;
+        // refresh: float64-class while the device asks for it, native float64 to certify
+        cudaEvent_t r0 = c->ev[0], r1 = c->ev[1];
+        OMM_CUDA_TRY(cudaEventRecord(r0, b->st));
+        const bool certify = last_done[i] != 0;
+        if (certify) recompute_state_fp64(c);
+        else emu_recompute_state(c->emu, b->st, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
+        OMM_CUDA_TRY(cudaEventRecord(r1, b->st));
+        read_scalars(c);
+        ms_ref[i] += elapsed(r0, r1);
+        ++rounds[i];
+        if (!std::isfinite(h.gmax) || !std::isfinite(h.E)) {
+          result[i] = OMM_ERR_NONFINITE;
+          finished[i] = 1;
+        } else if (certify && (h.gmax < c->opts.tol_grad || energy_stop[i])) {
+          finished[i] = 1;
+          c->solved = true;
+        } else if (rounds[i] > 64 || h.iter >= c->opts.max_iter) {
+          result[i] = OMM_ERR_NO_CONVERGENCE;
+          finished[i] = 1;
+        }
+        if (finished[i]) {
+          h.done = 1;
+          write_scalars(c);
+          continue;
+        }
+        ++refinements[i];
+        round_start[i] = h.iter;
+        begin_round(b, i, h.gmax, h.iter);
+      }
+    }
+    OMM_CUDA_TRY(cudaEventRecord(e1, b->st));
+    OMM_CUDA_TRY(cudaEventSynchronize(e1));
+    cudaEventElapsedTime(&ms_total, e0, e1);
+    for (int i = 0; i < cnt; ++i) {
+      omm_ctx* c = b->ctx[i];
+      const Scalars& h = *c->sc_host;
+      if ((result[i] == OMM_OK || result[i] == OMM_ERR_NO_CONVERGENCE) && C && C[i])
+        OMM_CUDA_TRY(cudaMemcpyAsync(C[i], c->C, (size_t)c->n * c->m * sizeof(double), cudaMemcpyDefault, b->st));
+      if (E) E[i] = h.E + 2.0 * c->n * c->eta;
+      if (info) {
+        omm_info inf{};
+        inf.status = result[i];
+        inf.iterations = h.iter;
+        inf.refinements = refinements[i];
+        inf.E = h.E + 2.0 * c->n * c->eta;
+        inf.Etilde = h.E;
+        inf.gmax = h.gmax;
+        inf.ms_setup = c->ms_setup;
+        inf.ms_refine = ms_ref[i];
+        inf.ms_iterate = ms_total;  // the whole batched solve (shared by all instances)
+        info[i] = inf;
+      }
+      if (result[i] != OMM_OK && worst == OMM_OK) worst = result[i];
+    }
+    OMM_CUDA_TRY(cudaStreamSynchronize(b->st));
+  } catch (const CudaError& e) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return fail(OMM_ERR_CUDA, std::string("omm_solve_batched: ") + e.what + ": " + cudaGetErrorString(e.err));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (worst != OMM_OK) return fail(worst, "omm_solve_batched: at least one instance failed");
+  return OMM_OK;
+}
+
+omm_ctx* omm_batch_instance(omm_batch* b, int i) {
+  if (!b || i < 0 || i >= b->count) return nullptr;
+  return b->ctx[i];
+}
+
+void omm_free_batched(omm_batch* b) { batch_destroy(b); }
+
+}  // extern "C"

@@ -98,6 +98,31 @@ MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const 
   return ms;
 }
 
+MixedView mixed_view(MixedState* ms) {
+  MixedView v;
+  v.ldm = ms->ldm;
+  v.ld4 = ms->ld2n;
+  v.G_hi = ms->G_hi;
+  v.D_hi = ms->D_hi;
+  v.Y_hi = ms->Y_hi;
+  v.YT_hi = ms->YT_hi;
+  v.W_hi = ms->W_hi;
+  v.Gref = ms->Gref;
+  v.dY = ms->dY;
+  v.Wref = ms->Wref;
+  v.opHS = &ms->opHS;
+  v.opP = &ms->opP;
+  v.opG = &ms->opG;
+  v.opD = &ms->opD;
+  v.opY = &ms->opY;
+  v.opYT = &ms->opYT;
+  v.opW = &ms->opW;
+  v.err = ms->err;
+  v.npass = ms->npass;
+  v.precond = ms->precond;
+  return v;
+}
+
 void mixed_update_H(MixedState* ms, cudaStream_t st, const double* HS) {
   tc::split(st, HS, ms->m, ms->m, ms->m, ms->HS_hi, ms->HS_lo, ms->ldm, nullptr);
 }

@@ -12,8 +12,7 @@
 //   HD,SD = Dir [H~;S]^T, Proj = Dir Y4^T, G = 8 HC - 4 SWHW [HC;SC], PG = G P.
 #include "../../include/omm.h"
 #include "omm_internal.cuh"
-#include "omm_mixed.cuh"
-#include "emu.cuh"
+#include "omm_ctx.cuh"
 
 #include <algorithm>
 #include <atomic>
@@ -75,46 +74,11 @@ Profiler::~Profiler() {
 
 using namespace omm;
 
-struct omm_ctx {
-  int m = 0, n = 0;
-  double eta = 0.0, tau = 0.0;
-  omm_opts opts{};
-  cudaStream_t st = nullptr;
-  bool precond = true;
-  bool solved = false;
-  double* HS = nullptr;
-  double* P = nullptr;
-  double* C = nullptr;
-  double* Dir = nullptr;
-  double* G = nullptr;
-  double* Gold = nullptr;
-  double* PG = nullptr;
-  double* Y4 = nullptr;
-  double* SWHW = nullptr;
-  double* Proj = nullptr;
-  double* nn = nullptr;      // n x n scratch
-  double* part = nullptr;    // reduction partials
-  double* part2 = nullptr;   // trace partials
-  double* mm = nullptr;      // m x m output scratch (lazy)
-  Scalars* sc = nullptr;
-  Scalars* sc_host = nullptr;  // pinned
-  int* info_dev = nullptr;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  double ms_setup = 0.0;
-  MixedState* mixed = nullptr;
-  EmuState* emu = nullptr;  // float64-class tensor-core refresh of the mixed path
-  Profiler prof;  // main contraction kernel of the iteration (tensor-core or float64 GEMM)
-};
 
-namespace {
+namespace omm {
 
 constexpr int kMixedRoundCap = 400;
 constexpr int kEmuSlices = 10;  // fixed-point slices of the float64-class refresh (about 50 bits)
-
-struct Status {
-  omm_status s;
-  std::string msg;
-};
 
 omm_status fail(omm_status s, const std::string& msg) {
   set_last_error(msg);
@@ -280,7 +244,7 @@ void destroy(omm_ctx* c) {
   delete c;
 }
 
-}  // namespace
+}  // namespace omm
 
 extern "C" {
 
@@ -446,8 +410,9 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
       // the mixed path starts from a tensor-core state; every later state is float64
       // mixed path: a tensor-core first state, float64-class (sliced) refreshes while the
       // device asks for them, and a native float64 state once it reports convergence
+      const bool emu_certify = mixed && c->opts.emulated_certificate != 0;
       const bool tc_state = mixed && round == 0;
-      const bool emu_state = mixed && round > 0 && !last_round_done;
+      const bool emu_state = mixed && round > 0 && (!last_round_done || emu_certify);
       OMM_CUDA_TRY(cudaEventRecord(c->ev[0], c->st));
       if (tc_state) {
         mixed_recompute_state(c->mixed, c->st, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
@@ -473,7 +438,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
         break;
       }
       // only a native float64 state certifies (or Eq. 18 met)
-      if (!tc_state && !emu_state && (h.gmax < c->opts.tol_grad || energy_stop)) break;
+      if (!tc_state && (!emu_state || emu_certify) && (h.gmax < c->opts.tol_grad || energy_stop)) break;
       if (round > 0) ++refinements;
       if (iter_total >= c->opts.max_iter) {
         result = OMM_ERR_NO_CONVERGENCE;

@@ -146,7 +146,7 @@ void launch_symmetrize_lower(cudaStream_t st, int m, double* A);  // A[j,i] = A[
 void launch_fill(cudaStream_t st, long count, double v, double* dst);
 
 // Device-side line minimum (first local minimum of the quartic along x > 0).
-__host__ __device__ int quartic_first_minimum(const double a[5], double* x_out);
+
 void launch_line_minimum(cudaStream_t st, const double* a, double* x, int* status);
 
 }  // namespace omm

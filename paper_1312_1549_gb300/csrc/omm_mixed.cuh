@@ -3,10 +3,23 @@
 // products with FP32 accumulation; the state stays in float64.
 #pragma once
 #include "omm_internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace omm {
 
 struct MixedState;
+
+// Buffers and operands of a mixed state, for the batched driver.
+struct MixedView {
+  long ldm, ld4;
+  __nv_bfloat16 *G_hi, *D_hi, *Y_hi, *YT_hi, *W_hi;  // [hi; lo] stacks
+  double *Gref, *dY, *Wref;
+  const tc::Operand *opHS, *opP, *opG, *opD, *opY, *opYT, *opW;
+  int* err;
+  int npass;
+  bool precond;
+};
+MixedView mixed_view(MixedState* ms);
 
 MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const double* P);
 void mixed_update_H(MixedState* ms, cudaStream_t st, const double* HS);

@@ -134,9 +134,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1)
-gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-                       int K, int rowsA, int rowsB, const __grid_constant__ PairList pl, Epilogue ep) {
+// One 128 x 256 output tile (shared by the single and the grouped kernel).
+__device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorMap* mB, int K, int rowsA,
+                                          int rowsB, const PairList& pl, const Epilogue& ep_in, int tile) {
+  const Epilogue ep = ep_in;
   if (ep.skip != nullptr && (ep.skip[0] | ep.skip[1])) return;  // uniform: before any resource use
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -149,7 +150,7 @@ gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA, const __grid_cons
   // M-fastest rasterisation: CTAs that run together share one B tile (read
   // from DRAM once, then from L2) and sweep the small A operand
   const int tiles_m = (ep.M + BM - 1) / BM;
-  const int m0 = (blockIdx.x % tiles_m) * BM, n0 = (blockIdx.x / tiles_m) * BN;
+  const int m0 = (tile % tiles_m) * BM, n0 = (tile / tiles_m) * BN;
   const int nkb = (K + BK - 1) / BK;
   const int total = pl.n * nkb;
 
@@ -176,8 +177,8 @@ gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA, const __grid_cons
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
-    prefetch_tmap(&mA);
-    prefetch_tmap(&mB);
+    prefetch_tmap(mA);
+    prefetch_tmap(mB);
     for (int t = 0; t < total; ++t) {
       const int s = t % STAGES, r = t / STAGES;
       if (!mbar_wait(smem_u32(&bars[STAGES + s]), (r & 1) ^ 1)) {
@@ -190,8 +191,8 @@ gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA, const __grid_cons
       const uint32_t full = smem_u32(&bars[s]);
       const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
       mbar_expect_tx(full, STAGE_BYTES);
-      tma_load_2d(sa, &mA, full, kb * BK, (int)pl.a[p] * rowsA + m0);
-      tma_load_2d(sa + A_BYTES, &mB, full, kb * BK, (int)pl.b[p] * rowsB + n0);
+      tma_load_2d(sa, mA, full, kb * BK, (int)pl.a[p] * rowsA + m0);
+      tma_load_2d(sa + A_BYTES, mB, full, kb * BK, (int)pl.b[p] * rowsB + n0);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
@@ -247,6 +248,27 @@ gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA, const __grid_cons
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+                       int K, int rowsA, int rowsB, const __grid_constant__ PairList pl, Epilogue ep) {
+  gemm_tile(&mA, &mB, K, rowsA, rowsB, pl, ep, blockIdx.x);
+}
+
+// One launch over the tiles of many independent GEMMs (a batch of OMM
+// instances): CTA b works on tile b - g.tile_begin of the group g that holds it.
+__global__ void __launch_bounds__(NTHREADS, 1)
+gemm_grouped_kernel(const GroupDesc* __restrict__ groups, int ngroups, const __grid_constant__ PairList pl) {
+  int lo = 0, hi = ngroups - 1;
+  const int b = (int)blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (groups[mid].tile_begin <= b) lo = mid; else hi = mid - 1;
+  }
+  const GroupDesc* g = groups + lo;
+  gemm_tile(reinterpret_cast<const CUtensorMap*>(&g->a), reinterpret_cast<const CUtensorMap*>(&g->b), g->K,
+            g->rowsA, g->rowsB, pl, g->ep, b - g->tile_begin);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -322,6 +344,36 @@ void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const Pair
   const CUtensorMap* a = reinterpret_cast<const CUtensorMap*>(&A.map);
   const CUtensorMap* b = reinterpret_cast<const CUtensorMap*>(&B.map);
   gemm_bf16_split_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(*a, *b, K, (int)A.rows, (int)B.rows, pl, ep);
+  OMM_LAUNCH_CHECK();
+}
+
+int tiles_of(const Epilogue& ep) { return ((ep.M + BM - 1) / BM) * ((ep.N + BN - 1) / BN); }
+
+GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin) {
+  GroupDesc g{};
+  g.a = A.map;
+  g.b = B.map;
+  g.ep = ep;
+  g.K = K;
+  g.rowsA = (int)A.rows;
+  g.rowsB = (int)B.rows;
+  g.tile_begin = tile_begin;
+  return g;
+}
+
+void prepare_grouped() {
+  static bool attr_set = false;
+  if (!attr_set) {
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      SMEM_BYTES));
+    attr_set = true;
+  }
+}
+
+void gemm_grouped(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl) {
+  prepare_grouped();
+  if (ngroups <= 0 || total_tiles <= 0) return;
+  gemm_grouped_kernel<<<(unsigned)total_tiles, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, pl);
   OMM_LAUNCH_CHECK();
 }
 

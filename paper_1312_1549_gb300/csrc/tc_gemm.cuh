@@ -59,6 +59,19 @@ inline void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, int
 }
 int tile_m();
 int tile_n();
+int tiles_of(const Epilogue& ep);  // output tiles of one GEMM
+
+// One GEMM of a grouped launch (device array element; tensor maps in global memory).
+struct alignas(64) GroupDesc {
+  TensorMap a;
+  TensorMap b;
+  Epilogue ep;
+  int K, rowsA, rowsB, tile_begin;
+};
+GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin);
+// groups_dev: ngroups descriptors in device memory, sorted by tile_begin; all share the pair list
+void prepare_grouped();  // kernel attributes (call before a stream capture)
+void gemm_grouped(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl);
 
 // x (float64, rows x cols, ld_src) -> hi = bf16(x), lo = bf16(x - hi) (ld_dst);
 // transposed variants write dst[j][i]. Skipped when sc's done/halt is set.

@@ -45,7 +45,7 @@ class OMMSolver:
 
     def __init__(self, H, S, T, n, eta, tau, precision="fp64", stream=None, max_iter=0,
                  tol_grad=1e-9, e_tol=0.0, refine_ratio=0.0, precondition=True, check_every=0,
-                 profile=False):
+                 profile=False, emulated_certificate=False):
         lib = N.lib()
         m = int(H.shape[0])
         self.m, self.n, self.eta, self.tau = m, int(n), float(eta), float(tau)
@@ -54,7 +54,8 @@ class OMMSolver:
                          max_iter=int(max_iter), no_precondition=0 if precondition else 1,
                          check_every=int(check_every), tol_grad=float(tol_grad),
                          e_tol=float(e_tol), refine_ratio=float(refine_ratio),
-                         profile=1 if profile else 0)
+                         profile=1 if profile else 0,
+                         emulated_certificate=1 if emulated_certificate else 0)
         self._keep = (H, S, T)
         h = ct.c_void_p()
         tau_arg = math.inf if tau is None else float(tau)
@@ -175,3 +176,79 @@ def gemm_emu(A, B, C, alpha=1.0, beta=0.0, slices=10, stream=None):
 def launch_count():
     """Kernels launched by the library in this process."""
     return int(N.lib().omm_launch_count())
+
+
+class OMMBatch:
+    """Independent problems solved together: omm_create_batched / omm_solve_batched.
+
+    problems: list of (H, S, T, n, eta, tau). With precision="mixed" every phase of a
+    line search is one launch over the batch (grouped tensor-core GEMMs, batched vector
+    kernels) replayed from a CUDA graph; "fp64" solves the instances one by one.
+    """
+
+    def __init__(self, problems, precision="mixed", stream=None, max_iter=0, tol_grad=1e-9,
+                 refine_ratio=0.0, precondition=True, check_every=0):
+        lib = N.lib()
+        cnt = len(problems)
+        self.count = cnt
+        self.shapes = [(int(p[0].shape[0]), int(p[3])) for p in problems]
+        opts = N.OmmOpts(precision=N.PREC_MIXED if precision == "mixed" else N.PREC_FP64,
+                         max_iter=int(max_iter), no_precondition=0 if precondition else 1,
+                         check_every=int(check_every), tol_grad=float(tol_grad), e_tol=0.0,
+                         refine_ratio=float(refine_ratio), profile=0)
+        P = ct.c_void_p * cnt
+        ms = (ct.c_int * cnt)(*[s[0] for s in self.shapes])
+        ns = (ct.c_int * cnt)(*[s[1] for s in self.shapes])
+        Hs = P(*[_ptr(p[0]) for p in problems])
+        Ss = P(*[_ptr(p[1]) for p in problems])
+        Ts = P(*[_ptr(p[2]) for p in problems])
+        etas = (ct.c_double * cnt)(*[float(p[4]) for p in problems])
+        taus = (ct.c_double * cnt)(*[float(p[5]) for p in problems])
+        self.etas = [float(p[4]) for p in problems]
+        h = ct.c_void_p()
+        N.check(lib.omm_create_batched(cnt, ms, ns, Hs, Ss, Ts, etas, taus, ct.byref(opts),
+                                       _stream_handle(stream), ct.byref(h)), "omm_create_batched")
+        self._h = h
+        self.infos = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().omm_free_batched(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, C0s, C_outs=None, raise_on_error=True):
+        """Solve all instances from C0s (list of n_i x m_i). Returns (C list, E array, infos)."""
+        cnt = self.count
+        if C_outs is None:
+            C_outs = [torch.empty_like(c) if isinstance(c, torch.Tensor) else np.empty_like(c) for c in C0s]
+        P = ct.c_void_p * cnt
+        E = (ct.c_double * cnt)()
+        infos = (N.OmmInfo * cnt)()
+        rc = N.lib().omm_solve_batched(self._h, P(*[_ptr(c) for c in C0s]), P(*[_ptr(c) for c in C_outs]),
+                                       E, infos)
+        self.infos = [infos[i].as_dict() for i in range(cnt)]
+        if raise_on_error:
+            N.check(rc, "omm_solve_batched")
+        return C_outs, np.array(list(E)), self.infos
+
+    def backward(self, i, device=None):
+        """(dE/dH, dE/dS) of instance i after a converged batched solve."""
+        m = self.shapes[i][0]
+        dev = device if device is not None else torch.device("cuda")
+        ctx = N.lib().omm_batch_instance(self._h, int(i))
+        dH = torch.empty((m, m), dtype=torch.float64, device=dev)
+        dS = torch.empty((m, m), dtype=torch.float64, device=dev)
+        N.check(N.lib().omm_backward(ctx, _ptr(dH), _ptr(dS)), "omm_backward")
+        return dH, dS
