@@ -33,6 +33,10 @@ WORKLOADS = {
        "eta=HOMO+0.1 Ha, |G|inf<1e-9",
     3: "water256_dzp: 256 H2O at 1 g/cm3, DZP-like 23 orbitals/molecule, m=5888, n=1024, tau=5 Ha, "
        "eta=HOMO+0.1 Ha, |G|inf<1e-9",
+    4: "batch64: 64 independent Si DZP-like / water instances, m ~ U[512,4096], n/m 0.15-0.17, "
+       "one batched solve (grouped tensor-core launches in a CUDA graph), |G|inf<1e-9 each",
+    5: "si4096_sz_warmstart: Si 4096-atom single-zeta, m=16384, n=8192, 10 Hamiltonians "
+       "H_k = H_0 + k delta (on-site, sigma 0.01 Ha), each solve from the previous C, dE/dH each step",
 }
 # Line searches the float64 solve takes on each workload from its seeded C0
 # (measured with the float64 GPU path); used to extrapolate bounded oracle samples.
@@ -148,7 +152,7 @@ def run_reference(args):
     cores = os.cpu_count()
     sample = (f"per step: oracle setup + initial state + certificate, plus 2 line searches, timed; "
               f"extrapolated to {iters} line searches")
-    out = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": 0, "steps": args.steps,
+    out = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
@@ -159,13 +163,143 @@ def run_reference(args):
     return 0
 
 
+def _base_line(args, value_s, world=1):
+    return {"metric": METRIC, "value": value_s, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": value_s * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.config], "precision": "mixed",
+                       "l2": "inputs larger than L2", "parallelism": "1 GPU"}}
+
+
+def run_batch(args):
+    """Config 4: one batched solve of independent instances (create + solve per step)."""
+    import numpy as np
+    import torch
+    from paper_1312_1549_gb300 import build as _build
+    _build.build()
+    from paper_1312_1549_gb300 import solver as S
+    from synth import configs
+    probs = [configs.config4_instance(i) for i in range(args.instances)]
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dev = [(t(p.H), t(p.S), t(p.T), p.n, p.eta, p.tau) for p in probs]
+    C0 = [t(p.C0) for p in probs]
+    stream = torch.cuda.Stream()
+
+    def step(precision="mixed", subset=None):
+        idx = range(len(probs)) if subset is None else subset
+        with S.OMMBatch([dev[i] for i in idx], precision=precision, stream=stream) as b:
+            _, E, infos = b.solve([C0[i] for i in idx])
+        return E, infos
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = S.launch_count()
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            E, infos = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    out = _base_line(args, ms * 1e-3)
+    logical = sum(i["iterations"] * (6.0 * p.m * p.m * p.n + 16.0 * p.m * p.n * p.n)
+                  for i, p in zip(infos, probs))
+    out.update({"instances": len(probs), "m_range": [min(p.m for p in probs), max(p.m for p in probs)],
+                "line_searches_max": max(i["iterations"] for i in infos),
+                "line_searches_total": sum(i["iterations"] for i in infos),
+                "gemm_tflops_logical": logical / (ms * 1e-3) / 1e12,
+                "gpu_launches": S.launch_count() - launches0, "clocks": clk.summary(),
+                "roofline": {"bound": "tensor", "achieved": None, "peak": load_peaks()[0]["bf16_tflops_sustained"],
+                             "unit": "TFLOP/s", "frac": None, "traffic": None,
+                             "kernel": "gemm_grouped_kernel (tcgen05)", "note": "not separated in batch mode"}})
+    # accuracy on a sample of instances against the eigenpair definition
+    from oracle import exact
+    sample = list(range(0, len(probs), max(1, len(probs) // 4)))
+    out["rel_err_E_vs_exact_sample"] = max(
+        abs(E[i] - exact.exact_minimum(probs[i].H, probs[i].S, probs[i].n, want_matrices=False)["E"])
+        / abs(E[i]) for i in sample)
+    if not args.no_fp64_compare:
+        # the float64 GPU path instance by instance on every 8th instance, scaled by flops
+        sub = list(range(0, len(probs), 8))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, inf64 = step("fp64", sub)
+        torch.cuda.synchronize()
+        t_sub = time.perf_counter() - t0
+        f = lambda ids: sum(6.0 * probs[i].m ** 2 * probs[i].n + 12.0 * probs[i].m * probs[i].n ** 2 for i in ids)
+        est = t_sub * f(range(len(probs))) / f(sub)
+        out["fp64_gpu_loop"] = {"time_to_solution_s_estimate": est, "measured_instances": len(sub),
+                                "measured_s": t_sub, "speedup_batched_mixed": est / (ms * 1e-3),
+                                "note": "instances solved one by one on the float64 path; measured on every "
+                                        "8th instance, scaled by per-line-search flops"}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_sequence(args):
+    """Config 5: warm-started sequence H_k = H_0 + k delta, dE/dH each step."""
+    import numpy as np
+    import torch
+    from paper_1312_1549_gb300 import build as _build
+    _build.build()
+    from paper_1312_1549_gb300 import solver as S
+    from synth import configs
+    p = configs.config5_base()
+    delta = configs.warm_start_delta(p, 1)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    H0, Sm, T, C0 = t(p.H), t(p.S), t(p.T), t(p.C0)
+    dvec = t(delta)
+    stream = torch.cuda.Stream()
+    Hk = H0.clone()
+    dH = torch.empty_like(H0)
+
+    def step():
+        infos = []
+        with S.OMMSolver(H0, Sm, T, p.n, p.eta, p.tau, precision="mixed", stream=stream,
+                         emulated_certificate=args.emulated_certificate) as s:
+            C = C0
+            for k in range(args.sequence):
+                if k > 0:
+                    with torch.cuda.stream(stream):
+                        Hk.copy_(H0)
+                        Hk.diagonal().add_(k * dvec)
+                    s.update_H(Hk)
+                C, E, _, info = s.solve(C)
+                s.backward(dEdH=dH, want_S=False)   # dE/dH = D each step
+                infos.append((E, info))
+        return infos
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    out = _base_line(args, ms * 1e-3)
+    out["config"]["certificate"] = "float64-class (sliced)" if args.emulated_certificate else "native float64"
+    out.update({"line_searches": [i["iterations"] for _, i in infos], "E": [E for E, _ in infos],
+                "gmax": max(i["gmax"] for _, i in infos), "clocks": clk.summary()})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    ap.add_argument("--instances", type=int, default=64, help="config 4: batch size")
+    ap.add_argument("--sequence", type=int, default=10, help="config 5: Hamiltonians in the sequence")
+    ap.add_argument("--emulated-certificate", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -174,6 +308,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == 4:
+        return run_batch(args)
+    if args.config == 5:
+        return run_sequence(args)
 
     import numpy as np
     import torch
@@ -252,6 +390,8 @@ def main():
            "E": energies[-1], "gmax": infos[-1]["gmax"],
            "ms_setup": statistics.mean(i["ms_setup"] for i in infos),
            "ms_iterate": it_ms, "ms_refine": statistics.mean(i["ms_refine"] for i in infos),
+           "ms_certify": statistics.mean(i["ms_certify"] for i in infos),
+           "ms_outputs": statistics.mean(i["ms_outputs"] for i in infos),
            "gemm_tflops_logical": logical / (ms * 1e-3) / 1e12,
            "gemm_tflops_logical_in_iterations": (infos[-1]["gemm_flop"] and
                                                  (iters * (6.0 * p.m * p.m * p.n + 12.0 * p.m * p.n * p.n))

@@ -84,9 +84,10 @@ typedef struct {
                            the last float64 refinement; 0 -> 1e-4 */
   int profile;          /* 1 -> time every launch of the line-search GEMM with CUDA events on
                            the context's stream (omm_info.ms_main_gemm and friends) */
-  int emulated_certificate; /* mixed: 1 -> certify the final point with float64-class
-                           tensor-core products (fixed-point slices, about 2^-50 of each
-                           row-scaled operand) instead of native float64 (0, default) */
+  int emulated_certificate; /* mixed: 1 -> certify the final point, and form the density
+                           matrix D of omm_solve, with float64-class tensor-core products
+                           (fixed-point slices, about 2^-50 resp. 2^-40 of each row-scaled
+                           operand) instead of native float64 (0, default) */
 } omm_opts;
 
 /* Per-solve report. */
@@ -108,6 +109,7 @@ typedef struct {
   double ms_main_gemm;       /* with opts.profile: summed duration of the line-search GEMM launches */
   double main_gemm_launches; /* with opts.profile: number of those launches */
   double main_gemm_flop;     /* with opts.profile: flops they issued (tensor-core flops when mixed) */
+  double ms_certify;         /* native float64 state recomputes (part of ms_refine) */
 } omm_info;
 
 /* Create a solver context for one (H, S, T) and do the per-geometry setup:

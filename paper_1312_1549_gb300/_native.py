@@ -33,7 +33,7 @@ class OmmInfo(ct.Structure):
                 ("ms_refine", ct.c_double), ("ms_outputs", ct.c_double), ("gemm_flop", ct.c_double),
                 ("gemm_flop_tc", ct.c_double), ("kernel_launches", ct.c_double),
                 ("ms_main_gemm", ct.c_double), ("main_gemm_launches", ct.c_double),
-                ("main_gemm_flop", ct.c_double)]
+                ("main_gemm_flop", ct.c_double), ("ms_certify", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

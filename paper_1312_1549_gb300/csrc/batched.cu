@@ -18,6 +18,8 @@
 #include "tc_gemm.cuh"
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -155,6 +157,7 @@ struct omm_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool precond = true;
+  int* err = nullptr;  // bounded-wait failures of the grouped GEMMs
 };
 
 namespace {
@@ -174,6 +177,7 @@ void batch_destroy(omm_batch* b) {
   for (Grouped* g : {&b->gPG, &b->gHD, &b->gPr, &b->gG})
     if (g->dev) cudaFree(g->dev);
   if (b->args) cudaFree(b->args);
+  if (b->err) cudaFree(b->err);
   if (b->sc_all) cudaFree(b->sc_all);
   if (b->sc_host_all) cudaFreeHost(b->sc_host_all);
   delete b;
@@ -197,7 +201,7 @@ void enqueue_line_search(omm_batch* b) {
   if (b->precond) {
     b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitG);
     OMM_LAUNCH_CHECK();
-    tc::gemm_grouped(st, b->gPG.dev, b->gPG.ngroups, b->gPG.tiles, pl);
+    tc::gemm_persistent(st, b->gPG.dev, b->gPG.ngroups, b->gPG.tiles, pl, b->err);
   } else {
     b_copy_gradient_kernel<<<vec_grid, 256, 0, st>>>(b->args);
     OMM_LAUNCH_CHECK();
@@ -210,10 +214,10 @@ void enqueue_line_search(omm_batch* b) {
   OMM_LAUNCH_CHECK();
   b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitD);
   OMM_LAUNCH_CHECK();
-  tc::gemm_grouped(st, b->gHD.dev, b->gHD.ngroups, b->gHD.tiles, pl);
+  tc::gemm_persistent(st, b->gHD.dev, b->gHD.ngroups, b->gHD.tiles, pl, b->err);
   b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitHDSD);
   OMM_LAUNCH_CHECK();
-  tc::gemm_grouped(st, b->gPr.dev, b->gPr.ngroups, b->gPr.tiles, pl);
+  tc::gemm_persistent(st, b->gPr.dev, b->gPr.ngroups, b->gPr.tiles, pl, b->err);
   b_traces_kernel<<<dim3(b->max_tiles, cnt), dev::TB, 0, st>>>(b->args);
   OMM_LAUNCH_CHECK();
   b_control_linesearch_kernel<<<dim3(1, cnt), dev::TB, 0, st>>>(b->args);
@@ -230,7 +234,7 @@ void enqueue_line_search(omm_batch* b) {
   OMM_LAUNCH_CHECK();
   b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitW);
   OMM_LAUNCH_CHECK();
-  tc::gemm_grouped(st, b->gG.dev, b->gG.ngroups, b->gG.tiles, pl);
+  tc::gemm_persistent(st, b->gG.dev, b->gG.ngroups, b->gG.tiles, pl, b->err);
 }
 
 // start a mixed round of instance i from its current (just recomputed) state
@@ -266,14 +270,39 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
   b->opts = o;
   b->precond = o.no_precondition == 0;
   b->ctx.assign(count, nullptr);
-  for (int i = 0; i < count; ++i) {
-    omm_status rc = omm_create(m[i], n[i], H[i], S[i], T ? T[i] : nullptr, eta[i], tau[i], &o, stream, &b->ctx[i]);
-    if (rc != OMM_OK) {
-      const std::string msg = std::string("omm_create_batched: instance ") + std::to_string(i) + ": " +
-                              omm_last_error();
-      batch_destroy(b);
-      return fail(rc, msg);
-    }
+  // per-instance setup (float64 Cholesky inverse etc.) from several host threads, each on its
+  // own stream, so that the small factorisations of different instances overlap on the GPU
+  {
+    const int nthreads = std::min(count, 8);
+    std::vector<omm_status> rcs(count, OMM_OK);
+    std::vector<std::string> msgs(count);
+    std::atomic<int> next{0};
+    int device = 0;
+    cudaGetDevice(&device);
+    auto worker = [&]() {
+      cudaSetDevice(device);
+      cudaStream_t s = nullptr;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) s = nullptr;
+      for (int i = next++; i < count; i = next++) {
+        rcs[i] = omm_create(m[i], n[i], H[i], S[i], T ? T[i] : nullptr, eta[i], tau[i], &o, s, &b->ctx[i]);
+        if (rcs[i] != OMM_OK) msgs[i] = omm_last_error();
+        else b->ctx[i]->st = b->st;  // from now on everything is ordered on the batch stream
+      }
+      if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+    };
+    std::vector<std::thread> pool;
+    for (int k = 0; k < nthreads; ++k) pool.emplace_back(worker);
+    for (auto& th : pool) th.join();
+    for (int i = 0; i < count; ++i)
+      if (rcs[i] != OMM_OK) {
+        const std::string msg = std::string("omm_create_batched: instance ") + std::to_string(i) + ": " + msgs[i];
+        const omm_status rc = rcs[i];
+        batch_destroy(b);
+        return fail(rc, msg);
+      }
   }
   if (o.precision != OMM_PREC_MIXED) {
     *out = b;  // float64 batches solve instance by instance
@@ -327,6 +356,8 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       b->max_ttiles = std::max(b->max_ttiles, (int)(((2L * ni + 31) / 32) * ((mi + 31) / 32)));
     }
     alloc(&b->args, count);
+    alloc(&b->err, 1);
+    OMM_CUDA_TRY(cudaMemsetAsync(b->err, 0, sizeof(int), b->st));
     OMM_CUDA_TRY(cudaMemcpyAsync(b->args, args.data(), count * sizeof(IterArgs), cudaMemcpyHostToDevice, b->st));
     upload_groups(b->st, &b->gPG, gpg);
     upload_groups(b->st, &b->gHD, ghd);
@@ -471,6 +502,13 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
     OMM_CUDA_TRY(cudaEventRecord(e1, b->st));
     OMM_CUDA_TRY(cudaEventSynchronize(e1));
     cudaEventElapsedTime(&ms_total, e0, e1);
+    int gerr = 0;
+    OMM_CUDA_TRY(cudaMemcpy(&gerr, b->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (gerr != 0) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(OMM_ERR_TIMEOUT, "omm_solve_batched: a bounded device wait expired in a grouped GEMM");
+    }
     for (int i = 0; i < cnt; ++i) {
       omm_ctx* c = b->ctx[i];
       const Scalars& h = *c->sc_host;

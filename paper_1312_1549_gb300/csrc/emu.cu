@@ -140,10 +140,19 @@ struct EmuState {
   __nv_bfloat16* Ys = nullptr;   // s slices of [HC; SC]    2n x m
   __nv_bfloat16* Ws = nullptr;   // s slices of [S_W | H_W] n x 2n
   __nv_bfloat16* YTs = nullptr;  // s slices of [HC | SC]^T m x 2n
-  double* T64 = nullptr;         // [HC; SC]^T in float64  m x 2n
-  tc::Operand opHS, opC, opY, opW, opYT;
+  double* T64 = nullptr;         // [HC; SC]^T in float64  m x 2n (also C^T and C^T S_W for D)
+  __nv_bfloat16* CTs = nullptr;  // kDensitySlices slices of C^T          m x n
+  __nv_bfloat16* XTs = nullptr;  // kDensitySlices slices of C^T S_W      m x n
+  __nv_bfloat16* SWs = nullptr;  // kDensitySlices slices of S_W          n x n
+  long ldn = 0;
+  tc::Operand opHS, opC, opY, opW, opYT, opCT, opXT, opSW, opCTb;  // opCTb: C^T as a B operand
   int* err = nullptr;
 };
+
+namespace {
+// D needs |dD| <= 1e-7 at O(1) entries: 8 slices (40 bits) leave a wide margin
+constexpr int kDensitySlices = 8;
+}
 
 EmuState* emu_create(cudaStream_t st, int m, int n, int slices, const double* HS) {
   EmuState* es = new EmuState();
@@ -160,6 +169,10 @@ EmuState* emu_create(cudaStream_t st, int m, int n, int slices, const double* HS
     alloc(&es->Ws, (size_t)s * n * ld2n);
     alloc(&es->YTs, (size_t)s * m * ld2n);
     alloc(&es->T64, (size_t)m * 2 * n);
+    es->ldn = round8(n);
+    alloc(&es->CTs, (size_t)kDensitySlices * m * es->ldn);
+    alloc(&es->XTs, (size_t)kDensitySlices * m * es->ldn);
+    alloc(&es->SWs, (size_t)kDensitySlices * n * es->ldn);
     alloc(&es->err, 1);
     OMM_CUDA_TRY(cudaMemsetAsync(es->err, 0, sizeof(int), st));
     emu::slice_rows(st, HS, 2L * m, m, m, slices, es->HSs, ldm, nullptr);
@@ -168,6 +181,10 @@ EmuState* emu_create(cudaStream_t st, int m, int n, int slices, const double* HS
     es->opY = tc::make_operand(es->Ys, 2L * n, m, ldm, slices, false);
     es->opW = tc::make_operand(es->Ws, n, 2L * n, ld2n, slices, true);
     es->opYT = tc::make_operand(es->YTs, m, 2L * n, ld2n, slices, false);
+    es->opCT = tc::make_operand(es->CTs, m, n, es->ldn, kDensitySlices, true);
+    es->opXT = tc::make_operand(es->XTs, m, n, es->ldn, kDensitySlices, true);
+    es->opSW = tc::make_operand(es->SWs, n, n, es->ldn, kDensitySlices, false);
+    es->opCTb = tc::make_operand(es->CTs, m, n, es->ldn, kDensitySlices, false);
   } catch (...) {
     emu_destroy(es);
     throw;
@@ -181,7 +198,7 @@ void emu_update_H(EmuState* es, cudaStream_t st, const double* HS) {
 
 void emu_destroy(EmuState* es) {
   if (!es) return;
-  void* bufs[] = {es->HSs, es->Cs, es->Ys, es->Ws, es->YTs, es->T64, es->err};
+  void* bufs[] = {es->HSs, es->Cs, es->Ys, es->Ws, es->YTs, es->T64, es->CTs, es->XTs, es->SWs, es->err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete es;
@@ -216,6 +233,26 @@ void emu_recompute_state(EmuState* es, cudaStream_t st, Scalars* sc, const doubl
   emu::gemm(st, es->opW, es->opYT, 2 * n, s, tc::Epilogue{G, m, m, 0, -4.0, 1.0, n, m, nullptr, es->err});
   launch_gmax(st, nm, G, part);
   launch_finish_gmax(st, sc, part);
+}
+
+}  // namespace omm
+
+namespace omm {
+
+// D = 2 C^T (2I - S_W) C = 4 C^T C - 2 (C^T S_W) C (n x m layout of C), float64-class:
+// X = C^T S_W from sliced C^T and S_W, then D = 4 C^T (C^T)^T - 2 X (C^T)^T.
+// The B operand C^T is the same slice stack as the A operand, mapped with B-sized TMA boxes.
+void emu_density(EmuState* es, cudaStream_t st, const double* C, const double* SWHW, double* D) {
+  const int m = es->m, n = es->n, s = kDensitySlices;
+  double* CT = es->T64;                  // m x n
+  double* XT = es->T64 + (long)m * n;    // m x n
+  emu::transpose(st, C, n, m, m, CT, n);
+  emu::slice_rows(st, CT, m, n, n, s, es->CTs, es->ldn, nullptr);
+  emu::slice_rows(st, SWHW, n, n, 2L * n, s, es->SWs, es->ldn, nullptr);   // S_W is symmetric
+  emu::gemm(st, es->opCT, es->opSW, n, s, tc::Epilogue{XT, n, n, 0, 1.0, 0.0, m, n, nullptr, es->err});
+  emu::slice_rows(st, XT, m, n, n, s, es->XTs, es->ldn, nullptr);
+  emu::gemm(st, es->opCT, es->opCTb, n, s, tc::Epilogue{D, m, m, 0, 4.0, 0.0, m, m, nullptr, es->err});
+  emu::gemm(st, es->opXT, es->opCTb, n, s, tc::Epilogue{D, m, m, 0, -2.0, 1.0, m, m, nullptr, es->err});
 }
 
 }  // namespace omm

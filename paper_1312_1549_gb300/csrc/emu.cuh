@@ -19,6 +19,8 @@ EmuState* emu_create(cudaStream_t st, int m, int n, int slices, const double* HS
 void emu_update_H(EmuState* es, cudaStream_t st, const double* HS);
 void emu_destroy(EmuState* es);
 int emu_error(EmuState* es, cudaStream_t st);
+// density matrix D = 2 C^T (2I - S_W) C (m x m) with float64-class products
+void emu_density(EmuState* es, cudaStream_t st, const double* C, const double* SWHW, double* D);
 void emu_recompute_state(EmuState* es, cudaStream_t st, Scalars* sc, const double* C, double* Y4,
                          double* SWHW, double* G, double* part, double* part2);
 

@@ -137,11 +137,13 @@ omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double
   const long ld = (K + 7) / 8 * 8;
   __nv_bfloat16* buf = nullptr;
   int* err = nullptr;
+  tc::GroupDesc* desc = nullptr;
   omm_status rc = OMM_OK;
   try {
     const size_t na = (size_t)M * ld, nb = (size_t)N * ld;
     if (cudaMalloc((void**)&buf, 2 * (na + nb) * sizeof(__nv_bfloat16)) != cudaSuccess ||
-        cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess) {
+        cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&desc, sizeof(tc::GroupDesc)) != cudaSuccess) {
       cudaGetLastError();
       if (buf) cudaFree(buf);
       set_last_error("omm_kernel_gemm_tc: device allocation failed");
@@ -153,7 +155,11 @@ omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double
     tc::split(st, B, N, K, K, b_hi, b_lo, ld, nullptr);
     tc::Operand oa = tc::make_operand(a_hi, M, K, ld, 2, true);
     tc::Operand ob = tc::make_operand(b_hi, N, K, ld, 2, false);
-    tc::gemm(st, oa, ob, K, npass, tc::Epilogue{C, N, N, 0, alpha, beta, M, N, nullptr, err});
+    // the persistent launch the solver uses for its line-search GEMMs
+    const tc::Epilogue ep{C, N, N, 0, alpha, beta, M, N, nullptr, err};
+    const tc::GroupDesc g = tc::make_group(oa, ob, K, ep, 0);
+    OMM_CUDA_TRY(cudaMemcpyAsync(desc, &g, sizeof(g), cudaMemcpyHostToDevice, st));
+    tc::gemm_persistent(st, desc, 1, tc::tiles_of(ep), npass == 3 ? tc::pairs_split3() : tc::pairs_single(), err);
     int h = 0;
     OMM_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -166,6 +172,7 @@ omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double
   }
   if (buf) cudaFree(buf);
   if (err) cudaFree(err);
+  if (desc) cudaFree(desc);
   return rc;
 }
 

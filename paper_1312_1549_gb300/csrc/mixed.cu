@@ -37,6 +37,10 @@ struct MixedState {
   double* Wref = nullptr;                              // [S_W | H_W] at the last refresh, n x 2n
   tc::Operand opHS, opP, opG, opD, opY, opYT, opW;
   int* err = nullptr;
+  // the four line-search GEMMs as persistent-launch descriptors (device), built on first use
+  tc::GroupDesc* plans = nullptr;
+  int plan_tiles[4] = {0, 0, 0, 0};
+  const Scalars* plan_sc = nullptr;
 };
 
 namespace {
@@ -136,6 +140,7 @@ void mixed_destroy(MixedState* ms) {
   if (ms->Gref) cudaFree(ms->Gref);
   if (ms->dY) cudaFree(ms->dY);
   if (ms->Wref) cudaFree(ms->Wref);
+  if (ms->plans) cudaFree(ms->plans);
   delete ms;
 }
 
@@ -189,6 +194,39 @@ void mixed_recompute_state(MixedState* ms, cudaStream_t st, Scalars* sc, const d
   launch_finish_gmax(st, sc, part);
 }
 
+namespace {
+
+enum { kPlanPG = 0, kPlanHD, kPlanProj, kPlanG };
+
+void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double* PG, double* Y4, double* Proj) {
+  const int m = ms->m, n = ms->n;
+  const long nm = (long)n * m;
+  const int* skip = &sc->done;
+  tc::GroupDesc h[4];
+  const tc::Epilogue epg{PG, m, m, 0, 1.0, 0.0, n, m, skip, ms->err};
+  const tc::Epilogue ehd{Y4 + 2 * nm, m, m, nm, 1.0, 0.0, n, 2 * m, skip, ms->err};
+  const tc::Epilogue epr{Proj, 4L * n, 4L * n, 0, 1.0, 0.0, n, 4 * n, skip, ms->err};
+  const tc::Epilogue eg{G, m, m, 0, -4.0, 1.0, n, m, skip, ms->err};
+  h[kPlanPG] = tc::make_group(ms->opG, ms->precond ? ms->opP : ms->opG, m, epg, 0);
+  h[kPlanHD] = tc::make_group(ms->opD, ms->opHS, m, ehd, 0);
+  h[kPlanProj] = tc::make_group(ms->opD, ms->opY, m, epr, 0);
+  h[kPlanG] = tc::make_group(ms->opW, ms->opYT, 4 * n, eg, 0);
+  ms->plan_tiles[kPlanPG] = tc::tiles_of(epg);
+  ms->plan_tiles[kPlanHD] = tc::tiles_of(ehd);
+  ms->plan_tiles[kPlanProj] = tc::tiles_of(epr);
+  ms->plan_tiles[kPlanG] = tc::tiles_of(eg);
+  if (!ms->plans) alloc(&ms->plans, 4);
+  OMM_CUDA_TRY(cudaMemcpyAsync(ms->plans, h, sizeof(h), cudaMemcpyHostToDevice, st));
+  OMM_CUDA_TRY(cudaStreamSynchronize(st));  // h is a stack buffer
+  ms->plan_sc = sc;
+}
+
+void run_plan(MixedState* ms, cudaStream_t st, int k) {
+  tc::gemm_persistent(st, ms->plans + k, 1, ms->plan_tiles[k], tc::pairs_split3(), ms->err);
+}
+
+}  // namespace
+
 void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, double* Dir, double* G,
                    double* Gold, double* PG, double* Y4, double* SWHW, double* Proj, double* part,
                    double* part2, const double* HS, const double* P, bool precond, Profiler& pf) {
@@ -196,13 +234,13 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   (void)P;
   const int m = ms->m, n = ms->n;
   const long nm = (long)n * m;
-  const int* skip = &sc->done;
   const int np = ms->npass;
+  if (ms->plan_sc != sc) build_plans(ms, st, sc, G, PG, Y4, Proj);
   // P G (Sec. 2.4)
   if (precond) {
     tc::split(st, G, n, m, m, ms->G_hi, ms->G_lo, ms->ldm, sc);
     pf.begin(st);
-    tc::gemm(st, ms->opG, ms->opP, m, np, tc::Epilogue{PG, m, m, 0, 1.0, 0.0, n, m, skip, ms->err});
+    run_plan(ms, st, kPlanPG);
     pf.end(st, 2.0 * np * n * (double)m * m);
   } else {
     launch_scale_copy(st, nm, G, 1.0, PG, sc);
@@ -213,12 +251,12 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   tc::split(st, Dir, n, m, m, ms->D_hi, ms->D_lo, ms->ldm, sc);
   // [H~ D ; S D] (n x m layout): one GEMM over the stacked [H~; S]
   pf.begin(st);
-  tc::gemm(st, ms->opD, ms->opHS, m, np, tc::Epilogue{Y4 + 2 * nm, m, m, nm, 1.0, 0.0, n, 2 * m, skip, ms->err});
+  run_plan(ms, st, kPlanHD);
   pf.end(st, 4.0 * np * n * (double)m * m);
   tc::split(st, Y4 + 2 * nm, 2L * n, m, m, ms->Y_hi + 2L * n * ms->ldm, ms->Y_lo + 2L * n * ms->ldm, ms->ldm, sc);
   // [H' | S' | H'' | S''] = D [HC; SC; HD; SD]^T (Eqs. 14-15)
   pf.begin(st);
-  tc::gemm(st, ms->opD, ms->opY, m, np, tc::Epilogue{Proj, 4L * n, 4L * n, 0, 1.0, 0.0, n, 4 * n, skip, ms->err});
+  run_plan(ms, st, kPlanProj);
   pf.end(st, 8.0 * np * n * (double)n * m);
   launch_traces(st, n, SWHW, Proj, part2, sc);
   launch_control_linesearch(st, sc, part2, traces_blocks(n));
@@ -231,7 +269,7 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   // G = Gref + 8 dHC - 4 [dS_W | dH_W | S_W,ref | H_W,ref] [HC; SC; dHC; dSC] (Eq. 12 about
   // the refresh point); the update preset G = Gref + 8 dHC
   pf.begin(st);
-  tc::gemm(st, ms->opW, ms->opYT, 4 * n, np, tc::Epilogue{G, m, m, 0, -4.0, 1.0, n, m, skip, ms->err});
+  run_plan(ms, st, kPlanG);
   pf.end(st, 8.0 * np * n * (double)n * m);
 }
 

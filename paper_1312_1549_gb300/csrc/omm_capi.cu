@@ -398,7 +398,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     double flop = 0.0, flop_tc = 0.0;
     const double per_it = 6.0 * m * (double)m * n + (c->mixed ? 16.0 : 12.0) * (double)m * n * n;
     const double per_state = 4.0 * m * (double)m * n + 8.0 * (double)m * n * n;
-    double ms_iter = 0.0, ms_ref = 0.0;
+    double ms_iter = 0.0, ms_ref = 0.0, ms_cert = 0.0;
     int fp64_iters = 0, refinements = 0;
     int iter_total = 0;
     double g_ref = -1.0;  // max|G| at the last float64 recompute
@@ -432,6 +432,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
       read_scalars(c);
       if (tc_state) ms_iter += elapsed(c->ev[0], c->ev[1]);
       else ms_ref += elapsed(c->ev[0], c->ev[1]);
+      if (!tc_state && !emu_state) ms_cert += elapsed(c->ev[0], c->ev[1]);
       Scalars& h = *c->sc_host;
       if (!std::isfinite(h.gmax) || !std::isfinite(h.E)) {
         result = OMM_ERR_NONFINITE;
@@ -505,6 +506,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     inf.ms_setup = c->ms_setup;
     inf.ms_iterate = ms_iter;
     inf.ms_refine = ms_ref;
+    inf.ms_certify = ms_cert;
     if (result == OMM_OK || result == OMM_ERR_NO_CONVERGENCE) {
       if (Cout) OMM_CUDA_TRY(cudaMemcpyAsync(Cout, c->C, nm * sizeof(double), cudaMemcpyDefault, c->st));
       if (E) *E = inf.E;
@@ -518,7 +520,8 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
           ensure_mm(c);
           tgt = c->mm;
         }
-        density_into(c, tgt);
+        if (c->emu && c->opts.emulated_certificate) emu_density(c->emu, c->st, c->C, c->SWHW, tgt);
+        else density_into(c, tgt);
         if (tgt != D)
           OMM_CUDA_TRY(cudaMemcpyAsync(D, tgt, (size_t)m * m * sizeof(double), cudaMemcpyDefault, c->st));
         flop += 2.0 * n * (double)n * m + 2.0 * m * (double)m * n;
@@ -557,7 +560,9 @@ omm_status omm_backward(omm_ctx* c, double* dEdH, double* dEdS) {
     double* tS = dEdS;
     if (dEdH && !is_device_ptr(dEdH)) { ensure_mm(c); tH = c->mm; }
     if (dEdH) {
-      density_into(c, tH);
+      // the same density matrix omm_solve returns
+      if (c->emu && c->opts.emulated_certificate) emu_density(c->emu, c->st, c->C, c->SWHW, tH);
+      else density_into(c, tH);
       if (tH != dEdH) OMM_CUDA_TRY(cudaMemcpyAsync(dEdH, tH, bytes, cudaMemcpyDefault, c->st));
     }
     if (dEdS) {

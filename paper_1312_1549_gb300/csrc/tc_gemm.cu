@@ -22,6 +22,8 @@
 #include "omm_internal.cuh"
 #include "tc_gemm.cuh"
 
+#include <algorithm>
+
 namespace omm {
 namespace tc {
 namespace {
@@ -134,16 +136,54 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// C = alpha * v + beta * C for the 32 accumulator columns [col0, col0 + 32) of one row.
+__device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col0, const float (&v)[32]) {
+  if (row >= ep.M || col0 >= ep.N) return;
+  const int nvalid = min(32, ep.N - col0);
+  const long blk0 = col0 / ep.split_cols;
+  const long blk1 = (col0 + nvalid - 1) / ep.split_cols;
+  if (blk0 == blk1) {
+    double* base = ep.C + blk0 * ep.split_stride + (long)row * ep.ldc + (col0 - blk0 * ep.split_cols);
+    if (ep.beta == 0.0) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < nvalid) base[j] = ep.alpha * (double)v[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < nvalid) base[j] = fma(ep.beta, base[j], ep.alpha * (double)v[j]);
+    }
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    if (j >= nvalid) break;
+    const int col = col0 + j;
+    const long blk = col / ep.split_cols;
+    double* p = ep.C + blk * ep.split_stride + (long)row * ep.ldc + (col - blk * ep.split_cols);
+    const double a = ep.alpha * (double)v[j];
+    *p = (ep.beta == 0.0) ? a : fma(ep.beta, *p, a);
+  }
+}
+
 // One 128 x 256 output tile (shared by the single and the grouped kernel).
+// FUSED: the pair list is the split form (A_hi B_hi + A_hi B_lo + A_lo B_hi);
+// each stage then holds A_hi, A_lo, B_hi and B_lo of one K block (96 KB, two
+// stages) and feeds three MMA groups, so every operand byte is fetched once
+// per K block instead of once per pair (2.25x less shared-memory fill traffic).
+template <bool FUSED>
 __device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorMap* mB, int K, int rowsA,
                                           int rowsB, const PairList& pl, const Epilogue& ep_in, int tile) {
+  constexpr int NS = FUSED ? 2 : STAGES;
+  constexpr int SB = FUSED ? 2 * STAGE_BYTES : STAGE_BYTES;
+  static_assert(NS * SB == STAGES * STAGE_BYTES, "both modes use the same shared memory");
   const Epilogue ep = ep_in;
   if (ep.skip != nullptr && (ep.skip[0] | ep.skip[1])) return;  // uniform: before any resource use
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NS * SB);
   // bars[0..S) full, bars[S..2S) empty, bars[2S] accumulator ready
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -152,14 +192,14 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorM
   const int tiles_m = (ep.M + BM - 1) / BM;
   const int m0 = (tile % tiles_m) * BM, n0 = (tile / tiles_m) * BN;
   const int nkb = (K + BK - 1) / BK;
-  const int total = pl.n * nkb;
+  const int total = FUSED ? nkb : pl.n * nkb;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(smem_u32(&bars[s]), 1);
-      mbar_init(smem_u32(&bars[STAGES + s]), 1);
+      mbar_init(smem_u32(&bars[NS + s]), 1);
     }
-    mbar_init(smem_u32(&bars[2 * STAGES]), 1);
+    mbar_init(smem_u32(&bars[2 * NS]), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -180,26 +220,34 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorM
     prefetch_tmap(mA);
     prefetch_tmap(mB);
     for (int t = 0; t < total; ++t) {
-      const int s = t % STAGES, r = t / STAGES;
-      if (!mbar_wait(smem_u32(&bars[STAGES + s]), (r & 1) ^ 1)) {
+      const int s = t % NS, r = t / NS;
+      if (!mbar_wait(smem_u32(&bars[NS + s]), (r & 1) ^ 1)) {
         *abort_flag = 1;
         atomicCAS(ep.err, 0, 1);
         break;
       }
       if (*abort_flag) break;
-      const int p = t / nkb, kb = t % nkb;
       const uint32_t full = smem_u32(&bars[s]);
-      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-      mbar_expect_tx(full, STAGE_BYTES);
-      tma_load_2d(sa, mA, full, kb * BK, (int)pl.a[p] * rowsA + m0);
-      tma_load_2d(sa + A_BYTES, mB, full, kb * BK, (int)pl.b[p] * rowsB + n0);
+      const uint32_t sa = smem_u32(smem + s * SB);
+      mbar_expect_tx(full, SB);
+      if (FUSED) {
+        const int kb = t;
+        tma_load_2d(sa, mA, full, kb * BK, m0);                                  // A_hi
+        tma_load_2d(sa + A_BYTES, mA, full, kb * BK, rowsA + m0);               // A_lo
+        tma_load_2d(sa + 2 * A_BYTES, mB, full, kb * BK, n0);                   // B_hi
+        tma_load_2d(sa + 2 * A_BYTES + B_BYTES, mB, full, kb * BK, rowsB + n0); // B_lo
+      } else {
+        const int p = t / nkb, kb = t % nkb;
+        tma_load_2d(sa, mA, full, kb * BK, (int)pl.a[p] * rowsA + m0);
+        tma_load_2d(sa + A_BYTES, mB, full, kb * BK, (int)pl.b[p] * rowsB + n0);
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     constexpr uint32_t idesc = idesc_bf16(BM, BN);
     int t = 0;
     for (; t < total; ++t) {
-      const int s = t % STAGES, r = t / STAGES;
+      const int s = t % NS, r = t / NS;
       if (!mbar_wait(smem_u32(&bars[s]), r & 1)) {
         *abort_flag = 1;
         atomicCAS(ep.err, 0, 2);
@@ -207,18 +255,28 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorM
       }
       if (*abort_flag) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-      const uint32_t sb = sa + A_BYTES;
+      const uint32_t sa = smem_u32(smem + s * SB);
+      if (FUSED) {
+        const uint32_t alo = sa + A_BYTES, bhi = sa + 2 * A_BYTES, blo = bhi + B_BYTES;
 #pragma unroll
-      for (int k = 0; k < BK / 16; ++k) {
-        umma_bf16(tmem, smem_desc(sa + k * 32), smem_desc(sb + k * 32), idesc, (t > 0 || k > 0) ? 1u : 0u);
+        for (int k = 0; k < BK / 16; ++k) {
+          umma_bf16(tmem, smem_desc(sa + k * 32), smem_desc(bhi + k * 32), idesc, (t > 0 || k > 0) ? 1u : 0u);
+          umma_bf16(tmem, smem_desc(sa + k * 32), smem_desc(blo + k * 32), idesc, 1u);
+          umma_bf16(tmem, smem_desc(alo + k * 32), smem_desc(bhi + k * 32), idesc, 1u);
+        }
+      } else {
+        const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          umma_bf16(tmem, smem_desc(sa + k * 32), smem_desc(sb + k * 32), idesc, (t > 0 || k > 0) ? 1u : 0u);
+        }
       }
-      umma_commit(smem_u32(&bars[STAGES + s]));  // stage s is free once these MMAs have read it
+      umma_commit(smem_u32(&bars[NS + s]));  // stage s is free once these MMAs have read it
     }
-    umma_commit(smem_u32(&bars[2 * STAGES]));    // accumulator complete (also on abort: drains MMAs)
+    umma_commit(smem_u32(&bars[2 * NS]));    // accumulator complete (also on abort: drains MMAs)
   } else if (warp >= 2) {
     // ---------------- epilogue
-    const bool ok = mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
+    const bool ok = mbar_wait(smem_u32(&bars[2 * NS]), 0);
     if (!ok) atomicCAS(ep.err, 0, 3);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int lane_base = (warp & 3) * 32;
@@ -228,17 +286,7 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorM
     for (int c = 0; c < BN / 32; ++c) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(c * 32), v);
-      if (!write || row >= ep.M) continue;
-      const int col0 = n0 + c * 32;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int col = col0 + j;
-        if (col >= ep.N) break;
-        const long blk = col / ep.split_cols;
-        double* p = ep.C + blk * ep.split_stride + (long)row * ep.ldc + (col - blk * ep.split_cols);
-        const double a = ep.alpha * (double)v[j];
-        *p = (ep.beta == 0.0) ? a : fma(ep.beta, *p, a);
-      }
+      if (write) store_chunk(ep, row, n0 + c * 32, v);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -250,14 +298,16 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorM
   }
 }
 
+template <bool FUSED>
 __global__ void __launch_bounds__(NTHREADS, 1)
 gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                        int K, int rowsA, int rowsB, const __grid_constant__ PairList pl, Epilogue ep) {
-  gemm_tile(&mA, &mB, K, rowsA, rowsB, pl, ep, blockIdx.x);
+  gemm_tile<FUSED>(&mA, &mB, K, rowsA, rowsB, pl, ep, blockIdx.x);
 }
 
 // One launch over the tiles of many independent GEMMs (a batch of OMM
 // instances): CTA b works on tile b - g.tile_begin of the group g that holds it.
+template <bool FUSED>
 __global__ void __launch_bounds__(NTHREADS, 1)
 gemm_grouped_kernel(const GroupDesc* __restrict__ groups, int ngroups, const __grid_constant__ PairList pl) {
   int lo = 0, hi = ngroups - 1;
@@ -267,21 +317,212 @@ gemm_grouped_kernel(const GroupDesc* __restrict__ groups, int ngroups, const __g
     if (groups[mid].tile_begin <= b) lo = mid; else hi = mid - 1;
   }
   const GroupDesc* g = groups + lo;
-  gemm_tile(reinterpret_cast<const CUtensorMap*>(&g->a), reinterpret_cast<const CUtensorMap*>(&g->b), g->K,
-            g->rowsA, g->rowsB, pl, g->ep, b - g->tile_begin);
+  gemm_tile<FUSED>(reinterpret_cast<const CUtensorMap*>(&g->a), reinterpret_cast<const CUtensorMap*>(&g->b),
+                   g->K, g->rowsA, g->rowsB, pl, g->ep, b - g->tile_begin);
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ int find_group(const GroupDesc* __restrict__ groups, int ngroups, int tile) {
+  int lo = 0, hi = ngroups - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (groups[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Persistent version of the grouped launch: one CTA per SM walks the tiles
+// b, b + gridDim.x, ... of all groups. The accumulator is double-buffered in
+// TMEM (2 x 256 columns) so the epilogue of one tile overlaps the main loop
+// of the next; the producer's stage ring continues across tiles.
+template <bool FUSED>
+__global__ void __launch_bounds__(NTHREADS, 1)
+gemm_persistent_kernel(const GroupDesc* __restrict__ groups, int ngroups, int total_tiles,
+                       const __grid_constant__ PairList pl, int* err) {
+  constexpr int NS = FUSED ? 2 : STAGES;
+  constexpr int SB = FUSED ? 2 * STAGE_BYTES : STAGE_BYTES;
+  constexpr int ACC_COLS = 256;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NS * SB);
+  // bars[0..NS) full, [NS..2NS) empty, [2NS..2NS+2) accumulator full, [2NS+2..2NS+4) accumulator empty
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NS; ++q) {
+      mbar_init(smem_u32(&bars[q]), 1);
+      mbar_init(smem_u32(&bars[NS + q]), 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(smem_u32(&bars[2 * NS + q]), 1);      // committed by the MMA thread
+      mbar_init(smem_u32(&bars[2 * NS + 2 + q]), 4);  // one arrival per epilogue warp
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * ACC_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    uint32_t it = 0;
+    for (int tile = blockIdx.x; tile < total_tiles && !*abort_flag; tile += gridDim.x) {
+      const GroupDesc* g = groups + find_group(groups, ngroups, tile);
+      const int* skip = g->ep.skip;
+      if (skip != nullptr && (skip[0] | skip[1])) continue;
+      const CUtensorMap* mA = reinterpret_cast<const CUtensorMap*>(&g->a);
+      const CUtensorMap* mB = reinterpret_cast<const CUtensorMap*>(&g->b);
+      const int local = tile - g->tile_begin, tiles_m = (g->ep.M + BM - 1) / BM;
+      const int m0 = (local % tiles_m) * BM, n0 = (local / tiles_m) * BN;
+      const int nkb = (g->K + BK - 1) / BK;
+      const int total = FUSED ? nkb : pl.n * nkb;
+      for (int t = 0; t < total; ++t, ++it) {
+        const int q = it % NS;
+        const uint32_t r = it / NS;
+        if (!mbar_wait(smem_u32(&bars[NS + q]), (r & 1) ^ 1)) {
+          *abort_flag = 1;
+          atomicCAS(err, 0, 1);
+          break;
+        }
+        const uint32_t full = smem_u32(&bars[q]);
+        const uint32_t sa = smem_u32(smem + q * SB);
+        mbar_expect_tx(full, SB);
+        if (FUSED) {
+          tma_load_2d(sa, mA, full, t * BK, m0);
+          tma_load_2d(sa + A_BYTES, mA, full, t * BK, g->rowsA + m0);
+          tma_load_2d(sa + 2 * A_BYTES, mB, full, t * BK, n0);
+          tma_load_2d(sa + 2 * A_BYTES + B_BYTES, mB, full, t * BK, g->rowsB + n0);
+        } else {
+          const int p = t / nkb, kb = t % nkb;
+          tma_load_2d(sa, mA, full, kb * BK, (int)pl.a[p] * g->rowsA + m0);
+          tma_load_2d(sa + A_BYTES, mB, full, kb * BK, (int)pl.b[p] * g->rowsB + n0);
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    uint32_t it = 0, lt = 0;
+    for (int tile = blockIdx.x; tile < total_tiles && !*abort_flag; tile += gridDim.x) {
+      const GroupDesc* g = groups + find_group(groups, ngroups, tile);
+      const int* skip = g->ep.skip;
+      if (skip != nullptr && (skip[0] | skip[1])) continue;
+      const uint32_t buf = lt & 1, use = lt >> 1;
+      if (!mbar_wait(smem_u32(&bars[2 * NS + 2 + buf]), (use & 1) ^ 1)) {
+        *abort_flag = 1;
+        atomicCAS(err, 0, 4);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t d = tmem + buf * ACC_COLS;
+      const int nkb = (g->K + BK - 1) / BK;
+      const int total = FUSED ? nkb : pl.n * nkb;
+      for (int t = 0; t < total; ++t, ++it) {
+        const int q = it % NS;
+        const uint32_t r = it / NS;
+        if (!mbar_wait(smem_u32(&bars[q]), r & 1)) {
+          *abort_flag = 1;
+          atomicCAS(err, 0, 2);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = smem_u32(smem + q * SB);
+        if (FUSED) {
+          const uint32_t alo = sa + A_BYTES, bhi = sa + 2 * A_BYTES, blo = bhi + B_BYTES;
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+            umma_bf16(d, smem_desc(sa + k * 32), smem_desc(bhi + k * 32), idesc, (t > 0 || k > 0) ? 1u : 0u);
+            umma_bf16(d, smem_desc(sa + k * 32), smem_desc(blo + k * 32), idesc, 1u);
+            umma_bf16(d, smem_desc(alo + k * 32), smem_desc(bhi + k * 32), idesc, 1u);
+          }
+        } else {
+          const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k)
+            umma_bf16(d, smem_desc(sa + k * 32), smem_desc(sb + k * 32), idesc, (t > 0 || k > 0) ? 1u : 0u);
+        }
+        umma_commit(smem_u32(&bars[NS + q]));
+      }
+      umma_commit(smem_u32(&bars[2 * NS + buf]));  // this tile's accumulator is complete
+      ++lt;
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue
+    const int lane_base = (warp & 3) * 32;
+    uint32_t lt = 0;
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+      const GroupDesc* g = groups + find_group(groups, ngroups, tile);
+      const int* skip = g->ep.skip;
+      if (skip != nullptr && (skip[0] | skip[1])) continue;
+      const uint32_t buf = lt & 1, use = lt >> 1;
+      const bool ok = !*abort_flag && mbar_wait(smem_u32(&bars[2 * NS + buf]), use & 1);
+      if (!ok) {
+        atomicCAS(err, 0, 3);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const Epilogue ep = g->ep;
+      const int local = tile - g->tile_begin, tiles_m = (ep.M + BM - 1) / BM;
+      const int m0 = (local % tiles_m) * BM, n0 = (local / tiles_m) * BN;
+      const int row = m0 + lane_base + lane;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+        tmem_ld32(tmem + buf * ACC_COLS + ((uint32_t)lane_base << 16) + (uint32_t)(c * 32), v);
+        store_chunk(ep, row, n0 + c * 32, v);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars[2 * NS + 2 + buf]));
+      ++lt;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC_COLS) : "memory");
+  }
+}
+
+int sm_count() {
+  static const int n = [] {
+    int dev = 0, c = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) c = 148;
+    return c;
+  }();
+  return n;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 lookup_encoder() {
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    fn = nullptr;
+  return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 encoder() {
-  if (!g_encode) {
-    cudaDriverEntryPointQueryResult q;
-    void* fn = nullptr;
-    OMM_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !fn) throw CudaError{cudaErrorNotSupported, "cuTensorMapEncodeTiled"};
-    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
-  return g_encode;
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = lookup_encoder();  // thread-safe one-time lookup
+  if (!fn) throw CudaError{cudaErrorNotSupported, "cuTensorMapEncodeTiled"};
+  return fn;
 }
 
 }  // namespace
@@ -330,10 +571,16 @@ PairList pairs_single() {
   return p;
 }
 
+bool is_split3(const PairList& pl) {
+  return pl.n == 3 && pl.a[0] == 0 && pl.b[0] == 0 && pl.a[1] == 0 && pl.b[1] == 1 && pl.a[2] == 1 && pl.b[2] == 0;
+}
+
 void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const PairList& pl, const Epilogue& ep) {
   static bool attr_set = false;
   if (!attr_set) {
-    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_split_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      SMEM_BYTES));
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_bf16_split_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       SMEM_BYTES));
     attr_set = true;
   }
@@ -343,7 +590,10 @@ void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const Pair
   dim3 grid((unsigned)(((ep.N + BN - 1) / BN) * ((ep.M + BM - 1) / BM)));
   const CUtensorMap* a = reinterpret_cast<const CUtensorMap*>(&A.map);
   const CUtensorMap* b = reinterpret_cast<const CUtensorMap*>(&B.map);
-  gemm_bf16_split_kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(*a, *b, K, (int)A.rows, (int)B.rows, pl, ep);
+  if (is_split3(pl) && A.slices >= 2 && B.slices >= 2)
+    gemm_bf16_split_kernel<true><<<grid, NTHREADS, SMEM_BYTES, st>>>(*a, *b, K, (int)A.rows, (int)B.rows, pl, ep);
+  else
+    gemm_bf16_split_kernel<false><<<grid, NTHREADS, SMEM_BYTES, st>>>(*a, *b, K, (int)A.rows, (int)B.rows, pl, ep);
   OMM_LAUNCH_CHECK();
 }
 
@@ -362,18 +612,49 @@ GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& 
 }
 
 void prepare_grouped() {
+  prepare_persistent();
   static bool attr_set = false;
   if (!attr_set) {
-    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_grouped_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      SMEM_BYTES));
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_grouped_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       SMEM_BYTES));
     attr_set = true;
   }
 }
 
+void prepare_persistent() {
+  static bool attr_set = false;
+  if (!attr_set) {
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      SMEM_BYTES));
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      SMEM_BYTES));
+    sm_count();
+    attr_set = true;
+  }
+}
+
+void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl,
+                     int* err) {
+  prepare_persistent();
+  if (ngroups <= 0 || total_tiles <= 0) return;
+  const unsigned grid = (unsigned)std::min(total_tiles, sm_count());
+  if (is_split3(pl))
+    gemm_persistent_kernel<true><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, pl, err);
+  else
+    gemm_persistent_kernel<false><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, pl, err);
+  OMM_LAUNCH_CHECK();
+}
+
 void gemm_grouped(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl) {
   prepare_grouped();
   if (ngroups <= 0 || total_tiles <= 0) return;
-  gemm_grouped_kernel<<<(unsigned)total_tiles, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, pl);
+  // every operand of a grouped launch is a split pair (2-slice stack)
+  if (is_split3(pl))
+    gemm_grouped_kernel<true><<<(unsigned)total_tiles, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, pl);
+  else
+    gemm_grouped_kernel<false><<<(unsigned)total_tiles, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, pl);
   OMM_LAUNCH_CHECK();
 }
 

@@ -70,7 +70,12 @@ struct alignas(64) GroupDesc {
 };
 GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin);
 // groups_dev: ngroups descriptors in device memory, sorted by tile_begin; all share the pair list
-void prepare_grouped();  // kernel attributes (call before a stream capture)
+void prepare_grouped();     // kernel attributes (call before a stream capture)
+void prepare_persistent();
+// persistent grouped launch: one CTA per SM, double-buffered TMEM accumulators; err receives a
+// nonzero code if a bounded wait expired
+void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl,
+                     int* err);
 void gemm_grouped(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl);
 
 // x (float64, rows x cols, ld_src) -> hi = bf16(x), lo = bf16(x - hi) (ld_dst);

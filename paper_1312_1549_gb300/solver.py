@@ -104,12 +104,12 @@ class OMMSolver:
             N.check(rc, "omm_solve")
         return C_out, E.value, (D_out if want_D else None), self.info
 
-    def backward(self, dEdH=None, dEdS=None, device=None):
+    def backward(self, dEdH=None, dEdS=None, device=None, want_H=True, want_S=True):
         """(dE/dH, dE/dS) = (D, -EDM) at the last converged solve (m x m)."""
         dev = device if device is not None else torch.device("cuda")
-        if dEdH is None:
+        if dEdH is None and want_H:
             dEdH = torch.empty((self.m, self.m), dtype=torch.float64, device=dev)
-        if dEdS is None:
+        if dEdS is None and want_S:
             dEdS = torch.empty((self.m, self.m), dtype=torch.float64, device=dev)
         N.check(N.lib().omm_backward(self._h, _ptr(dEdH), _ptr(dEdS)), "omm_backward")
         return dEdH, dEdS
