@@ -185,10 +185,19 @@ def run_batch(args):
     C0 = [t(p.C0) for p in probs]
     stream = torch.cuda.Stream()
 
+    phases = []
+
     def step(precision="mixed", subset=None):
         idx = range(len(probs)) if subset is None else subset
-        with S.OMMBatch([dev[i] for i in idx], precision=precision, stream=stream) as b:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with S.OMMBatch([dev[i] for i in idx], precision=precision, stream=stream,
+                        profile=precision == "mixed",
+                        native_certificate=args.native_certificate) as b:
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
             _, E, infos = b.solve([C0[i] for i in idx])
+        phases.append((t1 - t0, time.perf_counter() - t1))
         return E, infos
 
     for _ in range(args.warmup):
@@ -204,16 +213,30 @@ def run_batch(args):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     out = _base_line(args, ms * 1e-3)
+    out["config"]["certificate"] = "native float64" if args.native_certificate else "float64-class (sliced)"
     logical = sum(i["iterations"] * (6.0 * p.m * p.m * p.n + 16.0 * p.m * p.n * p.n)
                   for i, p in zip(infos, probs))
+    timed = phases[-args.steps:]
+    b0 = infos[0]  # batch totals are repeated in every instance's report
+    achieved = (b0["main_gemm_flop"] / (b0["ms_main_gemm"] * 1e-3) / 1e12) if b0["ms_main_gemm"] > 0 else None
+    peak = load_peaks()[0]["bf16_tflops_sustained"]
     out.update({"instances": len(probs), "m_range": [min(p.m for p in probs), max(p.m for p in probs)],
                 "line_searches_max": max(i["iterations"] for i in infos),
                 "line_searches_total": sum(i["iterations"] for i in infos),
                 "gemm_tflops_logical": logical / (ms * 1e-3) / 1e12,
+                "s_create_wall": statistics.mean(t[0] for t in timed),
+                "s_solve_wall": statistics.mean(t[1] for t in timed),
+                "ms_line_search_graphs": b0["ms_iterate"],
+                "ms_refresh_sum": sum(i["ms_refine"] - i["ms_certify"] for i in infos),
+                "ms_certify_sum": sum(i["ms_certify"] for i in infos),
                 "gpu_launches": S.launch_count() - launches0, "clocks": clk.summary(),
-                "roofline": {"bound": "tensor", "achieved": None, "peak": load_peaks()[0]["bf16_tflops_sustained"],
-                             "unit": "TFLOP/s", "frac": None, "traffic": None,
-                             "kernel": "gemm_grouped_kernel (tcgen05)", "note": "not separated in batch mode"}})
+                "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
+                             "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                             "traffic": None,
+                             "kernel": "gemm_persistent_kernel (grouped over the batch, tcgen05, fused 3-term split)",
+                             "peak_source": "bf16_tflops_sustained of measured MEASURED_PEAKS",
+                             "launches": b0["main_gemm_launches"],
+                             "avg_launch_ms": b0["ms_main_gemm"] / max(b0["main_gemm_launches"], 1)}})
     # accuracy on a sample of instances against the eigenpair definition
     from oracle import exact
     sample = list(range(0, len(probs), max(1, len(probs) // 4)))
@@ -258,7 +281,7 @@ def run_sequence(args):
     def step():
         infos = []
         with S.OMMSolver(H0, Sm, T, p.n, p.eta, p.tau, precision="mixed", stream=stream,
-                         emulated_certificate=args.emulated_certificate) as s:
+                         native_certificate=args.native_certificate) as s:
             C = C0
             for k in range(args.sequence):
                 if k > 0:
@@ -283,7 +306,7 @@ def run_sequence(args):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     out = _base_line(args, ms * 1e-3)
-    out["config"]["certificate"] = "float64-class (sliced)" if args.emulated_certificate else "native float64"
+    out["config"]["certificate"] = "native float64" if args.native_certificate else "float64-class (sliced)"
     out.update({"line_searches": [i["iterations"] for _, i in infos], "E": [E for E, _ in infos],
                 "gmax": max(i["gmax"] for _, i in infos), "clocks": clk.summary()})
     print(json.dumps(out), flush=True)
@@ -299,7 +322,7 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
     ap.add_argument("--instances", type=int, default=64, help="config 4: batch size")
     ap.add_argument("--sequence", type=int, default=10, help="config 5: Hamiltonians in the sequence")
-    ap.add_argument("--emulated-certificate", action="store_true")
+    ap.add_argument("--native-certificate", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -331,7 +354,7 @@ def main():
 
     def step(precision=args.precision, profile=True):
         with S.OMMSolver(H, Sm, T, p.n, p.eta, p.tau, precision=precision, stream=stream,
-                         profile=profile) as s:
+                         profile=profile, native_certificate=args.native_certificate) as s:
             _, E, _, info = s.solve(C0, want_D=True, C_out=Cbuf, D_out=Dbuf)
         return E, info
 
@@ -376,7 +399,8 @@ def main():
     peak = peaks["bf16_tflops_sustained"] if mixed else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
-                "kernel": "gemm_bf16_split_kernel (tcgen05, 3-term split)" if mixed else "dgemm_kernel (DFMA)",
+                "kernel": ("gemm_persistent_kernel (tcgen05, fused 3-term split)" if mixed
+                           else "dgemm_kernel (DFMA)"),
                 "peak_source": f"bf16_tflops_sustained of {peak_kind} MEASURED_PEAKS" if mixed else
                 "float64 DFMA (no measured peak; see fp64 fields)",
                 "launches": main_launches, "avg_launch_ms": main_ms / max(main_launches, 1)}
@@ -384,11 +408,14 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "bf16x3+f64" if mixed else "f64", "data": "synthetic",
            "config": {"workload": WORKLOADS[args.config], "precision": args.precision,
+                      "certificate": ("native float64" if args.native_certificate or not mixed
+                                      else "float64-class (sliced)"),
                       "l2": "inputs larger than L2 (H, S, T are m*m*8 bytes each)",
                       "parallelism": "replicas only" if world > 1 else "1 GPU"},
            "line_searches": iters, "refinements": infos[-1]["refinements"],
            "E": energies[-1], "gmax": infos[-1]["gmax"],
            "ms_setup": statistics.mean(i["ms_setup"] for i in infos),
+           "ms_precond": statistics.mean(i["ms_precond"] for i in infos),
            "ms_iterate": it_ms, "ms_refine": statistics.mean(i["ms_refine"] for i in infos),
            "ms_certify": statistics.mean(i["ms_certify"] for i in infos),
            "ms_outputs": statistics.mean(i["ms_outputs"] for i in infos),
@@ -416,7 +443,8 @@ def main():
         Dh = torch.empty((p.m, p.m), dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with S.OMMSolver(Hh, Sh, Th, p.n, p.eta, p.tau, precision=args.precision, stream=stream) as s:
+        with S.OMMSolver(Hh, Sh, Th, p.n, p.eta, p.tau, precision=args.precision, stream=stream,
+                         native_certificate=args.native_certificate) as s:
             _, Ee, _, _ = s.solve(C0h, want_D=True, C_out=Ch, D_out=Dh)
         te = time.perf_counter() - t0
         out["e2e"] = {"value": te, "unit": "s", "h2d_bytes_per_step": (3 * p.m * p.m + p.n * p.m) * 8,

@@ -84,10 +84,11 @@ typedef struct {
                            the last float64 refinement; 0 -> 1e-4 */
   int profile;          /* 1 -> time every launch of the line-search GEMM with CUDA events on
                            the context's stream (omm_info.ms_main_gemm and friends) */
-  int emulated_certificate; /* mixed: 1 -> certify the final point, and form the density
-                           matrix D of omm_solve, with float64-class tensor-core products
-                           (fixed-point slices, about 2^-50 resp. 2^-40 of each row-scaled
-                           operand) instead of native float64 (0, default) */
+  int native_certificate; /* mixed: 0 (default) -> certify the final point, and form the
+                           density matrix D and the gradients of omm_backward, with
+                           float64-class tensor-core products (fixed-point slices, about
+                           2^-50 resp. 2^-40 of each row-scaled operand); 1 -> with native
+                           float64 GEMMs */
 } omm_opts;
 
 /* Per-solve report. */
@@ -110,6 +111,10 @@ typedef struct {
   double main_gemm_launches; /* with opts.profile: number of those launches */
   double main_gemm_flop;     /* with opts.profile: flops they issued (tensor-core flops when mixed) */
   double ms_certify;         /* native float64 state recomputes (part of ms_refine) */
+  double ms_precond;         /* the float64 Cholesky inverse P = (S + T/tau)^-1 (part of ms_setup) */
+  double ms_batch;           /* omm_solve_batched only: the whole batched solve. There ms_iterate,
+                                ms_main_gemm, main_gemm_launches and main_gemm_flop are batch
+                                totals too (the same in every instance's report) */
 } omm_info;
 
 /* Create a solver context for one (H, S, T) and do the per-geometry setup:

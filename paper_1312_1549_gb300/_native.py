@@ -23,7 +23,7 @@ class OmmOpts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("max_iter", ct.c_int), ("no_precondition", ct.c_int),
                 ("check_every", ct.c_int), ("tol_grad", ct.c_double), ("e_tol", ct.c_double),
                 ("refine_ratio", ct.c_double), ("profile", ct.c_int),
-                ("emulated_certificate", ct.c_int)]
+                ("native_certificate", ct.c_int)]
 
 
 class OmmInfo(ct.Structure):
@@ -33,7 +33,8 @@ class OmmInfo(ct.Structure):
                 ("ms_refine", ct.c_double), ("ms_outputs", ct.c_double), ("gemm_flop", ct.c_double),
                 ("gemm_flop_tc", ct.c_double), ("kernel_launches", ct.c_double),
                 ("ms_main_gemm", ct.c_double), ("main_gemm_launches", ct.c_double),
-                ("main_gemm_flop", ct.c_double), ("ms_certify", ct.c_double)]
+                ("main_gemm_flop", ct.c_double), ("ms_certify", ct.c_double),
+                ("ms_precond", ct.c_double), ("ms_batch", ct.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -128,6 +128,9 @@ struct Grouped {
   int ngroups = 0, tiles = 0;
 };
 
+constexpr int kGroupedGemms = 4;
+constexpr int kRefreshStreams = 8;
+
 template <typename T>
 void alloc(T** p, size_t count) {
   if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
@@ -158,6 +161,13 @@ struct omm_batch {
   cudaGraphExec_t exec = nullptr;
   bool precond = true;
   int* err = nullptr;  // bounded-wait failures of the grouped GEMMs
+  // with opts.profile the line searches are launched eagerly instead of replayed, and
+  // the grouped GEMMs (PG, [HD; SD], projections, gradient) are timed with CUDA events
+  bool profile = false;
+  Profiler prof;
+  // refreshes and certificates of different instances run concurrently on these
+  cudaStream_t pool[kRefreshStreams] = {};
+  std::vector<double> gemm_flop[kGroupedGemms];  // issued flops of each instance's group
 };
 
 namespace {
@@ -165,6 +175,11 @@ namespace {
 void batch_destroy(omm_batch* b) {
   if (!b) return;
   if (b->st) cudaStreamSynchronize(b->st);
+  for (cudaStream_t& q : b->pool)
+    if (q) {
+      cudaStreamSynchronize(q);
+      cudaStreamDestroy(q);
+    }
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (omm_ctx* c : b->ctx) {
@@ -191,6 +206,12 @@ void upload_groups(cudaStream_t st, Grouped* g, const std::vector<tc::GroupDesc>
   OMM_CUDA_TRY(cudaMemcpyAsync(g->dev, v.data(), v.size() * sizeof(tc::GroupDesc), cudaMemcpyHostToDevice, st));
 }
 
+void timed_gemm(omm_batch* b, const Grouped& g, const tc::PairList& pl) {
+  b->prof.begin(b->st);
+  tc::gemm_persistent(b->st, g.dev, g.ngroups, g.tiles, pl, b->err);
+  b->prof.end(b->st, 0.0);
+}
+
 // one line search of every instance (captured into the graph)
 void enqueue_line_search(omm_batch* b) {
   cudaStream_t st = b->st;
@@ -201,7 +222,7 @@ void enqueue_line_search(omm_batch* b) {
   if (b->precond) {
     b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitG);
     OMM_LAUNCH_CHECK();
-    tc::gemm_persistent(st, b->gPG.dev, b->gPG.ngroups, b->gPG.tiles, pl, b->err);
+    timed_gemm(b, b->gPG, pl);
   } else {
     b_copy_gradient_kernel<<<vec_grid, 256, 0, st>>>(b->args);
     OMM_LAUNCH_CHECK();
@@ -214,10 +235,10 @@ void enqueue_line_search(omm_batch* b) {
   OMM_LAUNCH_CHECK();
   b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitD);
   OMM_LAUNCH_CHECK();
-  tc::gemm_persistent(st, b->gHD.dev, b->gHD.ngroups, b->gHD.tiles, pl, b->err);
+  timed_gemm(b, b->gHD, pl);
   b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitHDSD);
   OMM_LAUNCH_CHECK();
-  tc::gemm_persistent(st, b->gPr.dev, b->gPr.ngroups, b->gPr.tiles, pl, b->err);
+  timed_gemm(b, b->gPr, pl);
   b_traces_kernel<<<dim3(b->max_tiles, cnt), dev::TB, 0, st>>>(b->args);
   OMM_LAUNCH_CHECK();
   b_control_linesearch_kernel<<<dim3(1, cnt), dev::TB, 0, st>>>(b->args);
@@ -234,7 +255,7 @@ void enqueue_line_search(omm_batch* b) {
   OMM_LAUNCH_CHECK();
   b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitW);
   OMM_LAUNCH_CHECK();
-  tc::gemm_persistent(st, b->gG.dev, b->gG.ngroups, b->gG.tiles, pl, b->err);
+  timed_gemm(b, b->gG, pl);
 }
 
 // start a mixed round of instance i from its current (just recomputed) state
@@ -351,10 +372,17 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       tc::Epilogue eg{c->G, mi, mi, 0, -4.0, 1.0, ni, mi, skip, v.err};
       gg.push_back(tc::make_group(*v.opW, *v.opYT, 4 * ni, eg, tgg));
       tgg += tc::tiles_of(eg);
+      // issued tensor flops, 3 x 2 M N K (3-term split), of this instance's share of each GEMM
+      const double issued = 3.0 * 2.0 * ni;  // x N x K
+      b->gemm_flop[0].push_back(b->precond ? issued * mi * mi : 0.0);
+      b->gemm_flop[1].push_back(issued * 2.0 * mi * mi);
+      b->gemm_flop[2].push_back(issued * 4.0 * ni * mi);
+      b->gemm_flop[3].push_back(issued * mi * 4.0 * ni);
       b->max_rows = std::max(b->max_rows, 2 * ni);
       b->max_tiles = std::max(b->max_tiles, a.tiles);
       b->max_ttiles = std::max(b->max_ttiles, (int)(((2L * ni + 31) / 32) * ((mi + 31) / 32)));
     }
+    for (cudaStream_t& q : b->pool) OMM_CUDA_TRY(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
     alloc(&b->args, count);
     alloc(&b->err, 1);
     OMM_CUDA_TRY(cudaMemsetAsync(b->err, 0, sizeof(int), b->st));
@@ -415,13 +443,20 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
   std::vector<int> finished(cnt, 0), rounds(cnt, 0), refinements(cnt, 0), energy_stop(cnt, 0);
   std::vector<int> iter_total(cnt, 0), last_done(cnt, 0), round_start(cnt, 0);
   std::vector<omm_status> result(cnt, OMM_OK);
-  std::vector<double> ms_ref(cnt, 0.0);
+  std::vector<double> ms_ref(cnt, 0.0), ms_cert(cnt, 0.0);
+  std::vector<int> iter_before(cnt, 0);
+  std::vector<char> active(cnt, 0);
   omm_status worst = OMM_OK;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, g0 = nullptr, g1 = nullptr;
   float ms_total = 0.f;
+  double ms_graph = 0.0, gemm_flop = 0.0;
+  const bool profile = b->opts.profile != 0;
   try {
     OMM_CUDA_TRY(cudaEventCreate(&e0));
     OMM_CUDA_TRY(cudaEventCreate(&e1));
+    OMM_CUDA_TRY(cudaEventCreate(&g0));
+    OMM_CUDA_TRY(cudaEventCreate(&g1));
+    b->prof.reset();
     OMM_CUDA_TRY(cudaEventRecord(e0, b->st));
     for (int i = 0; i < cnt; ++i) {
       omm_ctx* c = b->ctx[i];
@@ -444,14 +479,45 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
       }
       begin_round(b, i, h.gmax, 0);
     }
-    const int check = b->ctx[0]->opts.check_every;
+    // profiling reads the GEMM events after every replay
+    const int check = profile ? 1 : b->ctx[0]->opts.check_every;
     for (int poll = 0;; ++poll) {
-      int active = 0;
-      for (int i = 0; i < cnt; ++i) active += !finished[i];
-      if (active == 0) break;
-      for (int k = 0; k < check; ++k) OMM_CUDA_TRY(cudaGraphLaunch(b->exec, b->st));
+      int unfinished = 0;
+      for (int i = 0; i < cnt; ++i) {
+        unfinished += !finished[i];
+        const Scalars& h = b->sc_host_all[i];
+        active[i] = !finished[i] && !(h.done || h.halt || h.status);
+        iter_before[i] = h.iter;
+      }
+      if (unfinished == 0) break;
+      OMM_CUDA_TRY(cudaEventRecord(g0, b->st));
+      for (int k = 0; k < check; ++k) {
+        if (profile) {
+          b->prof.on = true;
+          enqueue_line_search(b);  // the captured launches, issued eagerly and timed
+          b->prof.on = false;
+        } else {
+          OMM_CUDA_TRY(cudaGraphLaunch(b->exec, b->st));
+        }
+      }
+      OMM_CUDA_TRY(cudaEventRecord(g1, b->st));
       OMM_CUDA_TRY(cudaMemcpyAsync(b->sc_host_all, b->sc_all, cnt * sizeof(Scalars), cudaMemcpyDeviceToHost, b->st));
       OMM_CUDA_TRY(cudaStreamSynchronize(b->st));
+      ms_graph += elapsed(g0, g1);
+      if (profile) {
+        b->prof.collect();
+        // an instance that completed its line search ran all four products; one that
+        // stopped at the convergence test after the preconditioner ran only the first
+        for (int i = 0; i < cnt; ++i) {
+          if (!active[i]) continue;
+          const bool full = b->sc_host_all[i].iter > iter_before[i];
+          for (int w = 0; w < (full ? kGroupedGemms : 1); ++w) gemm_flop += b->gemm_flop[w][i];
+        }
+      }
+      // pass 1: instances that stopped get their refresh (float64-class) or certificate
+      // (float64-class, or native float64 on request) enqueued, spread over the pool
+      // streams so that the small instances' products overlap on the GPU
+      std::vector<int> todo;
       for (int i = 0; i < cnt; ++i) {
         if (finished[i]) continue;
         omm_ctx* c = b->ctx[i];
@@ -469,15 +535,34 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
         }
         if (h.done && h.stop_reason == 2) energy_stop[i] = 1;
         last_done[i] = h.done != 0;
-        // refresh: float64-class while the device asks for it, native float64 to certify
-        cudaEvent_t r0 = c->ev[0], r1 = c->ev[1];
-        OMM_CUDA_TRY(cudaEventRecord(r0, b->st));
+        const bool native = last_done[i] && c->opts.native_certificate != 0;
+        cudaStream_t q = b->pool[todo.size() % kRefreshStreams];
+        c->st = q;
+        OMM_CUDA_TRY(cudaEventRecord(c->ev[0], q));
+        if (native) recompute_state_fp64(c);
+        else emu_recompute_state(c->emu, q, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
+        OMM_CUDA_TRY(cudaEventRecord(c->ev[1], q));
+        c->st = b->st;
+        todo.push_back(i);
+      }
+      if (todo.empty()) continue;
+      for (cudaStream_t q : b->pool) OMM_CUDA_TRY(cudaStreamSynchronize(q));
+      OMM_CUDA_TRY(cudaMemcpyAsync(b->sc_host_all, b->sc_all, cnt * sizeof(Scalars), cudaMemcpyDeviceToHost, b->st));
+      OMM_CUDA_TRY(cudaStreamSynchronize(b->st));
+      // pass 2: read the recomputed states and start the next rounds
+      for (int i : todo) {
+        omm_ctx* c = b->ctx[i];
+        Scalars& h = *c->sc_host;
         const bool certify = last_done[i] != 0;
-        if (certify) recompute_state_fp64(c);
-        else emu_recompute_state(c->emu, b->st, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
-        OMM_CUDA_TRY(cudaEventRecord(r1, b->st));
-        read_scalars(c);
-        ms_ref[i] += elapsed(r0, r1);
+        const bool native = certify && c->opts.native_certificate != 0;
+        if (!native && emu_error(c->emu, b->st) != 0) {
+          result[i] = OMM_ERR_TIMEOUT;
+          finished[i] = 1;
+          h.done = 1;
+          write_scalars(c);
+          continue;
+        }
+        (certify ? ms_cert : ms_ref)[i] += elapsed(c->ev[0], c->ev[1]);
         ++rounds[i];
         if (!std::isfinite(h.gmax) || !std::isfinite(h.E)) {
           result[i] = OMM_ERR_NONFINITE;
@@ -505,8 +590,7 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
     int gerr = 0;
     OMM_CUDA_TRY(cudaMemcpy(&gerr, b->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (gerr != 0) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
+      for (cudaEvent_t ev : {e0, e1, g0, g1}) cudaEventDestroy(ev);
       return fail(OMM_ERR_TIMEOUT, "omm_solve_batched: a bounded device wait expired in a grouped GEMM");
     }
     for (int i = 0; i < cnt; ++i) {
@@ -524,20 +608,27 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
         inf.Etilde = h.E;
         inf.gmax = h.gmax;
         inf.ms_setup = c->ms_setup;
-        inf.ms_refine = ms_ref[i];
-        inf.ms_iterate = ms_total;  // the whole batched solve (shared by all instances)
+        inf.ms_precond = c->ms_precond;
+        inf.ms_refine = ms_ref[i] + ms_cert[i];
+        inf.ms_certify = ms_cert[i];
+        // batch totals, shared by all instances: the replayed line searches and, with
+        // opts.profile, the grouped tensor-core GEMMs inside them
+        inf.ms_iterate = ms_graph;
+        inf.ms_batch = ms_total;
+        inf.ms_main_gemm = b->prof.ms;
+        inf.main_gemm_launches = (double)b->prof.launches;
+        inf.main_gemm_flop = gemm_flop;
         info[i] = inf;
       }
       if (result[i] != OMM_OK && worst == OMM_OK) worst = result[i];
     }
     OMM_CUDA_TRY(cudaStreamSynchronize(b->st));
   } catch (const CudaError& e) {
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
+    for (cudaEvent_t ev : {e0, e1, g0, g1})
+      if (ev) cudaEventDestroy(ev);
     return fail(OMM_ERR_CUDA, std::string("omm_solve_batched: ") + e.what + ": " + cudaGetErrorString(e.err));
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (cudaEvent_t ev : {e0, e1, g0, g1}) cudaEventDestroy(ev);
   if (worst != OMM_OK) return fail(worst, "omm_solve_batched: at least one instance failed");
   return OMM_OK;
 }

@@ -30,7 +30,13 @@ constexpr int kSliceBits = 5;
 
 __device__ __forceinline__ bool stopped(const Scalars* sc) { return sc != nullptr && (sc->done | sc->halt); }
 
-// one warp per row
+// One warp per row. The row scale sigma = 2^esig comes from the largest
+// magnitude (compared as integer bit patterns). Each element becomes the
+// integer N = rint(x 2^(5s - esig)) (|N| < 2^(5s-1); one float64 multiply by
+// a power of two and one conversion), whose balanced base-32 digits
+// a_{s-1}, ..., a_0 in [-16, 16] are peeled off on the integer pipe:
+// x = sigma sum_i a_i 2^-5(i+1) + r, |r| <= sigma 2^-(5s+1). Slice i holds
+// a_i 2^(esig - 5(i+1)), exact in bf16 (at most 5 significant bits).
 __global__ void slice_rows_kernel(const double* __restrict__ src, long rows, long cols, long ld_src, int s,
                                   __nv_bfloat16* __restrict__ dst, long ld_dst, long slice_stride,
                                   const Scalars* sc) {
@@ -39,21 +45,27 @@ __global__ void slice_rows_kernel(const double* __restrict__ src, long rows, lon
   const int lane = threadIdx.x & 31;
   if (row >= rows) return;
   const double* x = src + row * ld_src;
-  double mx = 0.0;
-  for (long c = lane; c < cols; c += 32) mx = fmax(mx, fabs(x[c]));
+  unsigned long long mx = 0;  // |x| as bits: ordered like the magnitudes (finite values)
+  for (long c = lane; c < cols; c += 32)
+    mx = max(mx, (unsigned long long)__double_as_longlong(x[c]) & 0x7FFFFFFFFFFFFFFFull);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);  // mx < 2^e
-  const int esig = e + 1;        // sigma = 2^(e+1) > 2 max|x|
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int e = 0;  // max|x| < 2^e (frexp convention; 0 for an all-zero row)
+  const int ebits = (int)(mx >> 52);
+  if (ebits > 0) e = ebits - 1022;
+  else if (mx != 0) frexp(__longlong_as_double((long long)mx), &e);  // subnormal maximum
+  const int esig = e + 1;  // sigma = 2^esig > 2 max|x|
   __nv_bfloat16* out = dst + row * ld_dst;
+  const double to_int = ldexp(1.0, kSliceBits * s - esig);
   for (long c = lane; c < cols; c += 32) {
-    double r = ldexp(x[c], -esig);  // |r| < 1/2, exact
-    for (int i = 0; i < s; ++i) {
-      const double t = r * 32.0;
-      const double a = rint(t);
-      r = t - a;
-      out[i * slice_stride + c] = __double2bfloat16(ldexp(a, esig - kSliceBits * (i + 1)));
+    long long N = __double2ll_rn(x[c] * to_int);  // |x| 2^-esig < 1/2, so |N| < 2^(5s-1)
+    for (int i = s - 1; i >= 0; --i) {
+      long long a = N;
+      if (i > 0) {
+        a = ((N + 16) & 31) - 16;  // balanced digit in [-16, 15]
+        N = (N - a) >> kSliceBits;
+      }
+      out[i * slice_stride + c] = __float2bfloat16_rn(ldexpf((float)a, esig - kSliceBits * (i + 1)));
     }
   }
 }
@@ -107,27 +119,31 @@ void transpose(cudaStream_t st, const double* src, long rows, long cols, long ld
   OMM_LAUNCH_CHECK();
 }
 
-void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep) {
-  // Every launch accumulates at most g slice pairs of one level, so that its
-  // FP32 sum of integer units stays below 2^24 and is exact; the float64
-  // epilogue adds the launches, smallest level first.
+tc::PairList level_chunks(int K, int s) {
+  // Every chunk holds at most g slice pairs of one level, so that its FP32 sum
+  // of integer units stays below 2^24 and is exact; the float64 epilogue adds
+  // the chunks, smallest level first.
   const long g_max = (1L << 24) / (256L * (K > 0 ? K : 1));
   const int g = (int)(g_max < 1 ? 1 : (g_max > tc::kMaxPairs ? tc::kMaxPairs : g_max));
-  tc::Epilogue e = ep;
-  bool first = true;
+  tc::PairList pl{};
   for (int d = s - 1; d >= 0; --d) {
     for (int i0 = 0; i0 <= d; i0 += g) {
-      tc::PairList pl{};
       for (int i = i0; i <= d && i < i0 + g; ++i) {
+        if (pl.n == tc::kMaxPairs) throw CudaError{cudaErrorInvalidValue, "emu: too many slice pairs"};
         pl.a[pl.n] = (unsigned char)i;
         pl.b[pl.n] = (unsigned char)(d - i);
         ++pl.n;
       }
-      e.beta = first ? ep.beta : 1.0;
-      tc::gemm(st, A, B, K, pl, e);
-      first = false;
+      if (pl.nchunk == tc::kMaxChunks) throw CudaError{cudaErrorInvalidValue, "emu: too many chunks"};
+      pl.chunk_end[pl.nchunk++] = (unsigned char)pl.n;
     }
   }
+  return pl;
+}
+
+void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep) {
+  // one persistent launch: every output tile runs its chunks in order on one CTA
+  tc::gemm_persistent(st, A, B, K, level_chunks(K, s), ep);
 }
 
 }  // namespace emu

@@ -10,6 +10,9 @@ namespace emu {
 void slice_rows(cudaStream_t st, const double* src, long rows, long cols, long ld_src, int s,
                 __nv_bfloat16* dst, long ld_dst, const Scalars* sc);
 void transpose(cudaStream_t st, const double* src, long rows, long cols, long ld_src, double* dst, long ld_dst);
+// the slice pairs (i, j), i + j < s, level by level from the smallest, in chunks whose
+// FP32 sums are exact for a contraction of length K
+tc::PairList level_chunks(int K, int s);
 // C = alpha A B^T + beta C from s-slice operands (A, B made by slice_rows)
 void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep);
 }  // namespace emu

@@ -16,9 +16,13 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// NaN-propagating (fmax would drop a NaN)
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = (w > v || w != w) ? w : v;
+  }
   return v;
 }
 template <int N>
@@ -128,7 +132,9 @@ __device__ __forceinline__ void grad_reduce_body(long count, const double* __res
   if (stopped(sc)) return;
   const bool have_dir = sc->have_dir;
   double v[3] = {0.0, 0.0, 0.0};
-  double mx = 0.0;
+  // max|G| on the bit patterns (integer pipe): for |x| they order like the
+  // values, and a NaN's pattern exceeds every number's, so the max keeps it
+  unsigned long long mb = 0;
   for (long i = bx_ * (long)TB + threadIdx.x; i < count; i += (long)nbx_ * TB) {
     const double g = G[i], pg = PG[i];
     v[0] = fma(g, pg, v[0]);
@@ -136,13 +142,13 @@ __device__ __forceinline__ void grad_reduce_body(long count, const double* __res
       v[1] = fma(Gold[i], pg, v[1]);
       v[2] = fma(g, Dir[i], v[2]);
     }
-    // NaN-propagating max: fmax would drop a NaN
-    const double a = fabs(g);
-    mx = (a > mx || a != a) ? a : mx;
+    mb = max(mb, (unsigned long long)__double_as_longlong(g) & 0x7FFFFFFFFFFFFFFFull);
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
   __shared__ double sh[3][TB / 32];
   __shared__ double shm[TB / 32];
-  const double wm = warp_max(mx);
+  const double wm = __longlong_as_double((long long)mb);
   if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = wm;
   block_sum<3>(v, sh);
   if (threadIdx.x == 0) {

@@ -114,7 +114,10 @@ void copy_in(double* dst, const double* src, size_t count, cudaStream_t st) {
 
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, a, b);
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();  // a failed timing query must not surface as a later launch error
+    ms = 0.f;
+  }
   return ms;
 }
 
@@ -319,7 +322,9 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
       } else {
         OMM_CUDA_TRY(cudaMemcpyAsync(A, c->HS + mm, mm * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
       }
+      OMM_CUDA_TRY(cudaEventRecord(c->ev[2], c->st));
       spd_inverse(c->st, m, A, c->P, work, c->info_dev);
+      OMM_CUDA_TRY(cudaEventRecord(c->ev[3], c->st));
     }
     dev_alloc(&c->C, nm);
     dev_alloc(&c->Dir, nm);
@@ -341,6 +346,7 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     OMM_CUDA_TRY(cudaMemcpyAsync(&info, c->info_dev, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     OMM_CUDA_TRY(cudaStreamSynchronize(c->st));
     c->ms_setup = elapsed(c->ev[0], c->ev[1]);
+    c->ms_precond = precond ? elapsed(c->ev[2], c->ev[3]) : 0.0;
     dev_free(A);
     dev_free(work);
     A = work = nullptr;
@@ -410,7 +416,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
       // the mixed path starts from a tensor-core state; every later state is float64
       // mixed path: a tensor-core first state, float64-class (sliced) refreshes while the
       // device asks for them, and a native float64 state once it reports convergence
-      const bool emu_certify = mixed && c->opts.emulated_certificate != 0;
+      const bool emu_certify = mixed && c->opts.native_certificate == 0;
       const bool tc_state = mixed && round == 0;
       const bool emu_state = mixed && round > 0 && (!last_round_done || emu_certify);
       OMM_CUDA_TRY(cudaEventRecord(c->ev[0], c->st));
@@ -504,6 +510,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     inf.E = h.E + 2.0 * n * c->eta;
     inf.gmax = h.gmax;
     inf.ms_setup = c->ms_setup;
+    inf.ms_precond = c->ms_precond;
     inf.ms_iterate = ms_iter;
     inf.ms_refine = ms_ref;
     inf.ms_certify = ms_cert;
@@ -520,7 +527,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
           ensure_mm(c);
           tgt = c->mm;
         }
-        if (c->emu && c->opts.emulated_certificate) emu_density(c->emu, c->st, c->C, c->SWHW, tgt);
+        if (c->emu && !c->opts.native_certificate) emu_density(c->emu, c->st, c->C, c->SWHW, tgt);
         else density_into(c, tgt);
         if (tgt != D)
           OMM_CUDA_TRY(cudaMemcpyAsync(D, tgt, (size_t)m * m * sizeof(double), cudaMemcpyDefault, c->st));
@@ -561,7 +568,7 @@ omm_status omm_backward(omm_ctx* c, double* dEdH, double* dEdS) {
     if (dEdH && !is_device_ptr(dEdH)) { ensure_mm(c); tH = c->mm; }
     if (dEdH) {
       // the same density matrix omm_solve returns
-      if (c->emu && c->opts.emulated_certificate) emu_density(c->emu, c->st, c->C, c->SWHW, tH);
+      if (c->emu && !c->opts.native_certificate) emu_density(c->emu, c->st, c->C, c->SWHW, tH);
       else density_into(c, tH);
       if (tH != dEdH) OMM_CUDA_TRY(cudaMemcpyAsync(dEdH, tH, bytes, cudaMemcpyDefault, c->st));
     }

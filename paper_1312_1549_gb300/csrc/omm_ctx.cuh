@@ -34,6 +34,7 @@ struct omm_ctx {
   int* info_dev = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   double ms_setup = 0.0;
+  double ms_precond = 0.0;  // the Cholesky inverse inside ms_setup
   omm::MixedState* mixed = nullptr;
   omm::EmuState* emu = nullptr;  // float64-class tensor-core refresh of the mixed path
   omm::Profiler prof;  // main contraction kernel of the iteration (tensor-core or float64 GEMM)

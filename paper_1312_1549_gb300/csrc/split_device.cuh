@@ -7,10 +7,50 @@
 namespace omm {
 namespace dev {
 
+// float64 -> bf16 with round-to-nearest-even, on the integer pipe. The float64
+// units of this GPU retire about two instructions per SM and clock, so format
+// conversions are done on the bits: for a result in the normal bf16 range the
+// 52-bit mantissa is rounded to 7 bits (ties to even; a carry moves into the
+// exponent, which also gives the overflow to infinity) and the exponent is
+// rebiased from 1023 to 127. Zeros keep their sign; everything else (bf16
+// subnormals, infinities, NaN) takes the library conversion.
+__device__ __forceinline__ unsigned short bf16_bits_rne(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long mag = u & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned int sign = (unsigned int)(u >> 48) & 0x8000u;
+  if (mag == 0) return (unsigned short)sign;
+  const unsigned int e = (unsigned int)(mag >> 52);
+  if (e < 1023u - 126u || e > 1023u + 127u) return __bfloat16_as_ushort(__double2bfloat16(x));
+  const unsigned long long r = mag + 0x00000FFFFFFFFFFFull + ((mag >> 45) & 1ull);  // 2^44 - 1 + lsb
+  const unsigned int em = (unsigned int)(r >> 45) - ((1023u - 127u) << 7);
+  return (unsigned short)(sign | em);
+}
+
+// the float64 value of a finite bf16 (exact; integer pipe)
+__device__ __forceinline__ double bf16_bits_to_double(unsigned short b) {
+  const unsigned long long sign = (unsigned long long)(b & 0x8000u) << 48;
+  const unsigned int e = (b >> 7) & 0xFFu;
+  if (e == 0) {
+    if ((b & 0x7Fu) == 0) return __longlong_as_double((long long)sign);  // signed zero
+    return (double)__bfloat162float(__ushort_as_bfloat16(b));             // subnormal
+  }
+  const unsigned long long bits = sign | ((unsigned long long)(e - 127u + 1023u) << 52) |
+                                  ((unsigned long long)(b & 0x7Fu) << 45);
+  return __longlong_as_double((long long)bits);
+}
+
+// hi = bf16(x), lo = bf16(x - hi), both rounded to nearest even; one float64 add
 __device__ __forceinline__ void split_store(double x, __nv_bfloat16* hi, __nv_bfloat16* lo, long off) {
-  const __nv_bfloat16 h = __double2bfloat16(x);
-  hi[off] = h;
-  if (lo) lo[off] = __double2bfloat16(x - (double)__bfloat162float(h));
+  const unsigned short h = bf16_bits_rne(x);
+  hi[off] = __ushort_as_bfloat16(h);
+  if (lo) {
+    const unsigned int he = (h >> 7) & 0xFFu;
+    // x - hi is exact in float64; an infinite or NaN hi keeps the library path
+    const unsigned short l = (he == 0xFFu) ? __bfloat16_as_ushort(__double2bfloat16(x - (double)__bfloat162float(
+                                                 __ushort_as_bfloat16(h))))
+                                           : bf16_bits_rne(x - bf16_bits_to_double(h));
+    lo[off] = __ushort_as_bfloat16(l);
+  }
 }
 
 // rows handled by blocks bx, bx + nbx, ...; the block's threads stride over columns

@@ -136,6 +136,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// float -> float64 on the integer pipe (exact): the float64 units of this GPU
+// retire about two instructions per SM and clock, so the epilogue widens the
+// FP32 accumulator by rebiasing the exponent (127 -> 1023) and shifting the
+// mantissa; zeros keep their sign, subnormals/infinities/NaN take the
+// hardware conversion.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if ((u & 0x7FFFFFFFu) == 0) return __longlong_as_double((long long)sign);
+  if (e == 0 || e == 0xFFu) return (double)f;
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e + (1023u - 127u)) << 52) |
+                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
 // C = alpha * v + beta * C for the 32 accumulator columns [col0, col0 + 32) of one row.
 __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col0, const float (&v)[32]) {
   if (row >= ep.M || col0 >= ep.N) return;
@@ -145,13 +160,23 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
   if (blk0 == blk1) {
     double* base = ep.C + blk0 * ep.split_stride + (long)row * ep.ldc + (col0 - blk0 * ep.split_cols);
     if (ep.beta == 0.0) {
+      if (ep.alpha == 1.0) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < nvalid) base[j] = widen(v[j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < nvalid) base[j] = ep.alpha * widen(v[j]);
+      }
+    } else if (ep.beta == 1.0) {
 #pragma unroll
       for (int j = 0; j < 32; ++j)
-        if (j < nvalid) base[j] = ep.alpha * (double)v[j];
+        if (j < nvalid) base[j] = fma(ep.alpha, widen(v[j]), base[j]);
     } else {
 #pragma unroll
       for (int j = 0; j < 32; ++j)
-        if (j < nvalid) base[j] = fma(ep.beta, base[j], ep.alpha * (double)v[j]);
+        if (j < nvalid) base[j] = fma(ep.beta, base[j], ep.alpha * widen(v[j]));
     }
     return;
   }
@@ -161,7 +186,7 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
     const int col = col0 + j;
     const long blk = col / ep.split_cols;
     double* p = ep.C + blk * ep.split_stride + (long)row * ep.ldc + (col - blk * ep.split_cols);
-    const double a = ep.alpha * (double)v[j];
+    const double a = ep.alpha * widen(v[j]);
     *p = (ep.beta == 0.0) ? a : fma(ep.beta, *p, a);
   }
 }
@@ -338,10 +363,12 @@ __device__ __forceinline__ int find_group(const GroupDesc* __restrict__ groups, 
 // b, b + gridDim.x, ... of all groups. The accumulator is double-buffered in
 // TMEM (2 x 256 columns) so the epilogue of one tile overlaps the main loop
 // of the next; the producer's stage ring continues across tiles.
+// With a chunked pair list (emulation levels) every chunk of a tile is one
+// accumulator round: the MMA thread fills a TMEM buffer with the chunk's pairs,
+// the epilogue adds it to C, and the chunks of a tile stay on one CTA, in order.
 template <bool FUSED>
-__global__ void __launch_bounds__(NTHREADS, 1)
-gemm_persistent_kernel(const GroupDesc* __restrict__ groups, int ngroups, int total_tiles,
-                       const __grid_constant__ PairList pl, int* err) {
+__device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ groups, int ngroups, int total_tiles,
+                                                const PairList& pl, int* err) {
   constexpr int NS = FUSED ? 2 : STAGES;
   constexpr int SB = FUSED ? 2 * STAGE_BYTES : STAGE_BYTES;
   constexpr int ACC_COLS = 256;
@@ -352,6 +379,9 @@ gemm_persistent_kernel(const GroupDesc* __restrict__ groups, int ngroups, int to
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 4);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunk = (FUSED || pl.nchunk <= 0) ? 1 : pl.nchunk;
+  auto chunk_begin = [&](int c) { return (c == 0 || pl.nchunk <= 0) ? 0 : (int)pl.chunk_end[c - 1]; };
+  auto chunk_end = [&](int c) { return pl.nchunk <= 0 ? pl.n : (int)pl.chunk_end[c]; };
 
   if (threadIdx.x == 0) {
     for (int q = 0; q < NS; ++q) {
@@ -421,74 +451,81 @@ gemm_persistent_kernel(const GroupDesc* __restrict__ groups, int ngroups, int to
       const GroupDesc* g = groups + find_group(groups, ngroups, tile);
       const int* skip = g->ep.skip;
       if (skip != nullptr && (skip[0] | skip[1])) continue;
-      const uint32_t buf = lt & 1, use = lt >> 1;
-      if (!mbar_wait(smem_u32(&bars[2 * NS + 2 + buf]), (use & 1) ^ 1)) {
-        *abort_flag = 1;
-        atomicCAS(err, 0, 4);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t d = tmem + buf * ACC_COLS;
       const int nkb = (g->K + BK - 1) / BK;
-      const int total = FUSED ? nkb : pl.n * nkb;
-      for (int t = 0; t < total; ++t, ++it) {
-        const int q = it % NS;
-        const uint32_t r = it / NS;
-        if (!mbar_wait(smem_u32(&bars[q]), r & 1)) {
+      for (int c = 0; c < nchunk && !*abort_flag; ++c) {
+        const uint32_t buf = lt & 1, use = lt >> 1;
+        if (!mbar_wait(smem_u32(&bars[2 * NS + 2 + buf]), (use & 1) ^ 1)) {
           *abort_flag = 1;
-          atomicCAS(err, 0, 2);
+          atomicCAS(err, 0, 4);
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sa = smem_u32(smem + q * SB);
-        if (FUSED) {
-          const uint32_t alo = sa + A_BYTES, bhi = sa + 2 * A_BYTES, blo = bhi + B_BYTES;
-#pragma unroll
-          for (int k = 0; k < BK / 16; ++k) {
-            umma_bf16(d, smem_desc(sa + k * 32), smem_desc(bhi + k * 32), idesc, (t > 0 || k > 0) ? 1u : 0u);
-            umma_bf16(d, smem_desc(sa + k * 32), smem_desc(blo + k * 32), idesc, 1u);
-            umma_bf16(d, smem_desc(alo + k * 32), smem_desc(bhi + k * 32), idesc, 1u);
+        const uint32_t d = tmem + buf * ACC_COLS;
+        const int total = FUSED ? nkb : (chunk_end(c) - chunk_begin(c)) * nkb;
+        for (int t = 0; t < total; ++t, ++it) {
+          const int q = it % NS;
+          const uint32_t r = it / NS;
+          if (!mbar_wait(smem_u32(&bars[q]), r & 1)) {
+            *abort_flag = 1;
+            atomicCAS(err, 0, 2);
+            break;
           }
-        } else {
-          const uint32_t sb = sa + A_BYTES;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(smem + q * SB);
+          if (FUSED) {
+            const uint32_t alo = sa + A_BYTES, bhi = sa + 2 * A_BYTES, blo = bhi + B_BYTES;
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k)
-            umma_bf16(d, smem_desc(sa + k * 32), smem_desc(sb + k * 32), idesc, (t > 0 || k > 0) ? 1u : 0u);
+            for (int k = 0; k < BK / 16; ++k) {
+              umma_bf16(d, smem_desc(sa + k * 32), smem_desc(bhi + k * 32), idesc, (t > 0 || k > 0) ? 1u : 0u);
+              umma_bf16(d, smem_desc(sa + k * 32), smem_desc(blo + k * 32), idesc, 1u);
+              umma_bf16(d, smem_desc(alo + k * 32), smem_desc(bhi + k * 32), idesc, 1u);
+            }
+          } else {
+            const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k)
+              umma_bf16(d, smem_desc(sa + k * 32), smem_desc(sb + k * 32), idesc, (t > 0 || k > 0) ? 1u : 0u);
+          }
+          umma_commit(smem_u32(&bars[NS + q]));
         }
-        umma_commit(smem_u32(&bars[NS + q]));
+        umma_commit(smem_u32(&bars[2 * NS + buf]));  // this chunk's accumulator is complete
+        ++lt;
       }
-      umma_commit(smem_u32(&bars[2 * NS + buf]));  // this tile's accumulator is complete
-      ++lt;
     }
   } else if (warp >= 2) {
     // ---------------- epilogue
     const int lane_base = (warp & 3) * 32;
     uint32_t lt = 0;
-    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+    bool failed = false;
+    for (int tile = blockIdx.x; tile < total_tiles && !failed; tile += gridDim.x) {
       const GroupDesc* g = groups + find_group(groups, ngroups, tile);
       const int* skip = g->ep.skip;
       if (skip != nullptr && (skip[0] | skip[1])) continue;
-      const uint32_t buf = lt & 1, use = lt >> 1;
-      const bool ok = !*abort_flag && mbar_wait(smem_u32(&bars[2 * NS + buf]), use & 1);
-      if (!ok) {
-        atomicCAS(err, 0, 3);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const Epilogue ep = g->ep;
-      const int local = tile - g->tile_begin, tiles_m = (ep.M + BM - 1) / BM;
-      const int m0 = (local % tiles_m) * BM, n0 = (local / tiles_m) * BN;
-      const int row = m0 + lane_base + lane;
+      for (int c = 0; c < nchunk; ++c) {
+        const uint32_t buf = lt & 1, use = lt >> 1;
+        const bool ok = !*abort_flag && mbar_wait(smem_u32(&bars[2 * NS + buf]), use & 1);
+        if (!ok) {
+          atomicCAS(err, 0, 3);
+          failed = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        Epilogue ep = g->ep;
+        if (c > 0) ep.beta = 1.0;
+        const int local = tile - g->tile_begin, tiles_m = (ep.M + BM - 1) / BM;
+        const int m0 = (local % tiles_m) * BM, n0 = (local / tiles_m) * BN;
+        const int row = m0 + lane_base + lane;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
-        float v[32];
-        tmem_ld32(tmem + buf * ACC_COLS + ((uint32_t)lane_base << 16) + (uint32_t)(c * 32), v);
-        store_chunk(ep, row, n0 + c * 32, v);
+        for (int j = 0; j < BN / 32; ++j) {
+          float v[32];
+          tmem_ld32(tmem + buf * ACC_COLS + ((uint32_t)lane_base << 16) + (uint32_t)(j * 32), v);
+          store_chunk(ep, row, n0 + j * 32, v);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars[2 * NS + 2 + buf]));
+        ++lt;
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bars[2 * NS + 2 + buf]));
-      ++lt;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -498,6 +535,21 @@ gemm_persistent_kernel(const GroupDesc* __restrict__ groups, int ngroups, int to
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC_COLS) : "memory");
   }
+}
+
+template <bool FUSED>
+__global__ void __launch_bounds__(NTHREADS, 1)
+gemm_persistent_kernel(const GroupDesc* __restrict__ groups, int ngroups, int total_tiles,
+                       const __grid_constant__ PairList pl, int* err) {
+  persistent_body<FUSED>(groups, ngroups, total_tiles, pl, err);
+}
+
+// one GEMM, its descriptor (tensor maps included) in the kernel's parameter space
+template <bool FUSED>
+__global__ void __launch_bounds__(NTHREADS, 1)
+gemm_persistent_one_kernel(const __grid_constant__ GroupDesc g, int total_tiles, const __grid_constant__ PairList pl,
+                           int* err) {
+  persistent_body<FUSED>(&g, 1, total_tiles, pl, err);
 }
 
 int sm_count() {
@@ -571,8 +623,20 @@ PairList pairs_single() {
   return p;
 }
 
+void check_pairs(const PairList& pl, int slices_a, int slices_b) {
+  if (pl.n <= 0 || pl.n > kMaxPairs || pl.nchunk < 0 || pl.nchunk > kMaxChunks)
+    throw CudaError{cudaErrorInvalidValue, "tc: pair list"};
+  for (int p = 0; p < pl.n; ++p)
+    if (pl.a[p] >= slices_a || pl.b[p] >= slices_b) throw CudaError{cudaErrorInvalidValue, "tc: slice index"};
+  for (int c = 0; c < pl.nchunk; ++c) {
+    const int lo = c ? pl.chunk_end[c - 1] : 0;
+    if (pl.chunk_end[c] <= lo || pl.chunk_end[c] > pl.n) throw CudaError{cudaErrorInvalidValue, "tc: chunk list"};
+  }
+  if (pl.nchunk > 0 && pl.chunk_end[pl.nchunk - 1] != pl.n) throw CudaError{cudaErrorInvalidValue, "tc: chunk list"};
+}
+
 bool is_split3(const PairList& pl) {
-  return pl.n == 3 && pl.a[0] == 0 && pl.b[0] == 0 && pl.a[1] == 0 && pl.b[1] == 1 && pl.a[2] == 1 && pl.b[2] == 0;
+  return pl.n == 3 && pl.nchunk <= 1 && pl.a[0] == 0 && pl.b[0] == 0 && pl.a[1] == 0 && pl.b[1] == 1 && pl.a[2] == 1 && pl.b[2] == 0;
 }
 
 void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const PairList& pl, const Epilogue& ep) {
@@ -584,9 +648,8 @@ void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const Pair
                                       SMEM_BYTES));
     attr_set = true;
   }
-  if (pl.n <= 0 || pl.n > kMaxPairs) throw CudaError{cudaErrorInvalidValue, "tc::gemm: pair list"};
-  for (int p = 0; p < pl.n; ++p)
-    if (pl.a[p] >= A.slices || pl.b[p] >= B.slices) throw CudaError{cudaErrorInvalidValue, "tc::gemm: slice index"};
+  check_pairs(pl, A.slices, B.slices);
+  if (pl.nchunk > 1) throw CudaError{cudaErrorInvalidValue, "tc::gemm: chunked pair lists need the persistent launch"};
   dim3 grid((unsigned)(((ep.N + BN - 1) / BN) * ((ep.M + BM - 1) / BM)));
   const CUtensorMap* a = reinterpret_cast<const CUtensorMap*>(&A.map);
   const CUtensorMap* b = reinterpret_cast<const CUtensorMap*>(&B.map);
@@ -630,6 +693,10 @@ void prepare_persistent() {
                                       SMEM_BYTES));
     OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       SMEM_BYTES));
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_one_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      SMEM_BYTES));
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_one_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      SMEM_BYTES));
     sm_count();
     attr_set = true;
   }
@@ -638,12 +705,28 @@ void prepare_persistent() {
 void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl,
                      int* err) {
   prepare_persistent();
+  check_pairs(pl, kMaxPairs, kMaxPairs);  // slice counts are checked where the groups are made
   if (ngroups <= 0 || total_tiles <= 0) return;
   const unsigned grid = (unsigned)std::min(total_tiles, sm_count());
   if (is_split3(pl))
     gemm_persistent_kernel<true><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, pl, err);
   else
     gemm_persistent_kernel<false><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, pl, err);
+  OMM_LAUNCH_CHECK();
+}
+
+void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K, const PairList& pl,
+                     const Epilogue& ep) {
+  prepare_persistent();
+  check_pairs(pl, A.slices, B.slices);
+  const int tiles = tiles_of(ep);
+  if (tiles <= 0 || K <= 0) return;
+  const GroupDesc g = make_group(A, B, K, ep, 0);
+  const unsigned grid = (unsigned)std::min(tiles, sm_count());
+  if (is_split3(pl) && pl.nchunk <= 1 && A.slices >= 2 && B.slices >= 2)
+    gemm_persistent_one_kernel<true><<<grid, NTHREADS, SMEM_BYTES, st>>>(g, tiles, pl, ep.err);
+  else
+    gemm_persistent_one_kernel<false><<<grid, NTHREADS, SMEM_BYTES, st>>>(g, tiles, pl, ep.err);
   OMM_LAUNCH_CHECK();
 }
 

@@ -21,12 +21,20 @@ struct Operand {
   int slices = 1;
 };
 
-// Which slice products one GEMM accumulates into its FP32 accumulator.
+// Which slice products one GEMM accumulates. With nchunk > 0 the pairs are cut
+// into consecutive chunks: chunk c holds pairs [chunk_end[c-1], chunk_end[c]),
+// is summed in an FP32 accumulator of its own and added to the float64 output
+// by its own epilogue pass, in chunk order (the first pass with the Epilogue's
+// beta, the later ones with beta = 1). nchunk = 0: all pairs form one chunk.
+// Chunks are honoured by the persistent launch only.
 constexpr int kMaxPairs = 64;
+constexpr int kMaxChunks = 32;
 struct PairList {
   int n;
   unsigned char a[kMaxPairs];
   unsigned char b[kMaxPairs];
+  int nchunk;
+  unsigned char chunk_end[kMaxChunks];
 };
 PairList pairs_split3();   // A_hi B_hi + A_hi B_lo + A_lo B_hi
 PairList pairs_single();   // A_0 B_0
@@ -76,6 +84,9 @@ void prepare_persistent();
 // nonzero code if a bounded wait expired
 void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl,
                      int* err);
+// the same persistent kernel for one GEMM whose descriptor travels as a kernel parameter
+void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K, const PairList& pl,
+                     const Epilogue& ep);
 void gemm_grouped(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl);
 
 // x (float64, rows x cols, ld_src) -> hi = bf16(x), lo = bf16(x - hi) (ld_dst);

@@ -45,7 +45,7 @@ class OMMSolver:
 
     def __init__(self, H, S, T, n, eta, tau, precision="fp64", stream=None, max_iter=0,
                  tol_grad=1e-9, e_tol=0.0, refine_ratio=0.0, precondition=True, check_every=0,
-                 profile=False, emulated_certificate=False):
+                 profile=False, native_certificate=False):
         lib = N.lib()
         m = int(H.shape[0])
         self.m, self.n, self.eta, self.tau = m, int(n), float(eta), float(tau)
@@ -55,7 +55,7 @@ class OMMSolver:
                          check_every=int(check_every), tol_grad=float(tol_grad),
                          e_tol=float(e_tol), refine_ratio=float(refine_ratio),
                          profile=1 if profile else 0,
-                         emulated_certificate=1 if emulated_certificate else 0)
+                         native_certificate=1 if native_certificate else 0)
         self._keep = (H, S, T)
         h = ct.c_void_p()
         tau_arg = math.inf if tau is None else float(tau)
@@ -187,7 +187,8 @@ class OMMBatch:
     """
 
     def __init__(self, problems, precision="mixed", stream=None, max_iter=0, tol_grad=1e-9,
-                 refine_ratio=0.0, precondition=True, check_every=0):
+                 refine_ratio=0.0, precondition=True, check_every=0, profile=False,
+                 native_certificate=False):
         lib = N.lib()
         cnt = len(problems)
         self.count = cnt
@@ -195,7 +196,8 @@ class OMMBatch:
         opts = N.OmmOpts(precision=N.PREC_MIXED if precision == "mixed" else N.PREC_FP64,
                          max_iter=int(max_iter), no_precondition=0 if precondition else 1,
                          check_every=int(check_every), tol_grad=float(tol_grad), e_tol=0.0,
-                         refine_ratio=float(refine_ratio), profile=0)
+                         refine_ratio=float(refine_ratio), profile=1 if profile else 0,
+                         native_certificate=1 if native_certificate else 0)
         P = ct.c_void_p * cnt
         ms = (ct.c_int * cnt)(*[s[0] for s in self.shapes])
         ns = (ct.c_int * cnt)(*[s[1] for s in self.shapes])

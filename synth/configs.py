@@ -97,17 +97,17 @@ def silicon(k=(2, 2, 2), basis="SZ", seed=0, name=None, need_eta=True, eta=None)
     return _finish(name or key, key, H, S, T, n, seed, streams, meta, need_eta, eta)
 
 
-def water(nmol=256, seed=0, name=None, need_eta=True, eta=None) -> Problem:
+def water(nmol=256, seed=0, name=None, need_eta=True, eta=None, basis="DZP") -> Problem:
     """Liquid-water box of nmol molecules at 1 g/cm^3; n = 4 per molecule."""
     streams = _streams(seed)
-    model = water_model()
+    model = water_model(basis)
     symbols, pos, cell = water_box(nmol, streams[0])
     m = sum(model.species[s].norb for s in symbols)
     jitter = streams[1].normal(0.0, JITTER_SIGMA, size=m)
     S, T, H, _ = build_matrices(model, symbols, pos, cell, jitter)
     n = 4 * nmol
-    key = f"water_{nmol}"
-    meta = {"system": "water", "molecules": nmol, "cell": cell.tolist()}
+    key = f"water_{nmol}" if basis == "DZP" else f"water_{basis}_{nmol}"
+    meta = {"system": "water", "basis": basis, "molecules": nmol, "cell": cell.tolist()}
     return _finish(name or key, key, H, S, T, n, seed, streams, meta, need_eta, eta)
 
 
@@ -136,21 +136,41 @@ def config3(seed=0) -> Problem:
     return _gap_guarded(water, seed, nmol=256, name="water256_dzp")
 
 
-SI_CELL_SHAPES = {5: (1, 1, 5), 6: (1, 2, 3), 8: (2, 2, 2), 9: (1, 3, 3), 10: (1, 2, 5),
+SI_CELL_SHAPES = {4: (1, 2, 2), 5: (1, 1, 5), 6: (1, 2, 3), 8: (2, 2, 2), 9: (1, 3, 3), 10: (1, 2, 5),
                   12: (2, 2, 3), 16: (2, 2, 4), 18: (2, 3, 3), 20: (2, 2, 5), 24: (2, 3, 4),
-                  27: (3, 3, 3), 30: (2, 3, 5), 32: (2, 4, 4), 36: (3, 3, 4)}
+                  27: (3, 3, 3), 30: (2, 3, 5), 32: (2, 4, 4), 36: (3, 3, 4), 40: (2, 4, 5),
+                  45: (3, 3, 5), 48: (3, 4, 4), 50: (2, 5, 5), 60: (3, 4, 5), 64: (4, 4, 4)}
+
+# occupied fraction n/m of each basis (n = 2 per Si atom, 4 per water molecule)
+SI_BASIS_FRACTION = {"DZ": 2 / 8, "TZ": 2 / 12, "DZP": 2 / 13, "DZP+p": 2 / 16}
+WATER_BASIS_FRACTION = {"DZ+d": 4 / 17, "DZP": 4 / 23, "TZP": 4 / 29}
+
+
+def config4_recipe(i: int):
+    """(builder, kwargs) of instance i of the uneven batch.
+
+    m ~ U[512, 4096] and a target occupied fraction ~ U[0.12, 0.25]; the basis is the one
+    whose fraction is nearest the target, the cell the one whose m is nearest. Si for even
+    i, water for odd i.
+    """
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([4, i])))
+    target = rng.uniform(512, 4096)
+    frac = rng.uniform(0.12, 0.25)
+    if i % 2 == 0:
+        basis = min(SI_BASIS_FRACTION, key=lambda b: abs(SI_BASIS_FRACTION[b] - frac))
+        per_cell = 8 * 2 / SI_BASIS_FRACTION[basis]   # orbitals per 8-atom cubic cell
+        ncell = min(SI_CELL_SHAPES, key=lambda c: abs(per_cell * c - target))
+        return silicon, dict(k=SI_CELL_SHAPES[ncell], basis=basis,
+                             name=f"batch{i:02d}_si{8 * ncell}_{basis}")
+    basis = min(WATER_BASIS_FRACTION, key=lambda b: abs(WATER_BASIS_FRACTION[b] - frac))
+    nmol = int(np.clip(round(target * WATER_BASIS_FRACTION[basis] / 4.0), 18, 241))
+    return water, dict(nmol=nmol, basis=basis, name=f"batch{i:02d}_water{nmol}_{basis}")
 
 
 def config4_instance(i: int) -> Problem:
-    """Instance i of the uneven batch: m ~ U[512, 4096], Si DZP (even i) or water (odd i)."""
-    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([4, i])))
-    target = rng.uniform(512, 4096)
-    if i % 2 == 0:
-        ncell = min(SI_CELL_SHAPES, key=lambda c: abs(104 * c - target))
-        return _gap_guarded(silicon, i, k=SI_CELL_SHAPES[ncell], basis="DZP",
-                            name=f"batch{i:02d}_si{8 * ncell}")
-    nmol = int(np.clip(round(target / 23.0), 23, 178))
-    return _gap_guarded(water, i, nmol=nmol, name=f"batch{i:02d}_water{nmol}")
+    """Instance i of the uneven batch (see config4_recipe), gap-guarded."""
+    builder, kw = config4_recipe(i)
+    return _gap_guarded(builder, i, **kw)
 
 
 def config5_base(seed=0) -> Problem:

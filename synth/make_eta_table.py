@@ -5,7 +5,9 @@ one generalised eigensolve of the generated matrices. This script does those
 solves once (scipy.linalg.eigh, host) so that building a workload later does
 not repeat them. Run from the repository root:
 
-    python -m synth.make_eta_table [--batch]
+    python -m synth.make_eta_table [--batch] [--sequence] [--fresh]
+
+--fresh starts from an empty table instead of updating the stored one.
 """
 from __future__ import annotations
 
@@ -16,7 +18,7 @@ from . import configs
 
 
 def main(argv):
-    table = configs._load_table()
+    table = {} if "--fresh" in argv else configs._load_table()
 
     def record(p):
         homo, lumo = configs.spectrum_edges(p.H, p.S, p.n)
@@ -36,18 +38,13 @@ def main(argv):
     guarded(configs.silicon, 0, k=(2, 2, 2), basis="SZ")
     guarded(configs.silicon, 0, k=(4, 4, 4), basis="DZP")
     guarded(configs.water, 0, nmol=256)
+    if "--sequence" in argv:
+        guarded(configs.silicon, 0, k=(8, 8, 8), basis="SZ")   # m = 16384: a long solve
     if "--batch" in argv:
-        import numpy as np
         for i in range(64):
-            rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([4, i])))
-            target = rng.uniform(512, 4096)
-            if i % 2 == 0:
-                ncell = min(configs.SI_CELL_SHAPES, key=lambda c: abs(104 * c - target))
-                guarded(configs.silicon, i, k=configs.SI_CELL_SHAPES[ncell], basis="DZP")
-            else:
-                nmol = int(np.clip(round(target / 23.0), 23, 178))
-                guarded(configs.water, i, nmol=nmol)
-
+            builder, kw = configs.config4_recipe(i)
+            kw.pop("name")
+            guarded(builder, i, **kw)
 
 if __name__ == "__main__":
     main(sys.argv[1:])

@@ -31,17 +31,29 @@ DIAMOND_BASIS = np.array([
 ])
 
 
+# Basis sets by orbitals per atom (n = 2 per Si atom, so the occupied fraction is 2 / norb):
+#   SZ 4 (50%), DZ 8 (25%), TZ 12 (16.7%), DZP 13 (15.4%), DZP+p 16 (12.5%).
+# Higher zetas are tighter Gaussians; only the first zeta enters the two-centre terms.
+SI_SHELLS = {
+    "s1": Shell("s1", "s", 0.35, True), "p1": Shell("p1", "p", 0.30, True),
+    "s2": Shell("s2", "s", 0.875, False), "p2": Shell("p2", "p", 0.75, False),
+    "s3": Shell("s3", "s", 2.2, False), "p3": Shell("p3", "p", 1.9, False),
+    "d": Shell("d", "d", 0.35, False),
+}
+SI_BASES = {
+    "SZ": ["s1", "p1"],
+    "DZ": ["s1", "p1", "s2", "p2"],
+    "TZ": ["s1", "p1", "s2", "p2", "s3", "p3"],
+    "DZP": ["s1", "p1", "s2", "p2", "d"],
+    "DZP+p": ["s1", "p1", "s2", "p2", "d", "p3"],
+}
+
+
 def si_species(basis: str) -> Species:
     eps = {"s": -13.55 / HARTREE_EV, "p": -6.52 / HARTREE_EV, "d": 0.15}
-    if basis == "SZ":
-        shells = [Shell("s1", "s", 0.35, True), Shell("p1", "p", 0.30, True)]
-    elif basis == "DZP":
-        shells = [Shell("s1", "s", 0.35, True), Shell("p1", "p", 0.30, True),
-                  Shell("s2", "s", 0.875, False), Shell("p2", "p", 0.75, False),
-                  Shell("d", "d", 0.35, False)]
-    else:
+    if basis not in SI_BASES:
         raise ValueError(basis)
-    return Species("Si", shells, eps)
+    return Species("Si", [SI_SHELLS[k] for k in SI_BASES[basis]], eps)
 
 
 def si_model(basis: str) -> Model:
@@ -69,19 +81,37 @@ AVOGADRO = 6.02214076e23
 BOHR_CM = 0.529177210903e-8
 
 
-def water_species():
-    o = Species("O", [Shell("s1", "s", 0.80, True), Shell("p1", "p", 0.60, True),
-                      Shell("s2", "s", 2.0, False), Shell("p2", "p", 1.5, False),
-                      Shell("d", "d", 0.8, False)],
-                {"s": -1.20, "p": -0.45, "d": 0.40})
-    h = Species("H", [Shell("s1", "s", 0.60, True), Shell("s2", "s", 1.5, False),
-                      Shell("p", "p", 0.75, False)],
-                {"s": -0.20, "p": 0.40})
+# Water basis sets by orbitals per molecule (n = 4 per molecule):
+#   DZ+d 17 (O s,p,s,p,d; H s,s: 23.5%), DZP 23 (H adds p: 17.4%),
+#   TZP 29 (O and H add a third, tighter s and O a third p: 13.8%).
+O_SHELLS = {
+    "s1": Shell("s1", "s", 0.80, True), "p1": Shell("p1", "p", 0.60, True),
+    "s2": Shell("s2", "s", 2.0, False), "p2": Shell("p2", "p", 1.5, False),
+    "s3": Shell("s3", "s", 5.0, False), "p3": Shell("p3", "p", 3.8, False),
+    "d": Shell("d", "d", 0.8, False),
+}
+H_SHELLS = {
+    "s1": Shell("s1", "s", 0.60, True), "s2": Shell("s2", "s", 1.5, False),
+    "s3": Shell("s3", "s", 3.8, False), "p": Shell("p", "p", 0.75, False),
+}
+WATER_BASES = {
+    "DZ+d": (["s1", "p1", "s2", "p2", "d"], ["s1", "s2"]),
+    "DZP": (["s1", "p1", "s2", "p2", "d"], ["s1", "s2", "p"]),
+    "TZP": (["s1", "p1", "s2", "p2", "s3", "p3", "d"], ["s1", "s2", "s3", "p"]),
+}
+
+
+def water_species(basis: str = "DZP"):
+    if basis not in WATER_BASES:
+        raise ValueError(basis)
+    o_keys, h_keys = WATER_BASES[basis]
+    o = Species("O", [O_SHELLS[k] for k in o_keys], {"s": -1.20, "p": -0.45, "d": 0.40})
+    h = Species("H", [H_SHELLS[k] for k in h_keys], {"s": -0.20, "p": 0.40})
     return o, h
 
 
-def water_model() -> Model:
-    o, h = water_species()
+def water_model(basis: str = "DZP") -> Model:
+    o, h = water_species(basis)
     oh = SKPair(d0=R_OH, ss=-0.60, sp=0.0, ps=0.80)          # s_O-s_H, s_H-p_O
     ho = SKPair(d0=R_OH, ss=-0.60, sp=0.80, ps=0.0)
     oo = SKPair(d0=5.4, ss=-0.02, sp=0.03, ps=0.03, pp_sigma=0.05, pp_pi=-0.012)
@@ -89,7 +119,7 @@ def water_model() -> Model:
     hh = SKPair(d0=d_hh, ss=-0.03)
     return Model(species={"O": o, "H": h},
                  sk={("O", "H"): oh, ("H", "O"): ho, ("O", "O"): oo, ("H", "H"): hh},
-                 rc=9.0, params={"system": "water"})
+                 rc=9.0, params={"system": "water", "basis": basis})
 
 
 def water_box_length(nmol: int, density_g_cm3: float = 1.0) -> float:

@@ -11,8 +11,8 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("emulated_certificate", [False, True])
-def test_warm_started_sequence_matches_exact(emulated_certificate):
+@pytest.mark.parametrize("native_certificate", [False, True])
+def test_warm_started_sequence_matches_exact(native_certificate):
     from paper_1312_1549_gb300 import build
     build.build()
     from paper_1312_1549_gb300.solver import OMMSolver
@@ -22,7 +22,7 @@ def test_warm_started_sequence_matches_exact(emulated_certificate):
     delta = configs.warm_start_delta(p, 1)
     iters = []
     with OMMSolver(dev(p.H), dev(p.S), dev(p.T), p.n, p.eta, p.tau, precision="mixed",
-                   emulated_certificate=emulated_certificate) as s:
+                   native_certificate=native_certificate) as s:
         C = dev(p.C0)
         for k in range(4):
             Hk = p.H + np.diag(k * delta)

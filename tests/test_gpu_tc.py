@@ -118,11 +118,11 @@ def test_gemm_emu_error_falls_with_slices(S):
     assert all(errs[i + 1] < errs[i] / 100 for i in range(3)), errs
 
 
-def test_mixed_solve_with_emulated_certificate(S, si64):
-    """Float64-class certificate and density matrix meet the same bars as the native ones."""
+def test_mixed_solve_with_native_certificate(S, si64):
+    """A native float64 certificate and density matrix meet the same bars as the sliced ones."""
     p, ref, ex = si64
     with S.OMMSolver(dev(p.H), dev(p.S), dev(p.T), p.n, p.eta, p.tau, precision="mixed",
-                     emulated_certificate=True) as s:
+                     native_certificate=True) as s:
         C, E, D, info = s.solve(dev(p.C0), want_D=True)
     assert info["status"] == 0 and info["gmax"] < 1e-9
     assert abs(E - ex["E"]) / abs(ex["E"]) <= 1e-9
