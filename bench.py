@@ -187,12 +187,11 @@ def run_batch(args):
 
     phases = []
 
-    def step(precision="mixed", subset=None):
+    def step(precision="mixed", subset=None, profile=False):
         idx = range(len(probs)) if subset is None else subset
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with S.OMMBatch([dev[i] for i in idx], precision=precision, stream=stream,
-                        profile=precision == "mixed",
+        with S.OMMBatch([dev[i] for i in idx], precision=precision, stream=stream, profile=profile,
                         native_certificate=args.native_certificate) as b:
             torch.cuda.synchronize()
             t1 = time.perf_counter()
@@ -211,13 +210,17 @@ def run_batch(args):
             E, infos = step()
         e1.record(stream)
         torch.cuda.synchronize()
+    launches = S.launch_count() - launches0
     ms = e0.elapsed_time(e1) / args.steps
     out = _base_line(args, ms * 1e-3)
     out["config"]["certificate"] = "native float64" if args.native_certificate else "float64-class (sliced)"
     logical = sum(i["iterations"] * (6.0 * p.m * p.m * p.n + 16.0 * p.m * p.n * p.n)
                   for i, p in zip(infos, probs))
     timed = phases[-args.steps:]
-    b0 = infos[0]  # batch totals are repeated in every instance's report
+    # the GEMM roofline comes from one more solve with profiling on: the line searches are then
+    # launched eagerly and polled after each one, so that solve is not the timed one
+    _, prof_infos = step(profile=True)
+    b0 = prof_infos[0]  # batch totals are repeated in every instance's report
     achieved = (b0["main_gemm_flop"] / (b0["ms_main_gemm"] * 1e-3) / 1e12) if b0["ms_main_gemm"] > 0 else None
     peak = load_peaks()[0]["bf16_tflops_sustained"]
     out.update({"instances": len(probs), "m_range": [min(p.m for p in probs), max(p.m for p in probs)],
@@ -226,23 +229,25 @@ def run_batch(args):
                 "gemm_tflops_logical": logical / (ms * 1e-3) / 1e12,
                 "s_create_wall": statistics.mean(t[0] for t in timed),
                 "s_solve_wall": statistics.mean(t[1] for t in timed),
-                "ms_line_search_graphs": b0["ms_iterate"],
+                "ms_line_search_graphs": infos[0]["ms_iterate"],
                 "ms_refresh_sum": sum(i["ms_refine"] - i["ms_certify"] for i in infos),
                 "ms_certify_sum": sum(i["ms_certify"] for i in infos),
-                "gpu_launches": S.launch_count() - launches0, "clocks": clk.summary(),
+                "gpu_launches": launches, "clocks": clk.summary(),
                 "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
                              "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                              "traffic": None,
                              "kernel": "gemm_persistent_kernel (grouped over the batch, tcgen05, fused 3-term split)",
                              "peak_source": "bf16_tflops_sustained of measured MEASURED_PEAKS",
                              "launches": b0["main_gemm_launches"],
-                             "avg_launch_ms": b0["ms_main_gemm"] / max(b0["main_gemm_launches"], 1)}})
+                             "avg_launch_ms": b0["ms_main_gemm"] / max(b0["main_gemm_launches"], 1),
+                             "measured_in": "one extra profiled batched solve after the timed steps"}})
     # accuracy on a sample of instances against the eigenpair definition
-    from oracle import exact
-    sample = list(range(0, len(probs), max(1, len(probs) // 4)))
-    out["rel_err_E_vs_exact_sample"] = max(
-        abs(E[i] - exact.exact_minimum(probs[i].H, probs[i].S, probs[i].n, want_matrices=False)["E"])
-        / abs(E[i]) for i in sample)
+    if not args.no_exact_check:
+        from oracle import exact
+        sample = list(range(0, len(probs), max(1, len(probs) // 4)))
+        out["rel_err_E_vs_exact_sample"] = max(
+            abs(E[i] - exact.exact_minimum(probs[i].H, probs[i].S, probs[i].n, want_matrices=False)["E"])
+            / abs(E[i]) for i in sample)
     if not args.no_fp64_compare:
         # the float64 GPU path instance by instance on every 8th instance, scaled by flops
         sub = list(range(0, len(probs), 8))
@@ -304,6 +309,7 @@ def run_sequence(args):
             infos = step()
         e1.record(stream)
         torch.cuda.synchronize()
+    launches = S.launch_count() - launches0
     ms = e0.elapsed_time(e1) / args.steps
     out = _base_line(args, ms * 1e-3)
     out["config"]["certificate"] = "native float64" if args.native_certificate else "float64-class (sliced)"

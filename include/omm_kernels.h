@@ -34,6 +34,16 @@ omm_status omm_kernel_dgemm(int transA, int transB, int M, int N, int K, double 
  * call returns OMM_ERR_NOT_SPD and P is unspecified. */
 omm_status omm_kernel_spd_inverse(int m, const double* A, double* P, int* info, void* stream);
 
+/* The same P = A^-1 (Sec. 2.4, Eq. 17) with float64-class products on the BF16
+ * tensor cores, as the mixed-precision solver computes its preconditioner: a
+ * recursive Cholesky factorisation, inverse and product L^-T L^-1 on halves,
+ * whose off-diagonal products use 10 fixed-point slices per operand (the Ozaki
+ * scheme; about 2^-50 of each row-scaled operand), with the 64 x 64 diagonal
+ * blocks factored and inverted in float64. Arguments, ownership and *info as
+ * for omm_kernel_spd_inverse; OMM_ERR_TIMEOUT if a bounded wait of a tensor-core
+ * GEMM expired. Workspace: about (m^2 + 0.75 m^2) float64 + 5 m^2 bytes. */
+omm_status omm_kernel_spd_inverse_sliced(int m, const double* A, double* P, int* info, void* stream);
+
 /* Line minimum of the quartic a0 + a1 x + a2 x^2 + a3 x^3 + a4 x^4 (Sec. 2.3,
  * Eq. 13) as the solver takes it on the device: the first local minimum along
  * x > 0 (a1 < 0). alpha (host, 5 values), x (host) receives the step.

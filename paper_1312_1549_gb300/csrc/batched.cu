@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) b_split_t_kernel(const IterArgs* __restri
   const IterArgs& a = A[blockIdx.y];
   if (dev::stopped(a.sc)) return;
   const long rows = 2L * a.n, cols = a.m;
-  const long tiles = ((rows + 31) / 32) * ((cols + 31) / 32);
+  const long tiles = ((rows + 63) / 64) * ((cols + 31) / 32);
   if ((long)blockIdx.x >= tiles) return;
   const double* src = job == 0 ? a.Y4 : a.dY;
   __nv_bfloat16* hi = a.YT_hi + (job == 0 ? 0 : 2L * a.n);
@@ -334,7 +334,6 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
     OMM_CUDA_TRY(cudaMallocHost((void**)&b->sc_host_all, count * sizeof(Scalars)));
     std::vector<IterArgs> args(count);
     std::vector<tc::GroupDesc> gpg, ghd, gpr, gg;
-    int tpg = 0, thd = 0, tpr = 0, tgg = 0;
     for (int i = 0; i < count; ++i) {
       omm_ctx* c = b->ctx[i];
       cudaFree(c->sc);
@@ -360,18 +359,14 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       const int* skip = &c->sc->done;
       if (b->precond) {
         tc::Epilogue e{c->PG, mi, mi, 0, 1.0, 0.0, ni, mi, skip, v.err};
-        gpg.push_back(tc::make_group(*v.opG, *v.opP, mi, e, tpg));
-        tpg += tc::tiles_of(e);
+        gpg.push_back(tc::make_group(*v.opG, *v.opP, mi, e, 0));
       }
       tc::Epilogue ehd{c->Y4 + 2 * nm, mi, mi, nm, 1.0, 0.0, ni, 2 * mi, skip, v.err};
-      ghd.push_back(tc::make_group(*v.opD, *v.opHS, mi, ehd, thd));
-      thd += tc::tiles_of(ehd);
+      ghd.push_back(tc::make_group(*v.opD, *v.opHS, mi, ehd, 0));
       tc::Epilogue epr{c->Proj, 4L * ni, 4L * ni, 0, 1.0, 0.0, ni, 4 * ni, skip, v.err};
-      gpr.push_back(tc::make_group(*v.opD, *v.opY, mi, epr, tpr));
-      tpr += tc::tiles_of(epr);
+      gpr.push_back(tc::make_group(*v.opD, *v.opY, mi, epr, 0));
       tc::Epilogue eg{c->G, mi, mi, 0, -4.0, 1.0, ni, mi, skip, v.err};
-      gg.push_back(tc::make_group(*v.opW, *v.opYT, 4 * ni, eg, tgg));
-      tgg += tc::tiles_of(eg);
+      gg.push_back(tc::make_group(*v.opW, *v.opYT, 4 * ni, eg, 0));
       // issued tensor flops, 3 x 2 M N K (3-term split), of this instance's share of each GEMM
       const double issued = 3.0 * 2.0 * ni;  // x N x K
       b->gemm_flop[0].push_back(b->precond ? issued * mi * mi : 0.0);
@@ -380,7 +375,19 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       b->gemm_flop[3].push_back(issued * mi * 4.0 * ni);
       b->max_rows = std::max(b->max_rows, 2 * ni);
       b->max_tiles = std::max(b->max_tiles, a.tiles);
-      b->max_ttiles = std::max(b->max_ttiles, (int)(((2L * ni + 31) / 32) * ((mi + 31) / 32)));
+      b->max_ttiles = std::max(b->max_ttiles, (int)(((2L * ni + 63) / 64) * ((mi + 31) / 32)));
+    }
+    // Longest tiles first: a persistent CTA takes tiles b, b + grid, ..., so ordering the groups
+    // by falling contraction length spreads the long tiles over all SMs before the short ones
+    // fill in (the largest-processing-time-first rule)
+    for (auto* gv : {&gpg, &ghd, &gpr, &gg}) {
+      std::stable_sort(gv->begin(), gv->end(),
+                       [](const tc::GroupDesc& x, const tc::GroupDesc& y) { return x.K > y.K; });
+      int t = 0;
+      for (tc::GroupDesc& g : *gv) {
+        g.tile_begin = t;
+        t += tc::tiles_of(g.ep);
+      }
     }
     for (cudaStream_t& q : b->pool) OMM_CUDA_TRY(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
     alloc(&b->args, count);

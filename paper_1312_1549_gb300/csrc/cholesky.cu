@@ -10,7 +10,21 @@
 //   3. P = Y^T Y (lower tiles only, K loop from the diagonal), then mirrored.
 // A failed pivot (<= 0 or NaN) is recorded in info_dev and replaced by 1 so
 // that the remaining stages stay finite; the caller reports the failure.
+//
+// spd_inverse_sliced computes the same P with float64-class products on the
+// BF16 tensor cores (the fixed-point slicing of emu.cu), recursively on
+// halves so that every product has a long contraction:
+//   chol_inv([A11 A21^T; A21 A22]):  L11, Y11 = chol_inv(A11);
+//     L21 = A21 Y11^T;  A22 -= L21 L21^T;  L22, Y22 = chol_inv(A22);
+//     Y21 = -(Y22 L21) Y11                         (Y = L^-1)
+//   lauum(Y) = Y^T Y:  P22 = lauum(Y22);  P21 = Y22^T Y21;
+//     P11 = lauum(Y11) + Y21^T Y21
+// with 64 x 64 leaves factored and inverted in float64 by one CTA.
+#include "emu.cuh"
 #include "omm_internal.cuh"
+#include "tc_gemm.cuh"
+
+#include <algorithm>
 
 namespace omm {
 namespace {
@@ -154,6 +168,160 @@ void spd_inverse(cudaStream_t st, int m, double* A, double* P, double* work, int
   trtri_rec(st, m, A, w, 0, m);
   // 3. P = Y^T Y (lower), mirrored
   dgemm(st, 1, 0, m, m, m, 1.0, A, m, 0, A, m, 0, 0.0, P, m, 0, 1, kTriLower | kTriKStart);
+  launch_symmetrize_lower(st, m, P);
+}
+
+// ------------------------------------------------------------------ float64-class (sliced) variant
+namespace {
+
+constexpr int kInvSlices = 10;
+
+long round8(long x) { return (x + 7) / 8 * 8; }
+
+struct SlicedWork {
+  int m = 0;
+  double* A = nullptr;       // the matrix, factor L in its lower triangle
+  double* Y = nullptr;       // L^-1 (lower triangle, zero above)
+  double* P = nullptr;
+  double* tr0 = nullptr;     // float64 scratch: transposes and one product
+  double* tr1 = nullptr;
+  double* prod = nullptr;
+  double* leaf = nullptr;    // NB x NB inverse of a diagonal block
+  __nv_bfloat16* sl0 = nullptr;  // slices of two operands
+  __nv_bfloat16* sl1 = nullptr;
+  int* info = nullptr;
+  int* err = nullptr;
+  double* partial = nullptr;  // per-chunk sums of the products with few output tiles
+  long partial_cap = 0;
+};
+
+// C (M x N, ldc) = alpha A B^T + beta C with A (M x K, lda) and B (N x K, ldb) row-major;
+// the slices of A go to sl0, those of B to sl1 (or B = A: one slicing, both maps)
+void sliced_nt(cudaStream_t st, SlicedWork& w, int M, int N, int K, double alpha, const double* A, long lda,
+               const double* B, long ldb, double beta, double* C, long ldc) {
+  const long ld = round8(K);
+  emu::slice_rows(st, A, M, K, lda, kInvSlices, w.sl0, ld, nullptr);
+  const tc::Operand oa = tc::make_operand(w.sl0, M, K, ld, kInvSlices, true);
+  tc::Operand ob;
+  if (B == A && ldb == lda && N == M) {
+    ob = tc::make_operand(w.sl0, N, K, ld, kInvSlices, false);
+  } else {
+    emu::slice_rows(st, B, N, K, ldb, kInvSlices, w.sl1, ld, nullptr);
+    ob = tc::make_operand(w.sl1, N, K, ld, kInvSlices, false);
+  }
+  emu::gemm(st, oa, ob, K, kInvSlices, tc::Epilogue{C, ldc, N, 0, alpha, beta, M, N, nullptr, w.err}, w.partial,
+            w.partial_cap);
+}
+
+// leaf: factor A[r0:r0+b, r0:r0+b] in place and write its inverse into Y
+void leaf(cudaStream_t st, SlicedWork& w, int r0, int b) {
+  const long m = w.m;
+  potf2_inv_kernel<<<1, 256, 0, st>>>(w.A + r0 * m + r0, m, b, w.leaf, w.info, r0);
+  OMM_LAUNCH_CHECK();
+  copy_block_kernel<<<16, 256, 0, st>>>(b, w.leaf, NB, w.Y + r0 * m + r0, m);
+  OMM_LAUNCH_CHECK();
+}
+
+int half_of(int b) { return ((b / NB + 1) / 2) * NB; }  // a multiple of NB, about b / 2
+
+void chol_inv(cudaStream_t st, SlicedWork& w, int r0, int b) {
+  if (b <= NB) {
+    leaf(st, w, r0, b);
+    return;
+  }
+  const long m = w.m;
+  const int b1 = half_of(b), b2 = b - b1, r1 = r0 + b1;
+  chol_inv(st, w, r0, b1);
+  double* A21 = w.A + (long)r1 * m + r0;
+  double* A22 = w.A + (long)r1 * m + r1;
+  const double* Y11 = w.Y + (long)r0 * m + r0;
+  const double* Y22 = w.Y + (long)r1 * m + r1;
+  double* Y21 = w.Y + (long)r1 * m + r0;
+  // L21 = A21 Y11^T (to scratch, then over A21)
+  sliced_nt(st, w, b2, b1, b1, 1.0, A21, m, Y11, m, 0.0, w.prod, b1);
+  OMM_CUDA_TRY(cudaMemcpy2DAsync(A21, sizeof(double) * m, w.prod, sizeof(double) * b1, sizeof(double) * b1, b2,
+                                 cudaMemcpyDeviceToDevice, st));
+  // A22 -= L21 L21^T
+  sliced_nt(st, w, b2, b2, b1, -1.0, A21, m, A21, m, 1.0, A22, m);
+  chol_inv(st, w, r1, b2);
+  // Z = Y22 L21 (b2 x b1): B operand L21^T (b1 x b2)
+  emu::transpose(st, A21, b2, b1, m, w.tr0, b2);
+  sliced_nt(st, w, b2, b1, b2, 1.0, Y22, m, w.tr0, b2, 0.0, w.prod, b1);
+  // Y21 = -Z Y11: B operand Y11^T (b1 x b1)
+  emu::transpose(st, Y11, b1, b1, m, w.tr1, b1);
+  sliced_nt(st, w, b2, b1, b1, -1.0, w.prod, b1, w.tr1, b1, 0.0, Y21, m);
+}
+
+// P[r0:r0+b, r0:r0+b] (lower blocks) = Yb^T Yb for the lower-triangular Yb = Y[r0:r0+b, r0:r0+b]
+void lauum(cudaStream_t st, SlicedWork& w, int r0, int b) {
+  const long m = w.m;
+  if (b <= NB) {
+    const double* Yb = w.Y + (long)r0 * m + r0;
+    dgemm(st, 1, 0, b, b, b, 1.0, Yb, m, 0, Yb, m, 0, 0.0, w.P + (long)r0 * m + r0, m, 0, 1,
+          kTriLower | kTriKStart);
+    return;
+  }
+  const int b1 = half_of(b), b2 = b - b1, r1 = r0 + b1;
+  // the recursions use the scratch buffers, so they come first
+  lauum(st, w, r1, b2);
+  lauum(st, w, r0, b1);
+  const double* Y21 = w.Y + (long)r1 * m + r0;
+  const double* Y22 = w.Y + (long)r1 * m + r1;
+  // Y21^T (b1 x b2) serves both products below
+  emu::transpose(st, Y21, b2, b1, m, w.tr0, b2);
+  // P21 = Y22^T Y21: A operand Y22^T (b2 x b2), B operand Y21^T
+  emu::transpose(st, Y22, b2, b2, m, w.tr1, b2);
+  sliced_nt(st, w, b2, b1, b2, 1.0, w.tr1, b2, w.tr0, b2, 0.0, w.P + (long)r1 * m + r0, m);
+  // P11 = lauum(Y11) + Y21^T Y21
+  sliced_nt(st, w, b1, b1, b2, 1.0, w.tr0, b2, w.tr0, b2, 1.0, w.P + (long)r0 * m + r0, m);
+}
+
+}  // namespace
+
+// chunk sums of the GEMMs with fewer than ~76 output tiles of 128 x 256 (at most 11 chunks)
+long partial_capacity(int m) {
+  const long h = (m + 1) / 2 + NB;
+  return std::min(11L * h * h, 11L * 76 * 128 * 256);
+}
+
+size_t spd_inverse_sliced_workspace_bytes(int m) {
+  const long h = (m + 1) / 2 + NB;  // the largest off-diagonal block edge
+  const size_t f64 = (size_t)m * m + 3 * (size_t)h * h + (size_t)NB * NB +   // Y, tr0, tr1, prod, leaf
+                     (size_t)partial_capacity(m);
+  const size_t bf = 2 * (size_t)kInvSlices * (size_t)h * round8(h);        // sl0, sl1
+  return f64 * sizeof(double) + bf * sizeof(__nv_bfloat16) + 2 * 256;
+}
+
+void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work, int* info_dev, int* err_dev) {
+  const long h = (m + 1) / 2 + NB;
+  SlicedWork w;
+  w.m = m;
+  w.A = A;
+  w.P = P;
+  w.info = info_dev;
+  w.err = err_dev;
+  double* f = static_cast<double*>(work);
+  w.Y = f;
+  f += (long)m * m;
+  w.tr0 = f;
+  f += h * h;
+  w.tr1 = f;
+  f += h * h;
+  w.prod = f;
+  f += h * h;
+  w.leaf = f;
+  f += NB * NB;
+  w.partial = f;
+  w.partial_cap = partial_capacity(m);
+  f += w.partial_cap;
+  uintptr_t p = (reinterpret_cast<uintptr_t>(f) + 255) & ~uintptr_t(255);
+  w.sl0 = reinterpret_cast<__nv_bfloat16*>(p);
+  w.sl1 = w.sl0 + (size_t)kInvSlices * h * round8(h);
+  OMM_CUDA_TRY(cudaMemsetAsync(info_dev, 0, sizeof(int), st));
+  OMM_CUDA_TRY(cudaMemsetAsync(w.Y, 0, sizeof(double) * m * (size_t)m, st));
+  OMM_CUDA_TRY(cudaMemsetAsync(P, 0, sizeof(double) * m * (size_t)m, st));
+  chol_inv(st, w, 0, m);
+  lauum(st, w, 0, m);
   launch_symmetrize_lower(st, m, P);
 }
 

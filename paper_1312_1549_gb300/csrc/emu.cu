@@ -21,6 +21,7 @@
 #include "emu.cuh"
 #include "tc_gemm.cuh"
 
+#include <algorithm>
 #include <new>
 
 namespace omm {
@@ -141,9 +142,11 @@ tc::PairList level_chunks(int K, int s) {
   return pl;
 }
 
-void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep) {
-  // one persistent launch: every output tile runs its chunks in order on one CTA
-  tc::gemm_persistent(st, A, B, K, level_chunks(K, s), ep);
+void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep,
+          double* partial, long partial_capacity) {
+  // one persistent launch: every output tile runs its chunks in order on one CTA (or, for a
+  // product of few tiles with scratch given, every chunk on its own CTA, then one reduction)
+  tc::gemm_persistent(st, A, B, K, level_chunks(K, s), ep, partial, partial_capacity);
 }
 
 }  // namespace emu
@@ -163,6 +166,8 @@ struct EmuState {
   long ldn = 0;
   tc::Operand opHS, opC, opY, opW, opYT, opCT, opXT, opSW, opCTb;  // opCTb: C^T as a B operand
   int* err = nullptr;
+  double* partial = nullptr;  // per-chunk sums of the products with few output tiles
+  long partial_cap = 0;
 };
 
 namespace {
@@ -190,6 +195,9 @@ EmuState* emu_create(cudaStream_t st, int m, int n, int slices, const double* HS
     alloc(&es->XTs, (size_t)kDensitySlices * m * es->ldn);
     alloc(&es->SWs, (size_t)kDensitySlices * n * es->ldn);
     alloc(&es->err, 1);
+    // the [S_W | H_W] product (n x 2n) is the one with few tiles; 11 chunks at most for K <= 16384
+    es->partial_cap = std::min(11L * n * 2L * n, 1L << 25);
+    alloc(&es->partial, (size_t)es->partial_cap);
     OMM_CUDA_TRY(cudaMemsetAsync(es->err, 0, sizeof(int), st));
     emu::slice_rows(st, HS, 2L * m, m, m, slices, es->HSs, ldm, nullptr);
     es->opHS = tc::make_operand(es->HSs, 2L * m, m, ldm, slices, false);
@@ -214,7 +222,7 @@ void emu_update_H(EmuState* es, cudaStream_t st, const double* HS) {
 
 void emu_destroy(EmuState* es) {
   if (!es) return;
-  void* bufs[] = {es->HSs, es->Cs, es->Ys, es->Ws, es->YTs, es->T64, es->CTs, es->XTs, es->SWs, es->err};
+  void* bufs[] = {es->HSs, es->Cs, es->Ys, es->Ws, es->YTs, es->T64, es->CTs, es->XTs, es->SWs, es->err, es->partial};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete es;
@@ -234,11 +242,13 @@ void emu_recompute_state(EmuState* es, cudaStream_t st, Scalars* sc, const doubl
   const long nm = (long)n * m;
   emu::slice_rows(st, C, n, m, m, s, es->Cs, es->ldm, nullptr);
   // [HC; SC] (n x m layout) = C [H~; S]^T
-  emu::gemm(st, es->opC, es->opHS, m, s, tc::Epilogue{Y4, m, m, nm, 1.0, 0.0, n, 2 * m, nullptr, es->err});
+  emu::gemm(st, es->opC, es->opHS, m, s, tc::Epilogue{Y4, m, m, nm, 1.0, 0.0, n, 2 * m, nullptr, es->err},
+            es->partial, es->partial_cap);
   emu::slice_rows(st, Y4, 2L * n, m, m, s, es->Ys, es->ldm, nullptr);
   // [S_W | H_W] = C [SC; HC]^T
   emu::gemm(st, es->opC, es->opY, m, s,
-            tc::Epilogue{SWHW + n, 2L * n, n, -(long)n, 1.0, 0.0, n, 2 * n, nullptr, es->err});
+            tc::Epilogue{SWHW + n, 2L * n, n, -(long)n, 1.0, 0.0, n, 2 * n, nullptr, es->err}, es->partial,
+            es->partial_cap);
   launch_functional(st, n, SWHW, part2);
   launch_finish_functional(st, sc, part2, traces_blocks(n));
   // G = 8 HC - 4 [S_W | H_W] [HC; SC]
@@ -246,7 +256,8 @@ void emu_recompute_state(EmuState* es, cudaStream_t st, Scalars* sc, const doubl
   emu::transpose(st, Y4, 2L * n, m, m, es->T64, 2L * n);
   emu::slice_rows(st, es->T64, m, 2L * n, 2L * n, s, es->YTs, es->ld2n, nullptr);
   launch_scale_copy(st, nm, Y4, 8.0, G, nullptr);
-  emu::gemm(st, es->opW, es->opYT, 2 * n, s, tc::Epilogue{G, m, m, 0, -4.0, 1.0, n, m, nullptr, es->err});
+  emu::gemm(st, es->opW, es->opYT, 2 * n, s, tc::Epilogue{G, m, m, 0, -4.0, 1.0, n, m, nullptr, es->err},
+            es->partial, es->partial_cap);
   launch_gmax(st, nm, G, part);
   launch_finish_gmax(st, sc, part);
 }

@@ -14,7 +14,8 @@ void transpose(cudaStream_t st, const double* src, long rows, long cols, long ld
 // FP32 sums are exact for a contraction of length K
 tc::PairList level_chunks(int K, int s);
 // C = alpha A B^T + beta C from s-slice operands (A, B made by slice_rows)
-void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep);
+void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep,
+          double* partial = nullptr, long partial_capacity = 0);
 }  // namespace emu
 
 struct EmuState;

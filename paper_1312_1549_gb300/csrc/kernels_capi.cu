@@ -4,6 +4,8 @@
 #include "tc_gemm.cuh"
 #include "emu.cuh"
 
+#include <algorithm>
+
 #include <cstring>
 #include <string>
 
@@ -68,6 +70,44 @@ omm_status omm_kernel_spd_inverse(int m, const double* A, double* P, int* info, 
   if (W) cudaFree(W);
   if (work) cudaFree(work);
   if (info_dev) cudaFree(info_dev);
+  return rc;
+}
+
+omm_status omm_kernel_spd_inverse_sliced(int m, const double* A, double* P, int* info, void* stream) {
+  if (m <= 0 || !A || !P) {
+    set_last_error("omm_kernel_spd_inverse_sliced: invalid argument");
+    return OMM_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double* W = nullptr;
+  void* work = nullptr;
+  int* flags = nullptr;  // [0] pivot info, [1] bounded-wait failures
+  omm_status rc = OMM_OK;
+  try {
+    const size_t mm = (size_t)m * m;
+    OMM_CUDA_TRY(cudaMalloc((void**)&W, mm * sizeof(double)));
+    OMM_CUDA_TRY(cudaMalloc(&work, spd_inverse_sliced_workspace_bytes(m)));
+    OMM_CUDA_TRY(cudaMalloc((void**)&flags, 2 * sizeof(int)));
+    OMM_CUDA_TRY(cudaMemsetAsync(flags, 0, 2 * sizeof(int), st));
+    OMM_CUDA_TRY(cudaMemcpyAsync(W, A, mm * sizeof(double), cudaMemcpyDefault, st));
+    spd_inverse_sliced(st, m, W, P, work, flags, flags + 1);
+    int h[2] = {0, 0};
+    OMM_CUDA_TRY(cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (info) *info = h[0];
+    if (h[1] != 0) {
+      set_last_error("omm_kernel_spd_inverse_sliced: a bounded device wait expired");
+      rc = OMM_ERR_TIMEOUT;
+    } else if (h[0] != 0) {
+      set_last_error("omm_kernel_spd_inverse_sliced: not positive definite");
+      rc = OMM_ERR_NOT_SPD;
+    }
+  } catch (const CudaError& e) {
+    rc = cuda_fail("omm_kernel_spd_inverse_sliced", e);
+  }
+  if (W) cudaFree(W);
+  if (work) cudaFree(work);
+  if (flags) cudaFree(flags);
   return rc;
 }
 
@@ -186,13 +226,17 @@ omm_status omm_kernel_gemm_emu(int M, int N, int K, const double* A, const doubl
   const long ld = (K + 7) / 8 * 8;
   __nv_bfloat16* buf = nullptr;
   int* err = nullptr;
+  double* partial = nullptr;  // chunk sums, for products of few tiles (as the solver runs them)
+  const long partial_cap = std::min(11L * M * N, 1L << 24);
   omm_status rc = OMM_OK;
   try {
     const size_t na = (size_t)slices * M * ld, nb = (size_t)slices * N * ld;
     if (cudaMalloc((void**)&buf, (na + nb) * sizeof(__nv_bfloat16)) != cudaSuccess ||
-        cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess) {
+        cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&partial, partial_cap * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       if (buf) cudaFree(buf);
+      if (err) cudaFree(err);
       set_last_error("omm_kernel_gemm_emu: device allocation failed");
       return OMM_ERR_OOM;
     }
@@ -201,7 +245,8 @@ omm_status omm_kernel_gemm_emu(int M, int N, int K, const double* A, const doubl
     emu::slice_rows(st, B, N, K, K, slices, buf + na, ld, nullptr);
     tc::Operand oa = tc::make_operand(buf, M, K, ld, slices, true);
     tc::Operand ob = tc::make_operand(buf + na, N, K, ld, slices, false);
-    emu::gemm(st, oa, ob, K, slices, tc::Epilogue{C, N, N, 0, alpha, beta, M, N, nullptr, err});
+    emu::gemm(st, oa, ob, K, slices, tc::Epilogue{C, N, N, 0, alpha, beta, M, N, nullptr, err}, partial,
+              partial_cap);
     int h = 0;
     OMM_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -214,6 +259,7 @@ omm_status omm_kernel_gemm_emu(int M, int N, int K, const double* A, const doubl
   }
   if (buf) cudaFree(buf);
   if (err) cudaFree(err);
+  if (partial) cudaFree(partial);
   return rc;
 }
 

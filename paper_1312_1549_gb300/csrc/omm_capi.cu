@@ -301,6 +301,7 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
   c->precond = precond;
   double* A = nullptr;
   double* work = nullptr;
+  int* inv_err = nullptr;
   try {
     const long mm = (long)m * m, nm = (long)n * m;
     for (auto& e : c->ev) OMM_CUDA_TRY(cudaEventCreate(&e));
@@ -312,10 +313,18 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     copy_in(c->HS, H, mm, c->st);
     copy_in(c->HS + mm, S, mm, c->st);
     launch_axpby_shift(c->st, mm, c->HS, c->HS + mm, eta, c->HS);
+    // the mixed path factors with float64-class tensor-core products, the float64 path natively
+    const bool sliced_inverse = o.precision == OMM_PREC_MIXED;
     if (precond) {
       dev_alloc(&c->P, mm);
       dev_alloc(&A, mm);
-      dev_alloc(&work, spd_inverse_workspace(m));
+      if (sliced_inverse) {
+        dev_alloc(&work, (spd_inverse_sliced_workspace_bytes(m) + sizeof(double) - 1) / sizeof(double));
+        dev_alloc(&inv_err, 1);
+        OMM_CUDA_TRY(cudaMemsetAsync(inv_err, 0, sizeof(int), c->st));
+      } else {
+        dev_alloc(&work, spd_inverse_workspace(m));
+      }
       if (std::isfinite(tau)) {
         copy_in(A, T, mm, c->st);
         launch_add_scaled(c->st, mm, c->HS + mm, A, 1.0 / tau, A);
@@ -323,7 +332,8 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
         OMM_CUDA_TRY(cudaMemcpyAsync(A, c->HS + mm, mm * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
       }
       OMM_CUDA_TRY(cudaEventRecord(c->ev[2], c->st));
-      spd_inverse(c->st, m, A, c->P, work, c->info_dev);
+      if (sliced_inverse) spd_inverse_sliced(c->st, m, A, c->P, work, c->info_dev, inv_err);
+      else spd_inverse(c->st, m, A, c->P, work, c->info_dev);
       OMM_CUDA_TRY(cudaEventRecord(c->ev[3], c->st));
     }
     dev_alloc(&c->C, nm);
@@ -342,14 +352,21 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
       c->emu = emu_create(c->st, m, n, kEmuSlices, c->HS);
     }
     OMM_CUDA_TRY(cudaEventRecord(c->ev[1], c->st));
-    int info = 0;
+    int info = 0, ierr = 0;
     OMM_CUDA_TRY(cudaMemcpyAsync(&info, c->info_dev, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    if (inv_err) OMM_CUDA_TRY(cudaMemcpyAsync(&ierr, inv_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     OMM_CUDA_TRY(cudaStreamSynchronize(c->st));
     c->ms_setup = elapsed(c->ev[0], c->ev[1]);
     c->ms_precond = precond ? elapsed(c->ev[2], c->ev[3]) : 0.0;
     dev_free(A);
     dev_free(work);
+    dev_free(inv_err);
     A = work = nullptr;
+    inv_err = nullptr;
+    if (ierr != 0) {
+      destroy(c);
+      return fail(OMM_ERR_TIMEOUT, "omm_create: a bounded device wait expired in the preconditioner inverse");
+    }
     if (info != 0) {
       destroy(c);
       return fail(OMM_ERR_NOT_SPD, "omm_create: S + T/tau is not positive definite (pivot " +
@@ -358,11 +375,13 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
   } catch (const std::bad_alloc&) {
     dev_free(A);
     dev_free(work);
+    dev_free(inv_err);
     destroy(c);
     return fail(OMM_ERR_OOM, "omm_create: device allocation failed");
   } catch (const CudaError& e) {
     dev_free(A);
     dev_free(work);
+    dev_free(inv_err);
     destroy(c);
     return fail(OMM_ERR_CUDA, std::string("omm_create: ") + e.what + ": " + cudaGetErrorString(e.err));
   }

@@ -113,6 +113,10 @@ void dgemm(cudaStream_t st, int transA, int transB, int M, int N, int K, double 
 // receives 0 or the 1-based column of the first non-positive pivot.
 size_t spd_inverse_workspace(int m);
 void spd_inverse(cudaStream_t st, int m, double* A, double* P, double* work, int* info_dev);
+// The same inverse with float64-class (sliced, tensor-core) products; A is overwritten.
+// err_dev receives a nonzero code if a bounded wait of a tensor-core GEMM expired.
+size_t spd_inverse_sliced_workspace_bytes(int m);
+void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work, int* info_dev, int* err_dev);
 
 // ------------------------------------------------------------------ iteration kernels
 void launch_axpby_shift(cudaStream_t st, long count, const double* H, const double* S, double eta,

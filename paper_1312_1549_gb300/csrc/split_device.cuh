@@ -53,36 +53,75 @@ __device__ __forceinline__ void split_store(double x, __nv_bfloat16* hi, __nv_bf
   }
 }
 
-// rows handled by blocks bx, bx + nbx, ...; the block's threads stride over columns
+// hi/lo of two neighbouring elements, stored as bf16 pairs
+__device__ __forceinline__ void split_store2(double x0, double x1, __nv_bfloat16* hi, __nv_bfloat16* lo, long off) {
+  __nv_bfloat16 h[2], l[2];
+  split_store(x0, h, lo ? l : nullptr, 0);
+  split_store(x1, h, lo ? l : nullptr, 1);
+  *reinterpret_cast<__nv_bfloat162*>(hi + off) = __halves2bfloat162(h[0], h[1]);
+  if (lo) *reinterpret_cast<__nv_bfloat162*>(lo + off) = __halves2bfloat162(l[0], l[1]);
+}
+
+// rows handled by blocks bx, bx + nbx, ...; the block's threads stride over columns,
+// two columns at a time (16-byte loads, 4-byte stores) where the row is aligned for it
 __device__ __forceinline__ void split_body(const double* __restrict__ src, const double* __restrict__ sub,
                                            long rows, long cols, long ld_src, __nv_bfloat16* __restrict__ hi,
                                            __nv_bfloat16* __restrict__ lo, long ld_dst, int bx, int nbx) {
   for (long r = bx; r < rows; r += nbx) {
     const double* s = src + r * ld_src;
     const double* u = sub ? sub + r * ld_src : nullptr;
-    for (long c = threadIdx.x; c < cols; c += blockDim.x) {
+    __nv_bfloat16* h = hi + r * ld_dst;
+    __nv_bfloat16* l = lo ? lo + r * ld_dst : nullptr;
+    const bool vec = ((reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(u)) & 15) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(h) | reinterpret_cast<uintptr_t>(l)) & 3) == 0;
+    long c0 = 0;
+    if (vec) {
+      const long npair = cols / 2;
+#pragma unroll 4
+      for (long q = threadIdx.x; q < npair; q += blockDim.x) {
+        double2 x = reinterpret_cast<const double2*>(s)[q];
+        if (u) {
+          const double2 y = reinterpret_cast<const double2*>(u)[q];
+          x.x -= y.x;
+          x.y -= y.y;
+        }
+        split_store2(x.x, x.y, h, l, 2 * q);
+      }
+      c0 = 2 * npair;
+    }
+    for (long c = c0 + threadIdx.x; c < cols; c += blockDim.x) {
       const double x = u ? s[c] - u[c] : s[c];
-      split_store(x, hi, lo, r * ld_dst + c);
+      split_store(x, h, l, c);
     }
   }
 }
 
-// dst[c][r] = split(src[r][c]) for the 32 x 32 tile `tile` (row-major tile grid), 256 threads
+// dst[c][r] = split(src[r][c]) for the 64 x 32 tile `tile` (row-major grid of 64-row by 32-column
+// tiles), 256 threads: every warp writes whole 64-element runs of destination rows, as bf16 pairs
+// where the destination allows it
 __device__ __forceinline__ void split_t_body(const double* __restrict__ src, long rows, long cols, long ld_src,
                                              __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                                              long ld_dst, long tile) {
-  __shared__ double t[32][33];
+  __shared__ double t[64][33];
   const long tiles_c = (cols + 31) / 32;
-  const long r0 = (tile / tiles_c) * 32, c0 = (tile % tiles_c) * 32;
+  const long r0 = (tile / tiles_c) * 64, c0 = (tile % tiles_c) * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int k = ty; k < 32; k += 8) {
+  for (int k = ty; k < 64; k += 8) {
     const long r = r0 + k, c = c0 + tx;
     t[k][tx] = (r < rows && c < cols) ? src[r * ld_src + c] : 0.0;
   }
   __syncthreads();
-  for (int k = ty; k < 32; k += 8) {
-    const long c = c0 + k, r = r0 + tx;
-    if (c < cols && r < rows) split_store(t[tx][k], hi, lo, c * ld_dst + r);
+  const bool pairs = ((ld_dst & 1) == 0) && ((r0 & 1) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(hi) | reinterpret_cast<uintptr_t>(lo)) & 3) == 0;
+  for (int k = ty; k < 32; k += 8) {  // destination row c0 + k, columns r0 + 2 tx, r0 + 2 tx + 1
+    const long c = c0 + k, r = r0 + 2 * tx;
+    if (c >= cols || r >= rows) continue;
+    if (pairs && r + 1 < rows) {
+      split_store2(t[2 * tx][k], t[2 * tx + 1][k], hi, lo, c * ld_dst + r);
+    } else {
+      split_store(t[2 * tx][k], hi, lo, c * ld_dst + r);
+      if (r + 1 < rows) split_store(t[2 * tx + 1][k], hi, lo, c * ld_dst + r + 1);
+    }
   }
 }
 

@@ -368,7 +368,7 @@ __device__ __forceinline__ int find_group(const GroupDesc* __restrict__ groups, 
 // the epilogue adds it to C, and the chunks of a tile stay on one CTA, in order.
 template <bool FUSED>
 __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ groups, int ngroups, int total_tiles,
-                                                const PairList& pl, int* err) {
+                                                const PairList& pl, int* err, double* partial) {
   constexpr int NS = FUSED ? 2 : STAGES;
   constexpr int SB = FUSED ? 2 * STAGE_BYTES : STAGE_BYTES;
   constexpr int ACC_COLS = 256;
@@ -382,6 +382,14 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
   const int nchunk = (FUSED || pl.nchunk <= 0) ? 1 : pl.nchunk;
   auto chunk_begin = [&](int c) { return (c == 0 || pl.nchunk <= 0) ? 0 : (int)pl.chunk_end[c - 1]; };
   auto chunk_end = [&](int c) { return pl.nchunk <= 0 ? pl.n : (int)pl.chunk_end[c]; };
+  // Work units: a tile with all its chunks, or (with a partial buffer, for GEMMs of few
+  // tiles) a single chunk of a tile, whose FP32 sum goes to its own float64 slice of
+  // `partial` for chunk_reduce_kernel to add in chunk order
+  const int upt = (partial != nullptr && !FUSED) ? nchunk : 1;  // units per tile
+  const int total_units = total_tiles * upt;
+  auto unit_tile = [&](int u) { return u / upt; };
+  auto unit_c0 = [&](int u) { return upt == 1 ? 0 : u % upt; };
+  auto unit_c1 = [&](int u) { return upt == 1 ? nchunk : u % upt + 1; };
 
   if (threadIdx.x == 0) {
     for (int q = 0; q < NS; ++q) {
@@ -410,7 +418,8 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
     uint32_t it = 0;
-    for (int tile = blockIdx.x; tile < total_tiles && !*abort_flag; tile += gridDim.x) {
+    for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
+      const int tile = unit_tile(u);
       const GroupDesc* g = groups + find_group(groups, ngroups, tile);
       const int* skip = g->ep.skip;
       if (skip != nullptr && (skip[0] | skip[1])) continue;
@@ -419,7 +428,8 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
       const int local = tile - g->tile_begin, tiles_m = (g->ep.M + BM - 1) / BM;
       const int m0 = (local % tiles_m) * BM, n0 = (local / tiles_m) * BN;
       const int nkb = (g->K + BK - 1) / BK;
-      const int total = FUSED ? nkb : pl.n * nkb;
+      const int p0 = chunk_begin(unit_c0(u));
+      const int total = FUSED ? nkb : (chunk_end(unit_c1(u) - 1) - p0) * nkb;
       for (int t = 0; t < total; ++t, ++it) {
         const int q = it % NS;
         const uint32_t r = it / NS;
@@ -437,7 +447,7 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
           tma_load_2d(sa + 2 * A_BYTES, mB, full, t * BK, n0);
           tma_load_2d(sa + 2 * A_BYTES + B_BYTES, mB, full, t * BK, g->rowsB + n0);
         } else {
-          const int p = t / nkb, kb = t % nkb;
+          const int p = p0 + t / nkb, kb = t % nkb;
           tma_load_2d(sa, mA, full, kb * BK, (int)pl.a[p] * g->rowsA + m0);
           tma_load_2d(sa + A_BYTES, mB, full, kb * BK, (int)pl.b[p] * g->rowsB + n0);
         }
@@ -447,12 +457,12 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
     // ---------------- MMA issuer
     constexpr uint32_t idesc = idesc_bf16(BM, BN);
     uint32_t it = 0, lt = 0;
-    for (int tile = blockIdx.x; tile < total_tiles && !*abort_flag; tile += gridDim.x) {
-      const GroupDesc* g = groups + find_group(groups, ngroups, tile);
+    for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
+      const GroupDesc* g = groups + find_group(groups, ngroups, unit_tile(u));
       const int* skip = g->ep.skip;
       if (skip != nullptr && (skip[0] | skip[1])) continue;
       const int nkb = (g->K + BK - 1) / BK;
-      for (int c = 0; c < nchunk && !*abort_flag; ++c) {
+      for (int c = unit_c0(u); c < unit_c1(u) && !*abort_flag; ++c) {
         const uint32_t buf = lt & 1, use = lt >> 1;
         if (!mbar_wait(smem_u32(&bars[2 * NS + 2 + buf]), (use & 1) ^ 1)) {
           *abort_flag = 1;
@@ -497,11 +507,12 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
     const int lane_base = (warp & 3) * 32;
     uint32_t lt = 0;
     bool failed = false;
-    for (int tile = blockIdx.x; tile < total_tiles && !failed; tile += gridDim.x) {
+    for (int u = blockIdx.x; u < total_units && !failed; u += gridDim.x) {
+      const int tile = unit_tile(u);
       const GroupDesc* g = groups + find_group(groups, ngroups, tile);
       const int* skip = g->ep.skip;
       if (skip != nullptr && (skip[0] | skip[1])) continue;
-      for (int c = 0; c < nchunk; ++c) {
+      for (int c = unit_c0(u); c < unit_c1(u); ++c) {
         const uint32_t buf = lt & 1, use = lt >> 1;
         const bool ok = !*abort_flag && mbar_wait(smem_u32(&bars[2 * NS + buf]), use & 1);
         if (!ok) {
@@ -511,7 +522,16 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         Epilogue ep = g->ep;
-        if (c > 0) ep.beta = 1.0;
+        if (upt > 1) {  // this chunk's FP32 sum, widened, into its slice of the partial buffer
+          ep.C = partial + (long)c * ep.M * ep.N;
+          ep.ldc = ep.N;
+          ep.split_cols = ep.N;
+          ep.split_stride = 0;
+          ep.alpha = 1.0;
+          ep.beta = 0.0;
+        } else if (c > 0) {
+          ep.beta = 1.0;
+        }
         const int local = tile - g->tile_begin, tiles_m = (ep.M + BM - 1) / BM;
         const int m0 = (local % tiles_m) * BM, n0 = (local / tiles_m) * BN;
         const int row = m0 + lane_base + lane;
@@ -541,15 +561,33 @@ template <bool FUSED>
 __global__ void __launch_bounds__(NTHREADS, 1)
 gemm_persistent_kernel(const GroupDesc* __restrict__ groups, int ngroups, int total_tiles,
                        const __grid_constant__ PairList pl, int* err) {
-  persistent_body<FUSED>(groups, ngroups, total_tiles, pl, err);
+  persistent_body<FUSED>(groups, ngroups, total_tiles, pl, err, nullptr);
 }
 
 // one GEMM, its descriptor (tensor maps included) in the kernel's parameter space
 template <bool FUSED>
 __global__ void __launch_bounds__(NTHREADS, 1)
 gemm_persistent_one_kernel(const __grid_constant__ GroupDesc g, int total_tiles, const __grid_constant__ PairList pl,
-                           int* err) {
-  persistent_body<FUSED>(&g, 1, total_tiles, pl, err);
+                           int* err, double* partial) {
+  persistent_body<FUSED>(&g, 1, total_tiles, pl, err, partial);
+}
+
+// C = beta C + alpha sum_c partial[c] (chunk order; the same float64 operations, in the same
+// order, as the in-kernel chunk epilogues)
+__global__ void chunk_reduce_kernel(const double* __restrict__ partial, int nchunk, Epilogue ep) {
+  const long count = (long)ep.M * ep.N;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < count; idx += (long)gridDim.x * blockDim.x) {
+    const long row = idx / ep.N, col = idx % ep.N;
+    const long blk = col / ep.split_cols;
+    double* p = ep.C + blk * ep.split_stride + row * ep.ldc + (col - blk * ep.split_cols);
+    const double a0 = partial[idx];
+    double acc;
+    if (ep.beta == 0.0) acc = (ep.alpha == 1.0) ? a0 : ep.alpha * a0;
+    else if (ep.beta == 1.0) acc = fma(ep.alpha, a0, *p);
+    else acc = fma(ep.beta, *p, ep.alpha * a0);
+    for (int c = 1; c < nchunk; ++c) acc = fma(ep.alpha, partial[(long)c * count + idx], acc);
+    *p = acc;
+  }
 }
 
 int sm_count() {
@@ -716,18 +754,31 @@ void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, 
 }
 
 void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K, const PairList& pl,
-                     const Epilogue& ep) {
+                     const Epilogue& ep, double* partial, long partial_capacity) {
   prepare_persistent();
   check_pairs(pl, A.slices, B.slices);
   const int tiles = tiles_of(ep);
   if (tiles <= 0 || K <= 0) return;
   const GroupDesc g = make_group(A, B, K, ep, 0);
-  const unsigned grid = (unsigned)std::min(tiles, sm_count());
-  if (is_split3(pl) && pl.nchunk <= 1 && A.slices >= 2 && B.slices >= 2)
-    gemm_persistent_one_kernel<true><<<grid, NTHREADS, SMEM_BYTES, st>>>(g, tiles, pl, ep.err);
+  const bool fused = is_split3(pl) && pl.nchunk <= 1 && A.slices >= 2 && B.slices >= 2;
+  // a GEMM of few tiles spreads its chunks over the SMs when scratch for them was given
+  const int nchunk = pl.nchunk > 0 ? pl.nchunk : 1;
+  const bool split = !fused && partial != nullptr && nchunk > 1 && 2 * tiles < sm_count() &&
+                     (long)nchunk * ep.M * ep.N <= partial_capacity && ep.skip == nullptr;
+  const int units = split ? tiles * nchunk : tiles;
+  const unsigned grid = (unsigned)std::min(units, sm_count());
+  if (fused)
+    gemm_persistent_one_kernel<true><<<grid, NTHREADS, SMEM_BYTES, st>>>(g, tiles, pl, ep.err, nullptr);
   else
-    gemm_persistent_one_kernel<false><<<grid, NTHREADS, SMEM_BYTES, st>>>(g, tiles, pl, ep.err);
+    gemm_persistent_one_kernel<false><<<grid, NTHREADS, SMEM_BYTES, st>>>(g, tiles, pl, ep.err,
+                                                                          split ? partial : nullptr);
   OMM_LAUNCH_CHECK();
+  if (split) {
+    const long count = (long)ep.M * ep.N;
+    const unsigned rb = (unsigned)std::min<long>((count + 255) / 256, 4L * sm_count());
+    chunk_reduce_kernel<<<rb, 256, 0, st>>>(partial, nchunk, ep);
+    OMM_LAUNCH_CHECK();
+  }
 }
 
 void gemm_grouped(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl) {

@@ -84,9 +84,11 @@ void prepare_persistent();
 // nonzero code if a bounded wait expired
 void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl,
                      int* err);
-// the same persistent kernel for one GEMM whose descriptor travels as a kernel parameter
+// the same persistent kernel for one GEMM whose descriptor travels as a kernel parameter.
+// partial (optional, partial_capacity doubles): scratch that lets a GEMM of few output tiles run
+// each chunk of its pair list on its own CTA and add the chunks afterwards, in chunk order.
 void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K, const PairList& pl,
-                     const Epilogue& ep);
+                     const Epilogue& ep, double* partial = nullptr, long partial_capacity = 0);
 void gemm_grouped(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl);
 
 // x (float64, rows x cols, ld_src) -> hi = bf16(x), lo = bf16(x - hi) (ld_dst);

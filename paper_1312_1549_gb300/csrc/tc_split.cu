@@ -42,7 +42,7 @@ void split_diff(cudaStream_t st, const double* src, const double* sub, long rows
 
 void split_transposed(cudaStream_t st, const double* src, long rows, long cols, long ld_src,
                       __nv_bfloat16* hi_t, __nv_bfloat16* lo_t, long ld_dst, const Scalars* sc) {
-  const long blocks = ((rows + 31) / 32) * ((cols + 31) / 32);
+  const long blocks = ((rows + 63) / 64) * ((cols + 31) / 32);
   split_t_kernel<<<(int)blocks, 256, 0, st>>>(src, rows, cols, ld_src, hi_t, lo_t, ld_dst, sc);
   OMM_LAUNCH_CHECK();
 }

@@ -65,3 +65,22 @@ def test_backward_matches_energy_density_matrix(solved):
     r = solved
     assert r["dH_equals_D"]
     assert np.abs(r["dS_rows"] + r["EDMstar_rows"]).max() <= 1e-7
+
+
+def test_sliced_preconditioner_inverse_at_si512():
+    """The mixed path's float64-class inverse of S + T/tau against the native float64 one, m = 6656."""
+    from paper_1312_1549_gb300 import build
+    build.build()
+    from paper_1312_1549_gb300 import solver as S
+    from synth import configs
+    p = configs.config2()
+    A = dev(p.S + p.T / p.tau)
+    P_native = S.spd_inverse(A)
+    P_sliced = S.spd_inverse(A, sliced=True)
+    assert torch.equal(P_sliced, P_sliced.T)
+    scale = P_native.abs().max().item()
+    assert (P_sliced - P_native).abs().max().item() <= 1e-11 * scale
+    rows = torch.from_numpy(np.random.default_rng(1).choice(p.m, size=128, replace=False)).cuda()
+    R = P_sliced[rows] @ A
+    R[torch.arange(128, device=R.device), rows] -= 1.0
+    assert R.abs().max().item() <= 1e-11

@@ -92,7 +92,10 @@ def test_mixed_solve_without_preconditioner(S, si64):
     assert np.abs(D.cpu().numpy() - ex["D"]).max() <= 1e-7
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (200, 300, 1000), (64, 1000, 6656), (130, 70, 16384)])
+# few output tiles: every chunk on its own CTA and a reduction; (1024, 4096, 2048): 128 tiles, chunks in
+# order on one CTA per tile
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (200, 300, 1000), (64, 1000, 6656), (130, 70, 16384),
+                                   (1024, 4096, 2048)])
 def test_gemm_emu_is_float64_class(S, M, N, K):
     """10 fixed-point slices: error within 2^-44 of |alpha||A||B|^T + |beta C| elementwise."""
     rng = np.random.default_rng(M * N + K)
@@ -127,3 +130,35 @@ def test_mixed_solve_with_native_certificate(S, si64):
     assert info["status"] == 0 and info["gmax"] < 1e-9
     assert abs(E - ex["E"]) / abs(ex["E"]) <= 1e-9
     assert np.abs(D.cpu().numpy() - ex["D"]).max() <= 1e-7
+
+
+# ---------------------------------------------------------------- float64-class preconditioner inverse
+# Every off-diagonal product of the recursive factorisation carries at most about 2^-44 of
+# |A||B| (10 slices, see test_gemm_emu_is_float64_class); with condition numbers near 10 the
+# residual P A - I stays within 1e-11, as for the native float64 path.
+@pytest.mark.parametrize("m", [1, 5, 64, 65, 128, 200, 333, 1000, 2500])
+def test_spd_inverse_sliced(S, m):
+    rng = np.random.default_rng(m)
+    X = rng.normal(size=(m, m))
+    A = X @ X.T / m + 0.5 * np.eye(m)
+    P = S.spd_inverse(dev(A), sliced=True).cpu().numpy()
+    assert np.array_equal(P, P.T)
+    assert np.abs(P @ A - np.eye(m)).max() <= 1e-11
+
+
+def test_spd_inverse_sliced_rejects_indefinite(S):
+    A = np.eye(200)
+    A[150, 150] = -1.0
+    from paper_1312_1549_gb300 import _native as N
+    with pytest.raises(N.OMMError) as e:
+        S.spd_inverse(dev(A), sliced=True)
+    assert e.value.status == 2
+
+
+def test_spd_inverse_sliced_preconditioner_matches_oracle(S):
+    from synth import configs
+    from oracle import omm
+    p = configs.silicon(k=(2, 2, 2), basis="DZP", seed=0)   # m = 832
+    P_ref = omm.preconditioner(p.S, p.T, p.tau)
+    P = S.spd_inverse(dev(p.S + p.T / p.tau), sliced=True).cpu().numpy()
+    assert np.abs(P - P_ref).max() <= 1e-11 * np.abs(P_ref).max()
