@@ -7,50 +7,58 @@
 namespace omm {
 namespace dev {
 
-// float64 -> bf16 with round-to-nearest-even, on the integer pipe. The float64
-// units of this GPU retire about two instructions per SM and clock, so format
-// conversions are done on the bits: for a result in the normal bf16 range the
-// 52-bit mantissa is rounded to 7 bits (ties to even; a carry moves into the
-// exponent, which also gives the overflow to infinity) and the exponent is
-// rebiased from 1023 to 127. Zeros keep their sign; everything else (bf16
-// subnormals, infinities, NaN) takes the library conversion.
+// float64 -> bf16 with round-to-nearest-even, entirely on the integer pipe. The
+// float64 units of this GPU retire about two instructions per SM and clock, and a
+// library conversion on a rarely taken branch still costs its float64 instructions
+// when the compiler predicates it, so every case is done on the bits: in the normal
+// bf16 range the 52-bit mantissa is rounded to 7 bits (ties to even; a carry moves
+// into the exponent, which also gives the overflow to infinity) and the exponent is
+// rebiased from 1023 to 127; below it the value is rounded to a multiple of the
+// smallest bf16 subnormal 2^-133; infinities stay infinite and NaNs become quiet NaNs.
 __device__ __forceinline__ unsigned short bf16_bits_rne(double x) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const unsigned long long mag = u & 0x7FFFFFFFFFFFFFFFull;
   const unsigned int sign = (unsigned int)(u >> 48) & 0x8000u;
-  if (mag == 0) return (unsigned short)sign;
   const unsigned int e = (unsigned int)(mag >> 52);
-  if (e < 1023u - 126u || e > 1023u + 127u) return __bfloat16_as_ushort(__double2bfloat16(x));
-  const unsigned long long r = mag + 0x00000FFFFFFFFFFFull + ((mag >> 45) & 1ull);  // 2^44 - 1 + lsb
-  const unsigned int em = (unsigned int)(r >> 45) - ((1023u - 127u) << 7);
-  return (unsigned short)(sign | em);
+  if (e >= 1023u - 126u && e <= 1023u + 127u) {
+    const unsigned long long r = mag + 0x00000FFFFFFFFFFFull + ((mag >> 45) & 1ull);  // 2^44 - 1 + lsb
+    return (unsigned short)(sign | ((unsigned int)(r >> 45) - ((1023u - 127u) << 7)));
+  }
+  if (e == 0x7FFu) return (unsigned short)(sign | 0x7F80u | ((mag << 12) != 0 ? 0x40u : 0u));
+  if (e > 1023u + 127u) return (unsigned short)(sign | 0x7F80u);
+  // |x| < 2^-126: x = M 2^(max(e,1) - 1075), in units of 2^-133 that is M >> (942 - max(e,1))
+  const unsigned long long M = (mag & 0x000FFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+  const int shift = 942 - (int)(e ? e : 1u);  // >= 46
+  if (shift >= 64) return (unsigned short)sign;
+  const unsigned long long q = M >> shift, rem = M & ((1ull << shift) - 1ull), half = 1ull << (shift - 1);
+  const unsigned long long r = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+  return (unsigned short)(sign | (unsigned int)r);
 }
 
-// the float64 value of a finite bf16 (exact; integer pipe)
+// the float64 value of a bf16 (exact; integer pipe)
 __device__ __forceinline__ double bf16_bits_to_double(unsigned short b) {
   const unsigned long long sign = (unsigned long long)(b & 0x8000u) << 48;
-  const unsigned int e = (b >> 7) & 0xFFu;
-  if (e == 0) {
-    if ((b & 0x7Fu) == 0) return __longlong_as_double((long long)sign);  // signed zero
-    return (double)__bfloat162float(__ushort_as_bfloat16(b));             // subnormal
+  const unsigned int e = (b >> 7) & 0xFFu, f = b & 0x7Fu;
+  unsigned long long bits;
+  if (e == 0xFFu) {
+    bits = sign | (0x7FFull << 52) | ((unsigned long long)f << 45);
+  } else if (e != 0) {
+    bits = sign | ((unsigned long long)(e - 127u + 1023u) << 52) | ((unsigned long long)f << 45);
+  } else if (f == 0) {
+    bits = sign;
+  } else {  // subnormal: f 2^-133 with the top bit of f at position p
+    const int p = 31 - __clz(f);
+    bits = sign | ((unsigned long long)(p - 133 + 1023) << 52) |
+           (((unsigned long long)f << (52 - p)) & 0x000FFFFFFFFFFFFFull);
   }
-  const unsigned long long bits = sign | ((unsigned long long)(e - 127u + 1023u) << 52) |
-                                  ((unsigned long long)(b & 0x7Fu) << 45);
   return __longlong_as_double((long long)bits);
 }
 
-// hi = bf16(x), lo = bf16(x - hi), both rounded to nearest even; one float64 add
+// hi = bf16(x), lo = bf16(x - hi), both rounded to nearest even; one float64 subtraction
 __device__ __forceinline__ void split_store(double x, __nv_bfloat16* hi, __nv_bfloat16* lo, long off) {
   const unsigned short h = bf16_bits_rne(x);
   hi[off] = __ushort_as_bfloat16(h);
-  if (lo) {
-    const unsigned int he = (h >> 7) & 0xFFu;
-    // x - hi is exact in float64; an infinite or NaN hi keeps the library path
-    const unsigned short l = (he == 0xFFu) ? __bfloat16_as_ushort(__double2bfloat16(x - (double)__bfloat162float(
-                                                 __ushort_as_bfloat16(h))))
-                                           : bf16_bits_rne(x - bf16_bits_to_double(h));
-    lo[off] = __ushort_as_bfloat16(l);
-  }
+  if (lo) lo[off] = __ushort_as_bfloat16(bf16_bits_rne(x - bf16_bits_to_double(h)));  // x - hi is exact
 }
 
 // hi/lo of two neighbouring elements, stored as bf16 pairs

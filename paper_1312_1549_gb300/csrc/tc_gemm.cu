@@ -139,16 +139,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // float -> float64 on the integer pipe (exact): the float64 units of this GPU
 // retire about two instructions per SM and clock, so the epilogue widens the
 // FP32 accumulator by rebiasing the exponent (127 -> 1023) and shifting the
-// mantissa; zeros keep their sign, subnormals/infinities/NaN take the
-// hardware conversion.
+// mantissa; zeros keep their sign, subnormals are normalised, infinities and
+// NaNs keep their class.
 __device__ __forceinline__ double widen(float f) {
   const unsigned int u = __float_as_uint(f);
-  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned int e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
   const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-  if ((u & 0x7FFFFFFFu) == 0) return __longlong_as_double((long long)sign);
-  if (e == 0 || e == 0xFFu) return (double)f;
-  return __longlong_as_double((long long)(sign | ((unsigned long long)(e + (1023u - 127u)) << 52) |
-                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+  unsigned long long bits;
+  if (e != 0 && e != 0xFFu) {
+    bits = sign | ((unsigned long long)(e + (1023u - 127u)) << 52) | ((unsigned long long)m << 29);
+  } else if (e == 0xFFu) {
+    bits = sign | (0x7FFull << 52) | ((unsigned long long)m << 29);
+  } else if (m == 0) {
+    bits = sign;
+  } else {  // subnormal: m 2^-149 with its top bit at position p
+    const int p = 31 - __clz(m);
+    bits = sign | ((unsigned long long)(p - 149 + 1023) << 52) |
+           (((unsigned long long)m << (52 - p)) & 0x000FFFFFFFFFFFFFull);
+  }
+  return __longlong_as_double((long long)bits);
 }
 
 // C = alpha * v + beta * C for the 32 accumulator columns [col0, col0 + 32) of one row.
