@@ -12,6 +12,7 @@
 // itself out through its device flags, so the graph never changes. The host
 // polls all status words with one copy every `check_every` replays and runs
 // the per-instance refreshes (float64-class) and certificates (float64).
+#include "fused_device.cuh"
 #include "iter_device.cuh"
 #include "omm_ctx.cuh"
 #include "split_device.cuh"
@@ -42,7 +43,9 @@ struct IterArgs {
   long ldm, ld4;
 };
 
-enum SplitJob { kSplitG = 0, kSplitD, kSplitHDSD, kSplitHCSC, kSplitW };
+// the splits that no producing kernel writes: G (before P G), [HD; SD] (after the GEMM) and
+// [dS_W | dH_W] = [S_W | H_W] - W_ref
+enum SplitJob { kSplitG = 0, kSplitHDSD, kSplitW };
 
 __global__ void __launch_bounds__(256) b_split_kernel(const IterArgs* __restrict__ A, int job) {
   const IterArgs& a = A[blockIdx.y];
@@ -52,15 +55,9 @@ __global__ void __launch_bounds__(256) b_split_kernel(const IterArgs* __restrict
     case kSplitG:
       dev::split_body(a.G, nullptr, n, m, m, a.G_hi, a.G_hi + n * a.ldm, a.ldm, blockIdx.x, gridDim.x);
       break;
-    case kSplitD:
-      dev::split_body(a.Dir, nullptr, n, m, m, a.D_hi, a.D_hi + n * a.ldm, a.ldm, blockIdx.x, gridDim.x);
-      break;
     case kSplitHDSD:
       dev::split_body(a.Y4 + 2 * a.nm, nullptr, 2 * n, m, m, a.Y_hi + 2 * n * a.ldm, a.Y_hi + 6 * n * a.ldm,
                       a.ldm, blockIdx.x, gridDim.x);
-      break;
-    case kSplitHCSC:
-      dev::split_body(a.Y4, nullptr, 2 * n, m, m, a.Y_hi, a.Y_hi + 4 * n * a.ldm, a.ldm, blockIdx.x, gridDim.x);
       break;
     default:
       dev::split_body(a.SWHW, a.Wref, n, 2 * n, 2 * n, a.W_hi, a.W_hi + n * a.ld4, a.ld4, blockIdx.x, gridDim.x);
@@ -90,9 +87,11 @@ __global__ void __launch_bounds__(dev::TB) b_control_direction_kernel(const Iter
   dev::control_direction_body(a.sc, a.part, 1, kBatchReduceBlocks, 0, 1);
 }
 
+// Delta and its split (the operand of the next two products)
 __global__ void __launch_bounds__(256) b_direction_kernel(const IterArgs* __restrict__ A) {
   const IterArgs& a = A[blockIdx.y];
-  dev::direction_body(a.nm, a.PG, a.Dir, a.sc, blockIdx.x, gridDim.x);
+  dev::direction_split_body(a.n, a.m, a.PG, a.Dir, a.D_hi, a.D_hi + (long)a.n * a.ldm, a.ldm, a.sc, blockIdx.x,
+                            gridDim.x);
 }
 
 __global__ void __launch_bounds__(256) b_copy_gradient_kernel(const IterArgs* __restrict__ A) {
@@ -111,10 +110,11 @@ __global__ void __launch_bounds__(dev::TB) b_control_linesearch_kernel(const Ite
   dev::control_linesearch_body(a.sc, a.part2, a.tiles, 0, 1);
 }
 
+// the state update and the split of the new [HC; SC]
 __global__ void __launch_bounds__(256) b_update_state_kernel(const IterArgs* __restrict__ A) {
   const IterArgs& a = A[blockIdx.y];
-  dev::update_state_mixed_body(a.n, a.m, a.C, a.Y4, a.Dir, a.G, a.Gold, a.dY, a.Gref, a.sc, blockIdx.x,
-                               gridDim.x);
+  dev::update_state_split_body(a.n, a.m, a.C, a.Y4, a.Dir, a.G, a.Gold, a.dY, a.Gref, a.Y_hi,
+                               a.Y_hi + 4L * a.n * a.ldm, a.ldm, a.sc, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(dev::TB) b_update_subspace_kernel(const IterArgs* __restrict__ A) {
@@ -231,9 +231,7 @@ void enqueue_line_search(omm_batch* b) {
   OMM_LAUNCH_CHECK();
   b_control_direction_kernel<<<dim3(1, cnt), dev::TB, 0, st>>>(b->args);
   OMM_LAUNCH_CHECK();
-  b_direction_kernel<<<vec_grid, 256, 0, st>>>(b->args);
-  OMM_LAUNCH_CHECK();
-  b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitD);
+  b_direction_kernel<<<rows_grid, 256, 0, st>>>(b->args);
   OMM_LAUNCH_CHECK();
   timed_gemm(b, b->gHD, pl);
   b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitHDSD);
@@ -243,9 +241,7 @@ void enqueue_line_search(omm_batch* b) {
   OMM_LAUNCH_CHECK();
   b_control_linesearch_kernel<<<dim3(1, cnt), dev::TB, 0, st>>>(b->args);
   OMM_LAUNCH_CHECK();
-  b_update_state_kernel<<<vec_grid, 256, 0, st>>>(b->args);
-  OMM_LAUNCH_CHECK();
-  b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitHCSC);
+  b_update_state_kernel<<<rows_grid, 256, 0, st>>>(b->args);
   OMM_LAUNCH_CHECK();
   b_split_t_kernel<<<dim3(b->max_ttiles, cnt), 256, 0, st>>>(b->args, 0);
   OMM_LAUNCH_CHECK();

@@ -7,6 +7,7 @@
 // reproducible from run to run.
 #include "omm_internal.cuh"
 #include "iter_device.cuh"
+#include "fused_device.cuh"
 
 namespace omm {
 namespace {
@@ -279,6 +280,37 @@ void launch_control_linesearch(cudaStream_t st, Scalars* sc, const double* part,
 void launch_update_state(cudaStream_t st, int n, long m, double* C, double* Y4, const double* Dir,
                          double* G, double* Gold, const Scalars* sc) {
   update_state_kernel<<<grid_for((long)n * m), TB, 0, st>>>(n, m, C, Y4, Dir, G, Gold, sc);
+  OMM_LAUNCH_CHECK();
+}
+namespace {
+__global__ void __launch_bounds__(256)
+direction_split_kernel(long n, long m, const double* __restrict__ PG, double* __restrict__ Dir,
+                       __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo, long ldm, const Scalars* sc) {
+  dev::direction_split_body(n, m, PG, Dir, hi, lo, ldm, sc, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(256)
+update_state_split_kernel(long n, long m, double* C, double* Y4, const double* Dir, double* G, double* Gold,
+                          double* dY, const double* Gref, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, long ldm,
+                          const Scalars* sc) {
+  dev::update_state_split_body(n, m, C, Y4, Dir, G, Gold, dY, Gref, Yhi, Ylo, ldm, sc, blockIdx.x, gridDim.x);
+}
+}  // namespace
+
+// one block per (row, 256 column pairs) unit, at most 16384 blocks
+static unsigned pair_grid(long rows, long cols) {
+  const long units = rows * (((cols + 1) / 2 + 255) / 256);
+  return (unsigned)(units < 1 ? 1 : (units > 16384 ? 16384 : units));
+}
+
+void launch_direction_split(cudaStream_t st, long n, long m, const double* PG, double* Dir, __nv_bfloat16* hi,
+                            __nv_bfloat16* lo, long ldm, const Scalars* sc) {
+  direction_split_kernel<<<pair_grid(n, m), 256, 0, st>>>(n, m, PG, Dir, hi, lo, ldm, sc);
+  OMM_LAUNCH_CHECK();
+}
+void launch_update_state_split(cudaStream_t st, long n, long m, double* C, double* Y4, const double* Dir, double* G,
+                               double* Gold, double* dY, const double* Gref, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo,
+                               long ldm, const Scalars* sc) {
+  update_state_split_kernel<<<pair_grid(n, m), 256, 0, st>>>(n, m, C, Y4, Dir, G, Gold, dY, Gref, Yhi, Ylo, ldm, sc);
   OMM_LAUNCH_CHECK();
 }
 void launch_update_state_mixed(cudaStream_t st, int n, long m, double* C, double* Y4, const double* Dir,

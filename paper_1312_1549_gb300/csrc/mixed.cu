@@ -247,8 +247,7 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   }
   launch_grad_reduce(st, nm, G, PG, Gold, Dir, part, sc);
   launch_control_direction(st, sc, part, 1);
-  launch_direction(st, nm, PG, Dir, sc);
-  tc::split(st, Dir, n, m, m, ms->D_hi, ms->D_lo, ms->ldm, sc);
+  launch_direction_split(st, n, m, PG, Dir, ms->D_hi, ms->D_lo, ms->ldm, sc);
   // [H~ D ; S D] (n x m layout): one GEMM over the stacked [H~; S]
   pf.begin(st);
   run_plan(ms, st, kPlanHD);
@@ -260,8 +259,7 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   pf.end(st, 8.0 * np * n * (double)n * m);
   launch_traces(st, n, SWHW, Proj, part2, sc);
   launch_control_linesearch(st, sc, part2, traces_blocks(n));
-  launch_update_state_mixed(st, n, m, C, Y4, Dir, G, Gold, ms->dY, ms->Gref, sc);
-  tc::split(st, Y4, 2L * n, m, m, ms->Y_hi, ms->Y_lo, ms->ldm, sc);
+  launch_update_state_split(st, n, m, C, Y4, Dir, G, Gold, ms->dY, ms->Gref, ms->Y_hi, ms->Y_lo, ms->ldm, sc);
   tc::split_transposed(st, Y4, 2L * n, m, m, ms->YT_hi, ms->YT_lo, ms->ld2n, sc);
   tc::split_transposed(st, ms->dY, 2L * n, m, m, ms->YT_hi + 2L * n, ms->YT_lo + 2L * n, ms->ld2n, sc);
   launch_update_subspace(st, n, SWHW, Proj, sc);

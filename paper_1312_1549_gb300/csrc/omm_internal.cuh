@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of the OMM library.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
@@ -127,6 +128,13 @@ void launch_grad_reduce(cudaStream_t st, long count, const double* G, const doub
                         const double* Gold, const double* Dir, double* part, const Scalars* sc);
 void launch_control_direction(cudaStream_t st, Scalars* sc, const double* part, int mixed);
 void launch_direction(cudaStream_t st, long count, const double* PG, double* Dir, const Scalars* sc);
+// the mixed path's fused forms: the direction (n x m) and its bf16 split (leading dimension ldm);
+// the state update and the split of the new [HC; SC] into Yhi/Ylo
+void launch_direction_split(cudaStream_t st, long n, long m, const double* PG, double* Dir, __nv_bfloat16* hi,
+                            __nv_bfloat16* lo, long ldm, const Scalars* sc);
+void launch_update_state_split(cudaStream_t st, long n, long m, double* C, double* Y4, const double* Dir, double* G,
+                               double* Gold, double* dY, const double* Gref, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo,
+                               long ldm, const Scalars* sc);
 void launch_traces(cudaStream_t st, int n, const double* SWHW, const double* Proj, double* part,
                    const Scalars* sc);
 int traces_blocks(int n);

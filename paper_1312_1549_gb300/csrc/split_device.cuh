@@ -70,36 +70,44 @@ __device__ __forceinline__ void split_store2(double x0, double x1, __nv_bfloat16
   if (lo) *reinterpret_cast<__nv_bfloat162*>(lo + off) = __halves2bfloat162(l[0], l[1]);
 }
 
-// rows handled by blocks bx, bx + nbx, ...; the block's threads stride over columns,
-// two columns at a time (16-byte loads, 4-byte stores) where the row is aligned for it
+// Work units of the row-wise vector kernels: (row, run of blockDim.x column pairs); unit u of
+// block bx, bx + nbx, ... Every thread takes one column pair (16-byte float64 loads, 4-byte bf16
+// stores) and issues its loads at once, so that many loads are in flight per SM.
+__device__ __forceinline__ long pair_units(long rows, long cols) {
+  const long npair = (cols + 1) / 2;
+  return rows * ((npair + blockDim.x - 1) / blockDim.x);
+}
+__device__ __forceinline__ void unit_pos(long u, long cols, long& row, long& col) {
+  const long npair = (cols + 1) / 2, nseg = (npair + blockDim.x - 1) / blockDim.x;
+  row = u / nseg;
+  col = 2 * ((u - row * nseg) * blockDim.x + threadIdx.x);
+}
+
+// hi/lo of (src - sub) (sub may be null), rows x cols, by column pairs
 __device__ __forceinline__ void split_body(const double* __restrict__ src, const double* __restrict__ sub,
                                            long rows, long cols, long ld_src, __nv_bfloat16* __restrict__ hi,
                                            __nv_bfloat16* __restrict__ lo, long ld_dst, int bx, int nbx) {
-  for (long r = bx; r < rows; r += nbx) {
-    const double* s = src + r * ld_src;
-    const double* u = sub ? sub + r * ld_src : nullptr;
-    __nv_bfloat16* h = hi + r * ld_dst;
-    __nv_bfloat16* l = lo ? lo + r * ld_dst : nullptr;
-    const bool vec = ((reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(u)) & 15) == 0 &&
-                     ((reinterpret_cast<uintptr_t>(h) | reinterpret_cast<uintptr_t>(l)) & 3) == 0;
-    long c0 = 0;
+  const long units = pair_units(rows, cols);
+  for (long u = bx; u < units; u += nbx) {
+    long r, c;
+    unit_pos(u, cols, r, c);
+    if (c >= cols) continue;
+    const double* s = src + r * ld_src + c;
+    const double* w = sub ? sub + r * ld_src + c : nullptr;
+    const long off = r * ld_dst + c;
+    const bool vec = c + 1 < cols && ((reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(w)) & 15) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(hi + off) | reinterpret_cast<uintptr_t>(lo ? lo + off : nullptr)) &
+                      3) == 0;
     if (vec) {
-      const long npair = cols / 2;
-#pragma unroll 4
-      for (long q = threadIdx.x; q < npair; q += blockDim.x) {
-        double2 x = reinterpret_cast<const double2*>(s)[q];
-        if (u) {
-          const double2 y = reinterpret_cast<const double2*>(u)[q];
-          x.x -= y.x;
-          x.y -= y.y;
-        }
-        split_store2(x.x, x.y, h, l, 2 * q);
+      double2 x = *reinterpret_cast<const double2*>(s);
+      if (w) {
+        const double2 y = *reinterpret_cast<const double2*>(w);
+        x.x -= y.x;
+        x.y -= y.y;
       }
-      c0 = 2 * npair;
-    }
-    for (long c = c0 + threadIdx.x; c < cols; c += blockDim.x) {
-      const double x = u ? s[c] - u[c] : s[c];
-      split_store(x, h, l, c);
+      split_store2(x.x, x.y, hi, lo, off);
+    } else {
+      for (int k = 0; k < 2 && c + k < cols; ++k) split_store(w ? s[k] - w[k] : s[k], hi, lo, off + k);
     }
   }
 }

@@ -160,13 +160,20 @@ __device__ __forceinline__ double widen(float f) {
   return __longlong_as_double((long long)bits);
 }
 
+// alpha a + beta c in float64 (the same operations on every path)
+__device__ __forceinline__ double combine(const Epilogue& ep, double a, const double* c) {
+  if (ep.beta == 0.0) return ep.alpha == 1.0 ? a : ep.alpha * a;
+  if (ep.beta == 1.0) return fma(ep.alpha, a, *c);
+  return fma(ep.beta, *c, ep.alpha * a);
+}
+
 // C = alpha * v + beta * C for the 32 accumulator columns [col0, col0 + 32) of one row.
 __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col0, const float (&v)[32]) {
   if (row >= ep.M || col0 >= ep.N) return;
   const int nvalid = min(32, ep.N - col0);
   const long blk0 = col0 / ep.split_cols;
   const long blk1 = (col0 + nvalid - 1) / ep.split_cols;
-  if (blk0 == blk1) {
+  if (blk0 == blk1) {  // specialised loops, no per-element branching
     double* base = ep.C + blk0 * ep.split_stride + (long)row * ep.ldc + (col0 - blk0 * ep.split_cols);
     if (ep.beta == 0.0) {
       if (ep.alpha == 1.0) {
@@ -195,8 +202,7 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
     const int col = col0 + j;
     const long blk = col / ep.split_cols;
     double* p = ep.C + blk * ep.split_stride + (long)row * ep.ldc + (col - blk * ep.split_cols);
-    const double a = ep.alpha * widen(v[j]);
-    *p = (ep.beta == 0.0) ? a : fma(ep.beta, *p, a);
+    *p = combine(ep, widen(v[j]), p);
   }
 }
 

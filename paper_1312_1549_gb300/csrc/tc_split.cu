@@ -26,16 +26,22 @@ __global__ void split_t_kernel(const double* __restrict__ src, long rows, long c
 
 }  // namespace
 
+// one block per (row, 256 column pairs) unit, at most 16384 blocks
+static long pair_grid(long rows, long cols) {
+  const long units = rows * (((cols + 1) / 2 + 255) / 256);
+  return units < 1 ? 1 : (units > 16384 ? 16384 : units);
+}
+
 void split(cudaStream_t st, const double* src, long rows, long cols, long ld_src, __nv_bfloat16* hi,
            __nv_bfloat16* lo, long ld_dst, const Scalars* sc) {
-  const long g = rows < 8192 ? (rows > 0 ? rows : 1) : 8192;
+  const long g = pair_grid(rows, cols);
   split_kernel<<<(int)g, 256, 0, st>>>(src, nullptr, rows, cols, ld_src, hi, lo, ld_dst, sc);
   OMM_LAUNCH_CHECK();
 }
 
 void split_diff(cudaStream_t st, const double* src, const double* sub, long rows, long cols, long ld_src,
                 __nv_bfloat16* hi, __nv_bfloat16* lo, long ld_dst, const Scalars* sc) {
-  const long g = rows < 8192 ? (rows > 0 ? rows : 1) : 8192;
+  const long g = pair_grid(rows, cols);
   split_kernel<<<(int)g, 256, 0, st>>>(src, sub, rows, cols, ld_src, hi, lo, ld_dst, sc);
   OMM_LAUNCH_CHECK();
 }
