@@ -33,8 +33,9 @@ WORKLOADS = {
        "eta=HOMO+0.1 Ha, |G|inf<1e-9",
     3: "water256_dzp: 256 H2O at 1 g/cm3, DZP-like 23 orbitals/molecule, m=5888, n=1024, tau=5 Ha, "
        "eta=HOMO+0.1 Ha, |G|inf<1e-9",
-    4: "batch64: 64 independent Si DZP-like / water instances, m ~ U[512,4096], n/m 0.15-0.17, "
-       "one batched solve (grouped tensor-core launches in a CUDA graph), |G|inf<1e-9 each",
+    4: "batch64: 64 independent Si / water instances (DZ, TZ, DZP, DZP+p / DZ+d, DZP, TZP bases), "
+       "m ~ U[512,4096], n/m 0.125-0.25, one batched solve (grouped tensor-core launches in a CUDA graph), "
+       "|G|inf<1e-9 each",
     5: "si4096_sz_warmstart: Si 4096-atom single-zeta, m=16384, n=8192, 10 Hamiltonians "
        "H_k = H_0 + k delta (on-site, sigma 0.01 Ha), each solve from the previous C, dE/dH each step",
 }
@@ -230,6 +231,7 @@ def run_batch(args):
                 "s_create_wall": statistics.mean(t[0] for t in timed),
                 "s_solve_wall": statistics.mean(t[1] for t in timed),
                 "ms_line_search_graphs": infos[0]["ms_iterate"],
+                "tile_width_autotuned": infos[0]["tile_width"],
                 "ms_refresh_sum": sum(i["ms_refine"] - i["ms_certify"] for i in infos),
                 "ms_certify_sum": sum(i["ms_certify"] for i in infos),
                 "gpu_launches": launches, "clocks": clk.summary(),
@@ -303,6 +305,7 @@ def run_sequence(args):
         step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = S.launch_count()
     with ClockSampler(0) as clk:
         e0.record(stream)
         for _ in range(args.steps):
@@ -314,7 +317,11 @@ def run_sequence(args):
     out = _base_line(args, ms * 1e-3)
     out["config"]["certificate"] = "native float64" if args.native_certificate else "float64-class (sliced)"
     out.update({"line_searches": [i["iterations"] for _, i in infos], "E": [E for E, _ in infos],
-                "gmax": max(i["gmax"] for _, i in infos), "clocks": clk.summary()})
+                "gmax": max(i["gmax"] for _, i in infos), "status": [i["status"] for _, i in infos],
+                "ms_setup": infos[0][1]["ms_setup"], "ms_precond": infos[0][1]["ms_precond"],
+                "ms_iterate": [i["ms_iterate"] for _, i in infos],
+                "ms_refine": [i["ms_refine"] for _, i in infos],
+                "gpu_launches": launches, "clocks": clk.summary()})
     print(json.dumps(out), flush=True)
     return 0
 
@@ -422,6 +429,7 @@ def main():
            "E": energies[-1], "gmax": infos[-1]["gmax"],
            "ms_setup": statistics.mean(i["ms_setup"] for i in infos),
            "ms_precond": statistics.mean(i["ms_precond"] for i in infos),
+           "tile_width_autotuned": infos[-1]["tile_width"],
            "ms_iterate": it_ms, "ms_refine": statistics.mean(i["ms_refine"] for i in infos),
            "ms_certify": statistics.mean(i["ms_certify"] for i in infos),
            "ms_outputs": statistics.mean(i["ms_outputs"] for i in infos),

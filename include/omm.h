@@ -112,6 +112,9 @@ typedef struct {
   double main_gemm_flop;     /* with opts.profile: flops they issued (tensor-core flops when mixed) */
   double ms_certify;         /* native float64 state recomputes (part of ms_refine) */
   double ms_precond;         /* the float64 Cholesky inverse P = (S + T/tau)^-1 (part of ms_setup) */
+  int tile_width[4];         /* mixed: output tile width (256 or 128 columns) the autotuner chose for
+                                the P G, [H D; S D], projection and gradient GEMMs (0: not run) */
+  double ms_autotune;        /* time the autotuner spent timing candidates (0 when cached) */
   double ms_batch;           /* omm_solve_batched only: the whole batched solve. There ms_iterate,
                                 ms_main_gemm, main_gemm_launches and main_gemm_flop are batch
                                 totals too (the same in every instance's report) */

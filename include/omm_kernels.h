@@ -67,6 +67,12 @@ omm_status omm_kernel_quartic_coefficients(int n, const double* SWHW, const doub
  * product), npass = 1 only A_hi B_hi. Scratch for the splits is allocated and
  * freed inside the call. Errors: OMM_ERR_ARG, OMM_ERR_OOM, OMM_ERR_TIMEOUT
  * (a bounded device wait expired), OMM_ERR_CUDA. */
+/* The same contraction with a chosen output tile width: tile_n = 256 (128 x 256 tiles, what
+ * omm_kernel_gemm_tc uses) or 128 (128 x 128 tiles), the two widths the solver's autotuner picks
+ * from. OMM_ERR_ARG for any other tile_n. */
+omm_status omm_kernel_gemm_tc_tiled(int M, int N, int K, const double* A, const double* B, double alpha,
+                                    double beta, double* C, int npass, int tile_n, void* stream);
+
 omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double* B, double alpha,
                               double beta, double* C, int npass, void* stream);
 

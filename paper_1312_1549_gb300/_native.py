@@ -34,10 +34,15 @@ class OmmInfo(ct.Structure):
                 ("gemm_flop_tc", ct.c_double), ("kernel_launches", ct.c_double),
                 ("ms_main_gemm", ct.c_double), ("main_gemm_launches", ct.c_double),
                 ("main_gemm_flop", ct.c_double), ("ms_certify", ct.c_double),
-                ("ms_precond", ct.c_double), ("ms_batch", ct.c_double)]
+                ("ms_precond", ct.c_double),
+                ("tile_width", ct.c_int * 4), ("ms_autotune", ct.c_double), ("ms_batch", ct.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if isinstance(v, ct.Array) else v
+        return out
 
 
 class OMMError(RuntimeError):
@@ -69,6 +74,7 @@ _SIGNATURES = {
     "omm_kernel_dgemm": (_I, [_I, _I, _I, _I, _I, _D, _P, _L, _P, _L, _D, _P, _L, _P]),
     "omm_kernel_spd_inverse": (_I, [_I, _P, _P, ct.POINTER(_I), _P]),
     "omm_kernel_spd_inverse_sliced": (_I, [_I, _P, _P, ct.POINTER(_I), _P]),
+    "omm_kernel_gemm_tc_tiled": (_I, [_I, _I, _I, _P, _P, ct.c_double, ct.c_double, _P, _I, _I, _P]),
     "omm_kernel_line_minimum": (_I, [ct.POINTER(_D), ct.POINTER(_D)]),
     "omm_kernel_quartic_coefficients": (_I, [_I, _P, _P, _D, ct.POINTER(_D), _P]),
     "omm_kernel_gemm_tc": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _P]),

@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(dev::TB) b_update_subspace_kernel(const IterAr
 struct Grouped {
   tc::GroupDesc* dev = nullptr;
   int ngroups = 0, tiles = 0;
+  int bn = 256;  // output tile width chosen by the autotuner
 };
 
 constexpr int kGroupedGemms = 4;
@@ -165,6 +166,8 @@ struct omm_batch {
   // the grouped GEMMs (PG, [HD; SD], projections, gradient) are timed with CUDA events
   bool profile = false;
   Profiler prof;
+  int tile_width[4] = {256, 256, 256, 256};  // autotuned widths of the P G, [HD; SD], projection, G GEMMs
+  double ms_autotune = 0.0;
   // refreshes and certificates of different instances run concurrently on these
   cudaStream_t pool[kRefreshStreams] = {};
   std::vector<double> gemm_flop[kGroupedGemms];  // issued flops of each instance's group
@@ -201,14 +204,15 @@ void batch_destroy(omm_batch* b) {
 void upload_groups(cudaStream_t st, Grouped* g, const std::vector<tc::GroupDesc>& v) {
   g->ngroups = (int)v.size();
   if (v.empty()) return;
-  g->tiles = v.back().tile_begin + tc::tiles_of(v.back().ep);
+  g->tiles = v.back().tile_begin + tc::tiles_of(v.back().ep, v.back().bn);
+  g->bn = v.back().bn;
   alloc(&g->dev, v.size());
   OMM_CUDA_TRY(cudaMemcpyAsync(g->dev, v.data(), v.size() * sizeof(tc::GroupDesc), cudaMemcpyHostToDevice, st));
 }
 
 void timed_gemm(omm_batch* b, const Grouped& g, const tc::PairList& pl) {
   b->prof.begin(b->st);
-  tc::gemm_persistent(b->st, g.dev, g.ngroups, g.tiles, pl, b->err);
+  tc::gemm_persistent(b->st, g.dev, g.ngroups, g.tiles, pl, b->err, g.bn);
   b->prof.end(b->st, 0.0);
 }
 
@@ -330,6 +334,7 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
     OMM_CUDA_TRY(cudaMallocHost((void**)&b->sc_host_all, count * sizeof(Scalars)));
     std::vector<IterArgs> args(count);
     std::vector<tc::GroupDesc> gpg, ghd, gpr, gg;
+    std::vector<tc::GemmSpec> spg, shd, spr, sg;
     for (int i = 0; i < count; ++i) {
       omm_ctx* c = b->ctx[i];
       cudaFree(c->sc);
@@ -355,14 +360,14 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       const int* skip = &c->sc->done;
       if (b->precond) {
         tc::Epilogue e{c->PG, mi, mi, 0, 1.0, 0.0, ni, mi, skip, v.err};
-        gpg.push_back(tc::make_group(*v.opG, *v.opP, mi, e, 0));
+        spg.push_back(tc::GemmSpec{v.opG, v.opP, mi, e});
       }
       tc::Epilogue ehd{c->Y4 + 2 * nm, mi, mi, nm, 1.0, 0.0, ni, 2 * mi, skip, v.err};
-      ghd.push_back(tc::make_group(*v.opD, *v.opHS, mi, ehd, 0));
+      shd.push_back(tc::GemmSpec{v.opD, v.opHS, mi, ehd});
       tc::Epilogue epr{c->Proj, 4L * ni, 4L * ni, 0, 1.0, 0.0, ni, 4 * ni, skip, v.err};
-      gpr.push_back(tc::make_group(*v.opD, *v.opY, mi, epr, 0));
+      spr.push_back(tc::GemmSpec{v.opD, v.opY, mi, epr});
       tc::Epilogue eg{c->G, mi, mi, 0, -4.0, 1.0, ni, mi, skip, v.err};
-      gg.push_back(tc::make_group(*v.opW, *v.opYT, 4 * ni, eg, 0));
+      sg.push_back(tc::GemmSpec{v.opW, v.opYT, 4 * ni, eg});
       // issued tensor flops, 3 x 2 M N K (3-term split), of this instance's share of each GEMM
       const double issued = 3.0 * 2.0 * ni;  // x N x K
       b->gemm_flop[0].push_back(b->precond ? issued * mi * mi : 0.0);
@@ -373,16 +378,25 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       b->max_tiles = std::max(b->max_tiles, a.tiles);
       b->max_ttiles = std::max(b->max_ttiles, (int)(((2L * ni + 63) / 64) * ((mi + 31) / 32)));
     }
-    // Longest tiles first: a persistent CTA takes tiles b, b + grid, ..., so ordering the groups
-    // by falling contraction length spreads the long tiles over all SMs before the short ones
-    // fill in (the largest-processing-time-first rule)
-    for (auto* gv : {&gpg, &ghd, &gpr, &gg}) {
-      std::stable_sort(gv->begin(), gv->end(),
+    // Tile width of each grouped GEMM from the autotuner (timed once per batch shape in a
+    // process); then longest tiles first: a persistent CTA takes tiles b, b + grid, ..., so
+    // ordering the groups by falling contraction length spreads the long tiles over all SMs
+    // before the short ones fill in (the largest-processing-time-first rule)
+    const std::vector<tc::GemmSpec>* specs[4] = {&spg, &shd, &spr, &sg};
+    std::vector<tc::GroupDesc>* groups[4] = {&gpg, &ghd, &gpr, &gg};
+    for (int k = 0; k < 4; ++k) {
+      if (specs[k]->empty()) continue;
+      double ms_tune = 0.0;
+      const int bn = tc::choose_tile_width(b->st, *specs[k], tc::pairs_split3(), &ms_tune);
+      b->ms_autotune += ms_tune;
+      b->tile_width[k] = bn;
+      for (const tc::GemmSpec& sp : *specs[k]) groups[k]->push_back(tc::make_group(*sp.A, *sp.B, sp.K, sp.ep, 0, bn));
+      std::stable_sort(groups[k]->begin(), groups[k]->end(),
                        [](const tc::GroupDesc& x, const tc::GroupDesc& y) { return x.K > y.K; });
       int t = 0;
-      for (tc::GroupDesc& g : *gv) {
+      for (tc::GroupDesc& g : *groups[k]) {
         g.tile_begin = t;
-        t += tc::tiles_of(g.ep);
+        t += tc::tiles_of(g.ep, g.bn);
       }
     }
     for (cudaStream_t& q : b->pool) OMM_CUDA_TRY(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
@@ -612,6 +626,8 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
         inf.gmax = h.gmax;
         inf.ms_setup = c->ms_setup;
         inf.ms_precond = c->ms_precond;
+        for (int k = 0; k < 4; ++k) inf.tile_width[k] = (k == 0 && !b->precond) ? 0 : b->tile_width[k];
+        inf.ms_autotune = b->ms_autotune;
         inf.ms_refine = ms_ref[i] + ms_cert[i];
         inf.ms_certify = ms_cert[i];
         // batch totals, shared by all instances: the replayed line searches and, with

@@ -167,10 +167,11 @@ omm_status omm_kernel_quartic_coefficients(int n, const double* SWHW, const doub
   return rc;
 }
 
-omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double* B, double alpha,
-                              double beta, double* C, int npass, void* stream) {
-  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || (npass != 1 && npass != 3)) {
-    set_last_error("omm_kernel_gemm_tc: invalid argument");
+omm_status omm_kernel_gemm_tc_tiled(int M, int N, int K, const double* A, const double* B, double alpha,
+                                    double beta, double* C, int npass, int tile_n, void* stream) {
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || (npass != 1 && npass != 3) ||
+      (tile_n != 128 && tile_n != 256)) {
+    set_last_error("omm_kernel_gemm_tc_tiled: invalid argument");
     return OMM_ERR_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -186,7 +187,7 @@ omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double
         cudaMalloc((void**)&desc, sizeof(tc::GroupDesc)) != cudaSuccess) {
       cudaGetLastError();
       if (buf) cudaFree(buf);
-      set_last_error("omm_kernel_gemm_tc: device allocation failed");
+      set_last_error("omm_kernel_gemm_tc_tiled: device allocation failed");
       return OMM_ERR_OOM;
     }
     __nv_bfloat16 *a_hi = buf, *a_lo = buf + na, *b_hi = buf + 2 * na, *b_lo = buf + 2 * na + nb;
@@ -197,23 +198,29 @@ omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double
     tc::Operand ob = tc::make_operand(b_hi, N, K, ld, 2, false);
     // the persistent launch the solver uses for its line-search GEMMs
     const tc::Epilogue ep{C, N, N, 0, alpha, beta, M, N, nullptr, err};
-    const tc::GroupDesc g = tc::make_group(oa, ob, K, ep, 0);
+    const tc::GroupDesc g = tc::make_group(oa, ob, K, ep, 0, tile_n);
     OMM_CUDA_TRY(cudaMemcpyAsync(desc, &g, sizeof(g), cudaMemcpyHostToDevice, st));
-    tc::gemm_persistent(st, desc, 1, tc::tiles_of(ep), npass == 3 ? tc::pairs_split3() : tc::pairs_single(), err);
+    tc::gemm_persistent(st, desc, 1, tc::tiles_of(ep, tile_n), npass == 3 ? tc::pairs_split3() : tc::pairs_single(),
+                        err, tile_n);
     int h = 0;
     OMM_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
     if (h != 0) {
-      set_last_error("omm_kernel_gemm_tc: a bounded device wait expired (code " + std::to_string(h) + ")");
+      set_last_error("omm_kernel_gemm_tc_tiled: a bounded device wait expired (code " + std::to_string(h) + ")");
       rc = OMM_ERR_TIMEOUT;
     }
   } catch (const CudaError& e) {
-    rc = cuda_fail("omm_kernel_gemm_tc", e);
+    rc = cuda_fail("omm_kernel_gemm_tc_tiled", e);
   }
   if (buf) cudaFree(buf);
   if (err) cudaFree(err);
   if (desc) cudaFree(desc);
   return rc;
+}
+
+omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double* B, double alpha,
+                              double beta, double* C, int npass, void* stream) {
+  return omm_kernel_gemm_tc_tiled(M, N, K, A, B, alpha, beta, C, npass, 256, stream);
 }
 
 omm_status omm_kernel_gemm_emu(int M, int N, int K, const double* A, const double* B, double alpha,

@@ -40,6 +40,8 @@ struct MixedState {
   // the four line-search GEMMs as persistent-launch descriptors (device), built on first use
   tc::GroupDesc* plans = nullptr;
   int plan_tiles[4] = {0, 0, 0, 0};
+  int plan_bn[4] = {256, 256, 256, 256};  // output tile widths chosen by the autotuner
+  double ms_autotune = 0.0;               // time the autotuner spent timing candidates
   const Scalars* plan_sc = nullptr;
 };
 
@@ -100,6 +102,12 @@ MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const 
     throw;
   }
   return ms;
+}
+
+void mixed_tuning(const MixedState* ms, int bn[4], double* ms_autotune) {
+  for (int k = 0; k < 4; ++k) bn[k] = ms->plans ? ms->plan_bn[k] : 0;
+  if (!ms->precond) bn[0] = 0;
+  *ms_autotune = ms->ms_autotune;
 }
 
 MixedView mixed_view(MixedState* ms) {
@@ -202,19 +210,24 @@ void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double
   const int m = ms->m, n = ms->n;
   const long nm = (long)n * m;
   const int* skip = &sc->done;
-  tc::GroupDesc h[4];
+  tc::GroupDesc h[4] = {};
   const tc::Epilogue epg{PG, m, m, 0, 1.0, 0.0, n, m, skip, ms->err};
   const tc::Epilogue ehd{Y4 + 2 * nm, m, m, nm, 1.0, 0.0, n, 2 * m, skip, ms->err};
   const tc::Epilogue epr{Proj, 4L * n, 4L * n, 0, 1.0, 0.0, n, 4 * n, skip, ms->err};
   const tc::Epilogue eg{G, m, m, 0, -4.0, 1.0, n, m, skip, ms->err};
-  h[kPlanPG] = tc::make_group(ms->opG, ms->precond ? ms->opP : ms->opG, m, epg, 0);
-  h[kPlanHD] = tc::make_group(ms->opD, ms->opHS, m, ehd, 0);
-  h[kPlanProj] = tc::make_group(ms->opD, ms->opY, m, epr, 0);
-  h[kPlanG] = tc::make_group(ms->opW, ms->opYT, 4 * n, eg, 0);
-  ms->plan_tiles[kPlanPG] = tc::tiles_of(epg);
-  ms->plan_tiles[kPlanHD] = tc::tiles_of(ehd);
-  ms->plan_tiles[kPlanProj] = tc::tiles_of(epr);
-  ms->plan_tiles[kPlanG] = tc::tiles_of(eg);
+  const tc::Operand* opA[4] = {&ms->opG, &ms->opD, &ms->opD, &ms->opW};
+  const tc::Operand* opB[4] = {ms->precond ? &ms->opP : &ms->opG, &ms->opHS, &ms->opY, &ms->opYT};
+  const int K[4] = {m, m, m, 4 * n};
+  const tc::Epilogue* ep[4] = {&epg, &ehd, &epr, &eg};
+  for (int k = ms->precond ? 0 : 1; k < 4; ++k) {  // without P there is no P G product
+    // output tile width from the autotuner (timed once per shape in a process)
+    double ms_tune = 0.0;
+    ms->plan_bn[k] = tc::choose_tile_width(st, {tc::GemmSpec{opA[k], opB[k], K[k], *ep[k]}}, tc::pairs_split3(),
+                                           &ms_tune);
+    ms->ms_autotune += ms_tune;
+    h[k] = tc::make_group(*opA[k], *opB[k], K[k], *ep[k], 0, ms->plan_bn[k]);
+    ms->plan_tiles[k] = tc::tiles_of(*ep[k], ms->plan_bn[k]);
+  }
   if (!ms->plans) alloc(&ms->plans, 4);
   OMM_CUDA_TRY(cudaMemcpyAsync(ms->plans, h, sizeof(h), cudaMemcpyHostToDevice, st));
   OMM_CUDA_TRY(cudaStreamSynchronize(st));  // h is a stack buffer
@@ -222,7 +235,7 @@ void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double
 }
 
 void run_plan(MixedState* ms, cudaStream_t st, int k) {
-  tc::gemm_persistent(st, ms->plans + k, 1, ms->plan_tiles[k], tc::pairs_split3(), ms->err);
+  tc::gemm_persistent(st, ms->plans + k, 1, ms->plan_tiles[k], tc::pairs_split3(), ms->err, ms->plan_bn[k]);
 }
 
 }  // namespace

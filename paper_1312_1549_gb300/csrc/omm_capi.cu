@@ -530,6 +530,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     inf.gmax = h.gmax;
     inf.ms_setup = c->ms_setup;
     inf.ms_precond = c->ms_precond;
+    if (c->mixed) mixed_tuning(c->mixed, inf.tile_width, &inf.ms_autotune);
     inf.ms_iterate = ms_iter;
     inf.ms_refine = ms_ref;
     inf.ms_certify = ms_cert;

@@ -20,6 +20,9 @@ struct MixedView {
   bool precond;
 };
 MixedView mixed_view(MixedState* ms);
+// the autotuner's tile widths of the four line-search GEMMs (0 before the first line search) and
+// the time it spent
+void mixed_tuning(const MixedState* ms, int bn[4], double* ms_autotune);
 
 MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const double* P);
 void mixed_update_H(MixedState* ms, cudaStream_t st, const double* HS);

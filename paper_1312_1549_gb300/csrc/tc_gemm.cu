@@ -23,6 +23,10 @@
 #include "tc_gemm.cuh"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
 
 namespace omm {
 namespace tc {
@@ -381,12 +385,16 @@ __device__ __forceinline__ int find_group(const GroupDesc* __restrict__ groups, 
 // With a chunked pair list (emulation levels) every chunk of a tile is one
 // accumulator round: the MMA thread fills a TMEM buffer with the chunk's pairs,
 // the epilogue adds it to C, and the chunks of a tile stay on one CTA, in order.
-template <bool FUSED>
+template <bool FUSED, int TBN>
 __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ groups, int ngroups, int total_tiles,
                                                 const PairList& pl, int* err, double* partial) {
-  constexpr int NS = FUSED ? 2 : STAGES;
-  constexpr int SB = FUSED ? 2 * STAGE_BYTES : STAGE_BYTES;
-  constexpr int ACC_COLS = 256;
+  // TBN: output tile width (256 or 128); the stage ring keeps the same shared memory
+  constexpr int TB_BYTES = TBN * BK * 2;
+  constexpr int TSTAGE = A_BYTES + TB_BYTES;
+  constexpr int SB = FUSED ? 2 * TSTAGE : TSTAGE;
+  constexpr int NS = (STAGES * STAGE_BYTES) / SB;
+  constexpr int ACC_COLS = TBN;
+  static_assert(NS >= 2 && NS * SB <= STAGES * STAGE_BYTES && 2 * NS + 4 <= 28, "stage ring");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NS * SB);
@@ -441,7 +449,7 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
       const CUtensorMap* mA = reinterpret_cast<const CUtensorMap*>(&g->a);
       const CUtensorMap* mB = reinterpret_cast<const CUtensorMap*>(&g->b);
       const int local = tile - g->tile_begin, tiles_m = (g->ep.M + BM - 1) / BM;
-      const int m0 = (local % tiles_m) * BM, n0 = (local / tiles_m) * BN;
+      const int m0 = (local % tiles_m) * BM, n0 = (local / tiles_m) * TBN;
       const int nkb = (g->K + BK - 1) / BK;
       const int p0 = chunk_begin(unit_c0(u));
       const int total = FUSED ? nkb : (chunk_end(unit_c1(u) - 1) - p0) * nkb;
@@ -460,7 +468,7 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
           tma_load_2d(sa, mA, full, t * BK, m0);
           tma_load_2d(sa + A_BYTES, mA, full, t * BK, g->rowsA + m0);
           tma_load_2d(sa + 2 * A_BYTES, mB, full, t * BK, n0);
-          tma_load_2d(sa + 2 * A_BYTES + B_BYTES, mB, full, t * BK, g->rowsB + n0);
+          tma_load_2d(sa + 2 * A_BYTES + TB_BYTES, mB, full, t * BK, g->rowsB + n0);
         } else {
           const int p = p0 + t / nkb, kb = t % nkb;
           tma_load_2d(sa, mA, full, kb * BK, (int)pl.a[p] * g->rowsA + m0);
@@ -470,7 +478,7 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    constexpr uint32_t idesc = idesc_bf16(BM, TBN);
     uint32_t it = 0, lt = 0;
     for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
       const GroupDesc* g = groups + find_group(groups, ngroups, unit_tile(u));
@@ -498,7 +506,7 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sa = smem_u32(smem + q * SB);
           if (FUSED) {
-            const uint32_t alo = sa + A_BYTES, bhi = sa + 2 * A_BYTES, blo = bhi + B_BYTES;
+            const uint32_t alo = sa + A_BYTES, bhi = sa + 2 * A_BYTES, blo = bhi + TB_BYTES;
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k) {
               umma_bf16(d, smem_desc(sa + k * 32), smem_desc(bhi + k * 32), idesc, (t > 0 || k > 0) ? 1u : 0u);
@@ -548,10 +556,10 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
           ep.beta = 1.0;
         }
         const int local = tile - g->tile_begin, tiles_m = (ep.M + BM - 1) / BM;
-        const int m0 = (local % tiles_m) * BM, n0 = (local / tiles_m) * BN;
+        const int m0 = (local % tiles_m) * BM, n0 = (local / tiles_m) * TBN;
         const int row = m0 + lane_base + lane;
 #pragma unroll 1
-        for (int j = 0; j < BN / 32; ++j) {
+        for (int j = 0; j < TBN / 32; ++j) {
           float v[32];
           tmem_ld32(tmem + buf * ACC_COLS + ((uint32_t)lane_base << 16) + (uint32_t)(j * 32), v);
           store_chunk(ep, row, n0 + j * 32, v);
@@ -572,11 +580,11 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
   }
 }
 
-template <bool FUSED>
+template <bool FUSED, int TBN>
 __global__ void __launch_bounds__(NTHREADS, 1)
 gemm_persistent_kernel(const GroupDesc* __restrict__ groups, int ngroups, int total_tiles,
                        const __grid_constant__ PairList pl, int* err) {
-  persistent_body<FUSED>(groups, ngroups, total_tiles, pl, err, nullptr);
+  persistent_body<FUSED, TBN>(groups, ngroups, total_tiles, pl, err, nullptr);
 }
 
 // one GEMM, its descriptor (tensor maps included) in the kernel's parameter space
@@ -584,7 +592,7 @@ template <bool FUSED>
 __global__ void __launch_bounds__(NTHREADS, 1)
 gemm_persistent_one_kernel(const __grid_constant__ GroupDesc g, int total_tiles, const __grid_constant__ PairList pl,
                            int* err, double* partial) {
-  persistent_body<FUSED>(&g, 1, total_tiles, pl, err, partial);
+  persistent_body<FUSED, BN>(&g, 1, total_tiles, pl, err, partial);
 }
 
 // C = beta C + alpha sum_c partial[c] (chunk order; the same float64 operations, in the same
@@ -654,7 +662,9 @@ TensorMap make_map(const __nv_bfloat16* base, long rows, long cols, long ld, int
 
 Operand make_operand(const __nv_bfloat16* base, long rows, long cols, long ld, int slices, bool is_a) {
   Operand o;
-  o.map = make_map(base, rows * slices, cols, ld, is_a ? BM : BN);
+  o.box_rows = is_a ? BM : BN;
+  o.map = make_map(base, rows * slices, cols, ld, o.box_rows);
+  o.map_n128 = is_a ? o.map : make_map(base, rows * slices, cols, ld, 128);  // for 128-wide output tiles
   o.rows = rows;
   o.cols = cols;
   o.slices = slices;
@@ -713,17 +723,22 @@ void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const Pair
   OMM_LAUNCH_CHECK();
 }
 
-int tiles_of(const Epilogue& ep) { return ((ep.M + BM - 1) / BM) * ((ep.N + BN - 1) / BN); }
+int tiles_of(const Epilogue& ep, int bn) { return ((ep.M + BM - 1) / BM) * ((ep.N + bn - 1) / bn); }
 
-GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin) {
+GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin, int bn) {
+  if (bn != 256 && bn != 128) throw CudaError{cudaErrorInvalidValue, "tc::make_group: tile width"};
+  // the TMA boxes must match the tile: A in 128-row boxes, B in boxes of the tile width
+  if (A.box_rows != BM || (bn == 256 && B.box_rows != 256))
+    throw CudaError{cudaErrorInvalidValue, "tc::make_group: operand boxes do not match the tile"};
   GroupDesc g{};
   g.a = A.map;
-  g.b = B.map;
+  g.b = bn == 128 ? B.map_n128 : B.map;
   g.ep = ep;
   g.K = K;
   g.rowsA = (int)A.rows;
   g.rowsB = (int)B.rows;
   g.tile_begin = tile_begin;
+  g.bn = bn;
   return g;
 }
 
@@ -742,10 +757,14 @@ void prepare_grouped() {
 void prepare_persistent() {
   static bool attr_set = false;
   if (!attr_set) {
-    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      SMEM_BYTES));
-    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      SMEM_BYTES));
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_kernel<false, 256>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_kernel<true, 256>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_kernel<false, 128>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_kernel<true, 128>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_one_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       SMEM_BYTES));
     OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_one_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -756,15 +775,21 @@ void prepare_persistent() {
 }
 
 void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl,
-                     int* err) {
+                     int* err, int bn) {
   prepare_persistent();
   check_pairs(pl, kMaxPairs, kMaxPairs);  // slice counts are checked where the groups are made
   if (ngroups <= 0 || total_tiles <= 0) return;
+  if (bn != 256 && bn != 128) throw CudaError{cudaErrorInvalidValue, "tc::gemm_persistent: tile width"};
   const unsigned grid = (unsigned)std::min(total_tiles, sm_count());
-  if (is_split3(pl))
-    gemm_persistent_kernel<true><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, pl, err);
+  const bool fused = is_split3(pl);
+  if (bn == 256 && fused)
+    gemm_persistent_kernel<true, 256><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, pl, err);
+  else if (bn == 256)
+    gemm_persistent_kernel<false, 256><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, pl, err);
+  else if (fused)
+    gemm_persistent_kernel<true, 128><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, pl, err);
   else
-    gemm_persistent_kernel<false><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, pl, err);
+    gemm_persistent_kernel<false, 128><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, pl, err);
   OMM_LAUNCH_CHECK();
 }
 
@@ -805,6 +830,93 @@ void gemm_grouped(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int
   else
     gemm_grouped_kernel<false><<<(unsigned)total_tiles, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, pl);
   OMM_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ tile-width autotuner
+namespace {
+std::mutex& tune_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+std::map<std::string, int>& tune_cache() {
+  static std::map<std::string, int> cache;
+  return cache;
+}
+}  // namespace
+
+int choose_tile_width(cudaStream_t st, const std::vector<GemmSpec>& specs, const PairList& pl, double* ms_spent) {
+  if (ms_spent) *ms_spent = 0.0;
+  if (specs.empty()) return 256;
+  std::string key = std::to_string(pl.n) + (is_split3(pl) ? "s" : "g");
+  long out_elems = 0;
+  for (const GemmSpec& g : specs) {
+    key += ":" + std::to_string(g.ep.M) + "x" + std::to_string(g.ep.N) + "x" + std::to_string(g.K);
+    out_elems += (long)g.ep.M * g.ep.N;
+  }
+  {
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    auto it = tune_cache().find(key);
+    if (it != tune_cache().end()) return it->second;
+  }
+  // time both widths on the real operands; outputs go to scratch (beta = 0, no skip flags)
+  double* scratch = nullptr;
+  int* err = nullptr;
+  GroupDesc* dev = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best = 256;
+  float best_ms = 0.f;
+  auto release = [&]() {
+    if (scratch) cudaFree(scratch);
+    if (err) cudaFree(err);
+    if (dev) cudaFree(dev);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  try {
+    OMM_CUDA_TRY(cudaMalloc((void**)&scratch, out_elems * sizeof(double)));
+    OMM_CUDA_TRY(cudaMalloc((void**)&err, sizeof(int)));
+    OMM_CUDA_TRY(cudaMalloc((void**)&dev, specs.size() * sizeof(GroupDesc)));
+    OMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    OMM_CUDA_TRY(cudaEventCreate(&e0));
+    OMM_CUDA_TRY(cudaEventCreate(&e1));
+    float total_ms = 0.f;
+    for (int bn : {256, 128}) {
+      std::vector<GroupDesc> h;
+      long off = 0;
+      int tiles = 0;
+      for (const GemmSpec& g : specs) {
+        Epilogue ep{scratch + off, g.ep.N, g.ep.N, 0, 1.0, 0.0, g.ep.M, g.ep.N, nullptr, err};
+        h.push_back(make_group(*g.A, *g.B, g.K, ep, tiles, bn));
+        tiles += tiles_of(ep, bn);
+        off += (long)g.ep.M * g.ep.N;
+      }
+      OMM_CUDA_TRY(cudaMemcpyAsync(dev, h.data(), h.size() * sizeof(GroupDesc), cudaMemcpyHostToDevice, st));
+      gemm_persistent(st, dev, (int)h.size(), tiles, pl, err, bn);  // warm-up
+      constexpr int kReps = 3;
+      OMM_CUDA_TRY(cudaEventRecord(e0, st));
+      for (int r = 0; r < kReps; ++r) gemm_persistent(st, dev, (int)h.size(), tiles, pl, err, bn);
+      OMM_CUDA_TRY(cudaEventRecord(e1, st));
+      OMM_CUDA_TRY(cudaEventSynchronize(e1));  // h stays alive until the copy has been consumed
+      float ms = 0.f;
+      OMM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      total_ms += ms * (kReps + 1) / kReps;
+      if (bn == 256 || ms < best_ms) {
+        best = bn;
+        best_ms = ms;
+      }
+    }
+    int h_err = 0;
+    OMM_CUDA_TRY(cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h_err != 0) best = 256;  // a bounded wait expired: keep the default, the real launch reports it
+    if (ms_spent) *ms_spent = total_ms;
+  } catch (...) {
+    release();
+    throw;
+  }
+  release();
+  std::lock_guard<std::mutex> lock(tune_mutex());
+  tune_cache()[key] = best;
+  return best;
 }
 
 int tile_m() { return BM; }

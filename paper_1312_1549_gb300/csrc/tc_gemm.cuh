@@ -1,6 +1,7 @@
 // BF16 tensor-core GEMM (tcgen05 + TMEM + TMA) with a float64 epilogue.
 #pragma once
 #include <cuda_bf16.h>
+#include <vector>
 #include "omm_internal.cuh"
 
 namespace omm {
@@ -16,7 +17,9 @@ struct alignas(64) TensorMap {
 // leading dimension ld: slice i starts at row i * rows. A split pair
 // x = hi + lo is the 2-slice stack [hi; lo].
 struct Operand {
-  TensorMap map;
+  TensorMap map;       // boxes of 128 rows (A role) or 256 rows (B role)
+  TensorMap map_n128;  // boxes of 128 rows (as a B operand of 128-wide output tiles)
+  int box_rows = 0;    // rows of the boxes of `map`
   long rows = 0, cols = 0;
   int slices = 1;
 };
@@ -67,7 +70,7 @@ inline void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, int
 }
 int tile_m();
 int tile_n();
-int tiles_of(const Epilogue& ep);  // output tiles of one GEMM
+int tiles_of(const Epilogue& ep, int bn = 256);  // output tiles of one GEMM (128 x bn)
 
 // One GEMM of a grouped launch (device array element; tensor maps in global memory).
 struct alignas(64) GroupDesc {
@@ -75,21 +78,35 @@ struct alignas(64) GroupDesc {
   TensorMap b;
   Epilogue ep;
   int K, rowsA, rowsB, tile_begin;
+  int bn;  // output tile width, 256 or 128 (all groups of one launch share it)
 };
-GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin);
+GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin, int bn = 256);
 // groups_dev: ngroups descriptors in device memory, sorted by tile_begin; all share the pair list
 void prepare_grouped();     // kernel attributes (call before a stream capture)
 void prepare_persistent();
 // persistent grouped launch: one CTA per SM, double-buffered TMEM accumulators; err receives a
 // nonzero code if a bounded wait expired
 void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl,
-                     int* err);
+                     int* err, int bn = 256);
 // the same persistent kernel for one GEMM whose descriptor travels as a kernel parameter.
 // partial (optional, partial_capacity doubles): scratch that lets a GEMM of few output tiles run
 // each chunk of its pair list on its own CTA and add the chunks afterwards, in chunk order.
 void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K, const PairList& pl,
                      const Epilogue& ep, double* partial = nullptr, long partial_capacity = 0);
 void gemm_grouped(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl);
+
+// Tile-width autotuner: times one persistent launch over these GEMMs (the operands as given,
+// the outputs redirected to scratch) with 128 x 256 and with 128 x 128 output tiles, returns the
+// faster width, and remembers it per shape signature for the life of the process. ms_spent
+// receives the time spent timing (0 when the answer came from the cache).
+struct GemmSpec {
+  const Operand* A;
+  const Operand* B;
+  int K;
+  Epilogue ep;  // only M and N are used
+};
+int choose_tile_width(cudaStream_t st, const std::vector<GemmSpec>& specs, const PairList& pl,
+                      double* ms_spent = nullptr);
 
 // x (float64, rows x cols, ld_src) -> hi = bf16(x), lo = bf16(x - hi) (ld_dst);
 // transposed variants write dst[j][i]. Skipped when sc's done/halt is set.

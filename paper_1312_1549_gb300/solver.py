@@ -156,12 +156,17 @@ def quartic_coefficients(SWHW, Proj, E, stream=None):
     return np.array(list(out))
 
 
-def gemm_tc(A, B, C, alpha=1.0, beta=0.0, npass=3, stream=None):
-    """C = alpha A B^T + beta C on the BF16 tensor cores (split operands)."""
+def gemm_tc(A, B, C, alpha=1.0, beta=0.0, npass=3, stream=None, tile_n=None):
+    """C = alpha A B^T + beta C on the BF16 tensor cores (split operands); tile_n 256 or 128."""
     M, K = A.shape
     Nn = B.shape[0]
-    N.check(N.lib().omm_kernel_gemm_tc(M, Nn, K, _ptr(A), _ptr(B), float(alpha), float(beta), _ptr(C),
-                                       int(npass), _stream_handle(stream)), "omm_kernel_gemm_tc")
+    if tile_n is None:
+        N.check(N.lib().omm_kernel_gemm_tc(M, Nn, K, _ptr(A), _ptr(B), float(alpha), float(beta), _ptr(C),
+                                           int(npass), _stream_handle(stream)), "omm_kernel_gemm_tc")
+    else:
+        N.check(N.lib().omm_kernel_gemm_tc_tiled(M, Nn, K, _ptr(A), _ptr(B), float(alpha), float(beta), _ptr(C),
+                                                 int(npass), int(tile_n), _stream_handle(stream)),
+                "omm_kernel_gemm_tc_tiled")
     return C
 
 

@@ -25,26 +25,28 @@ def bf16_round(x):
     return np.ldexp(np.rint(m * 256.0) / 256.0, e)
 
 
+@pytest.mark.parametrize("tile_n", [256, 128])
 @pytest.mark.parametrize("M,N,K", [(128, 256, 64), (130, 257, 70), (256, 512, 1000), (1, 1, 1), (384, 96, 200)])
-def test_gemm_tc_single_pass_is_exact_bf16_product(S, M, N, K):
+def test_gemm_tc_single_pass_is_exact_bf16_product(S, M, N, K, tile_n):
     """npass = 1: the product of the bf16-rounded operands up to FP32 accumulation (K * 2^-23)."""
     rng = np.random.default_rng(M + N + K)
     A = rng.normal(size=(M, K)); B = rng.normal(size=(N, K))
     C = dev(np.zeros((M, N)))
-    S.gemm_tc(dev(A), dev(B), C, npass=1)
+    S.gemm_tc(dev(A), dev(B), C, npass=1, tile_n=tile_n)
     ref = bf16_round(A) @ bf16_round(B).T
     scale = np.abs(bf16_round(A)) @ np.abs(bf16_round(B)).T
     assert np.all(np.abs(C.cpu().numpy() - ref) <= K * 2.0 ** -23 * scale + 1e-30)
 
 
+@pytest.mark.parametrize("tile_n", [256, 128])
 @pytest.mark.parametrize("M,N,K", [(128, 256, 64), (200, 300, 100), (256, 512, 1024), (129, 700, 333)])
-def test_gemm_tc_split_error_bound(S, M, N, K):
+def test_gemm_tc_split_error_bound(S, M, N, K, tile_n):
     """npass = 3: error of the 3-term split product within 2^-14 |A||B|^T elementwise."""
     rng = np.random.default_rng(7 * M + N + K)
     A = rng.normal(size=(M, K)); B = rng.normal(size=(N, K))
     C0 = rng.normal(size=(M, N))
     C = dev(C0)
-    S.gemm_tc(dev(A), dev(B), C, alpha=2.0, beta=-1.0, npass=3)
+    S.gemm_tc(dev(A), dev(B), C, alpha=2.0, beta=-1.0, npass=3, tile_n=tile_n)
     ref = 2.0 * A @ B.T - C0
     scale = 2.0 * np.abs(A) @ np.abs(B).T
     err = np.abs(C.cpu().numpy() - ref)
