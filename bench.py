@@ -417,6 +417,16 @@ def main():
                 "peak_source": f"bf16_tflops_sustained of {peak_kind} MEASURED_PEAKS" if mixed else
                 "float64 DFMA (no measured peak; see fp64 fields)",
                 "launches": main_launches, "avg_launch_ms": main_ms / max(main_launches, 1)}
+    sl_ms = sum(i["ms_sliced_gemm"] for i in infos)
+    sl_flop = sum(i["sliced_gemm_flop"] for i in infos)
+    sl_n = sum(i["sliced_gemm_launches"] for i in infos)
+    roofline_sliced = None
+    if mixed and sl_ms > 0:
+        a = sl_flop / (sl_ms * 1e-3) / 1e12
+        roofline_sliced = {"bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                           "traffic": None, "kernel": "gemm_persistent_one_kernel (tcgen05, sliced float64-class "
+                           "products: inverse, refreshes, certificate, D)", "launches": sl_n,
+                           "avg_launch_ms": sl_ms / max(sl_n, 1), "ms_per_solve": sl_ms / len(infos)}
     out = {"metric": METRIC, "value": ms * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "bf16x3+f64" if mixed else "f64", "data": "synthetic",
@@ -437,7 +447,7 @@ def main():
            "gemm_tflops_logical_in_iterations": (infos[-1]["gemm_flop"] and
                                                  (iters * (6.0 * p.m * p.m * p.n + 12.0 * p.m * p.n * p.n))
                                                  / (it_ms * 1e-3) / 1e12),
-           "roofline": roofline, "gpu_launches": launches, "clocks": clocks}
+           "roofline": roofline, "roofline_sliced": roofline_sliced, "gpu_launches": launches, "clocks": clocks}
     if not args.no_exact_check and args.config in (1, 2, 3):
         from oracle import exact
         ex = exact.exact_minimum(p.H, p.S, p.n, want_matrices=False)

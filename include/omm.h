@@ -115,6 +115,11 @@ typedef struct {
   int tile_width[4];         /* mixed: output tile width (256 or 128 columns) the autotuner chose for
                                 the P G, [H D; S D], projection and gradient GEMMs (0: not run) */
   double ms_autotune;        /* time the autotuner spent timing candidates (0 when cached) */
+  double ms_sliced_gemm;     /* with opts.profile: summed duration of the float64-class sliced
+                                products of omm_create (inverse) and this solve (refreshes,
+                                certificate, D) */
+  double sliced_gemm_flop;   /* with opts.profile: tensor flops they issued */
+  double sliced_gemm_launches; /* with opts.profile: their number */
   double ms_batch;           /* omm_solve_batched only: the whole batched solve. There ms_iterate,
                                 ms_main_gemm, main_gemm_launches and main_gemm_flop are batch
                                 totals too (the same in every instance's report) */

@@ -35,7 +35,9 @@ class OmmInfo(ct.Structure):
                 ("ms_main_gemm", ct.c_double), ("main_gemm_launches", ct.c_double),
                 ("main_gemm_flop", ct.c_double), ("ms_certify", ct.c_double),
                 ("ms_precond", ct.c_double),
-                ("tile_width", ct.c_int * 4), ("ms_autotune", ct.c_double), ("ms_batch", ct.c_double)]
+                ("tile_width", ct.c_int * 4), ("ms_autotune", ct.c_double),
+                ("ms_sliced_gemm", ct.c_double), ("sliced_gemm_flop", ct.c_double),
+                ("sliced_gemm_launches", ct.c_double), ("ms_batch", ct.c_double)]
 
     def as_dict(self):
         out = {}

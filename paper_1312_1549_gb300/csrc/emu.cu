@@ -142,11 +142,20 @@ tc::PairList level_chunks(int K, int s) {
   return pl;
 }
 
+namespace {
+thread_local Profiler* t_prof = nullptr;
+}
+
+void set_profiler(Profiler* p) { t_prof = p; }
+
 void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep,
           double* partial, long partial_capacity) {
   // one persistent launch: every output tile runs its chunks in order on one CTA (or, for a
   // product of few tiles with scratch given, every chunk on its own CTA, then one reduction)
-  tc::gemm_persistent(st, A, B, K, level_chunks(K, s), ep, partial, partial_capacity);
+  const tc::PairList pl = level_chunks(K, s);
+  if (t_prof) t_prof->begin(st);
+  tc::gemm_persistent(st, A, B, K, pl, ep, partial, partial_capacity);
+  if (t_prof) t_prof->end(st, 2.0 * ep.M * (double)ep.N * K * pl.n);  // issued tensor flops
 }
 
 }  // namespace emu

@@ -13,6 +13,8 @@ void transpose(cudaStream_t st, const double* src, long rows, long cols, long ld
 // the slice pairs (i, j), i + j < s, level by level from the smallest, in chunks whose
 // FP32 sums are exact for a contraction of length K
 tc::PairList level_chunks(int K, int s);
+// CUDA-event timing of every sliced product issued by this host thread (nullptr: off)
+void set_profiler(Profiler* p);
 // C = alpha A B^T + beta C from s-slice operands (A, B made by slice_rows)
 void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep,
           double* partial = nullptr, long partial_capacity = 0);

@@ -305,6 +305,8 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
   try {
     const long mm = (long)m * m, nm = (long)n * m;
     for (auto& e : c->ev) OMM_CUDA_TRY(cudaEventCreate(&e));
+    c->prof_sliced.on = o.profile != 0;
+    if (c->prof_sliced.on) emu::set_profiler(&c->prof_sliced);
     OMM_CUDA_TRY(cudaMallocHost((void**)&c->sc_host, sizeof(Scalars)));
     dev_alloc(&c->sc, 1);
     dev_alloc(&c->info_dev, 1);
@@ -357,6 +359,14 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     if (inv_err) OMM_CUDA_TRY(cudaMemcpyAsync(&ierr, inv_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     OMM_CUDA_TRY(cudaStreamSynchronize(c->st));
     c->ms_setup = elapsed(c->ev[0], c->ev[1]);
+    if (c->prof_sliced.on) {
+      emu::set_profiler(nullptr);
+      c->prof_sliced.collect();
+      c->sliced_setup[0] = c->prof_sliced.ms;
+      c->sliced_setup[1] = c->prof_sliced.flop;
+      c->sliced_setup[2] = (double)c->prof_sliced.launches;
+      c->prof_sliced.reset();
+    }
     c->ms_precond = precond ? elapsed(c->ev[2], c->ev[3]) : 0.0;
     dev_free(A);
     dev_free(work);
@@ -373,12 +383,14 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
                                        std::to_string(info) + ")");
     }
   } catch (const std::bad_alloc&) {
+    emu::set_profiler(nullptr);
     dev_free(A);
     dev_free(work);
     dev_free(inv_err);
     destroy(c);
     return fail(OMM_ERR_OOM, "omm_create: device allocation failed");
   } catch (const CudaError& e) {
+    emu::set_profiler(nullptr);
     dev_free(A);
     dev_free(work);
     dev_free(inv_err);
@@ -416,6 +428,8 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     const unsigned long long launches0 = g_launches.load();
     c->prof.on = c->opts.profile != 0;
     c->prof.reset();
+    c->prof_sliced.reset();
+    if (c->prof_sliced.on) emu::set_profiler(&c->prof_sliced);
     copy_in(c->C, C0, nm, c->st);
     reset_loop_flags(c, true);
     write_scalars(c);
@@ -564,6 +578,12 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     inf.ms_main_gemm = c->prof.ms;
     inf.main_gemm_launches = (double)c->prof.launches;
     inf.main_gemm_flop = c->prof.flop;
+    if (c->prof_sliced.on) {
+      c->prof_sliced.collect();
+      inf.ms_sliced_gemm = c->sliced_setup[0] + c->prof_sliced.ms;
+      inf.sliced_gemm_flop = c->sliced_setup[1] + c->prof_sliced.flop;
+      inf.sliced_gemm_launches = c->sliced_setup[2] + (double)c->prof_sliced.launches;
+    }
   } catch (const std::bad_alloc&) {
     result = OMM_ERR_OOM;
     set_last_error("omm_solve: device allocation failed");
@@ -571,6 +591,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     result = OMM_ERR_CUDA;
     set_last_error(std::string("omm_solve: ") + e.what + ": " + cudaGetErrorString(e.err));
   }
+  emu::set_profiler(nullptr);
   inf.status = result;
   if (info) *info = inf;
   if (result != OMM_OK && result != OMM_ERR_CUDA && result != OMM_ERR_OOM)

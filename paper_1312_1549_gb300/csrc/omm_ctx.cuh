@@ -38,6 +38,8 @@ struct omm_ctx {
   omm::MixedState* mixed = nullptr;
   omm::EmuState* emu = nullptr;  // float64-class tensor-core refresh of the mixed path
   omm::Profiler prof;  // main contraction kernel of the iteration (tensor-core or float64 GEMM)
+  omm::Profiler prof_sliced;  // the float64-class sliced products (inverse, refreshes, certificate, D)
+  double sliced_setup[3] = {0.0, 0.0, 0.0};  // ms, flops, launches of those in omm_create
 };
 
 namespace omm {
