@@ -84,3 +84,46 @@ def test_sliced_preconditioner_inverse_at_si512():
     R = P_sliced[rows] @ A
     R[torch.arange(128, device=R.device), rows] -= 1.0
     assert R.abs().max().item() <= 1e-11
+
+
+def test_water256_autograd_central_differences():
+    """Mixed-precision dE/dH and dE/dS of water256 against central differences.
+
+    32 random symmetric directions for H and 32 for S (S's sparsity pattern), unit Frobenius norm,
+    h = 1e-5, warm-started re-solves. The energies carry about 1e-12 absolute error (relative 1e-15
+    of |E| ~ 1e3), so the difference quotient is good to about 1e-7; the h^2 truncation term is
+    far smaller for unit-norm directions.
+    """
+    from paper_1312_1549_gb300 import build
+    build.build()
+    from paper_1312_1549_gb300.autograd import omm_energy
+    from synth import configs
+    p = configs.config3()
+    H = dev(p.H).requires_grad_(True)
+    S = dev(p.S).requires_grad_(True)
+    T = dev(p.T)
+    E, C = omm_energy(H, S, T, dev(p.C0), p.n, p.eta, p.tau, precision="mixed", tol_grad=1e-10)
+    E.backward()
+    gH, gS = H.grad.detach(), S.grad.detach()
+    rng = np.random.default_rng(3)
+    h = 1e-5
+    mask = dev((np.abs(p.S) > 0).astype(np.float64))
+    worst = 0.0
+    for k in range(32):
+        dH = dev(rng.normal(size=(p.m, p.m)))
+        dH = 0.5 * (dH + dH.T)
+        dH /= torch.linalg.norm(dH)
+        dS = dev(rng.normal(size=(p.m, p.m)))
+        dS = (dS + dS.T) * mask
+        dS /= torch.linalg.norm(dS)
+        with torch.no_grad():
+            for g, direction, which in ((gH, dH, "H"), (gS, dS, "S")):
+                args_p = (H + h * direction, S) if which == "H" else (H, S + h * direction)
+                args_m = (H - h * direction, S) if which == "H" else (H, S - h * direction)
+                Ep, _ = omm_energy(*args_p, T, C, p.n, p.eta, p.tau, precision="mixed", tol_grad=1e-10)
+                Em, _ = omm_energy(*args_m, T, C, p.n, p.eta, p.tau, precision="mixed", tol_grad=1e-10)
+                fd = (Ep.item() - Em.item()) / (2 * h)
+                an = float((g * direction).sum())
+                worst = max(worst, abs(fd - an) / max(1.0, abs(an)))
+                assert fd == pytest.approx(an, rel=1e-6, abs=1e-6), (k, which, fd, an)
+    print("worst relative difference", worst)
