@@ -32,10 +32,15 @@ namespace {
 constexpr int NB = 64;
 
 // Factor the b x b diagonal block at A (ld lda) in place (lower) and write
-// its inverse to Linv (NB x NB, row-major, zero above the diagonal).
+// its inverse to Linv (NB x NB, row-major, zero above the diagonal); with Pblk
+// (ld ldp) also the block Linv^T Linv (both triangles). Every division is a
+// multiplication by one reciprocal per pivot: float64 division is a long
+// instruction sequence on this GPU's narrow float64 pipe.
 __global__ void __launch_bounds__(256)
-potf2_inv_kernel(double* A, long lda, int b, double* Linv, int* info, int col_offset) {
+potf2_inv_kernel(double* A, long lda, int b, double* Linv, int* info, int col_offset, double* Pblk, long ldp) {
   __shared__ double L[NB][NB + 1];
+  __shared__ double X[NB][NB + 1];
+  __shared__ double rdiag[NB];
   const int tid = threadIdx.x;
   for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
     const int i = idx / NB, j = idx % NB;
@@ -49,16 +54,18 @@ potf2_inv_kernel(double* A, long lda, int b, double* Linv, int* info, int col_of
         atomicCAS(info, 0, col_offset + j + 1);
         d = 1.0;
       }
-      L[j][j] = sqrt(d);
+      const double r = sqrt(d);
+      L[j][j] = r;
+      rdiag[j] = 1.0 / r;
     }
     __syncthreads();
-    const double djj = L[j][j];
-    for (int i = j + 1 + tid; i < b; i += blockDim.x) L[i][j] /= djj;
+    const double rj = rdiag[j];
+    for (int i = j + 1 + tid; i < b; i += blockDim.x) L[i][j] *= rj;
     __syncthreads();
     const int r = b - j - 1;
     for (int idx = tid; idx < r * r; idx += blockDim.x) {
       const int i = j + 1 + idx / r, l = j + 1 + idx % r;
-      if (l <= i) L[i][l] -= L[i][j] * L[l][j];
+      if (l <= i) L[i][l] = fma(-L[i][j], L[l][j], L[i][l]);
     }
     __syncthreads();
   }
@@ -67,16 +74,15 @@ potf2_inv_kernel(double* A, long lda, int b, double* Linv, int* info, int col_of
     A[(long)i * lda + j] = (j <= i) ? L[i][j] : 0.0;
   }
   // inverse of the lower-triangular block: column c solves L x = e_c
-  __shared__ double X[NB][NB + 1];
   if (tid < NB) {
     const int c = tid;
     for (int i = 0; i < NB; ++i) X[i][c] = 0.0;
     if (c < b) {
-      X[c][c] = 1.0 / L[c][c];
+      X[c][c] = rdiag[c];
       for (int i = c + 1; i < b; ++i) {
-        double s = 0.0;
-        for (int k = c; k < i; ++k) s = fma(L[i][k], X[k][c], s);
-        X[i][c] = -s / L[i][i];
+        double acc = 0.0;
+        for (int k = c; k < i; ++k) acc = fma(L[i][k], X[k][c], acc);
+        X[i][c] = -acc * rdiag[i];
       }
     }
   }
@@ -84,6 +90,17 @@ potf2_inv_kernel(double* A, long lda, int b, double* Linv, int* info, int col_of
   for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
     const int i = idx / NB, j = idx % NB;
     Linv[idx] = X[i][j];
+  }
+  if (Pblk != nullptr) {
+    // (X^T X)_ij = sum_{k >= i} X_ki X_kj for j <= i, mirrored
+    for (int idx = tid; idx < b * b; idx += blockDim.x) {
+      const int i = idx / b, j = idx % b;
+      if (j > i) continue;
+      double acc = 0.0;
+      for (int k = i; k < b; ++k) acc = fma(X[k][i], X[k][j], acc);
+      Pblk[(long)i * ldp + j] = acc;
+      Pblk[(long)j * ldp + i] = acc;
+    }
   }
 }
 
@@ -148,7 +165,7 @@ void spd_inverse(cudaStream_t st, int m, double* A, double* P, double* work, int
     const int k = kb * NB;
     const int b = (m - k < NB) ? (m - k) : NB;
     double* Akk = A + (long)k * m + k;
-    potf2_inv_kernel<<<1, 256, 0, st>>>(Akk, m, b, w.Dinv + (long)kb * NB * NB, info_dev, k);
+    potf2_inv_kernel<<<1, 256, 0, st>>>(Akk, m, b, w.Dinv + (long)kb * NB * NB, info_dev, k, nullptr, 0);
     OMM_LAUNCH_CHECK();
     const int r = m - k - b;
     if (r > 0) {
@@ -213,10 +230,10 @@ void sliced_nt(cudaStream_t st, SlicedWork& w, int M, int N, int K, double alpha
             w.partial_cap);
 }
 
-// leaf: factor A[r0:r0+b, r0:r0+b] in place and write its inverse into Y
+// leaf: factor A[r0:r0+b, r0:r0+b] in place, write its inverse into Y and Y_leaf^T Y_leaf into P
 void leaf(cudaStream_t st, SlicedWork& w, int r0, int b) {
   const long m = w.m;
-  potf2_inv_kernel<<<1, 256, 0, st>>>(w.A + r0 * m + r0, m, b, w.leaf, w.info, r0);
+  potf2_inv_kernel<<<1, 256, 0, st>>>(w.A + r0 * m + r0, m, b, w.leaf, w.info, r0, w.P + r0 * m + r0, m);
   OMM_LAUNCH_CHECK();
   copy_block_kernel<<<16, 256, 0, st>>>(b, w.leaf, NB, w.Y + r0 * m + r0, m);
   OMM_LAUNCH_CHECK();
@@ -255,12 +272,7 @@ void chol_inv(cudaStream_t st, SlicedWork& w, int r0, int b) {
 // P[r0:r0+b, r0:r0+b] (lower blocks) = Yb^T Yb for the lower-triangular Yb = Y[r0:r0+b, r0:r0+b]
 void lauum(cudaStream_t st, SlicedWork& w, int r0, int b) {
   const long m = w.m;
-  if (b <= NB) {
-    const double* Yb = w.Y + (long)r0 * m + r0;
-    dgemm(st, 1, 0, b, b, b, 1.0, Yb, m, 0, Yb, m, 0, 0.0, w.P + (long)r0 * m + r0, m, 0, 1,
-          kTriLower | kTriKStart);
-    return;
-  }
+  if (b <= NB) return;  // the leaf kernel of chol_inv wrote Yb^T Yb
   const int b1 = half_of(b), b2 = b - b1, r1 = r0 + b1;
   // the recursions use the scratch buffers, so they come first
   lauum(st, w, r1, b2);
