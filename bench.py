@@ -119,6 +119,21 @@ def dist_setup(gpus):
     return rank, world, local, None
 
 
+def max_over_ranks(value, dist, device):
+    """The job's time: the largest of the ranks' values (identity without a process group)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(count, rank, world):
+    """Instances of rank `rank` when `count` independent instances are split over `world` ranks."""
+    return list(range(rank, count, world))
+
+
 def build_problem(config):
     from synth import configs
     return configs.CONFIGS[config]()
@@ -180,7 +195,10 @@ def run_batch(args):
     _build.build()
     from paper_1312_1549_gb300 import solver as S
     from synth import configs
-    probs = [configs.config4_instance(i) for i in range(args.instances)]
+    # instances are independent: ranks take disjoint shards, no collective on the data path
+    rank, world, local, dist = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    probs = [configs.config4_instance(i) for i in shard(args.instances, rank, world)]
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     dev = [(t(p.H), t(p.S), t(p.T), p.n, p.eta, p.tau) for p in probs]
     C0 = [t(p.C0) for p in probs]
@@ -212,8 +230,16 @@ def run_batch(args):
         e1.record(stream)
         torch.cuda.synchronize()
     launches = S.launch_count() - launches0
-    ms = e0.elapsed_time(e1) / args.steps
-    out = _base_line(args, ms * 1e-3)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, torch.device("cuda", local))
+    if dist is not None:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+    out = _base_line(args, ms * 1e-3, world)
+    if world > 1:
+        out["scaling"] = "strong"
+        out["config"]["parallelism"] = f"{args.instances} instances sharded over {world} GPUs (rank 0 shown)"
     out["config"]["certificate"] = "native float64" if args.native_certificate else "float64-class (sliced)"
     logical = sum(i["iterations"] * (6.0 * p.m * p.m * p.n + 16.0 * p.m * p.n * p.n)
                   for i, p in zip(infos, probs))
@@ -224,7 +250,7 @@ def run_batch(args):
     b0 = prof_infos[0]  # batch totals are repeated in every instance's report
     achieved = (b0["main_gemm_flop"] / (b0["ms_main_gemm"] * 1e-3) / 1e12) if b0["ms_main_gemm"] > 0 else None
     peak = load_peaks()[0]["bf16_tflops_sustained"]
-    out.update({"instances": len(probs), "m_range": [min(p.m for p in probs), max(p.m for p in probs)],
+    out.update({"instances": args.instances, "instances_rank0": len(probs), "m_range": [min(p.m for p in probs), max(p.m for p in probs)],
                 "line_searches_max": max(i["iterations"] for i in infos),
                 "line_searches_total": sum(i["iterations"] for i in infos),
                 "gemm_tflops_logical": logical / (ms * 1e-3) / 1e12,
@@ -250,7 +276,7 @@ def run_batch(args):
         out["rel_err_E_vs_exact_sample"] = max(
             abs(E[i] - exact.exact_minimum(probs[i].H, probs[i].S, probs[i].n, want_matrices=False)["E"])
             / abs(E[i]) for i in sample)
-    if not args.no_fp64_compare:
+    if not args.no_fp64_compare and world == 1:
         # the float64 GPU path instance by instance on every 8th instance, scaled by flops
         sub = list(range(0, len(probs), 8))
         torch.cuda.synchronize()
@@ -265,6 +291,8 @@ def run_batch(args):
                                 "note": "instances solved one by one on the float64 path; measured on every "
                                         "8th instance, scaled by per-line-search flops"}
     print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 
@@ -392,10 +420,8 @@ def main():
     launches = S.launch_count() - launches0
     clocks = clk.summary()
     ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, dist, dev)
     if dist is not None:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
         dist.barrier()
     if rank != 0:
         return 0
