@@ -73,6 +73,13 @@ omm_status omm_kernel_quartic_coefficients(int n, const double* SWHW, const doub
 omm_status omm_kernel_gemm_tc_tiled(int M, int N, int K, const double* A, const double* B, double alpha,
                                     double beta, double* C, int npass, int tile_n, void* stream);
 
+/* The same contraction, block-sparse in B (the finite-range operators of Sec. 2.6): the 64-wide K
+ * blocks where a block of tile_n rows of B is exactly zero are skipped. The result equals that of
+ * omm_kernel_gemm_tc_tiled bit for bit (the skipped products are exact zeros); the block lists
+ * are built from B inside the call. Arguments and errors as omm_kernel_gemm_tc_tiled. */
+omm_status omm_kernel_gemm_tc_blocksparse(int M, int N, int K, const double* A, const double* B, double alpha,
+                                          double beta, double* C, int npass, int tile_n, void* stream);
+
 omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double* B, double alpha,
                               double beta, double* C, int npass, void* stream);
 

@@ -77,6 +77,7 @@ _SIGNATURES = {
     "omm_kernel_spd_inverse": (_I, [_I, _P, _P, ct.POINTER(_I), _P]),
     "omm_kernel_spd_inverse_sliced": (_I, [_I, _P, _P, ct.POINTER(_I), _P]),
     "omm_kernel_gemm_tc_tiled": (_I, [_I, _I, _I, _P, _P, ct.c_double, ct.c_double, _P, _I, _I, _P]),
+    "omm_kernel_gemm_tc_blocksparse": (_I, [_I, _I, _I, _P, _P, ct.c_double, ct.c_double, _P, _I, _I, _P]),
     "omm_kernel_line_minimum": (_I, [ct.POINTER(_D), ct.POINTER(_D)]),
     "omm_kernel_quartic_coefficients": (_I, [_I, _P, _P, _D, ct.POINTER(_D), _P]),
     "omm_kernel_gemm_tc": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _P]),

@@ -363,7 +363,10 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
         spg.push_back(tc::GemmSpec{v.opG, v.opP, mi, e});
       }
       tc::Epilogue ehd{c->Y4 + 2 * nm, mi, mi, nm, 1.0, 0.0, ni, 2 * mi, skip, v.err};
-      shd.push_back(tc::GemmSpec{v.opD, v.opHS, mi, ehd});
+      tc::GemmSpec hd{v.opD, v.opHS, mi, ehd};
+      hd.sparse[0] = &v.hs_blocks[0];
+      hd.sparse[1] = &v.hs_blocks[1];
+      shd.push_back(hd);
       tc::Epilogue epr{c->Proj, 4L * ni, 4L * ni, 0, 1.0, 0.0, ni, 4 * ni, skip, v.err};
       spr.push_back(tc::GemmSpec{v.opD, v.opY, mi, epr});
       tc::Epilogue eg{c->G, mi, mi, 0, -4.0, 1.0, ni, mi, skip, v.err};
@@ -390,7 +393,8 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       const int bn = tc::choose_tile_width(b->st, *specs[k], tc::pairs_split3(), &ms_tune);
       b->ms_autotune += ms_tune;
       b->tile_width[k] = bn;
-      for (const tc::GemmSpec& sp : *specs[k]) groups[k]->push_back(tc::make_group(*sp.A, *sp.B, sp.K, sp.ep, 0, bn));
+      for (const tc::GemmSpec& sp : *specs[k])
+        groups[k]->push_back(tc::make_group(*sp.A, *sp.B, sp.K, sp.ep, 0, bn, sp.sparse[bn == 256 ? 0 : 1]));
       std::stable_sort(groups[k]->begin(), groups[k]->end(),
                        [](const tc::GroupDesc& x, const tc::GroupDesc& y) { return x.K > y.K; });
       int t = 0;

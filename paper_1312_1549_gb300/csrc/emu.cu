@@ -149,12 +149,12 @@ thread_local Profiler* t_prof = nullptr;
 void set_profiler(Profiler* p) { t_prof = p; }
 
 void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep,
-          double* partial, long partial_capacity) {
+          double* partial, long partial_capacity, const tc::BlockLists* sparse) {
   // one persistent launch: every output tile runs its chunks in order on one CTA (or, for a
   // product of few tiles with scratch given, every chunk on its own CTA, then one reduction)
   const tc::PairList pl = level_chunks(K, s);
   if (t_prof) t_prof->begin(st);
-  tc::gemm_persistent(st, A, B, K, pl, ep, partial, partial_capacity);
+  tc::gemm_persistent(st, A, B, K, pl, ep, partial, partial_capacity, sparse);
   if (t_prof) t_prof->end(st, 2.0 * ep.M * (double)ep.N * K * pl.n);  // issued tensor flops
 }
 
@@ -177,6 +177,7 @@ struct EmuState {
   int* err = nullptr;
   double* partial = nullptr;  // per-chunk sums of the products with few output tiles
   long partial_cap = 0;
+  tc::BlockLists hs_blocks;   // block sparsity of [H~; S] (256-row blocks)
 };
 
 namespace {
@@ -209,6 +210,7 @@ EmuState* emu_create(cudaStream_t st, int m, int n, int slices, const double* HS
     alloc(&es->partial, (size_t)es->partial_cap);
     OMM_CUDA_TRY(cudaMemsetAsync(es->err, 0, sizeof(int), st));
     emu::slice_rows(st, HS, 2L * m, m, m, slices, es->HSs, ldm, nullptr);
+    tc::block_lists(st, HS, 2L * m, m, m, 256, es->hs_blocks);
     es->opHS = tc::make_operand(es->HSs, 2L * m, m, ldm, slices, false);
     es->opC = tc::make_operand(es->Cs, n, m, ldm, slices, true);
     es->opY = tc::make_operand(es->Ys, 2L * n, m, ldm, slices, false);
@@ -227,6 +229,7 @@ EmuState* emu_create(cudaStream_t st, int m, int n, int slices, const double* HS
 
 void emu_update_H(EmuState* es, cudaStream_t st, const double* HS) {
   emu::slice_rows(st, HS, 2L * es->m, es->m, es->m, es->s, es->HSs, es->ldm, nullptr);
+  tc::block_lists(st, HS, 2L * es->m, es->m, es->m, 256, es->hs_blocks);
 }
 
 void emu_destroy(EmuState* es) {
@@ -234,6 +237,7 @@ void emu_destroy(EmuState* es) {
   void* bufs[] = {es->HSs, es->Cs, es->Ys, es->Ws, es->YTs, es->T64, es->CTs, es->XTs, es->SWs, es->err, es->partial};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  tc::free_block_lists(es->hs_blocks);
   delete es;
 }
 
@@ -252,7 +256,7 @@ void emu_recompute_state(EmuState* es, cudaStream_t st, Scalars* sc, const doubl
   emu::slice_rows(st, C, n, m, m, s, es->Cs, es->ldm, nullptr);
   // [HC; SC] (n x m layout) = C [H~; S]^T
   emu::gemm(st, es->opC, es->opHS, m, s, tc::Epilogue{Y4, m, m, nm, 1.0, 0.0, n, 2 * m, nullptr, es->err},
-            es->partial, es->partial_cap);
+            es->partial, es->partial_cap, &es->hs_blocks);
   emu::slice_rows(st, Y4, 2L * n, m, m, s, es->Ys, es->ldm, nullptr);
   // [S_W | H_W] = C [SC; HC]^T
   emu::gemm(st, es->opC, es->opY, m, s,

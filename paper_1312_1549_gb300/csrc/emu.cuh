@@ -17,7 +17,7 @@ tc::PairList level_chunks(int K, int s);
 void set_profiler(Profiler* p);
 // C = alpha A B^T + beta C from s-slice operands (A, B made by slice_rows)
 void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep,
-          double* partial = nullptr, long partial_capacity = 0);
+          double* partial = nullptr, long partial_capacity = 0, const tc::BlockLists* sparse = nullptr);
 }  // namespace emu
 
 struct EmuState;

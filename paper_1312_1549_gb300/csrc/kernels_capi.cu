@@ -167,11 +167,17 @@ omm_status omm_kernel_quartic_coefficients(int n, const double* SWHW, const doub
   return rc;
 }
 
-omm_status omm_kernel_gemm_tc_tiled(int M, int N, int K, const double* A, const double* B, double alpha,
-                                    double beta, double* C, int npass, int tile_n, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// the persistent launch the solver uses for its line-search GEMMs, on freshly split operands;
+// block_sparse: skip the 64-wide K blocks where B is zero (lists built from B)
+omm_status gemm_tc_impl(const char* name, int M, int N, int K, const double* A, const double* B, double alpha,
+                        double beta, double* C, int npass, int tile_n, bool block_sparse, void* stream) {
   if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || (npass != 1 && npass != 3) ||
       (tile_n != 128 && tile_n != 256)) {
-    set_last_error("omm_kernel_gemm_tc_tiled: invalid argument");
+    set_last_error(std::string(name) + ": invalid argument");
     return OMM_ERR_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -179,6 +185,7 @@ omm_status omm_kernel_gemm_tc_tiled(int M, int N, int K, const double* A, const 
   __nv_bfloat16* buf = nullptr;
   int* err = nullptr;
   tc::GroupDesc* desc = nullptr;
+  tc::BlockLists lists;
   omm_status rc = OMM_OK;
   try {
     const size_t na = (size_t)M * ld, nb = (size_t)N * ld;
@@ -187,7 +194,8 @@ omm_status omm_kernel_gemm_tc_tiled(int M, int N, int K, const double* A, const 
         cudaMalloc((void**)&desc, sizeof(tc::GroupDesc)) != cudaSuccess) {
       cudaGetLastError();
       if (buf) cudaFree(buf);
-      set_last_error("omm_kernel_gemm_tc_tiled: device allocation failed");
+      if (err) cudaFree(err);
+      set_last_error(std::string(name) + ": device allocation failed");
       return OMM_ERR_OOM;
     }
     __nv_bfloat16 *a_hi = buf, *a_lo = buf + na, *b_hi = buf + 2 * na, *b_lo = buf + 2 * na + nb;
@@ -196,9 +204,9 @@ omm_status omm_kernel_gemm_tc_tiled(int M, int N, int K, const double* A, const 
     tc::split(st, B, N, K, K, b_hi, b_lo, ld, nullptr);
     tc::Operand oa = tc::make_operand(a_hi, M, K, ld, 2, true);
     tc::Operand ob = tc::make_operand(b_hi, N, K, ld, 2, false);
-    // the persistent launch the solver uses for its line-search GEMMs
+    if (block_sparse) tc::block_lists(st, B, N, K, K, tile_n, lists);
     const tc::Epilogue ep{C, N, N, 0, alpha, beta, M, N, nullptr, err};
-    const tc::GroupDesc g = tc::make_group(oa, ob, K, ep, 0, tile_n);
+    const tc::GroupDesc g = tc::make_group(oa, ob, K, ep, 0, tile_n, block_sparse ? &lists : nullptr);
     OMM_CUDA_TRY(cudaMemcpyAsync(desc, &g, sizeof(g), cudaMemcpyHostToDevice, st));
     tc::gemm_persistent(st, desc, 1, tc::tiles_of(ep, tile_n), npass == 3 ? tc::pairs_split3() : tc::pairs_single(),
                         err, tile_n);
@@ -206,21 +214,37 @@ omm_status omm_kernel_gemm_tc_tiled(int M, int N, int K, const double* A, const 
     OMM_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
     if (h != 0) {
-      set_last_error("omm_kernel_gemm_tc_tiled: a bounded device wait expired (code " + std::to_string(h) + ")");
+      set_last_error(std::string(name) + ": a bounded device wait expired (code " + std::to_string(h) + ")");
       rc = OMM_ERR_TIMEOUT;
     }
   } catch (const CudaError& e) {
-    rc = cuda_fail("omm_kernel_gemm_tc_tiled", e);
+    rc = cuda_fail(name, e);
   }
   if (buf) cudaFree(buf);
   if (err) cudaFree(err);
   if (desc) cudaFree(desc);
+  tc::free_block_lists(lists);
   return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+omm_status omm_kernel_gemm_tc_tiled(int M, int N, int K, const double* A, const double* B, double alpha,
+                                    double beta, double* C, int npass, int tile_n, void* stream) {
+  return gemm_tc_impl("omm_kernel_gemm_tc_tiled", M, N, K, A, B, alpha, beta, C, npass, tile_n, false, stream);
 }
 
 omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double* B, double alpha,
                               double beta, double* C, int npass, void* stream) {
-  return omm_kernel_gemm_tc_tiled(M, N, K, A, B, alpha, beta, C, npass, 256, stream);
+  return gemm_tc_impl("omm_kernel_gemm_tc", M, N, K, A, B, alpha, beta, C, npass, 256, false, stream);
+}
+
+omm_status omm_kernel_gemm_tc_blocksparse(int M, int N, int K, const double* A, const double* B, double alpha,
+                                          double beta, double* C, int npass, int tile_n, void* stream) {
+  return gemm_tc_impl("omm_kernel_gemm_tc_blocksparse", M, N, K, A, B, alpha, beta, C, npass, tile_n, true,
+                      stream);
 }
 
 omm_status omm_kernel_gemm_emu(int M, int N, int K, const double* A, const double* B, double alpha,

@@ -36,6 +36,7 @@ struct MixedState {
   double* dY = nullptr;                                // [HC - HC_ref; SC - SC_ref], 2n x m
   double* Wref = nullptr;                              // [S_W | H_W] at the last refresh, n x 2n
   tc::Operand opHS, opP, opG, opD, opY, opYT, opW;
+  tc::BlockLists hs_blocks[2];  // block sparsity of [H~; S] for 256- and 128-row blocks (Sec. 2.6)
   int* err = nullptr;
   // the four line-search GEMMs as persistent-launch descriptors (device), built on first use
   tc::GroupDesc* plans = nullptr;
@@ -97,6 +98,9 @@ MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const 
     ms->opY = tc::make_operand(ms->Y_hi, 4L * n, m, ldm, 2, false);
     ms->opYT = tc::make_operand(ms->YT_hi, m, 4L * n, ld2n, 2, false);
     ms->opW = tc::make_operand(ms->W_hi, n, 4L * n, ld2n, 2, true);
+    // finite-range H and S: the operator product skips the K blocks where [H~; S] is zero
+    tc::block_lists(st, HS, 2L * m, m, m, 256, ms->hs_blocks[0]);
+    tc::block_lists(st, HS, 2L * m, m, m, 128, ms->hs_blocks[1]);
   } catch (...) {
     mixed_destroy(ms);
     throw;
@@ -130,6 +134,7 @@ MixedView mixed_view(MixedState* ms) {
   v.opYT = &ms->opYT;
   v.opW = &ms->opW;
   v.err = ms->err;
+  v.hs_blocks = ms->hs_blocks;
   v.npass = ms->npass;
   v.precond = ms->precond;
   return v;
@@ -137,6 +142,8 @@ MixedView mixed_view(MixedState* ms) {
 
 void mixed_update_H(MixedState* ms, cudaStream_t st, const double* HS) {
   tc::split(st, HS, ms->m, ms->m, ms->m, ms->HS_hi, ms->HS_lo, ms->ldm, nullptr);
+  tc::block_lists(st, HS, 2L * ms->m, ms->m, ms->m, 256, ms->hs_blocks[0]);  // the pattern may change
+  tc::block_lists(st, HS, 2L * ms->m, ms->m, ms->m, 128, ms->hs_blocks[1]);
 }
 
 void mixed_destroy(MixedState* ms) {
@@ -149,6 +156,8 @@ void mixed_destroy(MixedState* ms) {
   if (ms->dY) cudaFree(ms->dY);
   if (ms->Wref) cudaFree(ms->Wref);
   if (ms->plans) cudaFree(ms->plans);
+  tc::free_block_lists(ms->hs_blocks[0]);
+  tc::free_block_lists(ms->hs_blocks[1]);
   delete ms;
 }
 
@@ -220,12 +229,18 @@ void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double
   const int K[4] = {m, m, m, 4 * n};
   const tc::Epilogue* ep[4] = {&epg, &ehd, &epr, &eg};
   for (int k = ms->precond ? 0 : 1; k < 4; ++k) {  // without P there is no P G product
-    // output tile width from the autotuner (timed once per shape in a process)
+    // output tile width from the autotuner (timed once per shape in a process); the operator
+    // product runs block-sparse over [H~; S]
+    tc::GemmSpec spec{opA[k], opB[k], K[k], *ep[k]};
+    if (k == kPlanHD) {
+      spec.sparse[0] = &ms->hs_blocks[0];
+      spec.sparse[1] = &ms->hs_blocks[1];
+    }
     double ms_tune = 0.0;
-    ms->plan_bn[k] = tc::choose_tile_width(st, {tc::GemmSpec{opA[k], opB[k], K[k], *ep[k]}}, tc::pairs_split3(),
-                                           &ms_tune);
+    ms->plan_bn[k] = tc::choose_tile_width(st, {spec}, tc::pairs_split3(), &ms_tune);
     ms->ms_autotune += ms_tune;
-    h[k] = tc::make_group(*opA[k], *opB[k], K[k], *ep[k], 0, ms->plan_bn[k]);
+    h[k] = tc::make_group(*opA[k], *opB[k], K[k], *ep[k], 0, ms->plan_bn[k],
+                          spec.sparse[ms->plan_bn[k] == 256 ? 0 : 1]);
     ms->plan_tiles[k] = tc::tiles_of(*ep[k], ms->plan_bn[k]);
   }
   if (!ms->plans) alloc(&ms->plans, 4);

@@ -15,6 +15,7 @@ struct MixedView {
   __nv_bfloat16 *G_hi, *D_hi, *Y_hi, *YT_hi, *W_hi;  // [hi; lo] stacks
   double *Gref, *dY, *Wref;
   const tc::Operand *opHS, *opP, *opG, *opD, *opY, *opYT, *opW;
+  const tc::BlockLists* hs_blocks;  // [0]: 256-row blocks, [1]: 128-row blocks
   int* err;
   int npass;
   bool precond;

@@ -382,6 +382,26 @@ __device__ __forceinline__ int find_group(const GroupDesc* __restrict__ groups, 
 // b, b + gridDim.x, ... of all groups. The accumulator is double-buffered in
 // TMEM (2 x 256 columns) so the epilogue of one tile overlaps the main loop
 // of the next; the producer's stage ring continues across tiles.
+// The K blocks of one output tile: all of them, or the listed ones where B is block-sparse.
+struct KBlocks {
+  const int* list;  // null: 0 .. count-1
+  int count;
+  __device__ __forceinline__ int at(int i) const { return list ? list[i] : i; }
+};
+__device__ __forceinline__ KBlocks tile_kblocks(const GroupDesc* g, int local, int tiles_m) {
+  KBlocks kb;
+  if (g->kb_off != nullptr) {
+    const int nb = local / tiles_m;
+    const int o0 = g->kb_off[nb];
+    kb.list = g->kb_idx + o0;
+    kb.count = g->kb_off[nb + 1] - o0;
+  } else {
+    kb.list = nullptr;
+    kb.count = (g->K + BK - 1) / BK;
+  }
+  return kb;
+}
+
 // With a chunked pair list (emulation levels) every chunk of a tile is one
 // accumulator round: the MMA thread fills a TMEM buffer with the chunk's pairs,
 // the epilogue adds it to C, and the chunks of a tile stay on one CTA, in order.
@@ -450,7 +470,8 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
       const CUtensorMap* mB = reinterpret_cast<const CUtensorMap*>(&g->b);
       const int local = tile - g->tile_begin, tiles_m = (g->ep.M + BM - 1) / BM;
       const int m0 = (local % tiles_m) * BM, n0 = (local / tiles_m) * TBN;
-      const int nkb = (g->K + BK - 1) / BK;
+      const KBlocks kbs = tile_kblocks(g, local, tiles_m);
+      const int nkb = kbs.count;
       const int p0 = chunk_begin(unit_c0(u));
       const int total = FUSED ? nkb : (chunk_end(unit_c1(u) - 1) - p0) * nkb;
       for (int t = 0; t < total; ++t, ++it) {
@@ -465,12 +486,13 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
         const uint32_t sa = smem_u32(smem + q * SB);
         mbar_expect_tx(full, SB);
         if (FUSED) {
-          tma_load_2d(sa, mA, full, t * BK, m0);
-          tma_load_2d(sa + A_BYTES, mA, full, t * BK, g->rowsA + m0);
-          tma_load_2d(sa + 2 * A_BYTES, mB, full, t * BK, n0);
-          tma_load_2d(sa + 2 * A_BYTES + TB_BYTES, mB, full, t * BK, g->rowsB + n0);
+          const int kb = kbs.at(t);
+          tma_load_2d(sa, mA, full, kb * BK, m0);
+          tma_load_2d(sa + A_BYTES, mA, full, kb * BK, g->rowsA + m0);
+          tma_load_2d(sa + 2 * A_BYTES, mB, full, kb * BK, n0);
+          tma_load_2d(sa + 2 * A_BYTES + TB_BYTES, mB, full, kb * BK, g->rowsB + n0);
         } else {
-          const int p = p0 + t / nkb, kb = t % nkb;
+          const int p = p0 + t / nkb, kb = kbs.at(t % nkb);
           tma_load_2d(sa, mA, full, kb * BK, (int)pl.a[p] * g->rowsA + m0);
           tma_load_2d(sa + A_BYTES, mB, full, kb * BK, (int)pl.b[p] * g->rowsB + n0);
         }
@@ -481,10 +503,11 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
     constexpr uint32_t idesc = idesc_bf16(BM, TBN);
     uint32_t it = 0, lt = 0;
     for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
-      const GroupDesc* g = groups + find_group(groups, ngroups, unit_tile(u));
+      const int tile = unit_tile(u);
+      const GroupDesc* g = groups + find_group(groups, ngroups, tile);
       const int* skip = g->ep.skip;
       if (skip != nullptr && (skip[0] | skip[1])) continue;
-      const int nkb = (g->K + BK - 1) / BK;
+      const int nkb = tile_kblocks(g, tile - g->tile_begin, (g->ep.M + BM - 1) / BM).count;
       for (int c = unit_c0(u); c < unit_c1(u) && !*abort_flag; ++c) {
         const uint32_t buf = lt & 1, use = lt >> 1;
         if (!mbar_wait(smem_u32(&bars[2 * NS + 2 + buf]), (use & 1) ^ 1)) {
@@ -725,7 +748,8 @@ void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const Pair
 
 int tiles_of(const Epilogue& ep, int bn) { return ((ep.M + BM - 1) / BM) * ((ep.N + bn - 1) / bn); }
 
-GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin, int bn) {
+GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin, int bn,
+                     const BlockLists* sparse) {
   if (bn != 256 && bn != 128) throw CudaError{cudaErrorInvalidValue, "tc::make_group: tile width"};
   // the TMA boxes must match the tile: A in 128-row boxes, B in boxes of the tile width
   if (A.box_rows != BM || (bn == 256 && B.box_rows != 256))
@@ -739,6 +763,10 @@ GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& 
   g.rowsB = (int)B.rows;
   g.tile_begin = tile_begin;
   g.bn = bn;
+  g.kb_off = sparse ? sparse->off : nullptr;
+  g.kb_idx = sparse ? sparse->idx : nullptr;
+  if (sparse && sparse->nblocks != (ep.N + bn - 1) / bn)
+    throw CudaError{cudaErrorInvalidValue, "tc::make_group: block lists do not match the tiles"};
   return g;
 }
 
@@ -794,12 +822,12 @@ void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, 
 }
 
 void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K, const PairList& pl,
-                     const Epilogue& ep, double* partial, long partial_capacity) {
+                     const Epilogue& ep, double* partial, long partial_capacity, const BlockLists* sparse) {
   prepare_persistent();
   check_pairs(pl, A.slices, B.slices);
   const int tiles = tiles_of(ep);
   if (tiles <= 0 || K <= 0) return;
-  const GroupDesc g = make_group(A, B, K, ep, 0);
+  const GroupDesc g = make_group(A, B, K, ep, 0, BN, sparse);
   const bool fused = is_split3(pl) && pl.nchunk <= 1 && A.slices >= 2 && B.slices >= 2;
   // a GEMM of few tiles spreads its chunks over the SMs when scratch for them was given
   const int nchunk = pl.nchunk > 0 ? pl.nchunk : 1;
@@ -832,6 +860,81 @@ void gemm_grouped(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int
   OMM_LAUNCH_CHECK();
 }
 
+// ------------------------------------------------------------------ block sparsity of B
+namespace {
+// occ[rb * nkb + kb] = 1 if rows [128 rb, 128 rb + 128) x columns [64 kb, 64 kb + 64) hold a nonzero
+__global__ void __launch_bounds__(256)
+occupancy_kernel(const double* __restrict__ B, long rows, long cols, long ld, int nkb, unsigned char* occ) {
+  const long blk = blockIdx.x;
+  const long rb = blk / nkb, kb = blk % nkb;
+  int any = 0;
+  for (int e = threadIdx.x; e < 128 * 64; e += blockDim.x) {
+    const long r = rb * 128 + e / 64, c = kb * 64 + e % 64;
+    if (r < rows && c < cols && B[r * ld + c] != 0.0) any = 1;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) occ[blk] = (unsigned char)any;
+}
+}  // namespace
+
+void block_lists(cudaStream_t st, const double* B, long rows, long cols, long ld, int bn, BlockLists& bl) {
+  if (bn != 128 && bn != 256) throw CudaError{cudaErrorInvalidValue, "tc::block_lists: tile width"};
+  const int nkb = (int)((cols + BK - 1) / BK);
+  const long nrb128 = (rows + 127) / 128;
+  unsigned char* occ = nullptr;
+  std::vector<unsigned char> h(nrb128 * nkb);
+  OMM_CUDA_TRY(cudaMalloc((void**)&occ, h.size()));
+  try {
+    occupancy_kernel<<<(unsigned)(nrb128 * nkb), 256, 0, st>>>(B, rows, cols, ld, nkb, occ);
+    OMM_LAUNCH_CHECK();
+    OMM_CUDA_TRY(cudaMemcpyAsync(h.data(), occ, h.size(), cudaMemcpyDeviceToHost, st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
+  } catch (...) {
+    cudaFree(occ);
+    throw;
+  }
+  cudaFree(occ);
+  const int per = bn / 128;  // 128-row blocks per row block of bn
+  const int nblocks = (int)((rows + bn - 1) / bn);
+  std::vector<int> off(nblocks + 1, 0), idx;
+  for (int r = 0; r < nblocks; ++r) {
+    const size_t before = idx.size();
+    for (int kb = 0; kb < nkb; ++kb) {
+      bool any = false;
+      for (int q = 0; q < per; ++q) {
+        const long r128 = (long)r * per + q;
+        if (r128 < nrb128 && h[r128 * nkb + kb]) any = true;
+      }
+      if (any) idx.push_back(kb);
+    }
+    if (idx.size() == before) idx.push_back(0);  // an all-zero block row still writes its zeros
+    off[r + 1] = (int)idx.size();
+  }
+  if (bl.off != nullptr && (bl.nblocks != nblocks || bl.dense != (long)nblocks * nkb))
+    throw CudaError{cudaErrorInvalidValue, "tc::block_lists: shape changed"};
+  if (bl.off == nullptr) {  // capacity for a dense pattern: later updates rewrite in place
+    bl.nblocks = nblocks;
+    bl.dense = (long)nblocks * nkb;
+    try {
+      OMM_CUDA_TRY(cudaMalloc((void**)&bl.off, off.size() * sizeof(int)));
+      OMM_CUDA_TRY(cudaMalloc((void**)&bl.idx, (size_t)bl.dense * sizeof(int)));
+    } catch (...) {
+      free_block_lists(bl);
+      throw;
+    }
+  }
+  bl.nnz = (long)idx.size();
+  // the stream was synchronised above, so no earlier launch still reads the old lists
+  OMM_CUDA_TRY(cudaMemcpy(bl.off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+  OMM_CUDA_TRY(cudaMemcpy(bl.idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice));
+}
+
+void free_block_lists(BlockLists& bl) {
+  if (bl.off) cudaFree(bl.off);
+  if (bl.idx) cudaFree(bl.idx);
+  bl = BlockLists{};
+}
+
 // ------------------------------------------------------------------ tile-width autotuner
 namespace {
 std::mutex& tune_mutex() {
@@ -851,6 +954,7 @@ int choose_tile_width(cudaStream_t st, const std::vector<GemmSpec>& specs, const
   long out_elems = 0;
   for (const GemmSpec& g : specs) {
     key += ":" + std::to_string(g.ep.M) + "x" + std::to_string(g.ep.N) + "x" + std::to_string(g.K);
+    if (g.sparse[0]) key += "s" + std::to_string(g.sparse[0]->nnz) + "/" + std::to_string(g.sparse[1]->nnz);
     out_elems += (long)g.ep.M * g.ep.N;
   }
   {
@@ -886,7 +990,7 @@ int choose_tile_width(cudaStream_t st, const std::vector<GemmSpec>& specs, const
       int tiles = 0;
       for (const GemmSpec& g : specs) {
         Epilogue ep{scratch + off, g.ep.N, g.ep.N, 0, 1.0, 0.0, g.ep.M, g.ep.N, nullptr, err};
-        h.push_back(make_group(*g.A, *g.B, g.K, ep, tiles, bn));
+        h.push_back(make_group(*g.A, *g.B, g.K, ep, tiles, bn, g.sparse[bn == 256 ? 0 : 1]));
         tiles += tiles_of(ep, bn);
         off += (long)g.ep.M * g.ep.N;
       }

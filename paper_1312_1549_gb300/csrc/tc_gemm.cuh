@@ -73,14 +73,34 @@ int tile_n();
 int tiles_of(const Epilogue& ep, int bn = 256);  // output tiles of one GEMM (128 x bn)
 
 // One GEMM of a grouped launch (device array element; tensor maps in global memory).
+// Block sparsity of a B operand (rows x K): for every block of bn rows, the 64-wide K blocks that
+// hold a nonzero (CSR on the device: blocks of row block r are idx[off[r] .. off[r+1]), at least
+// one per row block). A product skips the K blocks where B is exactly zero: the FP32 sums, and so
+// the results, are the same as the dense product's.
+struct BlockLists {
+  int* off = nullptr;  // device, nblocks + 1
+  int* idx = nullptr;  // device
+  int nblocks = 0;
+  long nnz = 0;
+  long dense = 0;  // nblocks x K blocks
+};
+// (re)computes bl for B (rows x cols float64, leading dimension ld, device) and row blocks of bn;
+// the first call allocates room for a dense pattern, later calls (same shape) rewrite in place so
+// that descriptors holding the pointers stay valid. Synchronises the stream.
+void block_lists(cudaStream_t st, const double* B, long rows, long cols, long ld, int bn, BlockLists& bl);
+void free_block_lists(BlockLists& bl);
+
 struct alignas(64) GroupDesc {
   TensorMap a;
   TensorMap b;
   Epilogue ep;
   int K, rowsA, rowsB, tile_begin;
   int bn;  // output tile width, 256 or 128 (all groups of one launch share it)
+  const int* kb_off;  // block sparsity of B for row blocks of bn (null: dense)
+  const int* kb_idx;
 };
-GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin, int bn = 256);
+GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin, int bn = 256,
+                     const BlockLists* sparse = nullptr);
 // groups_dev: ngroups descriptors in device memory, sorted by tile_begin; all share the pair list
 void prepare_grouped();     // kernel attributes (call before a stream capture)
 void prepare_persistent();
@@ -92,7 +112,8 @@ void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, 
 // partial (optional, partial_capacity doubles): scratch that lets a GEMM of few output tiles run
 // each chunk of its pair list on its own CTA and add the chunks afterwards, in chunk order.
 void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K, const PairList& pl,
-                     const Epilogue& ep, double* partial = nullptr, long partial_capacity = 0);
+                     const Epilogue& ep, double* partial = nullptr, long partial_capacity = 0,
+                     const BlockLists* sparse = nullptr);
 void gemm_grouped(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl);
 
 // Tile-width autotuner: times one persistent launch over these GEMMs (the operands as given,
@@ -103,7 +124,8 @@ struct GemmSpec {
   const Operand* A;
   const Operand* B;
   int K;
-  Epilogue ep;  // only M and N are used
+  Epilogue ep;                              // only M and N are used
+  const BlockLists* sparse[2] = {nullptr, nullptr};  // block lists of B for bn = 256 and 128
 };
 int choose_tile_width(cudaStream_t st, const std::vector<GemmSpec>& specs, const PairList& pl,
                       double* ms_spent = nullptr);

@@ -156,11 +156,16 @@ def quartic_coefficients(SWHW, Proj, E, stream=None):
     return np.array(list(out))
 
 
-def gemm_tc(A, B, C, alpha=1.0, beta=0.0, npass=3, stream=None, tile_n=None):
-    """C = alpha A B^T + beta C on the BF16 tensor cores (split operands); tile_n 256 or 128."""
+def gemm_tc(A, B, C, alpha=1.0, beta=0.0, npass=3, stream=None, tile_n=None, block_sparse=False):
+    """C = alpha A B^T + beta C on the BF16 tensor cores (split operands); tile_n 256 or 128;
+    block_sparse skips the K blocks where B is zero."""
     M, K = A.shape
     Nn = B.shape[0]
-    if tile_n is None:
+    if block_sparse:
+        N.check(N.lib().omm_kernel_gemm_tc_blocksparse(M, Nn, K, _ptr(A), _ptr(B), float(alpha), float(beta),
+                                                       _ptr(C), int(npass), int(tile_n or 256),
+                                                       _stream_handle(stream)), "omm_kernel_gemm_tc_blocksparse")
+    elif tile_n is None:
         N.check(N.lib().omm_kernel_gemm_tc(M, Nn, K, _ptr(A), _ptr(B), float(alpha), float(beta), _ptr(C),
                                            int(npass), _stream_handle(stream)), "omm_kernel_gemm_tc")
     else:

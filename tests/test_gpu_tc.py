@@ -164,3 +164,26 @@ def test_spd_inverse_sliced_preconditioner_matches_oracle(S):
     P_ref = omm.preconditioner(p.S, p.T, p.tau)
     P = S.spd_inverse(dev(p.S + p.T / p.tau), sliced=True).cpu().numpy()
     assert np.abs(P - P_ref).max() <= 1e-11 * np.abs(P_ref).max()
+
+
+# ---------------------------------------------------------------- block-sparse operator products
+@pytest.mark.parametrize("tile_n", [256, 128])
+@pytest.mark.parametrize("M,N,K", [(256, 1024, 640), (130, 700, 333), (1024, 2048, 1024)])
+def test_gemm_tc_blocksparse_equals_dense(S, M, N, K, tile_n):
+    """Skipping the all-zero 64-wide K blocks of B changes no bit of the result."""
+    rng = np.random.default_rng(M + 3 * N + K + tile_n)
+    A = rng.normal(size=(M, K))
+    B = rng.normal(size=(N, K))
+    # zero a random pattern of (tile_n rows x 64 columns) blocks, and a whole block row
+    for r0 in range(0, N, tile_n):
+        for k0 in range(0, K, 64):
+            if rng.uniform() < 0.6:
+                B[r0:r0 + tile_n, k0:k0 + 64] = 0.0
+    B[:min(tile_n, N), :] = 0.0
+    C0 = rng.normal(size=(M, N))
+    Cd, Cs = dev(C0), dev(C0)
+    S.gemm_tc(dev(A), dev(B), Cd, alpha=-4.0, beta=1.0, npass=3, tile_n=tile_n)
+    S.gemm_tc(dev(A), dev(B), Cs, alpha=-4.0, beta=1.0, npass=3, tile_n=tile_n, block_sparse=True)
+    assert torch.equal(Cd, Cs)
+    ref = -4.0 * A @ B.T + C0
+    assert np.all(np.abs(Cs.cpu().numpy() - ref) <= 2.0 ** -14 * 4.0 * np.abs(A) @ np.abs(B).T + 1e-12)
