@@ -393,8 +393,12 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       const int bn = tc::choose_tile_width(b->st, *specs[k], tc::pairs_split3(), &ms_tune);
       b->ms_autotune += ms_tune;
       b->tile_width[k] = bn;
-      for (const tc::GemmSpec& sp : *specs[k])
-        groups[k]->push_back(tc::make_group(*sp.A, *sp.B, sp.K, sp.ep, 0, bn, sp.sparse[bn == 256 ? 0 : 1]));
+      for (size_t i = 0; i < specs[k]->size(); ++i) {
+        const tc::GemmSpec& sp = (*specs[k])[i];
+        const tc::BlockLists* bl = sp.sparse[bn == 256 ? 0 : 1];
+        groups[k]->push_back(tc::make_group(*sp.A, *sp.B, sp.K, sp.ep, 0, bn, bl));
+        if (bl && k == 1) b->gemm_flop[1][i] *= tc::block_density(bl);  // issued flops of the visited blocks
+      }
       std::stable_sort(groups[k]->begin(), groups[k]->end(),
                        [](const tc::GroupDesc& x, const tc::GroupDesc& y) { return x.K > y.K; });
       int t = 0;

@@ -155,7 +155,8 @@ void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, in
   const tc::PairList pl = level_chunks(K, s);
   if (t_prof) t_prof->begin(st);
   tc::gemm_persistent(st, A, B, K, pl, ep, partial, partial_capacity, sparse);
-  if (t_prof) t_prof->end(st, 2.0 * ep.M * (double)ep.N * K * pl.n);  // issued tensor flops
+  // issued tensor flops (only the visited K blocks of a block-sparse product)
+  if (t_prof) t_prof->end(st, 2.0 * ep.M * (double)ep.N * K * pl.n * tc::block_density(sparse));
 }
 
 }  // namespace emu

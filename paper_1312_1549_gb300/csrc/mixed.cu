@@ -279,7 +279,7 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   // [H~ D ; S D] (n x m layout): one GEMM over the stacked [H~; S]
   pf.begin(st);
   run_plan(ms, st, kPlanHD);
-  pf.end(st, 4.0 * np * n * (double)m * m);
+  pf.end(st, 4.0 * np * n * (double)m * m * tc::block_density(&ms->hs_blocks[ms->plan_bn[kPlanHD] == 256 ? 0 : 1]));
   tc::split(st, Y4 + 2 * nm, 2L * n, m, m, ms->Y_hi + 2L * n * ms->ldm, ms->Y_lo + 2L * n * ms->ldm, ms->ldm, sc);
   // [H' | S' | H'' | S''] = D [HC; SC; HD; SD]^T (Eqs. 14-15)
   pf.begin(st);

@@ -89,6 +89,10 @@ struct BlockLists {
 // that descriptors holding the pointers stay valid. Synchronises the stream.
 void block_lists(cudaStream_t st, const double* B, long rows, long cols, long ld, int bn, BlockLists& bl);
 void free_block_lists(BlockLists& bl);
+// fraction of the K blocks a product over these lists visits (1 for a dense product)
+inline double block_density(const BlockLists* bl) {
+  return (bl == nullptr || bl->dense == 0) ? 1.0 : (double)bl->nnz / (double)bl->dense;
+}
 
 struct alignas(64) GroupDesc {
   TensorMap a;
