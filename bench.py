@@ -2,13 +2,18 @@
 """Time-to-solution of the OMM solve on GB300 (and its oracle on the host cores).
 
 One step = one whole solve of the Si512 DZP-like workload (m = 6656 basis
-functions, n = 1024 Wannier functions): omm_create (shift, float64 Cholesky
+functions, n = 1024 Wannier functions): omm_create (shift, float64-class Cholesky
 inverse of S + T/tau, operand splits) + omm_solve to max|G| < 1e-9
-(certified in float64) + the density matrix D. Inputs are resident in HBM
-when the timed region starts; H, S, T (354 MB each) are larger than L2.
+(certified with float64-class products) + the density matrix D. Inputs are
+resident in HBM when the timed region starts; H, S, T (354 MB each) are larger
+than L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config 2] [--precision mixed|fp64]
+                    [--workload si512_dzp] [--precision mixed|fp64]
+
+Workloads: si64_sz, si512_dzp (default), water256_dzp (single solves), batch64
+(64 independent instances in one batched solve), si4096_sequence (10
+warm-started Hamiltonians).
 
 Prints one JSON line (rank 0).
 """
@@ -28,20 +33,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "OMM time-to-solution & GEMM TFLOP/s, mixed vs FP64 GPU at |ΔE|/|E|≤1e-9"
 WORKLOADS = {
-    1: "si64_sz: Si 64-atom diamond, sp single-zeta, m=256, n=128, tau=5 Ha, eta=HOMO+0.1 Ha, |G|inf<1e-9",
-    2: "si512_dzp: Si 512-atom diamond, DZP-like 13 orbitals/atom, m=6656, n=1024, tau=5 Ha, "
+    "si64_sz": "si64_sz: Si 64-atom diamond, sp single-zeta, m=256, n=128, tau=5 Ha, eta=HOMO+0.1 Ha, |G|inf<1e-9",
+    "si512_dzp": "si512_dzp: Si 512-atom diamond, DZP-like 13 orbitals/atom, m=6656, n=1024, tau=5 Ha, "
        "eta=HOMO+0.1 Ha, |G|inf<1e-9",
-    3: "water256_dzp: 256 H2O at 1 g/cm3, DZP-like 23 orbitals/molecule, m=5888, n=1024, tau=5 Ha, "
+    "water256_dzp": "water256_dzp: 256 H2O at 1 g/cm3, DZP-like 23 orbitals/molecule, m=5888, n=1024, tau=5 Ha, "
        "eta=HOMO+0.1 Ha, |G|inf<1e-9",
-    4: "batch64: 64 independent Si / water instances (DZ, TZ, DZP, DZP+p / DZ+d, DZP, TZP bases), "
+    "batch64": "batch64: 64 independent Si / water instances (DZ, TZ, DZP, DZP+p / DZ+d, DZP, TZP bases), "
        "m ~ U[512,4096], n/m 0.125-0.25, one batched solve (grouped tensor-core launches in a CUDA graph), "
        "|G|inf<1e-9 each",
-    5: "si4096_sz_warmstart: Si 4096-atom single-zeta, m=16384, n=8192, 10 Hamiltonians "
+    "si4096_sequence": "si4096_sz_warmstart: Si 4096-atom single-zeta, m=16384, n=8192, 10 Hamiltonians "
        "H_k = H_0 + k delta (on-site, sigma 0.01 Ha), each solve from the previous C, dE/dH each step",
 }
 # Line searches the float64 solve takes on each workload from its seeded C0
 # (measured with the float64 GPU path); used to extrapolate bounded oracle samples.
-FP64_LINE_SEARCHES = {1: 43, 2: 63, 3: 160}
+FP64_LINE_SEARCHES = {"si64_sz": 43, "si512_dzp": 63, "water256_dzp": 160}
 
 
 def load_peaks():
@@ -134,12 +139,12 @@ def shard(count, rank, world):
     return list(range(rank, count, world))
 
 
-def build_problem(config):
+def build_problem(workload):
     from synth import configs
-    return configs.CONFIGS[config]()
+    return configs.NAMED[workload]()
 
 
-def cpu_oracle_sample(p, config, n_iter=2):
+def cpu_oracle_sample(p, workload, n_iter=2):
     """Oracle (plain float64 numpy OMM) on the host cores: setup + n_iter line searches."""
     from oracle import omm as oomm
     t0 = time.perf_counter()
@@ -156,13 +161,13 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    p = build_problem(args.config)
-    iters = FP64_LINE_SEARCHES[args.config]
+    p = build_problem(args.workload)
+    iters = FP64_LINE_SEARCHES[args.workload]
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state; warm-up steps are not repeated
     times = []
     for _ in range(args.steps):
-        t_base, t_iter = cpu_oracle_sample(p, args.config)
+        t_base, t_iter = cpu_oracle_sample(p, args.workload)
         times.append(t_base + iters * t_iter)
     value = statistics.mean(times)
     cores = os.cpu_count()
@@ -172,7 +177,7 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": WORKLOADS[args.config], "l2": "inputs larger than L2"},
+           "config": {"workload": WORKLOADS[args.workload], "l2": "inputs larger than L2"},
            "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -183,12 +188,12 @@ def _base_line(args, value_s, world=1):
     return {"metric": METRIC, "value": value_s, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": value_s * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3+f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.config], "precision": "mixed",
+            "config": {"workload": WORKLOADS[args.workload], "precision": "mixed",
                        "l2": "inputs larger than L2", "parallelism": "1 GPU"}}
 
 
 def run_batch(args):
-    """Config 4: one batched solve of independent instances (create + solve per step)."""
+    """The batch workload: one batched solve of independent instances (create + solve per step)."""
     import numpy as np
     import torch
     from paper_1312_1549_gb300 import build as _build
@@ -198,7 +203,7 @@ def run_batch(args):
     # instances are independent: ranks take disjoint shards, no collective on the data path
     rank, world, local, dist = dist_setup(args.gpus)
     torch.cuda.set_device(local)
-    probs = [configs.config4_instance(i) for i in shard(args.instances, rank, world)]
+    probs = [configs.batch_instance(i) for i in shard(args.instances, rank, world)]
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     dev = [(t(p.H), t(p.S), t(p.T), p.n, p.eta, p.tau) for p in probs]
     C0 = [t(p.C0) for p in probs]
@@ -297,14 +302,14 @@ def run_batch(args):
 
 
 def run_sequence(args):
-    """Config 5: warm-started sequence H_k = H_0 + k delta, dE/dH each step."""
+    """The warm-start workload: sequence H_k = H_0 + k delta, dE/dH each step."""
     import numpy as np
     import torch
     from paper_1312_1549_gb300 import build as _build
     _build.build()
     from paper_1312_1549_gb300 import solver as S
     from synth import configs
-    p = configs.config5_base()
+    p = configs.si4096_sz()
     delta = configs.warm_start_delta(p, 1)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     H0, Sm, T, C0 = t(p.H), t(p.S), t(p.T), t(p.C0)
@@ -360,9 +365,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
-    ap.add_argument("--instances", type=int, default=64, help="config 4: batch size")
-    ap.add_argument("--sequence", type=int, default=10, help="config 5: Hamiltonians in the sequence")
+    ap.add_argument("--workload", default="si512_dzp", choices=list(WORKLOADS))
+    ap.add_argument("--instances", type=int, default=64, help="batch64: instances in the batch")
+    ap.add_argument("--sequence", type=int, default=10, help="si4096_sequence: Hamiltonians in the sequence")
     ap.add_argument("--native-certificate", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
@@ -372,9 +377,9 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.config == 4:
+    if args.workload == "batch64":
         return run_batch(args)
-    if args.config == 5:
+    if args.workload == "si4096_sequence":
         return run_sequence(args)
 
     import numpy as np
@@ -386,7 +391,7 @@ def main():
     rank, world, local, dist = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    p = build_problem(args.config)
+    p = build_problem(args.workload)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     H, Sm, T, C0 = t(p.H), t(p.S), t(p.T), t(p.C0)
     stream = torch.cuda.Stream(device=dev)
@@ -456,7 +461,7 @@ def main():
     out = {"metric": METRIC, "value": ms * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "bf16x3+f64" if mixed else "f64", "data": "synthetic",
-           "config": {"workload": WORKLOADS[args.config], "precision": args.precision,
+           "config": {"workload": WORKLOADS[args.workload], "precision": args.precision,
                       "certificate": ("native float64" if args.native_certificate or not mixed
                                       else "float64-class (sliced)"),
                       "l2": "inputs larger than L2 (H, S, T are m*m*8 bytes each)",
@@ -474,7 +479,7 @@ def main():
                                                  (iters * (6.0 * p.m * p.m * p.n + 12.0 * p.m * p.n * p.n))
                                                  / (it_ms * 1e-3) / 1e12),
            "roofline": roofline, "roofline_sliced": roofline_sliced, "gpu_launches": launches, "clocks": clocks}
-    if not args.no_exact_check and args.config in (1, 2, 3):
+    if not args.no_exact_check and args.workload in FP64_LINE_SEARCHES:
         from oracle import exact
         ex = exact.exact_minimum(p.H, p.S, p.n, want_matrices=False)
         out["rel_err_E_vs_exact"] = abs(energies[-1] - ex["E"]) / abs(ex["E"])
@@ -501,8 +506,8 @@ def main():
                       "d2h_bytes_per_step": (p.n * p.m + p.m * p.m + 1) * 8,
                       "api": "omm_create + omm_solve with pinned host H, S, T, C0 and host C, D, E"}
     if not args.no_cpu_baseline and world == 1:
-        t_base, t_iter = cpu_oracle_sample(p, args.config)
-        n_ls = FP64_LINE_SEARCHES[args.config]
+        t_base, t_iter = cpu_oracle_sample(p, args.workload)
+        n_ls = FP64_LINE_SEARCHES[args.workload]
         out["cpu_baseline"] = {"value": t_base + n_ls * t_iter, "unit": "s", "cores": os.cpu_count(),
                                "kind": "oracle",
                                "sample": f"oracle setup + initial state + certificate ({t_base:.1f} s) and 2 "

@@ -41,7 +41,9 @@ omm_status omm_kernel_spd_inverse(int m, const double* A, double* P, int* info, 
  * scheme; about 2^-50 of each row-scaled operand), with the 64 x 64 diagonal
  * blocks factored and inverted in float64. Arguments, ownership and *info as
  * for omm_kernel_spd_inverse; OMM_ERR_TIMEOUT if a bounded wait of a tensor-core
- * GEMM expired. Workspace: about (m^2 + 0.75 m^2) float64 + 5 m^2 bytes. */
+ * GEMM expired. Workspace (allocated inside the call): about 2.3 m^2 float64 plus
+ * 20 m^2 bytes of slices and up to 430 MB of chunk sums; a second stream runs the
+ * Y^T Y updates beside the factorisation and is joined before the call returns. */
 omm_status omm_kernel_spd_inverse_sliced(int m, const double* A, double* P, int* info, void* stream);
 
 /* Line minimum of the quartic a0 + a1 x + a2 x^2 + a3 x^3 + a4 x^4 (Sec. 2.3,

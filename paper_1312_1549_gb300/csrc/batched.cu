@@ -418,7 +418,7 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
     upload_groups(b->st, &b->gG, gg);
     OMM_CUDA_TRY(cudaStreamSynchronize(b->st));
     // capture one line search of the whole batch
-    tc::prepare_grouped();
+    tc::prepare_persistent();
     cudaStream_t cap = nullptr;
     OMM_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaStream_t saved = b->st;

@@ -19,12 +19,15 @@
 //     Y21 = -(Y22 L21) Y11                         (Y = L^-1)
 //   lauum(Y) = Y^T Y:  P22 = lauum(Y22);  P21 = Y22^T Y21;
 //     P11 = lauum(Y11) + Y21^T Y21
-// with 64 x 64 leaves factored and inverted in float64 by one CTA.
+// with 64 x 64 leaves factored and inverted in float64 by one CTA (which also writes the leaf's
+// block of Y^T Y). The P updates of a node run on a second stream as soon as its Y is final,
+// beside the factorisation of the blocks that follow.
 #include "emu.cuh"
 #include "omm_internal.cuh"
 #include "tc_gemm.cuh"
 
 #include <algorithm>
+#include <vector>
 
 namespace omm {
 namespace {
@@ -195,97 +198,112 @@ constexpr int kInvSlices = 10;
 
 long round8(long x) { return (x + 7) / 8 * 8; }
 
+// scratch of one stream's products
+struct Lane {
+  cudaStream_t st = nullptr;
+  double* tr0 = nullptr;     // float64 transposes
+  double* tr1 = nullptr;
+  __nv_bfloat16* sl0 = nullptr;  // slices of two operands
+  __nv_bfloat16* sl1 = nullptr;
+  double* partial = nullptr;  // per-chunk sums of the products with few output tiles
+  long partial_cap = 0;
+};
+
 struct SlicedWork {
   int m = 0;
   double* A = nullptr;       // the matrix, factor L in its lower triangle
   double* Y = nullptr;       // L^-1 (lower triangle, zero above)
   double* P = nullptr;
-  double* tr0 = nullptr;     // float64 scratch: transposes and one product
-  double* tr1 = nullptr;
-  double* prod = nullptr;
+  double* prod = nullptr;    // one product of the factorisation
   double* leaf = nullptr;    // NB x NB inverse of a diagonal block
-  __nv_bfloat16* sl0 = nullptr;  // slices of two operands
-  __nv_bfloat16* sl1 = nullptr;
   int* info = nullptr;
   int* err = nullptr;
-  double* partial = nullptr;  // per-chunk sums of the products with few output tiles
-  long partial_cap = 0;
+  Lane main, side;           // factorisation and inverse on `main`; the P = Y^T Y updates on `side`
+  std::vector<cudaEvent_t> events;
 };
 
 // C (M x N, ldc) = alpha A B^T + beta C with A (M x K, lda) and B (N x K, ldb) row-major;
 // the slices of A go to sl0, those of B to sl1 (or B = A: one slicing, both maps)
-void sliced_nt(cudaStream_t st, SlicedWork& w, int M, int N, int K, double alpha, const double* A, long lda,
-               const double* B, long ldb, double beta, double* C, long ldc) {
+void sliced_nt(Lane& L, int* err, int M, int N, int K, double alpha, const double* A, long lda, const double* B,
+               long ldb, double beta, double* C, long ldc) {
   const long ld = round8(K);
-  emu::slice_rows(st, A, M, K, lda, kInvSlices, w.sl0, ld, nullptr);
-  const tc::Operand oa = tc::make_operand(w.sl0, M, K, ld, kInvSlices, true);
+  emu::slice_rows(L.st, A, M, K, lda, kInvSlices, L.sl0, ld, nullptr);
+  const tc::Operand oa = tc::make_operand(L.sl0, M, K, ld, kInvSlices, true);
   tc::Operand ob;
   if (B == A && ldb == lda && N == M) {
-    ob = tc::make_operand(w.sl0, N, K, ld, kInvSlices, false);
+    ob = tc::make_operand(L.sl0, N, K, ld, kInvSlices, false);
   } else {
-    emu::slice_rows(st, B, N, K, ldb, kInvSlices, w.sl1, ld, nullptr);
-    ob = tc::make_operand(w.sl1, N, K, ld, kInvSlices, false);
+    emu::slice_rows(L.st, B, N, K, ldb, kInvSlices, L.sl1, ld, nullptr);
+    ob = tc::make_operand(L.sl1, N, K, ld, kInvSlices, false);
   }
-  emu::gemm(st, oa, ob, K, kInvSlices, tc::Epilogue{C, ldc, N, 0, alpha, beta, M, N, nullptr, w.err}, w.partial,
-            w.partial_cap);
+  emu::gemm(L.st, oa, ob, K, kInvSlices, tc::Epilogue{C, ldc, N, 0, alpha, beta, M, N, nullptr, err}, L.partial,
+            L.partial_cap);
 }
 
 // leaf: factor A[r0:r0+b, r0:r0+b] in place, write its inverse into Y and Y_leaf^T Y_leaf into P
-void leaf(cudaStream_t st, SlicedWork& w, int r0, int b) {
+void leaf(SlicedWork& w, int r0, int b) {
   const long m = w.m;
-  potf2_inv_kernel<<<1, 256, 0, st>>>(w.A + r0 * m + r0, m, b, w.leaf, w.info, r0, w.P + r0 * m + r0, m);
+  potf2_inv_kernel<<<1, 256, 0, w.main.st>>>(w.A + r0 * m + r0, m, b, w.leaf, w.info, r0, w.P + r0 * m + r0, m);
   OMM_LAUNCH_CHECK();
-  copy_block_kernel<<<16, 256, 0, st>>>(b, w.leaf, NB, w.Y + r0 * m + r0, m);
+  copy_block_kernel<<<16, 256, 0, w.main.st>>>(b, w.leaf, NB, w.Y + r0 * m + r0, m);
   OMM_LAUNCH_CHECK();
 }
 
 int half_of(int b) { return ((b / NB + 1) / 2) * NB; }  // a multiple of NB, about b / 2
 
-void chol_inv(cudaStream_t st, SlicedWork& w, int r0, int b) {
+// P21 = Y22^T Y21 and P11 += Y21^T Y21 of one node (its Y is final), on the side lane
+void p_update(SlicedWork& w, int r0, int b1, int b2) {
+  const long m = w.m;
+  const int r1 = r0 + b1;
+  Lane& L = w.side;
+  const double* Y21 = w.Y + (long)r1 * m + r0;
+  const double* Y22 = w.Y + (long)r1 * m + r1;
+  // Y21^T (b1 x b2) serves both products
+  emu::transpose(L.st, Y21, b2, b1, m, L.tr0, b2);
+  // P21 = Y22^T Y21: A operand Y22^T (b2 x b2), B operand Y21^T
+  emu::transpose(L.st, Y22, b2, b2, m, L.tr1, b2);
+  sliced_nt(L, w.err, b2, b1, b2, 1.0, L.tr1, b2, L.tr0, b2, 0.0, w.P + (long)r1 * m + r0, m);
+  // P11 = Y11^T Y11 (the updates of the left subtree, already queued on this lane) + Y21^T Y21
+  sliced_nt(L, w.err, b1, b1, b2, 1.0, L.tr0, b2, L.tr0, b2, 1.0, w.P + (long)r0 * m + r0, m);
+}
+
+// Y and L of the block [r0, r0 + b) on the main lane; once a node's Y is final its contribution
+// to P = Y^T Y is queued on the side lane, in post-order, so it runs beside the factorisation
+// of the blocks that follow
+void chol_inv(SlicedWork& w, int r0, int b) {
   if (b <= NB) {
-    leaf(st, w, r0, b);
+    leaf(w, r0, b);
     return;
   }
   const long m = w.m;
+  Lane& L = w.main;
   const int b1 = half_of(b), b2 = b - b1, r1 = r0 + b1;
-  chol_inv(st, w, r0, b1);
+  chol_inv(w, r0, b1);
   double* A21 = w.A + (long)r1 * m + r0;
   double* A22 = w.A + (long)r1 * m + r1;
   const double* Y11 = w.Y + (long)r0 * m + r0;
   const double* Y22 = w.Y + (long)r1 * m + r1;
   double* Y21 = w.Y + (long)r1 * m + r0;
   // L21 = A21 Y11^T (to scratch, then over A21)
-  sliced_nt(st, w, b2, b1, b1, 1.0, A21, m, Y11, m, 0.0, w.prod, b1);
+  sliced_nt(L, w.err, b2, b1, b1, 1.0, A21, m, Y11, m, 0.0, w.prod, b1);
   OMM_CUDA_TRY(cudaMemcpy2DAsync(A21, sizeof(double) * m, w.prod, sizeof(double) * b1, sizeof(double) * b1, b2,
-                                 cudaMemcpyDeviceToDevice, st));
+                                 cudaMemcpyDeviceToDevice, L.st));
   // A22 -= L21 L21^T
-  sliced_nt(st, w, b2, b2, b1, -1.0, A21, m, A21, m, 1.0, A22, m);
-  chol_inv(st, w, r1, b2);
+  sliced_nt(L, w.err, b2, b2, b1, -1.0, A21, m, A21, m, 1.0, A22, m);
+  chol_inv(w, r1, b2);
   // Z = Y22 L21 (b2 x b1): B operand L21^T (b1 x b2)
-  emu::transpose(st, A21, b2, b1, m, w.tr0, b2);
-  sliced_nt(st, w, b2, b1, b2, 1.0, Y22, m, w.tr0, b2, 0.0, w.prod, b1);
+  emu::transpose(L.st, A21, b2, b1, m, L.tr0, b2);
+  sliced_nt(L, w.err, b2, b1, b2, 1.0, Y22, m, L.tr0, b2, 0.0, w.prod, b1);
   // Y21 = -Z Y11: B operand Y11^T (b1 x b1)
-  emu::transpose(st, Y11, b1, b1, m, w.tr1, b1);
-  sliced_nt(st, w, b2, b1, b1, -1.0, w.prod, b1, w.tr1, b1, 0.0, Y21, m);
-}
-
-// P[r0:r0+b, r0:r0+b] (lower blocks) = Yb^T Yb for the lower-triangular Yb = Y[r0:r0+b, r0:r0+b]
-void lauum(cudaStream_t st, SlicedWork& w, int r0, int b) {
-  const long m = w.m;
-  if (b <= NB) return;  // the leaf kernel of chol_inv wrote Yb^T Yb
-  const int b1 = half_of(b), b2 = b - b1, r1 = r0 + b1;
-  // the recursions use the scratch buffers, so they come first
-  lauum(st, w, r1, b2);
-  lauum(st, w, r0, b1);
-  const double* Y21 = w.Y + (long)r1 * m + r0;
-  const double* Y22 = w.Y + (long)r1 * m + r1;
-  // Y21^T (b1 x b2) serves both products below
-  emu::transpose(st, Y21, b2, b1, m, w.tr0, b2);
-  // P21 = Y22^T Y21: A operand Y22^T (b2 x b2), B operand Y21^T
-  emu::transpose(st, Y22, b2, b2, m, w.tr1, b2);
-  sliced_nt(st, w, b2, b1, b2, 1.0, w.tr1, b2, w.tr0, b2, 0.0, w.P + (long)r1 * m + r0, m);
-  // P11 = lauum(Y11) + Y21^T Y21
-  sliced_nt(st, w, b1, b1, b2, 1.0, w.tr0, b2, w.tr0, b2, 1.0, w.P + (long)r0 * m + r0, m);
+  emu::transpose(L.st, Y11, b1, b1, m, L.tr1, b1);
+  sliced_nt(L, w.err, b2, b1, b1, -1.0, w.prod, b1, L.tr1, b1, 0.0, Y21, m);
+  // this node's Y is final: its P updates may start
+  cudaEvent_t ev = nullptr;
+  OMM_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  w.events.push_back(ev);
+  OMM_CUDA_TRY(cudaEventRecord(ev, L.st));
+  OMM_CUDA_TRY(cudaStreamWaitEvent(w.side.st, ev, 0));
+  p_update(w, r0, b1, b2);
 }
 
 }  // namespace
@@ -298,10 +316,11 @@ long partial_capacity(int m) {
 
 size_t spd_inverse_sliced_workspace_bytes(int m) {
   const long h = (m + 1) / 2 + NB;  // the largest off-diagonal block edge
-  const size_t f64 = (size_t)m * m + 3 * (size_t)h * h + (size_t)NB * NB +   // Y, tr0, tr1, prod, leaf
-                     (size_t)partial_capacity(m);
-  const size_t bf = 2 * (size_t)kInvSlices * (size_t)h * round8(h);        // sl0, sl1
-  return f64 * sizeof(double) + bf * sizeof(__nv_bfloat16) + 2 * 256;
+  // Y, prod, leaf; per lane: tr0, tr1, partial
+  const size_t f64 = (size_t)m * m + (size_t)h * h + (size_t)NB * NB +
+                     2 * (2 * (size_t)h * h + (size_t)partial_capacity(m));
+  const size_t bf = 2 * 2 * (size_t)kInvSlices * (size_t)h * round8(h);  // per lane: sl0, sl1
+  return f64 * sizeof(double) + bf * sizeof(__nv_bfloat16) + 4 * 256;
 }
 
 void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work, int* info_dev, int* err_dev) {
@@ -315,26 +334,53 @@ void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work
   double* f = static_cast<double*>(work);
   w.Y = f;
   f += (long)m * m;
-  w.tr0 = f;
-  f += h * h;
-  w.tr1 = f;
-  f += h * h;
   w.prod = f;
   f += h * h;
   w.leaf = f;
   f += NB * NB;
-  w.partial = f;
-  w.partial_cap = partial_capacity(m);
-  f += w.partial_cap;
+  for (Lane* L : {&w.main, &w.side}) {
+    L->tr0 = f;
+    f += h * h;
+    L->tr1 = f;
+    f += h * h;
+    L->partial = f;
+    L->partial_cap = partial_capacity(m);
+    f += L->partial_cap;
+  }
   uintptr_t p = (reinterpret_cast<uintptr_t>(f) + 255) & ~uintptr_t(255);
-  w.sl0 = reinterpret_cast<__nv_bfloat16*>(p);
-  w.sl1 = w.sl0 + (size_t)kInvSlices * h * round8(h);
-  OMM_CUDA_TRY(cudaMemsetAsync(info_dev, 0, sizeof(int), st));
-  OMM_CUDA_TRY(cudaMemsetAsync(w.Y, 0, sizeof(double) * m * (size_t)m, st));
-  OMM_CUDA_TRY(cudaMemsetAsync(P, 0, sizeof(double) * m * (size_t)m, st));
-  chol_inv(st, w, 0, m);
-  lauum(st, w, 0, m);
-  launch_symmetrize_lower(st, m, P);
+  const size_t sl = (size_t)kInvSlices * h * round8(h);
+  w.main.sl0 = reinterpret_cast<__nv_bfloat16*>(p);
+  w.main.sl1 = w.main.sl0 + sl;
+  w.side.sl0 = w.main.sl1 + sl;
+  w.side.sl1 = w.side.sl0 + sl;
+  w.main.st = st;
+  OMM_CUDA_TRY(cudaStreamCreateWithFlags(&w.side.st, cudaStreamNonBlocking));
+  // streams and events may be released with work pending: the driver frees them once it is done
+  auto cleanup = [&]() {
+    if (w.side.st) cudaStreamDestroy(w.side.st);
+    for (cudaEvent_t e : w.events) cudaEventDestroy(e);
+  };
+  try {
+    OMM_CUDA_TRY(cudaMemsetAsync(info_dev, 0, sizeof(int), st));
+    OMM_CUDA_TRY(cudaMemsetAsync(w.Y, 0, sizeof(double) * m * (size_t)m, st));
+    OMM_CUDA_TRY(cudaMemsetAsync(P, 0, sizeof(double) * m * (size_t)m, st));
+    cudaEvent_t ready = nullptr;  // the side lane starts after the memsets
+    OMM_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    w.events.push_back(ready);
+    OMM_CUDA_TRY(cudaEventRecord(ready, st));
+    OMM_CUDA_TRY(cudaStreamWaitEvent(w.side.st, ready, 0));
+    chol_inv(w, 0, m);
+    cudaEvent_t done = nullptr;  // join: the main lane waits for the last P update
+    OMM_CUDA_TRY(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    w.events.push_back(done);
+    OMM_CUDA_TRY(cudaEventRecord(done, w.side.st));
+    OMM_CUDA_TRY(cudaStreamWaitEvent(st, done, 0));
+    launch_symmetrize_lower(st, m, P);
+  } catch (...) {
+    cleanup();
+    throw;
+  }
+  cleanup();
 }
 
 }  // namespace omm

@@ -326,29 +326,6 @@ __device__ __forceinline__ void control_linesearch_body(Scalars* sc, const doubl
   sc->iter_round += 1;
   sc->have_dir = 1;
 }
-__device__ __forceinline__ void update_state_mixed_body(int n, long m, double* C, double* Y4, const double* Dir, double* G,
-                                          double* Gold, double* dY, const double* Gref, const Scalars* sc, int bx_, int nbx_) {
-  if (stopped(sc)) return;
-  const double x = sc->x;
-  const long count = (long)n * m;
-  double* HC = Y4;
-  double* SC = Y4 + count;
-  const double* HD = Y4 + 2 * count;
-  const double* SD = Y4 + 3 * count;
-  double* dHC = dY;
-  double* dSC = dY + count;
-  for (long i = bx_ * (long)blockDim.x + threadIdx.x; i < count; i += (long)nbx_ * blockDim.x) {
-    C[i] = fma(x, Dir[i], C[i]);
-    const double hd = x * HD[i], sd = x * SD[i];
-    HC[i] += hd;
-    SC[i] += sd;
-    const double dh = dHC[i] + hd;
-    dHC[i] = dh;
-    dSC[i] += sd;
-    Gold[i] = G[i];
-    G[i] = fma(8.0, dh, Gref[i]);
-  }
-}
 __device__ __forceinline__ void update_subspace_body(int n, double* SWHW, const double* __restrict__ Proj, const Scalars* sc, int bx_, int nbx_) {
   if (stopped(sc)) return;
   const double x = sc->x, x2 = x * x;

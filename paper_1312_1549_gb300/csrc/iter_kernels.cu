@@ -117,10 +117,6 @@ __global__ void update_state_kernel(int n, long m, double* C, double* Y4, const 
   }
 }
 
-__global__ void update_state_mixed_kernel(int n, long m, double* C, double* Y4, const double* Dir, double* G,
-                                          double* Gold, double* dY, const double* Gref, const Scalars* sc) {
-  update_state_mixed_body(n, m, C, Y4, Dir, G, Gold, dY, Gref, sc, blockIdx.x, gridDim.x);
-}
 
 
 // H_W += x (H' + H'^T) + x^2 H''; S_W likewise (Eq. 16), on 32x32 tiles
@@ -311,11 +307,6 @@ void launch_update_state_split(cudaStream_t st, long n, long m, double* C, doubl
                                double* Gold, double* dY, const double* Gref, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo,
                                long ldm, const Scalars* sc) {
   update_state_split_kernel<<<pair_grid(n, m), 256, 0, st>>>(n, m, C, Y4, Dir, G, Gold, dY, Gref, Yhi, Ylo, ldm, sc);
-  OMM_LAUNCH_CHECK();
-}
-void launch_update_state_mixed(cudaStream_t st, int n, long m, double* C, double* Y4, const double* Dir,
-                               double* G, double* Gold, double* dY, const double* Gref, const Scalars* sc) {
-  update_state_mixed_kernel<<<grid_for((long)n * m), TB, 0, st>>>(n, m, C, Y4, Dir, G, Gold, dY, Gref, sc);
   OMM_LAUNCH_CHECK();
 }
 void launch_update_subspace(cudaStream_t st, int n, double* SWHW, const double* Proj, const Scalars* sc) {

@@ -143,8 +143,6 @@ void launch_update_state(cudaStream_t st, int n, long m, double* C, double* Y4, 
                          double* G, double* Gold, const Scalars* sc);
 // mixed precision: as launch_update_state, plus dY = [dHC; dSC] += x [HD; SD] and
 // G = Gref + 8 (HC - HC_ref) as the base of the incremental gradient GEMM
-void launch_update_state_mixed(cudaStream_t st, int n, long m, double* C, double* Y4, const double* Dir,
-                               double* G, double* Gold, double* dY, const double* Gref, const Scalars* sc);
 void launch_update_subspace(cudaStream_t st, int n, double* SWHW, const double* Proj,
                             const Scalars* sc);
 void launch_scale_copy(cudaStream_t st, long count, const double* src, double a, double* dst,

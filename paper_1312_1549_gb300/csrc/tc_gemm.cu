@@ -349,22 +349,6 @@ gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA, const __grid_cons
   gemm_tile<FUSED>(&mA, &mB, K, rowsA, rowsB, pl, ep, blockIdx.x);
 }
 
-// One launch over the tiles of many independent GEMMs (a batch of OMM
-// instances): CTA b works on tile b - g.tile_begin of the group g that holds it.
-template <bool FUSED>
-__global__ void __launch_bounds__(NTHREADS, 1)
-gemm_grouped_kernel(const GroupDesc* __restrict__ groups, int ngroups, const __grid_constant__ PairList pl) {
-  int lo = 0, hi = ngroups - 1;
-  const int b = (int)blockIdx.x;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (groups[mid].tile_begin <= b) lo = mid; else hi = mid - 1;
-  }
-  const GroupDesc* g = groups + lo;
-  gemm_tile<FUSED>(reinterpret_cast<const CUtensorMap*>(&g->a), reinterpret_cast<const CUtensorMap*>(&g->b),
-                   g->K, g->rowsA, g->rowsB, pl, g->ep, b - g->tile_begin);
-}
-
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -770,18 +754,6 @@ GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& 
   return g;
 }
 
-void prepare_grouped() {
-  prepare_persistent();
-  static bool attr_set = false;
-  if (!attr_set) {
-    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_grouped_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      SMEM_BYTES));
-    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_grouped_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      SMEM_BYTES));
-    attr_set = true;
-  }
-}
-
 void prepare_persistent() {
   static bool attr_set = false;
   if (!attr_set) {
@@ -849,16 +821,6 @@ void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K,
   }
 }
 
-void gemm_grouped(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl) {
-  prepare_grouped();
-  if (ngroups <= 0 || total_tiles <= 0) return;
-  // every operand of a grouped launch is a split pair (2-slice stack)
-  if (is_split3(pl))
-    gemm_grouped_kernel<true><<<(unsigned)total_tiles, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, pl);
-  else
-    gemm_grouped_kernel<false><<<(unsigned)total_tiles, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, pl);
-  OMM_LAUNCH_CHECK();
-}
 
 // ------------------------------------------------------------------ block sparsity of B
 namespace {
@@ -1023,8 +985,6 @@ int choose_tile_width(cudaStream_t st, const std::vector<GemmSpec>& specs, const
   return best;
 }
 
-int tile_m() { return BM; }
-int tile_n() { return BN; }
 
 }  // namespace tc
 }  // namespace omm

@@ -68,8 +68,6 @@ void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const Pair
 inline void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, int npass, const Epilogue& ep) {
   gemm(st, A, B, K, npass == 3 ? pairs_split3() : pairs_single(), ep);
 }
-int tile_m();
-int tile_n();
 int tiles_of(const Epilogue& ep, int bn = 256);  // output tiles of one GEMM (128 x bn)
 
 // One GEMM of a grouped launch (device array element; tensor maps in global memory).
@@ -106,8 +104,7 @@ struct alignas(64) GroupDesc {
 GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin, int bn = 256,
                      const BlockLists* sparse = nullptr);
 // groups_dev: ngroups descriptors in device memory, sorted by tile_begin; all share the pair list
-void prepare_grouped();     // kernel attributes (call before a stream capture)
-void prepare_persistent();
+void prepare_persistent();  // kernel attributes (call before a stream capture)
 // persistent grouped launch: one CTA per SM, double-buffered TMEM accumulators; err receives a
 // nonzero code if a bounded wait expired
 void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl,
@@ -118,7 +115,6 @@ void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, 
 void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K, const PairList& pl,
                      const Epilogue& ep, double* partial = nullptr, long partial_capacity = 0,
                      const BlockLists* sparse = nullptr);
-void gemm_grouped(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl);
 
 // Tile-width autotuner: times one persistent launch over these GEMMs (the operands as given,
 // the outputs redirected to scratch) with 128 x 256 and with 128 x 128 output tiles, returns the

@@ -121,17 +121,17 @@ def _gap_guarded(builder, seed, **kw):
 
 
 # ------------------------------------------------------------------ named configs
-def config1(seed=0) -> Problem:
+def si64_sz(seed=0) -> Problem:
     """Si64 sp single-zeta: m = 256, n = 128."""
     return _gap_guarded(silicon, seed, k=(2, 2, 2), basis="SZ", name="si64_sz")
 
 
-def config2(seed=0) -> Problem:
+def si512_dzp(seed=0) -> Problem:
     """Si512 DZP-like (13 orbitals per atom): m = 6656, n = 1024."""
     return _gap_guarded(silicon, seed, k=(4, 4, 4), basis="DZP", name="si512_dzp")
 
 
-def config3(seed=0) -> Problem:
+def water256_dzp(seed=0) -> Problem:
     """Water256 DZP-like (23 orbitals per molecule): m = 5888, n = 1024."""
     return _gap_guarded(water, seed, nmol=256, name="water256_dzp")
 
@@ -146,7 +146,7 @@ SI_BASIS_FRACTION = {"DZ": 2 / 8, "TZ": 2 / 12, "DZP": 2 / 13, "DZP+p": 2 / 16}
 WATER_BASIS_FRACTION = {"DZ+d": 4 / 17, "DZP": 4 / 23, "TZP": 4 / 29}
 
 
-def config4_recipe(i: int):
+def batch_recipe(i: int):
     """(builder, kwargs) of instance i of the uneven batch.
 
     m ~ U[512, 4096] and a target occupied fraction ~ U[0.12, 0.25]; the basis is the one
@@ -167,13 +167,13 @@ def config4_recipe(i: int):
     return water, dict(nmol=nmol, basis=basis, name=f"batch{i:02d}_water{nmol}_{basis}")
 
 
-def config4_instance(i: int) -> Problem:
-    """Instance i of the uneven batch (see config4_recipe), gap-guarded."""
-    builder, kw = config4_recipe(i)
+def batch_instance(i: int) -> Problem:
+    """Instance i of the uneven batch (see batch_recipe), gap-guarded."""
+    builder, kw = batch_recipe(i)
     return _gap_guarded(builder, i, **kw)
 
 
-def config5_base(seed=0) -> Problem:
+def si4096_sz(seed=0) -> Problem:
     """Si4096 single-zeta: m = 16384, n = 8192 (the warm-start sequence's H_0)."""
     return _gap_guarded(silicon, seed, k=(8, 8, 8), basis="SZ", name="si4096_sz")
 
@@ -184,4 +184,4 @@ def warm_start_delta(p: Problem, k: int, sigma: float = JITTER_SIGMA) -> np.ndar
     return rng.normal(0.0, sigma, size=p.m)
 
 
-CONFIGS = {1: config1, 2: config2, 3: config3}
+NAMED = {"si64_sz": si64_sz, "si512_dzp": si512_dzp, "water256_dzp": water256_dzp}

@@ -42,7 +42,7 @@ def main(argv):
         guarded(configs.silicon, 0, k=(8, 8, 8), basis="SZ")   # m = 16384: a long solve
     if "--batch" in argv:
         for i in range(64):
-            builder, kw = configs.config4_recipe(i)
+            builder, kw = configs.batch_recipe(i)
             kw.pop("name")
             guarded(builder, i, **kw)
 

@@ -12,9 +12,9 @@ def setup():
     from paper_1312_1549_gb300 import build
     build.build()
     from paper_1312_1549_gb300.autograd import omm_energy
-    from synth import config1
+    from synth import si64_sz
     from oracle import exact
-    p = config1()
+    p = si64_sz()
     return omm_energy, p, exact.exact_minimum(p.H, p.S, p.n)
 
 

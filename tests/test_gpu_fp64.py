@@ -66,9 +66,9 @@ def test_spd_inverse_rejects_indefinite(S):
 
 
 def test_preconditioner_of_si64(S):
-    from synth import config1
+    from synth import si64_sz
     from oracle import omm
-    p = config1()
+    p = si64_sz()
     P_ref = omm.preconditioner(p.S, p.T, p.tau)
     P = S.spd_inverse(dev(p.S + p.T / p.tau)).cpu().numpy()
     assert np.abs(P - P_ref).max() < 1e-11 * np.abs(P_ref).max()
@@ -108,9 +108,9 @@ def test_quartic_coefficients_match_oracle(S):
 # ---------------------------------------------------------------- whole solve, Si64
 @pytest.fixture(scope="module")
 def si64():
-    from synth import config1
+    from synth import si64_sz
     from oracle import exact, omm
-    p = config1()
+    p = si64_sz()
     ref = omm.solve(p.H, p.S, p.T, p.eta, p.tau, p.C0, tol_grad=1e-9)
     ex = exact.exact_minimum(p.H, p.S, p.n)
     return p, ref, ex

@@ -15,14 +15,14 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.fixture(scope="module", params=[2, 3], ids=["si512_dzp", "water256_dzp"])
+@pytest.fixture(scope="module", params=["si512_dzp", "water256_dzp"])
 def solved(request):
     from paper_1312_1549_gb300 import build
     build.build()
     from paper_1312_1549_gb300.solver import OMMSolver
     from synth import configs
     from oracle import exact
-    p = configs.CONFIGS[request.param]()
+    p = configs.NAMED[request.param]()
     with OMMSolver(dev(p.H), dev(p.S), dev(p.T), p.n, p.eta, p.tau, precision="mixed") as s:
         C, E, D, info = s.solve(dev(p.C0), want_D=True)
         dH, dS = s.backward()
@@ -73,7 +73,7 @@ def test_sliced_preconditioner_inverse_at_si512():
     build.build()
     from paper_1312_1549_gb300 import solver as S
     from synth import configs
-    p = configs.config2()
+    p = configs.si512_dzp()
     A = dev(p.S + p.T / p.tau)
     P_native = S.spd_inverse(A)
     P_sliced = S.spd_inverse(A, sliced=True)
@@ -98,7 +98,7 @@ def test_water256_autograd_central_differences():
     build.build()
     from paper_1312_1549_gb300.autograd import omm_energy
     from synth import configs
-    p = configs.config3()
+    p = configs.water256_dzp()
     H = dev(p.H).requires_grad_(True)
     S = dev(p.S).requires_grad_(True)
     T = dev(p.T)

@@ -60,9 +60,9 @@ def test_gemm_tc_split_error_bound(S, M, N, K, tile_n):
 
 @pytest.fixture(scope="module")
 def si64():
-    from synth import config1
+    from synth import si64_sz
     from oracle import exact, omm
-    p = config1()
+    p = si64_sz()
     ref = omm.solve(p.H, p.S, p.T, p.eta, p.tau, p.C0, tol_grad=1e-9)
     ex = exact.exact_minimum(p.H, p.S, p.n)
     return p, ref, ex

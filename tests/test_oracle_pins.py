@@ -228,8 +228,8 @@ def test_backward_central_differences():
 
 # ---------------------------------------------------------------- the Si64 workload
 def test_si64_workload_reaches_lapack_minimum():
-    from synth import config1
-    p = config1()
+    from synth import si64_sz
+    p = si64_sz()
     r = omm.solve(p.H, p.S, p.T, p.eta, p.tau, p.C0, tol_grad=1e-9)
     assert r["status"] == omm.STATUS_OK and r["gmax"] < 1e-9
     ex = exact.exact_minimum(p.H, p.S, p.n)
