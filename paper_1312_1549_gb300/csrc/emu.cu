@@ -280,20 +280,43 @@ void emu_recompute_state(EmuState* es, cudaStream_t st, Scalars* sc, const doubl
 
 namespace omm {
 
-// D = 2 C^T (2I - S_W) C = 4 C^T C - 2 (C^T S_W) C (n x m layout of C), float64-class:
-// X = C^T S_W from sliced C^T and S_W, then D = 4 C^T (C^T)^T - 2 X (C^T)^T.
-// The B operand C^T is the same slice stack as the A operand, mapped with B-sized TMA boxes.
+namespace {
+// out = a x + b y (float64, count elements)
+__global__ void combine_kernel(long count, double a, const double* __restrict__ x, double b,
+                               const double* __restrict__ y, double* out) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x)
+    out[i] = fma(a, x[i], b * y[i]);
+}
+}  // namespace
+
+// D = 2 C^T (2I - S_W) C (n x m layout of C), float64-class: X = C^T S_W from the sliced C^T and
+// S_W, W = 4 C^T - 2 X in float64, then one sliced product D = W (C^T)^T. The B operand C^T is
+// the same slice stack as the A operand, mapped with B-sized TMA boxes.
 void emu_density(EmuState* es, cudaStream_t st, const double* C, const double* SWHW, double* D) {
   const int m = es->m, n = es->n, s = kDensitySlices;
-  double* CT = es->T64;                  // m x n
-  double* XT = es->T64 + (long)m * n;    // m x n
+  const long mn = (long)m * n;
+  double* CT = es->T64;       // m x n
+  double* XT = es->T64 + mn;  // m x n
   emu::transpose(st, C, n, m, m, CT, n);
   emu::slice_rows(st, CT, m, n, n, s, es->CTs, es->ldn, nullptr);
   emu::slice_rows(st, SWHW, n, n, 2L * n, s, es->SWs, es->ldn, nullptr);   // S_W is symmetric
   emu::gemm(st, es->opCT, es->opSW, n, s, tc::Epilogue{XT, n, n, 0, 1.0, 0.0, m, n, nullptr, es->err});
+  combine_kernel<<<(unsigned)std::min<long>((mn + 255) / 256, 4096), 256, 0, st>>>(mn, 4.0, CT, -2.0, XT, XT);
+  OMM_LAUNCH_CHECK();
   emu::slice_rows(st, XT, m, n, n, s, es->XTs, es->ldn, nullptr);
-  emu::gemm(st, es->opCT, es->opCTb, n, s, tc::Epilogue{D, m, m, 0, 4.0, 0.0, m, m, nullptr, es->err});
-  emu::gemm(st, es->opXT, es->opCTb, n, s, tc::Epilogue{D, m, m, 0, -2.0, 1.0, m, m, nullptr, es->err});
+  emu::gemm(st, es->opXT, es->opCTb, n, s, tc::Epilogue{D, m, m, 0, 1.0, 0.0, m, m, nullptr, es->err});
+}
+
+// out = -(2 C^T H~_W C + eta D) given out = D (dE/dS at the minimum), float64-class:
+// V = C^T H_W from the sliced C^T and H_W (C^T, sliced, as left by emu_density), then one
+// sliced product out = -2 V (C^T)^T - eta out.
+void emu_minus_edm(EmuState* es, cudaStream_t st, const double* SWHW, double eta, double* out) {
+  const int m = es->m, n = es->n, s = kDensitySlices;
+  double* VT = es->T64 + (long)m * n;  // m x n
+  emu::slice_rows(st, SWHW + n, n, n, 2L * n, s, es->SWs, es->ldn, nullptr);  // H_W is symmetric
+  emu::gemm(st, es->opCT, es->opSW, n, s, tc::Epilogue{VT, n, n, 0, 1.0, 0.0, m, n, nullptr, es->err});
+  emu::slice_rows(st, VT, m, n, n, s, es->XTs, es->ldn, nullptr);
+  emu::gemm(st, es->opXT, es->opCTb, n, s, tc::Epilogue{out, m, m, 0, -2.0, -eta, m, m, nullptr, es->err});
 }
 
 }  // namespace omm

@@ -27,6 +27,8 @@ void emu_destroy(EmuState* es);
 int emu_error(EmuState* es, cudaStream_t st);
 // density matrix D = 2 C^T (2I - S_W) C (m x m) with float64-class products
 void emu_density(EmuState* es, cudaStream_t st, const double* C, const double* SWHW, double* D);
+// out = -(2 C^T H~_W C + eta D) from out = D; call right after emu_density (it reuses the sliced C^T)
+void emu_minus_edm(EmuState* es, cudaStream_t st, const double* SWHW, double eta, double* out);
 void emu_recompute_state(EmuState* es, cudaStream_t st, Scalars* sc, const double* C, double* Y4,
                          double* SWHW, double* G, double* part, double* part2);
 

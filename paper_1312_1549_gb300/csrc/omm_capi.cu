@@ -615,8 +615,13 @@ omm_status omm_backward(omm_ctx* c, double* dEdH, double* dEdS) {
     }
     if (dEdS) {
       if (!is_device_ptr(dEdS)) { ensure_mm(c); tS = c->mm; }
-      density_into(c, tS);
-      minus_edm_into(c, tS);
+      if (c->emu && !c->opts.native_certificate) {  // float64-class, like the certificate
+        emu_density(c->emu, c->st, c->C, c->SWHW, tS);
+        emu_minus_edm(c->emu, c->st, c->SWHW, c->eta, tS);
+      } else {
+        density_into(c, tS);
+        minus_edm_into(c, tS);
+      }
       if (tS != dEdS) OMM_CUDA_TRY(cudaMemcpyAsync(dEdS, tS, bytes, cudaMemcpyDefault, c->st));
     }
     OMM_CUDA_TRY(cudaStreamSynchronize(c->st));
