@@ -46,6 +46,7 @@ WORKLOADS = {
 }
 # Line searches the float64 solve takes on each workload from its seeded C0
 # (measured with the float64 GPU path); used to extrapolate bounded oracle samples.
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 float64 FMA rate, nominal
 FP64_LINE_SEARCHES = {"si64_sz": 43, "si512_dzp": 63, "water256_dzp": 160}
 
 
@@ -492,6 +493,12 @@ def main():
                                             if i64["ms_main_gemm"] > 0 else None),
                            "E": E64, "speedup_mixed_over_fp64": None}
         out["fp64_gpu"]["speedup_mixed_over_fp64"] = out["fp64_gpu"]["time_to_solution_s"] / (ms * 1e-3)
+        dg = out["fp64_gpu"]["dgemm_tflops"]
+        if dg:  # the float64 path is bound by the float64 FMA units (no tensor-core float64 here)
+            out["fp64_gpu"]["roofline"] = {"bound": "alu", "achieved": dg, "peak": FP64_NOMINAL_TFLOPS,
+                                           "unit": "TFLOP/s", "frac": dg / FP64_NOMINAL_TFLOPS,
+                                           "kernel": "dgemm_kernel (DFMA)",
+                                           "peak_source": "nominal GB300 float64 rate (not measured)"}
     if not args.no_e2e:
         Hh, Sh, Th, C0h = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (p.H, p.S, p.T, p.C0))
         Ch = torch.empty_like(C0h).pin_memory()

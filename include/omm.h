@@ -68,8 +68,11 @@ typedef enum {
 typedef enum {
   OMM_PREC_FP64 = 0,   /* every contraction in float64 */
   OMM_PREC_MIXED = 1   /* bulk contractions on the BF16 tensor cores as 3-term split products
-                          with FP32 accumulation, state in float64, float64 refinement and a
-                          float64 certificate of the final point */
+                          with FP32 accumulation, state and every scalar in float64; the
+                          preconditioner inverse, the refreshes of the state and the
+                          certificate of the final point use float64-class products (fixed-point
+                          slices on the tensor cores, the Ozaki scheme; native float64 for the
+                          certificate with native_certificate = 1) */
 } omm_precision;
 
 /* Options. A zero-filled struct (or NULL) selects every default. */
@@ -80,8 +83,8 @@ typedef struct {
   int check_every;      /* line searches between host convergence polls; 0 -> 8 */
   double tol_grad;      /* stop when max|G| < tol_grad, G the exact gradient of Eq. 12; 0 -> 1e-9 */
   double e_tol;         /* also stop when |2(E_new-E)/(E_new+E)| <= e_tol (Eq. 18); 0 -> off */
-  double refine_ratio;  /* mixed: refine in float64 once max|G| fell by this factor since
-                           the last float64 refinement; 0 -> 1e-4 */
+  double refine_ratio;  /* mixed: refresh the state with float64-class products once max|G|
+                           fell by this factor since the last refresh (or stalls); 0 -> 1e-3 */
   int profile;          /* 1 -> time every launch of the line-search GEMM with CUDA events on
                            the context's stream (omm_info.ms_main_gemm and friends) */
   int native_certificate; /* mixed: 0 (default) -> certify the final point, and form the
@@ -96,13 +99,13 @@ typedef struct {
   int status;           /* omm_status of the solve */
   int iterations;       /* line searches in total */
   int iterations_fp64;  /* line searches run with float64 contractions */
-  int refinements;      /* float64 recomputations of the state (mixed precision) */
+  int refinements;      /* recomputations of the state before the certificate (mixed precision) */
   double E;             /* band energy 2 sum eps_i = E~ + 2 n eta (certified in float64) */
   double Etilde;        /* the shifted functional E~ at the returned C */
   double gmax;          /* max|G| of the certified gradient at the returned C */
   double ms_setup;      /* omm_create GPU time (shift, Cholesky, inverse, splits) */
   double ms_iterate;    /* CG line searches */
-  double ms_refine;     /* float64 refinements and the final certificate */
+  double ms_refine;     /* refreshes of the state and the final certificate */
   double ms_outputs;    /* density matrix */
   double gemm_flop;     /* logical contraction flops of the solve (FP64-equivalent) */
   double gemm_flop_tc;  /* flops issued to the BF16 tensor cores (3 per logical in split form) */
@@ -111,7 +114,8 @@ typedef struct {
   double main_gemm_launches; /* with opts.profile: number of those launches */
   double main_gemm_flop;     /* with opts.profile: flops they issued (tensor-core flops when mixed) */
   double ms_certify;         /* native float64 state recomputes (part of ms_refine) */
-  double ms_precond;         /* the float64 Cholesky inverse P = (S + T/tau)^-1 (part of ms_setup) */
+  double ms_precond;         /* the Cholesky inverse P = (S + T/tau)^-1 (part of ms_setup): float64,
+                                or float64-class sliced products on the mixed path */
   int tile_width[4];         /* mixed: output tile width (256 or 128 columns) the autotuner chose for
                                 the P G, [H D; S D], projection and gradient GEMMs (0: not run) */
   double ms_autotune;        /* time the autotuner spent timing candidates (0 when cached) */

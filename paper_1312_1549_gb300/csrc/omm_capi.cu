@@ -282,7 +282,7 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
   if (o.check_every <= 0) o.check_every = 8;
   if (!(o.tol_grad > 0.0)) o.tol_grad = 1e-9;
   if (!(o.e_tol >= 0.0)) o.e_tol = 0.0;
-  if (!(o.refine_ratio > 0.0)) o.refine_ratio = 1e-4;
+  if (!(o.refine_ratio > 0.0)) o.refine_ratio = 1e-3;
   if (o.precision != OMM_PREC_FP64 && o.precision != OMM_PREC_MIXED)
     return fail(OMM_ERR_ARG, "omm_create: unknown precision");
   const bool precond = (o.no_precondition == 0);
