@@ -92,6 +92,14 @@ typedef struct {
                            float64-class tensor-core products (fixed-point slices, about
                            2^-50 resp. 2^-40 of each row-scaled operand); 1 -> with native
                            float64 GEMMs */
+  int cholesky;         /* 1 -> reduce to standard form instead of preconditioning (Sec. 2.4,
+                           last paragraph): S = L L^T, H_r = L^-1 H L^-T, and the OMM runs on
+                           H_r with S = I and no preconditioner (T and tau are ignored), from
+                           C_r = L^T C0; the result is transformed back, C = L^-T C_r. The
+                           iterates are those of the original problem preconditioned by S^-1;
+                           tol_grad and omm_info.gmax then refer to the gradient of the reduced
+                           problem (Eq. 12 with S = I). Products as for the preconditioner:
+                           float64, or float64-class slices on the mixed path. 0 (default) -> off */
 } omm_opts;
 
 /* Per-solve report. */
@@ -115,7 +123,8 @@ typedef struct {
   double main_gemm_flop;     /* with opts.profile: flops they issued (tensor-core flops when mixed) */
   double ms_certify;         /* native float64 state recomputes (part of ms_refine) */
   double ms_precond;         /* the Cholesky inverse P = (S + T/tau)^-1 (part of ms_setup): float64,
-                                or float64-class sliced products on the mixed path */
+                                or float64-class sliced products on the mixed path; with
+                                opts.cholesky the factor L, L^-1 and H_r = L^-1 H L^-T instead */
   int tile_width[4];         /* mixed: output tile width (256 or 128 columns) the autotuner chose for
                                 the P G, [H D; S D], projection and gradient GEMMs (0: not run) */
   double ms_autotune;        /* time the autotuner spent timing candidates (0 when cached) */
@@ -127,6 +136,8 @@ typedef struct {
   double ms_batch;           /* omm_solve_batched only: the whole batched solve. There ms_iterate,
                                 ms_main_gemm, main_gemm_launches and main_gemm_flop are batch
                                 totals too (the same in every instance's report) */
+  double ms_transform;       /* opts.cholesky: the coefficient transforms C_r = L^T C0 and
+                                C = L^-T C_r of this solve */
 } omm_info;
 
 /* Create a solver context for one (H, S, T) and do the per-geometry setup:
@@ -140,6 +151,8 @@ typedef struct {
  *   tau    kinetic-energy scale, > 0; +infinity gives P = S^-1.
  *   stream cudaStream_t (as void*) for every GPU operation of this context.
  *   out    receives the context; *out is NULL on failure.
+ * With opts->cholesky the setup is the factorisation S = L L^T and the reduction
+ * H_r = L^-1 H L^-T instead of P (S must then be positive definite: OMM_ERR_NOT_SPD).
  * Errors: OMM_ERR_ARG, OMM_ERR_NOT_SPD, OMM_ERR_OOM, OMM_ERR_CUDA. */
 omm_status omm_create(int m, int n, const double* H, const double* S, const double* T,
                       double eta, double tau, const omm_opts* opts, void* stream,
@@ -163,7 +176,8 @@ omm_status omm_solve(omm_ctx* ctx, const double* C0, double* C, double* E, doubl
  * with H~ = H - eta S). Errors: OMM_ERR_STATE (no converged solve), OMM_ERR_CUDA. */
 omm_status omm_backward(omm_ctx* ctx, double* dEdH, double* dEdS);
 
-/* Replace H (SCF warm start: S, T and P are kept; Sec. 2.5.2). */
+/* Replace H (SCF warm start: S, T and P are kept; Sec. 2.5.2). With opts.cholesky the new
+ * H is reduced with the kept factor: H_r = L^-1 H L^-T. */
 omm_status omm_update_H(omm_ctx* ctx, const double* H);
 
 /* Release every resource of the context (NULL is ignored). */

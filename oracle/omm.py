@@ -15,6 +15,8 @@ Steps and their sources (Corsetti, arXiv:1312.1549):
   update           C, H_W, S_W (and HC, SC)                 Sec. 2.3, Eq. 16 and its footnote
   stopping         |G|_inf < tol, and optionally Eq. 18     Sec. 2.5.2
   outputs          E = E~ + 2 n eta, D, EDM                 Sec. 2.1-2.2
+  Cholesky flavour S = L L^T, H_r = L^-1 H L^-T, S -> I,    Sec. 2.4 (last paragraph)
+                   C_r = L^T C, no preconditioner, and back
 
 Readings where the paper is silent or ambiguous (each one also listed in the
 design notes of the repository):
@@ -32,6 +34,8 @@ design notes of the repository):
     no lower bound (observed without preconditioning on the Si64 workload).
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -213,4 +217,36 @@ def solve(H, S, T, eta, tau, C0_nm, tol_grad=1e-9, max_iter=2000, precondition=T
         D = density_matrix(C, SW)
         out["D"] = D
         out["EDM"] = energy_density_matrix(C, HW, D, eta)
+    return out
+
+
+def solve_cholesky(H, S, eta, C0_nm, tol_grad=1e-9, max_iter=2000, e_tol=0.0, C_is_mn=False,
+                   callback=None, want_matrices=True):
+    """The Cholesky flavour of the OMM (Sec. 2.4, last paragraph).
+
+    The generalised problem is reduced to standard form with the Cholesky factor
+    S = L L^T: H_r = L^-1 H L^-T and C_r = L^T C, so that S_W = C_r^T C_r. The OMM then
+    minimises with S = I and without a preconditioner, and the result goes back to the
+    original basis, C = L^-T C_r (the density matrix with it: D = L^-T D_r L^-1). H_W,
+    S_W, the energies and the line-search steps are the same in both bases; the
+    gradient and its stopping test (tol_grad) are those of the reduced problem.
+    """
+    m = H.shape[0]
+    L = np.linalg.cholesky(S)
+    Linv = np.linalg.inv(L)
+    Hr = Linv @ H @ Linv.T
+    Hr = 0.5 * (Hr + Hr.T)
+    C = np.array(C0_nm if C_is_mn else np.asarray(C0_nm).T, dtype=float, copy=True)
+    Cr0 = L.T @ C
+    r = solve(Hr, np.eye(m), None, eta, math.inf, Cr0, tol_grad=tol_grad, max_iter=max_iter,
+              precondition=False, e_tol=e_tol, C_is_mn=True, callback=callback, want_matrices=False)
+    Cback = Linv.T @ r["C"]
+    out = dict(r)
+    out["C"] = Cback
+    out["C_reduced"] = r["C"]
+    if want_matrices:
+        D = density_matrix(Cback, r["SW"])
+        HW_shifted = Cback.T @ shift(H, S, eta) @ Cback
+        out["D"] = D
+        out["EDM"] = energy_density_matrix(Cback, HW_shifted, D, eta)
     return out

@@ -23,7 +23,7 @@ class OmmOpts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("max_iter", ct.c_int), ("no_precondition", ct.c_int),
                 ("check_every", ct.c_int), ("tol_grad", ct.c_double), ("e_tol", ct.c_double),
                 ("refine_ratio", ct.c_double), ("profile", ct.c_int),
-                ("native_certificate", ct.c_int)]
+                ("native_certificate", ct.c_int), ("cholesky", ct.c_int)]
 
 
 class OmmInfo(ct.Structure):
@@ -37,7 +37,8 @@ class OmmInfo(ct.Structure):
                 ("ms_precond", ct.c_double),
                 ("tile_width", ct.c_int * 4), ("ms_autotune", ct.c_double),
                 ("ms_sliced_gemm", ct.c_double), ("sliced_gemm_flop", ct.c_double),
-                ("sliced_gemm_launches", ct.c_double), ("ms_batch", ct.c_double)]
+                ("sliced_gemm_launches", ct.c_double), ("ms_batch", ct.c_double),
+                ("ms_transform", ct.c_double)]
 
     def as_dict(self):
         out = {}

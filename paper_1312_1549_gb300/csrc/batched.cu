@@ -289,7 +289,7 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
   omm_opts o{};
   if (opts) o = *opts;
   b->opts = o;
-  b->precond = o.no_precondition == 0;
+  b->precond = o.no_precondition == 0 && o.cholesky == 0;
   b->ctx.assign(count, nullptr);
   // per-instance setup (float64 Cholesky inverse etc.) from several host threads, each on its
   // own stream, so that the small factorisations of different instances overlap on the GPU
@@ -487,6 +487,11 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
       omm_ctx* c = b->ctx[i];
       c->solved = false;
       copy_in(c->C, C0[i], (size_t)c->n * c->m, b->st);
+      if (c->red) {  // C_r = L^T C0 (Sec. 2.4)
+        reduce_coefficients(c->red, b->st, c->n, c->C, c->Dir);
+        OMM_CUDA_TRY(cudaMemcpyAsync(c->C, c->Dir, (size_t)c->n * c->m * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     b->st));
+      }
       reset_loop_flags(c, true);
       write_scalars(c);
       mixed_recompute_state(c->mixed, b->st, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
@@ -621,6 +626,15 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
     for (int i = 0; i < cnt; ++i) {
       omm_ctx* c = b->ctx[i];
       const Scalars& h = *c->sc_host;
+      if (c->red && (result[i] == OMM_OK || result[i] == OMM_ERR_NO_CONVERGENCE)) {  // C = L^-T C_r
+        restore_coefficients(c->red, b->st, c->n, c->C, c->Dir);
+        OMM_CUDA_TRY(cudaMemcpyAsync(c->C, c->Dir, (size_t)c->n * c->m * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     b->st));
+        if (reduction_error(c->red, b->st) != 0) {
+          result[i] = OMM_ERR_TIMEOUT;
+          c->solved = false;
+        }
+      }
       if ((result[i] == OMM_OK || result[i] == OMM_ERR_NO_CONVERGENCE) && C && C[i])
         OMM_CUDA_TRY(cudaMemcpyAsync(C[i], c->C, (size_t)c->n * c->m * sizeof(double), cudaMemcpyDefault, b->st));
       if (E) E[i] = h.E + 2.0 * c->n * c->eta;

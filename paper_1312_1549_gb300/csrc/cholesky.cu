@@ -159,11 +159,11 @@ size_t spd_inverse_workspace(int m) {
   return (size_t)(nblk * NB * NB) + (size_t)(half * half) + (size_t)m * NB;
 }
 
-void spd_inverse(cudaStream_t st, int m, double* A, double* P, double* work, int* info_dev) {
+namespace {
+// stage 1: A = L L^T in place (lower triangle; the upper one is zeroed)
+void factor_blocked(cudaStream_t st, int m, double* A, const Work& w, int* info_dev) {
   const int nblk = (m + NB - 1) / NB;
-  Work w{work, work + (long)nblk * NB * NB};
   OMM_CUDA_TRY(cudaMemsetAsync(info_dev, 0, sizeof(int), st));
-  // 1. Cholesky
   for (int kb = 0; kb < nblk; ++kb) {
     const int k = kb * NB;
     const int b = (m - k < NB) ? (m - k) : NB;
@@ -184,11 +184,27 @@ void spd_inverse(cudaStream_t st, int m, double* A, double* P, double* work, int
   }
   zero_upper_kernel<<<1024, 256, 0, st>>>(m, A);
   OMM_LAUNCH_CHECK();
+}
+}  // namespace
+
+void spd_inverse(cudaStream_t st, int m, double* A, double* P, double* work, int* info_dev) {
+  const int nblk = (m + NB - 1) / NB;
+  Work w{work, work + (long)nblk * NB * NB};
+  // 1. Cholesky
+  factor_blocked(st, m, A, w, info_dev);
   // 2. Y = L^-1 in place
   trtri_rec(st, m, A, w, 0, m);
   // 3. P = Y^T Y (lower), mirrored
   dgemm(st, 1, 0, m, m, m, 1.0, A, m, 0, A, m, 0, 0.0, P, m, 0, 1, kTriLower | kTriKStart);
   launch_symmetrize_lower(st, m, P);
+}
+
+void spd_factor_inverse(cudaStream_t st, int m, double* A, double* Y, double* work, int* info_dev) {
+  const int nblk = (m + NB - 1) / NB;
+  Work w{work, work + (long)nblk * NB * NB};
+  factor_blocked(st, m, A, w, info_dev);
+  OMM_CUDA_TRY(cudaMemcpyAsync(Y, A, sizeof(double) * m * (size_t)m, cudaMemcpyDeviceToDevice, st));
+  trtri_rec(st, m, Y, w, 0, m);
 }
 
 // ------------------------------------------------------------------ float64-class (sliced) variant
@@ -243,7 +259,8 @@ void sliced_nt(Lane& L, int* err, int M, int N, int K, double alpha, const doubl
 // leaf: factor A[r0:r0+b, r0:r0+b] in place, write its inverse into Y and Y_leaf^T Y_leaf into P
 void leaf(SlicedWork& w, int r0, int b) {
   const long m = w.m;
-  potf2_inv_kernel<<<1, 256, 0, w.main.st>>>(w.A + r0 * m + r0, m, b, w.leaf, w.info, r0, w.P + r0 * m + r0, m);
+  potf2_inv_kernel<<<1, 256, 0, w.main.st>>>(w.A + r0 * m + r0, m, b, w.leaf, w.info, r0,
+                                             w.P ? w.P + r0 * m + r0 : nullptr, m);
   OMM_LAUNCH_CHECK();
   copy_block_kernel<<<16, 256, 0, w.main.st>>>(b, w.leaf, NB, w.Y + r0 * m + r0, m);
   OMM_LAUNCH_CHECK();
@@ -297,6 +314,7 @@ void chol_inv(SlicedWork& w, int r0, int b) {
   // Y21 = -Z Y11: B operand Y11^T (b1 x b1)
   emu::transpose(L.st, Y11, b1, b1, m, L.tr1, b1);
   sliced_nt(L, w.err, b2, b1, b1, -1.0, w.prod, b1, L.tr1, b1, 0.0, Y21, m);
+  if (w.P == nullptr) return;  // the factor and its inverse only
   // this node's Y is final: its P updates may start
   cudaEvent_t ev = nullptr;
   OMM_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -323,7 +341,10 @@ size_t spd_inverse_sliced_workspace_bytes(int m) {
   return f64 * sizeof(double) + bf * sizeof(__nv_bfloat16) + 4 * 256;
 }
 
-void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work, int* info_dev, int* err_dev) {
+namespace {
+// P = A^-1 (P != nullptr) and/or L, Y = L^-1 (Y_out != nullptr: A keeps L, zero above the diagonal)
+void sliced_impl(cudaStream_t st, int m, double* A, double* P, double* Y_out, void* work, int* info_dev,
+                 int* err_dev) {
   const long h = (m + 1) / 2 + NB;
   SlicedWork w;
   w.m = m;
@@ -332,7 +353,7 @@ void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work
   w.info = info_dev;
   w.err = err_dev;
   double* f = static_cast<double*>(work);
-  w.Y = f;
+  w.Y = Y_out ? Y_out : f;
   f += (long)m * m;
   w.prod = f;
   f += h * h;
@@ -354,7 +375,7 @@ void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work
   w.side.sl0 = w.main.sl1 + sl;
   w.side.sl1 = w.side.sl0 + sl;
   w.main.st = st;
-  OMM_CUDA_TRY(cudaStreamCreateWithFlags(&w.side.st, cudaStreamNonBlocking));
+  if (P) OMM_CUDA_TRY(cudaStreamCreateWithFlags(&w.side.st, cudaStreamNonBlocking));
   // streams and events may be released with work pending: the driver frees them once it is done
   auto cleanup = [&]() {
     if (w.side.st) cudaStreamDestroy(w.side.st);
@@ -363,24 +384,43 @@ void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work
   try {
     OMM_CUDA_TRY(cudaMemsetAsync(info_dev, 0, sizeof(int), st));
     OMM_CUDA_TRY(cudaMemsetAsync(w.Y, 0, sizeof(double) * m * (size_t)m, st));
-    OMM_CUDA_TRY(cudaMemsetAsync(P, 0, sizeof(double) * m * (size_t)m, st));
-    cudaEvent_t ready = nullptr;  // the side lane starts after the memsets
-    OMM_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-    w.events.push_back(ready);
-    OMM_CUDA_TRY(cudaEventRecord(ready, st));
-    OMM_CUDA_TRY(cudaStreamWaitEvent(w.side.st, ready, 0));
+    if (P) {
+      OMM_CUDA_TRY(cudaMemsetAsync(P, 0, sizeof(double) * m * (size_t)m, st));
+      cudaEvent_t ready = nullptr;  // the side lane starts after the memsets
+      OMM_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+      w.events.push_back(ready);
+      OMM_CUDA_TRY(cudaEventRecord(ready, st));
+      OMM_CUDA_TRY(cudaStreamWaitEvent(w.side.st, ready, 0));
+    }
     chol_inv(w, 0, m);
-    cudaEvent_t done = nullptr;  // join: the main lane waits for the last P update
-    OMM_CUDA_TRY(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
-    w.events.push_back(done);
-    OMM_CUDA_TRY(cudaEventRecord(done, w.side.st));
-    OMM_CUDA_TRY(cudaStreamWaitEvent(st, done, 0));
-    launch_symmetrize_lower(st, m, P);
+    if (P) {
+      cudaEvent_t done = nullptr;  // join: the main lane waits for the last P update
+      OMM_CUDA_TRY(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+      w.events.push_back(done);
+      OMM_CUDA_TRY(cudaEventRecord(done, w.side.st));
+      OMM_CUDA_TRY(cudaStreamWaitEvent(st, done, 0));
+      launch_symmetrize_lower(st, m, P);
+    }
+    if (Y_out) {
+      zero_upper_kernel<<<1024, 256, 0, st>>>(m, A);
+      OMM_LAUNCH_CHECK();
+    }
   } catch (...) {
     cleanup();
     throw;
   }
   cleanup();
+}
+
+}  // namespace
+
+void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work, int* info_dev, int* err_dev) {
+  sliced_impl(st, m, A, P, nullptr, work, info_dev, err_dev);
+}
+
+void spd_factor_inverse_sliced(cudaStream_t st, int m, double* A, double* Y, void* work, int* info_dev,
+                               int* err_dev) {
+  sliced_impl(st, m, A, nullptr, Y, work, info_dev, err_dev);
 }
 
 }  // namespace omm

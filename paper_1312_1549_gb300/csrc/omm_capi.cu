@@ -244,6 +244,7 @@ void destroy(omm_ctx* c) {
     if (e) cudaEventDestroy(e);
   if (c->mixed) mixed_destroy(c->mixed);
   if (c->emu) emu_destroy(c->emu);
+  if (c->red) reduction_destroy(c->red);
   delete c;
 }
 
@@ -285,7 +286,8 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
   if (!(o.refine_ratio > 0.0)) o.refine_ratio = 1e-3;
   if (o.precision != OMM_PREC_FP64 && o.precision != OMM_PREC_MIXED)
     return fail(OMM_ERR_ARG, "omm_create: unknown precision");
-  const bool precond = (o.no_precondition == 0);
+  const bool chol = o.cholesky != 0;
+  const bool precond = !chol && o.no_precondition == 0;
   if (precond && !(tau > 0.0)) return fail(OMM_ERR_ARG, "omm_create: tau must be > 0");
   if (precond && !T && std::isfinite(tau)) return fail(OMM_ERR_ARG, "omm_create: T is NULL");
   if (!std::isfinite(eta)) return fail(OMM_ERR_ARG, "omm_create: eta is not finite");
@@ -314,9 +316,19 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     OMM_CUDA_TRY(cudaEventRecord(c->ev[0], c->st));
     copy_in(c->HS, H, mm, c->st);
     copy_in(c->HS + mm, S, mm, c->st);
-    launch_axpby_shift(c->st, mm, c->HS, c->HS + mm, eta, c->HS);
     // the mixed path factors with float64-class tensor-core products, the float64 path natively
     const bool sliced_inverse = o.precision == OMM_PREC_MIXED;
+    if (chol) {
+      // standard form (Sec. 2.4): H_r = L^-1 H L^-T in the H slot, the identity in the S slot
+      dev_alloc(&A, mm);
+      copy_in(A, S, mm, c->st);
+      OMM_CUDA_TRY(cudaEventRecord(c->ev[2], c->st));
+      c->red = reduction_create(c->st, m, sliced_inverse, A, c->info_dev);
+      reduce_hamiltonian(c->red, c->st, c->HS);
+      OMM_CUDA_TRY(cudaEventRecord(c->ev[3], c->st));
+      launch_identity(c->st, m, c->HS + mm);
+    }
+    launch_axpby_shift(c->st, mm, c->HS, c->HS + mm, eta, c->HS);
     if (precond) {
       dev_alloc(&c->P, mm);
       dev_alloc(&A, mm);
@@ -367,7 +379,8 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
       c->sliced_setup[2] = (double)c->prof_sliced.launches;
       c->prof_sliced.reset();
     }
-    c->ms_precond = precond ? elapsed(c->ev[2], c->ev[3]) : 0.0;
+    c->ms_precond = (precond || chol) ? elapsed(c->ev[2], c->ev[3]) : 0.0;
+    if (c->red && reduction_error(c->red, c->st) != 0) ierr = 1;
     dev_free(A);
     dev_free(work);
     dev_free(inv_err);
@@ -379,8 +392,8 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     }
     if (info != 0) {
       destroy(c);
-      return fail(OMM_ERR_NOT_SPD, "omm_create: S + T/tau is not positive definite (pivot " +
-                                       std::to_string(info) + ")");
+      return fail(OMM_ERR_NOT_SPD, std::string("omm_create: ") + (chol ? "S" : "S + T/tau") +
+                                       " is not positive definite (pivot " + std::to_string(info) + ")");
     }
   } catch (const std::bad_alloc&) {
     emu::set_profiler(nullptr);
@@ -406,11 +419,14 @@ omm_status omm_update_H(omm_ctx* c, const double* H) {
   try {
     const long mm = (long)c->m * c->m;
     copy_in(c->HS, H, mm, c->st);
+    if (c->red) reduce_hamiltonian(c->red, c->st, c->HS);  // the S slot holds the identity
     launch_axpby_shift(c->st, mm, c->HS, c->HS + mm, c->eta, c->HS);
     if (c->mixed) mixed_update_H(c->mixed, c->st, c->HS);
     if (c->emu) emu_update_H(c->emu, c->st, c->HS);
     OMM_CUDA_TRY(cudaStreamSynchronize(c->st));
     c->solved = false;
+    if (c->red && reduction_error(c->red, c->st) != 0)
+      return fail(OMM_ERR_TIMEOUT, "omm_update_H: a bounded device wait expired in the reduction");
   } catch (const CudaError& e) {
     return fail(OMM_ERR_CUDA, std::string("omm_update_H: ") + e.what + ": " + cudaGetErrorString(e.err));
   }
@@ -431,6 +447,15 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     c->prof_sliced.reset();
     if (c->prof_sliced.on) emu::set_profiler(&c->prof_sliced);
     copy_in(c->C, C0, nm, c->st);
+    double ms_transform = 0.0;
+    if (c->red) {  // C_r = L^T C0 (Sec. 2.4)
+      OMM_CUDA_TRY(cudaEventRecord(c->ev[0], c->st));
+      reduce_coefficients(c->red, c->st, n, c->C, c->Dir);
+      OMM_CUDA_TRY(cudaMemcpyAsync(c->C, c->Dir, nm * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+      OMM_CUDA_TRY(cudaEventRecord(c->ev[1], c->st));
+      OMM_CUDA_TRY(cudaEventSynchronize(c->ev[1]));
+      ms_transform += elapsed(c->ev[0], c->ev[1]);
+    }
     reset_loop_flags(c, true);
     write_scalars(c);
     const bool mixed = c->mixed != nullptr;
@@ -548,6 +573,18 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     inf.ms_iterate = ms_iter;
     inf.ms_refine = ms_ref;
     inf.ms_certify = ms_cert;
+    if (c->red && (result == OMM_OK || result == OMM_ERR_NO_CONVERGENCE)) {
+      // back to the original basis: C = L^-T C_r; S_W, H_W and E are the same in both bases
+      OMM_CUDA_TRY(cudaEventRecord(c->ev[0], c->st));
+      restore_coefficients(c->red, c->st, n, c->C, c->Dir);
+      OMM_CUDA_TRY(cudaMemcpyAsync(c->C, c->Dir, nm * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+      OMM_CUDA_TRY(cudaEventRecord(c->ev[1], c->st));
+      OMM_CUDA_TRY(cudaEventSynchronize(c->ev[1]));
+      ms_transform += elapsed(c->ev[0], c->ev[1]);
+      if (reduction_error(c->red, c->st) != 0) result = OMM_ERR_TIMEOUT;
+      flop += 2.0 * n * (double)m * m;  // two triangular n x m x m products
+    }
+    inf.ms_transform = ms_transform;
     if (result == OMM_OK || result == OMM_ERR_NO_CONVERGENCE) {
       if (Cout) OMM_CUDA_TRY(cudaMemcpyAsync(Cout, c->C, nm * sizeof(double), cudaMemcpyDefault, c->st));
       if (E) *E = inf.E;

@@ -7,6 +7,7 @@
 #include "emu.cuh"
 #include "omm_internal.cuh"
 #include "omm_mixed.cuh"
+#include "reduce.cuh"
 
 struct omm_ctx {
   int m = 0, n = 0;
@@ -37,6 +38,7 @@ struct omm_ctx {
   double ms_precond = 0.0;  // the Cholesky inverse inside ms_setup
   omm::MixedState* mixed = nullptr;
   omm::EmuState* emu = nullptr;  // float64-class tensor-core refresh of the mixed path
+  omm::Reduction* red = nullptr; // Cholesky reduction to standard form (opts.cholesky)
   omm::Profiler prof;  // main contraction kernel of the iteration (tensor-core or float64 GEMM)
   omm::Profiler prof_sliced;  // the float64-class sliced products (inverse, refreshes, certificate, D)
   double sliced_setup[3] = {0.0, 0.0, 0.0};  // ms, flops, launches of those in omm_create

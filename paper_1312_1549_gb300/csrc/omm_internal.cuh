@@ -117,7 +117,13 @@ void spd_inverse(cudaStream_t st, int m, double* A, double* P, double* work, int
 // The same inverse with float64-class (sliced, tensor-core) products; A is overwritten.
 // err_dev receives a nonzero code if a bounded wait of a tensor-core GEMM expired.
 size_t spd_inverse_sliced_workspace_bytes(int m);
+long partial_capacity(int m);  // chunk-sum scratch (doubles) of the sliced products of an m x m inverse
 void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work, int* info_dev, int* err_dev);
+// The factor alone, for the reduction to standard form: A = L L^T with L left in A (lower
+// triangle, zero above) and Y = L^-1 (lower, zero above); same workspaces as the inverses.
+void spd_factor_inverse(cudaStream_t st, int m, double* A, double* Y, double* work, int* info_dev);
+void spd_factor_inverse_sliced(cudaStream_t st, int m, double* A, double* Y, void* work, int* info_dev,
+                               int* err_dev);
 
 // ------------------------------------------------------------------ iteration kernels
 void launch_axpby_shift(cudaStream_t st, long count, const double* H, const double* S, double eta,

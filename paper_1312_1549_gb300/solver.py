@@ -41,11 +41,13 @@ class OMMSolver:
 
     H, S, T: m x m float64 (torch CUDA/CPU tensors or numpy arrays).
     n: number of Wannier functions. precision: "fp64" or "mixed".
+    cholesky=True: reduce to standard form by S = L L^T instead of preconditioning (the
+    paper's Cholesky flavour, end of Sec. 2.4); T and tau are then ignored.
     """
 
     def __init__(self, H, S, T, n, eta, tau, precision="fp64", stream=None, max_iter=0,
                  tol_grad=1e-9, e_tol=0.0, refine_ratio=0.0, precondition=True, check_every=0,
-                 profile=False, native_certificate=False):
+                 profile=False, native_certificate=False, cholesky=False):
         lib = N.lib()
         m = int(H.shape[0])
         self.m, self.n, self.eta, self.tau = m, int(n), float(eta), float(tau)
@@ -55,7 +57,8 @@ class OMMSolver:
                          check_every=int(check_every), tol_grad=float(tol_grad),
                          e_tol=float(e_tol), refine_ratio=float(refine_ratio),
                          profile=1 if profile else 0,
-                         native_certificate=1 if native_certificate else 0)
+                         native_certificate=1 if native_certificate else 0,
+                         cholesky=1 if cholesky else 0)
         self._keep = (H, S, T)
         h = ct.c_void_p()
         tau_arg = math.inf if tau is None else float(tau)
@@ -199,7 +202,7 @@ class OMMBatch:
 
     def __init__(self, problems, precision="mixed", stream=None, max_iter=0, tol_grad=1e-9,
                  refine_ratio=0.0, precondition=True, check_every=0, profile=False,
-                 native_certificate=False):
+                 native_certificate=False, cholesky=False):
         lib = N.lib()
         cnt = len(problems)
         self.count = cnt
@@ -208,7 +211,8 @@ class OMMBatch:
                          max_iter=int(max_iter), no_precondition=0 if precondition else 1,
                          check_every=int(check_every), tol_grad=float(tol_grad), e_tol=0.0,
                          refine_ratio=float(refine_ratio), profile=1 if profile else 0,
-                         native_certificate=1 if native_certificate else 0)
+                         native_certificate=1 if native_certificate else 0,
+                         cholesky=1 if cholesky else 0)
         P = ct.c_void_p * cnt
         ms = (ct.c_int * cnt)(*[s[0] for s in self.shapes])
         ns = (ct.c_int * cnt)(*[s[1] for s in self.shapes])

@@ -236,3 +236,54 @@ def test_si64_workload_reaches_lapack_minimum():
     assert abs(r["E"] - ex["E"]) / abs(ex["E"]) < 1e-12
     assert np.abs(r["D"] - ex["D"]).max() < 1e-7
     assert np.abs(r["SW"] - np.eye(p.n)).max() < 1e-8
+
+
+# ---------------------------------------------------------------- the Cholesky flavour (Sec. 2.4)
+@pytest.mark.parametrize("m,n,seed", [(12, 3, 10), (20, 7, 11), (24, 10, 12)])
+def test_cholesky_flavour_reaches_brute_force(m, n, seed):
+    """Reduced to standard form, the OMM still reaches 2 sum eps_i, D and EDM of H x = eps S x."""
+    H, S, T, eta, C0, w = tiny_problem(m, n, seed)
+    r = omm.solve_cholesky(H, S, eta, C0, tol_grad=1e-11, max_iter=5000)
+    assert r["status"] == omm.STATUS_OK
+    ex = exact.exact_minimum(H, S, n, method="jacobi")
+    assert r["E"] == pytest.approx(ex["E"], rel=1e-12, abs=1e-12)
+    C = r["C"]                                     # back in the original basis
+    assert np.allclose(C.T @ S @ C, np.eye(n), atol=1e-9)
+    assert np.allclose(r["D"], ex["D"], atol=1e-9)
+    assert np.allclose(r["EDM"], ex["EDM"], atol=1e-9)
+    assert np.allclose(C.T @ (H - eta * S) @ C, r["HW"], atol=1e-9)   # H_W is basis-invariant
+
+
+@pytest.mark.parametrize("m,n,seed", [(20, 7, 11), (30, 9, 13)])
+def test_cholesky_flavour_follows_s_inverse_preconditioning(m, n, seed):
+    """Sec. 2.4: minimising the reduced problem follows the original one preconditioned by S^-1.
+
+    Same start (C_r = L^T C0), so the line-search steps x, the PR coefficients and the energies
+    agree iteration by iteration (up to rounding), and both stop after the same number of steps.
+    """
+    H, S, T, eta, C0, w = tiny_problem(m, n, seed)
+    red, orig = [], []
+    omm.solve_cholesky(H, S, eta, C0, tol_grad=1e-30, max_iter=12,
+                       callback=lambda it, E, x, b: red.append((E, x, b)), want_matrices=False)
+    omm.solve(H, S, None, eta, math.inf, C0, tol_grad=1e-30, max_iter=12, precondition=True,
+              callback=lambda it, E, x, b: orig.append((E, x, b)), want_matrices=False)
+    assert len(red) == len(orig) == 12
+    for (Er, xr, br), (Eo, xo, bo) in zip(red, orig):
+        assert Er == pytest.approx(Eo, rel=1e-10, abs=1e-12)
+        assert xr == pytest.approx(xo, rel=1e-7)
+        assert br == pytest.approx(bo, rel=1e-6, abs=1e-12)
+    # and not the unpreconditioned trajectory
+    plain = []
+    omm.solve(H, S, None, eta, math.inf, C0, tol_grad=1e-30, max_iter=12, precondition=False,
+              callback=lambda it, E, x, b: plain.append((E, x, b)), want_matrices=False)
+    assert any(abs(a[1] - b[1]) > 1e-3 * abs(b[1]) for a, b in zip(plain, orig))
+
+
+def test_cholesky_flavour_si64_workload():
+    from synth import si64_sz
+    p = si64_sz()
+    r = omm.solve_cholesky(p.H, p.S, p.eta, p.C0, tol_grad=1e-9)
+    assert r["status"] == omm.STATUS_OK and r["gmax"] < 1e-9
+    ex = exact.exact_minimum(p.H, p.S, p.n)
+    assert abs(r["E"] - ex["E"]) / abs(ex["E"]) < 1e-12
+    assert np.abs(r["D"] - ex["D"]).max() < 1e-7
