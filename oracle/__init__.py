@@ -10,13 +10,16 @@ Contents (all plain float64 CPU code, written from the paper):
   lowest generalised eigenpairs of H x = eps S x (Sec. 2.1, Eqs. 1 and 7-8).
 * `jacobi` -- a self-contained cyclic Jacobi eigensolver with Cholesky
   reduction, used to pin `exact` on tiny inputs without any library solver.
-* `omm`    -- the OMM itself, step by step: eigenspectrum shift (Sec. 2.2),
-  CG with Polak-Ribiere directions, the gradient (Eq. 9), the quartic line
-  search with directly computed coefficients (Eq. 10-12), the state update
-  (Eq. 13), the kinetic preconditioner (Eq. 14) and the outputs.
+* `omm`    -- the OMM itself, step by step: eigenspectrum shift (Sec. 2.2, Eq. 9),
+  CG with Polak-Ribiere directions, the gradient (Eq. 12), the quartic line
+  search with directly computed coefficients (Eqs. 13-15), the state update
+  (Eq. 16), the kinetic preconditioner (Eq. 17), the outputs, and the
+  Cholesky flavour (reduction to standard form, end of Sec. 2.4).
+* `hermitian` -- the same steps in complex arithmetic with Hermitian
+  conjugates, as the paper writes them (Secs. 2.1-2.3), for k-point problems.
 
 Parity status: every function here is pinned by a test in
-tests/test_oracle_pins.py against brute force, closed forms, finite
+tests/test_oracle_pins.py and tests/test_oracle_hermitian.py against brute force, closed forms, finite
 differences or invariants; none is "parity unpinned" except the CG iteration
 count, which the paper does not fix.
 """
