@@ -212,6 +212,39 @@ omm_ctx* omm_batch_instance(omm_batch* b, int i);
 /* Release the batch and its instances (NULL is ignored). */
 void omm_free_batched(omm_batch* b);
 
+/* ---- Hermitian problems (complex matrices: k points) ----
+ * The paper states the method for complex matrices (Secs. 2.1-2.3: H_W = C^H H C, S_W = C^H S C,
+ * the quartic of Eq. 13 with (S_W')^H) and uses them for its k-point tests (Sec. 3.3). These
+ * entry points take complex128 matrices -- interleaved (real, imaginary) float64 pairs, row-major:
+ * H, S, T, D, EDM m x m Hermitian (2 m^2 doubles each), C0 and C n x m (2 n m doubles; row j is
+ * Wannier function j, i.e. column j of the paper's C, not conjugated) -- host or device, with the
+ * conventions above. The library solves the real form [[Re A, -Im A], [Im A, Re A]] (2m x 2m,
+ * 2n Wannier functions) on its real path, from the real form of C0; the iterates stay the real
+ * forms of the complex ones, so the line-search steps are those of the complex method and
+ * max|G| (tol_grad, omm_info.gmax) is the largest |Re G_ij| or |Im G_ij| of the complex gradient
+ * of Eq. 12 (dE~ = Re Tr(G^H dC)). E is the complex problem's band energy 2 sum_{i<=n} eps_i
+ * (info.E and info.Etilde likewise); omm_info's counters and timings are those of the real
+ * solve, which does twice the arithmetic of complex products. D = 2 C (2I - S_W) C^H is dE/dH
+ * and dE/dS = -EDM in the sense dE = Re Tr(D dH) - Re Tr(EDM dS) for Hermitian dH, dS.
+ * A Hermitian context or batch is used only through these entry points (and omm_free,
+ * omm_free_batched, omm_batch_instance); the real ones return OMM_ERR_ARG for it. */
+omm_status omm_create_hermitian(int m, int n, const double* H, const double* S, const double* T,
+                                double eta, double tau, const omm_opts* opts, void* stream,
+                                omm_ctx** out);
+omm_status omm_solve_hermitian(omm_ctx* ctx, const double* C0, double* C, double* E, double* D,
+                               omm_info* info);
+omm_status omm_backward_hermitian(omm_ctx* ctx, double* dEdH, double* dEdS);
+/* SCF warm start with a new Hermitian H (S, T and the preconditioner kept). */
+omm_status omm_update_H_hermitian(omm_ctx* ctx, const double* H);
+/* A batch of Hermitian problems (e.g. the points of a k grid), solved in lockstep like
+ * omm_create_batched / omm_solve_batched. */
+omm_status omm_create_hermitian_batched(int count, const int* m, const int* n, const double* const* H,
+                                        const double* const* S, const double* const* T,
+                                        const double* eta, const double* tau, const omm_opts* opts,
+                                        void* stream, omm_batch** out);
+omm_status omm_solve_hermitian_batched(omm_batch* b, const double* const* C0, double* const* C,
+                                       double* E, omm_info* info);
+
 /* Static description of a status code. */
 const char* omm_status_str(omm_status s);
 

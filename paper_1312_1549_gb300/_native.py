@@ -74,6 +74,13 @@ _SIGNATURES = {
     "omm_solve_batched": (_I, [_P, _P, _P, _P, _P]),
     "omm_batch_instance": (_P, [_P, _I]),
     "omm_free_batched": (None, [_P]),
+    "omm_create_hermitian": (_I, [_I, _I, _P, _P, _P, _D, _D, ct.POINTER(OmmOpts), _P, ct.POINTER(_P)]),
+    "omm_solve_hermitian": (_I, [_P, _P, _P, ct.POINTER(_D), _P, ct.POINTER(OmmInfo)]),
+    "omm_backward_hermitian": (_I, [_P, _P, _P]),
+    "omm_update_H_hermitian": (_I, [_P, _P]),
+    "omm_create_hermitian_batched": (_I, [_I, _P, _P, _P, _P, _P, _P, _P, ct.POINTER(OmmOpts), _P,
+                                          ct.POINTER(_P)]),
+    "omm_solve_hermitian_batched": (_I, [_P, _P, _P, _P, _P]),
     "omm_kernel_dgemm": (_I, [_I, _I, _I, _I, _I, _D, _P, _L, _P, _L, _D, _P, _L, _P]),
     "omm_kernel_spd_inverse": (_I, [_I, _P, _P, ct.POINTER(_I), _P]),
     "omm_kernel_spd_inverse_sliced": (_I, [_I, _P, _P, ct.POINTER(_I), _P]),

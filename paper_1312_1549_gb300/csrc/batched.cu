@@ -173,6 +173,8 @@ struct omm_batch {
   std::vector<double> gemm_flop[kGroupedGemms];  // issued flops of each instance's group
 };
 
+int omm::batch_count(const omm_batch* b) { return b ? b->count : 0; }
+
 namespace {
 
 void batch_destroy(omm_batch* b) {
@@ -452,6 +454,9 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
 omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* const* C, double* E, omm_info* info) {
   if (!b || !C0) return fail(OMM_ERR_ARG, "omm_solve_batched: NULL argument");
   const int cnt = b->count;
+  for (int i = 0; i < cnt; ++i)
+    if (b->ctx[i]->hermitian)
+      return fail(OMM_ERR_ARG, "omm_solve_batched: Hermitian batch (use omm_solve_hermitian_batched)");
   if (b->opts.precision != OMM_PREC_MIXED) {
     // float64: instance after instance through the single-instance path
     omm_status worst = OMM_OK;

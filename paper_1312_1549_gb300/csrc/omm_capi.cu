@@ -239,6 +239,8 @@ void destroy(omm_ctx* c) {
   dev_free(c->mm);
   dev_free(c->sc);
   dev_free(c->info_dev);
+  dev_free(c->hz_stage);
+  dev_free(c->hz_rows);
   if (c->sc_host) cudaFreeHost(c->sc_host);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
@@ -416,6 +418,7 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
 
 omm_status omm_update_H(omm_ctx* c, const double* H) {
   if (!c || !H) return fail(OMM_ERR_ARG, "omm_update_H: NULL argument");
+  if (c->hermitian) return fail(OMM_ERR_ARG, "omm_update_H: Hermitian context (use omm_update_H_hermitian)");
   try {
     const long mm = (long)c->m * c->m;
     copy_in(c->HS, H, mm, c->st);
@@ -435,6 +438,7 @@ omm_status omm_update_H(omm_ctx* c, const double* H) {
 
 omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, double* D, omm_info* info) {
   if (!c || !C0) return fail(OMM_ERR_ARG, "omm_solve: NULL argument");
+  if (c->hermitian) return fail(OMM_ERR_ARG, "omm_solve: Hermitian context (use omm_solve_hermitian)");
   omm_info inf{};
   omm_status result = OMM_OK;
   const int m = c->m, n = c->n;
@@ -638,6 +642,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
 
 omm_status omm_backward(omm_ctx* c, double* dEdH, double* dEdS) {
   if (!c) return fail(OMM_ERR_ARG, "omm_backward: NULL context");
+  if (c->hermitian) return fail(OMM_ERR_ARG, "omm_backward: Hermitian context (use omm_backward_hermitian)");
   if (!c->solved) return fail(OMM_ERR_STATE, "omm_backward: no converged solve");
   try {
     const size_t bytes = (size_t)c->m * c->m * sizeof(double);

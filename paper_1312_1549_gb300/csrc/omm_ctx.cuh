@@ -39,6 +39,12 @@ struct omm_ctx {
   omm::MixedState* mixed = nullptr;
   omm::EmuState* emu = nullptr;  // float64-class tensor-core refresh of the mixed path
   omm::Reduction* red = nullptr; // Cholesky reduction to standard form (opts.cholesky)
+  // Hermitian problems (omm_create_hermitian): this context solves the real form of the
+  // mc x mc complex problem (m = 2 mc, n = 2 nc)
+  bool hermitian = false;
+  int mc = 0, nc = 0;
+  double* hz_stage = nullptr;  // complex staging, 2 mc^2 doubles
+  double* hz_rows = nullptr;   // the real form of C (2 nc x 2 mc)
   omm::Profiler prof;  // main contraction kernel of the iteration (tensor-core or float64 GEMM)
   omm::Profiler prof_sliced;  // the float64-class sliced products (inverse, refreshes, certificate, D)
   double sliced_setup[3] = {0.0, 0.0, 0.0};  // ms, flops, launches of those in omm_create
@@ -58,5 +64,6 @@ void read_scalars(omm_ctx* c);
 void write_scalars(omm_ctx* c);
 void density_into(omm_ctx* c, double* out);
 void destroy(omm_ctx* c);
+int batch_count(const omm_batch* b);
 
 }  // namespace omm

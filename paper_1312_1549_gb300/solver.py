@@ -269,3 +269,168 @@ class OMMBatch:
         dS = torch.empty((m, m), dtype=torch.float64, device=dev)
         N.check(N.lib().omm_backward(ctx, _ptr(dH), _ptr(dS)), "omm_backward")
         return dH, dS
+
+
+# ------------------------------------------------------------------ Hermitian (complex) problems
+def _zptr(x):
+    """Pointer to a contiguous complex128 tensor or array (interleaved real, imaginary)."""
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.complex128 or not x.is_contiguous():
+            raise ValueError("expected a contiguous complex128 tensor")
+        return ct.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.complex128 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a C-contiguous complex128 array")
+        return ct.c_void_p(x.ctypes.data)
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _zlike(x, shape):
+    if isinstance(x, torch.Tensor):
+        return torch.empty(shape, dtype=torch.complex128, device=x.device)
+    return np.empty(shape, dtype=np.complex128)
+
+
+def _opts(precision, max_iter, tol_grad, e_tol, refine_ratio, precondition, check_every, profile,
+          native_certificate, cholesky):
+    return N.OmmOpts(precision=N.PREC_MIXED if precision == "mixed" else N.PREC_FP64,
+                     max_iter=int(max_iter), no_precondition=0 if precondition else 1,
+                     check_every=int(check_every), tol_grad=float(tol_grad), e_tol=float(e_tol),
+                     refine_ratio=float(refine_ratio), profile=1 if profile else 0,
+                     native_certificate=1 if native_certificate else 0, cholesky=1 if cholesky else 0)
+
+
+class OMMHermitian:
+    """One Hermitian (complex) problem: omm_create_hermitian / omm_solve_hermitian / ...
+
+    H, S, T: m x m complex128 (torch or numpy); C0: n x m complex128. E is the complex problem's
+    band energy; D and dE/dS = -EDM are m x m complex128.
+    """
+
+    def __init__(self, H, S, T, n, eta, tau, precision="fp64", stream=None, max_iter=0,
+                 tol_grad=1e-9, e_tol=0.0, refine_ratio=0.0, precondition=True, check_every=0,
+                 profile=False, native_certificate=False, cholesky=False):
+        lib = N.lib()
+        self.m, self.n, self.eta, self.tau = int(H.shape[0]), int(n), float(eta), float(tau)
+        opts = _opts(precision, max_iter, tol_grad, e_tol, refine_ratio, precondition, check_every,
+                     profile, native_certificate, cholesky)
+        h = ct.c_void_p()
+        N.check(lib.omm_create_hermitian(self.m, self.n, _zptr(H), _zptr(S), _zptr(T), self.eta,
+                                         math.inf if tau is None else float(tau), ct.byref(opts),
+                                         _stream_handle(stream), ct.byref(h)), "omm_create_hermitian")
+        self._h = h
+        self.info = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().omm_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, C0, want_D=False, C_out=None, D_out=None, raise_on_error=True):
+        """Minimise from C0 (n x m complex). Returns (C, E, D or None, info dict)."""
+        if C_out is None:
+            C_out = _zlike(C0, (self.n, self.m))
+        if want_D and D_out is None:
+            D_out = _zlike(C0, (self.m, self.m))
+        E = ct.c_double(0.0)
+        info = N.OmmInfo()
+        rc = N.lib().omm_solve_hermitian(self._h, _zptr(C0), _zptr(C_out), ct.byref(E),
+                                         _zptr(D_out) if want_D else None, ct.byref(info))
+        self.info = info.as_dict()
+        if raise_on_error:
+            N.check(rc, "omm_solve_hermitian")
+        return C_out, E.value, (D_out if want_D else None), self.info
+
+    def backward(self, device=None):
+        """(dE/dH, dE/dS) = (D, -EDM) at the last converged solve (m x m complex)."""
+        dev = device if device is not None else torch.device("cuda")
+        dH = torch.empty((self.m, self.m), dtype=torch.complex128, device=dev)
+        dS = torch.empty((self.m, self.m), dtype=torch.complex128, device=dev)
+        N.check(N.lib().omm_backward_hermitian(self._h, _zptr(dH), _zptr(dS)), "omm_backward_hermitian")
+        return dH, dS
+
+    def update_H(self, H):
+        N.check(N.lib().omm_update_H_hermitian(self._h, _zptr(H)), "omm_update_H_hermitian")
+
+
+class OMMHermitianBatch:
+    """Hermitian problems solved together (the points of a k grid): problems are
+    (H, S, T, n, eta, tau) with complex128 matrices."""
+
+    def __init__(self, problems, precision="mixed", stream=None, max_iter=0, tol_grad=1e-9,
+                 refine_ratio=0.0, precondition=True, check_every=0, profile=False,
+                 native_certificate=False, cholesky=False):
+        cnt = len(problems)
+        self.count = cnt
+        self.shapes = [(int(p[0].shape[0]), int(p[3])) for p in problems]
+        opts = _opts(precision, max_iter, tol_grad, 0.0, refine_ratio, precondition, check_every, profile,
+                     native_certificate, cholesky)
+        P = ct.c_void_p * cnt
+        ms = (ct.c_int * cnt)(*[s[0] for s in self.shapes])
+        ns = (ct.c_int * cnt)(*[s[1] for s in self.shapes])
+        Ts = None if all(p[2] is None for p in problems) else P(*[_zptr(p[2]) for p in problems])
+        etas = (ct.c_double * cnt)(*[float(p[4]) for p in problems])
+        taus = (ct.c_double * cnt)(*[float(p[5]) for p in problems])
+        h = ct.c_void_p()
+        N.check(N.lib().omm_create_hermitian_batched(cnt, ms, ns, P(*[_zptr(p[0]) for p in problems]),
+                                                     P(*[_zptr(p[1]) for p in problems]), Ts, etas, taus,
+                                                     ct.byref(opts), _stream_handle(stream), ct.byref(h)),
+                "omm_create_hermitian_batched")
+        self._h = h
+        self.infos = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().omm_free_batched(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, C0s, C_outs=None, raise_on_error=True):
+        """Solve all instances from C0s (list of n_i x m_i complex). Returns (C list, E array, infos)."""
+        cnt = self.count
+        if C_outs is None:
+            C_outs = [_zlike(c, c.shape) for c in C0s]
+        P = ct.c_void_p * cnt
+        E = (ct.c_double * cnt)()
+        infos = (N.OmmInfo * cnt)()
+        rc = N.lib().omm_solve_hermitian_batched(self._h, P(*[_zptr(c) for c in C0s]),
+                                                 P(*[_zptr(c) for c in C_outs]), E, infos)
+        self.infos = [infos[i].as_dict() for i in range(cnt)]
+        if raise_on_error:
+            N.check(rc, "omm_solve_hermitian_batched")
+        return C_outs, np.array(list(E)), self.infos
+
+    def backward(self, i, device=None):
+        """(dE/dH, dE/dS) of instance i after a converged batched solve (m x m complex)."""
+        m = self.shapes[i][0]
+        dev = device if device is not None else torch.device("cuda")
+        ctx = N.lib().omm_batch_instance(self._h, int(i))
+        dH = torch.empty((m, m), dtype=torch.complex128, device=dev)
+        dS = torch.empty((m, m), dtype=torch.complex128, device=dev)
+        N.check(N.lib().omm_backward_hermitian(ctx, _zptr(dH), _zptr(dS)), "omm_backward_hermitian")
+        return dH, dS

@@ -12,6 +12,12 @@ which is exact for the k of this Gamma-centred grid: the supercell's Gamma-point
 is the union of the spectra of H(k) x = eps S(k) x. The diagonal jitter is periodic (the
 same for every cell) so that the supercell keeps the lattice's translation symmetry. One
 eta for all k: above the highest occupied level of the grid and inside the gap.
+
+For any other k (a Monkhorst-Pack grid such as the paper's 9 x 9 x 9) the real-space
+blocks h(R) are read from a 4 x 4 x 4 supercell (edge 41 bohr): every matrix element of
+the model has range r_c = 9 bohr and its separable potential sums paths of at most 3 r_c,
+so no element of that supercell mixes two periodic images, and each atom pair's element
+belongs to the translation of its minimum image. Then H(k) = sum_R h(R) exp(i k . R).
 """
 from __future__ import annotations
 
@@ -79,3 +85,85 @@ def silicon_kpoints(grid=(2, 2, 2), basis="DZP", seed=0, keep_supercell=False) -
     return KProblem(name=f"si8_{basis}_k{grid[0]}x{grid[1]}x{grid[2]}", m=m, n=n, k=ks, H=Hk, S=Sk, T=Tk,
                     eta=float(eta), tau=TAU_10RY, C0=C0, seed=seed, meta=meta,
                     supercell=(H_sc, S_sc) if keep_supercell else None)
+
+
+def _bloch_blocks(basis, seed, sc=(4, 4, 4)):
+    """Real-space blocks of the 8-atom cell read from an sc supercell.
+
+    Returns (m, norb, H_rows, S_rows, T_rows, R): rows of cell 0 against the whole supercell
+    (m x m_sc each) and R[a, b'] the lattice translation of atom b' relative to the cell-0 copy
+    of its sublattice site, taken at the minimum image from atom a (shape 8 x natoms x 3).
+    """
+    streams = _streams(seed)
+    model = si_model(basis)
+    norb = model.species["Si"].norb
+    m = 8 * norb
+    ncell = int(np.prod(sc))
+    jitter_cell = streams[1].normal(0.0, JITTER_SIGMA, size=m)
+    symbols, pos, cell = si_supercell(*sc)
+    S_sc, T_sc, H_sc, _ = build_matrices(model, symbols, pos, cell, np.tile(jitter_cell, ncell))
+    nat = len(symbols)
+    d = pos[None, :, :] - pos[:8, None, :]                      # (8, nat, 3) from atom a to b'
+    d -= cell * np.round(d / cell)
+    site = pos[np.arange(nat) % 8]                              # cell-0 copy of b'
+    R = pos[:8, None, :] + d - site[None, :, :]
+    return m, norb, H_sc[:m], S_sc[:m], T_sc[:m], R, streams
+
+
+def monkhorst_pack(q, time_reversal=True):
+    """Monkhorst-Pack grid q1 x q2 x q3 of the cubic cell: (k vectors, weights summing to 1).
+
+    With time_reversal, k and -k (H(-k) = conj H(k) for real h(R)) are merged: one of each
+    pair is kept with twice the weight.
+    """
+    axes = [(2.0 * np.arange(1, qi + 1) - qi - 1) / (2.0 * qi) for qi in q]
+    frac = np.array([(x, y, z) for x in axes[0] for y in axes[1] for z in axes[2]])
+    w = np.full(len(frac), 1.0 / len(frac))
+    if time_reversal:
+        key = {tuple(np.round(f, 12)): i for i, f in enumerate(frac)}
+        keep, wk = [], []
+        for i, f in enumerate(frac):
+            j = key.get(tuple(np.round(-f, 12)))
+            if j is None or j > i:
+                keep.append(i)
+                wk.append(w[i] * (2.0 if j is not None and j != i else 1.0))
+            elif j == i:
+                keep.append(i)
+                wk.append(w[i])
+        frac, w = frac[keep], np.array(wk)
+    return frac * (2.0 * np.pi / A_SI), w
+
+
+def bloch_matrices(ks, basis="DZP", seed=0, sc=(4, 4, 4)):
+    """H(k), S(k), T(k) = sum_R h(R) exp(i k . R) of the 8-atom cell at the wave vectors ks,
+    with h(R) read from an sc supercell. Returns (Hk, Sk, Tk, streams)."""
+    m, norb, Hr, Sr, Tr, R, streams = _bloch_blocks(basis, seed, sc)
+    nat = R.shape[1]
+
+    def bloch(rows, kv):
+        ph = np.exp(1j * (R @ kv))                                  # (8, nat)
+        full = rows.reshape(8, norb, nat, norb) * ph[:, None, :, None]   # [a, mu, b', nu]
+        out = full.reshape(8, norb, nat // 8, 8, norb).sum(axis=2).reshape(m, m)
+        return 0.5 * (out + out.conj().T)
+
+    return ([bloch(Hr, kv) for kv in ks], [bloch(Sr, kv) for kv in ks], [bloch(Tr, kv) for kv in ks],
+            streams)
+
+
+def silicon_mp_grid(q=(9, 9, 9), basis="DZP", seed=0, time_reversal=True) -> KProblem:
+    """Bulk Si (8-atom cell) on a q1 x q2 x q3 Monkhorst-Pack grid, the paper's k-point test
+    shape (Sec. 3.3: 9 x 9 x 9); k and -k merged with time_reversal (weights in meta)."""
+    ks, wk = monkhorst_pack(q, time_reversal)
+    Hk, Sk, Tk, streams = bloch_matrices(ks, basis, seed)
+    m, n = Hk[0].shape[0], 16
+    import scipy.linalg
+    ev = [scipy.linalg.eigh(h, s, eigvals_only=True, subset_by_index=[n - 1, n]) for h, s in zip(Hk, Sk)]
+    homo = max(float(e[0]) for e in ev)
+    lumo = min(float(e[1]) for e in ev)
+    eta = homo + min(ETA_ABOVE_HOMO, 0.5 * (lumo - homo))
+    C0 = [(streams[2].normal(0.0, 0.1, size=(n, m)) + 1j * streams[2].normal(0.0, 0.1, size=(n, m)))
+          / np.sqrt(2 * m) for _ in ks]
+    meta = {"system": "Si", "basis": basis, "mp_grid": list(q), "time_reversal": time_reversal,
+            "weights": wk.tolist(), "homo": homo, "lumo": lumo, "gap": lumo - homo, "atoms_per_cell": 8}
+    return KProblem(name=f"si8_{basis}_mp{q[0]}x{q[1]}x{q[2]}", m=m, n=n, k=ks, H=Hk, S=Sk, T=Tk,
+                    eta=float(eta), tau=TAU_10RY, C0=C0, seed=seed, meta=meta)

@@ -141,3 +141,26 @@ def test_kpoint_oracle_reaches_exact_minimum():
         assert r["status"] == omm.STATUS_OK
         assert abs(r["E"] - ex["E"]) / abs(ex["E"]) < 1e-12
         assert np.abs(r["D"] - ex["D"]).max() < 1e-8
+
+
+def test_bloch_sums_do_not_depend_on_the_supercell():
+    """h(R) read from the 4x4x4 and from the 4x4x5 supercell give the same H(k), S(k) at
+    Monkhorst-Pack points that neither supercell folds onto Gamma: no element mixes images."""
+    from synth.kpoints import bloch_matrices, monkhorst_pack
+    ks, _ = monkhorst_pack((9, 9, 9))
+    pick = ks[[1, 40, 200]]
+    H4, S4, _, _ = bloch_matrices(pick, sc=(4, 4, 4))
+    H5, S5, _, _ = bloch_matrices(pick, sc=(4, 4, 5))
+    for a, b in zip(H4 + S4, H5 + S5):
+        assert np.abs(a - b).max() < 1e-13
+    # time reversal: H(-k) = conj H(k)
+    Hm, _, _, _ = bloch_matrices(-pick[:1])
+    assert np.abs(Hm[0] - H4[0].conj()).max() < 1e-13
+
+
+def test_monkhorst_pack_weights():
+    from synth.kpoints import monkhorst_pack
+    k, w = monkhorst_pack((9, 9, 9))
+    assert len(k) == 365 and w.sum() == pytest.approx(1.0, abs=1e-14)
+    k, w = monkhorst_pack((4, 4, 4), time_reversal=False)
+    assert len(k) == 64 and np.all(w == 1.0 / 64)
