@@ -563,7 +563,10 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
         if (h.status != 0) {
           result[i] = (omm_status)h.status;
           finished[i] = 1;
-          if (result[i] == OMM_ERR_NO_CONVERGENCE) recompute_state_fp64(c);
+          if (result[i] == OMM_ERR_NO_CONVERGENCE) {
+            project_real_form(c, c->st);
+            recompute_state_fp64(c);
+          }
           h.done = 1;
           write_scalars(c);
           continue;
@@ -574,6 +577,7 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
         cudaStream_t q = b->pool[todo.size() % kRefreshStreams];
         c->st = q;
         OMM_CUDA_TRY(cudaEventRecord(c->ev[0], q));
+        project_real_form(c, q);
         if (native) recompute_state_fp64(c);
         else emu_recompute_state(c->emu, q, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
         OMM_CUDA_TRY(cudaEventRecord(c->ev[1], q));

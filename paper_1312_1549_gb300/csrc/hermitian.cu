@@ -63,6 +63,23 @@ __global__ void extract_matrix_kernel(int m, const double* __restrict__ src, dou
   }
 }
 
+// the nearest real form: rows j and n + j of C_e (2n x 2m) averaged onto one complex row
+__global__ void project_rows_kernel(int n, int m, double* __restrict__ Ce) {
+  const long count = (long)n * m;
+  const long ld = 2L * m;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < count; idx += (long)gridDim.x * blockDim.x) {
+    const long j = idx / m, k = idx % m;
+    double* top = Ce + j * ld;
+    double* bot = Ce + (n + j) * ld;
+    const double re = 0.5 * (top[k] + bot[m + k]);
+    const double im = 0.5 * (top[m + k] - bot[k]);
+    top[k] = re;
+    top[m + k] = im;
+    bot[k] = -im;
+    bot[m + k] = re;
+  }
+}
+
 unsigned grid_for(long count) { return (unsigned)std::min<long>((count + 255) / 256, 4096); }
 
 template <typename T>
@@ -128,6 +145,7 @@ void embed_inputs(cudaStream_t st, int m, const double* H, const double* S, cons
 // complex-side buffers of a context made by omm_create_hermitian
 void attach(omm_ctx* c, int m, int n) {
   c->hermitian = true;
+  c->real_form = true;
   c->mc = m;
   c->nc = n;
   alloc(&c->hz_stage, 2 * (size_t)m * m);
@@ -152,6 +170,13 @@ omm_status check_hermitian(omm_ctx* c, const char* who) {
 }
 
 }  // namespace
+
+void project_real_form(omm_ctx* c, cudaStream_t st) {
+  if (!c->real_form || c->red) return;  // (the Cholesky flavour's reduced basis has no such structure)
+  project_rows_kernel<<<grid_for((long)c->nc * c->mc), 256, 0, st>>>(c->nc, c->mc, c->C);
+  OMM_LAUNCH_CHECK();
+}
+
 }  // namespace omm
 
 using namespace omm;
@@ -163,6 +188,8 @@ omm_status omm_create_hermitian(int m, int n, const double* H, const double* S, 
   if (out) *out = nullptr;
   if (!out || !H || !S) return fail(OMM_ERR_ARG, "omm_create_hermitian: NULL argument");
   if (m <= 0 || n <= 0 || n >= m) return fail(OMM_ERR_ARG, "omm_create_hermitian: need 0 < n < m");
+  if (opts && opts->cholesky && opts->precision == OMM_PREC_MIXED)
+    return fail(OMM_ERR_ARG, "omm_create_hermitian: the Cholesky flavour of a Hermitian problem needs OMM_PREC_FP64");
   cudaStream_t st = (cudaStream_t)stream;
   Embedded e;
   omm_status rc = OMM_OK;
@@ -281,6 +308,9 @@ omm_status omm_create_hermitian_batched(int count, const int* m, const int* n, c
   if (out) *out = nullptr;
   if (!out || count <= 0 || !m || !n || !H || !S || !eta || !tau)
     return fail(OMM_ERR_ARG, "omm_create_hermitian_batched: invalid argument");
+  if (opts && opts->cholesky && opts->precision == OMM_PREC_MIXED)
+    return fail(OMM_ERR_ARG, "omm_create_hermitian_batched: the Cholesky flavour of a Hermitian problem needs "
+                             "OMM_PREC_FP64");
   for (int i = 0; i < count; ++i)
     if (m[i] <= 0 || n[i] <= 0 || n[i] >= m[i] || !H[i] || !S[i])
       return fail(OMM_ERR_ARG, "omm_create_hermitian_batched: instance " + std::to_string(i) + ": invalid argument");

@@ -486,6 +486,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
         mixed_recompute_state(c->mixed, c->st, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
         flop_tc += 3.0 * per_state;
       } else if (emu_state) {
+        project_real_form(c, c->st);
         emu_recompute_state(c->emu, c->st, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
         flop_tc += 0.5 * kEmuSlices * (kEmuSlices + 1) * per_state;
         if (emu_error(c->emu, c->st) != 0) {
@@ -493,6 +494,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
           break;
         }
       } else {
+        project_real_form(c, c->st);
         recompute_state_fp64(c);
       }
       flop += per_state;
@@ -556,6 +558,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
         result = (omm_status)h.status;
         if (result != OMM_ERR_NO_CONVERGENCE) break;
         // iteration cap: certify what we have, report no convergence
+        project_real_form(c, c->st);
         recompute_state_fp64(c);
         read_scalars(c);
         break;

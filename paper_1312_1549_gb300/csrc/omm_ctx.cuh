@@ -41,7 +41,8 @@ struct omm_ctx {
   omm::Reduction* red = nullptr; // Cholesky reduction to standard form (opts.cholesky)
   // Hermitian problems (omm_create_hermitian): this context solves the real form of the
   // mc x mc complex problem (m = 2 mc, n = 2 nc)
-  bool hermitian = false;
+  bool hermitian = false;   // gates the real entry points (lifted while a Hermitian call runs)
+  bool real_form = false;   // this context holds a real form (set once, never lifted)
   int mc = 0, nc = 0;
   double* hz_stage = nullptr;  // complex staging, 2 mc^2 doubles
   double* hz_rows = nullptr;   // the real form of C (2 nc x 2 mc)
@@ -65,5 +66,10 @@ void write_scalars(omm_ctx* c);
 void density_into(omm_ctx* c, double* out);
 void destroy(omm_ctx* c);
 int batch_count(const omm_batch* b);
+// real form of a Hermitian problem: C <- the nearest real form of a complex C (each pair of rows
+// j, n + j averaged onto [Re c | Im c], [-Im c | Re c]); no-op for other contexts. Called before
+// every recompute of the state, so that rounding of the mixed path cannot accumulate along the
+// directions that leave the real forms (they are flat: the functional does not see them).
+void project_real_form(omm_ctx* c, cudaStream_t st);
 
 }  // namespace omm
