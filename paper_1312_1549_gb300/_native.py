@@ -23,7 +23,8 @@ class OmmOpts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("max_iter", ct.c_int), ("no_precondition", ct.c_int),
                 ("check_every", ct.c_int), ("tol_grad", ct.c_double), ("e_tol", ct.c_double),
                 ("refine_ratio", ct.c_double), ("profile", ct.c_int),
-                ("native_certificate", ct.c_int), ("cholesky", ct.c_int)]
+                ("native_certificate", ct.c_int), ("cholesky", ct.c_int),
+                ("precond_slices", ct.c_int)]
 
 
 class OmmInfo(ct.Structure):

@@ -210,13 +210,14 @@ void spd_factor_inverse(cudaStream_t st, int m, double* A, double* Y, double* wo
 // ------------------------------------------------------------------ float64-class (sliced) variant
 namespace {
 
-constexpr int kInvSlices = 10;
+constexpr int kInvSlices = 10;  // the most slices a product of this file takes (workspace sizing)
 
 long round8(long x) { return (x + 7) / 8 * 8; }
 
 // scratch of one stream's products
 struct Lane {
   cudaStream_t st = nullptr;
+  int slices = kInvSlices;   // fixed-point slices of every product on this lane
   double* tr0 = nullptr;     // float64 transposes
   double* tr1 = nullptr;
   __nv_bfloat16* sl0 = nullptr;  // slices of two operands
@@ -243,16 +244,17 @@ struct SlicedWork {
 void sliced_nt(Lane& L, int* err, int M, int N, int K, double alpha, const double* A, long lda, const double* B,
                long ldb, double beta, double* C, long ldc) {
   const long ld = round8(K);
-  emu::slice_rows(L.st, A, M, K, lda, kInvSlices, L.sl0, ld, nullptr);
-  const tc::Operand oa = tc::make_operand(L.sl0, M, K, ld, kInvSlices, true);
+  const int s = L.slices;
+  emu::slice_rows(L.st, A, M, K, lda, s, L.sl0, ld, nullptr);
+  const tc::Operand oa = tc::make_operand(L.sl0, M, K, ld, s, true);
   tc::Operand ob;
   if (B == A && ldb == lda && N == M) {
-    ob = tc::make_operand(L.sl0, N, K, ld, kInvSlices, false);
+    ob = tc::make_operand(L.sl0, N, K, ld, s, false);
   } else {
-    emu::slice_rows(L.st, B, N, K, ldb, kInvSlices, L.sl1, ld, nullptr);
-    ob = tc::make_operand(L.sl1, N, K, ld, kInvSlices, false);
+    emu::slice_rows(L.st, B, N, K, ldb, s, L.sl1, ld, nullptr);
+    ob = tc::make_operand(L.sl1, N, K, ld, s, false);
   }
-  emu::gemm(L.st, oa, ob, K, kInvSlices, tc::Epilogue{C, ldc, N, 0, alpha, beta, M, N, nullptr, err}, L.partial,
+  emu::gemm(L.st, oa, ob, K, s, tc::Epilogue{C, ldc, N, 0, alpha, beta, M, N, nullptr, err}, L.partial,
             L.partial_cap);
 }
 
@@ -344,7 +346,7 @@ size_t spd_inverse_sliced_workspace_bytes(int m) {
 namespace {
 // P = A^-1 (P != nullptr) and/or L, Y = L^-1 (Y_out != nullptr: A keeps L, zero above the diagonal)
 void sliced_impl(cudaStream_t st, int m, double* A, double* P, double* Y_out, void* work, int* info_dev,
-                 int* err_dev) {
+                 int* err_dev, int slices) {
   const long h = (m + 1) / 2 + NB;
   SlicedWork w;
   w.m = m;
@@ -375,6 +377,7 @@ void sliced_impl(cudaStream_t st, int m, double* A, double* P, double* Y_out, vo
   w.side.sl0 = w.main.sl1 + sl;
   w.side.sl1 = w.side.sl0 + sl;
   w.main.st = st;
+  w.main.slices = w.side.slices = std::min(std::max(slices, 2), kInvSlices);
   if (P) OMM_CUDA_TRY(cudaStreamCreateWithFlags(&w.side.st, cudaStreamNonBlocking));
   // streams and events may be released with work pending: the driver frees them once it is done
   auto cleanup = [&]() {
@@ -414,13 +417,14 @@ void sliced_impl(cudaStream_t st, int m, double* A, double* P, double* Y_out, vo
 
 }  // namespace
 
-void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work, int* info_dev, int* err_dev) {
-  sliced_impl(st, m, A, P, nullptr, work, info_dev, err_dev);
+void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work, int* info_dev, int* err_dev,
+                        int slices) {
+  sliced_impl(st, m, A, P, nullptr, work, info_dev, err_dev, slices);
 }
 
 void spd_factor_inverse_sliced(cudaStream_t st, int m, double* A, double* Y, void* work, int* info_dev,
                                int* err_dev) {
-  sliced_impl(st, m, A, nullptr, Y, work, info_dev, err_dev);
+  sliced_impl(st, m, A, nullptr, Y, work, info_dev, err_dev, kInvSlices);
 }
 
 }  // namespace omm

@@ -79,6 +79,9 @@ namespace omm {
 
 constexpr int kMixedRoundCap = 400;
 constexpr int kEmuSlices = 10;  // fixed-point slices of the float64-class refresh (about 50 bits)
+// slices of the mixed path's preconditioner inverse: P reaches the line searches only through its
+// bf16 hi/lo split (about 2^-16 of each element), and the minimum does not depend on P
+constexpr int kPrecondSlices = 7;
 
 omm_status fail(omm_status s, const std::string& msg) {
   set_last_error(msg);
@@ -286,6 +289,9 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
   if (!(o.tol_grad > 0.0)) o.tol_grad = 1e-9;
   if (!(o.e_tol >= 0.0)) o.e_tol = 0.0;
   if (!(o.refine_ratio > 0.0)) o.refine_ratio = 1e-3;
+  if (o.precond_slices <= 0) o.precond_slices = kPrecondSlices;
+  if (o.precond_slices < 2 || o.precond_slices > 10)
+    return fail(OMM_ERR_ARG, "omm_create: precond_slices must be in 2..10");
   if (o.precision != OMM_PREC_FP64 && o.precision != OMM_PREC_MIXED)
     return fail(OMM_ERR_ARG, "omm_create: unknown precision");
   const bool chol = o.cholesky != 0;
@@ -348,7 +354,7 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
         OMM_CUDA_TRY(cudaMemcpyAsync(A, c->HS + mm, mm * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
       }
       OMM_CUDA_TRY(cudaEventRecord(c->ev[2], c->st));
-      if (sliced_inverse) spd_inverse_sliced(c->st, m, A, c->P, work, c->info_dev, inv_err);
+      if (sliced_inverse) spd_inverse_sliced(c->st, m, A, c->P, work, c->info_dev, inv_err, o.precond_slices);
       else spd_inverse(c->st, m, A, c->P, work, c->info_dev);
       OMM_CUDA_TRY(cudaEventRecord(c->ev[3], c->st));
     }

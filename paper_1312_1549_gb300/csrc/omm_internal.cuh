@@ -114,11 +114,13 @@ void dgemm(cudaStream_t st, int transA, int transB, int M, int N, int K, double 
 // receives 0 or the 1-based column of the first non-positive pivot.
 size_t spd_inverse_workspace(int m);
 void spd_inverse(cudaStream_t st, int m, double* A, double* P, double* work, int* info_dev);
-// The same inverse with float64-class (sliced, tensor-core) products; A is overwritten.
-// err_dev receives a nonzero code if a bounded wait of a tensor-core GEMM expired.
+// The same inverse with sliced tensor-core products (`slices` fixed-point slices of 5 bits,
+// 2..10; 10 is float64-class); A is overwritten. err_dev receives a nonzero code if a bounded
+// wait of a tensor-core GEMM expired.
 size_t spd_inverse_sliced_workspace_bytes(int m);
 long partial_capacity(int m);  // chunk-sum scratch (doubles) of the sliced products of an m x m inverse
-void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work, int* info_dev, int* err_dev);
+void spd_inverse_sliced(cudaStream_t st, int m, double* A, double* P, void* work, int* info_dev, int* err_dev,
+                        int slices = 10);
 // The factor alone, for the reduction to standard form: A = L L^T with L left in A (lower
 // triangle, zero above) and Y = L^-1 (lower, zero above); same workspaces as the inverses.
 void spd_factor_inverse(cudaStream_t st, int m, double* A, double* Y, double* work, int* info_dev);

@@ -47,7 +47,7 @@ class OMMSolver:
 
     def __init__(self, H, S, T, n, eta, tau, precision="fp64", stream=None, max_iter=0,
                  tol_grad=1e-9, e_tol=0.0, refine_ratio=0.0, precondition=True, check_every=0,
-                 profile=False, native_certificate=False, cholesky=False):
+                 profile=False, native_certificate=False, cholesky=False, precond_slices=0):
         lib = N.lib()
         m = int(H.shape[0])
         self.m, self.n, self.eta, self.tau = m, int(n), float(eta), float(tau)
@@ -58,7 +58,7 @@ class OMMSolver:
                          e_tol=float(e_tol), refine_ratio=float(refine_ratio),
                          profile=1 if profile else 0,
                          native_certificate=1 if native_certificate else 0,
-                         cholesky=1 if cholesky else 0)
+                         cholesky=1 if cholesky else 0, precond_slices=int(precond_slices))
         self._keep = (H, S, T)
         h = ct.c_void_p()
         tau_arg = math.inf if tau is None else float(tau)
@@ -202,7 +202,7 @@ class OMMBatch:
 
     def __init__(self, problems, precision="mixed", stream=None, max_iter=0, tol_grad=1e-9,
                  refine_ratio=0.0, precondition=True, check_every=0, profile=False,
-                 native_certificate=False, cholesky=False):
+                 native_certificate=False, cholesky=False, precond_slices=0):
         lib = N.lib()
         cnt = len(problems)
         self.count = cnt
@@ -212,7 +212,7 @@ class OMMBatch:
                          check_every=int(check_every), tol_grad=float(tol_grad), e_tol=0.0,
                          refine_ratio=float(refine_ratio), profile=1 if profile else 0,
                          native_certificate=1 if native_certificate else 0,
-                         cholesky=1 if cholesky else 0)
+                         cholesky=1 if cholesky else 0, precond_slices=int(precond_slices))
         P = ct.c_void_p * cnt
         ms = (ct.c_int * cnt)(*[s[0] for s in self.shapes])
         ns = (ct.c_int * cnt)(*[s[1] for s in self.shapes])
