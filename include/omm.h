@@ -101,7 +101,7 @@ typedef struct {
                            problem (Eq. 12 with S = I). Products as for the preconditioner:
                            float64, or float64-class slices on the mixed path. 0 (default) -> off */
   int precond_slices;   /* mixed: 5-bit fixed-point slices of the sliced tensor-core products that
-                           invert S + T/tau (2..10; 0 -> 7, about 35 bits of each row-scaled
+                           invert S + T/tau (2..10; 0 -> 5, about 25 bits of each row-scaled
                            operand). P enters the line searches only through its bf16 hi/lo split
                            (about 2^-16 of each element) and the converged point does not depend
                            on P, so the float64-class 10 slices buy nothing there; the Cholesky

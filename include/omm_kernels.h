@@ -46,6 +46,15 @@ omm_status omm_kernel_spd_inverse(int m, const double* A, double* P, int* info, 
  * Y^T Y updates beside the factorisation and is joined before the call returns. */
 omm_status omm_kernel_spd_inverse_sliced(int m, const double* A, double* P, int* info, void* stream);
 
+/* The preconditioner-grade variant the mixed solver uses by default (omm_opts.precond_slices):
+ * the same recursion with `slices` fixed-point slices per operand (2..9, 5 bits each) and the
+ * 64 x 64 diagonal blocks in float32. P enters the line searches only through its bf16 hi/lo
+ * split (about 2^-16 of each element), so an inverse to a few parts in 10^6 serves as well as a
+ * float64 one. Arguments and errors as for omm_kernel_spd_inverse_sliced; OMM_ERR_ARG for
+ * slices outside 2..9. */
+omm_status omm_kernel_spd_inverse_precond(int m, const double* A, double* P, int slices, int* info,
+                                          void* stream);
+
 /* Line minimum of the quartic a0 + a1 x + a2 x^2 + a3 x^3 + a4 x^4 (Sec. 2.3,
  * Eq. 13) as the solver takes it on the device: the first local minimum along
  * x > 0 (a1 < 0). alpha (host, 5 values), x (host) receives the step.

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "omm_kernel_dgemm": (_I, [_I, _I, _I, _I, _I, _D, _P, _L, _P, _L, _D, _P, _L, _P]),
     "omm_kernel_spd_inverse": (_I, [_I, _P, _P, ct.POINTER(_I), _P]),
     "omm_kernel_spd_inverse_sliced": (_I, [_I, _P, _P, ct.POINTER(_I), _P]),
+    "omm_kernel_spd_inverse_precond": (_I, [_I, _P, _P, _I, ct.POINTER(_I), _P]),
     "omm_kernel_gemm_tc_tiled": (_I, [_I, _I, _I, _P, _P, ct.c_double, ct.c_double, _P, _I, _I, _P]),
     "omm_kernel_gemm_tc_blocksparse": (_I, [_I, _I, _I, _P, _P, ct.c_double, ct.c_double, _P, _I, _I, _P]),
     "omm_kernel_line_minimum": (_I, [ct.POINTER(_D), ct.POINTER(_D)]),

@@ -573,7 +573,7 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
         }
         if (h.done && h.stop_reason == 2) energy_stop[i] = 1;
         last_done[i] = h.done != 0;
-        const bool native = last_done[i] && c->opts.native_certificate != 0;
+        const bool native = (last_done[i] && c->opts.native_certificate != 0) || c->emu == nullptr;
         cudaStream_t q = b->pool[todo.size() % kRefreshStreams];
         c->st = q;
         OMM_CUDA_TRY(cudaEventRecord(c->ev[0], q));
@@ -593,7 +593,7 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
         omm_ctx* c = b->ctx[i];
         Scalars& h = *c->sc_host;
         const bool certify = last_done[i] != 0;
-        const bool native = certify && c->opts.native_certificate != 0;
+        const bool native = (certify && c->opts.native_certificate != 0) || c->emu == nullptr;
         if (!native && emu_error(c->emu, b->st) != 0) {
           result[i] = OMM_ERR_TIMEOUT;
           finished[i] = 1;

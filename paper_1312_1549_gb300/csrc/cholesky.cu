@@ -38,31 +38,35 @@ constexpr int NB = 64;
 // its inverse to Linv (NB x NB, row-major, zero above the diagonal); with Pblk
 // (ld ldp) also the block Linv^T Linv (both triangles). Every division is a
 // multiplication by one reciprocal per pivot: float64 division is a long
-// instruction sequence on this GPU's narrow float64 pipe.
+// instruction sequence on this GPU's narrow float64 pipe. R is the arithmetic
+// type: double, or float for a preconditioner, which needs far less than float64
+// accuracy and which the float64 pipe (about 2 instructions per SM and clock)
+// would make the serial bottleneck of the recursive inverse.
+template <typename R>
 __global__ void __launch_bounds__(256)
 potf2_inv_kernel(double* A, long lda, int b, double* Linv, int* info, int col_offset, double* Pblk, long ldp) {
-  __shared__ double L[NB][NB + 1];
-  __shared__ double X[NB][NB + 1];
-  __shared__ double rdiag[NB];
+  __shared__ R L[NB][NB + 1];
+  __shared__ R X[NB][NB + 1];
+  __shared__ R rdiag[NB];
   const int tid = threadIdx.x;
   for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
     const int i = idx / NB, j = idx % NB;
-    L[i][j] = (i < b && j < b && j <= i) ? A[(long)i * lda + j] : 0.0;
+    L[i][j] = (i < b && j < b && j <= i) ? (R)A[(long)i * lda + j] : (R)0;
   }
   __syncthreads();
   for (int j = 0; j < b; ++j) {
     if (tid == 0) {
-      double d = L[j][j];
-      if (!(d > 0.0)) {
+      R d = L[j][j];
+      if (!(d > (R)0)) {
         atomicCAS(info, 0, col_offset + j + 1);
-        d = 1.0;
+        d = (R)1;
       }
-      const double r = sqrt(d);
+      const R r = sqrt(d);
       L[j][j] = r;
-      rdiag[j] = 1.0 / r;
+      rdiag[j] = (R)1 / r;
     }
     __syncthreads();
-    const double rj = rdiag[j];
+    const R rj = rdiag[j];
     for (int i = j + 1 + tid; i < b; i += blockDim.x) L[i][j] *= rj;
     __syncthreads();
     const int r = b - j - 1;
@@ -74,16 +78,16 @@ potf2_inv_kernel(double* A, long lda, int b, double* Linv, int* info, int col_of
   }
   for (int idx = tid; idx < b * b; idx += blockDim.x) {
     const int i = idx / b, j = idx % b;
-    A[(long)i * lda + j] = (j <= i) ? L[i][j] : 0.0;
+    A[(long)i * lda + j] = (j <= i) ? (double)L[i][j] : 0.0;
   }
   // inverse of the lower-triangular block: column c solves L x = e_c
   if (tid < NB) {
     const int c = tid;
-    for (int i = 0; i < NB; ++i) X[i][c] = 0.0;
+    for (int i = 0; i < NB; ++i) X[i][c] = (R)0;
     if (c < b) {
       X[c][c] = rdiag[c];
       for (int i = c + 1; i < b; ++i) {
-        double acc = 0.0;
+        R acc = (R)0;
         for (int k = c; k < i; ++k) acc = fma(L[i][k], X[k][c], acc);
         X[i][c] = -acc * rdiag[i];
       }
@@ -92,17 +96,17 @@ potf2_inv_kernel(double* A, long lda, int b, double* Linv, int* info, int col_of
   __syncthreads();
   for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
     const int i = idx / NB, j = idx % NB;
-    Linv[idx] = X[i][j];
+    Linv[idx] = (double)X[i][j];
   }
   if (Pblk != nullptr) {
     // (X^T X)_ij = sum_{k >= i} X_ki X_kj for j <= i, mirrored
     for (int idx = tid; idx < b * b; idx += blockDim.x) {
       const int i = idx / b, j = idx % b;
       if (j > i) continue;
-      double acc = 0.0;
+      R acc = (R)0;
       for (int k = i; k < b; ++k) acc = fma(X[k][i], X[k][j], acc);
-      Pblk[(long)i * ldp + j] = acc;
-      Pblk[(long)j * ldp + i] = acc;
+      Pblk[(long)i * ldp + j] = (double)acc;
+      Pblk[(long)j * ldp + i] = (double)acc;
     }
   }
 }
@@ -168,7 +172,7 @@ void factor_blocked(cudaStream_t st, int m, double* A, const Work& w, int* info_
     const int k = kb * NB;
     const int b = (m - k < NB) ? (m - k) : NB;
     double* Akk = A + (long)k * m + k;
-    potf2_inv_kernel<<<1, 256, 0, st>>>(Akk, m, b, w.Dinv + (long)kb * NB * NB, info_dev, k, nullptr, 0);
+    potf2_inv_kernel<double><<<1, 256, 0, st>>>(Akk, m, b, w.Dinv + (long)kb * NB * NB, info_dev, k, nullptr, 0);
     OMM_LAUNCH_CHECK();
     const int r = m - k - b;
     if (r > 0) {
@@ -261,8 +265,11 @@ void sliced_nt(Lane& L, int* err, int M, int N, int K, double alpha, const doubl
 // leaf: factor A[r0:r0+b, r0:r0+b] in place, write its inverse into Y and Y_leaf^T Y_leaf into P
 void leaf(SlicedWork& w, int r0, int b) {
   const long m = w.m;
-  potf2_inv_kernel<<<1, 256, 0, w.main.st>>>(w.A + r0 * m + r0, m, b, w.leaf, w.info, r0,
-                                             w.P ? w.P + r0 * m + r0 : nullptr, m);
+  double* pb = w.P ? w.P + r0 * m + r0 : nullptr;
+  if (w.main.slices < kInvSlices)  // a preconditioner: float32 leaves (see potf2_inv_kernel)
+    potf2_inv_kernel<float><<<1, 256, 0, w.main.st>>>(w.A + r0 * m + r0, m, b, w.leaf, w.info, r0, pb, m);
+  else
+    potf2_inv_kernel<double><<<1, 256, 0, w.main.st>>>(w.A + r0 * m + r0, m, b, w.leaf, w.info, r0, pb, m);
   OMM_LAUNCH_CHECK();
   copy_block_kernel<<<16, 256, 0, w.main.st>>>(b, w.leaf, NB, w.Y + r0 * m + r0, m);
   OMM_LAUNCH_CHECK();

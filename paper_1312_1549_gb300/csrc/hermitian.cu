@@ -116,30 +116,27 @@ void extract_matrix(cudaStream_t st, int m, const double* Ae, double* stage, dou
   OMM_CUDA_TRY(cudaMemcpyAsync(out, stage, 2L * m * m * sizeof(double), cudaMemcpyDefault, st));
 }
 
-// the embedded inputs of one instance, released after the real create copied them
+// the embedded inputs of one instance (carved from one block), released after the real create
+// copied them
 struct Embedded {
   double* stage = nullptr;
   double* H = nullptr;
   double* S = nullptr;
   double* T = nullptr;
-  void release() {
-    for (double* p : {stage, H, S, T})
-      if (p) cudaFree(p);
-    stage = H = S = T = nullptr;
-  }
 };
 
-void embed_inputs(cudaStream_t st, int m, const double* H, const double* S, const double* T, Embedded& e) {
+size_t embedded_doubles(int m, bool with_T) { return (size_t)m * m * (with_T ? 14 : 10); }
+
+void embed_inputs(cudaStream_t st, int m, const double* H, const double* S, const double* T, double* block,
+                  Embedded& e) {
   const size_t mm = (size_t)m * m;
-  alloc(&e.stage, 2 * mm);
-  alloc(&e.H, 4 * mm);
-  alloc(&e.S, 4 * mm);
+  e.stage = block;
+  e.H = block + 2 * mm;
+  e.S = block + 6 * mm;
+  e.T = T ? block + 10 * mm : nullptr;
   embed_matrix(st, m, H, e.stage, e.H);
   embed_matrix(st, m, S, e.stage, e.S);
-  if (T) {
-    alloc(&e.T, 4 * mm);
-    embed_matrix(st, m, T, e.stage, e.T);
-  }
+  if (T) embed_matrix(st, m, T, e.stage, e.T);
 }
 
 // complex-side buffers of a context made by omm_create_hermitian
@@ -192,22 +189,26 @@ omm_status omm_create_hermitian(int m, int n, const double* H, const double* S, 
     return fail(OMM_ERR_ARG, "omm_create_hermitian: the Cholesky flavour of a Hermitian problem needs OMM_PREC_FP64");
   cudaStream_t st = (cudaStream_t)stream;
   Embedded e;
+  double* block = nullptr;
   omm_status rc = OMM_OK;
+  auto release = [&]() {
+    cudaStreamSynchronize(st);
+    if (block) cudaFree(block);
+    block = nullptr;
+  };
   try {
-    embed_inputs(st, m, H, S, T, e);
+    alloc(&block, embedded_doubles(m, T != nullptr));
+    embed_inputs(st, m, H, S, T, block, e);
     rc = omm_create(2 * m, 2 * n, e.H, e.S, e.T, eta, tau, opts, stream, out);
-    OMM_CUDA_TRY(cudaStreamSynchronize(st));
-    e.release();
+    release();
     if (rc != OMM_OK) return rc;
     attach(*out, m, n);
   } catch (const std::bad_alloc&) {
-    cudaStreamSynchronize(st);
-    e.release();
+    release();
     if (*out) { omm_free(*out); *out = nullptr; }
     return fail(OMM_ERR_OOM, "omm_create_hermitian: device allocation failed");
   } catch (const CudaError& err) {
-    cudaStreamSynchronize(st);
-    e.release();
+    release();
     if (*out) { omm_free(*out); *out = nullptr; }
     return fail(OMM_ERR_CUDA, std::string("omm_create_hermitian: ") + err.what + ": " + cudaGetErrorString(err.err));
   }
@@ -318,14 +319,19 @@ omm_status omm_create_hermitian_batched(int count, const int* m, const int* n, c
   std::vector<Embedded> e(count);
   std::vector<int> m2(count), n2(count);
   std::vector<const double*> He(count), Se(count), Te(count);
+  std::vector<size_t> offset(count + 1, 0);
+  for (int i = 0; i < count; ++i) offset[i + 1] = offset[i] + embedded_doubles(m[i], T && T[i]);
+  double* block = nullptr;  // every instance's embedded inputs: one allocation, one release
   omm_status rc = OMM_OK;
   auto release = [&]() {
     cudaStreamSynchronize(st);
-    for (Embedded& x : e) x.release();
+    if (block) cudaFree(block);
+    block = nullptr;
   };
   try {
+    alloc(&block, offset[count]);
     for (int i = 0; i < count; ++i) {
-      embed_inputs(st, m[i], H[i], S[i], T ? T[i] : nullptr, e[i]);
+      embed_inputs(st, m[i], H[i], S[i], T ? T[i] : nullptr, block + offset[i], e[i]);
       m2[i] = 2 * m[i];
       n2[i] = 2 * n[i];
       He[i] = e[i].H;

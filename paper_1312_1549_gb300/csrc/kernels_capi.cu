@@ -73,9 +73,11 @@ omm_status omm_kernel_spd_inverse(int m, const double* A, double* P, int* info, 
   return rc;
 }
 
-omm_status omm_kernel_spd_inverse_sliced(int m, const double* A, double* P, int* info, void* stream) {
+namespace {
+omm_status spd_inverse_sliced_impl(const char* who, int m, const double* A, double* P, int slices, int* info,
+                                   void* stream) {
   if (m <= 0 || !A || !P) {
-    set_last_error("omm_kernel_spd_inverse_sliced: invalid argument");
+    set_last_error(std::string(who) + ": invalid argument");
     return OMM_ERR_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -90,25 +92,38 @@ omm_status omm_kernel_spd_inverse_sliced(int m, const double* A, double* P, int*
     OMM_CUDA_TRY(cudaMalloc((void**)&flags, 2 * sizeof(int)));
     OMM_CUDA_TRY(cudaMemsetAsync(flags, 0, 2 * sizeof(int), st));
     OMM_CUDA_TRY(cudaMemcpyAsync(W, A, mm * sizeof(double), cudaMemcpyDefault, st));
-    spd_inverse_sliced(st, m, W, P, work, flags, flags + 1);
+    spd_inverse_sliced(st, m, W, P, work, flags, flags + 1, slices);
     int h[2] = {0, 0};
     OMM_CUDA_TRY(cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
     if (info) *info = h[0];
     if (h[1] != 0) {
-      set_last_error("omm_kernel_spd_inverse_sliced: a bounded device wait expired");
+      set_last_error(std::string(who) + ": a bounded device wait expired");
       rc = OMM_ERR_TIMEOUT;
     } else if (h[0] != 0) {
-      set_last_error("omm_kernel_spd_inverse_sliced: not positive definite");
+      set_last_error(std::string(who) + ": not positive definite");
       rc = OMM_ERR_NOT_SPD;
     }
   } catch (const CudaError& e) {
-    rc = cuda_fail("omm_kernel_spd_inverse_sliced", e);
+    rc = cuda_fail(who, e);
   }
   if (W) cudaFree(W);
   if (work) cudaFree(work);
   if (flags) cudaFree(flags);
   return rc;
+}
+}  // namespace
+
+omm_status omm_kernel_spd_inverse_sliced(int m, const double* A, double* P, int* info, void* stream) {
+  return spd_inverse_sliced_impl("omm_kernel_spd_inverse_sliced", m, A, P, 10, info, stream);
+}
+
+omm_status omm_kernel_spd_inverse_precond(int m, const double* A, double* P, int slices, int* info, void* stream) {
+  if (slices < 2 || slices > 9) {
+    set_last_error("omm_kernel_spd_inverse_precond: slices must be in 2..9");
+    return OMM_ERR_ARG;
+  }
+  return spd_inverse_sliced_impl("omm_kernel_spd_inverse_precond", m, A, P, slices, info, stream);
 }
 
 omm_status omm_kernel_line_minimum(const double* alpha, double* x) {

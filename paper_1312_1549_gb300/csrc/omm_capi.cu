@@ -81,7 +81,13 @@ constexpr int kMixedRoundCap = 400;
 constexpr int kEmuSlices = 10;  // fixed-point slices of the float64-class refresh (about 50 bits)
 // slices of the mixed path's preconditioner inverse: P reaches the line searches only through its
 // bf16 hi/lo split (about 2^-16 of each element), and the minimum does not depend on P
-constexpr int kPrecondSlices = 7;
+constexpr int kPrecondSlices = 5;
+// Below these sizes the native float64 routines are cheaper than the sliced tensor-core ones,
+// whose many small launches are latency-bound there: the inverse (or factor) of an m x m matrix
+// with m < kSlicedInverseMin, and the state recompute (refresh, certificate, D) of a problem with
+// fewer than kSlicedStateMinFlop flops per recompute (4 m^2 n + 8 m n^2).
+constexpr int kSlicedInverseMin = 2048;
+constexpr double kSlicedStateMinFlop = 5e8;
 
 omm_status fail(omm_status s, const std::string& msg) {
   set_last_error(msg);
@@ -100,6 +106,21 @@ void dev_alloc(T** p, size_t count) {
 
 void dev_free(void* p) {
   if (p) cudaFree(p);
+}
+
+// stream-ordered temporaries: their release does not wait for the whole device (cudaFree does),
+// which matters when many contexts are created side by side
+template <typename T>
+void tmp_alloc(T** p, size_t count, cudaStream_t st) {
+  if (cudaMallocAsync((void**)p, count * sizeof(T), st) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    throw std::bad_alloc();
+  }
+}
+
+void tmp_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
 }
 
 bool is_device_ptr(const void* p) {
@@ -325,10 +346,10 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     copy_in(c->HS, H, mm, c->st);
     copy_in(c->HS + mm, S, mm, c->st);
     // the mixed path factors with float64-class tensor-core products, the float64 path natively
-    const bool sliced_inverse = o.precision == OMM_PREC_MIXED;
+    const bool sliced_inverse = o.precision == OMM_PREC_MIXED && m >= kSlicedInverseMin;
     if (chol) {
       // standard form (Sec. 2.4): H_r = L^-1 H L^-T in the H slot, the identity in the S slot
-      dev_alloc(&A, mm);
+      tmp_alloc(&A, mm, c->st);
       copy_in(A, S, mm, c->st);
       OMM_CUDA_TRY(cudaEventRecord(c->ev[2], c->st));
       c->red = reduction_create(c->st, m, sliced_inverse, A, c->info_dev);
@@ -339,13 +360,13 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     launch_axpby_shift(c->st, mm, c->HS, c->HS + mm, eta, c->HS);
     if (precond) {
       dev_alloc(&c->P, mm);
-      dev_alloc(&A, mm);
+      tmp_alloc(&A, mm, c->st);
       if (sliced_inverse) {
-        dev_alloc(&work, (spd_inverse_sliced_workspace_bytes(m) + sizeof(double) - 1) / sizeof(double));
-        dev_alloc(&inv_err, 1);
+        tmp_alloc(&work, (spd_inverse_sliced_workspace_bytes(m) + sizeof(double) - 1) / sizeof(double), c->st);
+        tmp_alloc(&inv_err, 1, c->st);
         OMM_CUDA_TRY(cudaMemsetAsync(inv_err, 0, sizeof(int), c->st));
       } else {
-        dev_alloc(&work, spd_inverse_workspace(m));
+        tmp_alloc(&work, spd_inverse_workspace(m), c->st);
       }
       if (std::isfinite(tau)) {
         copy_in(A, T, mm, c->st);
@@ -371,7 +392,8 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     dev_alloc(&c->part2, (size_t)traces_blocks(n) * kNumTraces);
     if (o.precision == OMM_PREC_MIXED) {
       c->mixed = mixed_create(c->st, m, n, c->HS, c->P);
-      c->emu = emu_create(c->st, m, n, kEmuSlices, c->HS);
+      if (4.0 * m * (double)m * n + 8.0 * m * (double)n * n >= kSlicedStateMinFlop)
+        c->emu = emu_create(c->st, m, n, kEmuSlices, c->HS);
     }
     OMM_CUDA_TRY(cudaEventRecord(c->ev[1], c->st));
     int info = 0, ierr = 0;
@@ -389,9 +411,9 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     }
     c->ms_precond = (precond || chol) ? elapsed(c->ev[2], c->ev[3]) : 0.0;
     if (c->red && reduction_error(c->red, c->st) != 0) ierr = 1;
-    dev_free(A);
-    dev_free(work);
-    dev_free(inv_err);
+    tmp_free(A, c->st);
+    tmp_free(work, c->st);
+    tmp_free(inv_err, c->st);
     A = work = nullptr;
     inv_err = nullptr;
     if (ierr != 0) {
@@ -405,16 +427,16 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     }
   } catch (const std::bad_alloc&) {
     emu::set_profiler(nullptr);
-    dev_free(A);
-    dev_free(work);
-    dev_free(inv_err);
+    tmp_free(A, c->st);
+    tmp_free(work, c->st);
+    tmp_free(inv_err, c->st);
     destroy(c);
     return fail(OMM_ERR_OOM, "omm_create: device allocation failed");
   } catch (const CudaError& e) {
     emu::set_profiler(nullptr);
-    dev_free(A);
-    dev_free(work);
-    dev_free(inv_err);
+    tmp_free(A, c->st);
+    tmp_free(work, c->st);
+    tmp_free(inv_err, c->st);
     destroy(c);
     return fail(OMM_ERR_CUDA, std::string("omm_create: ") + e.what + ": " + cudaGetErrorString(e.err));
   }
@@ -484,9 +506,9 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
       // the mixed path starts from a tensor-core state; every later state is float64
       // mixed path: a tensor-core first state, float64-class (sliced) refreshes while the
       // device asks for them, and a native float64 state once it reports convergence
-      const bool emu_certify = mixed && c->opts.native_certificate == 0;
+      const bool emu_certify = mixed && c->emu && c->opts.native_certificate == 0;
       const bool tc_state = mixed && round == 0;
-      const bool emu_state = mixed && round > 0 && (!last_round_done || emu_certify);
+      const bool emu_state = mixed && c->emu && round > 0 && (!last_round_done || emu_certify);
       OMM_CUDA_TRY(cudaEventRecord(c->ev[0], c->st));
       if (tc_state) {
         mixed_recompute_state(c->mixed, c->st, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);

@@ -845,17 +845,17 @@ void block_lists(cudaStream_t st, const double* B, long rows, long cols, long ld
   const long nrb128 = (rows + 127) / 128;
   unsigned char* occ = nullptr;
   std::vector<unsigned char> h(nrb128 * nkb);
-  OMM_CUDA_TRY(cudaMalloc((void**)&occ, h.size()));
+  OMM_CUDA_TRY(cudaMallocAsync((void**)&occ, h.size(), st));
   try {
     occupancy_kernel<<<(unsigned)(nrb128 * nkb), 256, 0, st>>>(B, rows, cols, ld, nkb, occ);
     OMM_LAUNCH_CHECK();
     OMM_CUDA_TRY(cudaMemcpyAsync(h.data(), occ, h.size(), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
   } catch (...) {
-    cudaFree(occ);
+    cudaFreeAsync(occ, st);
     throw;
   }
-  cudaFree(occ);
+  cudaFreeAsync(occ, st);
   const int per = bn / 128;  // 128-row blocks per row block of bn
   const int nblocks = (int)((rows + bn - 1) / bn);
   std::vector<int> off(nblocks + 1, 0), idx;

@@ -132,12 +132,17 @@ def dgemm(transA, transB, A, B, C, alpha=1.0, beta=0.0, stream=None):
     return C
 
 
-def spd_inverse(A, P=None, stream=None, sliced=False):
-    """P = A^-1 of an SPD matrix: float64 Cholesky, or (sliced=True) float64-class tensor-core products."""
+def spd_inverse(A, P=None, stream=None, sliced=False, slices=None):
+    """P = A^-1 of an SPD matrix: float64 Cholesky, or (sliced=True) float64-class tensor-core products,
+    or (slices=2..9) the preconditioner-grade sliced inverse with float32 diagonal blocks."""
     m = A.shape[0]
     if P is None:
         P = torch.empty_like(A)
     info = ct.c_int(0)
+    if slices is not None:
+        N.check(N.lib().omm_kernel_spd_inverse_precond(m, _ptr(A), _ptr(P), int(slices), ct.byref(info),
+                                                       _stream_handle(stream)), "omm_kernel_spd_inverse_precond")
+        return P
     fn = "omm_kernel_spd_inverse_sliced" if sliced else "omm_kernel_spd_inverse"
     N.check(getattr(N.lib(), fn)(m, _ptr(A), _ptr(P), ct.byref(info), _stream_handle(stream)), fn)
     return P

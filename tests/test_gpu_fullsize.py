@@ -96,6 +96,13 @@ def test_sliced_preconditioner_inverse_at_si512():
     R = P_sliced[rows] @ A
     R[torch.arange(128, device=R.device), rows] -= 1.0
     assert R.abs().max().item() <= 1e-11
+    # the preconditioner-grade inverse the mixed solver takes by default (5 slices, float32 leaves)
+    P_pre = S.spd_inverse(A, slices=5)
+    assert torch.equal(P_pre, P_pre.T)
+    assert (P_pre - P_native).abs().max().item() <= 1e-4 * scale
+    R = P_pre[rows] @ A
+    R[torch.arange(128, device=R.device), rows] -= 1.0
+    assert R.abs().max().item() <= 1e-4
 
 
 def test_water256_autograd_central_differences():

@@ -166,6 +166,33 @@ def test_spd_inverse_sliced_preconditioner_matches_oracle(S):
     assert np.abs(P - P_ref).max() <= 1e-11 * np.abs(P_ref).max()
 
 
+# The preconditioner-grade inverse (the mixed solver's default): fewer slices and float32 leaves.
+# P reaches the line searches only through its bf16 hi/lo split (about 2^-16 of each element);
+# the residual bound below (5 slices, about 2^-24 of each row-scaled operand, condition numbers
+# near 10) keeps P well inside that.
+@pytest.mark.parametrize("m", [5, 65, 200, 1000, 2500])
+@pytest.mark.parametrize("slices", [5, 7])
+def test_spd_inverse_precond(S, m, slices):
+    rng = np.random.default_rng(m)
+    X = rng.normal(size=(m, m))
+    A = X @ X.T / m + 0.5 * np.eye(m)
+    P = S.spd_inverse(dev(A), slices=slices).cpu().numpy()
+    assert np.array_equal(P, P.T)
+    assert np.abs(P @ A - np.eye(m)).max() <= 1e-5
+
+
+def test_spd_inverse_precond_rejects_bad_arguments(S):
+    from paper_1312_1549_gb300 import _native as N
+    A = np.eye(200)
+    A[150, 150] = -1.0
+    with pytest.raises(N.OMMError) as e:
+        S.spd_inverse(dev(A), slices=5)
+    assert e.value.status == 2
+    with pytest.raises(N.OMMError) as e:
+        S.spd_inverse(dev(np.eye(10)), slices=10)
+    assert e.value.status == 1
+
+
 # ---------------------------------------------------------------- block-sparse operator products
 @pytest.mark.parametrize("tile_n", [256, 128])
 @pytest.mark.parametrize("M,N,K", [(256, 1024, 640), (130, 700, 333), (1024, 2048, 1024)])
