@@ -579,8 +579,7 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
         OMM_CUDA_TRY(cudaEventRecord(c->ev[0], q));
         project_real_form(c, q);
         if (native) recompute_state_fp64(c);
-        else emu_recompute_state(c->emu, q, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2,
-                                 last_done[i] ? 0 : kRefreshSlices);  // certificate or refresh
+        else emu_recompute_state(c->emu, q, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
         OMM_CUDA_TRY(cudaEventRecord(c->ev[1], q));
         c->st = b->st;
         todo.push_back(i);

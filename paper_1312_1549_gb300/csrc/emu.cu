@@ -251,18 +251,16 @@ int emu_error(EmuState* es, cudaStream_t st) {
 
 // HC, SC, S_W, H_W, E~, G and max|G| from C with float64-class tensor-core products.
 void emu_recompute_state(EmuState* es, cudaStream_t st, Scalars* sc, const double* C, double* Y4,
-                         double* SWHW, double* G, double* part, double* part2, int pairs_slices) {
+                         double* SWHW, double* G, double* part, double* part2) {
   const int m = es->m, n = es->n, s = es->s;
-  // the operands keep all s slices; the products sum the pairs of the leading ps of them
-  const int ps = (pairs_slices > 0 && pairs_slices < s) ? pairs_slices : s;
   const long nm = (long)n * m;
   emu::slice_rows(st, C, n, m, m, s, es->Cs, es->ldm, nullptr);
   // [HC; SC] (n x m layout) = C [H~; S]^T
-  emu::gemm(st, es->opC, es->opHS, m, ps, tc::Epilogue{Y4, m, m, nm, 1.0, 0.0, n, 2 * m, nullptr, es->err},
+  emu::gemm(st, es->opC, es->opHS, m, s, tc::Epilogue{Y4, m, m, nm, 1.0, 0.0, n, 2 * m, nullptr, es->err},
             es->partial, es->partial_cap, &es->hs_blocks);
   emu::slice_rows(st, Y4, 2L * n, m, m, s, es->Ys, es->ldm, nullptr);
   // [S_W | H_W] = C [SC; HC]^T
-  emu::gemm(st, es->opC, es->opY, m, ps,
+  emu::gemm(st, es->opC, es->opY, m, s,
             tc::Epilogue{SWHW + n, 2L * n, n, -(long)n, 1.0, 0.0, n, 2 * n, nullptr, es->err}, es->partial,
             es->partial_cap);
   launch_functional(st, n, SWHW, part2);
@@ -272,7 +270,7 @@ void emu_recompute_state(EmuState* es, cudaStream_t st, Scalars* sc, const doubl
   emu::transpose(st, Y4, 2L * n, m, m, es->T64, 2L * n);
   emu::slice_rows(st, es->T64, m, 2L * n, 2L * n, s, es->YTs, es->ld2n, nullptr);
   launch_scale_copy(st, nm, Y4, 8.0, G, nullptr);
-  emu::gemm(st, es->opW, es->opYT, 2 * n, ps, tc::Epilogue{G, m, m, 0, -4.0, 1.0, n, m, nullptr, es->err},
+  emu::gemm(st, es->opW, es->opYT, 2 * n, s, tc::Epilogue{G, m, m, 0, -4.0, 1.0, n, m, nullptr, es->err},
             es->partial, es->partial_cap);
   launch_gmax(st, nm, G, part);
   launch_finish_gmax(st, sc, part);

@@ -20,10 +20,6 @@ void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, in
           double* partial = nullptr, long partial_capacity = 0, const tc::BlockLists* sparse = nullptr);
 }  // namespace emu
 
-// slices whose pairs a refresh between mixed rounds sums (about 2^-40 of each row-scaled operand,
-// far below the 1e-9 gradient tolerance); the certificate takes all of the state's slices
-constexpr int kRefreshSlices = 8;
-
 struct EmuState;
 EmuState* emu_create(cudaStream_t st, int m, int n, int slices, const double* HS);
 void emu_update_H(EmuState* es, cudaStream_t st, const double* HS);
@@ -33,9 +29,7 @@ int emu_error(EmuState* es, cudaStream_t st);
 void emu_density(EmuState* es, cudaStream_t st, const double* C, const double* SWHW, double* D);
 // out = -(2 C^T H~_W C + eta D) from out = D; call right after emu_density (it reuses the sliced C^T)
 void emu_minus_edm(EmuState* es, cudaStream_t st, const double* SWHW, double eta, double* out);
-// pairs: slices whose products are summed (0 -> all of the state's slices; a refresh between
-// rounds takes fewer than the certificate: it only resets the mixed path's reference point)
 void emu_recompute_state(EmuState* es, cudaStream_t st, Scalars* sc, const double* C, double* Y4,
-                         double* SWHW, double* G, double* part, double* part2, int pairs_slices = 0);
+                         double* SWHW, double* G, double* part, double* part2);
 
 }  // namespace omm

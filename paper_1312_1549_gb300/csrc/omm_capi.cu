@@ -515,9 +515,8 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
         flop_tc += 3.0 * per_state;
       } else if (emu_state) {
         project_real_form(c, c->st);
-        const int es = last_round_done ? kEmuSlices : kRefreshSlices;  // certificate or refresh
-        emu_recompute_state(c->emu, c->st, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2, es);
-        flop_tc += 0.5 * es * (es + 1) * per_state;
+        emu_recompute_state(c->emu, c->st, c->sc, c->C, c->Y4, c->SWHW, c->G, c->part, c->part2);
+        flop_tc += 0.5 * kEmuSlices * (kEmuSlices + 1) * per_state;
         if (emu_error(c->emu, c->st) != 0) {
           result = OMM_ERR_TIMEOUT;
           break;
