@@ -69,10 +69,12 @@ typedef enum {
   OMM_PREC_FP64 = 0,   /* every contraction in float64 */
   OMM_PREC_MIXED = 1   /* bulk contractions on the BF16 tensor cores as 3-term split products
                           with FP32 accumulation, state and every scalar in float64; the
-                          preconditioner inverse, the refreshes of the state and the
-                          certificate of the final point use float64-class products (fixed-point
-                          slices on the tensor cores, the Ozaki scheme; native float64 for the
-                          certificate with native_certificate = 1) */
+                          refreshes of the state and the certificate of the final point use
+                          float64-class products (fixed-point slices on the tensor cores, the
+                          Ozaki scheme; native float64 for the certificate with
+                          native_certificate = 1, and for problems small enough that native
+                          float64 is cheaper); the preconditioner inverse uses the same slicing
+                          at preconditioner grade (precond_slices) */
 } omm_precision;
 
 /* Options. A zero-filled struct (or NULL) selects every default. */
@@ -129,8 +131,9 @@ typedef struct {
   double main_gemm_flop;     /* with opts.profile: flops they issued (tensor-core flops when mixed) */
   double ms_certify;         /* native float64 state recomputes (part of ms_refine) */
   double ms_precond;         /* the Cholesky inverse P = (S + T/tau)^-1 (part of ms_setup): float64,
-                                or float64-class sliced products on the mixed path; with
-                                opts.cholesky the factor L, L^-1 and H_r = L^-1 H L^-T instead */
+                                or preconditioner-grade sliced products on the mixed path (m >=
+                                2048); with opts.cholesky the factor L, L^-1 and H_r = L^-1 H L^-T
+                                instead */
   int tile_width[4];         /* mixed: output tile width (256 or 128 columns) the autotuner chose for
                                 the P G, [H D; S D], projection and gradient GEMMs (0: not run) */
   double ms_autotune;        /* time the autotuner spent timing candidates (0 when cached) */
