@@ -287,3 +287,46 @@ def test_cholesky_flavour_si64_workload():
     ex = exact.exact_minimum(p.H, p.S, p.n)
     assert abs(r["E"] - ex["E"]) / abs(ex["E"]) < 1e-12
     assert np.abs(r["D"] - ex["D"]).max() < 1e-7
+
+
+# ---------------------------------------------------------------- degenerate and extreme cases
+def test_single_orbital_and_n_equals_m_minus_one():
+    """n = 1 (E = 2 eps_1) and n = m - 1 (all but the highest state occupied) reach the brute force."""
+    for (m, n, seed) in [(9, 1, 31), (9, 8, 32), (2, 1, 33)]:
+        H, S, T, eta, C0, w = tiny_problem(m, n, seed)
+        r = omm.solve(H, S, T, eta, 1.3, C0, tol_grad=1e-11, max_iter=5000)
+        assert r["status"] == omm.STATUS_OK, (m, n)
+        we, X = jacobi.generalized_eigh(H, S)
+        assert r["E"] == pytest.approx(2.0 * float(np.sum(we[:n])), rel=1e-12, abs=1e-12)
+        occ = X[:, :n]
+        assert np.abs(r["D"] - 2.0 * occ @ occ.T).max() < 1e-9
+
+
+def test_degenerate_occupied_levels():
+    """Equal eigenvalues inside the occupied set: the orbitals are not unique, D and E are."""
+    m, n = 14, 5
+    rng = np.random.default_rng(40)
+    S = np.eye(m) + 0.05 * np.diag(rng.uniform(size=m))
+    L = np.linalg.cholesky(S)
+    Q, _ = np.linalg.qr(rng.normal(size=(m, m)))
+    X = np.linalg.solve(L.T, Q)
+    w = np.sort(rng.uniform(0.0, 1.0, size=m)) + 0.5
+    w[:3] = -0.7                                  # a threefold degenerate level in the occupied set
+    w[3:5] = -0.2                                 # and a twofold one
+    H = S @ X @ np.diag(w) @ X.T @ S
+    H = 0.5 * (H + H.T)
+    C0 = rng.normal(0.0, 0.1, size=(n, m))
+    r = omm.solve(H, S, None, 0.1, 1.0, C0, tol_grad=1e-11, max_iter=5000, precondition=False)
+    assert r["status"] == omm.STATUS_OK
+    assert r["E"] == pytest.approx(2.0 * (3 * -0.7 + 2 * -0.2), rel=1e-12)
+    occ = X[:, :n]
+    assert np.abs(r["D"] - 2.0 * occ @ occ.T).max() < 1e-9
+
+
+def test_start_at_the_minimum_takes_no_line_search():
+    """From the converged C the gradient is already below the tolerance: zero line searches."""
+    H, S, T, eta, C0, w = tiny_problem(16, 5, 41)
+    r = omm.solve(H, S, T, eta, 1.3, C0, tol_grad=1e-11, max_iter=5000)
+    r2 = omm.solve(H, S, T, eta, 1.3, r["C"], tol_grad=1e-10, C_is_mn=True)
+    assert r2["iters"] == 0 and r2["status"] == omm.STATUS_OK
+    assert r2["E"] == pytest.approx(r["E"], rel=1e-14)
