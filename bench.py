@@ -2,8 +2,8 @@
 """Time-to-solution of the OMM solve on GB300 (and its oracle on the host cores).
 
 One step = one whole solve of the Si512 DZP-like workload (m = 6656 basis
-functions, n = 1024 Wannier functions): omm_create (shift, float64-class Cholesky
-inverse of S + T/tau, operand splits) + omm_solve to max|G| < 1e-9
+functions, n = 1024 Wannier functions): omm_create (shift, sliced tensor-core Cholesky
+inverse of S + T/tau at preconditioner grade, operand splits) + omm_solve to max|G| < 1e-9
 (certified with float64-class products) + the density matrix D. Inputs are
 resident in HBM when the timed region starts; H, S, T (354 MB each) are larger
 than L2.
@@ -590,8 +590,8 @@ def main():
     if mixed and sl_ms > 0:
         a = sl_flop / (sl_ms * 1e-3) / 1e12
         roofline_sliced = {"bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
-                           "traffic": None, "kernel": "gemm_persistent_one_kernel (tcgen05, sliced float64-class "
-                           "products: inverse, refreshes, certificate, D)", "launches": sl_n,
+                           "traffic": None, "kernel": "gemm_persistent_one_kernel (tcgen05, sliced products: "
+                           "preconditioner inverse (5 slices), refreshes and certificate (10), D (8))", "launches": sl_n,
                            "avg_launch_ms": sl_ms / max(sl_n, 1), "ms_per_solve": sl_ms / len(infos)}
     out = {"metric": METRIC, "value": ms * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",

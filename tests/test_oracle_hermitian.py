@@ -164,3 +164,17 @@ def test_monkhorst_pack_weights():
     assert len(k) == 365 and w.sum() == pytest.approx(1.0, abs=1e-14)
     k, w = monkhorst_pack((4, 4, 4), time_reversal=False)
     assert len(k) == 64 and np.all(w == 1.0 / 64)
+
+
+def test_mp_grid_problems_are_well_posed():
+    """Every problem of the 9 x 9 x 9 grid: Hermitian, S(k) positive definite, and the one eta lies
+    above its n-th and below its (n+1)-th level (Sec. 2.2), so each OMM minimum is its band energy."""
+    import scipy.linalg
+    from synth.kpoints import silicon_mp_grid
+    p = silicon_mp_grid((9, 9, 9))
+    assert len(p.H) == 365 and sum(p.meta["weights"]) == pytest.approx(1.0, abs=1e-14)
+    for h, s in zip(p.H, p.S):
+        assert np.abs(h - h.conj().T).max() == 0.0 and np.abs(s - s.conj().T).max() == 0.0
+        assert np.linalg.eigvalsh(s).min() > 1e-3
+        e = scipy.linalg.eigh(h, s, eigvals_only=True, subset_by_index=[p.n - 1, p.n])
+        assert e[0] < p.eta < e[1]
