@@ -117,3 +117,19 @@ def test_real_entry_points_reject_hermitian_context(S, grid):
         rc = N.lib().omm_solve(s._h, ct.c_void_p(C0.data_ptr()), None, ct.byref(E), None, None)
         assert rc == 1
         assert N.lib().omm_backward(s._h, None, None) == 1
+
+
+def test_neighbouring_k_point_start(S, grid):
+    """Sec. 3.3: the converged C of one k point as the start of its neighbour: fewer line searches
+    than from the seeded start, the neighbour's own minimum (float64 path)."""
+    from oracle import hermitian
+    p = grid
+    a, b = 1, 2                                        # neighbours along the third axis of the grid
+    with S.OMMHermitian(zdev(p.H[a]), zdev(p.S[a]), zdev(p.T[a]), p.n, p.eta, p.tau) as s:
+        Ca, _, _, _ = s.solve(zdev(p.C0[a]))
+    with S.OMMHermitian(zdev(p.H[b]), zdev(p.S[b]), zdev(p.T[b]), p.n, p.eta, p.tau) as s:
+        _, E_cold, _, i_cold = s.solve(zdev(p.C0[b]))
+        _, E_warm, _, i_warm = s.solve(Ca)
+    ex = hermitian.exact_minimum(p.H[b], p.S[b], p.n)
+    assert abs(E_warm - ex["E"]) / abs(ex["E"]) <= 1e-10
+    assert i_warm["iterations"] < i_cold["iterations"], (i_warm["iterations"], i_cold["iterations"])

@@ -178,3 +178,22 @@ def test_mp_grid_problems_are_well_posed():
         assert np.linalg.eigvalsh(s).min() > 1e-3
         e = scipy.linalg.eigh(h, s, eigvals_only=True, subset_by_index=[p.n - 1, p.n])
         assert e[0] < p.eta < e[1]
+
+
+def test_neighbouring_k_point_start_saves_line_searches():
+    """Sec. 3.3: solving the k points one after another, each from its neighbour's C, reuses
+    information: fewer line searches than from the seeded start, the same minimum."""
+    from synth.kpoints import silicon_mp_grid
+    p = silicon_mp_grid((9, 9, 9))
+    ks = np.array(p.k)
+    path = sorted((i for i, k in enumerate(ks) if abs(k[1] - ks[0][1]) < 1e-12 and abs(k[2] - ks[0][2]) < 1e-12),
+                  key=lambda i: ks[i][0])
+    prev = None
+    for i in path:
+        cold = hermitian.solve(p.H[i], p.S[i], p.T[i], p.eta, p.tau, p.C0[i], tol_grad=1e-9, want_matrices=False)
+        if prev is not None:
+            warm = hermitian.solve(p.H[i], p.S[i], p.T[i], p.eta, p.tau, prev.T.copy(), tol_grad=1e-9,
+                                   want_matrices=False)
+            assert warm["iters"] < cold["iters"], (i, warm["iters"], cold["iters"])
+            assert abs(warm["E"] - cold["E"]) <= 1e-12 * abs(cold["E"])
+        prev = cold["C"]
