@@ -167,3 +167,77 @@ def silicon_mp_grid(q=(9, 9, 9), basis="DZP", seed=0, time_reversal=True) -> KPr
             "weights": wk.tolist(), "homo": homo, "lumo": lumo, "gap": lumo - homo, "atoms_per_cell": 8}
     return KProblem(name=f"si8_{basis}_mp{q[0]}x{q[1]}x{q[2]}", m=m, n=n, k=ks, H=Hk, S=Sk, T=Tk,
                     eta=float(eta), tau=TAU_10RY, C0=C0, seed=seed, meta=meta)
+
+
+def hexagonal_mp(q1, q2, time_reversal=True):
+    """Monkhorst-Pack grid q1 x q2 of the hexagonal cell (reciprocal vectors of a1 = a(1, 0),
+    a2 = a(1/2, sqrt 3/2)): (k vectors, weights summing to 1)."""
+    from .systems import A_GRAPHENE
+    a = A_GRAPHENE
+    b1 = 2.0 * np.pi / a * np.array([1.0, -1.0 / np.sqrt(3.0), 0.0])
+    b2 = 2.0 * np.pi / a * np.array([0.0, 2.0 / np.sqrt(3.0), 0.0])
+    u1 = (2.0 * np.arange(1, q1 + 1) - q1 - 1) / (2.0 * q1)
+    u2 = (2.0 * np.arange(1, q2 + 1) - q2 - 1) / (2.0 * q2)
+    frac = np.array([(x, y) for x in u1 for y in u2])
+    w = np.full(len(frac), 1.0 / len(frac))
+    if time_reversal:
+        key = {tuple(np.round(f, 12)): i for i, f in enumerate(frac)}
+        keep, wk = [], []
+        for i, f in enumerate(frac):
+            j = key.get(tuple(np.round(-f, 12)))
+            if j is None or j > i or j == i:
+                keep.append(i)
+                wk.append(w[i] * (2.0 if (j is not None and j != i) else 1.0))
+        frac, w = frac[keep], np.array(wk)
+    return frac[:, :1] * b1[None, :] + frac[:, 1:] * b2[None, :], w
+
+
+def graphene_mp_grid(q=(19, 19), basis="DZP", seed=0, time_reversal=True, sc=(9, 6)) -> KProblem:
+    """One graphene layer on a q1 x q2 Monkhorst-Pack grid (the paper's second k-point test,
+    Sec. 3.3: 19 x 19 x 1, DZP m = 26, n = 4). h(R) is read from an sc rectangular supercell
+    (9 x 6: 42 x 48 bohr in the layer, 41 bohr of vacuum: no element mixes periodic images). This
+    model does not reproduce graphene's Dirac points: its fourth and fifth bands keep a gap of at
+    least 0.10 Ha over the grid, so one eta above every occupied level fits (when a grid has no
+    common gap, eta is nan and meta holds an eta per k point, inside each one's gap)."""
+    from .systems import carbon_model, graphene_supercell
+    streams = _streams(seed)
+    model = carbon_model(basis)
+    norb = model.species["C"].norb
+    m = 2 * norb
+    symbols, pos, cell, sub = graphene_supercell(*sc)
+    ncell = len(pos) // 2
+    jitter_cell = streams[1].normal(0.0, JITTER_SIGMA, size=m)
+    jitter = np.concatenate([jitter_cell[s * norb:(s + 1) * norb] for s in sub])
+    S_sc, T_sc, H_sc, _ = build_matrices(model, symbols, pos, cell, jitter)
+    nat = len(symbols)
+    d = pos[None, :, :] - pos[:2, None, :]
+    d -= cell * np.round(d / cell)
+    R = pos[:2, None, :] + d - pos[sub][None, :, :]                  # (2, nat, 3) lattice translations
+    ks, wk = hexagonal_mp(q[0], q[1], time_reversal)
+
+    def bloch(M, kv):
+        ph = np.exp(1j * (R @ kv))
+        full = M[:m].reshape(2, norb, nat, norb) * ph[:, None, :, None]
+        out = np.zeros((2, norb, 2, norb), dtype=complex)
+        for b in range(2):
+            out[:, :, b, :] = full[:, :, sub == b, :].sum(axis=2)
+        out = out.reshape(m, m)
+        return 0.5 * (out + out.conj().T)
+
+    Hk = [bloch(H_sc, kv) for kv in ks]
+    Sk = [bloch(S_sc, kv) for kv in ks]
+    Tk = [bloch(T_sc, kv) for kv in ks]
+    n = 4
+    import scipy.linalg
+    ev = [scipy.linalg.eigh(h, s, eigvals_only=True, subset_by_index=[n - 1, n]) for h, s in zip(Hk, Sk)]
+    etas = [float(e[0] + min(ETA_ABOVE_HOMO, 0.5 * (e[1] - e[0]))) for e in ev]
+    homo, lumo = max(float(e[0]) for e in ev), min(float(e[1]) for e in ev)
+    eta = homo + min(ETA_ABOVE_HOMO, 0.5 * (lumo - homo)) if lumo > homo else float("nan")
+    C0 = [(streams[2].normal(0.0, 0.1, size=(n, m)) + 1j * streams[2].normal(0.0, 0.1, size=(n, m)))
+          / np.sqrt(2 * m) for _ in ks]
+    gaps = [float(e[1] - e[0]) for e in ev]
+    meta = {"system": "graphene", "basis": basis, "mp_grid": [q[0], q[1], 1], "time_reversal": time_reversal,
+            "weights": wk.tolist(), "etas": etas, "gaps": gaps, "min_gap": min(gaps), "homo": homo, "lumo": lumo,
+            "cells_in_supercell": ncell}
+    return KProblem(name=f"graphene_{basis}_mp{q[0]}x{q[1]}x1", m=m, n=n, k=ks, H=Hk, S=Sk, T=Tk,
+                    eta=float(eta), tau=TAU_10RY, C0=C0, seed=seed, meta=meta)

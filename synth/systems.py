@@ -168,3 +168,48 @@ def water_box(nmol: int, rng: np.random.Generator, dmin: float = 4.7, max_tries:
     pos = np.array(pos)
     pos -= cell * np.floor(pos / cell)
     return symbols, pos, cell
+
+
+# ---------------------------------------------------------------- graphene
+# One layer, a = 2.46 Angstrom; the 2-atom hexagonal cell of the paper's second k-point test
+# (DZP: m = 26, n = 4). Carbon shells are the Si ones scaled to the shorter bond (exponents times
+# (d_Si / d_C)^2 ~ 2.7); Harrison's universal couplings at d0 = a / sqrt(3) and his carbon term
+# values eps_s = -17.52 eV, eps_p = -8.97 eV.
+A_GRAPHENE = 2.46 / 0.529177210903
+D0_C = A_GRAPHENE / np.sqrt(3.0)
+C_SHELLS = {
+    "s1": Shell("s1", "s", 0.96, True), "p1": Shell("p1", "p", 0.82, True),
+    "s2": Shell("s2", "s", 2.4, False), "p2": Shell("p2", "p", 2.05, False),
+    "d": Shell("d", "d", 0.96, False),
+}
+C_BASES = {"SZ": ["s1", "p1"], "DZP": ["s1", "p1", "s2", "p2", "d"]}
+
+
+def carbon_model(basis: str = "DZP") -> Model:
+    if basis not in C_BASES:
+        raise ValueError(basis)
+    eps = {"s": -17.52 / HARTREE_EV, "p": -8.97 / HARTREE_EV, "d": 0.15}
+    c = Species("C", [C_SHELLS[k] for k in C_BASES[basis]], eps)
+    inv = 1.0 / D0_C ** 2
+    pair = SKPair(d0=D0_C, ss=-1.40 * inv, sp=1.84 * inv, ps=1.84 * inv,
+                  pp_sigma=3.24 * inv, pp_pi=-0.81 * inv)
+    return Model(species={"C": c}, sk={("C", "C"): pair}, rc=9.0,
+                 params={"system": "graphene", "basis": basis, "a": A_GRAPHENE, "d0": D0_C})
+
+
+def graphene_supercell(n1: int, n2: int, vacuum: float = 41.0):
+    """n1 x n2 rectangular cells (a x sqrt(3) a, 4 atoms each) of one graphene layer in an
+    orthorhombic box of height `vacuum`. Atoms 0 and 1 are the A and B sites of the hexagonal cell
+    at the origin; sublattice[i] says which of the two atom i is a lattice translate of."""
+    a = A_GRAPHENE
+    rect = np.array([[0.0, 0.0], [a / 2, a / (2 * np.sqrt(3.0))], [a / 2, np.sqrt(3.0) * a / 2],
+                     [0.0, 2 * a / np.sqrt(3.0)]])
+    sub = np.array([0, 1, 0, 1])
+    pos, sl = [], []
+    for i in range(n1):
+        for j in range(n2):
+            for r, s in zip(rect, sub):
+                pos.append([r[0] + i * a, r[1] + j * np.sqrt(3.0) * a, 0.0])
+                sl.append(s)
+    cell = np.array([n1 * a, n2 * np.sqrt(3.0) * a, vacuum])
+    return ["C"] * len(pos), np.array(pos), cell, np.array(sl)

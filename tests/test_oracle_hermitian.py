@@ -197,3 +197,45 @@ def test_neighbouring_k_point_start_saves_line_searches():
             assert warm["iters"] < cold["iters"], (i, warm["iters"], cold["iters"])
             assert abs(warm["E"] - cold["E"]) <= 1e-12 * abs(cold["E"])
         prev = cold["C"]
+
+
+# ---------------------------------------------------------------- graphene (the second k-point system)
+@pytest.fixture(scope="module")
+def graphene():
+    from synth.kpoints import graphene_mp_grid
+    return graphene_mp_grid((19, 19))
+
+
+def test_graphene_grid_is_well_posed(graphene):
+    """19 x 19 grid, k/-k merged: 181 Hermitian problems of m = 26, n = 4, S(k) positive definite,
+    one eta inside every gap."""
+    import scipy.linalg
+    p = graphene
+    assert (p.m, p.n, len(p.H)) == (26, 4, 181)
+    assert sum(p.meta["weights"]) == pytest.approx(1.0, abs=1e-14)
+    gaps = []
+    for h, s in zip(p.H, p.S):
+        assert np.abs(h - h.conj().T).max() == 0.0
+        assert np.linalg.eigvalsh(s).min() > 1e-3
+        e = scipy.linalg.eigh(h, s, eigvals_only=True, subset_by_index=[p.n - 1, p.n])
+        assert e[0] < p.eta < e[1]
+        gaps.append(e[1] - e[0])
+    assert min(gaps) == pytest.approx(p.meta["min_gap"], rel=1e-12)
+
+
+def test_graphene_bloch_sums_do_not_depend_on_the_supercell():
+    from synth.kpoints import graphene_mp_grid
+    p1 = graphene_mp_grid((5, 5), sc=(9, 6))
+    p2 = graphene_mp_grid((5, 5), sc=(10, 7))
+    for a, b in zip(p1.H + p1.S, p2.H + p2.S):
+        assert np.abs(a - b).max() < 1e-13
+
+
+def test_graphene_oracle_reaches_exact_minimum(graphene):
+    p = graphene
+    for i in (0, 90, int(np.argmin(p.meta["gaps"]))):              # incl. the smallest gap
+        r = hermitian.solve(p.H[i], p.S[i], p.T[i], p.eta, p.tau, p.C0[i], tol_grad=1e-9)
+        ex = hermitian.exact_minimum(p.H[i], p.S[i], p.n)
+        assert r["status"] == omm.STATUS_OK
+        assert abs(r["E"] - ex["E"]) / abs(ex["E"]) < 1e-12
+        assert np.abs(r["D"] - ex["D"]).max() < 1e-8
