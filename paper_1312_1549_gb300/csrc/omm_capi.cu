@@ -345,7 +345,8 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     OMM_CUDA_TRY(cudaEventRecord(c->ev[0], c->st));
     copy_in(c->HS, H, mm, c->st);
     copy_in(c->HS + mm, S, mm, c->st);
-    // the mixed path factors with float64-class tensor-core products, the float64 path natively
+    // the mixed path factors large matrices with sliced tensor-core products (preconditioner grade
+    // for P, float64-class for the Cholesky flavour's factor), small ones and the float64 path natively
     const bool sliced_inverse = o.precision == OMM_PREC_MIXED && m >= kSlicedInverseMin;
     if (chol) {
       // standard form (Sec. 2.4): H_r = L^-1 H L^-T in the H slot, the identity in the S slot
@@ -503,9 +504,9 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     // Outer loop: float64 recompute of the state (refinement / certificate),
     // then line searches until converged, halted or capped.
     for (int round = 0;; ++round) {
-      // the mixed path starts from a tensor-core state; every later state is float64
-      // mixed path: a tensor-core first state, float64-class (sliced) refreshes while the
-      // device asks for them, and a native float64 state once it reports convergence
+      // mixed path: a tensor-core first state, then float64-class states (sliced products, or
+      // native float64 for small problems) for the refreshes the device asks for and for the
+      // certificate once it reports convergence (native float64 with native_certificate = 1)
       const bool emu_certify = mixed && c->emu && c->opts.native_certificate == 0;
       const bool tc_state = mixed && round == 0;
       const bool emu_state = mixed && c->emu && round > 0 && (!last_round_done || emu_certify);
@@ -536,7 +537,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
         result = OMM_ERR_NONFINITE;
         break;
       }
-      // only a native float64 state certifies (or Eq. 18 met)
+      // only a float64-class state taken for the certificate (or any native float64 state) certifies
       if (!tc_state && (!emu_state || emu_certify) && (h.gmax < c->opts.tol_grad || energy_stop)) break;
       if (round > 0) ++refinements;
       if (iter_total >= c->opts.max_iter) {
