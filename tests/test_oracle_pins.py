@@ -330,3 +330,16 @@ def test_start_at_the_minimum_takes_no_line_search():
     r2 = omm.solve(H, S, T, eta, 1.3, r["C"], tol_grad=1e-10, C_is_mn=True)
     assert r2["iters"] == 0 and r2["status"] == omm.STATUS_OK
     assert r2["E"] == pytest.approx(r["E"], rel=1e-14)
+
+
+def test_cholesky_flavour_trajectory_at_si64_dzp():
+    """Sec. 2.4 at a workload's size (m = 832): 30 line searches of the reduced problem and of the
+    S^-1-preconditioned original one give the same energies to rounding."""
+    from synth import configs
+    p = configs.silicon(k=(2, 2, 2), basis="DZP", seed=0)
+    a = omm.solve_cholesky(p.H, p.S, p.eta, p.C0, tol_grad=1e-30, max_iter=30, want_matrices=False)
+    b = omm.solve(p.H, p.S, None, p.eta, math.inf, p.C0, tol_grad=1e-30, max_iter=30, want_matrices=False)
+    ea = np.array([h[0] for h in a["history"]])
+    eb = np.array([h[0] for h in b["history"]])
+    assert len(ea) == len(eb) == 31
+    assert np.abs((ea - eb) / eb).max() < 1e-12
