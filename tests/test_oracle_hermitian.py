@@ -239,3 +239,23 @@ def test_graphene_oracle_reaches_exact_minimum(graphene):
         assert r["status"] == omm.STATUS_OK
         assert abs(r["E"] - ex["E"]) / abs(ex["E"]) < 1e-12
         assert np.abs(r["D"] - ex["D"]).max() < 1e-8
+
+
+def test_hermitian_backward_central_differences():
+    """dE = Re Tr(D dH) - Re Tr(EDM dS) for Hermitian dH, dS (the convention of the complex
+    dE/dH and dE/dS): central differences of re-solved energies."""
+    H, S, T, eta, C0, w = hermitian_problem(14, 4, 7)
+    r = hermitian.solve(H, S, T, eta, 1.3, C0, tol_grad=1e-12, max_iter=5000)
+    Cstar = r["C"].T.copy()
+    rng = np.random.default_rng(8)
+    A = rng.normal(size=H.shape) + 1j * rng.normal(size=H.shape)
+    dH = 0.5 * (A + A.conj().T)
+    B = rng.normal(size=S.shape) + 1j * rng.normal(size=S.shape)
+    dS = 0.05 * (B + B.conj().T)
+    h = 1e-5
+    Ep = hermitian.solve(H + h * dH, S, T, eta, 1.3, Cstar, tol_grad=1e-12)["E"]
+    Em = hermitian.solve(H - h * dH, S, T, eta, 1.3, Cstar, tol_grad=1e-12)["E"]
+    assert (Ep - Em) / (2 * h) == pytest.approx(float(np.real(np.trace(r["D"] @ dH))), rel=1e-7, abs=1e-8)
+    Ep = hermitian.solve(H, S + h * dS, T, eta, 1.3, Cstar, tol_grad=1e-12)["E"]
+    Em = hermitian.solve(H, S - h * dS, T, eta, 1.3, Cstar, tol_grad=1e-12)["E"]
+    assert (Ep - Em) / (2 * h) == pytest.approx(-float(np.real(np.trace(r["EDM"] @ dS))), rel=1e-7, abs=1e-8)
