@@ -14,6 +14,7 @@ per point of a Monkhorst-Pack grid. This module takes the same steps as
   quartic          alpha_0..alpha_4 from the traces of Eq. 13 with (S_W')^H, real parts
   update           H_W += x (H_W' + H_W'^H) + x^2 H_W''         Sec. 2.3, Eq. 16
   outputs          E = E~ + 2 n eta, D = 2 C (2I - S_W) C^H, EDM
+  Cholesky flavour S = L L^H, H_r = L^-1 H L^-H, S -> I        Sec. 2.4 (last paragraph)
 
 Conventions: C is m x n (column i = Wannier function i); inputs given in the
 library's n x m row-major layout are transposed (not conjugated) on entry, so
@@ -162,3 +163,29 @@ def embed(A: np.ndarray) -> np.ndarray:
     """The real form [[Re A, -Im A], [Im A, Re A]] of a complex matrix (a ring homomorphism)."""
     A = np.asarray(A, dtype=complex)
     return np.block([[A.real, -A.imag], [A.imag, A.real]])
+
+
+def solve_cholesky(H, S, eta, C0_nm, tol_grad=1e-9, max_iter=2000, callback=None, want_matrices=True):
+    """The Cholesky flavour for Hermitian matrices (Sec. 2.4, last paragraph, with C^H): S = L L^H,
+    H_r = L^-1 H L^-H, C_r = L^H C, the OMM with S = I and no preconditioner, then C = L^-H C_r.
+    H_W, S_W and E are the same in both bases; tol_grad applies to the reduced gradient."""
+    H = np.asarray(H, dtype=complex)
+    S = np.asarray(S, dtype=complex)
+    m = H.shape[0]
+    L = np.linalg.cholesky(S)
+    Linv = np.linalg.inv(L)
+    Hr = Linv @ H @ _h(Linv)
+    Hr = 0.5 * (Hr + _h(Hr))
+    C = np.asarray(C0_nm, dtype=complex).T
+    Cr0 = _h(L) @ C
+    r = solve(Hr, np.eye(m, dtype=complex), None, eta, math.inf, Cr0.T, tol_grad=tol_grad, max_iter=max_iter,
+              precondition=False, callback=callback, want_matrices=False)
+    Cback = _h(Linv) @ r["C"]
+    out = dict(r)
+    out["C"] = Cback
+    if want_matrices:
+        n = Cback.shape[1]
+        D = 2.0 * Cback @ (2.0 * np.eye(n) - r["SW"]) @ _h(Cback)
+        out["D"] = D
+        out["EDM"] = 2.0 * Cback @ r["HW"] @ _h(Cback) + eta * D
+    return out

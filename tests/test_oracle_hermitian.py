@@ -259,3 +259,25 @@ def test_hermitian_backward_central_differences():
     Ep = hermitian.solve(H, S + h * dS, T, eta, 1.3, Cstar, tol_grad=1e-12)["E"]
     Em = hermitian.solve(H, S - h * dS, T, eta, 1.3, Cstar, tol_grad=1e-12)["E"]
     assert (Ep - Em) / (2 * h) == pytest.approx(-float(np.real(np.trace(r["EDM"] @ dS))), rel=1e-7, abs=1e-8)
+
+
+def test_hermitian_cholesky_flavour():
+    """Complex Cholesky flavour: the brute-force minimum, and the steps of the S^-1-preconditioned
+    complex method (Sec. 2.4)."""
+    H, S, T, eta, C0, w = hermitian_problem(18, 6, 9)
+    r = hermitian.solve_cholesky(H, S, eta, C0, tol_grad=1e-11, max_iter=5000)
+    assert r["status"] == omm.STATUS_OK
+    assert r["E"] == pytest.approx(2.0 * float(np.sum(w[:6])), rel=1e-12, abs=1e-12)
+    ex = hermitian.exact_minimum(H, S, 6)
+    assert np.abs(r["D"] - ex["D"]).max() < 1e-9
+    assert np.abs(r["EDM"] - ex["EDM"]).max() < 1e-9
+    Cm = r["C"]
+    assert np.abs(Cm.conj().T @ S @ Cm - np.eye(6)).max() < 1e-9
+    red, orig = [], []
+    hermitian.solve_cholesky(H, S, eta, C0, tol_grad=1e-30, max_iter=10,
+                             callback=lambda it, E, x, b: red.append((E, x)), want_matrices=False)
+    hermitian.solve(H, S, None, eta, math.inf, C0, tol_grad=1e-30, max_iter=10,
+                    callback=lambda it, E, x, b: orig.append((E, x)), want_matrices=False)
+    for (Er, xr), (Eo, xo) in zip(red, orig):
+        assert Er == pytest.approx(Eo, rel=1e-10, abs=1e-12)
+        assert xr == pytest.approx(xo, rel=1e-7)
