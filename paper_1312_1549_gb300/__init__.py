@@ -5,13 +5,13 @@ include/omm_kernels.h); this package is its thin Python binding. Importing
 the package does not load the library; `OMMSolver(...)` does, and fails
 loudly if the library has not been built.
 """
-__all__ = ["OMMSolver", "omm_energy"]
+__all__ = ["OMMSolver", "OMMBatch", "OMMHermitian", "OMMHermitianBatch", "omm_energy"]
 
 
 def __getattr__(name):
-    if name == "OMMSolver":
-        from .solver import OMMSolver
-        return OMMSolver
+    if name in ("OMMSolver", "OMMBatch", "OMMHermitian", "OMMHermitianBatch"):
+        from . import solver
+        return getattr(solver, name)
     if name == "omm_energy":
         from .autograd import omm_energy
         return omm_energy
