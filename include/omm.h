@@ -150,8 +150,11 @@ typedef struct {
 } omm_info;
 
 /* Create a solver context for one (H, S, T) and do the per-geometry setup:
- * H~ = H - eta S (Eq. 9) and the preconditioner P = (S + T/tau)^-1 (Eq. 17) by a
- * float64 Cholesky factorisation and inverse (Sec. 2.4: once per geometry).
+ * H~ = H - eta S (Eq. 9) and the preconditioner P = (S + T/tau)^-1 (Eq. 17), once per
+ * geometry (Sec. 2.4): on the float64 path (and on the mixed path below m = 2048) by a
+ * blocked float64 Cholesky factorisation and inverse; on the mixed path from m = 2048 by a
+ * recursive Cholesky inverse whose products are fixed-point sliced tensor-core GEMMs at
+ * preconditioner grade (opts->precond_slices, default 5 slices, float32 diagonal blocks).
  *   m      number of basis functions, n number of Wannier functions, 0 < n < m.
  *   H,S,T  m x m symmetric float64 (host or device). T may be NULL when
  *          opts->no_precondition == 1. They are copied; the caller keeps ownership.

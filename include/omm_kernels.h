@@ -119,9 +119,12 @@ omm_status omm_kernel_gemm_emu(int M, int N, int K, const double* A, const doubl
  * process exits. Limit: n <= 2048 (larger n returns OMM_ERR_ARG and leaves
  * alpha untouched). The first call on each device, made with that device
  * current, looks the array's device address up (cudaGetSymbolAddress); make
- * that first call before any stream capture. All calls share the array:
- * calls that overlap on the GPU (other streams, other host threads) race and
- * must be serialised by the caller. Errors: OMM_ERR_ARG, OMM_ERR_CUDA. */
+ * that first call before any stream capture. The address is kept for the
+ * life of the process: do not call this entry point again on a device after a
+ * cudaDeviceReset of that device. The call waits on its stream before it
+ * returns (alpha is written on the host). All calls share the array: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller. Errors: OMM_ERR_ARG, OMM_ERR_CUDA. */
 omm_status omm_kernel_quartic_coefficients_noalloc(int n, const double* SWHW, const double* Proj,
                                                    double E, double* alpha, void* stream);
 

@@ -5,6 +5,11 @@ CUDA kernels form dE/dH = D = 2 C (2I - S_W) C^T and
 dE/dS = -EDM = -(2 C H~_W C^T + eta D) at the converged minimum (exact there
 by the envelope theorem on the OMM functional, Eq. 8 of the paper, with
 H~ = H - eta S). The upstream scalar gradient is applied by the chain rule.
+
+The two m x m gradients are formed once, on the first backward call, and kept
+on the autograd context, so a second backward through the same graph
+(retain_graph=True) reuses them; the solver context and its device buffers are
+released as soon as they exist, or with the graph if no backward ever runs.
 """
 from __future__ import annotations
 
@@ -26,10 +31,14 @@ class OMMEnergy(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, gE, gC):
-        solver = ctx.solver
-        dH, dS = solver.backward(device=ctx.device)
-        solver.close()
-        ctx.solver = None
+        if getattr(ctx, "grads", None) is None:
+            solver = ctx.solver
+            if solver is None:
+                raise RuntimeError("OMMEnergy.backward: the solver of this forward has been released")
+            ctx.grads = solver.backward(device=ctx.device)
+            solver.close()
+            ctx.solver = None
+        dH, dS = ctx.grads
         gH = dH * gE if ctx.needs_input_grad[0] else None
         gS = dS * gE if ctx.needs_input_grad[1] else None
         return gH, gS, None, None, None, None, None, None, None

@@ -564,8 +564,11 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
           result[i] = (omm_status)h.status;
           finished[i] = 1;
           if (result[i] == OMM_ERR_NO_CONVERGENCE) {
+            // certify what the capped instance has: the float64 recompute's E~ and max|G| are
+            // read back before the host flags go down again (they would overwrite them)
             project_real_form(c, c->st);
             recompute_state_fp64(c);
+            read_scalars(c);
           }
           h.done = 1;
           write_scalars(c);

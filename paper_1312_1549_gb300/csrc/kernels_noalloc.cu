@@ -13,7 +13,10 @@
 // names a host-side stand-in), so the device address is looked up once per
 // device with cudaGetSymbolAddress, on the first call made while that device
 // is current, and handed to the kernels. That first call should therefore
-// come before any stream capture. Every call shares the one array: calls that
+// come before any stream capture. The address stays cached for the life of the
+// process: after a cudaDeviceReset the device's modules are reloaded and the
+// cached address no longer names the array, so this entry point must not be
+// called again on a device that has been reset. Every call shares the one array: calls that
 // overlap on the GPU (several streams, or several host threads) race and must
 // be serialised by the caller. The control block is rewritten at the start of
 // every call; the partial sums are fully overwritten by the trace kernel.

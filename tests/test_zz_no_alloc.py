@@ -39,7 +39,8 @@ def test_noalloc_matches_allocating_entry_point_twice():
     from paper_1312_1549_gb300 import build
     build.build()
     from paper_1312_1549_gb300 import solver as S
-    for call, (n, seed) in enumerate([(300, 1), (64, 2)]):
+    # n = 2048 fills the static array exactly; the smaller calls after it reuse what it left there
+    for call, (n, seed) in enumerate([(2048, 4), (300, 1), (64, 2)]):
         SWHW, Proj, E = _inputs(n, seed)
         ref = S.quartic_coefficients(SWHW, Proj, E)
         rc, got = _noalloc(SWHW, Proj, E)
@@ -50,9 +51,10 @@ def test_noalloc_matches_allocating_entry_point_twice():
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     SWHW, Proj, E = _inputs(8, 3)
     from paper_1312_1549_gb300 import _native as N
-    out = (ct.c_double * 5)(*([7.0] * 5))
-    rc = N.lib().omm_kernel_quartic_coefficients_noalloc(4096, ct.c_void_p(SWHW.data_ptr()),
-                                                         ct.c_void_p(Proj.data_ptr()), E, out, None)
-    assert rc == 1
-    assert list(out) == [7.0] * 5
-    assert b"2048" in N.lib().omm_last_error()
+    for n in (2049, 4096):  # the first size past the limit, and one far past it
+        out = (ct.c_double * 5)(*([7.0] * 5))
+        rc = N.lib().omm_kernel_quartic_coefficients_noalloc(n, ct.c_void_p(SWHW.data_ptr()),
+                                                             ct.c_void_p(Proj.data_ptr()), E, out, None)
+        assert rc == 1
+        assert list(out) == [7.0] * 5
+        assert b"2048" in N.lib().omm_last_error()
