@@ -173,6 +173,35 @@ def batch_instance(i: int) -> Problem:
     return _gap_guarded(builder, i, **kw)
 
 
+def batch_instances(indices, workers=None) -> list:
+    """batch_instance(i) for every i in indices, built by a pool of worker processes.
+
+    The workers are started with the "spawn" method (never forked from a process that may
+    already hold a GPU context) and with one BLAS thread each; the result is the list of
+    problems in the order of `indices`, the same bits as building them one by one.
+    """
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    indices = list(indices)
+    workers = workers or min(len(indices), max(1, (os.cpu_count() or 2) // 2), 16)
+    if workers <= 1 or len(indices) <= 1:
+        return [batch_instance(i) for i in indices]
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        # a worker that dies raises BrokenProcessPool here instead of leaving the map waiting
+        with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as pool:
+            return list(pool.map(batch_instance, indices))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
 def si4096_sz(seed=0) -> Problem:
     """Si4096 single-zeta: m = 16384, n = 8192 (the warm-start sequence's H_0)."""
     return _gap_guarded(silicon, seed, k=(8, 8, 8), basis="SZ", name="si4096_sz")
