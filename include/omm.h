@@ -108,6 +108,12 @@ typedef struct {
                            (about 2^-16 of each element) and the converged point does not depend
                            on P, so the float64-class 10 slices buy nothing there; the Cholesky
                            flavour's factor always takes 10 */
+  int debug_expire_wait; /* tests of the timeout status only (0 = off, the default): 1 -> on the
+                           mixed path the first tensor-core GEMM of every line search waits about
+                           1 ms on a barrier that nothing arrives at, before it issues any copy or
+                           MMA; the wait expires and omm_solve returns OMM_ERR_TIMEOUT. The context
+                           stays usable (the next omm_solve of a context created without the flag
+                           succeeds) */
 } omm_opts;
 
 /* Per-solve report. */

@@ -91,6 +91,17 @@ omm_status omm_kernel_gemm_tc_tiled(int M, int N, int K, const double* A, const 
 omm_status omm_kernel_gemm_tc_blocksparse(int M, int N, int K, const double* A, const double* B, double alpha,
                                           double beta, double* C, int npass, int tile_n, void* stream);
 
+/* C = alpha A B + beta C on the BF16 tensor cores in 3-term split form, with B given K x N
+ * (row-major, the contracted index first): A M x K, C M x N, all row-major float64 (device). This
+ * is the operand layout of the mixed path's gradient product G = G_ref + 8 dHC - 4 W [dHC; dSC;
+ * HC; SC] (Eq. 12 about the last refresh point, Sec. 2.3): the stacked n x m blocks are read as
+ * an MN-major B operand (64 x 64 TMA boxes, the tcgen05 B-transpose bit), without a transposed
+ * copy. tile_n: 256 or 128 (output tile width). Error bound as omm_kernel_gemm_tc. Scratch is
+ * allocated and freed inside the call. Errors: OMM_ERR_ARG, OMM_ERR_OOM, OMM_ERR_TIMEOUT,
+ * OMM_ERR_CUDA. */
+omm_status omm_kernel_gemm_tc_kn(int M, int N, int K, const double* A, const double* B, double alpha,
+                                 double beta, double* C, int tile_n, void* stream);
+
 omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double* B, double alpha,
                               double beta, double* C, int npass, void* stream);
 

@@ -24,7 +24,7 @@ class OmmOpts(ct.Structure):
                 ("check_every", ct.c_int), ("tol_grad", ct.c_double), ("e_tol", ct.c_double),
                 ("refine_ratio", ct.c_double), ("profile", ct.c_int),
                 ("native_certificate", ct.c_int), ("cholesky", ct.c_int),
-                ("precond_slices", ct.c_int)]
+                ("precond_slices", ct.c_int), ("debug_expire_wait", ct.c_int)]
 
 
 class OmmInfo(ct.Structure):
@@ -91,6 +91,7 @@ _SIGNATURES = {
     "omm_kernel_line_minimum": (_I, [ct.POINTER(_D), ct.POINTER(_D)]),
     "omm_kernel_quartic_coefficients": (_I, [_I, _P, _P, _D, ct.POINTER(_D), _P]),
     "omm_kernel_gemm_tc": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _P]),
+    "omm_kernel_gemm_tc_kn": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _P]),
     "omm_kernel_gemm_emu": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _P]),
     "omm_kernel_quartic_coefficients_noalloc": (_I, [_I, _P, _P, _D, ct.POINTER(_D), _P]),
 }

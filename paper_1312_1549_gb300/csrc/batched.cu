@@ -35,56 +35,26 @@ constexpr int kBatchReduceBlocks = 64;  // gradient-reduction partials per insta
 struct IterArgs {
   int n, m;
   long nm;
-  int tiles;  // 32 x 32 tiles of an n x n matrix
+  int tiles;   // 32 x 32 tiles of an n x n matrix
+  int nparts;  // partial sums of the P G epilogue (4 per epilogue warp and output tile)
   int precond;
   Scalars* sc;
-  double *C, *Dir, *G, *Gold, *PG, *Y4, *SWHW, *Proj, *part, *part2, *dY, *Gref, *Wref;
-  __nv_bfloat16 *G_hi, *D_hi, *Y_hi, *YT_hi, *W_hi;
+  double *C, *Dir, *G, *Gold, *PG, *Y4, *SWHW, *Proj, *part, *part2, *dY, *Wref, *red;
+  __nv_bfloat16 *D_hi, *Y_hi, *W_hi;
   long ldm, ld4;
 };
-
-// the splits that no producing kernel writes: G (before P G), [HD; SD] (after the GEMM) and
-// [dS_W | dH_W] = [S_W | H_W] - W_ref
-enum SplitJob { kSplitG = 0, kSplitHDSD, kSplitW };
-
-__global__ void __launch_bounds__(256) b_split_kernel(const IterArgs* __restrict__ A, int job) {
-  const IterArgs& a = A[blockIdx.y];
-  if (dev::stopped(a.sc)) return;
-  const long n = a.n, m = a.m;
-  switch (job) {
-    case kSplitG:
-      dev::split_body(a.G, nullptr, n, m, m, a.G_hi, a.G_hi + n * a.ldm, a.ldm, blockIdx.x, gridDim.x);
-      break;
-    case kSplitHDSD:
-      dev::split_body(a.Y4 + 2 * a.nm, nullptr, 2 * n, m, m, a.Y_hi + 2 * n * a.ldm, a.Y_hi + 6 * n * a.ldm,
-                      a.ldm, blockIdx.x, gridDim.x);
-      break;
-    default:
-      dev::split_body(a.SWHW, a.Wref, n, 2 * n, 2 * n, a.W_hi, a.W_hi + n * a.ld4, a.ld4, blockIdx.x, gridDim.x);
-      break;
-  }
-}
-
-// job 0: [HC; SC] -> columns [0, 2n) of YT; job 1: [dHC; dSC] -> columns [2n, 4n)
-__global__ void __launch_bounds__(256) b_split_t_kernel(const IterArgs* __restrict__ A, int job) {
-  const IterArgs& a = A[blockIdx.y];
-  if (dev::stopped(a.sc)) return;
-  const long rows = 2L * a.n, cols = a.m;
-  const long tiles = ((rows + 63) / 64) * ((cols + 31) / 32);
-  if ((long)blockIdx.x >= tiles) return;
-  const double* src = job == 0 ? a.Y4 : a.dY;
-  __nv_bfloat16* hi = a.YT_hi + (job == 0 ? 0 : 2L * a.n);
-  dev::split_t_body(src, rows, cols, cols, hi, hi + (long)a.m * a.ld4, a.ld4, blockIdx.x);
-}
 
 __global__ void __launch_bounds__(dev::TB) b_grad_reduce_kernel(const IterArgs* __restrict__ A) {
   const IterArgs& a = A[blockIdx.y];
   dev::grad_reduce_body(a.nm, a.G, a.PG, a.Gold, a.Dir, a.part, a.sc, blockIdx.x, gridDim.x);
 }
 
+// Polak-Ribiere coefficient and stopping tests: from the P G epilogue's partial sums, or (without a
+// preconditioner) from the reduction kernel's
 __global__ void __launch_bounds__(dev::TB) b_control_direction_kernel(const IterArgs* __restrict__ A) {
   const IterArgs& a = A[blockIdx.y];
-  dev::control_direction_body(a.sc, a.part, 1, kBatchReduceBlocks, 0, 1);
+  if (a.precond) dev::control_direction_body(a.sc, a.red, 1, a.nparts, 0, 1);
+  else dev::control_direction_body(a.sc, a.part, 1, kBatchReduceBlocks, 0, 1);
 }
 
 // Delta and its split (the operand of the next two products)
@@ -94,15 +64,16 @@ __global__ void __launch_bounds__(256) b_direction_kernel(const IterArgs* __rest
                             gridDim.x);
 }
 
-__global__ void __launch_bounds__(256) b_copy_gradient_kernel(const IterArgs* __restrict__ A) {
+// without a preconditioner: PG = G (job 0) before the reductions, G_old = G (job 1) after them
+__global__ void __launch_bounds__(256) b_copy_gradient_kernel(const IterArgs* __restrict__ A, int job) {
   const IterArgs& a = A[blockIdx.y];
-  dev::scale_copy_body(a.nm, a.G, 1.0, a.PG, a.sc, blockIdx.x, gridDim.x);
+  dev::scale_copy_body(a.nm, a.G, 1.0, job == 0 ? a.PG : a.Gold, a.sc, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(dev::TB) b_traces_kernel(const IterArgs* __restrict__ A) {
   const IterArgs& a = A[blockIdx.y];
   if ((int)blockIdx.x >= a.tiles) return;
-  dev::traces_body(a.n, a.SWHW, a.Proj, a.part2, a.sc, blockIdx.x, a.tiles);
+  dev::traces_body<true>(a.n, a.SWHW, a.Proj, a.part2, a.sc, blockIdx.x, a.tiles);
 }
 
 __global__ void __launch_bounds__(dev::TB) b_control_linesearch_kernel(const IterArgs* __restrict__ A) {
@@ -110,17 +81,19 @@ __global__ void __launch_bounds__(dev::TB) b_control_linesearch_kernel(const Ite
   dev::control_linesearch_body(a.sc, a.part2, a.tiles, 0, 1);
 }
 
-// the state update and the split of the new [HC; SC]
+// the state update and the splits of the new dHC, dSC, HC, SC
 __global__ void __launch_bounds__(256) b_update_state_kernel(const IterArgs* __restrict__ A) {
   const IterArgs& a = A[blockIdx.y];
-  dev::update_state_split_body(a.n, a.m, a.C, a.Y4, a.Dir, a.G, a.Gold, a.dY, a.Gref, a.Y_hi,
-                               a.Y_hi + 4L * a.n * a.ldm, a.ldm, a.sc, blockIdx.x, gridDim.x);
+  dev::update_state_split_body(a.n, a.m, a.C, a.Y4, a.Dir, a.dY, a.Y_hi, a.Y_hi + 6L * a.n * a.ldm, a.ldm, a.sc,
+                               blockIdx.x, gridDim.x);
 }
 
+// H_W, S_W and the split of [dS_W | dH_W]
 __global__ void __launch_bounds__(dev::TB) b_update_subspace_kernel(const IterArgs* __restrict__ A) {
   const IterArgs& a = A[blockIdx.y];
   if ((int)blockIdx.x >= a.tiles) return;
-  dev::update_subspace_body(a.n, a.SWHW, a.Proj, a.sc, blockIdx.x, a.tiles);
+  dev::update_subspace_split_body(a.n, a.SWHW, a.Proj, a.Wref, a.W_hi + 2L * a.n, a.W_hi + (long)a.n * a.ld4 + 2L * a.n,
+                                  a.ld4, a.sc, blockIdx.x, a.tiles);
 }
 
 struct Grouped {
@@ -155,9 +128,8 @@ struct omm_batch {
   Scalars* sc_host_all = nullptr;  // pinned
   IterArgs* args = nullptr;        // device
   Grouped gPG, gHD, gPr, gG;
-  int max_rows = 0;        // largest 2n (split grid)
+  int max_rows = 0;        // largest 2n (vector-kernel grid)
   int max_tiles = 0;       // largest n x n tile count
-  int max_ttiles = 0;      // largest transposed-split tile count
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool precond = true;
@@ -226,22 +198,22 @@ void enqueue_line_search(omm_batch* b) {
   const dim3 vec_grid(256, cnt);
   const tc::PairList pl = tc::pairs_split3();
   if (b->precond) {
-    b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitG);
-    OMM_LAUNCH_CHECK();
-    timed_gemm(b, b->gPG, pl);
+    timed_gemm(b, b->gPG, pl);  // P G, the Polak-Ribiere products and max|G|, G_old <- G
   } else {
-    b_copy_gradient_kernel<<<vec_grid, 256, 0, st>>>(b->args);
+    b_copy_gradient_kernel<<<vec_grid, 256, 0, st>>>(b->args, 0);
+    OMM_LAUNCH_CHECK();
+    b_grad_reduce_kernel<<<dim3(kBatchReduceBlocks, cnt), dev::TB, 0, st>>>(b->args);
     OMM_LAUNCH_CHECK();
   }
-  b_grad_reduce_kernel<<<dim3(kBatchReduceBlocks, cnt), dev::TB, 0, st>>>(b->args);
-  OMM_LAUNCH_CHECK();
   b_control_direction_kernel<<<dim3(1, cnt), dev::TB, 0, st>>>(b->args);
   OMM_LAUNCH_CHECK();
+  if (!b->precond) {
+    b_copy_gradient_kernel<<<vec_grid, 256, 0, st>>>(b->args, 1);
+    OMM_LAUNCH_CHECK();
+  }
   b_direction_kernel<<<rows_grid, 256, 0, st>>>(b->args);
   OMM_LAUNCH_CHECK();
-  timed_gemm(b, b->gHD, pl);
-  b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitHDSD);
-  OMM_LAUNCH_CHECK();
+  timed_gemm(b, b->gHD, pl);  // [H D; S D] and its split
   timed_gemm(b, b->gPr, pl);
   b_traces_kernel<<<dim3(b->max_tiles, cnt), dev::TB, 0, st>>>(b->args);
   OMM_LAUNCH_CHECK();
@@ -249,15 +221,9 @@ void enqueue_line_search(omm_batch* b) {
   OMM_LAUNCH_CHECK();
   b_update_state_kernel<<<rows_grid, 256, 0, st>>>(b->args);
   OMM_LAUNCH_CHECK();
-  b_split_t_kernel<<<dim3(b->max_ttiles, cnt), 256, 0, st>>>(b->args, 0);
-  OMM_LAUNCH_CHECK();
-  b_split_t_kernel<<<dim3(b->max_ttiles, cnt), 256, 0, st>>>(b->args, 1);
-  OMM_LAUNCH_CHECK();
   b_update_subspace_kernel<<<dim3(b->max_tiles, cnt), dev::TB, 0, st>>>(b->args);
   OMM_LAUNCH_CHECK();
-  b_split_kernel<<<rows_grid, 256, 0, st>>>(b->args, kSplitW);
-  OMM_LAUNCH_CHECK();
-  timed_gemm(b, b->gG, pl);
+  timed_gemm(b, b->gG, pl);  // G and its split
 }
 
 // start a mixed round of instance i from its current (just recomputed) state
@@ -355,24 +321,19 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       a.sc = c->sc;
       a.C = c->C; a.Dir = c->Dir; a.G = c->G; a.Gold = c->Gold; a.PG = c->PG; a.Y4 = c->Y4;
       a.SWHW = c->SWHW; a.Proj = c->Proj; a.part = c->part; a.part2 = c->part2;
-      a.dY = v.dY; a.Gref = v.Gref; a.Wref = v.Wref;
-      a.G_hi = v.G_hi; a.D_hi = v.D_hi; a.Y_hi = v.Y_hi; a.YT_hi = v.YT_hi; a.W_hi = v.W_hi;
+      a.dY = v.dY; a.Wref = v.Wref; a.red = v.red;
+      a.D_hi = v.D_hi; a.Y_hi = v.Y_hi; a.W_hi = v.W_hi;
       a.ldm = v.ldm;
       a.ld4 = v.ld4;
-      const int* skip = &c->sc->done;
-      if (b->precond) {
-        tc::Epilogue e{c->PG, mi, mi, 0, 1.0, 0.0, ni, mi, skip, v.err};
-        spg.push_back(tc::GemmSpec{v.opG, v.opP, mi, e});
-      }
-      tc::Epilogue ehd{c->Y4 + 2 * nm, mi, mi, nm, 1.0, 0.0, ni, 2 * mi, skip, v.err};
-      tc::GemmSpec hd{v.opD, v.opHS, mi, ehd};
+      tc::Epilogue ep[4];
+      mixed_epilogues(c->mixed, c->sc, c->G, c->Gold, c->Dir, c->PG, c->Y4, c->Proj, ep);
+      if (b->precond) spg.push_back(tc::GemmSpec{v.opG, v.opP, mi, ep[0]});
+      tc::GemmSpec hd{v.opD, v.opHS, mi, ep[1]};
       hd.sparse[0] = &v.hs_blocks[0];
       hd.sparse[1] = &v.hs_blocks[1];
       shd.push_back(hd);
-      tc::Epilogue epr{c->Proj, 4L * ni, 4L * ni, 0, 1.0, 0.0, ni, 4 * ni, skip, v.err};
-      spr.push_back(tc::GemmSpec{v.opD, v.opY, mi, epr});
-      tc::Epilogue eg{c->G, mi, mi, 0, -4.0, 1.0, ni, mi, skip, v.err};
-      sg.push_back(tc::GemmSpec{v.opW, v.opYT, 4 * ni, eg});
+      spr.push_back(tc::GemmSpec{v.opD, v.opYproj, mi, ep[2]});
+      sg.push_back(tc::GemmSpec{v.opW, v.opYgrad, 4 * ni, ep[3]});
       // issued tensor flops, 3 x 2 M N K (3-term split), of this instance's share of each GEMM
       const double issued = 3.0 * 2.0 * ni;  // x N x K
       b->gemm_flop[0].push_back(b->precond ? issued * mi * mi : 0.0);
@@ -381,7 +342,6 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       b->gemm_flop[3].push_back(issued * mi * 4.0 * ni);
       b->max_rows = std::max(b->max_rows, 2 * ni);
       b->max_tiles = std::max(b->max_tiles, a.tiles);
-      b->max_ttiles = std::max(b->max_ttiles, (int)(((2L * ni + 63) / 64) * ((mi + 31) / 32)));
     }
     // Tile width of each grouped GEMM from the autotuner (timed once per batch shape in a
     // process); then longest tiles first: a persistent CTA takes tiles b, b + grid, ..., so
@@ -401,6 +361,8 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
         groups[k]->push_back(tc::make_group(*sp.A, *sp.B, sp.K, sp.ep, 0, bn, bl));
         if (bl && k == 1) b->gemm_flop[1][i] *= tc::block_density(bl);  // issued flops of the visited blocks
       }
+      if (k == 0)  // partial sums each instance's P G epilogue leaves for its direction step
+        for (int i = 0; i < count; ++i) args[i].nparts = 4 * tc::tiles_of((*specs[k])[i].ep, bn);
       std::stable_sort(groups[k]->begin(), groups[k]->end(),
                        [](const tc::GroupDesc& x, const tc::GroupDesc& y) { return x.K > y.K; });
       int t = 0;

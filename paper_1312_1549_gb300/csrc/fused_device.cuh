@@ -47,29 +47,24 @@ __device__ __forceinline__ void direction_split_body(long n, long m, const doubl
   }
 }
 
-// one element of the state update of Eq. 16 (mixed path: incremental gradient about the last
-// float64-class refresh)
+// one element of the state update of Eq. 16 (mixed path: dHC, dSC are the changes since the last
+// float64-class refresh, the corrections of the incremental gradient): five float64 FMAs
 __device__ __forceinline__ void update_element(double x, double& C, double dir, double& HC, double& SC, double HD,
-                                               double SD, double& dHC, double& dSC, double& G, double& Gold,
-                                               double Gref) {
+                                               double SD, double& dHC, double& dSC) {
   C = fma(x, dir, C);
-  const double hd = x * HD, sd = x * SD;
-  HC += hd;
-  SC += sd;
-  dHC += hd;
-  dSC += sd;
-  Gold = G;
-  G = fma(8.0, dHC, Gref);
+  HC = fma(x, HD, HC);
+  SC = fma(x, SD, SC);
+  dHC = fma(x, HD, dHC);
+  dSC = fma(x, SD, dSC);
 }
 
-// (row, column pair) units of n x m arrays: C, HC, SC += x (Delta, H Delta, S Delta); dHC, dSC +=
-// x (H Delta, S Delta); G_old = G; G = G_ref + 8 dHC (the GEMM of the line search adds the rest);
-// and the splits of the new HC (rows [0, n)) and SC (rows [n, 2n)) into Yhi/Ylo (leading dimension ldm)
+// (row, column pair) units of n x m arrays: C, HC, SC += x (Delta, H Delta, S Delta) and dHC, dSC
+// += x (H Delta, S Delta) (Eq. 16 and the footnote of Sec. 2.3), and the bf16 splits of the new
+// values into the operand stack [dHC; dSC; HC; SC; ...] (6n rows of leading dimension ldm; Ylo is
+// its lo half). G is not touched: the gradient GEMM's epilogue forms it.
 __device__ __forceinline__ void update_state_split_body(long n, long m, double* __restrict__ C,
                                                         double* __restrict__ Y4, const double* __restrict__ Dir,
-                                                        double* __restrict__ G, double* __restrict__ Gold,
-                                                        double* __restrict__ dY, const double* __restrict__ Gref,
-                                                        __nv_bfloat16* __restrict__ Yhi,
+                                                        double* __restrict__ dY, __nv_bfloat16* __restrict__ Yhi,
                                                         __nv_bfloat16* __restrict__ Ylo, long ldm,
                                                         const Scalars* sc, int bx, int nbx) {
   if (stopped(sc)) return;
@@ -77,9 +72,7 @@ __device__ __forceinline__ void update_state_split_body(long n, long m, double* 
   const long nm = n * m;
   const bool base_ok = ((m & 1) == 0) &&
                        ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(Y4) |
-                         reinterpret_cast<uintptr_t>(dY) | reinterpret_cast<uintptr_t>(G) |
-                         reinterpret_cast<uintptr_t>(Gold) | reinterpret_cast<uintptr_t>(Dir) |
-                         reinterpret_cast<uintptr_t>(Gref)) & 15) == 0 &&
+                         reinterpret_cast<uintptr_t>(dY) | reinterpret_cast<uintptr_t>(Dir)) & 15) == 0 &&
                        ((reinterpret_cast<uintptr_t>(Yhi) | reinterpret_cast<uintptr_t>(Ylo)) & 3) == 0 &&
                        (ldm & 1) == 0;
   const long units = pair_units(n, m);
@@ -88,43 +81,82 @@ __device__ __forceinline__ void update_state_split_body(long n, long m, double* 
     unit_pos(u, m, r, k);
     if (k >= m) continue;
     const long o = r * m + k;
-    const long oh = r * ldm + k, os = (n + r) * ldm + k;
+    // stack rows of dHC, dSC, HC, SC for Wannier function r
+    const long odh = r * ldm + k, ods = (n + r) * ldm + k, oh = (2 * n + r) * ldm + k, os = (3 * n + r) * ldm + k;
     if (base_ok) {  // k even, m even: the pair is complete and 16-byte aligned
       double2 C2 = *reinterpret_cast<double2*>(C + o), H2 = *reinterpret_cast<double2*>(Y4 + o);
       double2 S2 = *reinterpret_cast<double2*>(Y4 + nm + o), DH2 = *reinterpret_cast<double2*>(dY + o);
-      double2 DS2 = *reinterpret_cast<double2*>(dY + nm + o), G2 = *reinterpret_cast<double2*>(G + o);
+      double2 DS2 = *reinterpret_cast<double2*>(dY + nm + o);
       const double2 D2 = *reinterpret_cast<const double2*>(Dir + o);
       const double2 HD2 = *reinterpret_cast<const double2*>(Y4 + 2 * nm + o);
       const double2 SD2 = *reinterpret_cast<const double2*>(Y4 + 3 * nm + o);
-      const double2 R2 = *reinterpret_cast<const double2*>(Gref + o);
-      double2 O2;
-      update_element(x, C2.x, D2.x, H2.x, S2.x, HD2.x, SD2.x, DH2.x, DS2.x, G2.x, O2.x, R2.x);
-      update_element(x, C2.y, D2.y, H2.y, S2.y, HD2.y, SD2.y, DH2.y, DS2.y, G2.y, O2.y, R2.y);
+      update_element(x, C2.x, D2.x, H2.x, S2.x, HD2.x, SD2.x, DH2.x, DS2.x);
+      update_element(x, C2.y, D2.y, H2.y, S2.y, HD2.y, SD2.y, DH2.y, DS2.y);
       *reinterpret_cast<double2*>(C + o) = C2;
       *reinterpret_cast<double2*>(Y4 + o) = H2;
       *reinterpret_cast<double2*>(Y4 + nm + o) = S2;
       *reinterpret_cast<double2*>(dY + o) = DH2;
       *reinterpret_cast<double2*>(dY + nm + o) = DS2;
-      *reinterpret_cast<double2*>(G + o) = G2;
-      *reinterpret_cast<double2*>(Gold + o) = O2;
+      split_store2(DH2.x, DH2.y, Yhi, Ylo, odh);
+      split_store2(DS2.x, DS2.y, Yhi, Ylo, ods);
       split_store2(H2.x, H2.y, Yhi, Ylo, oh);
       split_store2(S2.x, S2.y, Yhi, Ylo, os);
     } else {
       for (int t = 0; t < 2 && k + t < m; ++t) {
         const long e = o + t;
-        double Cv = C[e], Hv = Y4[e], Sv = Y4[nm + e], DHv = dY[e], DSv = dY[nm + e], Gv = G[e], Ov;
-        update_element(x, Cv, Dir[e], Hv, Sv, Y4[2 * nm + e], Y4[3 * nm + e], DHv, DSv, Gv, Ov, Gref[e]);
+        double Cv = C[e], Hv = Y4[e], Sv = Y4[nm + e], DHv = dY[e], DSv = dY[nm + e];
+        update_element(x, Cv, Dir[e], Hv, Sv, Y4[2 * nm + e], Y4[3 * nm + e], DHv, DSv);
         C[e] = Cv;
         Y4[e] = Hv;
         Y4[nm + e] = Sv;
         dY[e] = DHv;
         dY[nm + e] = DSv;
-        G[e] = Gv;
-        Gold[e] = Ov;
+        split_store(DHv, Yhi, Ylo, odh + t);
+        split_store(DSv, Yhi, Ylo, ods + t);
         split_store(Hv, Yhi, Ylo, oh + t);
         split_store(Sv, Yhi, Ylo, os + t);
       }
     }
+  }
+}
+
+// H_W += x (H' + H'^T) + x^2 H''; S_W likewise (Eq. 16), on 32 x 32 tiles, and the split of
+// [S_W - S_W,ref | H_W - H_W,ref] (n x 2n) into Whi/Wlo (leading dimension ldw): the [dS_W | dH_W]
+// columns of the gradient GEMM's A operand
+__device__ __forceinline__ void update_subspace_split_body(int n, double* SWHW, const double* __restrict__ Proj,
+                                                           const double* __restrict__ Wref,
+                                                           __nv_bfloat16* __restrict__ Whi,
+                                                           __nv_bfloat16* __restrict__ Wlo, long ldw,
+                                                           const Scalars* sc, int bx_, int nbx_) {
+  if (stopped(sc)) return;
+  const double x = sc->x, x2 = x * x;
+  const int tiles = (n + 31) / 32;
+  const int I = bx_ / tiles, J = bx_ % tiles;
+  __shared__ double tH1[32][33], tS1[32][33];
+  const long l2 = 2L * n, l4 = 4L * n;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int gi = J * 32 + r, gj = I * 32 + tx;
+    const bool ok = gi < n && gj < n;
+    tH1[r][tx] = ok ? Proj[(long)gi * l4 + gj] : 0.0;
+    tS1[r][tx] = ok ? Proj[(long)gi * l4 + n + gj] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int gi = I * 32 + r, gj = J * 32 + tx;
+    if (gi >= n || gj >= n) continue;
+    const double* pr = Proj + (long)gi * l4;
+    const double h = pr[gj] + tH1[tx][r];
+    const double s = pr[n + gj] + tS1[tx][r];
+    double* sw = SWHW + (long)gi * l2 + gj;
+    double* hw = sw + n;
+    const double hn = fma(x2, pr[2L * n + gj], fma(x, h, *hw));
+    const double sn = fma(x2, pr[3L * n + gj], fma(x, s, *sw));
+    *hw = hn;
+    *sw = sn;
+    const double* wr = Wref + (long)gi * l2 + gj;
+    split_store(sn - wr[0], Whi, Wlo, (long)gi * ldw + gj);
+    split_store(hn - wr[n], Whi, Wlo, (long)gi * ldw + n + gj);
   }
 }
 

@@ -230,6 +230,28 @@ __device__ __forceinline__ void direction_body(long count, const double* __restr
   for (long i = bx_ * (long)blockDim.x + threadIdx.x; i < count; i += (long)nbx_ * blockDim.x)
     Dir[i] = (beta != 0.0) ? fma(beta, Dir[i], -PG[i]) : -PG[i];
 }
+// float64 -> float32 on the integer pipe, truncating the fraction; magnitudes below the float32
+// normal range become zero (the float64 units of this GPU retire about two lanes per SM and clock,
+// so even conversions are kept off them where 2^-23 relative accuracy is enough)
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7FFu);
+  if (e < 1023 - 126) return __uint_as_float(sign);
+  if (e > 1023 + 127) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)((u >> 29) & 0x7FFFFFu));
+}
+
+// The trace products of Eq. 13, Tr(XY) = sum_ij X_ij Y_ji, on 32x32 tiles
+// with the transposed tiles staged in shared memory.
+//   SWHW = [S_W | H_W] (n x 2n), Proj = [H' | S' | H'' | S''] (n x 4n).
+//   t0 Tr H'        t1 Tr(S' H_W)   t2 Tr(S_W H')   t3 Tr H''
+//   t4 Tr(S'' H_W)  t5 Tr(S_W H'')  t6 Tr(S' H')    t7 Tr(S'^T H')
+//   t8 Tr(S'' H')   t9 Tr(S' H'')   t10 Tr(S'' H'')
+// F32: the nine product traces multiply float32 copies of the elements (truncated on the integer
+// pipe) and sum each thread's four products in float32 before the float64 block sums: about 2^-22
+// of each term, far below the error of the tensor-core projections they come from (mixed path).
+template <bool F32>
 __device__ __forceinline__ void traces_body(int n, const double* __restrict__ SWHW, const double* __restrict__ Proj,
               double* part, const Scalars* sc, int bx_, int nbx_) {
   if (stopped(sc)) return;
@@ -250,6 +272,9 @@ __device__ __forceinline__ void traces_body(int n, const double* __restrict__ SW
   double t[kNumTraces];
 #pragma unroll
   for (int q = 0; q < kNumTraces; ++q) t[q] = 0.0;
+  float f[kNumTraces];
+#pragma unroll
+  for (int q = 0; q < kNumTraces; ++q) f[q] = 0.0f;
   for (int r = ty; r < 32; r += 8) {
     const int gi = I * 32 + r, gj = J * 32 + tx;
     if (gi >= n || gj >= n) continue;
@@ -263,15 +288,34 @@ __device__ __forceinline__ void traces_body(int n, const double* __restrict__ SW
       t[0] += h1;
       t[3] += Proj[(long)gi * l4 + 2L * n + gj];
     }
-    t[1] = fma(s1, hwT, t[1]);
-    t[2] = fma(sw, h1T, t[2]);
-    t[4] = fma(s2, hwT, t[4]);
-    t[5] = fma(sw, h2T, t[5]);
-    t[6] = fma(s1, h1T, t[6]);
-    t[7] = fma(s1, h1, t[7]);   // Tr(S'^T H') = sum_ij S'_ij H'_ij
-    t[8] = fma(s2, h1T, t[8]);
-    t[9] = fma(s1, h2T, t[9]);
-    t[10] = fma(s2, h2T, t[10]);
+    if (F32) {
+      const float fs1 = f32_trunc(s1), fsw = f32_trunc(sw), fs2 = f32_trunc(s2), fh1 = f32_trunc(h1);
+      const float fhwT = f32_trunc(hwT), fh1T = f32_trunc(h1T), fh2T = f32_trunc(h2T);
+      f[1] = fmaf(fs1, fhwT, f[1]);
+      f[2] = fmaf(fsw, fh1T, f[2]);
+      f[4] = fmaf(fs2, fhwT, f[4]);
+      f[5] = fmaf(fsw, fh2T, f[5]);
+      f[6] = fmaf(fs1, fh1T, f[6]);
+      f[7] = fmaf(fs1, fh1, f[7]);
+      f[8] = fmaf(fs2, fh1T, f[8]);
+      f[9] = fmaf(fs1, fh2T, f[9]);
+      f[10] = fmaf(fs2, fh2T, f[10]);
+    } else {
+      t[1] = fma(s1, hwT, t[1]);
+      t[2] = fma(sw, h1T, t[2]);
+      t[4] = fma(s2, hwT, t[4]);
+      t[5] = fma(sw, h2T, t[5]);
+      t[6] = fma(s1, h1T, t[6]);
+      t[7] = fma(s1, h1, t[7]);   // Tr(S'^T H') = sum_ij S'_ij H'_ij
+      t[8] = fma(s2, h1T, t[8]);
+      t[9] = fma(s1, h2T, t[9]);
+      t[10] = fma(s2, h2T, t[10]);
+    }
+  }
+  if (F32) {
+#pragma unroll
+    for (int q = 0; q < kNumTraces; ++q)
+      if (q != 0 && q != 3) t[q] = (double)f[q];
   }
   __shared__ double sh[kNumTraces][TB / 32];
   block_sum<kNumTraces>(t, sh);

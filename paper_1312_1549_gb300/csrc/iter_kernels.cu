@@ -51,8 +51,8 @@ grad_reduce_kernel(long count, const double* __restrict__ G, const double* __res
 
 // Polak-Ribiere coefficient and the stopping tests (one block).
 __global__ void __launch_bounds__(TB)
-control_direction_kernel(Scalars* sc, const double* part, int mixed) {
-  control_direction_body(sc, part, mixed, kReduceBlocks, blockIdx.x, gridDim.x);
+control_direction_kernel(Scalars* sc, const double* part, int mixed, int nparts) {
+  control_direction_body(sc, part, mixed, nparts, blockIdx.x, gridDim.x);
 }
 
 
@@ -68,10 +68,11 @@ __global__ void direction_kernel(long count, const double* __restrict__ PG, doub
 //   t0 Tr H'        t1 Tr(S' H_W)   t2 Tr(S_W H')   t3 Tr H''
 //   t4 Tr(S'' H_W)  t5 Tr(S_W H'')  t6 Tr(S' H')    t7 Tr(S'^T H')
 //   t8 Tr(S'' H')   t9 Tr(S' H'')   t10 Tr(S'' H'')
+template <bool F32>
 __global__ void __launch_bounds__(TB)
 traces_kernel(int n, const double* __restrict__ SWHW, const double* __restrict__ Proj,
               double* part, const Scalars* sc) {
-  traces_body(n, SWHW, Proj, part, sc, blockIdx.x, gridDim.x);
+  traces_body<F32>(n, SWHW, Proj, part, sc, blockIdx.x, gridDim.x);
 }
 
 
@@ -252,8 +253,8 @@ void launch_grad_reduce(cudaStream_t st, long count, const double* G, const doub
   grad_reduce_kernel<<<kReduceBlocks, TB, 0, st>>>(count, G, PG, Gold, Dir, part, sc);
   OMM_LAUNCH_CHECK();
 }
-void launch_control_direction(cudaStream_t st, Scalars* sc, const double* part, int mixed) {
-  control_direction_kernel<<<1, TB, 0, st>>>(sc, part, mixed);
+void launch_control_direction(cudaStream_t st, Scalars* sc, const double* part, int mixed, int nparts) {
+  control_direction_kernel<<<1, TB, 0, st>>>(sc, part, mixed, nparts);
   OMM_LAUNCH_CHECK();
 }
 void launch_direction(cudaStream_t st, long count, const double* PG, double* Dir, const Scalars* sc) {
@@ -265,8 +266,9 @@ int traces_blocks(int n) {
   return t * t;
 }
 void launch_traces(cudaStream_t st, int n, const double* SWHW, const double* Proj, double* part,
-                   const Scalars* sc) {
-  traces_kernel<<<traces_blocks(n), TB, 0, st>>>(n, SWHW, Proj, part, sc);
+                   const Scalars* sc, bool fp32_products) {
+  if (fp32_products) traces_kernel<true><<<traces_blocks(n), TB, 0, st>>>(n, SWHW, Proj, part, sc);
+  else traces_kernel<false><<<traces_blocks(n), TB, 0, st>>>(n, SWHW, Proj, part, sc);
   OMM_LAUNCH_CHECK();
 }
 void launch_control_linesearch(cudaStream_t st, Scalars* sc, const double* part, int nblocks) {
@@ -285,10 +287,14 @@ direction_split_kernel(long n, long m, const double* __restrict__ PG, double* __
   dev::direction_split_body(n, m, PG, Dir, hi, lo, ldm, sc, blockIdx.x, gridDim.x);
 }
 __global__ void __launch_bounds__(256)
-update_state_split_kernel(long n, long m, double* C, double* Y4, const double* Dir, double* G, double* Gold,
-                          double* dY, const double* Gref, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, long ldm,
-                          const Scalars* sc) {
-  dev::update_state_split_body(n, m, C, Y4, Dir, G, Gold, dY, Gref, Yhi, Ylo, ldm, sc, blockIdx.x, gridDim.x);
+update_state_split_kernel(long n, long m, double* C, double* Y4, const double* Dir, double* dY, __nv_bfloat16* Yhi,
+                          __nv_bfloat16* Ylo, long ldm, const Scalars* sc) {
+  dev::update_state_split_body(n, m, C, Y4, Dir, dY, Yhi, Ylo, ldm, sc, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(TB)
+update_subspace_split_kernel(int n, double* SWHW, const double* __restrict__ Proj, const double* __restrict__ Wref,
+                             __nv_bfloat16* Whi, __nv_bfloat16* Wlo, long ldw, const Scalars* sc) {
+  dev::update_subspace_split_body(n, SWHW, Proj, Wref, Whi, Wlo, ldw, sc, blockIdx.x, gridDim.x);
 }
 }  // namespace
 
@@ -303,10 +309,14 @@ void launch_direction_split(cudaStream_t st, long n, long m, const double* PG, d
   direction_split_kernel<<<pair_grid(n, m), 256, 0, st>>>(n, m, PG, Dir, hi, lo, ldm, sc);
   OMM_LAUNCH_CHECK();
 }
-void launch_update_state_split(cudaStream_t st, long n, long m, double* C, double* Y4, const double* Dir, double* G,
-                               double* Gold, double* dY, const double* Gref, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo,
-                               long ldm, const Scalars* sc) {
-  update_state_split_kernel<<<pair_grid(n, m), 256, 0, st>>>(n, m, C, Y4, Dir, G, Gold, dY, Gref, Yhi, Ylo, ldm, sc);
+void launch_update_state_split(cudaStream_t st, long n, long m, double* C, double* Y4, const double* Dir, double* dY,
+                               __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, long ldm, const Scalars* sc) {
+  update_state_split_kernel<<<pair_grid(n, m), 256, 0, st>>>(n, m, C, Y4, Dir, dY, Yhi, Ylo, ldm, sc);
+  OMM_LAUNCH_CHECK();
+}
+void launch_update_subspace_split(cudaStream_t st, int n, double* SWHW, const double* Proj, const double* Wref,
+                                  __nv_bfloat16* Whi, __nv_bfloat16* Wlo, long ldw, const Scalars* sc) {
+  update_subspace_split_kernel<<<traces_blocks(n), TB, 0, st>>>(n, SWHW, Proj, Wref, Whi, Wlo, ldw, sc);
   OMM_LAUNCH_CHECK();
 }
 void launch_update_subspace(cudaStream_t st, int n, double* SWHW, const double* Proj, const Scalars* sc) {

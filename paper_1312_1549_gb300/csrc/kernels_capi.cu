@@ -242,9 +242,65 @@ omm_status gemm_tc_impl(const char* name, int M, int N, int K, const double* A, 
   return rc;
 }
 
+// C = alpha A B + beta C with B stored K x N (row-major): the B operand is read MN-major, as the
+// solver's gradient GEMM reads its operand stack
+omm_status gemm_tc_kn_impl(const char* name, int M, int N, int K, const double* A, const double* B, double alpha,
+                           double beta, double* C, int tile_n, void* stream) {
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || (tile_n != 128 && tile_n != 256)) {
+    set_last_error(std::string(name) + ": invalid argument");
+    return OMM_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const long lda = (K + 7) / 8 * 8, ldb = (N + 7) / 8 * 8;
+  __nv_bfloat16* buf = nullptr;
+  int* err = nullptr;
+  tc::GroupDesc* desc = nullptr;
+  omm_status rc = OMM_OK;
+  try {
+    const size_t na = (size_t)M * lda, nb = (size_t)K * ldb;
+    if (cudaMalloc((void**)&buf, 2 * (na + nb) * sizeof(__nv_bfloat16)) != cudaSuccess ||
+        cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&desc, sizeof(tc::GroupDesc)) != cudaSuccess) {
+      cudaGetLastError();
+      if (buf) cudaFree(buf);
+      if (err) cudaFree(err);
+      set_last_error(std::string(name) + ": device allocation failed");
+      return OMM_ERR_OOM;
+    }
+    __nv_bfloat16 *a_hi = buf, *a_lo = buf + na, *b_hi = buf + 2 * na, *b_lo = buf + 2 * na + nb;
+    OMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    tc::split(st, A, M, K, K, a_hi, a_lo, lda, nullptr);
+    tc::split(st, B, K, N, N, b_hi, b_lo, ldb, nullptr);
+    tc::Operand oa = tc::make_operand(a_hi, M, K, lda, 2, true);
+    tc::Operand ob = tc::make_operand_view(b_hi, K, N, ldb, 2, false, 0, K, /*mn_major=*/true);
+    const tc::Epilogue ep{C, N, N, 0, alpha, beta, M, N, nullptr, err};
+    const tc::GroupDesc g = tc::make_group(oa, ob, K, ep, 0, tile_n, nullptr);
+    OMM_CUDA_TRY(cudaMemcpyAsync(desc, &g, sizeof(g), cudaMemcpyHostToDevice, st));
+    tc::gemm_persistent(st, desc, 1, tc::tiles_of(ep, tile_n), tc::pairs_split3(), err, tile_n);
+    int h = 0;
+    OMM_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OMM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h != 0) {
+      set_last_error(std::string(name) + ": a bounded device wait expired (code " + std::to_string(h) + ")");
+      rc = OMM_ERR_TIMEOUT;
+    }
+  } catch (const CudaError& e) {
+    rc = cuda_fail(name, e);
+  }
+  if (buf) cudaFree(buf);
+  if (err) cudaFree(err);
+  if (desc) cudaFree(desc);
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
+
+omm_status omm_kernel_gemm_tc_kn(int M, int N, int K, const double* A, const double* B, double alpha, double beta,
+                                 double* C, int tile_n, void* stream) {
+  return gemm_tc_kn_impl("omm_kernel_gemm_tc_kn", M, N, K, A, B, alpha, beta, C, tile_n, stream);
+}
 
 omm_status omm_kernel_gemm_tc_tiled(int M, int N, int K, const double* A, const double* B, double alpha,
                                     double beta, double* C, int npass, int tile_n, void* stream) {

@@ -22,22 +22,23 @@ namespace omm {
 
 struct MixedState {
   int m = 0, n = 0;
-  long ldm = 0, ld2n = 0;
+  long ldm = 0, ld4n = 0;
   bool precond = false;
   int npass = 3;
   __nv_bfloat16 *HS_hi = nullptr, *HS_lo = nullptr;   // [H~; S]   2m x m
   __nv_bfloat16 *P_hi = nullptr, *P_lo = nullptr;     // P         m x m
   __nv_bfloat16 *G_hi = nullptr, *G_lo = nullptr;     // G         n x m
   __nv_bfloat16 *D_hi = nullptr, *D_lo = nullptr;     // Delta     n x m
-  __nv_bfloat16 *Y_hi = nullptr, *Y_lo = nullptr;     // [HC;SC;HD;SD]  4n x m
-  __nv_bfloat16 *YT_hi = nullptr, *YT_lo = nullptr;   // [HC_mn | SC_mn | dHC_mn | dSC_mn] m x 4n
-  __nv_bfloat16 *W_hi = nullptr, *W_lo = nullptr;     // [dS_W | dH_W | S_W,ref | H_W,ref] n x 4n
+  __nv_bfloat16 *Y_hi = nullptr, *Y_lo = nullptr;     // [dHC; dSC; HC; SC; HD; SD]  6n x m
+  __nv_bfloat16 *W_hi = nullptr, *W_lo = nullptr;     // [S_W,ref | H_W,ref | dS_W | dH_W] n x 4n
   double* Gref = nullptr;                              // G at the last refresh, n x m
   double* dY = nullptr;                                // [HC - HC_ref; SC - SC_ref], 2n x m
   double* Wref = nullptr;                              // [S_W | H_W] at the last refresh, n x 2n
-  tc::Operand opHS, opP, opG, opD, opY, opYT, opW;
+  double* red = nullptr;                               // per (tile, warp) sums of the P G epilogue
+  tc::Operand opHS, opP, opG, opD, opYproj, opYgrad, opYhc, opW;
   tc::BlockLists hs_blocks[2];  // block sparsity of [H~; S] for 256- and 128-row blocks (Sec. 2.6)
   int* err = nullptr;
+  int expire = 0;  // tests: the first line-search GEMM of every line search waits on nothing and expires
   // the four line-search GEMMs as persistent-launch descriptors (device), built on first use
   tc::GroupDesc* plans = nullptr;
   int plan_tiles[4] = {0, 0, 0, 0};
@@ -67,9 +68,9 @@ MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const 
     ms->m = m;
     ms->n = n;
     ms->ldm = round8(m);
-    ms->ld2n = round8(4L * n);  // leading dimension of the 4n-wide gradient operands
+    ms->ld4n = round8(4L * n);  // leading dimension of the n x 4n gradient operand W
     ms->precond = (P != nullptr);
-    const long ldm = ms->ldm, ld2n = ms->ld2n;
+    const long ldm = ms->ldm, ld4n = ms->ld4n;
     // each split operand is one allocation holding the stack [hi; lo]
     auto pair = [](__nv_bfloat16** hi, __nv_bfloat16** lo, long rows, long ld) {
       alloc(hi, 2 * (size_t)rows * ld);
@@ -79,25 +80,31 @@ MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const 
     if (ms->precond) pair(&ms->P_hi, &ms->P_lo, m, ldm);
     pair(&ms->G_hi, &ms->G_lo, n, ldm);
     pair(&ms->D_hi, &ms->D_lo, n, ldm);
-    pair(&ms->Y_hi, &ms->Y_lo, 4L * n, ldm);
-    pair(&ms->YT_hi, &ms->YT_lo, m, ld2n);
-    pair(&ms->W_hi, &ms->W_lo, n, ld2n);
+    pair(&ms->Y_hi, &ms->Y_lo, 6L * n, ldm);
+    pair(&ms->W_hi, &ms->W_lo, n, ld4n);
     alloc(&ms->Gref, (size_t)n * m);
     alloc(&ms->dY, 2L * n * m);
     alloc(&ms->Wref, 2L * n * n);
+    alloc(&ms->red, (size_t)16 * ((n + 127) / 128) * ((m + 127) / 128));  // 4 warps x 4 sums per 128 x 128 tile
     alloc(&ms->err, 1);
     OMM_CUDA_TRY(cudaMemsetAsync(ms->err, 0, sizeof(int), st));
+    OMM_CUDA_TRY(cudaMemsetAsync(ms->red, 0, (size_t)16 * ((n + 127) / 128) * ((m + 127) / 128) * sizeof(double), st));
     // padding columns stay zero (the tensor maps never read them, but keep them defined)
-    OMM_CUDA_TRY(cudaMemsetAsync(ms->YT_hi, 0, 2 * (size_t)m * ld2n * 2, st));
+    OMM_CUDA_TRY(cudaMemsetAsync(ms->Y_hi, 0, 2 * (size_t)6 * n * ldm * 2, st));
+    OMM_CUDA_TRY(cudaMemsetAsync(ms->W_hi, 0, 2 * (size_t)n * ld4n * 2, st));
     tc::split(st, HS, 2L * m, m, m, ms->HS_hi, ms->HS_lo, ldm, nullptr);
     if (ms->precond) tc::split(st, P, m, m, m, ms->P_hi, ms->P_lo, ldm, nullptr);
     ms->opHS = tc::make_operand(ms->HS_hi, 2L * m, m, ldm, 2, false);
     if (ms->precond) ms->opP = tc::make_operand(ms->P_hi, m, m, ldm, 2, false);
     ms->opG = tc::make_operand(ms->G_hi, n, m, ldm, 2, true);
     ms->opD = tc::make_operand(ms->D_hi, n, m, ldm, 2, true);
-    ms->opY = tc::make_operand(ms->Y_hi, 4L * n, m, ldm, 2, false);
-    ms->opYT = tc::make_operand(ms->YT_hi, m, 4L * n, ld2n, 2, false);
-    ms->opW = tc::make_operand(ms->W_hi, n, 4L * n, ld2n, 2, true);
+    // views of the stack [dHC; dSC; HC; SC; HD; SD]: the projections read [HC; SC; HD; SD] as
+    // K-major rows, the gradient [dHC; dSC; HC; SC] as MN-major rows (its contracted index), the
+    // initial S_W, H_W product [HC; SC]
+    ms->opYproj = tc::make_operand_view(ms->Y_hi, 6L * n, m, ldm, 2, false, 2 * n, 4L * n);
+    ms->opYgrad = tc::make_operand_view(ms->Y_hi, 6L * n, m, ldm, 2, false, 0, 4L * n, true);
+    ms->opYhc = tc::make_operand_view(ms->Y_hi, 6L * n, m, ldm, 2, false, 2 * n, 2L * n);
+    ms->opW = tc::make_operand(ms->W_hi, n, 4L * n, ld4n, 2, true);
     // finite-range H and S: the operator product skips the K blocks where [H~; S] is zero
     tc::block_lists(st, HS, 2L * m, m, m, 256, ms->hs_blocks[0]);
     tc::block_lists(st, HS, 2L * m, m, m, 128, ms->hs_blocks[1]);
@@ -114,24 +121,33 @@ void mixed_tuning(const MixedState* ms, int bn[4], double* ms_autotune) {
   *ms_autotune = ms->ms_autotune;
 }
 
+void mixed_set_expire(MixedState* ms, int on) {
+  ms->expire = on;
+  ms->plan_sc = nullptr;  // rebuild the plans with the flag
+}
+
+void mixed_reset_error(MixedState* ms, cudaStream_t st) {
+  OMM_CUDA_TRY(cudaMemsetAsync(ms->err, 0, sizeof(int), st));
+}
+
 MixedView mixed_view(MixedState* ms) {
   MixedView v;
   v.ldm = ms->ldm;
-  v.ld4 = ms->ld2n;
+  v.ld4 = ms->ld4n;
   v.G_hi = ms->G_hi;
   v.D_hi = ms->D_hi;
   v.Y_hi = ms->Y_hi;
-  v.YT_hi = ms->YT_hi;
   v.W_hi = ms->W_hi;
   v.Gref = ms->Gref;
   v.dY = ms->dY;
   v.Wref = ms->Wref;
+  v.red = ms->red;
   v.opHS = &ms->opHS;
   v.opP = &ms->opP;
   v.opG = &ms->opG;
   v.opD = &ms->opD;
-  v.opY = &ms->opY;
-  v.opYT = &ms->opYT;
+  v.opYproj = &ms->opYproj;
+  v.opYgrad = &ms->opYgrad;
   v.opW = &ms->opW;
   v.err = ms->err;
   v.hs_blocks = ms->hs_blocks;
@@ -148,13 +164,12 @@ void mixed_update_H(MixedState* ms, cudaStream_t st, const double* HS) {
 
 void mixed_destroy(MixedState* ms) {
   if (!ms) return;
-  __nv_bfloat16* bufs[] = {ms->HS_hi, ms->P_hi, ms->G_hi, ms->D_hi, ms->Y_hi, ms->YT_hi, ms->W_hi};
+  __nv_bfloat16* bufs[] = {ms->HS_hi, ms->P_hi, ms->G_hi, ms->D_hi, ms->Y_hi, ms->W_hi};
   for (auto* b : bufs)
     if (b) cudaFree(b);
+  for (double* d : {ms->Gref, ms->dY, ms->Wref, ms->red})
+    if (d) cudaFree(d);
   if (ms->err) cudaFree(ms->err);
-  if (ms->Gref) cudaFree(ms->Gref);
-  if (ms->dY) cudaFree(ms->dY);
-  if (ms->Wref) cudaFree(ms->Wref);
   if (ms->plans) cudaFree(ms->plans);
   tc::free_block_lists(ms->hs_blocks[0]);
   tc::free_block_lists(ms->hs_blocks[1]);
@@ -168,45 +183,98 @@ int mixed_error(MixedState* ms, cudaStream_t st) {
   return e;
 }
 
-// after a float64 recompute: the new reference point of the incremental gradient
+// The epilogues of the four line-search GEMMs (shared by the single and the batched solve):
+//   [0] P G            PG, plus the sums <G,PG>, <G_old,PG>, <G,Delta_old>, max|G| per (tile, warp)
+//                      into ms->red, and G_old <- G
+//   [1] [H D; S D]     into Y4 rows [2n, 4n), and their bf16 split into the stack rows [4n, 6n)
+//   [2] projections    [H' | S' | H'' | S''] into Proj
+//   [3] gradient       G = G_ref + 8 dHC - 4 [..] [..], and its split (the next P G's operand)
+void mixed_epilogues(MixedState* ms, const Scalars* sc, double* G, double* Gold, const double* Dir, double* PG,
+                     double* Y4, double* Proj, tc::Epilogue out[4]) {
+  const int m = ms->m, n = ms->n;
+  const long nm = (long)n * m, ldm = ms->ldm;
+  const int* skip = &sc->done;
+  tc::Epilogue epg{PG, m, m, 0, 1.0, 0.0, n, m, skip, ms->err};
+  epg.mode = tc::kEpReduce;
+  epg.x0 = G;
+  epg.x1 = Gold;
+  epg.x2 = Dir;
+  epg.xout = Gold;
+  epg.part = ms->red;
+  epg.sc = sc;
+  tc::Epilogue ehd{Y4 + 2 * nm, m, m, nm, 1.0, 0.0, n, 2 * m, skip, ms->err};
+  ehd.bf_hi = ms->Y_hi + 4L * n * ldm;
+  ehd.bf_ld = ldm;
+  ehd.bf_blk = (long)n * ldm;
+  ehd.bf_lo = 6L * n * ldm;
+  const tc::Epilogue epr{Proj, 4L * n, 4L * n, 0, 1.0, 0.0, n, 4 * n, skip, ms->err};
+  tc::Epilogue eg{G, m, m, 0, -4.0, 0.0, n, m, skip, ms->err};
+  eg.mode = tc::kEpGrad;
+  eg.x0 = ms->Gref;
+  eg.x1 = ms->dY;
+  eg.xs = 8.0;
+  eg.bf_hi = ms->G_hi;
+  eg.bf_ld = ldm;
+  eg.bf_lo = (long)n * ldm;
+  out[0] = epg;
+  out[1] = ehd;
+  out[2] = epr;
+  out[3] = eg;
+  if (ms->expire) out[ms->precond ? 0 : 1].expire = 1;
+}
+
+// after a float64 recompute: the new reference point of the incremental gradient (G_ref = G,
+// W_ref = [S_W | H_W], dHC = dSC = 0) and the bf16 operands of the next line search
 void mixed_sync_state(MixedState* ms, cudaStream_t st, const double* Y4, const double* SWHW, const double* G) {
   const int m = ms->m, n = ms->n;
-  const long ld4 = ms->ld2n;
+  const long ldm = ms->ldm, ld4 = ms->ld4n;
   OMM_CUDA_TRY(cudaMemcpyAsync(ms->Gref, G, (size_t)n * m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   OMM_CUDA_TRY(cudaMemcpyAsync(ms->Wref, SWHW, 2L * n * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   OMM_CUDA_TRY(cudaMemsetAsync(ms->dY, 0, 2L * n * m * sizeof(double), st));
-  tc::split(st, Y4, 2L * n, m, m, ms->Y_hi, ms->Y_lo, ms->ldm, nullptr);
-  tc::split_transposed(st, Y4, 2L * n, m, m, ms->YT_hi, ms->YT_lo, ld4, nullptr);
-  tc::split_transposed(st, ms->dY, 2L * n, m, m, ms->YT_hi + 2L * n, ms->YT_lo + 2L * n, ld4, nullptr);
-  tc::split_diff(st, SWHW, ms->Wref, n, 2L * n, 2L * n, ms->W_hi, ms->W_lo, ld4, nullptr);
-  tc::split(st, ms->Wref, n, 2L * n, 2L * n, ms->W_hi + 2L * n, ms->W_lo + 2L * n, ld4, nullptr);
+  // stack rows [0, 2n): split of dHC = dSC = 0; rows [2n, 4n): split of [HC; SC]
+  OMM_CUDA_TRY(cudaMemsetAsync(ms->Y_hi, 0, 2L * n * ldm * sizeof(__nv_bfloat16), st));
+  OMM_CUDA_TRY(cudaMemsetAsync(ms->Y_lo, 0, 2L * n * ldm * sizeof(__nv_bfloat16), st));
+  tc::split(st, Y4, 2L * n, m, m, ms->Y_hi + 2L * n * ldm, ms->Y_lo + 2L * n * ldm, ldm, nullptr);
+  // W = [S_W,ref | H_W,ref | dS_W | dH_W] with dS_W = dH_W = 0
+  tc::split(st, ms->Wref, n, 2L * n, 2L * n, ms->W_hi, ms->W_lo, ld4, nullptr);
+  tc::split_diff(st, SWHW, ms->Wref, n, 2L * n, 2L * n, ms->W_hi + 2L * n, ms->W_lo + 2L * n, ld4, nullptr);
+  tc::split(st, G, n, m, m, ms->G_hi, ms->G_lo, ldm, nullptr);
 }
 
 // The initial state (HC, SC, S_W, H_W, E~, G and max|G|) on the tensor cores.
 // Its split-product error only has to stay below the first round's target
 // (refine_ratio of the starting gradient); every later refresh and the
-// certificate are float64.
+// certificate are float64-class.
 void mixed_recompute_state(MixedState* ms, cudaStream_t st, Scalars* sc, const double* C, double* Y4,
                            double* SWHW, double* G, double* part, double* part2) {
   const int m = ms->m, n = ms->n;
-  const long nm = (long)n * m, ld4 = ms->ld2n;
-  tc::split(st, C, n, m, m, ms->D_hi, ms->D_lo, ms->ldm, nullptr);
+  const long nm = (long)n * m, ldm = ms->ldm, ld4 = ms->ld4n;
+  tc::split(st, C, n, m, m, ms->D_hi, ms->D_lo, ldm, nullptr);
   tc::gemm(st, ms->opD, ms->opHS, m, ms->npass, tc::Epilogue{Y4, m, m, nm, 1.0, 0.0, n, 2 * m, nullptr, ms->err});
-  tc::split(st, Y4, 2L * n, m, m, ms->Y_hi, ms->Y_lo, ms->ldm, nullptr);
+  tc::split(st, Y4, 2L * n, m, m, ms->Y_hi + 2L * n * ldm, ms->Y_lo + 2L * n * ldm, ldm, nullptr);
   // [H_W | S_W] = C [HC; SC]^T written as SWHW = [S_W | H_W]
-  tc::gemm(st, ms->opD, ms->opY, m, ms->npass,
+  tc::gemm(st, ms->opD, ms->opYhc, m, ms->npass,
            tc::Epilogue{SWHW + n, 2L * n, n, -(long)n, 1.0, 0.0, n, 2 * n, nullptr, ms->err});
   launch_functional(st, n, SWHW, part2);
   launch_finish_functional(st, sc, part2, traces_blocks(n));
-  // G = 8 HC - 4 [S_W | H_W] [HC; SC]: the incremental GEMM about a zero reference
+  // G = 8 HC - 4 [S_W | H_W] [HC; SC]: the incremental gradient about the zero point (G_ref = 0,
+  // W_ref = 0, dHC = HC, dSC = SC), so that W = [0 | 0 | S_W | H_W] and the stack rows [0, 2n)
+  // hold the split of [HC; SC] too
+  OMM_CUDA_TRY(cudaMemsetAsync(ms->Gref, 0, (size_t)nm * sizeof(double), st));
   OMM_CUDA_TRY(cudaMemsetAsync(ms->Wref, 0, 2L * n * n * sizeof(double), st));
   OMM_CUDA_TRY(cudaMemcpyAsync(ms->dY, Y4, 2L * nm * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  launch_scale_copy(st, nm, Y4, 8.0, G, nullptr);
-  tc::split_transposed(st, Y4, 2L * n, m, m, ms->YT_hi, ms->YT_lo, ld4, nullptr);
-  tc::split_transposed(st, ms->dY, 2L * n, m, m, ms->YT_hi + 2L * n, ms->YT_lo + 2L * n, ld4, nullptr);
-  tc::split(st, SWHW, n, 2L * n, 2L * n, ms->W_hi, ms->W_lo, ld4, nullptr);
-  tc::split(st, ms->Wref, n, 2L * n, 2L * n, ms->W_hi + 2L * n, ms->W_lo + 2L * n, ld4, nullptr);
-  tc::gemm(st, ms->opW, ms->opYT, 4 * n, ms->npass, tc::Epilogue{G, m, m, 0, -4.0, 1.0, n, m, nullptr, ms->err});
+  OMM_CUDA_TRY(cudaMemcpyAsync(ms->Y_hi, ms->Y_hi + 2L * n * ldm, 2L * n * ldm * sizeof(__nv_bfloat16),
+                               cudaMemcpyDeviceToDevice, st));
+  OMM_CUDA_TRY(cudaMemcpyAsync(ms->Y_lo, ms->Y_lo + 2L * n * ldm, 2L * n * ldm * sizeof(__nv_bfloat16),
+                               cudaMemcpyDeviceToDevice, st));
+  tc::split(st, ms->Wref, n, 2L * n, 2L * n, ms->W_hi, ms->W_lo, ld4, nullptr);
+  tc::split(st, SWHW, n, 2L * n, 2L * n, ms->W_hi + 2L * n, ms->W_lo + 2L * n, ld4, nullptr);
+  tc::Epilogue eg{G, m, m, 0, -4.0, 0.0, n, m, nullptr, ms->err};
+  eg.mode = tc::kEpGrad;
+  eg.x0 = ms->Gref;
+  eg.x1 = ms->dY;
+  eg.xs = 8.0;
+  tc::gemm_persistent(st, ms->opW, ms->opYgrad, 4 * n, tc::pairs_split3(), eg);
   launch_gmax(st, nm, G, part);
   launch_finish_gmax(st, sc, part);
 }
@@ -215,23 +283,19 @@ namespace {
 
 enum { kPlanPG = 0, kPlanHD, kPlanProj, kPlanG };
 
-void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double* PG, double* Y4, double* Proj) {
+void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double* Gold, const double* Dir,
+                 double* PG, double* Y4, double* Proj) {
   const int m = ms->m, n = ms->n;
-  const long nm = (long)n * m;
-  const int* skip = &sc->done;
   tc::GroupDesc h[4] = {};
-  const tc::Epilogue epg{PG, m, m, 0, 1.0, 0.0, n, m, skip, ms->err};
-  const tc::Epilogue ehd{Y4 + 2 * nm, m, m, nm, 1.0, 0.0, n, 2 * m, skip, ms->err};
-  const tc::Epilogue epr{Proj, 4L * n, 4L * n, 0, 1.0, 0.0, n, 4 * n, skip, ms->err};
-  const tc::Epilogue eg{G, m, m, 0, -4.0, 1.0, n, m, skip, ms->err};
+  tc::Epilogue ep[4];
+  mixed_epilogues(ms, sc, G, Gold, Dir, PG, Y4, Proj, ep);
   const tc::Operand* opA[4] = {&ms->opG, &ms->opD, &ms->opD, &ms->opW};
-  const tc::Operand* opB[4] = {ms->precond ? &ms->opP : &ms->opG, &ms->opHS, &ms->opY, &ms->opYT};
+  const tc::Operand* opB[4] = {ms->precond ? &ms->opP : &ms->opG, &ms->opHS, &ms->opYproj, &ms->opYgrad};
   const int K[4] = {m, m, m, 4 * n};
-  const tc::Epilogue* ep[4] = {&epg, &ehd, &epr, &eg};
   for (int k = ms->precond ? 0 : 1; k < 4; ++k) {  // without P there is no P G product
     // output tile width from the autotuner (timed once per shape in a process); the operator
     // product runs block-sparse over [H~; S]
-    tc::GemmSpec spec{opA[k], opB[k], K[k], *ep[k]};
+    tc::GemmSpec spec{opA[k], opB[k], K[k], ep[k]};
     if (k == kPlanHD) {
       spec.sparse[0] = &ms->hs_blocks[0];
       spec.sparse[1] = &ms->hs_blocks[1];
@@ -239,9 +303,9 @@ void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double
     double ms_tune = 0.0;
     ms->plan_bn[k] = tc::choose_tile_width(st, {spec}, tc::pairs_split3(), &ms_tune);
     ms->ms_autotune += ms_tune;
-    h[k] = tc::make_group(*opA[k], *opB[k], K[k], *ep[k], 0, ms->plan_bn[k],
+    h[k] = tc::make_group(*opA[k], *opB[k], K[k], ep[k], 0, ms->plan_bn[k],
                           spec.sparse[ms->plan_bn[k] == 256 ? 0 : 1]);
-    ms->plan_tiles[k] = tc::tiles_of(*ep[k], ms->plan_bn[k]);
+    ms->plan_tiles[k] = tc::tiles_of(ep[k], ms->plan_bn[k]);
   }
   if (!ms->plans) alloc(&ms->plans, 4);
   OMM_CUDA_TRY(cudaMemcpyAsync(ms->plans, h, sizeof(h), cudaMemcpyHostToDevice, st));
@@ -255,6 +319,11 @@ void run_plan(MixedState* ms, cudaStream_t st, int k) {
 
 }  // namespace
 
+int mixed_reduce_parts(const MixedState* ms) {
+  // four partial sums per epilogue warp of every P G output tile
+  return 4 * ms->plan_tiles[kPlanPG];
+}
+
 void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, double* Dir, double* G,
                    double* Gold, double* PG, double* Y4, double* SWHW, double* Proj, double* part,
                    double* part2, const double* HS, const double* P, bool precond, Profiler& pf) {
@@ -263,37 +332,36 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   const int m = ms->m, n = ms->n;
   const long nm = (long)n * m;
   const int np = ms->npass;
-  if (ms->plan_sc != sc) build_plans(ms, st, sc, G, PG, Y4, Proj);
-  // P G (Sec. 2.4)
+  if (ms->plan_sc != sc) build_plans(ms, st, sc, G, Gold, Dir, PG, Y4, Proj);
+  // P G (Sec. 2.4); the epilogue also takes the Polak-Ribiere products and max|G| and moves G to G_old
   if (precond) {
-    tc::split(st, G, n, m, m, ms->G_hi, ms->G_lo, ms->ldm, sc);
     pf.begin(st);
     run_plan(ms, st, kPlanPG);
     pf.end(st, 2.0 * np * n * (double)m * m);
+    launch_control_direction(st, sc, ms->red, 1, mixed_reduce_parts(ms));
   } else {
     launch_scale_copy(st, nm, G, 1.0, PG, sc);
+    launch_grad_reduce(st, nm, G, PG, Gold, Dir, part, sc);
+    launch_control_direction(st, sc, part, 1, kReduceBlocks);
+    launch_scale_copy(st, nm, G, 1.0, Gold, sc);
   }
-  launch_grad_reduce(st, nm, G, PG, Gold, Dir, part, sc);
-  launch_control_direction(st, sc, part, 1);
   launch_direction_split(st, n, m, PG, Dir, ms->D_hi, ms->D_lo, ms->ldm, sc);
-  // [H~ D ; S D] (n x m layout): one GEMM over the stacked [H~; S]
+  // [H~ D ; S D] (n x m layout): one GEMM over the stacked [H~; S]; the epilogue splits the result
   pf.begin(st);
   run_plan(ms, st, kPlanHD);
   pf.end(st, 4.0 * np * n * (double)m * m * tc::block_density(&ms->hs_blocks[ms->plan_bn[kPlanHD] == 256 ? 0 : 1]));
-  tc::split(st, Y4 + 2 * nm, 2L * n, m, m, ms->Y_hi + 2L * n * ms->ldm, ms->Y_lo + 2L * n * ms->ldm, ms->ldm, sc);
   // [H' | S' | H'' | S''] = D [HC; SC; HD; SD]^T (Eqs. 14-15)
   pf.begin(st);
   run_plan(ms, st, kPlanProj);
   pf.end(st, 8.0 * np * n * (double)n * m);
-  launch_traces(st, n, SWHW, Proj, part2, sc);
+  launch_traces(st, n, SWHW, Proj, part2, sc, /*fp32_products=*/true);
   launch_control_linesearch(st, sc, part2, traces_blocks(n));
-  launch_update_state_split(st, n, m, C, Y4, Dir, G, Gold, ms->dY, ms->Gref, ms->Y_hi, ms->Y_lo, ms->ldm, sc);
-  tc::split_transposed(st, Y4, 2L * n, m, m, ms->YT_hi, ms->YT_lo, ms->ld2n, sc);
-  tc::split_transposed(st, ms->dY, 2L * n, m, m, ms->YT_hi + 2L * n, ms->YT_lo + 2L * n, ms->ld2n, sc);
-  launch_update_subspace(st, n, SWHW, Proj, sc);
-  tc::split_diff(st, SWHW, ms->Wref, n, 2L * n, 2L * n, ms->W_hi, ms->W_lo, ms->ld2n, sc);
-  // G = Gref + 8 dHC - 4 [dS_W | dH_W | S_W,ref | H_W,ref] [HC; SC; dHC; dSC] (Eq. 12 about
-  // the refresh point); the update preset G = Gref + 8 dHC
+  // Eq. 16 and the footnote's updates of C, HC, SC; dHC, dSC; and their splits
+  launch_update_state_split(st, n, m, C, Y4, Dir, ms->dY, ms->Y_hi, ms->Y_lo, ms->ldm, sc);
+  // H_W, S_W (Eq. 16) and the split of [dS_W | dH_W] into W
+  launch_update_subspace_split(st, n, SWHW, Proj, ms->Wref, ms->W_hi + 2L * n, ms->W_lo + 2L * n, ms->ld4n, sc);
+  // G = Gref + 8 dHC - 4 [S_W,ref | H_W,ref | dS_W | dH_W] [dHC; dSC; HC; SC] (Eq. 12 about the
+  // refresh point), and its split for the next P G
   pf.begin(st);
   run_plan(ms, st, kPlanG);
   pf.end(st, 8.0 * np * n * (double)n * m);

@@ -175,7 +175,7 @@ void iterate_fp64(omm_ctx* c) {
   } else
     launch_scale_copy(c->st, nm, c->G, 1.0, c->PG, c->sc);
   launch_grad_reduce(c->st, nm, c->G, c->PG, c->Gold, c->Dir, c->part, c->sc);
-  launch_control_direction(c->st, c->sc, c->part, 0);
+  launch_control_direction(c->st, c->sc, c->part, 0, kReduceBlocks);
   launch_direction(c->st, nm, c->PG, c->Dir, c->sc);
   pf.begin(c->st);
   dgemm(c->st, 0, 1, n, m, m, 1.0, c->Dir, m, 0, c->HS, m, mm, 0.0, c->Y4 + 2 * nm, m, nm, 2, 0, skip);
@@ -393,6 +393,7 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     dev_alloc(&c->part2, (size_t)traces_blocks(n) * kNumTraces);
     if (o.precision == OMM_PREC_MIXED) {
       c->mixed = mixed_create(c->st, m, n, c->HS, c->P);
+      if (o.debug_expire_wait) mixed_set_expire(c->mixed, 1);
       if (4.0 * m * (double)m * n + 8.0 * m * (double)n * n >= kSlicedStateMinFlop)
         c->emu = emu_create(c->st, m, n, kEmuSlices, c->HS);
     }
@@ -492,6 +493,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     reset_loop_flags(c, true);
     write_scalars(c);
     const bool mixed = c->mixed != nullptr;
+    if (mixed) mixed_reset_error(c->mixed, c->st);  // a context stays usable after a timed-out solve
     double flop = 0.0, flop_tc = 0.0;
     const double per_it = 6.0 * m * (double)m * n + (c->mixed ? 16.0 : 12.0) * (double)m * n * n;
     const double per_state = 4.0 * m * (double)m * n + 8.0 * (double)m * n * n;
@@ -569,6 +571,7 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
         read_scalars(c);
         c->prof.collect();
         if (h.done || h.halt) break;
+        if (mixed && mixed_error(c->mixed, c->st) != 0) break;  // a bounded wait expired: stop at once
         // a mixed round that stalls above its refinement threshold is refreshed in float64
         if (mixed && h.iter - prev_iter >= kMixedRoundCap) break;
       }

@@ -134,23 +134,27 @@ void launch_add_scaled(cudaStream_t st, long count, const double* S, const doubl
                        double* A);                       // A = S + T*inv_tau
 void launch_grad_reduce(cudaStream_t st, long count, const double* G, const double* PG,
                         const double* Gold, const double* Dir, double* part, const Scalars* sc);
-void launch_control_direction(cudaStream_t st, Scalars* sc, const double* part, int mixed);
+// Polak-Ribiere coefficient and stopping tests from nparts partial sums (4 doubles each: <G,PG>,
+// <G_old,PG>, <G,Delta_old>, max|G|)
+void launch_control_direction(cudaStream_t st, Scalars* sc, const double* part, int mixed, int nparts);
 void launch_direction(cudaStream_t st, long count, const double* PG, double* Dir, const Scalars* sc);
 // the mixed path's fused forms: the direction (n x m) and its bf16 split (leading dimension ldm);
-// the state update and the split of the new [HC; SC] into Yhi/Ylo
+// the state update of C, HC, SC, dHC, dSC with the splits of the new dHC, dSC, HC, SC into the
+// operand stack rows [0, 4n) (Yhi, Ylo: the stack's hi and lo halves); the update of H_W, S_W
+// with the split of [dS_W | dH_W] into W (Whi, Wlo: its columns 2n..4n, leading dimension ldw)
 void launch_direction_split(cudaStream_t st, long n, long m, const double* PG, double* Dir, __nv_bfloat16* hi,
                             __nv_bfloat16* lo, long ldm, const Scalars* sc);
-void launch_update_state_split(cudaStream_t st, long n, long m, double* C, double* Y4, const double* Dir, double* G,
-                               double* Gold, double* dY, const double* Gref, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo,
-                               long ldm, const Scalars* sc);
+void launch_update_state_split(cudaStream_t st, long n, long m, double* C, double* Y4, const double* Dir, double* dY,
+                               __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, long ldm, const Scalars* sc);
+void launch_update_subspace_split(cudaStream_t st, int n, double* SWHW, const double* Proj, const double* Wref,
+                                  __nv_bfloat16* Whi, __nv_bfloat16* Wlo, long ldw, const Scalars* sc);
+// fp32_products: the mixed path's traces (float32 products of the tensor-core projections)
 void launch_traces(cudaStream_t st, int n, const double* SWHW, const double* Proj, double* part,
-                   const Scalars* sc);
+                   const Scalars* sc, bool fp32_products = false);
 int traces_blocks(int n);
 void launch_control_linesearch(cudaStream_t st, Scalars* sc, const double* part, int nblocks);
 void launch_update_state(cudaStream_t st, int n, long m, double* C, double* Y4, const double* Dir,
                          double* G, double* Gold, const Scalars* sc);
-// mixed precision: as launch_update_state, plus dY = [dHC; dSC] += x [HD; SD] and
-// G = Gref + 8 (HC - HC_ref) as the base of the incremental gradient GEMM
 void launch_update_subspace(cudaStream_t st, int n, double* SWHW, const double* Proj,
                             const Scalars* sc);
 void launch_scale_copy(cudaStream_t st, long count, const double* src, double a, double* dst,

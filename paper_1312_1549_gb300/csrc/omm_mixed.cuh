@@ -12,9 +12,9 @@ struct MixedState;
 // Buffers and operands of a mixed state, for the batched driver.
 struct MixedView {
   long ldm, ld4;
-  __nv_bfloat16 *G_hi, *D_hi, *Y_hi, *YT_hi, *W_hi;  // [hi; lo] stacks
-  double *Gref, *dY, *Wref;
-  const tc::Operand *opHS, *opP, *opG, *opD, *opY, *opYT, *opW;
+  __nv_bfloat16 *G_hi, *D_hi, *Y_hi, *W_hi;  // [hi; lo] stacks (Y: [dHC; dSC; HC; SC; HD; SD], 6n rows)
+  double *Gref, *dY, *Wref, *red;
+  const tc::Operand *opHS, *opP, *opG, *opD, *opYproj, *opYgrad, *opW;
   const tc::BlockLists* hs_blocks;  // [0]: 256-row blocks, [1]: 128-row blocks
   int* err;
   int npass;
@@ -24,6 +24,14 @@ MixedView mixed_view(MixedState* ms);
 // the autotuner's tile widths of the four line-search GEMMs (0 before the first line search) and
 // the time it spent
 void mixed_tuning(const MixedState* ms, int bn[4], double* ms_autotune);
+// the epilogues of the P G, [H D; S D], projection and gradient GEMMs of a line search
+void mixed_epilogues(MixedState* ms, const Scalars* sc, double* G, double* Gold, const double* Dir, double* PG,
+                     double* Y4, double* Proj, tc::Epilogue out[4]);
+// partial-sum slots the P G epilogue fills (after the first line search has built the plans)
+int mixed_reduce_parts(const MixedState* ms);
+// tests of the timeout status: every line search's first GEMM expires its bounded wait
+void mixed_set_expire(MixedState* ms, int on);
+void mixed_reset_error(MixedState* ms, cudaStream_t st);
 
 MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const double* P);
 void mixed_update_H(MixedState* ms, cudaStream_t st, const double* HS);

@@ -54,11 +54,48 @@ __device__ __forceinline__ double bf16_bits_to_double(unsigned short b) {
   return __longlong_as_double((long long)bits);
 }
 
-// hi = bf16(x), lo = bf16(x - hi), both rounded to nearest even; one float64 subtraction
+// lo = bf16(x - hi) outside the range the integer path covers (|x| < 2^-126, |x| >= 2^128,
+// infinities and NaNs): one float64 subtraction, kept out of line so that the common path
+// never issues it, not even predicated off
+static __device__ __noinline__ unsigned short bf16_residual_slow(double x, unsigned short h) {
+  return bf16_bits_rne(x - bf16_bits_to_double(h));  // x - hi is exact
+}
+
+// hi = bf16(x) and lo = bf16(x - hi), both rounded to nearest even, on the integer pipe. For x
+// in the normal bf16 range hi keeps the top 8 significand bits of x rounded at bit 45 of the
+// float64 fraction; the residual x - hi is then the 45 bits below (rounded down) or minus their
+// complement to 2^45 (rounded up), in units of 2^(e - 1075). That integer is rebuilt as a
+// float64 (exact: at most 45 bits) and rounded to bf16 like any other value.
+__device__ __forceinline__ void split_bits(double x, unsigned short& h, unsigned short& l) {
+  h = bf16_bits_rne(x);
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long mag = u & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned int e = (unsigned int)(mag >> 52);
+  if (e < 1023u - 126u || e > 1023u + 127u || (h & 0x7F80u) == 0x7F80u) {  // (hi rounded to infinity)
+    l = bf16_residual_slow(x, h);
+    return;
+  }
+  const unsigned long long low = mag & 0x00001FFFFFFFFFFFull;        // the 45 bits below hi
+  const bool up = (unsigned int)(h & 0x7FFFu) != (unsigned int)((mag >> 45) - ((1023ull - 127ull) << 7));
+  const unsigned long long R = up ? (0x0000200000000000ull - low) : low;  // |x - hi| / 2^(e - 1075)
+  if (R == 0) {
+    l = 0;
+    return;
+  }
+  const unsigned long long sign = (u & 0x8000000000000000ull) ^ (up ? 0x8000000000000000ull : 0ull);
+  const int p = 63 - __clzll((long long)R);                      // top bit of R, p <= 45
+  // R 2^(e - 1075) = 1.f 2^(p + e - 1075): float64 exponent field p + e - 52 (>= 845, normal)
+  const unsigned long long bits = sign | ((unsigned long long)(p + (int)e - 52) << 52) |
+                                  ((R << (52 - p)) & 0x000FFFFFFFFFFFFFull);
+  l = bf16_bits_rne(__longlong_as_double((long long)bits));
+}
+
+// hi = bf16(x), lo = bf16(x - hi), both rounded to nearest even (integer pipe)
 __device__ __forceinline__ void split_store(double x, __nv_bfloat16* hi, __nv_bfloat16* lo, long off) {
-  const unsigned short h = bf16_bits_rne(x);
+  unsigned short h, l;
+  split_bits(x, h, l);
   hi[off] = __ushort_as_bfloat16(h);
-  if (lo) lo[off] = __ushort_as_bfloat16(bf16_bits_rne(x - bf16_bits_to_double(h)));  // x - hi is exact
+  if (lo) lo[off] = __ushort_as_bfloat16(l);
 }
 
 // hi/lo of two neighbouring elements, stored as bf16 pairs

@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 
 #include "omm_internal.cuh"
+#include "split_device.cuh"
 #include "tc_gemm.cuh"
 
 #include <algorithm>
@@ -71,15 +72,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait: false after WAIT_NS without completion
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// bounded wait: false after limit_ns without completion
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns = WAIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255u) == 0 && globaltimer() - t0 > WAIT_NS) return false;
+    if ((i & 255u) == 0 && globaltimer() - t0 > limit_ns) return false;
   }
 }
+
+constexpr uint64_t EXPIRE_NS = 1000000ull;  // the test expiry of Epilogue::expire: 1 ms
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
   asm volatile(
@@ -104,10 +107,27 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
+// UMMA shared-memory descriptor of an MN-major operand, 128-byte swizzle: each 1024-byte atom
+// holds 8 contracted rows of 64 output-index elements (128 B each); atoms of the next 64 output
+// indices are 8 KB apart (leading byte offset) and those of the next 8 contracted rows 1 KB apart
+// (stride byte offset). This is the layout a 64 x 64 TMA box with 128-byte swizzle leaves in
+// shared memory, the boxes of one stage placed 8 KB apart along the output index.
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)(8192 >> 4) << 16;               // leading byte offset: next 64 output indices
+  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: next 8 contracted rows
+  d |= (uint64_t)1 << 46;                         // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                         // layout: SWIZZLE_128B
+  return d;
+}
+
 // instruction descriptor, kind::f16: D f32, A/B bf16, both K-major, M x N
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// the same with B MN-major (the transpose bit of B)
+constexpr uint32_t kIdescBMN = 1u << 16;
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
@@ -171,32 +191,129 @@ __device__ __forceinline__ double combine(const Epilogue& ep, double a, const do
   return fma(ep.beta, *c, ep.alpha * a);
 }
 
-// C = alpha * v + beta * C for the 32 accumulator columns [col0, col0 + 32) of one row.
-__device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col0, const float (&v)[32]) {
+// running sums of one epilogue thread in kEpReduce mode
+struct EpiRed {
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+  unsigned long long mb = 0;  // max |g| as bits (integer pipe; a NaN's pattern exceeds every number's)
+  bool have_dir = false;
+};
+
+// the fused forms of one output element at float64 offset off (see Epilogue)
+__device__ __forceinline__ double fused_value(const Epilogue& ep, double a, long off, EpiRed& red) {
+  if (ep.mode == kEpGrad) return fma(ep.alpha, a, fma(ep.xs, ep.x1[off], ep.x0[off]));
+  if (ep.mode == kEpReduce) {
+    const double out = ep.alpha == 1.0 ? a : ep.alpha * a;
+    const double g = ep.x0[off];
+    red.v0 = fma(g, out, red.v0);
+    if (red.have_dir) {
+      red.v1 = fma(ep.x1[off], out, red.v1);
+      red.v2 = fma(g, ep.x2[off], red.v2);
+    }
+    red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g) & 0x7FFFFFFFFFFFFFFFull);
+    ep.xout[off] = g;
+    return out;
+  }
+  return combine(ep, a, ep.C + off);
+}
+
+// C = alpha * v + beta * C (or a fused form) for the 32 accumulator columns [col0, col0 + 32) of one row.
+__device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col0, const float (&v)[32], EpiRed& red) {
   if (row >= ep.M || col0 >= ep.N) return;
   const int nvalid = min(32, ep.N - col0);
   const long blk0 = col0 / ep.split_cols;
   const long blk1 = (col0 + nvalid - 1) / ep.split_cols;
-  if (blk0 == blk1) {  // specialised loops, no per-element branching
-    double* base = ep.C + blk0 * ep.split_stride + (long)row * ep.ldc + (col0 - blk0 * ep.split_cols);
-    if (ep.beta == 0.0) {
-      if (ep.alpha == 1.0) {
+  if (ep.mode == kEpPlain && ep.bf_hi == nullptr) {
+    if (blk0 == blk1) {  // specialised loops, no per-element branching
+      double* base = ep.C + blk0 * ep.split_stride + (long)row * ep.ldc + (col0 - blk0 * ep.split_cols);
+      if (ep.beta == 0.0) {
+        if (ep.alpha == 1.0) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < nvalid) base[j] = widen(v[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j < nvalid) base[j] = ep.alpha * widen(v[j]);
+        }
+      } else if (ep.beta == 1.0) {
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (j < nvalid) base[j] = widen(v[j]);
+          if (j < nvalid) base[j] = fma(ep.alpha, widen(v[j]), base[j]);
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (j < nvalid) base[j] = ep.alpha * widen(v[j]);
+          if (j < nvalid) base[j] = fma(ep.beta, base[j], ep.alpha * widen(v[j]));
       }
-    } else if (ep.beta == 1.0) {
+      return;
+    }
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < nvalid) base[j] = fma(ep.alpha, widen(v[j]), base[j]);
-    } else {
+    for (int j = 0; j < 32; ++j) {
+      if (j >= nvalid) break;
+      const int col = col0 + j;
+      const long blk = col / ep.split_cols;
+      double* p = ep.C + blk * ep.split_stride + (long)row * ep.ldc + (col - blk * ep.split_cols);
+      *p = combine(ep, widen(v[j]), p);
+    }
+    return;
+  }
+  // fused forms and split outputs (every index into v is a compile-time constant, so that the
+  // accumulator values stay in registers)
+  const long cb0 = col0 - blk0 * ep.split_cols;
+  const long off0 = blk0 * ep.split_stride + (long)row * ep.ldc + cb0;
+  const long bf0 = blk0 * ep.bf_blk + (long)row * ep.bf_ld + cb0;
+  const bool vec = blk0 == blk1 && nvalid == 32 && ((off0 & 1) == 0) &&
+                   (ep.bf_hi == nullptr || ((bf0 & 7) == 0 && (ep.bf_lo & 7) == 0));
+  if (vec) {  // eight columns at a time: 16-byte float64 pairs, 16-byte bf16 octets
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < nvalid) base[j] = fma(ep.beta, base[j], ep.alpha * widen(v[j]));
+    for (int g8 = 0; g8 < 4; ++g8) {
+      const long o = off0 + 8 * g8;
+      double out[8];
+      if (ep.mode == kEpGrad) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double2 a0 = *reinterpret_cast<const double2*>(ep.x0 + o + 2 * k);
+          const double2 a1 = *reinterpret_cast<const double2*>(ep.x1 + o + 2 * k);
+          out[2 * k] = fma(ep.alpha, widen(v[8 * g8 + 2 * k]), fma(ep.xs, a1.x, a0.x));
+          out[2 * k + 1] = fma(ep.alpha, widen(v[8 * g8 + 2 * k + 1]), fma(ep.xs, a1.y, a0.y));
+        }
+      } else if (ep.mode == kEpReduce) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double2 g = *reinterpret_cast<const double2*>(ep.x0 + o + 2 * k);
+          const double a0 = widen(v[8 * g8 + 2 * k]), a1 = widen(v[8 * g8 + 2 * k + 1]);
+          out[2 * k] = ep.alpha == 1.0 ? a0 : ep.alpha * a0;
+          out[2 * k + 1] = ep.alpha == 1.0 ? a1 : ep.alpha * a1;
+          red.v0 = fma(g.x, out[2 * k], red.v0);
+          red.v0 = fma(g.y, out[2 * k + 1], red.v0);
+          if (red.have_dir) {
+            const double2 go = *reinterpret_cast<const double2*>(ep.x1 + o + 2 * k);
+            const double2 d = *reinterpret_cast<const double2*>(ep.x2 + o + 2 * k);
+            red.v1 = fma(go.x, out[2 * k], red.v1);
+            red.v1 = fma(go.y, out[2 * k + 1], red.v1);
+            red.v2 = fma(g.x, d.x, red.v2);
+            red.v2 = fma(g.y, d.y, red.v2);
+          }
+          red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g.x) & 0x7FFFFFFFFFFFFFFFull);
+          red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g.y) & 0x7FFFFFFFFFFFFFFFull);
+          *reinterpret_cast<double2*>(ep.xout + o + 2 * k) = g;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) out[k] = combine(ep, widen(v[8 * g8 + k]), ep.C + o + k);
+      }
+      double2* c2 = reinterpret_cast<double2*>(ep.C + o);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) c2[k] = make_double2(out[2 * k], out[2 * k + 1]);
+      if (ep.bf_hi != nullptr) {
+        unsigned short h[8], l[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dev::split_bits(out[k], h[k], l[k]);
+        __nv_bfloat16* hp = ep.bf_hi + bf0 + 8 * g8;
+        *reinterpret_cast<uint4*>(hp) = make_uint4(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16),
+                                                   h[4] | ((uint32_t)h[5] << 16), h[6] | ((uint32_t)h[7] << 16));
+        *reinterpret_cast<uint4*>(hp + ep.bf_lo) = make_uint4(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16),
+                                                              l[4] | ((uint32_t)l[5] << 16), l[6] | ((uint32_t)l[7] << 16));
+      }
     }
     return;
   }
@@ -205,8 +322,33 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
     if (j >= nvalid) break;
     const int col = col0 + j;
     const long blk = col / ep.split_cols;
-    double* p = ep.C + blk * ep.split_stride + (long)row * ep.ldc + (col - blk * ep.split_cols);
-    *p = combine(ep, widen(v[j]), p);
+    const long cb = col - blk * ep.split_cols;
+    const long off = blk * ep.split_stride + (long)row * ep.ldc + cb;
+    const double out = fused_value(ep, widen(v[j]), off, red);
+    ep.C[off] = out;
+    if (ep.bf_hi != nullptr) {
+      __nv_bfloat16* hp = ep.bf_hi + blk * ep.bf_blk + (long)row * ep.bf_ld;
+      dev::split_store(out, hp, hp + ep.bf_lo, cb);
+    }
+  }
+}
+
+// kEpReduce: the epilogue warp's sums of this tile into its partial slot (fixed order)
+__device__ __forceinline__ void flush_reduce(const Epilogue& ep, int tile, int ewarp, EpiRed& red) {
+  if (ep.mode != kEpReduce) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    red.v0 += __shfl_xor_sync(0xffffffffu, red.v0, o);
+    red.v1 += __shfl_xor_sync(0xffffffffu, red.v1, o);
+    red.v2 += __shfl_xor_sync(0xffffffffu, red.v2, o);
+    red.mb = max(red.mb, __shfl_xor_sync(0xffffffffu, red.mb, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    double* p = ep.part + ((long)tile * 4 + ewarp) * 4;
+    p[0] = red.v0;
+    p[1] = red.v1;
+    p[2] = red.v2;
+    p[3] = __longlong_as_double((long long)red.mb);
   }
 }
 
@@ -217,7 +359,8 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
 // per K block instead of once per pair (2.25x less shared-memory fill traffic).
 template <bool FUSED>
 __device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorMap* mB, int K, int rowsA,
-                                          int rowsB, const PairList& pl, const Epilogue& ep_in, int tile) {
+                                          int rowsB, int offA, int offB, const PairList& pl, const Epilogue& ep_in,
+                                          int tile) {
   constexpr int NS = FUSED ? 2 : STAGES;
   constexpr int SB = FUSED ? 2 * STAGE_BYTES : STAGE_BYTES;
   static_assert(NS * SB == STAGES * STAGE_BYTES, "both modes use the same shared memory");
@@ -263,6 +406,7 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorM
     // ---------------- TMA producer
     prefetch_tmap(mA);
     prefetch_tmap(mB);
+    int armed = 0;
     for (int t = 0; t < total; ++t) {
       const int s = t % NS, r = t / NS;
       if (!mbar_wait(smem_u32(&bars[NS + s]), (r & 1) ^ 1)) {
@@ -276,15 +420,19 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorM
       mbar_expect_tx(full, SB);
       if (FUSED) {
         const int kb = t;
-        tma_load_2d(sa, mA, full, kb * BK, m0);                                  // A_hi
-        tma_load_2d(sa + A_BYTES, mA, full, kb * BK, rowsA + m0);               // A_lo
-        tma_load_2d(sa + 2 * A_BYTES, mB, full, kb * BK, n0);                   // B_hi
-        tma_load_2d(sa + 2 * A_BYTES + B_BYTES, mB, full, kb * BK, rowsB + n0); // B_lo
+        tma_load_2d(sa, mA, full, kb * BK, offA + m0);                                  // A_hi
+        tma_load_2d(sa + A_BYTES, mA, full, kb * BK, rowsA + offA + m0);               // A_lo
+        tma_load_2d(sa + 2 * A_BYTES, mB, full, kb * BK, offB + n0);                   // B_hi
+        tma_load_2d(sa + 2 * A_BYTES + B_BYTES, mB, full, kb * BK, rowsB + offB + n0); // B_lo
       } else {
         const int p = t / nkb, kb = t % nkb;
-        tma_load_2d(sa, mA, full, kb * BK, (int)pl.a[p] * rowsA + m0);
-        tma_load_2d(sa + A_BYTES, mB, full, kb * BK, (int)pl.b[p] * rowsB + n0);
+        tma_load_2d(sa, mA, full, kb * BK, (int)pl.a[p] * rowsA + offA + m0);
+        tma_load_2d(sa + A_BYTES, mB, full, kb * BK, (int)pl.b[p] * rowsB + offB + n0);
       }
+      ++armed;
+    }
+    if (*abort_flag) {  // let the copies already issued land before the CTA releases its memory
+      for (int j = armed > NS ? armed - NS : 0; j < armed; ++j) mbar_wait(smem_u32(&bars[j % NS]), (j / NS) & 1);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
@@ -318,6 +466,7 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorM
       umma_commit(smem_u32(&bars[NS + s]));  // stage s is free once these MMAs have read it
     }
     umma_commit(smem_u32(&bars[2 * NS]));    // accumulator complete (also on abort: drains MMAs)
+    if (*abort_flag) mbar_wait(smem_u32(&bars[2 * NS]), 0);  // the MMAs issued before are done
   } else if (warp >= 2) {
     // ---------------- epilogue
     const bool ok = mbar_wait(smem_u32(&bars[2 * NS]), 0);
@@ -326,12 +475,15 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorM
     const int lane_base = (warp & 3) * 32;
     const int row = m0 + lane_base + lane;
     const bool write = ok && !*abort_flag;
+    EpiRed red;
+    red.have_dir = ep.mode == kEpReduce && ep.sc != nullptr && ep.sc->have_dir;
 #pragma unroll 1
     for (int c = 0; c < BN / 32; ++c) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(c * 32), v);
-      if (write) store_chunk(ep, row, n0 + c * 32, v);
+      if (write) store_chunk(ep, row, n0 + c * 32, v, red);
     }
+    if (write) flush_reduce(ep, tile, warp & 3, red);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -345,8 +497,9 @@ __device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorM
 template <bool FUSED>
 __global__ void __launch_bounds__(NTHREADS, 1)
 gemm_bf16_split_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-                       int K, int rowsA, int rowsB, const __grid_constant__ PairList pl, Epilogue ep) {
-  gemm_tile<FUSED>(&mA, &mB, K, rowsA, rowsB, pl, ep, blockIdx.x);
+                       int K, int rowsA, int rowsB, int offA, int offB, const __grid_constant__ PairList pl,
+                       const __grid_constant__ Epilogue ep) {
+  gemm_tile<FUSED>(&mA, &mB, K, rowsA, rowsB, offA, offB, pl, ep, blockIdx.x);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -398,12 +551,13 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
   constexpr int SB = FUSED ? 2 * TSTAGE : TSTAGE;
   constexpr int NS = (STAGES * STAGE_BYTES) / SB;
   constexpr int ACC_COLS = TBN;
-  static_assert(NS >= 2 && NS * SB <= STAGES * STAGE_BYTES && 2 * NS + 4 <= 28, "stage ring");
+  static_assert(NS >= 2 && NS * SB <= STAGES * STAGE_BYTES && 2 * NS + 5 <= 28, "stage ring");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NS * SB);
-  // bars[0..NS) full, [NS..2NS) empty, [2NS..2NS+2) accumulator full, [2NS+2..2NS+4) accumulator empty
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 4);
+  // bars[0..NS) full, [NS..2NS) empty, [2NS..2NS+2) accumulator full, [2NS+2..2NS+4) accumulator
+  // empty, [2NS+4] drain (the MMA thread's last commit on an abort; the test expiry's wait)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nchunk = (FUSED || pl.nchunk <= 0) ? 1 : pl.nchunk;
@@ -427,6 +581,7 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
       mbar_init(smem_u32(&bars[2 * NS + q]), 1);      // committed by the MMA thread
       mbar_init(smem_u32(&bars[2 * NS + 2 + q]), 4);  // one arrival per epilogue warp
     }
+    mbar_init(smem_u32(&bars[2 * NS + 4]), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -441,6 +596,15 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  if (groups[0].ep.expire) {
+    // tests of the timeout status: a bounded wait on a barrier nothing arrives at, before any
+    // copy or MMA is issued; the CTA then only frees its tensor memory
+    if (threadIdx.x == 0) {
+      if (!mbar_wait(smem_u32(&bars[2 * NS + 4]), 0, EXPIRE_NS)) atomicCAS(err, 0, 6);
+      *abort_flag = 1;
+    }
+    __syncthreads();
+  }
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
@@ -469,22 +633,42 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
         const uint32_t full = smem_u32(&bars[q]);
         const uint32_t sa = smem_u32(smem + q * SB);
         mbar_expect_tx(full, SB);
+        // B: a K-major box of TBN rows, or (MN-major) TBN / 64 boxes of 64 x 64 placed 8 KB apart
         if (FUSED) {
           const int kb = kbs.at(t);
-          tma_load_2d(sa, mA, full, kb * BK, m0);
-          tma_load_2d(sa + A_BYTES, mA, full, kb * BK, g->rowsA + m0);
-          tma_load_2d(sa + 2 * A_BYTES, mB, full, kb * BK, n0);
-          tma_load_2d(sa + 2 * A_BYTES + TB_BYTES, mB, full, kb * BK, g->rowsB + n0);
+          tma_load_2d(sa, mA, full, kb * BK, g->offA + m0);
+          tma_load_2d(sa + A_BYTES, mA, full, kb * BK, g->rowsA + g->offA + m0);
+          if (g->b_mn) {
+#pragma unroll
+            for (int q = 0; q < TBN / 64; ++q) {
+              tma_load_2d(sa + 2 * A_BYTES + q * 8192, mB, full, n0 + 64 * q, g->offB + kb * BK);
+              tma_load_2d(sa + 2 * A_BYTES + TB_BYTES + q * 8192, mB, full, n0 + 64 * q,
+                          g->rowsB + g->offB + kb * BK);
+            }
+          } else {
+            tma_load_2d(sa + 2 * A_BYTES, mB, full, kb * BK, g->offB + n0);
+            tma_load_2d(sa + 2 * A_BYTES + TB_BYTES, mB, full, kb * BK, g->rowsB + g->offB + n0);
+          }
         } else {
           const int p = p0 + t / nkb, kb = kbs.at(t % nkb);
-          tma_load_2d(sa, mA, full, kb * BK, (int)pl.a[p] * g->rowsA + m0);
-          tma_load_2d(sa + A_BYTES, mB, full, kb * BK, (int)pl.b[p] * g->rowsB + n0);
+          tma_load_2d(sa, mA, full, kb * BK, (int)pl.a[p] * g->rowsA + g->offA + m0);
+          if (g->b_mn) {
+#pragma unroll
+            for (int q = 0; q < TBN / 64; ++q)
+              tma_load_2d(sa + A_BYTES + q * 8192, mB, full, n0 + 64 * q, (int)pl.b[p] * g->rowsB + g->offB + kb * BK);
+          } else {
+            tma_load_2d(sa + A_BYTES, mB, full, kb * BK, (int)pl.b[p] * g->rowsB + g->offB + n0);
+          }
         }
       }
     }
+    if (*abort_flag) {  // let the copies already issued land before the CTA releases its memory
+      for (uint32_t j = it > (uint32_t)NS ? it - NS : 0u; j < it; ++j)
+        mbar_wait(smem_u32(&bars[j % NS]), (j / NS) & 1);
+    }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(BM, TBN);
+    constexpr uint32_t idesc_k = idesc_bf16(BM, TBN);
     uint32_t it = 0, lt = 0;
     for (int u = blockIdx.x; u < total_units && !*abort_flag; u += gridDim.x) {
       const int tile = unit_tile(u);
@@ -492,6 +676,12 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
       const int* skip = g->ep.skip;
       if (skip != nullptr && (skip[0] | skip[1])) continue;
       const int nkb = tile_kblocks(g, tile - g->tile_begin, (g->ep.M + BM - 1) / BM).count;
+      const bool bmn = g->b_mn != 0;
+      const uint32_t idesc = idesc_k | (bmn ? kIdescBMN : 0u);
+      // the B descriptor of k step k (16 contracted indices) of a stage whose B starts at addr
+      auto bdesc = [bmn](uint32_t addr, int k) {
+        return bmn ? smem_desc_mn(addr + (uint32_t)k * 2048u) : smem_desc(addr + (uint32_t)k * 32u);
+      };
       for (int c = unit_c0(u); c < unit_c1(u) && !*abort_flag; ++c) {
         const uint32_t buf = lt & 1, use = lt >> 1;
         if (!mbar_wait(smem_u32(&bars[2 * NS + 2 + buf]), (use & 1) ^ 1)) {
@@ -516,21 +706,25 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
             const uint32_t alo = sa + A_BYTES, bhi = sa + 2 * A_BYTES, blo = bhi + TB_BYTES;
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k) {
-              umma_bf16(d, smem_desc(sa + k * 32), smem_desc(bhi + k * 32), idesc, (t > 0 || k > 0) ? 1u : 0u);
-              umma_bf16(d, smem_desc(sa + k * 32), smem_desc(blo + k * 32), idesc, 1u);
-              umma_bf16(d, smem_desc(alo + k * 32), smem_desc(bhi + k * 32), idesc, 1u);
+              umma_bf16(d, smem_desc(sa + k * 32), bdesc(bhi, k), idesc, (t > 0 || k > 0) ? 1u : 0u);
+              umma_bf16(d, smem_desc(sa + k * 32), bdesc(blo, k), idesc, 1u);
+              umma_bf16(d, smem_desc(alo + k * 32), bdesc(bhi, k), idesc, 1u);
             }
           } else {
             const uint32_t sb = sa + A_BYTES;
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k)
-              umma_bf16(d, smem_desc(sa + k * 32), smem_desc(sb + k * 32), idesc, (t > 0 || k > 0) ? 1u : 0u);
+              umma_bf16(d, smem_desc(sa + k * 32), bdesc(sb, k), idesc, (t > 0 || k > 0) ? 1u : 0u);
           }
           umma_commit(smem_u32(&bars[NS + q]));
         }
         umma_commit(smem_u32(&bars[2 * NS + buf]));  // this chunk's accumulator is complete
         ++lt;
       }
+    }
+    if (*abort_flag) {  // every MMA issued so far is complete before the tensor memory is freed
+      umma_commit(smem_u32(&bars[2 * NS + 4]));
+      mbar_wait(smem_u32(&bars[2 * NS + 4]), 0);
     }
   } else if (warp >= 2) {
     // ---------------- epilogue
@@ -565,12 +759,15 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
         const int local = tile - g->tile_begin, tiles_m = (ep.M + BM - 1) / BM;
         const int m0 = (local % tiles_m) * BM, n0 = (local / tiles_m) * TBN;
         const int row = m0 + lane_base + lane;
+        EpiRed red;
+        red.have_dir = ep.mode == kEpReduce && ep.sc != nullptr && ep.sc->have_dir;
 #pragma unroll 1
         for (int j = 0; j < TBN / 32; ++j) {
           float v[32];
           tmem_ld32(tmem + buf * ACC_COLS + ((uint32_t)lane_base << 16) + (uint32_t)(j * 32), v);
-          store_chunk(ep, row, n0 + j * 32, v);
+          store_chunk(ep, row, n0 + j * 32, v, red);
         }
+        flush_reduce(ep, local, warp & 3, red);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&bars[2 * NS + 2 + buf]));
@@ -649,7 +846,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 
 // Row-major bf16 matrix rows x cols (leading dimension ld elements, ld*2 a
 // multiple of 16 bytes, base 16-byte aligned) as a TMA map with box
-// {BK, box_rows} and 128-byte swizzle.
+// {BK, box_rows} (BK = 64 columns of 128 bytes) and 128-byte swizzle.
 TensorMap make_map(const __nv_bfloat16* base, long rows, long cols, long ld, int box_rows) {
   TensorMap tm;
   static_assert(sizeof(TensorMap) == sizeof(CUtensorMap), "TensorMap must hold a CUtensorMap");
@@ -667,15 +864,32 @@ TensorMap make_map(const __nv_bfloat16* base, long rows, long cols, long ld, int
   return tm;
 }
 
-Operand make_operand(const __nv_bfloat16* base, long rows, long cols, long ld, int slices, bool is_a) {
+Operand make_operand_view(const __nv_bfloat16* base, long slice_rows, long cols, long ld, int slices, bool is_a,
+                          int row_off, long rows, bool mn_major) {
+  if (row_off < 0 || rows <= 0 || row_off + rows > slice_rows || (mn_major && is_a))
+    throw CudaError{cudaErrorInvalidValue, "make_operand_view: rows outside the stack"};
   Operand o;
-  o.box_rows = is_a ? BM : BN;
-  o.map = make_map(base, rows * slices, cols, ld, o.box_rows);
-  o.map_n128 = is_a ? o.map : make_map(base, rows * slices, cols, ld, 128);  // for 128-wide output tiles
+  // the map covers the whole stack, so every slice and row offset stays inside it
+  if (mn_major) {
+    o.box_rows = 64;  // 64 contracted rows x 64 output columns per box
+    o.map = make_map(base, slice_rows * slices, cols, ld, 64);
+    o.map_n128 = o.map;
+  } else {
+    o.box_rows = is_a ? BM : BN;
+    o.map = make_map(base, slice_rows * slices, cols, ld, o.box_rows);
+    o.map_n128 = is_a ? o.map : make_map(base, slice_rows * slices, cols, ld, 128);  // 128-wide output tiles
+  }
   o.rows = rows;
   o.cols = cols;
   o.slices = slices;
+  o.slice_rows = slice_rows;
+  o.row_off = row_off;
+  o.mn_major = mn_major;
   return o;
+}
+
+Operand make_operand(const __nv_bfloat16* base, long rows, long cols, long ld, int slices, bool is_a) {
+  return make_operand_view(base, rows, cols, ld, slices, is_a, 0, rows, false);
 }
 
 PairList pairs_split3() {
@@ -720,13 +934,16 @@ void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const Pair
   }
   check_pairs(pl, A.slices, B.slices);
   if (pl.nchunk > 1) throw CudaError{cudaErrorInvalidValue, "tc::gemm: chunked pair lists need the persistent launch"};
+  if (B.mn_major || A.mn_major || ep.expire)
+    throw CudaError{cudaErrorInvalidValue, "tc::gemm: MN-major operands and the test expiry need the persistent launch"};
   dim3 grid((unsigned)(((ep.N + BN - 1) / BN) * ((ep.M + BM - 1) / BM)));
   const CUtensorMap* a = reinterpret_cast<const CUtensorMap*>(&A.map);
   const CUtensorMap* b = reinterpret_cast<const CUtensorMap*>(&B.map);
+  const int ra = (int)A.slice_rows, rb = (int)B.slice_rows;
   if (is_split3(pl) && A.slices >= 2 && B.slices >= 2)
-    gemm_bf16_split_kernel<true><<<grid, NTHREADS, SMEM_BYTES, st>>>(*a, *b, K, (int)A.rows, (int)B.rows, pl, ep);
+    gemm_bf16_split_kernel<true><<<grid, NTHREADS, SMEM_BYTES, st>>>(*a, *b, K, ra, rb, A.row_off, B.row_off, pl, ep);
   else
-    gemm_bf16_split_kernel<false><<<grid, NTHREADS, SMEM_BYTES, st>>>(*a, *b, K, (int)A.rows, (int)B.rows, pl, ep);
+    gemm_bf16_split_kernel<false><<<grid, NTHREADS, SMEM_BYTES, st>>>(*a, *b, K, ra, rb, A.row_off, B.row_off, pl, ep);
   OMM_LAUNCH_CHECK();
 }
 
@@ -735,16 +952,22 @@ int tiles_of(const Epilogue& ep, int bn) { return ((ep.M + BM - 1) / BM) * ((ep.
 GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin, int bn,
                      const BlockLists* sparse) {
   if (bn != 256 && bn != 128) throw CudaError{cudaErrorInvalidValue, "tc::make_group: tile width"};
-  // the TMA boxes must match the tile: A in 128-row boxes, B in boxes of the tile width
-  if (A.box_rows != BM || (bn == 256 && B.box_rows != 256))
+  // the TMA boxes must match the tile: A in 128-row boxes, B in boxes of the tile width (or, MN-major,
+  // 64 x 64 boxes for any width)
+  if (A.mn_major || A.box_rows != BM || (!B.mn_major && bn == 256 && B.box_rows != 256))
     throw CudaError{cudaErrorInvalidValue, "tc::make_group: operand boxes do not match the tile"};
+  if (B.mn_major && (sparse != nullptr || K > B.rows))
+    throw CudaError{cudaErrorInvalidValue, "tc::make_group: MN-major B: no block lists, K <= its rows"};
   GroupDesc g{};
   g.a = A.map;
-  g.b = bn == 128 ? B.map_n128 : B.map;
+  g.b = (bn == 128 && !B.mn_major) ? B.map_n128 : B.map;
   g.ep = ep;
   g.K = K;
-  g.rowsA = (int)A.rows;
-  g.rowsB = (int)B.rows;
+  g.rowsA = (int)A.slice_rows;
+  g.rowsB = (int)B.slice_rows;
+  g.offA = A.row_off;
+  g.offB = B.row_off;
+  g.b_mn = B.mn_major ? 1 : 0;
   g.tile_begin = tile_begin;
   g.bn = bn;
   g.kb_off = sparse ? sparse->off : nullptr;

@@ -14,14 +14,22 @@ struct alignas(64) TensorMap {
 
 // A bf16 operand made of `slices` row-major matrices (rows x cols each, the
 // contracted dimension is cols) stacked vertically in one allocation with
-// leading dimension ld: slice i starts at row i * rows. A split pair
-// x = hi + lo is the 2-slice stack [hi; lo].
+// leading dimension ld: slice i starts at row i * slice_rows (slice_rows = rows
+// unless the operand is a view of a taller stack) and the operand's own rows
+// start at row_off inside each slice. A split pair x = hi + lo is the 2-slice
+// stack [hi; lo].
+// An MN-major operand (B role only) is stored the other way round: its rows are
+// the contracted index and its columns the output columns (K x N, row-major);
+// it is loaded in 64 x 64 boxes and handed to the MMA as an MN-major matrix.
 struct Operand {
-  TensorMap map;       // boxes of 128 rows (A role) or 256 rows (B role)
+  TensorMap map;       // boxes of 128 rows (A role), 256 rows (B role) or 64 x 64 (MN-major)
   TensorMap map_n128;  // boxes of 128 rows (as a B operand of 128-wide output tiles)
   int box_rows = 0;    // rows of the boxes of `map`
   long rows = 0, cols = 0;
   int slices = 1;
+  long slice_rows = 0;  // rows between slices
+  int row_off = 0;      // first row of the operand inside each slice
+  bool mn_major = false;
 };
 
 // Which slice products one GEMM accumulates. With nchunk > 0 the pairs are cut
@@ -47,6 +55,21 @@ PairList pairs_single();   // A_0 B_0
 // (split_cols = N for a plain matrix), so one GEMM can fill several stacked
 // matrices. When skip[0] | skip[1] (the solver's done/halt flags) the kernel
 // does nothing. err receives a nonzero code if a bounded wait expired.
+//
+// Fused forms (mode; x0, x1, x2, xout are float64 matrices laid out like C, and need
+// split_cols = N):
+//   kEpPlain   the above.
+//   kEpGrad    C = alpha * acc + (x0 + xs * x1)   (the incremental gradient about a refresh
+//              point: x0 = G_ref, x1 = dHC, xs = 8, alpha = -4; beta is not used)
+//   kEpReduce  C = alpha * acc, and with g = x0, g_old = x1, d = x2 the sums <g, C>,
+//              <g_old, C>, <g, d> (the last two only when sc->have_dir) and max|g| of each
+//              epilogue warp's rows of the tile go to part[(tile * 4 + warp) * 4 + 0..3]; then
+//              xout = g (xout may alias x1: every element is read before it is written).
+// bf_hi != null (any mode): the stored value is also split into bf16 hi and lo, written to
+// bf_hi + blk * bf_blk + row * bf_ld + j % split_cols and the same plus bf_lo.
+// expire != 0 (tests only): before it issues any copy or MMA the kernel waits about 1 ms on a
+// barrier that nothing arrives at, reports the expired wait in err and does nothing else.
+enum { kEpPlain = 0, kEpGrad = 1, kEpReduce = 2 };
 struct Epilogue {
   double* C;
   long ldc;
@@ -58,10 +81,26 @@ struct Epilogue {
   int N;
   const int* skip;
   int* err;
+  int mode = kEpPlain;
+  const double* x0 = nullptr;
+  const double* x1 = nullptr;
+  const double* x2 = nullptr;
+  double* xout = nullptr;
+  double xs = 0.0;
+  double* part = nullptr;
+  const Scalars* sc = nullptr;
+  __nv_bfloat16* bf_hi = nullptr;
+  long bf_ld = 0, bf_blk = 0, bf_lo = 0;
+  int expire = 0;
 };
 
 // base: 16-byte aligned; ld * 2 bytes a multiple of 16.
 Operand make_operand(const __nv_bfloat16* base, long rows, long cols, long ld, int slices, bool is_a);
+// A view of rows [row_off, row_off + rows) of every slice of a stack whose slices are slice_rows
+// rows apart (a K-major A or B operand, or, with mn_major, an MN-major B operand whose rows are
+// the contracted index).
+Operand make_operand_view(const __nv_bfloat16* base, long slice_rows, long cols, long ld, int slices, bool is_a,
+                          int row_off, long rows, bool mn_major = false);
 // C = alpha * sum_p A_{pl.a[p]} B_{pl.b[p]}^T + beta * C (FP32 accumulation, float64 epilogue)
 void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const PairList& pl, const Epilogue& ep);
 // the npass convention of the split form: 3 -> pairs_split3(), 1 -> pairs_single()
@@ -96,7 +135,9 @@ struct alignas(64) GroupDesc {
   TensorMap a;
   TensorMap b;
   Epilogue ep;
-  int K, rowsA, rowsB, tile_begin;
+  int K, rowsA, rowsB, tile_begin;  // rowsA, rowsB: rows between the slices of A and B
+  int offA, offB;                   // first row of A and B inside each slice
+  int b_mn;                         // B is MN-major (its rows are the contracted index)
   int bn;  // output tile width, 256 or 128 (all groups of one launch share it)
   const int* kb_off;  // block sparsity of B for row blocks of bn (null: dense)
   const int* kb_idx;

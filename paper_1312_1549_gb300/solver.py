@@ -43,11 +43,14 @@ class OMMSolver:
     n: number of Wannier functions. precision: "fp64" or "mixed".
     cholesky=True: reduce to standard form by S = L L^T instead of preconditioning (the
     paper's Cholesky flavour, end of Sec. 2.4); T and tau are then ignored.
+    debug_expire_wait=True (tests of the timeout status only): every mixed line search's first
+    tensor-core GEMM lets a bounded wait expire, so solve() reports OMM_ERR_TIMEOUT.
     """
 
     def __init__(self, H, S, T, n, eta, tau, precision="fp64", stream=None, max_iter=0,
                  tol_grad=1e-9, e_tol=0.0, refine_ratio=0.0, precondition=True, check_every=0,
-                 profile=False, native_certificate=False, cholesky=False, precond_slices=0):
+                 profile=False, native_certificate=False, cholesky=False, precond_slices=0,
+                 debug_expire_wait=False):
         lib = N.lib()
         m = int(H.shape[0])
         self.m, self.n, self.eta, self.tau = m, int(n), float(eta), float(tau)
@@ -58,7 +61,8 @@ class OMMSolver:
                          e_tol=float(e_tol), refine_ratio=float(refine_ratio),
                          profile=1 if profile else 0,
                          native_certificate=1 if native_certificate else 0,
-                         cholesky=1 if cholesky else 0, precond_slices=int(precond_slices))
+                         cholesky=1 if cholesky else 0, precond_slices=int(precond_slices),
+                         debug_expire_wait=1 if debug_expire_wait else 0)
         self._keep = (H, S, T)
         h = ct.c_void_p()
         tau_arg = math.inf if tau is None else float(tau)
@@ -180,6 +184,16 @@ def gemm_tc(A, B, C, alpha=1.0, beta=0.0, npass=3, stream=None, tile_n=None, blo
         N.check(N.lib().omm_kernel_gemm_tc_tiled(M, Nn, K, _ptr(A), _ptr(B), float(alpha), float(beta), _ptr(C),
                                                  int(npass), int(tile_n), _stream_handle(stream)),
                 "omm_kernel_gemm_tc_tiled")
+    return C
+
+
+def gemm_tc_kn(A, B, C, alpha=1.0, beta=0.0, tile_n=256, stream=None):
+    """C = alpha A B + beta C on the BF16 tensor cores (split operands), B given K x N and read
+    MN-major (the gradient product's operand layout)."""
+    M, K = A.shape
+    Nn = B.shape[1]
+    N.check(N.lib().omm_kernel_gemm_tc_kn(M, Nn, K, _ptr(A), _ptr(B), float(alpha), float(beta), _ptr(C),
+                                          int(tile_n), _stream_handle(stream)), "omm_kernel_gemm_tc_kn")
     return C
 
 

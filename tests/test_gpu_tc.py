@@ -39,6 +39,25 @@ def test_gemm_tc_single_pass_is_exact_bf16_product(S, M, N, K, tile_n):
 
 
 @pytest.mark.parametrize("tile_n", [256, 128])
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (130, 300, 72), (200, 512, 1000), (1024, 640, 256)])
+def test_gemm_tc_kn_matches_the_k_major_product(S, M, N, K, tile_n):
+    """B given K x N and read MN-major (the gradient product's layout): within the split error bound
+    2^-14 |A||B| and the same bits as the K-major kernel on B^T (the same MMAs in the same order)."""
+    rng = np.random.default_rng(3 * M + N + K)
+    A = rng.normal(size=(M, K)); B = rng.normal(size=(K, N))
+    C0 = rng.normal(size=(M, N))
+    C = dev(C0)
+    S.gemm_tc_kn(dev(A), dev(B), C, alpha=2.0, beta=-1.0, tile_n=tile_n)
+    ref = 2.0 * A @ B - C0
+    scale = 2.0 * np.abs(A) @ np.abs(B)
+    got = C.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 2.0 ** -14 * scale + 1e-12)
+    Ck = dev(C0)
+    S.gemm_tc(dev(A), dev(np.ascontiguousarray(B.T)), Ck, alpha=2.0, beta=-1.0, npass=3, tile_n=tile_n)
+    assert np.array_equal(got, Ck.cpu().numpy())
+
+
+@pytest.mark.parametrize("tile_n", [256, 128])
 @pytest.mark.parametrize("M,N,K", [(128, 256, 64), (200, 300, 100), (256, 512, 1024), (129, 700, 333)])
 def test_gemm_tc_split_error_bound(S, M, N, K, tile_n):
     """npass = 3: error of the 3-term split product within 2^-14 |A||B|^T elementwise."""
