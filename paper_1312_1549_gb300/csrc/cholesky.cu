@@ -111,6 +111,132 @@ potf2_inv_kernel(double* A, long lda, int b, double* Linv, int* info, int col_of
   }
 }
 
+// ---- float32 leaves of edge up to 128 for the preconditioner-grade inverse
+constexpr int NL = 128;
+constexpr int kLeafThreads = 512;
+constexpr int kLeafSmem = (3 * NL * (NL + 1) + NL) * (int)sizeof(float);
+
+// float64 <-> float32 on the integer pipe (normal numbers; magnitudes outside the float32 normal
+// range become zero or infinity), so that the leaf's conversions stay off the narrow float64 units
+__device__ __forceinline__ float to_f32(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7FFu);
+  if (e < 1023 - 126) return __uint_as_float(sign);
+  if (e > 1023 + 127) return __uint_as_float(sign | 0x7F800000u);
+  // round the 52-bit fraction to 23 bits, ties to even (a carry moves into the exponent)
+  const unsigned long long f = u & 0x000FFFFFFFFFFFFFull;
+  const unsigned long long r = f + 0x0FFFFFFFull + ((f >> 29) & 1ull);
+  return __uint_as_float(sign + ((unsigned int)(e - 1023 + 127) << 23) + (unsigned int)(r >> 29));
+}
+__device__ __forceinline__ double to_f64(float v) {
+  const unsigned int u = __float_as_uint(v);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0) return __longlong_as_double((long long)sign);  // zero (subnormals flushed)
+  if (e == 0xFFu) return __longlong_as_double((long long)(sign | (0x7FFull << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)(e + 1023u - 127u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
+// One CTA: Cholesky factor of the b x b diagonal block at A (b <= 128, read only: the caller
+// does not need L itself), its inverse X = L^-1 into Linv (NL x NL, row-major, zero above the
+// diagonal) and, with Pblk, the block X^T X (both triangles) -- all in float32, for the
+// preconditioner (see potf2_inv_kernel). The triangular inverse is blocked so that all threads
+// work: 16 x 16 diagonal blocks are inverted by one warp each, then pairs of inverted blocks are
+// joined level by level, X21 = -X22 (L21 X11).
+__global__ void __launch_bounds__(kLeafThreads)
+leaf_f32_kernel(const double* A, long lda, int b, double* Linv, int* info, int col_offset, double* Pblk, long ldp) {
+  extern __shared__ float smf[];
+  float (*L)[NL + 1] = reinterpret_cast<float (*)[NL + 1]>(smf);
+  float (*X)[NL + 1] = reinterpret_cast<float (*)[NL + 1]>(smf + NL * (NL + 1));
+  float (*T)[NL + 1] = reinterpret_cast<float (*)[NL + 1]>(smf + 2 * NL * (NL + 1));
+  float* rdiag = smf + 3 * NL * (NL + 1);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < NL * NL; idx += nt) {
+    const int i = idx / NL, j = idx % NL;
+    L[i][j] = (i < b && j <= i) ? to_f32(A[(long)i * lda + j]) : 0.f;
+    X[i][j] = 0.f;
+  }
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {  // right-looking, one column at a time
+    if (tid == 0) {
+      float d = L[j][j];
+      if (!(d > 0.f)) {
+        atomicCAS(info, 0, col_offset + j + 1);
+        d = 1.f;
+      }
+      const float r = sqrtf(d);
+      L[j][j] = r;
+      rdiag[j] = 1.f / r;
+    }
+    __syncthreads();
+    const float rj = rdiag[j];
+    for (int i = j + 1 + tid; i < b; i += nt) L[i][j] *= rj;
+    __syncthreads();
+    const int r = b - j - 1;
+    for (int idx = tid; idx < r * r; idx += nt) {
+      const int i = j + 1 + idx / r, l = j + 1 + idx % r;
+      if (l <= i) L[i][l] = fmaf(-L[i][j], L[l][j], L[i][l]);
+    }
+    __syncthreads();
+  }
+  // 16 x 16 diagonal blocks: lane c of warp w solves column c of block w
+  const int warp = tid >> 5, lane = tid & 31;
+  const int nb16 = (b + 15) / 16;
+  if (warp < nb16 && lane < 16) {
+    const int o = warp * 16, e = min(16, b - o), c = lane;
+    if (c < e) {
+      X[o + c][o + c] = rdiag[o + c];
+      for (int i = c + 1; i < e; ++i) {
+        float acc = 0.f;
+        for (int k = c; k < i; ++k) acc = fmaf(L[o + i][o + k], X[o + k][o + c], acc);
+        X[o + i][o + c] = -acc * rdiag[o + i];
+      }
+    }
+  }
+  __syncthreads();
+  for (int s = 16; s < b; s *= 2) {  // join blocks of edge s into blocks of edge 2s
+    const int pairs = (b + 2 * s - 1) / (2 * s);
+    // T = L21 X11 for every pair (rows o+s .. o+2s, columns o .. o+s)
+    for (int idx = tid; idx < pairs * s * s; idx += nt) {
+      const int p = idx / (s * s), i = (idx / s) % s, j = idx % s;
+      const int o = 2 * s * p, gi = o + s + i, gj = o + j;
+      if (gi >= b) continue;
+      float acc = 0.f;
+      for (int k = j; k < s; ++k) acc = fmaf(L[gi][o + k], X[o + k][gj], acc);
+      T[gi][gj] = acc;
+    }
+    __syncthreads();
+    // X21 = -X22 T (X22 lower: k <= i)
+    for (int idx = tid; idx < pairs * s * s; idx += nt) {
+      const int p = idx / (s * s), i = (idx / s) % s, j = idx % s;
+      const int o = 2 * s * p, gi = o + s + i, gj = o + j;
+      if (gi >= b) continue;
+      float acc = 0.f;
+      for (int k = 0; k <= i; ++k) acc = fmaf(X[gi][o + s + k], T[o + s + k][gj], acc);
+      X[gi][gj] = -acc;
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < NL * NL; idx += nt) {
+    const int i = idx / NL, j = idx % NL;
+    Linv[idx] = to_f64(X[i][j]);
+  }
+  if (Pblk != nullptr) {
+    // (X^T X)_ij = sum_{k >= i} X_ki X_kj for j <= i, mirrored
+    for (int idx = tid; idx < b * b; idx += nt) {
+      const int i = idx / b, j = idx % b;
+      if (j > i) continue;
+      float acc = 0.f;
+      for (int k = i; k < b; ++k) acc = fmaf(X[k][i], X[k][j], acc);
+      const double v = to_f64(acc);
+      Pblk[(long)i * ldp + j] = v;
+      Pblk[(long)j * ldp + i] = v;
+    }
+  }
+}
+
 __global__ void zero_upper_kernel(int m, double* A) {
   const long count = (long)m * m;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < count;
@@ -232,11 +358,12 @@ struct Lane {
 
 struct SlicedWork {
   int m = 0;
+  int nb = NB;               // leaf edge: 64 (float64 leaves) or 128 (float32 leaves)
   double* A = nullptr;       // the matrix, factor L in its lower triangle
   double* Y = nullptr;       // L^-1 (lower triangle, zero above)
   double* P = nullptr;
   double* prod = nullptr;    // one product of the factorisation
-  double* leaf = nullptr;    // NB x NB inverse of a diagonal block
+  double* leaf = nullptr;    // nb x nb inverse of a diagonal block
   int* info = nullptr;
   int* err = nullptr;
   Lane main, side;           // factorisation and inverse on `main`; the P = Y^T Y updates on `side`
@@ -266,16 +393,16 @@ void sliced_nt(Lane& L, int* err, int M, int N, int K, double alpha, const doubl
 void leaf(SlicedWork& w, int r0, int b) {
   const long m = w.m;
   double* pb = w.P ? w.P + r0 * m + r0 : nullptr;
-  if (w.main.slices < kInvSlices)  // a preconditioner: float32 leaves (see potf2_inv_kernel)
-    potf2_inv_kernel<float><<<1, 256, 0, w.main.st>>>(w.A + r0 * m + r0, m, b, w.leaf, w.info, r0, pb, m);
+  if (w.nb == NL)  // a preconditioner: 128-wide float32 leaves (see leaf_f32_kernel)
+    leaf_f32_kernel<<<1, kLeafThreads, kLeafSmem, w.main.st>>>(w.A + r0 * m + r0, m, b, w.leaf, w.info, r0, pb, m);
   else
     potf2_inv_kernel<double><<<1, 256, 0, w.main.st>>>(w.A + r0 * m + r0, m, b, w.leaf, w.info, r0, pb, m);
   OMM_LAUNCH_CHECK();
-  copy_block_kernel<<<16, 256, 0, w.main.st>>>(b, w.leaf, NB, w.Y + r0 * m + r0, m);
+  copy_block_kernel<<<16, 256, 0, w.main.st>>>(b, w.leaf, w.nb, w.Y + r0 * m + r0, m);
   OMM_LAUNCH_CHECK();
 }
 
-int half_of(int b) { return ((b / NB + 1) / 2) * NB; }  // a multiple of NB, about b / 2
+int half_of(int b, int nb) { return ((b / nb + 1) / 2) * nb; }  // a multiple of nb, about b / 2
 
 // P21 = Y22^T Y21 and P11 += Y21^T Y21 of one node (its Y is final), on the side lane
 void p_update(SlicedWork& w, int r0, int b1, int b2) {
@@ -297,13 +424,13 @@ void p_update(SlicedWork& w, int r0, int b1, int b2) {
 // to P = Y^T Y is queued on the side lane, in post-order, so it runs beside the factorisation
 // of the blocks that follow
 void chol_inv(SlicedWork& w, int r0, int b) {
-  if (b <= NB) {
+  if (b <= w.nb) {
     leaf(w, r0, b);
     return;
   }
   const long m = w.m;
   Lane& L = w.main;
-  const int b1 = half_of(b), b2 = b - b1, r1 = r0 + b1;
+  const int b1 = half_of(b, w.nb), b2 = b - b1, r1 = r0 + b1;
   chol_inv(w, r0, b1);
   double* A21 = w.A + (long)r1 * m + r0;
   double* A22 = w.A + (long)r1 * m + r1;
@@ -337,14 +464,14 @@ void chol_inv(SlicedWork& w, int r0, int b) {
 
 // chunk sums of the GEMMs with fewer than ~76 output tiles of 128 x 256 (at most 11 chunks)
 long partial_capacity(int m) {
-  const long h = (m + 1) / 2 + NB;
+  const long h = (m + 1) / 2 + NL;
   return std::min(11L * h * h, 11L * 76 * 128 * 256);
 }
 
 size_t spd_inverse_sliced_workspace_bytes(int m) {
-  const long h = (m + 1) / 2 + NB;  // the largest off-diagonal block edge
+  const long h = (m + 1) / 2 + NL;  // the largest off-diagonal block edge (either leaf size)
   // Y, prod, leaf; per lane: tr0, tr1, partial
-  const size_t f64 = (size_t)m * m + (size_t)h * h + (size_t)NB * NB +
+  const size_t f64 = (size_t)m * m + (size_t)h * h + (size_t)NL * NL +
                      2 * (2 * (size_t)h * h + (size_t)partial_capacity(m));
   const size_t bf = 2 * 2 * (size_t)kInvSlices * (size_t)h * round8(h);  // per lane: sl0, sl1
   return f64 * sizeof(double) + bf * sizeof(__nv_bfloat16) + 4 * 256;
@@ -354,9 +481,11 @@ namespace {
 // P = A^-1 (P != nullptr) and/or L, Y = L^-1 (Y_out != nullptr: A keeps L, zero above the diagonal)
 void sliced_impl(cudaStream_t st, int m, double* A, double* P, double* Y_out, void* work, int* info_dev,
                  int* err_dev, int slices) {
-  const long h = (m + 1) / 2 + NB;
+  const long h = (m + 1) / 2 + NL;
   SlicedWork w;
   w.m = m;
+  // preconditioner grade: 128-wide float32 leaves; float64-class: 64-wide float64 leaves
+  w.nb = slices < kInvSlices ? NL : NB;
   w.A = A;
   w.P = P;
   w.info = info_dev;
@@ -367,7 +496,7 @@ void sliced_impl(cudaStream_t st, int m, double* A, double* P, double* Y_out, vo
   w.prod = f;
   f += h * h;
   w.leaf = f;
-  f += NB * NB;
+  f += NL * NL;
   for (Lane* L : {&w.main, &w.side}) {
     L->tr0 = f;
     f += h * h;
@@ -385,6 +514,13 @@ void sliced_impl(cudaStream_t st, int m, double* A, double* P, double* Y_out, vo
   w.side.sl1 = w.side.sl0 + sl;
   w.main.st = st;
   w.main.slices = w.side.slices = std::min(std::max(slices, 2), kInvSlices);
+  if (w.nb == NL) {
+    static bool attr = false;
+    if (!attr) {
+      OMM_CUDA_TRY(cudaFuncSetAttribute(leaf_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kLeafSmem));
+      attr = true;
+    }
+  }
   if (P) OMM_CUDA_TRY(cudaStreamCreateWithFlags(&w.side.st, cudaStreamNonBlocking));
   // streams and events may be released with work pending: the driver frees them once it is done
   auto cleanup = [&]() {

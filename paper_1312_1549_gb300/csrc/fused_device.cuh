@@ -18,6 +18,7 @@ __device__ __forceinline__ void direction_split_body(long n, long m, const doubl
                                                      int bx, int nbx) {
   if (stopped(sc)) return;
   const double beta = sc->beta;
+  const bool restart = sc->restart_dir != 0;  // beta = 0: the direction is -PG
   const long units = pair_units(n, m);
   for (long u = bx; u < units; u += nbx) {
     long r, c;
@@ -30,18 +31,22 @@ __device__ __forceinline__ void direction_split_body(long n, long m, const doubl
                      ((reinterpret_cast<uintptr_t>(hi + off) | reinterpret_cast<uintptr_t>(lo + off)) & 3) == 0;
     if (vec) {
       const double2 a = *reinterpret_cast<const double2*>(p);
-      double2 x = make_double2(-a.x, -a.y);
-      if (beta != 0.0) {
+      double2 x;
+      if (restart) {  // -PG: a sign flip on the integer pipe
+        x = make_double2(__longlong_as_double(__double_as_longlong(a.x) ^ (long long)0x8000000000000000ull),
+                         __longlong_as_double(__double_as_longlong(a.y) ^ (long long)0x8000000000000000ull));
+      } else {        // one float64 FMA per element (the negation folds into it)
         const double2 b = *reinterpret_cast<const double2*>(d);
         x = make_double2(fma(beta, b.x, -a.x), fma(beta, b.y, -a.y));
       }
       *reinterpret_cast<double2*>(d) = x;
-      split_store2(x.x, x.y, hi, lo, off);
+      split_store2_fast(x.x, x.y, hi, lo, off);
     } else {
       for (int k = 0; k < 2 && c + k < m; ++k) {
-        const double x = (beta != 0.0) ? fma(beta, d[k], -p[k]) : -p[k];
+        const double x = restart ? __longlong_as_double(__double_as_longlong(p[k]) ^ (long long)0x8000000000000000ull)
+                                 : fma(beta, d[k], -p[k]);
         d[k] = x;
-        split_store(x, hi, lo, off + k);
+        split_store_fast(x, hi, lo, off + k);
       }
     }
   }
@@ -97,10 +102,10 @@ __device__ __forceinline__ void update_state_split_body(long n, long m, double* 
       *reinterpret_cast<double2*>(Y4 + nm + o) = S2;
       *reinterpret_cast<double2*>(dY + o) = DH2;
       *reinterpret_cast<double2*>(dY + nm + o) = DS2;
-      split_store2(DH2.x, DH2.y, Yhi, Ylo, odh);
-      split_store2(DS2.x, DS2.y, Yhi, Ylo, ods);
-      split_store2(H2.x, H2.y, Yhi, Ylo, oh);
-      split_store2(S2.x, S2.y, Yhi, Ylo, os);
+      split_store2_fast(DH2.x, DH2.y, Yhi, Ylo, odh);
+      split_store2_fast(DS2.x, DS2.y, Yhi, Ylo, ods);
+      split_store2_fast(H2.x, H2.y, Yhi, Ylo, oh);
+      split_store2_fast(S2.x, S2.y, Yhi, Ylo, os);
     } else {
       for (int t = 0; t < 2 && k + t < m; ++t) {
         const long e = o + t;
@@ -111,10 +116,10 @@ __device__ __forceinline__ void update_state_split_body(long n, long m, double* 
         Y4[nm + e] = Sv;
         dY[e] = DHv;
         dY[nm + e] = DSv;
-        split_store(DHv, Yhi, Ylo, odh + t);
-        split_store(DSv, Yhi, Ylo, ods + t);
-        split_store(Hv, Yhi, Ylo, oh + t);
-        split_store(Sv, Yhi, Ylo, os + t);
+        split_store_fast(DHv, Yhi, Ylo, odh + t);
+        split_store_fast(DSv, Yhi, Ylo, ods + t);
+        split_store_fast(Hv, Yhi, Ylo, oh + t);
+        split_store_fast(Sv, Yhi, Ylo, os + t);
       }
     }
   }
@@ -155,8 +160,8 @@ __device__ __forceinline__ void update_subspace_split_body(int n, double* SWHW, 
     *hw = hn;
     *sw = sn;
     const double* wr = Wref + (long)gi * l2 + gj;
-    split_store(sn - wr[0], Whi, Wlo, (long)gi * ldw + gj);
-    split_store(hn - wr[n], Whi, Wlo, (long)gi * ldw + n + gj);
+    split_store_fast(sn - wr[0], Whi, Wlo, (long)gi * ldw + gj);
+    split_store_fast(hn - wr[n], Whi, Wlo, (long)gi * ldw + n + gj);
   }
 }
 

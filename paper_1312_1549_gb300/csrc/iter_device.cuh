@@ -219,6 +219,7 @@ __device__ __forceinline__ void control_direction_body(Scalars* sc, const double
     if (-gpg + beta * gdo >= 0.0) beta = 0.0;   // not a descent direction: restart
   }
   sc->beta = beta;
+  sc->restart_dir = beta == 0.0 ? 1 : 0;
   sc->gd = -gpg + beta * gdo;
   sc->gpg_old = gpg;
   sc->restart = 0;
@@ -312,12 +313,34 @@ __device__ __forceinline__ void traces_body(int n, const double* __restrict__ SW
       t[10] = fma(s2, h2T, t[10]);
     }
   }
-  if (F32) {
-#pragma unroll
-    for (int q = 0; q < kNumTraces; ++q)
-      if (q != 0 && q != 3) t[q] = (double)f[q];
-  }
   __shared__ double sh[kNumTraces][TB / 32];
+  if (F32) {
+    // warp sums in float32 (shuffles on the float32 units), one float64 value per warp; the
+    // diagonal traces t0, t3 stay float64 throughout
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kNumTraces; ++q) {
+      if (q == 0 || q == 3) {
+        const double w = warp_sum(t[q]);
+        if (lane == 0) sh[q][wid] = w;
+      } else {
+        float w = f[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane == 0) sh[q][wid] = (double)w;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < kNumTraces; ++q) {
+        double acc = 0.0;
+        for (int k = 0; k < TB / 32; ++k) acc += sh[q][k];
+        part[(long)bx_ * kNumTraces + q] = acc;
+      }
+    }
+    return;
+  }
   block_sum<kNumTraces>(t, sh);
   if (threadIdx.x == 0) {
 #pragma unroll

@@ -20,6 +20,7 @@ struct Scalars {
   int iter;          // line searches completed
   int have_dir;      // a previous search direction exists
   int restart;       // next direction is the preconditioned steepest descent
+  int restart_dir;   // the current direction is -PG (beta = 0)
   int stop_pending;  // Eq. 18 met at the last line search: stop at the next check
   int max_iter;
   int stop_reason;   // 1: gradient test met, 2: energy test (Eq. 18) met

@@ -90,6 +90,52 @@ __device__ __forceinline__ void split_bits(double x, unsigned short& h, unsigned
   l = bf16_bits_rne(__longlong_as_double((long long)bits));
 }
 
+// float64 -> float32 rounded to nearest even on the integer pipe (the float64 units retire about
+// one lane per SM and clock); magnitudes below the float32 normal range become zero, above it
+// infinity
+__device__ __forceinline__ float f32_rne_bits(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hi32 = (unsigned int)(u >> 32);
+  const unsigned int sign = hi32 & 0x80000000u;
+  const int e = (int)((hi32 >> 20) & 0x7FFu);
+  if (e < 1023 - 126) return __uint_as_float(sign);
+  if (e > 1023 + 127) return __uint_as_float(sign | 0x7F800000u);
+  // fraction f (52 bits) -> 23 bits: add half an ulp minus one plus the lsb (ties to even); a
+  // carry out of the fraction moves into the exponent
+  const unsigned long long f = u & 0x000FFFFFFFFFFFFFull;
+  const unsigned long long r = f + 0x000000000FFFFFFFull + ((f >> 29) & 1ull);
+  return __uint_as_float(sign + ((unsigned int)(e - 1023 + 127) << 23) + (unsigned int)(r >> 29));
+}
+
+// The operand split of the line-search products, cheap form: x is rounded to float32 (integer
+// pipe), hi = bf16(x32) and lo = bf16(x32 - hi) by the float32 units. hi can differ from the
+// correctly rounded bf16(x) by one unit in a rare double-rounding case; lo then holds the
+// difference, so hi + lo still carries x to about 2^-17 |x|, the accuracy of the split. About
+// twenty instructions per element against a hundred for the exact split, which matters in the
+// GEMM epilogues, where four warps per SM do this work beside the tensor cores.
+__device__ __forceinline__ void split_bits_fast(double x, unsigned short& h, unsigned short& l) {
+  const float xf = f32_rne_bits(x);
+  const __nv_bfloat16 hb = __float2bfloat16_rn(xf);
+  h = __bfloat16_as_ushort(hb);
+  l = __bfloat16_as_ushort(__float2bfloat16_rn(xf - __bfloat162float(hb)));
+}
+
+__device__ __forceinline__ void split_store_fast(double x, __nv_bfloat16* hi, __nv_bfloat16* lo, long off) {
+  unsigned short h, l;
+  split_bits_fast(x, h, l);
+  hi[off] = __ushort_as_bfloat16(h);
+  lo[off] = __ushort_as_bfloat16(l);
+}
+
+__device__ __forceinline__ void split_store2_fast(double x0, double x1, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                                  long off) {
+  unsigned short h0, l0, h1, l1;
+  split_bits_fast(x0, h0, l0);
+  split_bits_fast(x1, h1, l1);
+  *reinterpret_cast<unsigned int*>(hi + off) = h0 | ((unsigned int)h1 << 16);
+  *reinterpret_cast<unsigned int*>(lo + off) = l0 | ((unsigned int)l1 << 16);
+}
+
 // hi = bf16(x), lo = bf16(x - hi), both rounded to nearest even (integer pipe)
 __device__ __forceinline__ void split_store(double x, __nv_bfloat16* hi, __nv_bfloat16* lo, long off) {
   unsigned short h, l;

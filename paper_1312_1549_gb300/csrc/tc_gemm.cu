@@ -257,62 +257,84 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
     return;
   }
   // fused forms and split outputs (every index into v is a compile-time constant, so that the
-  // accumulator values stay in registers)
+  // accumulator values stay in registers). Sixteen columns at a time: their inputs are loaded
+  // first (read-only path, 16-byte pairs), so that one memory latency covers them all.
   const long cb0 = col0 - blk0 * ep.split_cols;
   const long off0 = blk0 * ep.split_stride + (long)row * ep.ldc + cb0;
   const long bf0 = blk0 * ep.bf_blk + (long)row * ep.bf_ld + cb0;
   const bool vec = blk0 == blk1 && nvalid == 32 && ((off0 & 1) == 0) &&
                    (ep.bf_hi == nullptr || ((bf0 & 7) == 0 && (ep.bf_lo & 7) == 0));
-  if (vec) {  // eight columns at a time: 16-byte float64 pairs, 16-byte bf16 octets
+  if (vec) {
+    const bool unit = ep.alpha == 1.0 && ep.beta == 0.0;  // plain store of the accumulator
 #pragma unroll
-    for (int g8 = 0; g8 < 4; ++g8) {
-      const long o = off0 + 8 * g8;
-      double out[8];
+    for (int h16 = 0; h16 < 2; ++h16) {
+      const long o = off0 + 16 * h16;
+      double out[16];
       if (ep.mode == kEpGrad) {
+        double2 a0[8], a1[8];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const double2 a0 = *reinterpret_cast<const double2*>(ep.x0 + o + 2 * k);
-          const double2 a1 = *reinterpret_cast<const double2*>(ep.x1 + o + 2 * k);
-          out[2 * k] = fma(ep.alpha, widen(v[8 * g8 + 2 * k]), fma(ep.xs, a1.x, a0.x));
-          out[2 * k + 1] = fma(ep.alpha, widen(v[8 * g8 + 2 * k + 1]), fma(ep.xs, a1.y, a0.y));
+        for (int k = 0; k < 8; ++k) {
+          a0[k] = __ldg(reinterpret_cast<const double2*>(ep.x0 + o) + k);
+          a1[k] = __ldg(reinterpret_cast<const double2*>(ep.x1 + o) + k);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          out[2 * k] = fma(ep.alpha, widen(v[16 * h16 + 2 * k]), fma(ep.xs, a1[k].x, a0[k].x));
+          out[2 * k + 1] = fma(ep.alpha, widen(v[16 * h16 + 2 * k + 1]), fma(ep.xs, a1[k].y, a0[k].y));
         }
       } else if (ep.mode == kEpReduce) {
+        double2 g[8], go[8], d[8];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const double2 g = *reinterpret_cast<const double2*>(ep.x0 + o + 2 * k);
-          const double a0 = widen(v[8 * g8 + 2 * k]), a1 = widen(v[8 * g8 + 2 * k + 1]);
-          out[2 * k] = ep.alpha == 1.0 ? a0 : ep.alpha * a0;
-          out[2 * k + 1] = ep.alpha == 1.0 ? a1 : ep.alpha * a1;
-          red.v0 = fma(g.x, out[2 * k], red.v0);
-          red.v0 = fma(g.y, out[2 * k + 1], red.v0);
+        for (int k = 0; k < 8; ++k) {
+          g[k] = __ldg(reinterpret_cast<const double2*>(ep.x0 + o) + k);
           if (red.have_dir) {
-            const double2 go = *reinterpret_cast<const double2*>(ep.x1 + o + 2 * k);
-            const double2 d = *reinterpret_cast<const double2*>(ep.x2 + o + 2 * k);
-            red.v1 = fma(go.x, out[2 * k], red.v1);
-            red.v1 = fma(go.y, out[2 * k + 1], red.v1);
-            red.v2 = fma(g.x, d.x, red.v2);
-            red.v2 = fma(g.y, d.y, red.v2);
+            go[k] = *(reinterpret_cast<const double2*>(ep.x1 + o) + k);
+            d[k] = __ldg(reinterpret_cast<const double2*>(ep.x2 + o) + k);
           }
-          red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g.x) & 0x7FFFFFFFFFFFFFFFull);
-          red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g.y) & 0x7FFFFFFFFFFFFFFFull);
-          *reinterpret_cast<double2*>(ep.xout + o + 2 * k) = g;
         }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) out[k] = unit ? widen(v[16 * h16 + k]) : ep.alpha * widen(v[16 * h16 + k]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          red.v0 = fma(g[k].x, out[2 * k], red.v0);
+          red.v0 = fma(g[k].y, out[2 * k + 1], red.v0);
+          red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g[k].x) & 0x7FFFFFFFFFFFFFFFull);
+          red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g[k].y) & 0x7FFFFFFFFFFFFFFFull);
+        }
+        if (red.have_dir) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            red.v1 = fma(go[k].x, out[2 * k], red.v1);
+            red.v1 = fma(go[k].y, out[2 * k + 1], red.v1);
+            red.v2 = fma(g[k].x, d[k].x, red.v2);
+            red.v2 = fma(g[k].y, d[k].y, red.v2);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) *(reinterpret_cast<double2*>(ep.xout + o) + k) = g[k];
+      } else if (unit) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) out[k] = widen(v[16 * h16 + k]);
       } else {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) out[k] = combine(ep, widen(v[8 * g8 + k]), ep.C + o + k);
+        for (int k = 0; k < 16; ++k) out[k] = combine(ep, widen(v[16 * h16 + k]), ep.C + o + k);
       }
       double2* c2 = reinterpret_cast<double2*>(ep.C + o);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) c2[k] = make_double2(out[2 * k], out[2 * k + 1]);
+      for (int k = 0; k < 8; ++k) c2[k] = make_double2(out[2 * k], out[2 * k + 1]);
       if (ep.bf_hi != nullptr) {
-        unsigned short h[8], l[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) dev::split_bits(out[k], h[k], l[k]);
-        __nv_bfloat16* hp = ep.bf_hi + bf0 + 8 * g8;
-        *reinterpret_cast<uint4*>(hp) = make_uint4(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16),
-                                                   h[4] | ((uint32_t)h[5] << 16), h[6] | ((uint32_t)h[7] << 16));
-        *reinterpret_cast<uint4*>(hp + ep.bf_lo) = make_uint4(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16),
-                                                              l[4] | ((uint32_t)l[5] << 16), l[6] | ((uint32_t)l[7] << 16));
+        for (int g8 = 0; g8 < 2; ++g8) {
+          unsigned short h[8], l[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) dev::split_bits_fast(out[8 * g8 + k], h[k], l[k]);
+          __nv_bfloat16* hp = ep.bf_hi + bf0 + 16 * h16 + 8 * g8;
+          *reinterpret_cast<uint4*>(hp) = make_uint4(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16),
+                                                     h[4] | ((uint32_t)h[5] << 16), h[6] | ((uint32_t)h[7] << 16));
+          *reinterpret_cast<uint4*>(hp + ep.bf_lo) =
+              make_uint4(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16), l[4] | ((uint32_t)l[5] << 16),
+                         l[6] | ((uint32_t)l[7] << 16));
+        }
       }
     }
     return;
@@ -328,7 +350,7 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
     ep.C[off] = out;
     if (ep.bf_hi != nullptr) {
       __nv_bfloat16* hp = ep.bf_hi + blk * ep.bf_blk + (long)row * ep.bf_ld;
-      dev::split_store(out, hp, hp + ep.bf_lo, cb);
+      dev::split_store_fast(out, hp, hp + ep.bf_lo, cb);
     }
   }
 }
