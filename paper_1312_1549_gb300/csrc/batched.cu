@@ -39,14 +39,17 @@ struct IterArgs {
   int nparts;  // partial sums of the P G epilogue (4 per epilogue warp and output tile)
   int precond;
   Scalars* sc;
-  double *C, *Dir, *G, *Gold, *PG, *Y4, *SWHW, *Proj, *part, *part2, *dY, *Wref, *red;
+  double *C, *G, *Gold, *Y4, *SWHW, *Proj, *part, *part2, *Wref, *red;
+  float *Dir32, *PG32, *HD32, *dY32;  // float32 side quantities (leading dimension ldm)
   __nv_bfloat16 *D_hi, *Y_hi, *W_hi;
   long ldm, ld4;
 };
 
-__global__ void __launch_bounds__(dev::TB) b_grad_reduce_kernel(const IterArgs* __restrict__ A) {
+// without a preconditioner: the Polak-Ribiere sums with PG = G (also writes PG and G_old)
+__global__ void __launch_bounds__(dev::TB) b_reduce_unpreconditioned_kernel(const IterArgs* __restrict__ A) {
   const IterArgs& a = A[blockIdx.y];
-  dev::grad_reduce_body(a.nm, a.G, a.PG, a.Gold, a.Dir, a.part, a.sc, blockIdx.x, gridDim.x);
+  dev::reduce_unpreconditioned_body(a.n, a.m, a.G, a.Gold, a.Dir32, a.PG32, a.ldm, a.part, a.sc, blockIdx.x,
+                                    gridDim.x);
 }
 
 // Polak-Ribiere coefficient and stopping tests: from the P G epilogue's partial sums, or (without a
@@ -60,14 +63,8 @@ __global__ void __launch_bounds__(dev::TB) b_control_direction_kernel(const Iter
 // Delta and its split (the operand of the next two products)
 __global__ void __launch_bounds__(256) b_direction_kernel(const IterArgs* __restrict__ A) {
   const IterArgs& a = A[blockIdx.y];
-  dev::direction_split_body(a.n, a.m, a.PG, a.Dir, a.D_hi, a.D_hi + (long)a.n * a.ldm, a.ldm, a.sc, blockIdx.x,
-                            gridDim.x);
-}
-
-// without a preconditioner: PG = G (job 0) before the reductions, G_old = G (job 1) after them
-__global__ void __launch_bounds__(256) b_copy_gradient_kernel(const IterArgs* __restrict__ A, int job) {
-  const IterArgs& a = A[blockIdx.y];
-  dev::scale_copy_body(a.nm, a.G, 1.0, job == 0 ? a.PG : a.Gold, a.sc, blockIdx.x, gridDim.x);
+  dev::direction_split32_body(a.n, a.m, a.PG32, a.Dir32, a.D_hi, a.D_hi + (long)a.n * a.ldm, a.ldm, a.sc, blockIdx.x,
+                              gridDim.x);
 }
 
 __global__ void __launch_bounds__(dev::TB) b_traces_kernel(const IterArgs* __restrict__ A) {
@@ -84,8 +81,8 @@ __global__ void __launch_bounds__(dev::TB) b_control_linesearch_kernel(const Ite
 // the state update and the splits of the new dHC, dSC, HC, SC
 __global__ void __launch_bounds__(256) b_update_state_kernel(const IterArgs* __restrict__ A) {
   const IterArgs& a = A[blockIdx.y];
-  dev::update_state_split_body(a.n, a.m, a.C, a.Y4, a.Dir, a.dY, a.Y_hi, a.Y_hi + 6L * a.n * a.ldm, a.ldm, a.sc,
-                               blockIdx.x, gridDim.x);
+  dev::update_state_split32_body(a.n, a.m, a.C, a.Y4, a.Dir32, a.HD32, a.dY32, a.Y_hi, a.Y_hi + 6L * a.n * a.ldm,
+                                 a.ldm, a.sc, blockIdx.x, gridDim.x);
 }
 
 // H_W, S_W and the split of [dS_W | dH_W]
@@ -195,22 +192,15 @@ void enqueue_line_search(omm_batch* b) {
   cudaStream_t st = b->st;
   const unsigned cnt = (unsigned)b->count;
   const dim3 rows_grid((unsigned)std::min(b->max_rows, 1024), cnt);
-  const dim3 vec_grid(256, cnt);
   const tc::PairList pl = tc::pairs_split3();
   if (b->precond) {
     timed_gemm(b, b->gPG, pl);  // P G, the Polak-Ribiere products and max|G|, G_old <- G
   } else {
-    b_copy_gradient_kernel<<<vec_grid, 256, 0, st>>>(b->args, 0);
-    OMM_LAUNCH_CHECK();
-    b_grad_reduce_kernel<<<dim3(kBatchReduceBlocks, cnt), dev::TB, 0, st>>>(b->args);
+    b_reduce_unpreconditioned_kernel<<<dim3(kBatchReduceBlocks, cnt), dev::TB, 0, st>>>(b->args);
     OMM_LAUNCH_CHECK();
   }
   b_control_direction_kernel<<<dim3(1, cnt), dev::TB, 0, st>>>(b->args);
   OMM_LAUNCH_CHECK();
-  if (!b->precond) {
-    b_copy_gradient_kernel<<<vec_grid, 256, 0, st>>>(b->args, 1);
-    OMM_LAUNCH_CHECK();
-  }
   b_direction_kernel<<<rows_grid, 256, 0, st>>>(b->args);
   OMM_LAUNCH_CHECK();
   timed_gemm(b, b->gHD, pl);  // [H D; S D] and its split
@@ -319,14 +309,15 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       a.tiles = traces_blocks(ni);
       a.precond = b->precond;
       a.sc = c->sc;
-      a.C = c->C; a.Dir = c->Dir; a.G = c->G; a.Gold = c->Gold; a.PG = c->PG; a.Y4 = c->Y4;
+      a.C = c->C; a.G = c->G; a.Gold = c->Gold; a.Y4 = c->Y4;
       a.SWHW = c->SWHW; a.Proj = c->Proj; a.part = c->part; a.part2 = c->part2;
-      a.dY = v.dY; a.Wref = v.Wref; a.red = v.red;
+      a.Wref = v.Wref; a.red = v.red;
+      a.Dir32 = v.Dir32; a.PG32 = v.PG32; a.HD32 = v.HD32; a.dY32 = v.dY32;
       a.D_hi = v.D_hi; a.Y_hi = v.Y_hi; a.W_hi = v.W_hi;
       a.ldm = v.ldm;
       a.ld4 = v.ld4;
       tc::Epilogue ep[4];
-      mixed_epilogues(c->mixed, c->sc, c->G, c->Gold, c->Dir, c->PG, c->Y4, c->Proj, ep);
+      mixed_epilogues(c->mixed, c->sc, c->G, c->Gold, c->Y4, c->Proj, ep);
       if (b->precond) spg.push_back(tc::GemmSpec{v.opG, v.opP, mi, ep[0]});
       tc::GemmSpec hd{v.opD, v.opHS, mi, ep[1]};
       hd.sparse[0] = &v.hs_blocks[0];

@@ -314,6 +314,40 @@ void launch_update_state_split(cudaStream_t st, long n, long m, double* C, doubl
   update_state_split_kernel<<<pair_grid(n, m), 256, 0, st>>>(n, m, C, Y4, Dir, dY, Yhi, Ylo, ldm, sc);
   OMM_LAUNCH_CHECK();
 }
+namespace {
+__global__ void __launch_bounds__(256)
+direction_split32_kernel(long n, long m, const float* PG, float* Dir, __nv_bfloat16* hi, __nv_bfloat16* lo, long ldm,
+                         const Scalars* sc) {
+  dev::direction_split32_body(n, m, PG, Dir, hi, lo, ldm, sc, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(256)
+update_state_split32_kernel(long n, long m, double* C, double* Y4, const float* Dir, const float* HD32, float* dY32,
+                            __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, long ldm, const Scalars* sc) {
+  dev::update_state_split32_body(n, m, C, Y4, Dir, HD32, dY32, Yhi, Ylo, ldm, sc, blockIdx.x, gridDim.x);
+}
+__global__ void __launch_bounds__(TB)
+reduce_unpreconditioned_kernel(long n, long m, const double* G, double* Gold, const float* Dir, float* PG, long ldm,
+                               double* part, const Scalars* sc) {
+  dev::reduce_unpreconditioned_body(n, m, G, Gold, Dir, PG, ldm, part, sc, blockIdx.x, gridDim.x);
+}
+}  // namespace
+
+void launch_direction_split32(cudaStream_t st, long n, long m, const float* PG, float* Dir, __nv_bfloat16* hi,
+                              __nv_bfloat16* lo, long ldm, const Scalars* sc) {
+  direction_split32_kernel<<<pair_grid(n, m), 256, 0, st>>>(n, m, PG, Dir, hi, lo, ldm, sc);
+  OMM_LAUNCH_CHECK();
+}
+void launch_update_state_split32(cudaStream_t st, long n, long m, double* C, double* Y4, const float* Dir,
+                                 const float* HD32, float* dY32, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, long ldm,
+                                 const Scalars* sc) {
+  update_state_split32_kernel<<<pair_grid(n, m), 256, 0, st>>>(n, m, C, Y4, Dir, HD32, dY32, Yhi, Ylo, ldm, sc);
+  OMM_LAUNCH_CHECK();
+}
+void launch_reduce_unpreconditioned(cudaStream_t st, long n, long m, const double* G, double* Gold, const float* Dir,
+                                    float* PG, long ldm, double* part, const Scalars* sc) {
+  reduce_unpreconditioned_kernel<<<kReduceBlocks, TB, 0, st>>>(n, m, G, Gold, Dir, PG, ldm, part, sc);
+  OMM_LAUNCH_CHECK();
+}
 void launch_update_subspace_split(cudaStream_t st, int n, double* SWHW, const double* Proj, const double* Wref,
                                   __nv_bfloat16* Whi, __nv_bfloat16* Wlo, long ldw, const Scalars* sc) {
   update_subspace_split_kernel<<<traces_blocks(n), TB, 0, st>>>(n, SWHW, Proj, Wref, Whi, Wlo, ldw, sc);

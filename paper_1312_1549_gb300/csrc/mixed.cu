@@ -32,9 +32,16 @@ struct MixedState {
   __nv_bfloat16 *Y_hi = nullptr, *Y_lo = nullptr;     // [dHC; dSC; HC; SC; HD; SD]  6n x m
   __nv_bfloat16 *W_hi = nullptr, *W_lo = nullptr;     // [S_W,ref | H_W,ref | dS_W | dH_W] n x 4n
   double* Gref = nullptr;                              // G at the last refresh, n x m
-  double* dY = nullptr;                                // [HC - HC_ref; SC - SC_ref], 2n x m
   double* Wref = nullptr;                              // [S_W | H_W] at the last refresh, n x 2n
   double* red = nullptr;                               // per (tile, warp) sums of the P G epilogue
+  // float32 side quantities of a line search (leading dimension ldm): the direction Delta, P G,
+  // [H Delta; S Delta] and [dHC; dSC] = [HC - HC_ref; SC - SC_ref]. Each enters the float64 state
+  // only as an increment or through a bf16 split product, whose own error (about 2^-17) is far
+  // above their float32 rounding (2^-24)
+  float* Dir32 = nullptr;                              // n x m
+  float* PG32 = nullptr;                               // n x m
+  float* HD32 = nullptr;                               // 2n x m
+  float* dY32 = nullptr;                               // 2n x m
   tc::Operand opHS, opP, opG, opD, opYproj, opYgrad, opYhc, opW;
   tc::BlockLists hs_blocks[2];  // block sparsity of [H~; S] for 256- and 128-row blocks (Sec. 2.6)
   int* err = nullptr;
@@ -83,8 +90,12 @@ MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const 
     pair(&ms->Y_hi, &ms->Y_lo, 6L * n, ldm);
     pair(&ms->W_hi, &ms->W_lo, n, ld4n);
     alloc(&ms->Gref, (size_t)n * m);
-    alloc(&ms->dY, 2L * n * m);
     alloc(&ms->Wref, 2L * n * n);
+    alloc(&ms->Dir32, (size_t)n * ldm);
+    alloc(&ms->PG32, (size_t)n * ldm);
+    alloc(&ms->HD32, 2L * n * ldm);
+    alloc(&ms->dY32, 2L * n * ldm);
+    OMM_CUDA_TRY(cudaMemsetAsync(ms->Dir32, 0, (size_t)n * ldm * sizeof(float), st));
     alloc(&ms->red, (size_t)16 * ((n + 127) / 128) * ((m + 127) / 128));  // 4 warps x 4 sums per 128 x 128 tile
     alloc(&ms->err, 1);
     OMM_CUDA_TRY(cudaMemsetAsync(ms->err, 0, sizeof(int), st));
@@ -139,9 +150,12 @@ MixedView mixed_view(MixedState* ms) {
   v.Y_hi = ms->Y_hi;
   v.W_hi = ms->W_hi;
   v.Gref = ms->Gref;
-  v.dY = ms->dY;
   v.Wref = ms->Wref;
   v.red = ms->red;
+  v.Dir32 = ms->Dir32;
+  v.PG32 = ms->PG32;
+  v.HD32 = ms->HD32;
+  v.dY32 = ms->dY32;
   v.opHS = &ms->opHS;
   v.opP = &ms->opP;
   v.opG = &ms->opG;
@@ -167,8 +181,10 @@ void mixed_destroy(MixedState* ms) {
   __nv_bfloat16* bufs[] = {ms->HS_hi, ms->P_hi, ms->G_hi, ms->D_hi, ms->Y_hi, ms->W_hi};
   for (auto* b : bufs)
     if (b) cudaFree(b);
-  for (double* d : {ms->Gref, ms->dY, ms->Wref, ms->red})
+  for (double* d : {ms->Gref, ms->Wref, ms->red})
     if (d) cudaFree(d);
+  for (float* f : {ms->Dir32, ms->PG32, ms->HD32, ms->dY32})
+    if (f) cudaFree(f);
   if (ms->err) cudaFree(ms->err);
   if (ms->plans) cudaFree(ms->plans);
   tc::free_block_lists(ms->hs_blocks[0]);
@@ -184,25 +200,30 @@ int mixed_error(MixedState* ms, cudaStream_t st) {
 }
 
 // The epilogues of the four line-search GEMMs (shared by the single and the batched solve):
-//   [0] P G            PG, plus the sums <G,PG>, <G_old,PG>, <G,Delta_old>, max|G| per (tile, warp)
-//                      into ms->red, and G_old <- G
-//   [1] [H D; S D]     into Y4 rows [2n, 4n), and their bf16 split into the stack rows [4n, 6n)
+//   [0] P G            P G as float32, plus the sums <G,PG>, <G_old,PG>, <G,Delta_old>, max|G| per
+//                      (tile, warp) into ms->red, and G_old <- G
+//   [1] [H D; S D]     as float32, and their bf16 split into the stack rows [4n, 6n)
 //   [2] projections    [H' | S' | H'' | S''] into Proj
 //   [3] gradient       G = G_ref + 8 dHC - 4 [..] [..], and its split (the next P G's operand)
-void mixed_epilogues(MixedState* ms, const Scalars* sc, double* G, double* Gold, const double* Dir, double* PG,
-                     double* Y4, double* Proj, tc::Epilogue out[4]) {
+void mixed_epilogues(MixedState* ms, const Scalars* sc, double* G, double* Gold, double* Y4, double* Proj,
+                     tc::Epilogue out[4]) {
+  (void)Y4;
   const int m = ms->m, n = ms->n;
-  const long nm = (long)n * m, ldm = ms->ldm;
+  const long ldm = ms->ldm;
   const int* skip = &sc->done;
-  tc::Epilogue epg{PG, m, m, 0, 1.0, 0.0, n, m, skip, ms->err};
+  tc::Epilogue epg{reinterpret_cast<double*>(ms->PG32), ldm, m, 0, 1.0, 0.0, n, m, skip, ms->err};
   epg.mode = tc::kEpReduce;
+  epg.c_f32 = 1;
   epg.x0 = G;
   epg.x1 = Gold;
-  epg.x2 = Dir;
   epg.xout = Gold;
+  epg.ldx = m;
+  epg.x2f = ms->Dir32;
+  epg.ldf = ldm;
   epg.part = ms->red;
   epg.sc = sc;
-  tc::Epilogue ehd{Y4 + 2 * nm, m, m, nm, 1.0, 0.0, n, 2 * m, skip, ms->err};
+  tc::Epilogue ehd{reinterpret_cast<double*>(ms->HD32), ldm, m, (long)n * ldm, 1.0, 0.0, n, 2 * m, skip, ms->err};
+  ehd.c_f32 = 1;
   ehd.bf_hi = ms->Y_hi + 4L * n * ldm;
   ehd.bf_ld = ldm;
   ehd.bf_blk = (long)n * ldm;
@@ -211,7 +232,9 @@ void mixed_epilogues(MixedState* ms, const Scalars* sc, double* G, double* Gold,
   tc::Epilogue eg{G, m, m, 0, -4.0, 0.0, n, m, skip, ms->err};
   eg.mode = tc::kEpGrad;
   eg.x0 = ms->Gref;
-  eg.x1 = ms->dY;
+  eg.ldx = m;
+  eg.x1f = ms->dY32;
+  eg.ldf = ldm;
   eg.xs = 8.0;
   eg.bf_hi = ms->G_hi;
   eg.bf_ld = ldm;
@@ -230,7 +253,7 @@ void mixed_sync_state(MixedState* ms, cudaStream_t st, const double* Y4, const d
   const long ldm = ms->ldm, ld4 = ms->ld4n;
   OMM_CUDA_TRY(cudaMemcpyAsync(ms->Gref, G, (size_t)n * m * sizeof(double), cudaMemcpyDeviceToDevice, st));
   OMM_CUDA_TRY(cudaMemcpyAsync(ms->Wref, SWHW, 2L * n * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  OMM_CUDA_TRY(cudaMemsetAsync(ms->dY, 0, 2L * n * m * sizeof(double), st));
+  OMM_CUDA_TRY(cudaMemsetAsync(ms->dY32, 0, 2L * n * ldm * sizeof(float), st));
   // stack rows [0, 2n): split of dHC = dSC = 0; rows [2n, 4n): split of [HC; SC]
   OMM_CUDA_TRY(cudaMemsetAsync(ms->Y_hi, 0, 2L * n * ldm * sizeof(__nv_bfloat16), st));
   OMM_CUDA_TRY(cudaMemsetAsync(ms->Y_lo, 0, 2L * n * ldm * sizeof(__nv_bfloat16), st));
@@ -257,22 +280,21 @@ void mixed_recompute_state(MixedState* ms, cudaStream_t st, Scalars* sc, const d
            tc::Epilogue{SWHW + n, 2L * n, n, -(long)n, 1.0, 0.0, n, 2 * n, nullptr, ms->err});
   launch_functional(st, n, SWHW, part2);
   launch_finish_functional(st, sc, part2, traces_blocks(n));
-  // G = 8 HC - 4 [S_W | H_W] [HC; SC]: the incremental gradient about the zero point (G_ref = 0,
-  // W_ref = 0, dHC = HC, dSC = SC), so that W = [0 | 0 | S_W | H_W] and the stack rows [0, 2n)
-  // hold the split of [HC; SC] too
-  OMM_CUDA_TRY(cudaMemsetAsync(ms->Gref, 0, (size_t)nm * sizeof(double), st));
+  // G = 8 HC - 4 [S_W | H_W] [HC; SC] through the incremental-gradient epilogue: G_ref = 8 HC,
+  // dHC = dSC = 0, W = [0 | 0 | S_W | H_W], so the stack rows [0, 2n) only meet zero columns of W
+  launch_scale_copy(st, nm, Y4, 8.0, ms->Gref, nullptr);
+  OMM_CUDA_TRY(cudaMemsetAsync(ms->dY32, 0, 2L * n * ldm * sizeof(float), st));
+  OMM_CUDA_TRY(cudaMemsetAsync(ms->Y_hi, 0, 2L * n * ldm * sizeof(__nv_bfloat16), st));
+  OMM_CUDA_TRY(cudaMemsetAsync(ms->Y_lo, 0, 2L * n * ldm * sizeof(__nv_bfloat16), st));
   OMM_CUDA_TRY(cudaMemsetAsync(ms->Wref, 0, 2L * n * n * sizeof(double), st));
-  OMM_CUDA_TRY(cudaMemcpyAsync(ms->dY, Y4, 2L * nm * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  OMM_CUDA_TRY(cudaMemcpyAsync(ms->Y_hi, ms->Y_hi + 2L * n * ldm, 2L * n * ldm * sizeof(__nv_bfloat16),
-                               cudaMemcpyDeviceToDevice, st));
-  OMM_CUDA_TRY(cudaMemcpyAsync(ms->Y_lo, ms->Y_lo + 2L * n * ldm, 2L * n * ldm * sizeof(__nv_bfloat16),
-                               cudaMemcpyDeviceToDevice, st));
   tc::split(st, ms->Wref, n, 2L * n, 2L * n, ms->W_hi, ms->W_lo, ld4, nullptr);
   tc::split(st, SWHW, n, 2L * n, 2L * n, ms->W_hi + 2L * n, ms->W_lo + 2L * n, ld4, nullptr);
   tc::Epilogue eg{G, m, m, 0, -4.0, 0.0, n, m, nullptr, ms->err};
   eg.mode = tc::kEpGrad;
   eg.x0 = ms->Gref;
-  eg.x1 = ms->dY;
+  eg.ldx = m;
+  eg.x1f = ms->dY32;
+  eg.ldf = ldm;
   eg.xs = 8.0;
   tc::gemm_persistent(st, ms->opW, ms->opYgrad, 4 * n, tc::pairs_split3(), eg);
   launch_gmax(st, nm, G, part);
@@ -283,12 +305,11 @@ namespace {
 
 enum { kPlanPG = 0, kPlanHD, kPlanProj, kPlanG };
 
-void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double* Gold, const double* Dir,
-                 double* PG, double* Y4, double* Proj) {
+void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double* Gold, double* Y4, double* Proj) {
   const int m = ms->m, n = ms->n;
   tc::GroupDesc h[4] = {};
   tc::Epilogue ep[4];
-  mixed_epilogues(ms, sc, G, Gold, Dir, PG, Y4, Proj, ep);
+  mixed_epilogues(ms, sc, G, Gold, Y4, Proj, ep);
   const tc::Operand* opA[4] = {&ms->opG, &ms->opD, &ms->opD, &ms->opW};
   const tc::Operand* opB[4] = {ms->precond ? &ms->opP : &ms->opG, &ms->opHS, &ms->opYproj, &ms->opYgrad};
   const int K[4] = {m, m, m, 4 * n};
@@ -329,23 +350,22 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
                    double* part2, const double* HS, const double* P, bool precond, Profiler& pf) {
   (void)HS;
   (void)P;
+  (void)Dir;
+  (void)PG;
   const int m = ms->m, n = ms->n;
-  const long nm = (long)n * m;
   const int np = ms->npass;
-  if (ms->plan_sc != sc) build_plans(ms, st, sc, G, Gold, Dir, PG, Y4, Proj);
+  if (ms->plan_sc != sc) build_plans(ms, st, sc, G, Gold, Y4, Proj);
   // P G (Sec. 2.4); the epilogue also takes the Polak-Ribiere products and max|G| and moves G to G_old
   if (precond) {
     pf.begin(st);
     run_plan(ms, st, kPlanPG);
     pf.end(st, 2.0 * np * n * (double)m * m);
     launch_control_direction(st, sc, ms->red, 1, mixed_reduce_parts(ms));
-  } else {
-    launch_scale_copy(st, nm, G, 1.0, PG, sc);
-    launch_grad_reduce(st, nm, G, PG, Gold, Dir, part, sc);
+  } else {  // P = I: the same products with PG = G
+    launch_reduce_unpreconditioned(st, n, m, G, Gold, ms->Dir32, ms->PG32, ms->ldm, part, sc);
     launch_control_direction(st, sc, part, 1, kReduceBlocks);
-    launch_scale_copy(st, nm, G, 1.0, Gold, sc);
   }
-  launch_direction_split(st, n, m, PG, Dir, ms->D_hi, ms->D_lo, ms->ldm, sc);
+  launch_direction_split32(st, n, m, ms->PG32, ms->Dir32, ms->D_hi, ms->D_lo, ms->ldm, sc);
   // [H~ D ; S D] (n x m layout): one GEMM over the stacked [H~; S]; the epilogue splits the result
   pf.begin(st);
   run_plan(ms, st, kPlanHD);
@@ -357,7 +377,7 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   launch_traces(st, n, SWHW, Proj, part2, sc, /*fp32_products=*/true);
   launch_control_linesearch(st, sc, part2, traces_blocks(n));
   // Eq. 16 and the footnote's updates of C, HC, SC; dHC, dSC; and their splits
-  launch_update_state_split(st, n, m, C, Y4, Dir, ms->dY, ms->Y_hi, ms->Y_lo, ms->ldm, sc);
+  launch_update_state_split32(st, n, m, C, Y4, ms->Dir32, ms->HD32, ms->dY32, ms->Y_hi, ms->Y_lo, ms->ldm, sc);
   // H_W, S_W (Eq. 16) and the split of [dS_W | dH_W] into W
   launch_update_subspace_split(st, n, SWHW, Proj, ms->Wref, ms->W_hi + 2L * n, ms->W_lo + 2L * n, ms->ld4n, sc);
   // G = Gref + 8 dHC - 4 [S_W,ref | H_W,ref | dS_W | dH_W] [dHC; dSC; HC; SC] (Eq. 12 about the

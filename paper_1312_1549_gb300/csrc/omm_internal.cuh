@@ -149,6 +149,17 @@ void launch_update_state_split(cudaStream_t st, long n, long m, double* C, doubl
                                __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, long ldm, const Scalars* sc);
 void launch_update_subspace_split(cudaStream_t st, int n, double* SWHW, const double* Proj, const double* Wref,
                                   __nv_bfloat16* Whi, __nv_bfloat16* Wlo, long ldw, const Scalars* sc);
+// the same steps on the mixed path's float32 side quantities (Delta, P G, [H Delta; S Delta],
+// [dHC; dSC], leading dimension ldm): the direction and its split; the state update with three
+// float64 FMAs per element; without a preconditioner, the reductions with PG = G (PG and G_old
+// written)
+void launch_direction_split32(cudaStream_t st, long n, long m, const float* PG, float* Dir, __nv_bfloat16* hi,
+                              __nv_bfloat16* lo, long ldm, const Scalars* sc);
+void launch_update_state_split32(cudaStream_t st, long n, long m, double* C, double* Y4, const float* Dir,
+                                 const float* HD32, float* dY32, __nv_bfloat16* Yhi, __nv_bfloat16* Ylo, long ldm,
+                                 const Scalars* sc);
+void launch_reduce_unpreconditioned(cudaStream_t st, long n, long m, const double* G, double* Gold, const float* Dir,
+                                    float* PG, long ldm, double* part, const Scalars* sc);
 // fp32_products: the mixed path's traces (float32 products of the tensor-core projections)
 void launch_traces(cudaStream_t st, int n, const double* SWHW, const double* Proj, double* part,
                    const Scalars* sc, bool fp32_products = false);

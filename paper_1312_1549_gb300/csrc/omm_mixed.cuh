@@ -13,7 +13,8 @@ struct MixedState;
 struct MixedView {
   long ldm, ld4;
   __nv_bfloat16 *G_hi, *D_hi, *Y_hi, *W_hi;  // [hi; lo] stacks (Y: [dHC; dSC; HC; SC; HD; SD], 6n rows)
-  double *Gref, *dY, *Wref, *red;
+  double *Gref, *Wref, *red;
+  float *Dir32, *PG32, *HD32, *dY32;  // float32 side quantities, leading dimension ldm
   const tc::Operand *opHS, *opP, *opG, *opD, *opYproj, *opYgrad, *opW;
   const tc::BlockLists* hs_blocks;  // [0]: 256-row blocks, [1]: 128-row blocks
   int* err;
@@ -25,8 +26,8 @@ MixedView mixed_view(MixedState* ms);
 // the time it spent
 void mixed_tuning(const MixedState* ms, int bn[4], double* ms_autotune);
 // the epilogues of the P G, [H D; S D], projection and gradient GEMMs of a line search
-void mixed_epilogues(MixedState* ms, const Scalars* sc, double* G, double* Gold, const double* Dir, double* PG,
-                     double* Y4, double* Proj, tc::Epilogue out[4]);
+void mixed_epilogues(MixedState* ms, const Scalars* sc, double* G, double* Gold, double* Y4, double* Proj,
+                     tc::Epilogue out[4]);
 // partial-sum slots the P G epilogue fills (after the first line search has built the plans)
 int mixed_reduce_parts(const MixedState* ms);
 // tests of the timeout status: every line search's first GEMM expires its bounded wait

@@ -107,6 +107,49 @@ __device__ __forceinline__ float f32_rne_bits(double x) {
   return __uint_as_float(sign + ((unsigned int)(e - 1023 + 127) << 23) + (unsigned int)(r >> 29));
 }
 
+// float32 -> float64 on the integer pipe (exact; zeros keep their sign, subnormals are
+// normalised, infinities and NaNs keep their class)
+__device__ __forceinline__ double f64_of_f32(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  unsigned long long bits;
+  if (e != 0 && e != 0xFFu) {
+    bits = sign | ((unsigned long long)(e + (1023u - 127u)) << 52) | ((unsigned long long)m << 29);
+  } else if (e == 0xFFu) {
+    bits = sign | (0x7FFull << 52) | ((unsigned long long)m << 29);
+  } else if (m == 0) {
+    bits = sign;
+  } else {  // subnormal: m 2^-149 with its top bit at position p
+    const int p = 31 - __clz(m);
+    bits = sign | ((unsigned long long)(p - 149 + 1023) << 52) | (((unsigned long long)m << (52 - p)) & 0x000FFFFFFFFFFFFFull);
+  }
+  return __longlong_as_double((long long)bits);
+}
+
+// hi/lo of a float32 value (the float32 side quantities of the mixed line search): two hardware
+// conversions and one float32 subtraction
+__device__ __forceinline__ void split_bits_f32(float x, unsigned short& h, unsigned short& l) {
+  const __nv_bfloat16 hb = __float2bfloat16_rn(x);
+  h = __bfloat16_as_ushort(hb);
+  l = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(hb)));
+}
+
+__device__ __forceinline__ void split_store2_f32(float x0, float x1, __nv_bfloat16* hi, __nv_bfloat16* lo, long off) {
+  unsigned short h0, l0, h1, l1;
+  split_bits_f32(x0, h0, l0);
+  split_bits_f32(x1, h1, l1);
+  *reinterpret_cast<unsigned int*>(hi + off) = h0 | ((unsigned int)h1 << 16);
+  *reinterpret_cast<unsigned int*>(lo + off) = l0 | ((unsigned int)l1 << 16);
+}
+
+__device__ __forceinline__ void split_store_f32(float x, __nv_bfloat16* hi, __nv_bfloat16* lo, long off) {
+  unsigned short h, l;
+  split_bits_f32(x, h, l);
+  hi[off] = __ushort_as_bfloat16(h);
+  lo[off] = __ushort_as_bfloat16(l);
+}
+
 // The operand split of the line-search products, cheap form: x is rounded to float32 (integer
 // pipe), hi = bf16(x32) and lo = bf16(x32 - hi) by the float32 units. hi can differ from the
 // correctly rounded bf16(x) by one unit in a rare double-rounding case; lo then holds the

@@ -1,6 +1,6 @@
 // BF16 tensor-core GEMM for sm_103a: tcgen05.mma with the accumulator in
 // tensor memory (TMEM), operands moved global -> shared by TMA
-// (cp.async.bulk.tensor, 128-byte swizzle), a 4-stage mbarrier pipeline and
+// (cp.async.bulk.tensor, 128-byte swizzle), a ring of 64-wide K stages and
 // warp specialisation:
 //   warp 0      TMA producer (one lane)
 //   warp 1      TMEM allocation and the MMA issuer (one lane)
@@ -33,13 +33,20 @@ namespace omm {
 namespace tc {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+// K is consumed in stages of BK = 64 contracted columns (one 128-byte swizzle atom of bf16 per
+// row). Stages of 32 columns (64-byte swizzle) were measured slower: twice the barrier and commit
+// round trips per contracted column, for no gain in the bytes kept in flight.
+constexpr int BM = 128, BN = 256, BK = 64;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int RING_BYTES = 192 * 1024;  // the stage ring
+constexpr int MAX_STAGES = 10;          // barrier room: 2 * stages + 5 barriers in 256 bytes
 constexpr int TMEM_COLS = 256;
 constexpr int NTHREADS = 192;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int SMEM_BYTES = RING_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int ring_stages(int stage_bytes) {
+  return RING_BYTES / stage_bytes < MAX_STAGES ? RING_BYTES / stage_bytes : MAX_STAGES;
+}
 constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -96,12 +103,13 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
-// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle (rows of 64 bf16), 8-row groups
+// 1024 B apart.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
-  d |= (uint64_t)(16 >> 4) << 16;                 // leading byte offset (unused for SW128 K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset
+  d |= (uint64_t)(16 >> 4) << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: next 8 rows
   d |= (uint64_t)1 << 46;                         // descriptor version (sm_100 family)
   d |= (uint64_t)2 << 61;                         // layout: SWIZZLE_128B
   return d;
@@ -110,12 +118,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 // UMMA shared-memory descriptor of an MN-major operand, 128-byte swizzle: each 1024-byte atom
 // holds 8 contracted rows of 64 output-index elements (128 B each); atoms of the next 64 output
 // indices are 8 KB apart (leading byte offset) and those of the next 8 contracted rows 1 KB apart
-// (stride byte offset). This is the layout a 64 x 64 TMA box with 128-byte swizzle leaves in
-// shared memory, the boxes of one stage placed 8 KB apart along the output index.
+// (stride byte offset). This is the layout a 64-column x 64-row TMA box with 128-byte swizzle
+// leaves in shared memory, the boxes of one stage placed 8 KB apart along the output index.
+constexpr int MN_BOX_BYTES = 64 * BK * 2;
 __device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
-  d |= (uint64_t)(8192 >> 4) << 16;               // leading byte offset: next 64 output indices
+  d |= (uint64_t)(MN_BOX_BYTES >> 4) << 16;       // leading byte offset: next 64 output indices
   d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: next 8 contracted rows
   d |= (uint64_t)1 << 46;                         // descriptor version (sm_100 family)
   d |= (uint64_t)2 << 61;                         // layout: SWIZZLE_128B
@@ -198,22 +207,52 @@ struct EpiRed {
   bool have_dir = false;
 };
 
-// the fused forms of one output element at float64 offset off (see Epilogue)
-__device__ __forceinline__ double fused_value(const Epilogue& ep, double a, long off, EpiRed& red) {
-  if (ep.mode == kEpGrad) return fma(ep.alpha, a, fma(ep.xs, ep.x1[off], ep.x0[off]));
-  if (ep.mode == kEpReduce) {
-    const double out = ep.alpha == 1.0 ? a : ep.alpha * a;
-    const double g = ep.x0[off];
-    red.v0 = fma(g, out, red.v0);
+// One output element of a fused form (see Epilogue): accumulator value a (FP32) at row, column
+// col of block blk (cb = col within the block); stores C (and its split) and returns nothing.
+__device__ __forceinline__ void fused_element(const Epilogue& ep, float a, int row, long blk, long cb, EpiRed& red) {
+  const long offc = blk * ep.split_stride + (long)row * ep.ldc + cb;
+  double out;
+  if (ep.mode == kEpGrad) {
+    const long ox = (long)row * ep.ldx + cb, of = (long)row * ep.ldf + cb;
+    out = fma(ep.alpha, widen(a), fma(ep.xs, dev::f64_of_f32(ep.x1f[of]), ep.x0[ox]));
+  } else if (ep.mode == kEpReduce) {
+    const long ox = (long)row * ep.ldx + cb, of = (long)row * ep.ldf + cb;
+    const double pg = widen(a), g = ep.x0[ox];
+    red.v0 = fma(g, pg, red.v0);
     if (red.have_dir) {
-      red.v1 = fma(ep.x1[off], out, red.v1);
-      red.v2 = fma(g, ep.x2[off], red.v2);
+      red.v1 = fma(ep.x1[ox], pg, red.v1);
+      red.v2 = fma(g, dev::f64_of_f32(ep.x2f[of]), red.v2);
     }
     red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g) & 0x7FFFFFFFFFFFFFFFull);
-    ep.xout[off] = g;
-    return out;
+    ep.xout[ox] = g;
+    reinterpret_cast<float*>(ep.C)[offc] = a;
+    if (ep.bf_hi != nullptr) {
+      __nv_bfloat16* hp = ep.bf_hi + blk * ep.bf_blk + (long)row * ep.bf_ld;
+      dev::split_store_f32(a, hp, hp + ep.bf_lo, cb);
+    }
+    return;
+  } else if (ep.c_f32) {
+    const float o = ep.alpha == 1.0 ? a : (float)ep.alpha * a;
+    reinterpret_cast<float*>(ep.C)[offc] = o;
+    if (ep.bf_hi != nullptr) {
+      __nv_bfloat16* hp = ep.bf_hi + blk * ep.bf_blk + (long)row * ep.bf_ld;
+      dev::split_store_f32(o, hp, hp + ep.bf_lo, cb);
+    }
+    return;
+  } else {
+    out = combine(ep, widen(a), ep.C + offc);
   }
-  return combine(ep, a, ep.C + off);
+  ep.C[offc] = out;
+  if (ep.bf_hi != nullptr) {
+    __nv_bfloat16* hp = ep.bf_hi + blk * ep.bf_blk + (long)row * ep.bf_ld;
+    dev::split_store_fast(out, hp, hp + ep.bf_lo, cb);
+  }
+}
+
+// eight bf16 values into one 16-byte store
+__device__ __forceinline__ void store_bf8(__nv_bfloat16* p, const unsigned short (&h)[8]) {
+  *reinterpret_cast<uint4*>(p) = make_uint4(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16),
+                                            h[4] | ((uint32_t)h[5] << 16), h[6] | ((uint32_t)h[7] << 16));
 }
 
 // C = alpha * v + beta * C (or a fused form) for the 32 accumulator columns [col0, col0 + 32) of one row.
@@ -222,7 +261,7 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
   const int nvalid = min(32, ep.N - col0);
   const long blk0 = col0 / ep.split_cols;
   const long blk1 = (col0 + nvalid - 1) / ep.split_cols;
-  if (ep.mode == kEpPlain && ep.bf_hi == nullptr) {
+  if (ep.mode == kEpPlain && ep.bf_hi == nullptr && !ep.c_f32) {
     if (blk0 == blk1) {  // specialised loops, no per-element branching
       double* base = ep.C + blk0 * ep.split_stride + (long)row * ep.ldc + (col0 - blk0 * ep.split_cols);
       if (ep.beta == 0.0) {
@@ -256,70 +295,95 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
     }
     return;
   }
-  // fused forms and split outputs (every index into v is a compile-time constant, so that the
-  // accumulator values stay in registers). Sixteen columns at a time: their inputs are loaded
-  // first (read-only path, 16-byte pairs), so that one memory latency covers them all.
+  // fused forms, float32 outputs and split outputs. Every index into v is a compile-time constant
+  // (the accumulator values stay in registers); sixteen columns at a time, their inputs loaded
+  // first (read-only path, 16-byte vectors) so that one memory latency covers them all.
   const long cb0 = col0 - blk0 * ep.split_cols;
-  const long off0 = blk0 * ep.split_stride + (long)row * ep.ldc + cb0;
+  const long offc = blk0 * ep.split_stride + (long)row * ep.ldc + cb0;
+  const long offx = (long)row * ep.ldx + cb0, offf = (long)row * ep.ldf + cb0;
   const long bf0 = blk0 * ep.bf_blk + (long)row * ep.bf_ld + cb0;
-  const bool vec = blk0 == blk1 && nvalid == 32 && ((off0 & 1) == 0) &&
+  const bool fused = ep.mode != kEpPlain;
+  const bool vec = blk0 == blk1 && nvalid == 32 && ((offc & (ep.c_f32 ? 3 : 1)) == 0) &&
+                   (!fused || ((offx & 1) == 0 && (offf & 3) == 0)) &&
                    (ep.bf_hi == nullptr || ((bf0 & 7) == 0 && (ep.bf_lo & 7) == 0));
   if (vec) {
     const bool unit = ep.alpha == 1.0 && ep.beta == 0.0;  // plain store of the accumulator
 #pragma unroll
     for (int h16 = 0; h16 < 2; ++h16) {
-      const long o = off0 + 16 * h16;
-      double out[16];
-      if (ep.mode == kEpGrad) {
-        double2 a0[8], a1[8];
+      const int c16 = 16 * h16;
+      if (ep.c_f32) {  // float32 output: the accumulator itself (kEpReduce, or kEpPlain with alpha 1)
+        float o[16];
+        const float al = (float)ep.alpha;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          a0[k] = __ldg(reinterpret_cast<const double2*>(ep.x0 + o) + k);
-          a1[k] = __ldg(reinterpret_cast<const double2*>(ep.x1 + o) + k);
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          out[2 * k] = fma(ep.alpha, widen(v[16 * h16 + 2 * k]), fma(ep.xs, a1[k].x, a0[k].x));
-          out[2 * k + 1] = fma(ep.alpha, widen(v[16 * h16 + 2 * k + 1]), fma(ep.xs, a1[k].y, a0[k].y));
-        }
-      } else if (ep.mode == kEpReduce) {
-        double2 g[8], go[8], d[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          g[k] = __ldg(reinterpret_cast<const double2*>(ep.x0 + o) + k);
-          if (red.have_dir) {
-            go[k] = *(reinterpret_cast<const double2*>(ep.x1 + o) + k);
-            d[k] = __ldg(reinterpret_cast<const double2*>(ep.x2 + o) + k);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 16; ++k) out[k] = unit ? widen(v[16 * h16 + k]) : ep.alpha * widen(v[16 * h16 + k]);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          red.v0 = fma(g[k].x, out[2 * k], red.v0);
-          red.v0 = fma(g[k].y, out[2 * k + 1], red.v0);
-          red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g[k].x) & 0x7FFFFFFFFFFFFFFFull);
-          red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g[k].y) & 0x7FFFFFFFFFFFFFFFull);
-        }
-        if (red.have_dir) {
+        for (int k = 0; k < 16; ++k) o[k] = (ep.mode == kEpReduce || unit) ? v[c16 + k] : al * v[c16 + k];
+        if (ep.mode == kEpReduce) {
+          double2 g[8], go[8];
+          float4 d[4];
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
-            red.v1 = fma(go[k].x, out[2 * k], red.v1);
-            red.v1 = fma(go[k].y, out[2 * k + 1], red.v1);
-            red.v2 = fma(g[k].x, d[k].x, red.v2);
-            red.v2 = fma(g[k].y, d[k].y, red.v2);
+            g[k] = __ldg(reinterpret_cast<const double2*>(ep.x0 + offx + c16) + k);
+            if (red.have_dir) go[k] = *(reinterpret_cast<const double2*>(ep.x1 + offx + c16) + k);
+          }
+          if (red.have_dir) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d[k] = __ldg(reinterpret_cast<const float4*>(ep.x2f + offf + c16) + k);
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const double p0 = widen(o[2 * k]), p1 = widen(o[2 * k + 1]);
+            red.v0 = fma(g[k].x, p0, red.v0);
+            red.v0 = fma(g[k].y, p1, red.v0);
+            red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g[k].x) & 0x7FFFFFFFFFFFFFFFull);
+            red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g[k].y) & 0x7FFFFFFFFFFFFFFFull);
+            if (red.have_dir) {
+              red.v1 = fma(go[k].x, p0, red.v1);
+              red.v1 = fma(go[k].y, p1, red.v1);
+              const float dx = (k & 1) ? d[k >> 1].z : d[k >> 1].x, dy = (k & 1) ? d[k >> 1].w : d[k >> 1].y;
+              red.v2 = fma(g[k].x, dev::f64_of_f32(dx), red.v2);
+              red.v2 = fma(g[k].y, dev::f64_of_f32(dy), red.v2);
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) *(reinterpret_cast<double2*>(ep.xout + offx + c16) + k) = g[k];
+        }
+        float4* c4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(ep.C) + offc + c16);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c4[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+        if (ep.bf_hi != nullptr) {
+#pragma unroll
+          for (int g8 = 0; g8 < 2; ++g8) {
+            unsigned short h[8], l[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) dev::split_bits_f32(o[8 * g8 + k], h[k], l[k]);
+            __nv_bfloat16* hp = ep.bf_hi + bf0 + c16 + 8 * g8;
+            store_bf8(hp, h);
+            store_bf8(hp + ep.bf_lo, l);
           }
         }
+        continue;
+      }
+      double out[16];
+      if (ep.mode == kEpGrad) {
+        double2 a0[8];
+        float4 a1[4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) *(reinterpret_cast<double2*>(ep.xout + o) + k) = g[k];
+        for (int k = 0; k < 8; ++k) a0[k] = __ldg(reinterpret_cast<const double2*>(ep.x0 + offx + c16) + k);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a1[k] = __ldg(reinterpret_cast<const float4*>(ep.x1f + offf + c16) + k);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float fx = (k & 1) ? a1[k >> 1].z : a1[k >> 1].x, fy = (k & 1) ? a1[k >> 1].w : a1[k >> 1].y;
+          out[2 * k] = fma(ep.alpha, widen(v[c16 + 2 * k]), fma(ep.xs, dev::f64_of_f32(fx), a0[k].x));
+          out[2 * k + 1] = fma(ep.alpha, widen(v[c16 + 2 * k + 1]), fma(ep.xs, dev::f64_of_f32(fy), a0[k].y));
+        }
       } else if (unit) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) out[k] = widen(v[16 * h16 + k]);
+        for (int k = 0; k < 16; ++k) out[k] = widen(v[c16 + k]);
       } else {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) out[k] = combine(ep, widen(v[16 * h16 + k]), ep.C + o + k);
+        for (int k = 0; k < 16; ++k) out[k] = combine(ep, widen(v[c16 + k]), ep.C + offc + c16 + k);
       }
-      double2* c2 = reinterpret_cast<double2*>(ep.C + o);
+      double2* c2 = reinterpret_cast<double2*>(ep.C + offc + c16);
 #pragma unroll
       for (int k = 0; k < 8; ++k) c2[k] = make_double2(out[2 * k], out[2 * k + 1]);
       if (ep.bf_hi != nullptr) {
@@ -328,12 +392,9 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
           unsigned short h[8], l[8];
 #pragma unroll
           for (int k = 0; k < 8; ++k) dev::split_bits_fast(out[8 * g8 + k], h[k], l[k]);
-          __nv_bfloat16* hp = ep.bf_hi + bf0 + 16 * h16 + 8 * g8;
-          *reinterpret_cast<uint4*>(hp) = make_uint4(h[0] | ((uint32_t)h[1] << 16), h[2] | ((uint32_t)h[3] << 16),
-                                                     h[4] | ((uint32_t)h[5] << 16), h[6] | ((uint32_t)h[7] << 16));
-          *reinterpret_cast<uint4*>(hp + ep.bf_lo) =
-              make_uint4(l[0] | ((uint32_t)l[1] << 16), l[2] | ((uint32_t)l[3] << 16), l[4] | ((uint32_t)l[5] << 16),
-                         l[6] | ((uint32_t)l[7] << 16));
+          __nv_bfloat16* hp = ep.bf_hi + bf0 + c16 + 8 * g8;
+          store_bf8(hp, h);
+          store_bf8(hp + ep.bf_lo, l);
         }
       }
     }
@@ -344,14 +405,7 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
     if (j >= nvalid) break;
     const int col = col0 + j;
     const long blk = col / ep.split_cols;
-    const long cb = col - blk * ep.split_cols;
-    const long off = blk * ep.split_stride + (long)row * ep.ldc + cb;
-    const double out = fused_value(ep, widen(v[j]), off, red);
-    ep.C[off] = out;
-    if (ep.bf_hi != nullptr) {
-      __nv_bfloat16* hp = ep.bf_hi + blk * ep.bf_blk + (long)row * ep.bf_ld;
-      dev::split_store_fast(out, hp, hp + ep.bf_lo, cb);
-    }
+    fused_element(ep, v[j], row, blk, col - blk * ep.split_cols, red);
   }
 }
 
@@ -383,9 +437,9 @@ template <bool FUSED>
 __device__ __forceinline__ void gemm_tile(const CUtensorMap* mA, const CUtensorMap* mB, int K, int rowsA,
                                           int rowsB, int offA, int offB, const PairList& pl, const Epilogue& ep_in,
                                           int tile) {
-  constexpr int NS = FUSED ? 2 : STAGES;
-  constexpr int SB = FUSED ? 2 * STAGE_BYTES : STAGE_BYTES;
-  static_assert(NS * SB == STAGES * STAGE_BYTES, "both modes use the same shared memory");
+  constexpr int SB = FUSED ? 2 * (A_BYTES + B_BYTES) : (A_BYTES + B_BYTES);
+  constexpr int NS = ring_stages(SB);
+  static_assert(NS >= 2 && NS * SB <= RING_BYTES && 2 * NS + 2 <= 28, "stage ring");
   const Epilogue ep = ep_in;
   if (ep.skip != nullptr && (ep.skip[0] | ep.skip[1])) return;  // uniform: before any resource use
   extern __shared__ uint8_t smem_raw[];
@@ -571,9 +625,9 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
   constexpr int TB_BYTES = TBN * BK * 2;
   constexpr int TSTAGE = A_BYTES + TB_BYTES;
   constexpr int SB = FUSED ? 2 * TSTAGE : TSTAGE;
-  constexpr int NS = (STAGES * STAGE_BYTES) / SB;
+  constexpr int NS = ring_stages(SB);
   constexpr int ACC_COLS = TBN;
-  static_assert(NS >= 2 && NS * SB <= STAGES * STAGE_BYTES && 2 * NS + 5 <= 28, "stage ring");
+  static_assert(NS >= 2 && NS * SB <= RING_BYTES && 2 * NS + 5 <= 28, "stage ring");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NS * SB);
@@ -655,7 +709,8 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
         const uint32_t full = smem_u32(&bars[q]);
         const uint32_t sa = smem_u32(smem + q * SB);
         mbar_expect_tx(full, SB);
-        // B: a K-major box of TBN rows, or (MN-major) TBN / 64 boxes of 64 x 64 placed 8 KB apart
+        // B: a K-major box of TBN rows, or (MN-major) TBN / 64 boxes of 64 x 64 placed
+        // MN_BOX_BYTES apart
         if (FUSED) {
           const int kb = kbs.at(t);
           tma_load_2d(sa, mA, full, kb * BK, g->offA + m0);
@@ -663,8 +718,8 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
           if (g->b_mn) {
 #pragma unroll
             for (int q = 0; q < TBN / 64; ++q) {
-              tma_load_2d(sa + 2 * A_BYTES + q * 8192, mB, full, n0 + 64 * q, g->offB + kb * BK);
-              tma_load_2d(sa + 2 * A_BYTES + TB_BYTES + q * 8192, mB, full, n0 + 64 * q,
+              tma_load_2d(sa + 2 * A_BYTES + q * MN_BOX_BYTES, mB, full, n0 + 64 * q, g->offB + kb * BK);
+              tma_load_2d(sa + 2 * A_BYTES + TB_BYTES + q * MN_BOX_BYTES, mB, full, n0 + 64 * q,
                           g->rowsB + g->offB + kb * BK);
             }
           } else {
@@ -677,7 +732,8 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
           if (g->b_mn) {
 #pragma unroll
             for (int q = 0; q < TBN / 64; ++q)
-              tma_load_2d(sa + A_BYTES + q * 8192, mB, full, n0 + 64 * q, (int)pl.b[p] * g->rowsB + g->offB + kb * BK);
+              tma_load_2d(sa + A_BYTES + q * MN_BOX_BYTES, mB, full, n0 + 64 * q,
+                          (int)pl.b[p] * g->rowsB + g->offB + kb * BK);
           } else {
             tma_load_2d(sa + A_BYTES, mB, full, kb * BK, (int)pl.b[p] * g->rowsB + g->offB + n0);
           }
@@ -775,6 +831,9 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
           ep.split_stride = 0;
           ep.alpha = 1.0;
           ep.beta = 0.0;
+          ep.mode = kEpPlain;
+          ep.c_f32 = 0;
+          ep.bf_hi = nullptr;
         } else if (c > 0) {
           ep.beta = 1.0;
         }
@@ -868,19 +927,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 
 // Row-major bf16 matrix rows x cols (leading dimension ld elements, ld*2 a
 // multiple of 16 bytes, base 16-byte aligned) as a TMA map with box
-// {BK, box_rows} (BK = 64 columns of 128 bytes) and 128-byte swizzle.
-TensorMap make_map(const __nv_bfloat16* base, long rows, long cols, long ld, int box_rows) {
+// {box_cols, box_rows} and 128-byte swizzle: {BK, rows} for K-major tiles (BK = 64 columns of
+// 128 bytes), {64, BK} for MN-major ones.
+TensorMap make_map(const __nv_bfloat16* base, long rows, long cols, long ld, int box_rows, int box_cols = BK) {
   TensorMap tm;
   static_assert(sizeof(TensorMap) == sizeof(CUtensorMap), "TensorMap must hold a CUtensorMap");
   if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15))
     throw CudaError{cudaErrorInvalidValue, "make_map: operand not 16-byte aligned"};
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B;
   CUresult r = encoder()(reinterpret_cast<CUtensorMap*>(&tm), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                          const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw CudaError{cudaErrorInvalidValue, "cuTensorMapEncodeTiled"};
   return tm;
@@ -893,8 +954,8 @@ Operand make_operand_view(const __nv_bfloat16* base, long slice_rows, long cols,
   Operand o;
   // the map covers the whole stack, so every slice and row offset stays inside it
   if (mn_major) {
-    o.box_rows = 64;  // 64 contracted rows x 64 output columns per box
-    o.map = make_map(base, slice_rows * slices, cols, ld, 64);
+    o.box_rows = BK;  // BK contracted rows x 64 output columns per box
+    o.map = make_map(base, slice_rows * slices, cols, ld, BK, 64);
     o.map_n128 = o.map;
   } else {
     o.box_rows = is_a ? BM : BN;
@@ -1069,14 +1130,14 @@ void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K,
 
 // ------------------------------------------------------------------ block sparsity of B
 namespace {
-// occ[rb * nkb + kb] = 1 if rows [128 rb, 128 rb + 128) x columns [64 kb, 64 kb + 64) hold a nonzero
+// occ[rb * nkb + kb] = 1 if rows [128 rb, 128 rb + 128) x columns [BK kb, BK kb + BK) hold a nonzero
 __global__ void __launch_bounds__(256)
 occupancy_kernel(const double* __restrict__ B, long rows, long cols, long ld, int nkb, unsigned char* occ) {
   const long blk = blockIdx.x;
   const long rb = blk / nkb, kb = blk % nkb;
   int any = 0;
-  for (int e = threadIdx.x; e < 128 * 64; e += blockDim.x) {
-    const long r = rb * 128 + e / 64, c = kb * 64 + e % 64;
+  for (int e = threadIdx.x; e < 128 * BK; e += blockDim.x) {
+    const long r = rb * 128 + e / BK, c = kb * BK + e % BK;
     if (r < rows && c < cols && B[r * ld + c] != 0.0) any = 1;
   }
   any = __syncthreads_or(any);

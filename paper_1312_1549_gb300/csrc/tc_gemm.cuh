@@ -56,17 +56,19 @@ PairList pairs_single();   // A_0 B_0
 // matrices. When skip[0] | skip[1] (the solver's done/halt flags) the kernel
 // does nothing. err receives a nonzero code if a bounded wait expired.
 //
-// Fused forms (mode; x0, x1, x2, xout are float64 matrices laid out like C, and need
-// split_cols = N):
-//   kEpPlain   the above.
-//   kEpGrad    C = alpha * acc + (x0 + xs * x1)   (the incremental gradient about a refresh
-//              point: x0 = G_ref, x1 = dHC, xs = 8, alpha = -4; beta is not used)
-//   kEpReduce  C = alpha * acc, and with g = x0, g_old = x1, d = x2 the sums <g, C>,
-//              <g_old, C>, <g, d> (the last two only when sc->have_dir) and max|g| of each
-//              epilogue warp's rows of the tile go to part[(tile * 4 + warp) * 4 + 0..3]; then
-//              xout = g (xout may alias x1: every element is read before it is written).
+// Fused forms (mode), all with split_cols = N unless stated:
+//   kEpPlain   the above; with c_f32 C is float32 and receives alpha * acc (beta is not used;
+//              split_cols and split_stride apply, in float elements).
+//   kEpGrad    C = alpha * acc + (x0 + xs * x1f)   (the incremental gradient about a refresh
+//              point: x0 = G_ref (float64), x1f = dHC (float32), xs = 8, alpha = -4)
+//   kEpReduce  C = acc as float32 (c_f32 = 1, alpha = 1), and with g = x0, g_old = x1 (float64),
+//              d = x2f (float32) the sums <g, C>, <g_old, C>, <g, d> (the last two only when
+//              sc->have_dir) and max|g| of each epilogue warp's rows of the tile go to
+//              part[(tile * 4 + warp) * 4 + 0..3]; then xout = g (xout may alias x1: every
+//              element is read before it is written).
+// Element (row, col) of x0, x1, xout is at row * ldx + col, of x1f, x2f at row * ldf + col.
 // bf_hi != null (any mode): the stored value is also split into bf16 hi and lo, written to
-// bf_hi + blk * bf_blk + row * bf_ld + j % split_cols and the same plus bf_lo.
+// bf_hi + blk * bf_blk + row * bf_ld + col % split_cols and the same plus bf_lo.
 // expire != 0 (tests only): before it issues any copy or MMA the kernel waits about 1 ms on a
 // barrier that nothing arrives at, reports the expired wait in err and does nothing else.
 enum { kEpPlain = 0, kEpGrad = 1, kEpReduce = 2 };
@@ -82,10 +84,14 @@ struct Epilogue {
   const int* skip;
   int* err;
   int mode = kEpPlain;
+  int c_f32 = 0;
   const double* x0 = nullptr;
   const double* x1 = nullptr;
-  const double* x2 = nullptr;
   double* xout = nullptr;
+  long ldx = 0;
+  const float* x1f = nullptr;
+  const float* x2f = nullptr;
+  long ldf = 0;
   double xs = 0.0;
   double* part = nullptr;
   const Scalars* sc = nullptr;
