@@ -140,8 +140,10 @@ typedef struct {
                                 or preconditioner-grade sliced products on the mixed path (m >=
                                 2048); with opts.cholesky the factor L, L^-1 and H_r = L^-1 H L^-T
                                 instead */
-  int tile_width[4];         /* mixed: output tile width (256 or 128 columns) the autotuner chose for
-                                the P G, [H D; S D], projection and gradient GEMMs (0: not run) */
+  int tile_width[4];         /* mixed: output tile shape the autotuner chose for the P G, [H D; S D],
+                                projection and gradient GEMMs: 256 or 128 (columns of a 128-row
+                                tile on one SM), 1000 + 128, 192 or 256 (a 256-row tile on a pair
+                                of SMs), 0: not run */
   double ms_autotune;        /* time the autotuner spent timing candidates (0 when cached) */
   double ms_sliced_gemm;     /* with opts.profile: summed duration of the float64-class sliced
                                 products of omm_create (inverse) and this solve (refreshes,

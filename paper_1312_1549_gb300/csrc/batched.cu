@@ -103,12 +103,8 @@ constexpr int kGroupedGemms = 4;
 constexpr int kRefreshStreams = 8;
 
 template <typename T>
-void alloc(T** p, size_t count) {
-  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
-    cudaGetLastError();
-    *p = nullptr;
-    throw std::bad_alloc();
-  }
+void alloc(T** p, size_t count, cudaStream_t st) {
+  mem::alloc(p, count, st);
 }
 
 }  // namespace
@@ -163,11 +159,10 @@ void batch_destroy(omm_batch* b) {
     }
     destroy(c);
   }
-  for (Grouped* g : {&b->gPG, &b->gHD, &b->gPr, &b->gG})
-    if (g->dev) cudaFree(g->dev);
-  if (b->args) cudaFree(b->args);
-  if (b->err) cudaFree(b->err);
-  if (b->sc_all) cudaFree(b->sc_all);
+  for (Grouped* g : {&b->gPG, &b->gHD, &b->gPr, &b->gG}) mem::release(g->dev, b->st);
+  mem::release(b->args, b->st);
+  mem::release(b->err, b->st);
+  mem::release(b->sc_all, b->st);
   if (b->sc_host_all) cudaFreeHost(b->sc_host_all);
   delete b;
 }
@@ -177,7 +172,7 @@ void upload_groups(cudaStream_t st, Grouped* g, const std::vector<tc::GroupDesc>
   if (v.empty()) return;
   g->tiles = v.back().tile_begin + tc::tiles_of(v.back().ep, v.back().bn);
   g->bn = v.back().bn;
-  alloc(&g->dev, v.size());
+  alloc(&g->dev, v.size(), st);
   OMM_CUDA_TRY(cudaMemcpyAsync(g->dev, v.data(), v.size() * sizeof(tc::GroupDesc), cudaMemcpyHostToDevice, st));
 }
 
@@ -288,14 +283,14 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
     return OMM_OK;
   }
   try {
-    alloc(&b->sc_all, count);
+    alloc(&b->sc_all, count, b->st);
     OMM_CUDA_TRY(cudaMallocHost((void**)&b->sc_host_all, count * sizeof(Scalars)));
     std::vector<IterArgs> args(count);
     std::vector<tc::GroupDesc> gpg, ghd, gpr, gg;
     std::vector<tc::GemmSpec> spg, shd, spr, sg;
     for (int i = 0; i < count; ++i) {
       omm_ctx* c = b->ctx[i];
-      cudaFree(c->sc);
+      mem::release(c->sc, b->st);
       c->sc = b->sc_all + i;
       cudaFreeHost(c->sc_host);
       c->sc_host = b->sc_host_all + i;
@@ -363,8 +358,8 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       }
     }
     for (cudaStream_t& q : b->pool) OMM_CUDA_TRY(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
-    alloc(&b->args, count);
-    alloc(&b->err, 1);
+    alloc(&b->args, count, b->st);
+    alloc(&b->err, 1, b->st);
     OMM_CUDA_TRY(cudaMemsetAsync(b->err, 0, sizeof(int), b->st));
     OMM_CUDA_TRY(cudaMemcpyAsync(b->args, args.data(), count * sizeof(IterArgs), cudaMemcpyHostToDevice, b->st));
     upload_groups(b->st, &b->gPG, gpg);

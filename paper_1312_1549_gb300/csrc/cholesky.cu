@@ -153,36 +153,45 @@ leaf_f32_kernel(const double* A, long lda, int b, double* Linv, int* info, int c
   float (*T)[NL + 1] = reinterpret_cast<float (*)[NL + 1]>(smf + 2 * NL * (NL + 1));
   float* rdiag = smf + 3 * NL * (NL + 1);
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int idx = tid; idx < NL * NL; idx += nt) {
-    const int i = idx / NL, j = idx % NL;
-    L[i][j] = (i < b && j <= i) ? to_f32(A[(long)i * lda + j]) : 0.f;
-    X[i][j] = 0.f;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+  for (int i = warp; i < NL; i += nwarps)
+    for (int j = lane; j < NL; j += 32) {
+      L[i][j] = (i < b && j <= i) ? to_f32(A[(long)i * lda + j]) : 0.f;
+      X[i][j] = 0.f;
+    }
+  __syncthreads();
+  // Right-looking, one column per step and one barrier per step: step j reads the pivot and
+  // column j (final after step j - 1) and updates the trailing lower triangle with the column
+  // scaled on the fly, L_il -= (L_ij / sqrt(d)) (L_lj / sqrt(d)); column j itself is scaled in
+  // step j + 1, which neither reads nor writes it otherwise. Warp w takes rows j+1+w, j+1+w+16,
+  // ..., its lanes the columns of a row.
+  float s_prev = 1.f, r_prev = 1.f;  // sqrt(d) and 1 / sqrt(d) of the previous pivot
+  for (int j = 0; j <= b; ++j) {
+    if (j > 0) {  // finish column j - 1
+      const int c = j - 1;
+      if (tid == 0) {
+        L[c][c] = s_prev;
+        rdiag[c] = r_prev;
+      }
+      for (int i = c + 1 + tid; i < b; i += nt) L[i][c] *= r_prev;
+    }
+    if (j == b) break;
+    float d = L[j][j];
+    if (!(d > 0.f)) {
+      if (tid == 0) atomicCAS(info, 0, col_offset + j + 1);
+      d = 1.f;
+    }
+    const float sj = sqrtf(d), rj = 1.f / sj;
+    for (int i = j + 1 + warp; i < b; i += nwarps) {
+      const float ai = L[i][j] * rj;
+      for (int l = j + 1 + lane; l <= i; l += 32) L[i][l] = fmaf(-ai, L[l][j] * rj, L[i][l]);
+    }
+    s_prev = sj;
+    r_prev = rj;
+    __syncthreads();
   }
   __syncthreads();
-  for (int j = 0; j < b; ++j) {  // right-looking, one column at a time
-    if (tid == 0) {
-      float d = L[j][j];
-      if (!(d > 0.f)) {
-        atomicCAS(info, 0, col_offset + j + 1);
-        d = 1.f;
-      }
-      const float r = sqrtf(d);
-      L[j][j] = r;
-      rdiag[j] = 1.f / r;
-    }
-    __syncthreads();
-    const float rj = rdiag[j];
-    for (int i = j + 1 + tid; i < b; i += nt) L[i][j] *= rj;
-    __syncthreads();
-    const int r = b - j - 1;
-    for (int idx = tid; idx < r * r; idx += nt) {
-      const int i = j + 1 + idx / r, l = j + 1 + idx % r;
-      if (l <= i) L[i][l] = fmaf(-L[i][j], L[l][j], L[i][l]);
-    }
-    __syncthreads();
-  }
   // 16 x 16 diagonal blocks: lane c of warp w solves column c of block w
-  const int warp = tid >> 5, lane = tid & 31;
   const int nb16 = (b + 15) / 16;
   if (warp < nb16 && lane < 16) {
     const int o = warp * 16, e = min(16, b - o), c = lane;

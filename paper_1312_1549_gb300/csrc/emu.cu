@@ -92,12 +92,8 @@ __global__ void transpose_kernel(const double* __restrict__ src, long rows, long
 long round8(long x) { return (x + 7) / 8 * 8; }
 
 template <typename T>
-void alloc(T** p, size_t count) {
-  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
-    cudaGetLastError();
-    *p = nullptr;
-    throw std::bad_alloc();
-  }
+void alloc(T** p, size_t count, cudaStream_t st) {
+  mem::alloc(p, count, st);
 }
 
 }  // namespace
@@ -195,20 +191,20 @@ EmuState* emu_create(cudaStream_t st, int m, int n, int slices, const double* HS
     es->ldm = round8(m);
     es->ld2n = round8(2L * n);
     const long s = slices, ldm = es->ldm, ld2n = es->ld2n;
-    alloc(&es->HSs, (size_t)s * 2 * m * ldm);
-    alloc(&es->Cs, (size_t)s * n * ldm);
-    alloc(&es->Ys, (size_t)s * 2 * n * ldm);
-    alloc(&es->Ws, (size_t)s * n * ld2n);
-    alloc(&es->YTs, (size_t)s * m * ld2n);
-    alloc(&es->T64, (size_t)m * 2 * n);
+    alloc(&es->HSs, (size_t)s * 2 * m * ldm, st);
+    alloc(&es->Cs, (size_t)s * n * ldm, st);
+    alloc(&es->Ys, (size_t)s * 2 * n * ldm, st);
+    alloc(&es->Ws, (size_t)s * n * ld2n, st);
+    alloc(&es->YTs, (size_t)s * m * ld2n, st);
+    alloc(&es->T64, (size_t)m * 2 * n, st);
     es->ldn = round8(n);
-    alloc(&es->CTs, (size_t)kDensitySlices * m * es->ldn);
-    alloc(&es->XTs, (size_t)kDensitySlices * m * es->ldn);
-    alloc(&es->SWs, (size_t)kDensitySlices * n * es->ldn);
-    alloc(&es->err, 1);
+    alloc(&es->CTs, (size_t)kDensitySlices * m * es->ldn, st);
+    alloc(&es->XTs, (size_t)kDensitySlices * m * es->ldn, st);
+    alloc(&es->SWs, (size_t)kDensitySlices * n * es->ldn, st);
+    alloc(&es->err, 1, st);
     // the [S_W | H_W] product (n x 2n) is the one with few tiles; 11 chunks at most for K <= 16384
     es->partial_cap = std::min(11L * n * 2L * n, 1L << 25);
-    alloc(&es->partial, (size_t)es->partial_cap);
+    alloc(&es->partial, (size_t)es->partial_cap, st);
     OMM_CUDA_TRY(cudaMemsetAsync(es->err, 0, sizeof(int), st));
     emu::slice_rows(st, HS, 2L * m, m, m, slices, es->HSs, ldm, nullptr);
     tc::block_lists(st, HS, 2L * m, m, m, 256, es->hs_blocks);
@@ -222,7 +218,7 @@ EmuState* emu_create(cudaStream_t st, int m, int n, int slices, const double* HS
     es->opSW = tc::make_operand(es->SWs, n, n, es->ldn, kDensitySlices, false);
     es->opCTb = tc::make_operand(es->CTs, m, n, es->ldn, kDensitySlices, false);
   } catch (...) {
-    emu_destroy(es);
+    emu_destroy(es, st);
     throw;
   }
   return es;
@@ -233,12 +229,11 @@ void emu_update_H(EmuState* es, cudaStream_t st, const double* HS) {
   tc::block_lists(st, HS, 2L * es->m, es->m, es->m, 256, es->hs_blocks);
 }
 
-void emu_destroy(EmuState* es) {
+void emu_destroy(EmuState* es, cudaStream_t st) {
   if (!es) return;
   void* bufs[] = {es->HSs, es->Cs, es->Ys, es->Ws, es->YTs, es->T64, es->CTs, es->XTs, es->SWs, es->err, es->partial};
-  for (void* b : bufs)
-    if (b) cudaFree(b);
-  tc::free_block_lists(es->hs_blocks);
+  for (void* b : bufs) mem::release(b, st);
+  tc::free_block_lists(es->hs_blocks, st);
   delete es;
 }
 

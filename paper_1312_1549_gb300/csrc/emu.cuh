@@ -23,7 +23,7 @@ void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, in
 struct EmuState;
 EmuState* emu_create(cudaStream_t st, int m, int n, int slices, const double* HS);
 void emu_update_H(EmuState* es, cudaStream_t st, const double* HS);
-void emu_destroy(EmuState* es);
+void emu_destroy(EmuState* es, cudaStream_t st);  // st: the owner's current stream
 int emu_error(EmuState* es, cudaStream_t st);
 // density matrix D = 2 C^T (2I - S_W) C (m x m) with float64-class products
 void emu_density(EmuState* es, cudaStream_t st, const double* C, const double* SWHW, double* D);

@@ -83,12 +83,8 @@ __global__ void project_rows_kernel(int n, int m, double* __restrict__ Ce) {
 unsigned grid_for(long count) { return (unsigned)std::min<long>((count + 255) / 256, 4096); }
 
 template <typename T>
-void alloc(T** p, size_t count) {
-  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
-    *p = nullptr;
-    cudaGetLastError();
-    throw std::bad_alloc();
-  }
+void alloc(T** p, size_t count, cudaStream_t st) {
+  mem::alloc(p, count, st);
 }
 
 // phi(A) of a complex m x m matrix (host or device) into dst (device, 4 m^2 doubles); stage: 2 m^2
@@ -145,8 +141,8 @@ void attach(omm_ctx* c, int m, int n) {
   c->real_form = true;
   c->mc = m;
   c->nc = n;
-  alloc(&c->hz_stage, 2 * (size_t)m * m);
-  alloc(&c->hz_rows, 4 * (size_t)n * m);
+  alloc(&c->hz_stage, 2 * (size_t)m * m, c->st);
+  alloc(&c->hz_rows, 4 * (size_t)n * m, c->st);
 }
 
 // complex C0 -> embedded rows in hz_rows
@@ -193,11 +189,11 @@ omm_status omm_create_hermitian(int m, int n, const double* H, const double* S, 
   omm_status rc = OMM_OK;
   auto release = [&]() {
     cudaStreamSynchronize(st);
-    if (block) cudaFree(block);
+    mem::release(block, st);
     block = nullptr;
   };
   try {
-    alloc(&block, embedded_doubles(m, T != nullptr));
+    alloc(&block, embedded_doubles(m, T != nullptr), st);
     embed_inputs(st, m, H, S, T, block, e);
     rc = omm_create(2 * m, 2 * n, e.H, e.S, e.T, eta, tau, opts, stream, out);
     release();
@@ -221,17 +217,17 @@ omm_status omm_update_H_hermitian(omm_ctx* c, const double* H) {
   if (!H) return fail(OMM_ERR_ARG, "omm_update_H_hermitian: NULL argument");
   double* He = nullptr;
   try {
-    alloc(&He, 4 * (size_t)c->mc * c->mc);
+    alloc(&He, 4 * (size_t)c->mc * c->mc, c->st);
     embed_matrix(c->st, c->mc, H, c->hz_stage, He);
     c->hermitian = false;  // the real update of the embedded matrix
     rc = omm_update_H(c, He);
     c->hermitian = true;
-    cudaFree(He);
+    mem::release(He, c->st);
   } catch (const std::bad_alloc&) {
     return fail(OMM_ERR_OOM, "omm_update_H_hermitian: device allocation failed");
   } catch (const CudaError& err) {
     cudaStreamSynchronize(c->st);
-    if (He) cudaFree(He);
+    mem::release(He, c->st);
     c->hermitian = true;
     return fail(OMM_ERR_CUDA, std::string("omm_update_H_hermitian: ") + err.what + ": " + cudaGetErrorString(err.err));
   }
@@ -249,7 +245,7 @@ omm_status omm_solve_hermitian(omm_ctx* c, const double* C0, double* C, double* 
   try {
     embed_start(c, c->st, C0);
     if (D) {
-      if (!c->mm) alloc(&c->mm, 4 * (size_t)m * m);
+      if (!c->mm) alloc(&c->mm, 4 * (size_t)m * m, c->st);
       De = c->mm;
     }
     c->hermitian = false;
@@ -280,7 +276,7 @@ omm_status omm_backward_hermitian(omm_ctx* c, double* dEdH, double* dEdS) {
   const int m = c->mc;
   double* tmp = nullptr;
   try {
-    alloc(&tmp, 4 * (size_t)m * m);
+    alloc(&tmp, 4 * (size_t)m * m, c->st);
     c->hermitian = false;
     for (int k = 0; k < 2 && rc == OMM_OK; ++k) {
       double* out = k == 0 ? dEdH : dEdS;
@@ -290,14 +286,14 @@ omm_status omm_backward_hermitian(omm_ctx* c, double* dEdH, double* dEdS) {
     }
     c->hermitian = true;
     OMM_CUDA_TRY(cudaStreamSynchronize(c->st));
-    cudaFree(tmp);
+    mem::release(tmp, c->st);
   } catch (const std::bad_alloc&) {
     c->hermitian = true;
     return fail(OMM_ERR_OOM, "omm_backward_hermitian: device allocation failed");
   } catch (const CudaError& err) {
     c->hermitian = true;
     cudaStreamSynchronize(c->st);
-    if (tmp) cudaFree(tmp);
+    mem::release(tmp, c->st);
     return fail(OMM_ERR_CUDA, std::string("omm_backward_hermitian: ") + err.what + ": " + cudaGetErrorString(err.err));
   }
   return rc;
@@ -325,11 +321,11 @@ omm_status omm_create_hermitian_batched(int count, const int* m, const int* n, c
   omm_status rc = OMM_OK;
   auto release = [&]() {
     cudaStreamSynchronize(st);
-    if (block) cudaFree(block);
+    mem::release(block, st);
     block = nullptr;
   };
   try {
-    alloc(&block, offset[count]);
+    alloc(&block, offset[count], st);
     for (int i = 0; i < count; ++i) {
       embed_inputs(st, m[i], H[i], S[i], T ? T[i] : nullptr, block + offset[i], e[i]);
       m2[i] = 2 * m[i];

@@ -186,78 +186,28 @@ omm_status omm_kernel_quartic_coefficients(int n, const double* SWHW, const doub
 
 namespace {
 
-// the persistent launch the solver uses for its line-search GEMMs, on freshly split operands;
-// block_sparse: skip the 64-wide K blocks where B is zero (lists built from B)
+// the persistent launch the solver uses for its line-search GEMMs, on freshly split operands.
+// block_sparse: skip the 64-wide K blocks where B is zero (lists built from B); b_kn: B is given
+// K x N and read MN-major; pair: 256-row tiles on pairs of SMs (split form only)
 omm_status gemm_tc_impl(const char* name, int M, int N, int K, const double* A, const double* B, double alpha,
-                        double beta, double* C, int npass, int tile_n, bool block_sparse, void* stream) {
-  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || (npass != 1 && npass != 3) ||
-      (tile_n != 128 && tile_n != 256)) {
+                        double beta, double* C, int npass, int tile_n, bool block_sparse, bool b_kn, bool pair,
+                        void* stream) {
+  const bool width_ok = pair ? (tile_n == 128 || tile_n == 256 || (tile_n == 192 && !b_kn))
+                             : (tile_n == 128 || tile_n == 256);
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || (npass != 1 && npass != 3) || (pair && npass != 3) ||
+      !width_ok || (b_kn && (npass != 3 || block_sparse))) {
     set_last_error(std::string(name) + ": invalid argument");
     return OMM_ERR_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  const long ld = (K + 7) / 8 * 8;
+  const long lda = (K + 7) / 8 * 8, ldb = b_kn ? (N + 7) / 8 * 8 : lda;
   __nv_bfloat16* buf = nullptr;
   int* err = nullptr;
   tc::GroupDesc* desc = nullptr;
   tc::BlockLists lists;
   omm_status rc = OMM_OK;
   try {
-    const size_t na = (size_t)M * ld, nb = (size_t)N * ld;
-    if (cudaMalloc((void**)&buf, 2 * (na + nb) * sizeof(__nv_bfloat16)) != cudaSuccess ||
-        cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess ||
-        cudaMalloc((void**)&desc, sizeof(tc::GroupDesc)) != cudaSuccess) {
-      cudaGetLastError();
-      if (buf) cudaFree(buf);
-      if (err) cudaFree(err);
-      set_last_error(std::string(name) + ": device allocation failed");
-      return OMM_ERR_OOM;
-    }
-    __nv_bfloat16 *a_hi = buf, *a_lo = buf + na, *b_hi = buf + 2 * na, *b_lo = buf + 2 * na + nb;
-    OMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
-    tc::split(st, A, M, K, K, a_hi, a_lo, ld, nullptr);
-    tc::split(st, B, N, K, K, b_hi, b_lo, ld, nullptr);
-    tc::Operand oa = tc::make_operand(a_hi, M, K, ld, 2, true);
-    tc::Operand ob = tc::make_operand(b_hi, N, K, ld, 2, false);
-    if (block_sparse) tc::block_lists(st, B, N, K, K, tile_n, lists);
-    const tc::Epilogue ep{C, N, N, 0, alpha, beta, M, N, nullptr, err};
-    const tc::GroupDesc g = tc::make_group(oa, ob, K, ep, 0, tile_n, block_sparse ? &lists : nullptr);
-    OMM_CUDA_TRY(cudaMemcpyAsync(desc, &g, sizeof(g), cudaMemcpyHostToDevice, st));
-    tc::gemm_persistent(st, desc, 1, tc::tiles_of(ep, tile_n), npass == 3 ? tc::pairs_split3() : tc::pairs_single(),
-                        err, tile_n);
-    int h = 0;
-    OMM_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    OMM_CUDA_TRY(cudaStreamSynchronize(st));
-    if (h != 0) {
-      set_last_error(std::string(name) + ": a bounded device wait expired (code " + std::to_string(h) + ")");
-      rc = OMM_ERR_TIMEOUT;
-    }
-  } catch (const CudaError& e) {
-    rc = cuda_fail(name, e);
-  }
-  if (buf) cudaFree(buf);
-  if (err) cudaFree(err);
-  if (desc) cudaFree(desc);
-  tc::free_block_lists(lists);
-  return rc;
-}
-
-// C = alpha A B + beta C with B stored K x N (row-major): the B operand is read MN-major, as the
-// solver's gradient GEMM reads its operand stack
-omm_status gemm_tc_kn_impl(const char* name, int M, int N, int K, const double* A, const double* B, double alpha,
-                           double beta, double* C, int tile_n, void* stream) {
-  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || (tile_n != 128 && tile_n != 256)) {
-    set_last_error(std::string(name) + ": invalid argument");
-    return OMM_ERR_ARG;
-  }
-  cudaStream_t st = (cudaStream_t)stream;
-  const long lda = (K + 7) / 8 * 8, ldb = (N + 7) / 8 * 8;
-  __nv_bfloat16* buf = nullptr;
-  int* err = nullptr;
-  tc::GroupDesc* desc = nullptr;
-  omm_status rc = OMM_OK;
-  try {
-    const size_t na = (size_t)M * lda, nb = (size_t)K * ldb;
+    const size_t na = (size_t)M * lda, nb = (size_t)(b_kn ? K : N) * ldb;
     if (cudaMalloc((void**)&buf, 2 * (na + nb) * sizeof(__nv_bfloat16)) != cudaSuccess ||
         cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess ||
         cudaMalloc((void**)&desc, sizeof(tc::GroupDesc)) != cudaSuccess) {
@@ -270,13 +220,21 @@ omm_status gemm_tc_kn_impl(const char* name, int M, int N, int K, const double* 
     __nv_bfloat16 *a_hi = buf, *a_lo = buf + na, *b_hi = buf + 2 * na, *b_lo = buf + 2 * na + nb;
     OMM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
     tc::split(st, A, M, K, K, a_hi, a_lo, lda, nullptr);
-    tc::split(st, B, K, N, N, b_hi, b_lo, ldb, nullptr);
     tc::Operand oa = tc::make_operand(a_hi, M, K, lda, 2, true);
-    tc::Operand ob = tc::make_operand_view(b_hi, K, N, ldb, 2, false, 0, K, /*mn_major=*/true);
+    tc::Operand ob;
+    if (b_kn) {
+      tc::split(st, B, K, N, N, b_hi, b_lo, ldb, nullptr);
+      ob = tc::make_operand_view(b_hi, K, N, ldb, 2, false, 0, K, /*mn_major=*/true);
+    } else {
+      tc::split(st, B, N, K, K, b_hi, b_lo, ldb, nullptr);
+      ob = tc::make_operand(b_hi, N, K, ldb, 2, false);
+    }
+    if (block_sparse) tc::block_lists(st, B, N, K, K, tile_n, lists);
     const tc::Epilogue ep{C, N, N, 0, alpha, beta, M, N, nullptr, err};
-    const tc::GroupDesc g = tc::make_group(oa, ob, K, ep, 0, tile_n, nullptr);
+    const tc::GroupDesc g = tc::make_group(oa, ob, K, ep, 0, tile_n, block_sparse ? &lists : nullptr, pair);
     OMM_CUDA_TRY(cudaMemcpyAsync(desc, &g, sizeof(g), cudaMemcpyHostToDevice, st));
-    tc::gemm_persistent(st, desc, 1, tc::tiles_of(ep, tile_n), tc::pairs_split3(), err, tile_n);
+    tc::gemm_persistent(st, desc, 1, tc::tiles_of(ep, tile_n, pair),
+                        npass == 3 ? tc::pairs_split3() : tc::pairs_single(), err, tile_n, pair);
     int h = 0;
     OMM_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -290,6 +248,7 @@ omm_status gemm_tc_kn_impl(const char* name, int M, int N, int K, const double* 
   if (buf) cudaFree(buf);
   if (err) cudaFree(err);
   if (desc) cudaFree(desc);
+  tc::free_block_lists(lists, st);
   return rc;
 }
 
@@ -299,23 +258,30 @@ extern "C" {
 
 omm_status omm_kernel_gemm_tc_kn(int M, int N, int K, const double* A, const double* B, double alpha, double beta,
                                  double* C, int tile_n, void* stream) {
-  return gemm_tc_kn_impl("omm_kernel_gemm_tc_kn", M, N, K, A, B, alpha, beta, C, tile_n, stream);
+  return gemm_tc_impl("omm_kernel_gemm_tc_kn", M, N, K, A, B, alpha, beta, C, 3, tile_n, false, true, false, stream);
+}
+
+omm_status omm_kernel_gemm_tc_pair(int M, int N, int K, const double* A, const double* B, double alpha, double beta,
+                                   double* C, int tile_n, int b_kn, int block_sparse, void* stream) {
+  return gemm_tc_impl("omm_kernel_gemm_tc_pair", M, N, K, A, B, alpha, beta, C, 3, tile_n, block_sparse != 0,
+                      b_kn != 0, true, stream);
 }
 
 omm_status omm_kernel_gemm_tc_tiled(int M, int N, int K, const double* A, const double* B, double alpha,
                                     double beta, double* C, int npass, int tile_n, void* stream) {
-  return gemm_tc_impl("omm_kernel_gemm_tc_tiled", M, N, K, A, B, alpha, beta, C, npass, tile_n, false, stream);
+  return gemm_tc_impl("omm_kernel_gemm_tc_tiled", M, N, K, A, B, alpha, beta, C, npass, tile_n, false, false, false,
+                      stream);
 }
 
 omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double* B, double alpha,
                               double beta, double* C, int npass, void* stream) {
-  return gemm_tc_impl("omm_kernel_gemm_tc", M, N, K, A, B, alpha, beta, C, npass, 256, false, stream);
+  return gemm_tc_impl("omm_kernel_gemm_tc", M, N, K, A, B, alpha, beta, C, npass, 256, false, false, false, stream);
 }
 
 omm_status omm_kernel_gemm_tc_blocksparse(int M, int N, int K, const double* A, const double* B, double alpha,
                                           double beta, double* C, int npass, int tile_n, void* stream) {
-  return gemm_tc_impl("omm_kernel_gemm_tc_blocksparse", M, N, K, A, B, alpha, beta, C, npass, tile_n, true,
-                      stream);
+  return gemm_tc_impl("omm_kernel_gemm_tc_blocksparse", M, N, K, A, B, alpha, beta, C, npass, tile_n, true, false,
+                      false, stream);
 }
 
 omm_status omm_kernel_gemm_emu(int M, int N, int K, const double* A, const double* B, double alpha,

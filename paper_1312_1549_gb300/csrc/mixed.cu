@@ -43,13 +43,13 @@ struct MixedState {
   float* HD32 = nullptr;                               // 2n x m
   float* dY32 = nullptr;                               // 2n x m
   tc::Operand opHS, opP, opG, opD, opYproj, opYgrad, opYhc, opW;
-  tc::BlockLists hs_blocks[2];  // block sparsity of [H~; S] for 256- and 128-row blocks (Sec. 2.6)
+  tc::BlockLists hs_blocks[3];  // block sparsity of [H~; S] for 256-, 128- and 192-row blocks (Sec. 2.6)
   int* err = nullptr;
   int expire = 0;  // tests: the first line-search GEMM of every line search waits on nothing and expires
   // the four line-search GEMMs as persistent-launch descriptors (device), built on first use
   tc::GroupDesc* plans = nullptr;
   int plan_tiles[4] = {0, 0, 0, 0};
-  int plan_bn[4] = {256, 256, 256, 256};  // output tile widths chosen by the autotuner
+  tc::TileShape plan_shape[4];             // output tile shapes chosen by the autotuner
   double ms_autotune = 0.0;               // time the autotuner spent timing candidates
   const Scalars* plan_sc = nullptr;
 };
@@ -57,14 +57,13 @@ struct MixedState {
 namespace {
 
 long round8(long x) { return (x + 7) / 8 * 8; }
+// output tiles of the P G product (n x m) counted as 128 x 128 tiles, rounded so that 256-row tiles
+// (two slots of four warps each) fit too
+long red_tiles(long n, long m) { return 2 * ((n + 255) / 256) * ((m + 127) / 128); }
 
 template <typename T>
-void alloc(T** p, size_t count) {
-  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
-    cudaGetLastError();
-    *p = nullptr;
-    throw std::bad_alloc();
-  }
+void alloc(T** p, size_t count, cudaStream_t st) {
+  mem::alloc(p, count, st);
 }
 
 }  // namespace
@@ -79,8 +78,8 @@ MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const 
     ms->precond = (P != nullptr);
     const long ldm = ms->ldm, ld4n = ms->ld4n;
     // each split operand is one allocation holding the stack [hi; lo]
-    auto pair = [](__nv_bfloat16** hi, __nv_bfloat16** lo, long rows, long ld) {
-      alloc(hi, 2 * (size_t)rows * ld);
+    auto pair = [st](__nv_bfloat16** hi, __nv_bfloat16** lo, long rows, long ld) {
+      alloc(hi, 2 * (size_t)rows * ld, st);
       *lo = *hi + rows * ld;
     };
     pair(&ms->HS_hi, &ms->HS_lo, 2L * m, ldm);
@@ -89,17 +88,19 @@ MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const 
     pair(&ms->D_hi, &ms->D_lo, n, ldm);
     pair(&ms->Y_hi, &ms->Y_lo, 6L * n, ldm);
     pair(&ms->W_hi, &ms->W_lo, n, ld4n);
-    alloc(&ms->Gref, (size_t)n * m);
-    alloc(&ms->Wref, 2L * n * n);
-    alloc(&ms->Dir32, (size_t)n * ldm);
-    alloc(&ms->PG32, (size_t)n * ldm);
-    alloc(&ms->HD32, 2L * n * ldm);
-    alloc(&ms->dY32, 2L * n * ldm);
+    alloc(&ms->Gref, (size_t)n * m, st);
+    alloc(&ms->Wref, 2L * n * n, st);
+    alloc(&ms->Dir32, (size_t)n * ldm, st);
+    alloc(&ms->PG32, (size_t)n * ldm, st);
+    alloc(&ms->HD32, 2L * n * ldm, st);
+    alloc(&ms->dY32, 2L * n * ldm, st);
     OMM_CUDA_TRY(cudaMemsetAsync(ms->Dir32, 0, (size_t)n * ldm * sizeof(float), st));
-    alloc(&ms->red, (size_t)16 * ((n + 127) / 128) * ((m + 127) / 128));  // 4 warps x 4 sums per 128 x 128 tile
-    alloc(&ms->err, 1);
+    // 4 sums per epilogue warp (4 per 128-row tile, 8 per 256-row tile) and output tile, at the
+    // narrowest tile (128 columns)
+    alloc(&ms->red, (size_t)16 * red_tiles(n, m), st);
+    alloc(&ms->err, 1, st);
     OMM_CUDA_TRY(cudaMemsetAsync(ms->err, 0, sizeof(int), st));
-    OMM_CUDA_TRY(cudaMemsetAsync(ms->red, 0, (size_t)16 * ((n + 127) / 128) * ((m + 127) / 128) * sizeof(double), st));
+    OMM_CUDA_TRY(cudaMemsetAsync(ms->red, 0, (size_t)16 * red_tiles(n, m) * sizeof(double), st));
     // padding columns stay zero (the tensor maps never read them, but keep them defined)
     OMM_CUDA_TRY(cudaMemsetAsync(ms->Y_hi, 0, 2 * (size_t)6 * n * ldm * 2, st));
     OMM_CUDA_TRY(cudaMemsetAsync(ms->W_hi, 0, 2 * (size_t)n * ld4n * 2, st));
@@ -117,17 +118,17 @@ MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const 
     ms->opYhc = tc::make_operand_view(ms->Y_hi, 6L * n, m, ldm, 2, false, 2 * n, 2L * n);
     ms->opW = tc::make_operand(ms->W_hi, n, 4L * n, ld4n, 2, true);
     // finite-range H and S: the operator product skips the K blocks where [H~; S] is zero
-    tc::block_lists(st, HS, 2L * m, m, m, 256, ms->hs_blocks[0]);
-    tc::block_lists(st, HS, 2L * m, m, m, 128, ms->hs_blocks[1]);
+    for (int bn : {256, 128, 192}) tc::block_lists(st, HS, 2L * m, m, m, bn, ms->hs_blocks[tc::sparse_slot(bn)]);
   } catch (...) {
-    mixed_destroy(ms);
+    mixed_destroy(ms, st);
     throw;
   }
   return ms;
 }
 
 void mixed_tuning(const MixedState* ms, int bn[4], double* ms_autotune) {
-  for (int k = 0; k < 4; ++k) bn[k] = ms->plans ? ms->plan_bn[k] : 0;
+  // the width of a 256-row (SM pair) tile is reported as 1000 + width
+  for (int k = 0; k < 4; ++k) bn[k] = ms->plans ? ms->plan_shape[k].bn + (ms->plan_shape[k].pair ? 1000 : 0) : 0;
   if (!ms->precond) bn[0] = 0;
   *ms_autotune = ms->ms_autotune;
 }
@@ -172,23 +173,19 @@ MixedView mixed_view(MixedState* ms) {
 
 void mixed_update_H(MixedState* ms, cudaStream_t st, const double* HS) {
   tc::split(st, HS, ms->m, ms->m, ms->m, ms->HS_hi, ms->HS_lo, ms->ldm, nullptr);
-  tc::block_lists(st, HS, 2L * ms->m, ms->m, ms->m, 256, ms->hs_blocks[0]);  // the pattern may change
-  tc::block_lists(st, HS, 2L * ms->m, ms->m, ms->m, 128, ms->hs_blocks[1]);
+  for (int bn : {256, 128, 192})  // the pattern may change
+    tc::block_lists(st, HS, 2L * ms->m, ms->m, ms->m, bn, ms->hs_blocks[tc::sparse_slot(bn)]);
 }
 
-void mixed_destroy(MixedState* ms) {
+void mixed_destroy(MixedState* ms, cudaStream_t st) {
   if (!ms) return;
   __nv_bfloat16* bufs[] = {ms->HS_hi, ms->P_hi, ms->G_hi, ms->D_hi, ms->Y_hi, ms->W_hi};
-  for (auto* b : bufs)
-    if (b) cudaFree(b);
-  for (double* d : {ms->Gref, ms->Wref, ms->red})
-    if (d) cudaFree(d);
-  for (float* f : {ms->Dir32, ms->PG32, ms->HD32, ms->dY32})
-    if (f) cudaFree(f);
-  if (ms->err) cudaFree(ms->err);
-  if (ms->plans) cudaFree(ms->plans);
-  tc::free_block_lists(ms->hs_blocks[0]);
-  tc::free_block_lists(ms->hs_blocks[1]);
+  for (auto* b : bufs) mem::release(b, st);
+  for (double* d : {ms->Gref, ms->Wref, ms->red}) mem::release(d, st);
+  for (float* f : {ms->Dir32, ms->PG32, ms->HD32, ms->dY32}) mem::release(f, st);
+  mem::release(ms->err, st);
+  mem::release(ms->plans, st);
+  for (tc::BlockLists& bl : ms->hs_blocks) tc::free_block_lists(bl, st);
   delete ms;
 }
 
@@ -317,32 +314,31 @@ void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double
     // output tile width from the autotuner (timed once per shape in a process); the operator
     // product runs block-sparse over [H~; S]
     tc::GemmSpec spec{opA[k], opB[k], K[k], ep[k]};
-    if (k == kPlanHD) {
-      spec.sparse[0] = &ms->hs_blocks[0];
-      spec.sparse[1] = &ms->hs_blocks[1];
-    }
+    if (k == kPlanHD)
+      for (int q = 0; q < 3; ++q) spec.sparse[q] = &ms->hs_blocks[q];
     double ms_tune = 0.0;
-    ms->plan_bn[k] = tc::choose_tile_width(st, {spec}, tc::pairs_split3(), &ms_tune);
+    const tc::TileShape ts = tc::choose_tile_shape(st, {spec}, tc::pairs_split3(), &ms_tune);
+    ms->plan_shape[k] = ts;
     ms->ms_autotune += ms_tune;
-    h[k] = tc::make_group(*opA[k], *opB[k], K[k], ep[k], 0, ms->plan_bn[k],
-                          spec.sparse[ms->plan_bn[k] == 256 ? 0 : 1]);
-    ms->plan_tiles[k] = tc::tiles_of(ep[k], ms->plan_bn[k]);
+    h[k] = tc::make_group(*opA[k], *opB[k], K[k], ep[k], 0, ts.bn, spec.sparse[tc::sparse_slot(ts.bn)], ts.pair);
+    ms->plan_tiles[k] = tc::tiles_of(ep[k], ts.bn, ts.pair);
   }
-  if (!ms->plans) alloc(&ms->plans, 4);
+  if (!ms->plans) alloc(&ms->plans, 4, st);
   OMM_CUDA_TRY(cudaMemcpyAsync(ms->plans, h, sizeof(h), cudaMemcpyHostToDevice, st));
   OMM_CUDA_TRY(cudaStreamSynchronize(st));  // h is a stack buffer
   ms->plan_sc = sc;
 }
 
 void run_plan(MixedState* ms, cudaStream_t st, int k) {
-  tc::gemm_persistent(st, ms->plans + k, 1, ms->plan_tiles[k], tc::pairs_split3(), ms->err, ms->plan_bn[k]);
+  tc::gemm_persistent(st, ms->plans + k, 1, ms->plan_tiles[k], tc::pairs_split3(), ms->err, ms->plan_shape[k].bn,
+                      ms->plan_shape[k].pair);
 }
 
 }  // namespace
 
 int mixed_reduce_parts(const MixedState* ms) {
-  // four partial sums per epilogue warp of every P G output tile
-  return 4 * ms->plan_tiles[kPlanPG];
+  // one slot of partial sums per epilogue warp of every P G output tile (eight on an SM pair's tile)
+  return 4 * ms->plan_tiles[kPlanPG] * (ms->plan_shape[kPlanPG].pair ? 2 : 1);
 }
 
 void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, double* Dir, double* G,
@@ -369,7 +365,7 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   // [H~ D ; S D] (n x m layout): one GEMM over the stacked [H~; S]; the epilogue splits the result
   pf.begin(st);
   run_plan(ms, st, kPlanHD);
-  pf.end(st, 4.0 * np * n * (double)m * m * tc::block_density(&ms->hs_blocks[ms->plan_bn[kPlanHD] == 256 ? 0 : 1]));
+  pf.end(st, 4.0 * np * n * (double)m * m * tc::block_density(&ms->hs_blocks[tc::sparse_slot(ms->plan_shape[kPlanHD].bn)]));
   // [H' | S' | H'' | S''] = D [HC; SC; HD; SD]^T (Eqs. 14-15)
   pf.begin(st);
   run_plan(ms, st, kPlanProj);

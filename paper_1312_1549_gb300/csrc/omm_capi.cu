@@ -94,34 +94,20 @@ omm_status fail(omm_status s, const std::string& msg) {
   return s;
 }
 
+// every buffer of a context comes from the library's stream-ordered pool (see mem.cu)
 template <typename T>
-void dev_alloc(T** p, size_t count) {
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    cudaGetLastError();
-    throw std::bad_alloc();
-  }
+void dev_alloc(T** p, size_t count, cudaStream_t st) {
+  mem::alloc(p, count, st);
 }
 
-void dev_free(void* p) {
-  if (p) cudaFree(p);
-}
+void dev_free(void* p, cudaStream_t st) { mem::release(p, st); }
 
-// stream-ordered temporaries: their release does not wait for the whole device (cudaFree does),
-// which matters when many contexts are created side by side
 template <typename T>
 void tmp_alloc(T** p, size_t count, cudaStream_t st) {
-  if (cudaMallocAsync((void**)p, count * sizeof(T), st) != cudaSuccess) {
-    *p = nullptr;
-    cudaGetLastError();
-    throw std::bad_alloc();
-  }
+  mem::alloc(p, count, st);
 }
 
-void tmp_free(void* p, cudaStream_t st) {
-  if (p) cudaFreeAsync(p, st);
-}
+void tmp_free(void* p, cudaStream_t st) { mem::release(p, st); }
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
@@ -241,36 +227,36 @@ void minus_edm_into(omm_ctx* c, double* out) {
 }
 
 void ensure_mm(omm_ctx* c) {
-  if (!c->mm) dev_alloc(&c->mm, (size_t)c->m * c->m);
+  if (!c->mm) dev_alloc(&c->mm, (size_t)c->m * c->m, c->st);
 }
 
 void destroy(omm_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
-  dev_free(c->HS);
-  dev_free(c->P);
-  dev_free(c->C);
-  dev_free(c->Dir);
-  dev_free(c->G);
-  dev_free(c->Gold);
-  dev_free(c->PG);
-  dev_free(c->Y4);
-  dev_free(c->SWHW);
-  dev_free(c->Proj);
-  dev_free(c->nn);
-  dev_free(c->part);
-  dev_free(c->part2);
-  dev_free(c->mm);
-  dev_free(c->sc);
-  dev_free(c->info_dev);
-  dev_free(c->hz_stage);
-  dev_free(c->hz_rows);
+  dev_free(c->HS, c->st);
+  dev_free(c->P, c->st);
+  dev_free(c->C, c->st);
+  dev_free(c->Dir, c->st);
+  dev_free(c->G, c->st);
+  dev_free(c->Gold, c->st);
+  dev_free(c->PG, c->st);
+  dev_free(c->Y4, c->st);
+  dev_free(c->SWHW, c->st);
+  dev_free(c->Proj, c->st);
+  dev_free(c->nn, c->st);
+  dev_free(c->part, c->st);
+  dev_free(c->part2, c->st);
+  dev_free(c->mm, c->st);
+  dev_free(c->sc, c->st);
+  dev_free(c->info_dev, c->st);
+  dev_free(c->hz_stage, c->st);
+  dev_free(c->hz_rows, c->st);
   if (c->sc_host) cudaFreeHost(c->sc_host);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
-  if (c->mixed) mixed_destroy(c->mixed);
-  if (c->emu) emu_destroy(c->emu);
-  if (c->red) reduction_destroy(c->red);
+  if (c->mixed) mixed_destroy(c->mixed, c->st);
+  if (c->emu) emu_destroy(c->emu, c->st);
+  if (c->red) reduction_destroy(c->red, c->st);
   delete c;
 }
 
@@ -339,9 +325,9 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     c->prof_sliced.on = o.profile != 0;
     if (c->prof_sliced.on) emu::set_profiler(&c->prof_sliced);
     OMM_CUDA_TRY(cudaMallocHost((void**)&c->sc_host, sizeof(Scalars)));
-    dev_alloc(&c->sc, 1);
-    dev_alloc(&c->info_dev, 1);
-    dev_alloc(&c->HS, 2 * mm);
+    dev_alloc(&c->sc, 1, c->st);
+    dev_alloc(&c->info_dev, 1, c->st);
+    dev_alloc(&c->HS, 2 * mm, c->st);
     OMM_CUDA_TRY(cudaEventRecord(c->ev[0], c->st));
     copy_in(c->HS, H, mm, c->st);
     copy_in(c->HS + mm, S, mm, c->st);
@@ -360,7 +346,7 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
     }
     launch_axpby_shift(c->st, mm, c->HS, c->HS + mm, eta, c->HS);
     if (precond) {
-      dev_alloc(&c->P, mm);
+      dev_alloc(&c->P, mm, c->st);
       tmp_alloc(&A, mm, c->st);
       if (sliced_inverse) {
         tmp_alloc(&work, (spd_inverse_sliced_workspace_bytes(m) + sizeof(double) - 1) / sizeof(double), c->st);
@@ -380,17 +366,17 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
       else spd_inverse(c->st, m, A, c->P, work, c->info_dev);
       OMM_CUDA_TRY(cudaEventRecord(c->ev[3], c->st));
     }
-    dev_alloc(&c->C, nm);
-    dev_alloc(&c->Dir, nm);
-    dev_alloc(&c->G, nm);
-    dev_alloc(&c->Gold, nm);
-    dev_alloc(&c->PG, nm);
-    dev_alloc(&c->Y4, 4 * nm);
-    dev_alloc(&c->SWHW, 2L * n * n);
-    dev_alloc(&c->Proj, 4L * n * n);
-    dev_alloc(&c->nn, (size_t)n * n);
-    dev_alloc(&c->part, (size_t)kReduceBlocks * 4);
-    dev_alloc(&c->part2, (size_t)traces_blocks(n) * kNumTraces);
+    dev_alloc(&c->C, nm, c->st);
+    dev_alloc(&c->Dir, nm, c->st);
+    dev_alloc(&c->G, nm, c->st);
+    dev_alloc(&c->Gold, nm, c->st);
+    dev_alloc(&c->PG, nm, c->st);
+    dev_alloc(&c->Y4, 4 * nm, c->st);
+    dev_alloc(&c->SWHW, 2L * n * n, c->st);
+    dev_alloc(&c->Proj, 4L * n * n, c->st);
+    dev_alloc(&c->nn, (size_t)n * n, c->st);
+    dev_alloc(&c->part, (size_t)kReduceBlocks * 4, c->st);
+    dev_alloc(&c->part2, (size_t)traces_blocks(n) * kNumTraces, c->st);
     if (o.precision == OMM_PREC_MIXED) {
       c->mixed = mixed_create(c->st, m, n, c->HS, c->P);
       if (o.debug_expire_wait) mixed_set_expire(c->mixed, 1);

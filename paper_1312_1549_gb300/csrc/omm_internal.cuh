@@ -71,6 +71,20 @@ void count_launch();
     if (e__ != cudaSuccess) throw ::omm::CudaError{e__, #call};              \
   } while (0)
 
+// ------------------------------------------------------------------ device memory
+// Stream-ordered allocations from a pool the library owns (one per device; freed blocks are kept
+// for reuse). alloc throws std::bad_alloc; the memory may be used on st at once and on other
+// streams after a synchronisation with st. release(nullptr) is ignored.
+namespace mem {
+void* alloc(size_t bytes, cudaStream_t st);
+void release(void* p, cudaStream_t st);
+template <typename T>
+void alloc(T** p, size_t count, cudaStream_t st) {
+  *p = nullptr;
+  *p = static_cast<T*>(alloc(count * sizeof(T), st));
+}
+}  // namespace mem
+
 // ------------------------------------------------------------------ kernel timing
 // CUDA-event timing of selected launches on their own stream (enabled by
 // omm_opts.profile): begin()/end() bracket a launch, collect() after a stream

@@ -16,7 +16,7 @@ struct MixedView {
   double *Gref, *Wref, *red;
   float *Dir32, *PG32, *HD32, *dY32;  // float32 side quantities, leading dimension ldm
   const tc::Operand *opHS, *opP, *opG, *opD, *opYproj, *opYgrad, *opW;
-  const tc::BlockLists* hs_blocks;  // [0]: 256-row blocks, [1]: 128-row blocks
+  const tc::BlockLists* hs_blocks;  // [0]: 256-row blocks, [1]: 128-row blocks, [2]: 192-row blocks
   int* err;
   int npass;
   bool precond;
@@ -36,7 +36,7 @@ void mixed_reset_error(MixedState* ms, cudaStream_t st);
 
 MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const double* P);
 void mixed_update_H(MixedState* ms, cudaStream_t st, const double* HS);
-void mixed_destroy(MixedState* ms);
+void mixed_destroy(MixedState* ms, cudaStream_t st);  // st: the owner's current stream
 // after a float64 recompute: take (G, HC, SC, S_W, H_W) as the new reference
 // point of the incremental gradient and refresh the bf16 copies
 void mixed_sync_state(MixedState* ms, cudaStream_t st, const double* Y4, const double* SWHW, const double* G);

@@ -45,12 +45,8 @@ struct Reduction {
 namespace {
 
 template <typename T>
-void alloc(T** p, size_t count) {
-  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
-    *p = nullptr;
-    cudaGetLastError();
-    throw std::bad_alloc();
-  }
+void alloc(T** p, size_t count, cudaStream_t st) {
+  mem::alloc(p, count, st);
 }
 
 // out (M x m) = alpha A B^T with A (M x m rows, float64) and B (m x m, float64) row-major
@@ -80,19 +76,19 @@ Reduction* reduction_create(cudaStream_t st, int m, bool sliced, double* S, int*
     r->m = m;
     r->sliced = sliced;
     const size_t mm = (size_t)m * m;
-    alloc(&r->L, mm);
-    alloc(&r->Y, mm);
-    alloc(&r->W, mm);
-    alloc(&r->err, 1);
+    alloc(&r->L, mm, st);
+    alloc(&r->Y, mm, st);
+    alloc(&r->W, mm, st);
+    alloc(&r->err, 1, st);
     OMM_CUDA_TRY(cudaMemsetAsync(r->err, 0, sizeof(int), st));
     if (sliced) {
       r->ldm = round8(m);
-      alloc(&r->YT, mm);
-      alloc(&r->slA, (size_t)kRedSlices * m * r->ldm);
-      alloc(&r->slB, (size_t)kRedSlices * m * r->ldm);
+      alloc(&r->YT, mm, st);
+      alloc(&r->slA, (size_t)kRedSlices * m * r->ldm, st);
+      alloc(&r->slB, (size_t)kRedSlices * m * r->ldm, st);
       r->partial_cap = partial_capacity(m);
-      alloc(&r->partial, (size_t)r->partial_cap);
-      alloc(reinterpret_cast<char**>(&work), spd_inverse_sliced_workspace_bytes(m));
+      alloc(&r->partial, (size_t)r->partial_cap, st);
+      alloc(reinterpret_cast<char**>(&work), spd_inverse_sliced_workspace_bytes(m), st);
       spd_factor_inverse_sliced(st, m, S, r->Y, work, info_dev, r->err);
       emu::transpose(st, S, m, m, m, r->L, m);     // L^T
       emu::transpose(st, r->Y, m, m, m, r->YT, m);  // L^-T
@@ -100,29 +96,27 @@ Reduction* reduction_create(cudaStream_t st, int m, bool sliced, double* S, int*
       tc::block_lists(st, r->YT, m, m, m, 256, r->blYT);
       tc::block_lists(st, r->L, m, m, m, 256, r->blLT);
     } else {
-      alloc(reinterpret_cast<double**>(&work), spd_inverse_workspace(m));
+      alloc(reinterpret_cast<double**>(&work), spd_inverse_workspace(m), st);
       spd_factor_inverse(st, m, S, r->Y, static_cast<double*>(work), info_dev);
       OMM_CUDA_TRY(cudaMemcpyAsync(r->L, S, mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
-    OMM_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(work);
+    mem::release(work, st);  // stream-ordered: after the factorisation that uses it
   } catch (...) {
     cudaStreamSynchronize(st);
-    if (work) cudaFree(work);
-    reduction_destroy(r);
+    mem::release(work, st);
+    reduction_destroy(r, st);
     throw;
   }
   return r;
 }
 
-void reduction_destroy(Reduction* r) {
+void reduction_destroy(Reduction* r, cudaStream_t st) {
   if (!r) return;
   void* bufs[] = {r->L, r->Y, r->YT, r->W, r->slA, r->slB, r->partial, r->err};
-  for (void* b : bufs)
-    if (b) cudaFree(b);
-  tc::free_block_lists(r->blY);
-  tc::free_block_lists(r->blYT);
-  tc::free_block_lists(r->blLT);
+  for (void* b : bufs) mem::release(b, st);
+  tc::free_block_lists(r->blY, st);
+  tc::free_block_lists(r->blYT, st);
+  tc::free_block_lists(r->blLT, st);
   delete r;
 }
 

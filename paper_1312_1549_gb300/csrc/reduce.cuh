@@ -16,7 +16,7 @@ struct Reduction;
 // sliced: float64-class products on the tensor cores (fixed-point slices) instead of native
 // float64. info_dev receives 0 or the 1-based column of the first non-positive pivot.
 Reduction* reduction_create(cudaStream_t st, int m, bool sliced, double* S, int* info_dev);
-void reduction_destroy(Reduction* r);
+void reduction_destroy(Reduction* r, cudaStream_t st);  // st: the owner's current stream
 // nonzero if a bounded wait of a tensor-core product expired (synchronises the stream)
 int reduction_error(Reduction* r, cudaStream_t st);
 // H (m x m, device) <- L^-1 H L^-T, exactly symmetric

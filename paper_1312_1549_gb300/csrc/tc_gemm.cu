@@ -6,8 +6,10 @@
 //   warp 1      TMEM allocation and the MMA issuer (one lane)
 //   warps 2-5   epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator,
 //               C = alpha * acc + beta * C written in float64
-// Each CTA computes one 128 x 256 tile of C = A B^T with A (M x K) and
-// B (N x K) both K-major bf16. Operands are stacks of slices; a pair list
+// Each CTA computes one 128 x 256 (or 128 x 128) tile of C = A B^T with A (M x K)
+// and B (N x K) both K-major bf16 (or B MN-major); the split form also runs on
+// pairs of SMs (a cluster of two CTAs, tcgen05 cta_group::2, 256-row tiles; see
+// pair_body). Operands are stacks of slices; a pair list
 // says which slice products are accumulated (passes over K into the same
 // accumulator). "Split" operands x = x_hi + x_lo use the three pairs
 // A_hi B_hi + A_hi B_lo + A_lo B_hi, which keep about 16 significant bits;
@@ -865,6 +867,274 @@ __device__ __forceinline__ void persistent_body(const GroupDesc* __restrict__ gr
   }
 }
 
+// ---------------------------------------------------------------- CTA pairs (cta_group::2)
+// The fused split product on a pair of SMs: a cluster of two CTAs computes one 256 x TBN output
+// tile with tcgen05.mma.cta_group::2 (M = 256), issued by the even CTA. Each CTA stages its own
+// 128 rows of A_hi and A_lo and its half of B_hi and B_lo (TBN / 2 rows, or TBN / 2 output columns
+// of an MN-major B), so that an SM fetches half the B bytes per output element of a single-CTA
+// tile of the same width; the tensor memory of each CTA holds the accumulator of its 128 rows
+// (all TBN columns), which its own epilogue warps read.
+// Barriers: full[q] of the even CTA receives the TMA bytes of both CTAs and is armed by the even
+// CTA's producer with the pair's total; the even CTA's MMA commits arrive at empty[q] and at the
+// accumulator-full barriers of both CTAs (multicast); the accumulator-empty barriers of the even
+// CTA count the arrivals of the eight epilogue warps of the pair.
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// the shared::cluster address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+// (not .aligned: the role branches may leave a warp's lanes diverged here)
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// a TMA load into this CTA's shared memory whose bytes count at an mbarrier of either CTA of the pair
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, uint32_t bar_cluster, int c0,
+                                                 int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void umma_bf16_pair(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// arrive at the barrier at this shared offset in both CTAs once the MMAs issued so far are complete
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"((uint16_t)3)
+      : "memory");
+}
+// the same, at this CTA's barrier only
+__device__ __forceinline__ void umma_commit_pair_local(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+constexpr uint32_t PAIR_TMEM_COLS = 512;  // two accumulator buffers, 256 columns apart
+constexpr uint64_t PAIR_ABORT_SETTLE_NS = 200000ull;
+
+template <int TBN>
+__device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, int ngroups, int total_units,
+                                          int* err) {
+  constexpr int TBH = TBN / 2;  // B rows (or MN-major output columns) staged by each CTA
+  constexpr int BH_BYTES = TBH * BK * 2;
+  constexpr int SB = 2 * (A_BYTES + BH_BYTES);  // one CTA's stage: A_hi, A_lo, B_hi, B_lo
+  constexpr int NS = ring_stages(SB);
+  constexpr uint32_t ACC_STRIDE = 256;
+  static_assert(TBN % 32 == 0 && TBN >= 64 && TBN <= 256 && NS >= 2 && NS * SB <= RING_BYTES && 2 * NS + 5 <= 28,
+                "pair tile");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NS * SB);
+  // bars[0..NS) full (even CTA), [NS..2NS) empty, [2NS..2NS+2) accumulator full, [2NS+2..2NS+4)
+  // accumulator empty (even CTA), [2NS+4] drain / test expiry
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const bool leader = rank == 0;
+  const int cluster = (int)(blockIdx.x >> 1), nclusters = (int)(gridDim.x >> 1);
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NS; ++q) {
+      mbar_init(smem_u32(&bars[q]), 1);
+      mbar_init(smem_u32(&bars[NS + q]), 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(smem_u32(&bars[2 * NS + q]), 1);      // the even CTA's multicast commit
+      mbar_init(smem_u32(&bars[2 * NS + 2 + q]), 8);  // one arrival per epilogue warp of the pair
+    }
+    mbar_init(smem_u32(&bars[2 * NS + 4]), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(PAIR_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  cluster_sync_all();  // the barriers of both CTAs are initialised before any copy, commit or arrival
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  if (groups[0].ep.expire) {
+    // tests of the timeout status (as in the single-CTA kernel): nothing is issued
+    if (threadIdx.x == 0) {
+      if (!mbar_wait(smem_u32(&bars[2 * NS + 4]), 0, EXPIRE_NS)) atomicCAS(err, 0, 6);
+      *abort_flag = 1;
+    }
+    __syncthreads();
+  }
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer (both CTAs)
+    uint32_t it = 0;
+    for (int u = cluster; u < total_units && !*abort_flag; u += nclusters) {
+      const GroupDesc* g = groups + find_group(groups, ngroups, u);
+      const int* skip = g->ep.skip;
+      if (skip != nullptr && (skip[0] | skip[1])) continue;
+      const CUtensorMap* mA = reinterpret_cast<const CUtensorMap*>(&g->a);
+      const CUtensorMap* mB = reinterpret_cast<const CUtensorMap*>(&g->b);
+      const int local = u - g->tile_begin, tiles_m = (g->ep.M + 2 * BM - 1) / (2 * BM);
+      const int m0 = (local % tiles_m) * 2 * BM + (int)rank * BM;  // this CTA's rows of A
+      const int n0 = (local / tiles_m) * TBN + (int)rank * TBH;     // this CTA's half of B
+      const KBlocks kbs = tile_kblocks(g, local, tiles_m);
+      for (int t = 0; t < kbs.count; ++t, ++it) {
+        const int q = it % NS;
+        const uint32_t r = it / NS;
+        if (!mbar_wait(smem_u32(&bars[NS + q]), (r & 1) ^ 1)) {
+          *abort_flag = 1;
+          atomicCAS(err, 0, 1);
+          break;
+        }
+        const uint32_t full = mapa_shared(smem_u32(&bars[q]), 0);
+        if (leader) mbar_expect_tx(smem_u32(&bars[q]), 2 * SB);  // the bytes of both CTAs
+        const uint32_t sa = smem_u32(smem + q * SB);
+        const int kb = kbs.at(t);
+        tma_load_2d_pair(sa, mA, full, kb * BK, g->offA + m0);
+        tma_load_2d_pair(sa + A_BYTES, mA, full, kb * BK, g->rowsA + g->offA + m0);
+        if (g->b_mn) {
+#pragma unroll
+          for (int h = 0; h < TBH / 64; ++h) {
+            tma_load_2d_pair(sa + 2 * A_BYTES + h * MN_BOX_BYTES, mB, full, n0 + 64 * h, g->offB + kb * BK);
+            tma_load_2d_pair(sa + 2 * A_BYTES + BH_BYTES + h * MN_BOX_BYTES, mB, full, n0 + 64 * h,
+                             g->rowsB + g->offB + kb * BK);
+          }
+        } else {
+          tma_load_2d_pair(sa + 2 * A_BYTES, mB, full, kb * BK, g->offB + n0);
+          tma_load_2d_pair(sa + 2 * A_BYTES + BH_BYTES, mB, full, kb * BK, g->rowsB + g->offB + n0);
+        }
+      }
+    }
+    if (*abort_flag) {
+      if (leader) {  // the copies of the stages issued last (both CTAs' bytes count here)
+        for (uint32_t j = it > (uint32_t)NS ? it - NS : 0u; j < it; ++j)
+          mbar_wait(smem_u32(&bars[j % NS]), (j / NS) & 1);
+      } else {  // the odd CTA's copies complete at the even CTA's barriers: give them time to land
+        const uint64_t t0 = globaltimer();
+        while (globaltimer() - t0 < PAIR_ABORT_SETTLE_NS) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0 && leader) {
+    // ---------------- MMA issuer (even CTA)
+    constexpr uint32_t idesc_k = idesc_bf16(2 * BM, TBN);
+    uint32_t it = 0, lt = 0;
+    for (int u = cluster; u < total_units && !*abort_flag; u += nclusters) {
+      const GroupDesc* g = groups + find_group(groups, ngroups, u);
+      const int* skip = g->ep.skip;
+      if (skip != nullptr && (skip[0] | skip[1])) continue;
+      const int nkb = tile_kblocks(g, u - g->tile_begin, (g->ep.M + 2 * BM - 1) / (2 * BM)).count;
+      const bool bmn = g->b_mn != 0;
+      const uint32_t idesc = idesc_k | (bmn ? kIdescBMN : 0u);
+      auto bdesc = [bmn](uint32_t addr, int k) {
+        return bmn ? smem_desc_mn(addr + (uint32_t)k * 2048u) : smem_desc(addr + (uint32_t)k * 32u);
+      };
+      const uint32_t buf = lt & 1, use = lt >> 1;
+      if (!mbar_wait(smem_u32(&bars[2 * NS + 2 + buf]), (use & 1) ^ 1)) {
+        *abort_flag = 1;
+        atomicCAS(err, 0, 4);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t d = tmem + buf * ACC_STRIDE;
+      for (int t = 0; t < nkb; ++t, ++it) {
+        const int q = it % NS;
+        const uint32_t r = it / NS;
+        if (!mbar_wait(smem_u32(&bars[q]), r & 1)) {
+          *abort_flag = 1;
+          atomicCAS(err, 0, 2);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = smem_u32(smem + q * SB);
+        const uint32_t alo = sa + A_BYTES, bhi = sa + 2 * A_BYTES, blo = bhi + BH_BYTES;
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          umma_bf16_pair(d, smem_desc(sa + k * 32), bdesc(bhi, k), idesc, (t > 0 || k > 0) ? 1u : 0u);
+          umma_bf16_pair(d, smem_desc(sa + k * 32), bdesc(blo, k), idesc, 1u);
+          umma_bf16_pair(d, smem_desc(alo + k * 32), bdesc(bhi, k), idesc, 1u);
+        }
+        umma_commit_pair(smem_u32(&bars[NS + q]));  // stage q of both CTAs is free
+      }
+      umma_commit_pair(smem_u32(&bars[2 * NS + buf]));  // both halves of the accumulator are complete
+      ++lt;
+    }
+    if (*abort_flag) {  // every MMA issued so far is complete before the tensor memory is freed
+      umma_commit_pair_local(smem_u32(&bars[2 * NS + 4]));
+      mbar_wait(smem_u32(&bars[2 * NS + 4]), 0);
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue (both CTAs: 128 rows each)
+    const int lane_base = (warp & 3) * 32;
+    const uint32_t acc_empty0 = mapa_shared(smem_u32(&bars[2 * NS + 2]), 0);
+    const uint32_t acc_empty1 = mapa_shared(smem_u32(&bars[2 * NS + 3]), 0);
+    uint32_t lt = 0;
+    for (int u = cluster; u < total_units; u += nclusters) {
+      const GroupDesc* g = groups + find_group(groups, ngroups, u);
+      const int* skip = g->ep.skip;
+      if (skip != nullptr && (skip[0] | skip[1])) continue;
+      const uint32_t buf = lt & 1, use = lt >> 1;
+      const bool ok = !*abort_flag && mbar_wait(smem_u32(&bars[2 * NS + buf]), use & 1);
+      if (!ok) {
+        atomicCAS(err, 0, 3);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const Epilogue ep = g->ep;
+      const int local = u - g->tile_begin, tiles_m = (ep.M + 2 * BM - 1) / (2 * BM);
+      const int m0 = (local % tiles_m) * 2 * BM + (int)rank * BM, n0 = (local / tiles_m) * TBN;
+      const int row = m0 + lane_base + lane;
+      EpiRed red;
+      red.have_dir = ep.mode == kEpReduce && ep.sc != nullptr && ep.sc->have_dir;
+#pragma unroll 1
+      for (int j = 0; j < TBN / 32; ++j) {
+        float v[32];
+        tmem_ld32(tmem + buf * ACC_STRIDE + ((uint32_t)lane_base << 16) + (uint32_t)(j * 32), v);
+        store_chunk(ep, row, n0 + j * 32, v, red);
+      }
+      flush_reduce(ep, local * 2 + (int)rank, warp & 3, red);  // slots of 128-row halves
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(buf ? acc_empty1 : acc_empty0);
+      ++lt;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  // neither CTA leaves while the pair's MMAs may read its shared memory or write its tensor
+  // memory, or the other CTA may still arrive at its barriers
+  cluster_sync_all();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PAIR_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+template <int TBN>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+gemm_pair_kernel(const GroupDesc* __restrict__ groups, int ngroups, int total_units, int* err) {
+  pair_body<TBN>(groups, ngroups, total_units, err);
+}
+
 template <bool FUSED, int TBN>
 __global__ void __launch_bounds__(NTHREADS, 1)
 gemm_persistent_kernel(const GroupDesc* __restrict__ groups, int ngroups, int total_tiles,
@@ -903,6 +1173,30 @@ int sm_count() {
     int dev = 0, c = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) c = 148;
+    return c;
+  }();
+  return n;
+}
+
+// clusters of two GEMM CTAs (one per SM) that the device holds at once
+int pair_clusters() {
+  static const int n = [] {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * (unsigned)sm_count());
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = SMEM_BYTES;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int c = 0;
+    if (cudaOccupancyMaxActiveClusters(&c, gemm_pair_kernel<256>, &cfg) != cudaSuccess || c <= 0) {
+      cudaGetLastError();
+      c = sm_count() / 2;
+    }
     return c;
   }();
   return n;
@@ -962,6 +1256,9 @@ Operand make_operand_view(const __nv_bfloat16* base, long slice_rows, long cols,
     o.map = make_map(base, slice_rows * slices, cols, ld, o.box_rows);
     o.map_n128 = is_a ? o.map : make_map(base, slice_rows * slices, cols, ld, 128);  // 128-wide output tiles
   }
+  o.base = base;
+  o.ld = ld;
+  o.map_rows = slice_rows * slices;
   o.rows = rows;
   o.cols = cols;
   o.slices = slices;
@@ -1030,20 +1327,31 @@ void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const Pair
   OMM_LAUNCH_CHECK();
 }
 
-int tiles_of(const Epilogue& ep, int bn) { return ((ep.M + BM - 1) / BM) * ((ep.N + bn - 1) / bn); }
+int tiles_of(const Epilogue& ep, int bn, bool pair) {
+  const int bm = pair ? 2 * BM : BM;
+  return ((ep.M + bm - 1) / bm) * ((ep.N + bn - 1) / bn);
+}
 
 GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin, int bn,
-                     const BlockLists* sparse) {
-  if (bn != 256 && bn != 128) throw CudaError{cudaErrorInvalidValue, "tc::make_group: tile width"};
-  // the TMA boxes must match the tile: A in 128-row boxes, B in boxes of the tile width (or, MN-major,
-  // 64 x 64 boxes for any width)
-  if (A.mn_major || A.box_rows != BM || (!B.mn_major && bn == 256 && B.box_rows != 256))
+                     const BlockLists* sparse, bool pair) {
+  if (pair ? (bn != 256 && bn != 192 && bn != 128) : (bn != 256 && bn != 128))
+    throw CudaError{cudaErrorInvalidValue, "tc::make_group: tile width"};
+  // the TMA boxes must match the tile: A in 128-row boxes, B in boxes of the tile width (of half of
+  // it on an SM pair), or, MN-major, in 64 x 64 boxes (then the width an SM stages is a multiple of 64)
+  if (A.mn_major || A.box_rows != BM || (!B.mn_major && !pair && bn == 256 && B.box_rows != 256) ||
+      (B.mn_major && pair && (bn / 2) % 64 != 0))
     throw CudaError{cudaErrorInvalidValue, "tc::make_group: operand boxes do not match the tile"};
   if (B.mn_major && (sparse != nullptr || K > B.rows))
     throw CudaError{cudaErrorInvalidValue, "tc::make_group: MN-major B: no block lists, K <= its rows"};
   GroupDesc g{};
   g.a = A.map;
-  g.b = (bn == 128 && !B.mn_major) ? B.map_n128 : B.map;
+  if (B.mn_major)
+    g.b = B.map;
+  else if (pair)
+    g.b = bn == 256 ? B.map_n128 : make_map(B.base, B.map_rows, B.cols, B.ld, bn / 2);
+  else
+    g.b = bn == 128 ? B.map_n128 : B.map;
+  g.pair = pair ? 1 : 0;
   g.ep = ep;
   g.K = K;
   g.rowsA = (int)A.slice_rows;
@@ -1075,19 +1383,36 @@ void prepare_persistent() {
                                       SMEM_BYTES));
     OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_one_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       SMEM_BYTES));
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_pair_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_pair_kernel<192>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_pair_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     sm_count();
+    pair_clusters();
     attr_set = true;
   }
 }
 
 void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl,
-                     int* err, int bn) {
+                     int* err, int bn, bool pair) {
   prepare_persistent();
   check_pairs(pl, kMaxPairs, kMaxPairs);  // slice counts are checked where the groups are made
   if (ngroups <= 0 || total_tiles <= 0) return;
+  const bool fused = is_split3(pl);
+  if (pair) {
+    if (!fused || (bn != 256 && bn != 192 && bn != 128))
+      throw CudaError{cudaErrorInvalidValue, "tc::gemm_persistent: SM pairs run the split form, 128/192/256 wide"};
+    const unsigned grid = 2u * (unsigned)std::min(total_tiles, pair_clusters());
+    if (bn == 256)
+      gemm_pair_kernel<256><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, err);
+    else if (bn == 192)
+      gemm_pair_kernel<192><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, err);
+    else
+      gemm_pair_kernel<128><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, err);
+    OMM_LAUNCH_CHECK();
+    return;
+  }
   if (bn != 256 && bn != 128) throw CudaError{cudaErrorInvalidValue, "tc::gemm_persistent: tile width"};
   const unsigned grid = (unsigned)std::min(total_tiles, sm_count());
-  const bool fused = is_split3(pl);
   if (bn == 256 && fused)
     gemm_persistent_kernel<true, 256><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, pl, err);
   else if (bn == 256)
@@ -1130,14 +1455,15 @@ void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K,
 
 // ------------------------------------------------------------------ block sparsity of B
 namespace {
-// occ[rb * nkb + kb] = 1 if rows [128 rb, 128 rb + 128) x columns [BK kb, BK kb + BK) hold a nonzero
+// occ[rb * nkb + kb] = 1 if rows [64 rb, 64 rb + 64) x columns [BK kb, BK kb + BK) hold a nonzero
+constexpr int OCC_ROWS = 64;
 __global__ void __launch_bounds__(256)
 occupancy_kernel(const double* __restrict__ B, long rows, long cols, long ld, int nkb, unsigned char* occ) {
   const long blk = blockIdx.x;
   const long rb = blk / nkb, kb = blk % nkb;
   int any = 0;
-  for (int e = threadIdx.x; e < 128 * BK; e += blockDim.x) {
-    const long r = rb * 128 + e / BK, c = kb * BK + e % BK;
+  for (int e = threadIdx.x; e < OCC_ROWS * BK; e += blockDim.x) {
+    const long r = rb * OCC_ROWS + e / BK, c = kb * BK + e % BK;
     if (r < rows && c < cols && B[r * ld + c] != 0.0) any = 1;
   }
   any = __syncthreads_or(any);
@@ -1146,14 +1472,14 @@ occupancy_kernel(const double* __restrict__ B, long rows, long cols, long ld, in
 }  // namespace
 
 void block_lists(cudaStream_t st, const double* B, long rows, long cols, long ld, int bn, BlockLists& bl) {
-  if (bn != 128 && bn != 256) throw CudaError{cudaErrorInvalidValue, "tc::block_lists: tile width"};
+  if (bn != 128 && bn != 192 && bn != 256) throw CudaError{cudaErrorInvalidValue, "tc::block_lists: tile width"};
   const int nkb = (int)((cols + BK - 1) / BK);
-  const long nrb128 = (rows + 127) / 128;
+  const long nrb64 = (rows + OCC_ROWS - 1) / OCC_ROWS;
   unsigned char* occ = nullptr;
-  std::vector<unsigned char> h(nrb128 * nkb);
+  std::vector<unsigned char> h(nrb64 * nkb);
   OMM_CUDA_TRY(cudaMallocAsync((void**)&occ, h.size(), st));
   try {
-    occupancy_kernel<<<(unsigned)(nrb128 * nkb), 256, 0, st>>>(B, rows, cols, ld, nkb, occ);
+    occupancy_kernel<<<(unsigned)(nrb64 * nkb), 256, 0, st>>>(B, rows, cols, ld, nkb, occ);
     OMM_LAUNCH_CHECK();
     OMM_CUDA_TRY(cudaMemcpyAsync(h.data(), occ, h.size(), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1162,7 +1488,7 @@ void block_lists(cudaStream_t st, const double* B, long rows, long cols, long ld
     throw;
   }
   cudaFreeAsync(occ, st);
-  const int per = bn / 128;  // 128-row blocks per row block of bn
+  const int per = bn / OCC_ROWS;  // 64-row blocks per row block of bn
   const int nblocks = (int)((rows + bn - 1) / bn);
   std::vector<int> off(nblocks + 1, 0), idx;
   for (int r = 0; r < nblocks; ++r) {
@@ -1170,8 +1496,8 @@ void block_lists(cudaStream_t st, const double* B, long rows, long cols, long ld
     for (int kb = 0; kb < nkb; ++kb) {
       bool any = false;
       for (int q = 0; q < per; ++q) {
-        const long r128 = (long)r * per + q;
-        if (r128 < nrb128 && h[r128 * nkb + kb]) any = true;
+        const long r64 = (long)r * per + q;
+        if (r64 < nrb64 && h[r64 * nkb + kb]) any = true;
       }
       if (any) idx.push_back(kb);
     }
@@ -1184,22 +1510,24 @@ void block_lists(cudaStream_t st, const double* B, long rows, long cols, long ld
     bl.nblocks = nblocks;
     bl.dense = (long)nblocks * nkb;
     try {
-      OMM_CUDA_TRY(cudaMalloc((void**)&bl.off, off.size() * sizeof(int)));
-      OMM_CUDA_TRY(cudaMalloc((void**)&bl.idx, (size_t)bl.dense * sizeof(int)));
+      mem::alloc(&bl.off, off.size(), st);
+      mem::alloc(&bl.idx, (size_t)bl.dense, st);
     } catch (...) {
-      free_block_lists(bl);
+      free_block_lists(bl, st);
       throw;
     }
   }
   bl.nnz = (long)idx.size();
-  // the stream was synchronised above, so no earlier launch still reads the old lists
-  OMM_CUDA_TRY(cudaMemcpy(bl.off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
-  OMM_CUDA_TRY(cudaMemcpy(bl.idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  // the stream was synchronised above, so no earlier launch still reads the old lists; the host
+  // vectors live until the copies are done
+  OMM_CUDA_TRY(cudaMemcpyAsync(bl.off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  OMM_CUDA_TRY(cudaMemcpyAsync(bl.idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  OMM_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
-void free_block_lists(BlockLists& bl) {
-  if (bl.off) cudaFree(bl.off);
-  if (bl.idx) cudaFree(bl.idx);
+void free_block_lists(BlockLists& bl, cudaStream_t st) {
+  mem::release(bl.off, st);
+  mem::release(bl.idx, st);
   bl = BlockLists{};
 }
 
@@ -1209,19 +1537,34 @@ std::mutex& tune_mutex() {
   static std::mutex mu;
   return mu;
 }
-std::map<std::string, int>& tune_cache() {
-  static std::map<std::string, int> cache;
+std::map<std::string, TileShape>& tune_cache() {
+  static std::map<std::string, TileShape> cache;
   return cache;
 }
 }  // namespace
 
-int choose_tile_width(cudaStream_t st, const std::vector<GemmSpec>& specs, const PairList& pl, double* ms_spent) {
+TileShape choose_tile_shape(cudaStream_t st, const std::vector<GemmSpec>& specs, const PairList& pl, double* ms_spent,
+                            bool allow_pair) {
   if (ms_spent) *ms_spent = 0.0;
-  if (specs.empty()) return 256;
-  std::string key = std::to_string(pl.n) + (is_split3(pl) ? "s" : "g");
+  if (specs.empty()) return TileShape{};
+  // candidates: one SM per 128-row tile, and (split form, every M >= 256) SM pairs; 192-wide pair
+  // tiles need K-major B (an SM stages 96 rows) and, for a block-sparse B, lists for that width
+  std::vector<TileShape> cands = {{256, false}, {128, false}};
+  bool pair_ok = allow_pair && is_split3(pl), w192 = true;
+  for (const GemmSpec& g : specs) {
+    if (g.ep.M < 2 * BM || g.A->slices < 2 || g.B->slices < 2) pair_ok = false;
+    if (g.B->mn_major || (g.sparse[0] != nullptr && g.sparse[2] == nullptr)) w192 = false;
+  }
+  if (pair_ok) {
+    cands.push_back({256, true});
+    cands.push_back({128, true});
+    if (w192) cands.push_back({192, true});
+  }
+  std::string key = std::to_string(pl.n) + (is_split3(pl) ? "s" : "g") + (pair_ok ? "p" : "");
   long out_elems = 0;
   for (const GemmSpec& g : specs) {
     key += ":" + std::to_string(g.ep.M) + "x" + std::to_string(g.ep.N) + "x" + std::to_string(g.K);
+    if (g.B->mn_major) key += "t";
     if (g.sparse[0]) key += "s" + std::to_string(g.sparse[0]->nnz) + "/" + std::to_string(g.sparse[1]->nnz);
     out_elems += (long)g.ep.M * g.ep.N;
   }
@@ -1230,12 +1573,12 @@ int choose_tile_width(cudaStream_t st, const std::vector<GemmSpec>& specs, const
     auto it = tune_cache().find(key);
     if (it != tune_cache().end()) return it->second;
   }
-  // time both widths on the real operands; outputs go to scratch (beta = 0, no skip flags)
+  // time every candidate on the real operands; outputs go to scratch (beta = 0, no skip flags)
   double* scratch = nullptr;
   int* err = nullptr;
   GroupDesc* dev = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  int best = 256;
+  TileShape best{};
   float best_ms = 0.f;
   auto release = [&]() {
     if (scratch) cudaFree(scratch);
@@ -1252,34 +1595,36 @@ int choose_tile_width(cudaStream_t st, const std::vector<GemmSpec>& specs, const
     OMM_CUDA_TRY(cudaEventCreate(&e0));
     OMM_CUDA_TRY(cudaEventCreate(&e1));
     float total_ms = 0.f;
-    for (int bn : {256, 128}) {
+    bool first = true;
+    for (const TileShape& ts : cands) {
       std::vector<GroupDesc> h;
       long off = 0;
       int tiles = 0;
       for (const GemmSpec& g : specs) {
         Epilogue ep{scratch + off, g.ep.N, g.ep.N, 0, 1.0, 0.0, g.ep.M, g.ep.N, nullptr, err};
-        h.push_back(make_group(*g.A, *g.B, g.K, ep, tiles, bn, g.sparse[bn == 256 ? 0 : 1]));
-        tiles += tiles_of(ep, bn);
+        h.push_back(make_group(*g.A, *g.B, g.K, ep, tiles, ts.bn, g.sparse[sparse_slot(ts.bn)], ts.pair));
+        tiles += tiles_of(ep, ts.bn, ts.pair);
         off += (long)g.ep.M * g.ep.N;
       }
       OMM_CUDA_TRY(cudaMemcpyAsync(dev, h.data(), h.size() * sizeof(GroupDesc), cudaMemcpyHostToDevice, st));
-      gemm_persistent(st, dev, (int)h.size(), tiles, pl, err, bn);  // warm-up
+      gemm_persistent(st, dev, (int)h.size(), tiles, pl, err, ts.bn, ts.pair);  // warm-up
       constexpr int kReps = 3;
       OMM_CUDA_TRY(cudaEventRecord(e0, st));
-      for (int r = 0; r < kReps; ++r) gemm_persistent(st, dev, (int)h.size(), tiles, pl, err, bn);
+      for (int r = 0; r < kReps; ++r) gemm_persistent(st, dev, (int)h.size(), tiles, pl, err, ts.bn, ts.pair);
       OMM_CUDA_TRY(cudaEventRecord(e1, st));
       OMM_CUDA_TRY(cudaEventSynchronize(e1));  // h stays alive until the copy has been consumed
       float ms = 0.f;
       OMM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
       total_ms += ms * (kReps + 1) / kReps;
-      if (bn == 256 || ms < best_ms) {
-        best = bn;
+      if (first || ms < best_ms) {
+        best = ts;
         best_ms = ms;
       }
+      first = false;
     }
     int h_err = 0;
     OMM_CUDA_TRY(cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (h_err != 0) best = 256;  // a bounded wait expired: keep the default, the real launch reports it
+    if (h_err != 0) best = TileShape{};  // a bounded wait expired: keep the default, the real launch reports it
     if (ms_spent) *ms_spent = total_ms;
   } catch (...) {
     release();

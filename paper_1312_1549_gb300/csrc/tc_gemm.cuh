@@ -24,6 +24,9 @@ struct alignas(64) TensorMap {
 struct Operand {
   TensorMap map;       // boxes of 128 rows (A role), 256 rows (B role) or 64 x 64 (MN-major)
   TensorMap map_n128;  // boxes of 128 rows (as a B operand of 128-wide output tiles)
+  const __nv_bfloat16* base = nullptr;  // the stack (maps of other box heights are made from it)
+  long ld = 0;
+  long map_rows = 0;   // rows of the whole stack
   int box_rows = 0;    // rows of the boxes of `map`
   long rows = 0, cols = 0;
   int slices = 1;
@@ -113,7 +116,18 @@ void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const Pair
 inline void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, int npass, const Epilogue& ep) {
   gemm(st, A, B, K, npass == 3 ? pairs_split3() : pairs_single(), ep);
 }
-int tiles_of(const Epilogue& ep, int bn = 256);  // output tiles of one GEMM (128 x bn)
+// Output tiles of a persistent launch: 128 x bn on one SM (bn = 128 or 256), or, with pair,
+// 256 x bn on a cluster of two SMs that share the MMA (tcgen05 cta_group::2; bn = 128, 192 or 256;
+// the split form only).
+struct TileShape {
+  int bn = 256;
+  bool pair = false;
+};
+int tiles_of(const Epilogue& ep, int bn = 256, bool pair = false);  // work units of one GEMM
+// the partial-sum slots (one per epilogue warp and 128-row tile half) a kEpReduce GEMM writes
+inline int reduce_slots(const Epilogue& ep, const TileShape& ts) {
+  return 4 * tiles_of(ep, ts.bn, ts.pair) * (ts.pair ? 2 : 1);
+}
 
 // One GEMM of a grouped launch (device array element; tensor maps in global memory).
 // Block sparsity of a B operand (rows x K): for every block of bn rows, the 64-wide K blocks that
@@ -128,10 +142,12 @@ struct BlockLists {
   long dense = 0;  // nblocks x K blocks
 };
 // (re)computes bl for B (rows x cols float64, leading dimension ld, device) and row blocks of bn;
-// the first call allocates room for a dense pattern, later calls (same shape) rewrite in place so
-// that descriptors holding the pointers stay valid. Synchronises the stream.
+// (bn = 128, 192 or 256); the first call allocates room for a dense pattern (from the library's
+// pool, on st), later calls
+// (same shape) rewrite in place so that descriptors holding the pointers stay valid. Synchronises
+// the stream.
 void block_lists(cudaStream_t st, const double* B, long rows, long cols, long ld, int bn, BlockLists& bl);
-void free_block_lists(BlockLists& bl);
+void free_block_lists(BlockLists& bl, cudaStream_t st);  // st: the owner's current stream
 // fraction of the K blocks a product over these lists visits (1 for a dense product)
 inline double block_density(const BlockLists* bl) {
   return (bl == nullptr || bl->dense == 0) ? 1.0 : (double)bl->nnz / (double)bl->dense;
@@ -144,18 +160,19 @@ struct alignas(64) GroupDesc {
   int K, rowsA, rowsB, tile_begin;  // rowsA, rowsB: rows between the slices of A and B
   int offA, offB;                   // first row of A and B inside each slice
   int b_mn;                         // B is MN-major (its rows are the contracted index)
-  int bn;  // output tile width, 256 or 128 (all groups of one launch share it)
+  int bn;    // output tile width (all groups of one launch share it and pair)
+  int pair;  // 256-row tiles on a cluster of two SMs
   const int* kb_off;  // block sparsity of B for row blocks of bn (null: dense)
   const int* kb_idx;
 };
 GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin, int bn = 256,
-                     const BlockLists* sparse = nullptr);
+                     const BlockLists* sparse = nullptr, bool pair = false);
 // groups_dev: ngroups descriptors in device memory, sorted by tile_begin; all share the pair list
 void prepare_persistent();  // kernel attributes (call before a stream capture)
 // persistent grouped launch: one CTA per SM, double-buffered TMEM accumulators; err receives a
 // nonzero code if a bounded wait expired
 void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl,
-                     int* err, int bn = 256);
+                     int* err, int bn = 256, bool pair = false);
 // the same persistent kernel for one GEMM whose descriptor travels as a kernel parameter.
 // partial (optional, partial_capacity doubles): scratch that lets a GEMM of few output tiles run
 // each chunk of its pair list on its own CTA and add the chunks afterwards, in chunk order.
@@ -163,19 +180,25 @@ void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K,
                      const Epilogue& ep, double* partial = nullptr, long partial_capacity = 0,
                      const BlockLists* sparse = nullptr);
 
-// Tile-width autotuner: times one persistent launch over these GEMMs (the operands as given,
-// the outputs redirected to scratch) with 128 x 256 and with 128 x 128 output tiles, returns the
-// faster width, and remembers it per shape signature for the life of the process. ms_spent
-// receives the time spent timing (0 when the answer came from the cache).
+// Tile-shape autotuner: times one persistent launch over these GEMMs (the operands as given,
+// the outputs redirected to scratch) with each candidate shape -- 128 x 256 and 128 x 128 on one
+// SM, and (split form, allow_pair, every M >= 256) 256 x 128, 256 x 192 and 256 x 256 on SM pairs
+// -- returns the fastest, and remembers it per shape signature for the life of the process.
+// ms_spent receives the time spent timing (0 when the answer came from the cache).
 struct GemmSpec {
   const Operand* A;
   const Operand* B;
   int K;
-  Epilogue ep;                              // only M and N are used
-  const BlockLists* sparse[2] = {nullptr, nullptr};  // block lists of B for bn = 256 and 128
+  Epilogue ep;                                            // only M and N are used
+  const BlockLists* sparse[3] = {nullptr, nullptr, nullptr};  // block lists of B for bn = 256, 128, 192
 };
-int choose_tile_width(cudaStream_t st, const std::vector<GemmSpec>& specs, const PairList& pl,
-                      double* ms_spent = nullptr);
+inline int sparse_slot(int bn) { return bn == 256 ? 0 : (bn == 128 ? 1 : 2); }
+TileShape choose_tile_shape(cudaStream_t st, const std::vector<GemmSpec>& specs, const PairList& pl,
+                            double* ms_spent = nullptr, bool allow_pair = true);
+inline int choose_tile_width(cudaStream_t st, const std::vector<GemmSpec>& specs, const PairList& pl,
+                             double* ms_spent = nullptr) {
+  return choose_tile_shape(st, specs, pl, ms_spent, false).bn;
+}
 
 // x (float64, rows x cols, ld_src) -> hi = bf16(x), lo = bf16(x - hi) (ld_dst);
 // transposed variants write dst[j][i]. Skipped when sc's done/halt is set.
