@@ -690,6 +690,17 @@ def main():
                 "float64 DFMA (see fp64_peak)",
                 "launches": main_launches, "avg_launch_ms": main_ms / max(main_launches, 1),
                 "measured_in": "one extra profiled solve after the timed steps (CUDA events on the solver's stream)"}
+    if mixed and peak:
+        # each line-search GEMM on its own: issued flops / summed launch time, against the same peak
+        names = ["P G (single bf16 pass)", "[H D; S D] (split, block-sparse)", "projections (split)",
+                 "gradient (split, MN-major B)"]
+        roofline["per_gemm"] = []
+        for k, name in enumerate(names):
+            t, f = prof_info["ms_gemm_plan"][k], prof_info["flop_gemm_plan"][k]
+            if t > 0:
+                a = f / (t * 1e-3) / 1e12
+                roofline["per_gemm"].append({"gemm": name, "shape": prof_info["tile_width"][k],
+                                             "ms_per_solve": t, "achieved": a, "frac": a / peak})
     sl_ms = prof_info["ms_sliced_gemm"]
     sl_flop = prof_info["sliced_gemm_flop"]
     sl_n = prof_info["sliced_gemm_launches"]

@@ -104,10 +104,10 @@ typedef struct {
                            float64, or float64-class slices on the mixed path. 0 (default) -> off */
   int precond_slices;   /* mixed: 5-bit fixed-point slices of the sliced tensor-core products that
                            invert S + T/tau (2..10; 0 -> 5, about 25 bits of each row-scaled
-                           operand). P enters the line searches only through its bf16 hi/lo split
-                           (about 2^-16 of each element) and the converged point does not depend
-                           on P, so the float64-class 10 slices buy nothing there; the Cholesky
-                           flavour's factor always takes 10 */
+                           operand). P enters the line searches only through its bf16 rounding (the
+                           single-pass P G of the search direction) and the converged point does
+                           not depend on P, so the float64-class 10 slices buy nothing there; the
+                           Cholesky flavour's factor always takes 10 */
   int debug_expire_wait; /* tests of the timeout status only (0 = off, the default): 1 -> on the
                            mixed path the first tensor-core GEMM of every line search waits about
                            1 ms on a barrier that nothing arrives at, before it issues any copy or
@@ -155,6 +155,9 @@ typedef struct {
                                 totals too (the same in every instance's report) */
   double ms_transform;       /* opts.cholesky: the coefficient transforms C_r = L^T C0 and
                                 C = L^-T C_r of this solve */
+  double ms_gemm_plan[4];    /* mixed single solve with opts.profile: ms_main_gemm split over the
+                                P G, [H D; S D], projection and gradient GEMMs */
+  double flop_gemm_plan[4];  /* the same for main_gemm_flop */
 } omm_info;
 
 /* Create a solver context for one (H, S, T) and do the per-geometry setup:

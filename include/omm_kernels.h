@@ -105,18 +105,19 @@ omm_status omm_kernel_gemm_tc_kn(int M, int N, int K, const double* A, const dou
 omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double* B, double alpha,
                               double beta, double* C, int npass, void* stream);
 
-/* The 3-term split product (as omm_kernel_gemm_tc with npass = 3) on pairs of SMs: each cluster of
- * two CTAs computes a 256 x tile_n output tile with one tcgen05.mma.cta_group::2 stream, each SM
- * staging 128 rows of A and half of the tile's B, so that it fetches half the B bytes of a
- * single-SM tile of the same width. b_kn = 0: C = alpha A B^T + beta C with B N x K; b_kn = 1:
- * C = alpha A B + beta C with B K x N, read MN-major (as omm_kernel_gemm_tc_kn). tile_n: 128, 192
- * (b_kn = 0 only) or 256. block_sparse (b_kn = 0 only): skip the zero 64-wide K blocks of B as
- * omm_kernel_gemm_tc_blocksparse, with the same result. Every FP32 accumulation runs over K in the
- * same order as the single-SM kernels, so the result equals omm_kernel_gemm_tc_tiled's (or
- * omm_kernel_gemm_tc_kn's) bit for bit. Scratch is allocated and freed inside the call. Errors:
- * OMM_ERR_ARG, OMM_ERR_OOM, OMM_ERR_TIMEOUT, OMM_ERR_CUDA. */
+/* The contraction of omm_kernel_gemm_tc (npass = 3: split form, npass = 1: single bf16 pass) on
+ * pairs of SMs: each cluster of two CTAs computes a 256 x tile_n output tile with one
+ * tcgen05.mma.cta_group::2 stream, each SM staging 128 rows of A and half of the tile's B, so that
+ * it fetches half the B bytes of a single-SM tile of the same width. b_kn = 0: C = alpha A B^T +
+ * beta C with B N x K; b_kn = 1 (npass = 3 only): C = alpha A B + beta C with B K x N, read
+ * MN-major (as omm_kernel_gemm_tc_kn). tile_n: 128, 192 (b_kn = 0 only) or 256. block_sparse
+ * (b_kn = 0 only): skip the zero 64-wide K blocks of B as omm_kernel_gemm_tc_blocksparse, with the
+ * same result. The FP32 accumulation runs over the same products in the same K order as the
+ * single-SM kernels. Scratch is allocated and freed inside the call. Errors: OMM_ERR_ARG,
+ * OMM_ERR_OOM, OMM_ERR_TIMEOUT, OMM_ERR_CUDA. */
 omm_status omm_kernel_gemm_tc_pair(int M, int N, int K, const double* A, const double* B, double alpha,
-                                   double beta, double* C, int tile_n, int b_kn, int block_sparse, void* stream);
+                                   double beta, double* C, int npass, int tile_n, int b_kn, int block_sparse,
+                                   void* stream);
 
 /* Float64-class contraction on the BF16 tensor cores, as the mixed path
  * refreshes its state (float64 emulation by error-free fixed-point slicing:

@@ -39,7 +39,8 @@ class OmmInfo(ct.Structure):
                 ("tile_width", ct.c_int * 4), ("ms_autotune", ct.c_double),
                 ("ms_sliced_gemm", ct.c_double), ("sliced_gemm_flop", ct.c_double),
                 ("sliced_gemm_launches", ct.c_double), ("ms_batch", ct.c_double),
-                ("ms_transform", ct.c_double)]
+                ("ms_transform", ct.c_double), ("ms_gemm_plan", ct.c_double * 4),
+                ("flop_gemm_plan", ct.c_double * 4)]
 
     def as_dict(self):
         out = {}
@@ -92,7 +93,7 @@ _SIGNATURES = {
     "omm_kernel_quartic_coefficients": (_I, [_I, _P, _P, _D, ct.POINTER(_D), _P]),
     "omm_kernel_gemm_tc": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _P]),
     "omm_kernel_gemm_tc_kn": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _P]),
-    "omm_kernel_gemm_tc_pair": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _I, _I, _P]),
+    "omm_kernel_gemm_tc_pair": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _I, _I, _I, _P]),
     "omm_kernel_gemm_emu": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _P]),
     "omm_kernel_quartic_coefficients_noalloc": (_I, [_I, _P, _P, _D, ct.POINTER(_D), _P]),
 }

@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(dev::TB) b_update_subspace_kernel(const IterAr
 struct Grouped {
   tc::GroupDesc* dev = nullptr;
   int ngroups = 0, tiles = 0;
-  int bn = 256;  // output tile width chosen by the autotuner
+  int bn = 256;       // output tile shape chosen by the autotuner
+  bool pair = false;
 };
 
 constexpr int kGroupedGemms = 4;
@@ -131,7 +132,8 @@ struct omm_batch {
   // the grouped GEMMs (PG, [HD; SD], projections, gradient) are timed with CUDA events
   bool profile = false;
   Profiler prof;
-  int tile_width[4] = {256, 256, 256, 256};  // autotuned widths of the P G, [HD; SD], projection, G GEMMs
+  int tile_width[4] = {256, 256, 256, 256};  // autotuned shapes of the P G, [HD; SD], projection, G GEMMs
+                                             // (width, + 1000 for 256-row tiles on SM pairs)
   double ms_autotune = 0.0;
   // refreshes and certificates of different instances run concurrently on these
   cudaStream_t pool[kRefreshStreams] = {};
@@ -170,15 +172,16 @@ void batch_destroy(omm_batch* b) {
 void upload_groups(cudaStream_t st, Grouped* g, const std::vector<tc::GroupDesc>& v) {
   g->ngroups = (int)v.size();
   if (v.empty()) return;
-  g->tiles = v.back().tile_begin + tc::tiles_of(v.back().ep, v.back().bn);
+  g->tiles = v.back().tile_begin + tc::tiles_of(v.back().ep, v.back().bn, v.back().pair != 0);
   g->bn = v.back().bn;
+  g->pair = v.back().pair != 0;
   alloc(&g->dev, v.size(), st);
   OMM_CUDA_TRY(cudaMemcpyAsync(g->dev, v.data(), v.size() * sizeof(tc::GroupDesc), cudaMemcpyHostToDevice, st));
 }
 
 void timed_gemm(omm_batch* b, const Grouped& g, const tc::PairList& pl) {
   b->prof.begin(b->st);
-  tc::gemm_persistent(b->st, g.dev, g.ngroups, g.tiles, pl, b->err, g.bn);
+  tc::gemm_persistent(b->st, g.dev, g.ngroups, g.tiles, pl, b->err, g.bn, g.pair);
   b->prof.end(b->st, 0.0);
 }
 
@@ -189,7 +192,7 @@ void enqueue_line_search(omm_batch* b) {
   const dim3 rows_grid((unsigned)std::min(b->max_rows, 1024), cnt);
   const tc::PairList pl = tc::pairs_split3();
   if (b->precond) {
-    timed_gemm(b, b->gPG, pl);  // P G, the Polak-Ribiere products and max|G|, G_old <- G
+    timed_gemm(b, b->gPG, tc::pairs_single());  // P G (one bf16 pass), the Polak-Ribiere products and max|G|, G_old <- G
   } else {
     b_reduce_unpreconditioned_kernel<<<dim3(kBatchReduceBlocks, cnt), dev::TB, 0, st>>>(b->args);
     OMM_LAUNCH_CHECK();
@@ -315,14 +318,14 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       mixed_epilogues(c->mixed, c->sc, c->G, c->Gold, c->Y4, c->Proj, ep);
       if (b->precond) spg.push_back(tc::GemmSpec{v.opG, v.opP, mi, ep[0]});
       tc::GemmSpec hd{v.opD, v.opHS, mi, ep[1]};
-      hd.sparse[0] = &v.hs_blocks[0];
-      hd.sparse[1] = &v.hs_blocks[1];
+      for (int q = 0; q < 3; ++q) hd.sparse[q] = &v.hs_blocks[q];
       shd.push_back(hd);
       spr.push_back(tc::GemmSpec{v.opD, v.opYproj, mi, ep[2]});
       sg.push_back(tc::GemmSpec{v.opW, v.opYgrad, 4 * ni, ep[3]});
-      // issued tensor flops, 3 x 2 M N K (3-term split), of this instance's share of each GEMM
+      // issued tensor flops, 3 x 2 M N K (3-term split; 2 M N K for the single-pass P G), of this
+      // instance's share of each GEMM
       const double issued = 3.0 * 2.0 * ni;  // x N x K
-      b->gemm_flop[0].push_back(b->precond ? issued * mi * mi : 0.0);
+      b->gemm_flop[0].push_back(b->precond ? issued / 3.0 * mi * mi : 0.0);
       b->gemm_flop[1].push_back(issued * 2.0 * mi * mi);
       b->gemm_flop[2].push_back(issued * 4.0 * ni * mi);
       b->gemm_flop[3].push_back(issued * mi * 4.0 * ni);
@@ -338,23 +341,24 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
     for (int k = 0; k < 4; ++k) {
       if (specs[k]->empty()) continue;
       double ms_tune = 0.0;
-      const int bn = tc::choose_tile_width(b->st, *specs[k], tc::pairs_split3(), &ms_tune);
+      const tc::TileShape ts =
+          tc::choose_tile_shape(b->st, *specs[k], k == 0 ? tc::pairs_single() : tc::pairs_split3(), &ms_tune);
       b->ms_autotune += ms_tune;
-      b->tile_width[k] = bn;
+      b->tile_width[k] = ts.bn + (ts.pair ? 1000 : 0);
       for (size_t i = 0; i < specs[k]->size(); ++i) {
         const tc::GemmSpec& sp = (*specs[k])[i];
-        const tc::BlockLists* bl = sp.sparse[bn == 256 ? 0 : 1];
-        groups[k]->push_back(tc::make_group(*sp.A, *sp.B, sp.K, sp.ep, 0, bn, bl));
+        const tc::BlockLists* bl = sp.sparse[tc::sparse_slot(ts.bn)];
+        groups[k]->push_back(tc::make_group(*sp.A, *sp.B, sp.K, sp.ep, 0, ts.bn, bl, ts.pair));
         if (bl && k == 1) b->gemm_flop[1][i] *= tc::block_density(bl);  // issued flops of the visited blocks
       }
       if (k == 0)  // partial sums each instance's P G epilogue leaves for its direction step
-        for (int i = 0; i < count; ++i) args[i].nparts = 4 * tc::tiles_of((*specs[k])[i].ep, bn);
+        for (int i = 0; i < count; ++i) args[i].nparts = tc::reduce_slots((*specs[k])[i].ep, ts);
       std::stable_sort(groups[k]->begin(), groups[k]->end(),
                        [](const tc::GroupDesc& x, const tc::GroupDesc& y) { return x.K > y.K; });
       int t = 0;
       for (tc::GroupDesc& g : *groups[k]) {
         g.tile_begin = t;
-        t += tc::tiles_of(g.ep, g.bn);
+        t += tc::tiles_of(g.ep, g.bn, g.pair != 0);
       }
     }
     for (cudaStream_t& q : b->pool) OMM_CUDA_TRY(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));

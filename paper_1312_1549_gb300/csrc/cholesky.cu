@@ -233,15 +233,30 @@ leaf_f32_kernel(const double* A, long lda, int b, double* Linv, int* info, int c
     Linv[idx] = to_f64(X[i][j]);
   }
   if (Pblk != nullptr) {
-    // (X^T X)_ij = sum_{k >= i} X_ki X_kj for j <= i, mirrored
-    for (int idx = tid; idx < b * b; idx += nt) {
-      const int i = idx / b, j = idx % b;
-      if (j > i) continue;
-      float acc = 0.f;
-      for (int k = i; k < b; ++k) acc = fmaf(X[k][i], X[k][j], acc);
-      const double v = to_f64(acc);
-      Pblk[(long)i * ldp + j] = v;
-      Pblk[(long)j * ldp + i] = v;
+    // (X^T X)_ij = sum_{k >= i} X_ki X_kj for j <= i, mirrored. A warp takes whole rows i, its
+    // lanes the columns j = lane + 32 q (q <= i / 32); rows are dealt from both ends of the block
+    // (w, 2 nw - 1 - w, 2 nw + w, ...) so that the warps' work, (b - i)(i / 32 + 1), evens out
+    for (int t = 0;; ++t) {
+      const int i = (t & 1) ? (t + 1) * nwarps - 1 - warp : t * nwarps + warp;
+      if (t * nwarps >= b) break;
+      if (i >= b) continue;
+      const int nq = i / 32 + 1;
+      float acc[NL / 32] = {0.f, 0.f, 0.f, 0.f};
+      for (int k = i; k < b; ++k) {
+        const float xi = X[k][i];
+#pragma unroll
+        for (int q = 0; q < NL / 32; ++q)
+          if (q < nq) acc[q] = fmaf(xi, X[k][lane + 32 * q], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < NL / 32; ++q) {
+        const int j = lane + 32 * q;
+        if (q < nq && j <= i) {
+          const double v = to_f64(acc[q]);
+          Pblk[(long)i * ldp + j] = v;
+          Pblk[(long)j * ldp + i] = v;
+        }
+      }
     }
   }
 }

@@ -188,14 +188,14 @@ namespace {
 
 // the persistent launch the solver uses for its line-search GEMMs, on freshly split operands.
 // block_sparse: skip the 64-wide K blocks where B is zero (lists built from B); b_kn: B is given
-// K x N and read MN-major; pair: 256-row tiles on pairs of SMs (split form only)
+// K x N and read MN-major; pair: 256-row tiles on pairs of SMs
 omm_status gemm_tc_impl(const char* name, int M, int N, int K, const double* A, const double* B, double alpha,
                         double beta, double* C, int npass, int tile_n, bool block_sparse, bool b_kn, bool pair,
                         void* stream) {
   const bool width_ok = pair ? (tile_n == 128 || tile_n == 256 || (tile_n == 192 && !b_kn))
                              : (tile_n == 128 || tile_n == 256);
-  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || (npass != 1 && npass != 3) || (pair && npass != 3) ||
-      !width_ok || (b_kn && (npass != 3 || block_sparse))) {
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || (npass != 1 && npass != 3) || !width_ok ||
+      (b_kn && (npass != 3 || block_sparse))) {
     set_last_error(std::string(name) + ": invalid argument");
     return OMM_ERR_ARG;
   }
@@ -262,8 +262,8 @@ omm_status omm_kernel_gemm_tc_kn(int M, int N, int K, const double* A, const dou
 }
 
 omm_status omm_kernel_gemm_tc_pair(int M, int N, int K, const double* A, const double* B, double alpha, double beta,
-                                   double* C, int tile_n, int b_kn, int block_sparse, void* stream) {
-  return gemm_tc_impl("omm_kernel_gemm_tc_pair", M, N, K, A, B, alpha, beta, C, 3, tile_n, block_sparse != 0,
+                                   double* C, int npass, int tile_n, int b_kn, int block_sparse, void* stream) {
+  return gemm_tc_impl("omm_kernel_gemm_tc_pair", M, N, K, A, B, alpha, beta, C, npass, tile_n, block_sparse != 0,
                       b_kn != 0, true, stream);
 }
 

@@ -1,11 +1,12 @@
 // Mixed-precision line searches: every contraction of a line search runs on
-// the BF16 tensor cores in 3-term split form (tc_gemm.cu) with FP32
-// accumulation, while the state C, HC, SC, H_W, S_W and every scalar stay in
-// float64. Each tensor-core product carries a factor that shrinks with the
-// step, so its error does too (iterative refinement):
+// the BF16 tensor cores with FP32 accumulation, in 3-term split form
+// (tc_gemm.cu) except the preconditioned gradient P G of the search direction,
+// which is a single bf16 pass; the state C, HC, SC, H_W, S_W and every scalar
+// stay in float64. Each tensor-core product carries a factor that shrinks with
+// the step, so its error does too (iterative refinement):
 //   HD, SD = [H~; S] Delta                 (Delta -> 0)
 //   H', S', H'', S'' = Delta^T [HC SC HD SD]
-//   P G                                     (G -> 0)
+//   P G                                     (G -> 0; steers the search only)
 //   G = G_ref + 8 dHC - 4 (dS_W HC + dH_W SC + S_W,ref dHC + H_W,ref dSC)
 // where _ref is the state at the last float64 refresh and d = now - ref
 // (Eq. 12 expanded around the refresh point). Computing Eq. 12 directly on
@@ -302,6 +303,12 @@ namespace {
 
 enum { kPlanPG = 0, kPlanHD, kPlanProj, kPlanG };
 
+// The search direction's P G is one bf16 pass, bf16(G) bf16(P) with FP32 accumulation: the
+// direction only steers the search (Sec. 2.4: P stands in for the inverse Hessian), while the
+// line search and the gradient it is measured by keep the split products and the float64 state,
+// so the minimum reached is the same. The three other products use the 3-term split form.
+tc::PairList plan_pairs(int k) { return k == kPlanPG ? tc::pairs_single() : tc::pairs_split3(); }
+
 void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double* Gold, double* Y4, double* Proj) {
   const int m = ms->m, n = ms->n;
   tc::GroupDesc h[4] = {};
@@ -317,7 +324,7 @@ void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double
     if (k == kPlanHD)
       for (int q = 0; q < 3; ++q) spec.sparse[q] = &ms->hs_blocks[q];
     double ms_tune = 0.0;
-    const tc::TileShape ts = tc::choose_tile_shape(st, {spec}, tc::pairs_split3(), &ms_tune);
+    const tc::TileShape ts = tc::choose_tile_shape(st, {spec}, plan_pairs(k), &ms_tune);
     ms->plan_shape[k] = ts;
     ms->ms_autotune += ms_tune;
     h[k] = tc::make_group(*opA[k], *opB[k], K[k], ep[k], 0, ts.bn, spec.sparse[tc::sparse_slot(ts.bn)], ts.pair);
@@ -330,7 +337,7 @@ void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double
 }
 
 void run_plan(MixedState* ms, cudaStream_t st, int k) {
-  tc::gemm_persistent(st, ms->plans + k, 1, ms->plan_tiles[k], tc::pairs_split3(), ms->err, ms->plan_shape[k].bn,
+  tc::gemm_persistent(st, ms->plans + k, 1, ms->plan_tiles[k], plan_pairs(k), ms->err, ms->plan_shape[k].bn,
                       ms->plan_shape[k].pair);
 }
 
@@ -355,7 +362,7 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   if (precond) {
     pf.begin(st);
     run_plan(ms, st, kPlanPG);
-    pf.end(st, 2.0 * np * n * (double)m * m);
+    pf.end(st, 2.0 * n * (double)m * m, kPlanPG);  // one bf16 pass
     launch_control_direction(st, sc, ms->red, 1, mixed_reduce_parts(ms));
   } else {  // P = I: the same products with PG = G
     launch_reduce_unpreconditioned(st, n, m, G, Gold, ms->Dir32, ms->PG32, ms->ldm, part, sc);
@@ -365,11 +372,12 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   // [H~ D ; S D] (n x m layout): one GEMM over the stacked [H~; S]; the epilogue splits the result
   pf.begin(st);
   run_plan(ms, st, kPlanHD);
-  pf.end(st, 4.0 * np * n * (double)m * m * tc::block_density(&ms->hs_blocks[tc::sparse_slot(ms->plan_shape[kPlanHD].bn)]));
+  pf.end(st, 4.0 * np * n * (double)m * m * tc::block_density(&ms->hs_blocks[tc::sparse_slot(ms->plan_shape[kPlanHD].bn)]),
+         kPlanHD);
   // [H' | S' | H'' | S''] = D [HC; SC; HD; SD]^T (Eqs. 14-15)
   pf.begin(st);
   run_plan(ms, st, kPlanProj);
-  pf.end(st, 8.0 * np * n * (double)n * m);
+  pf.end(st, 8.0 * np * n * (double)n * m, kPlanProj);
   launch_traces(st, n, SWHW, Proj, part2, sc, /*fp32_products=*/true);
   launch_control_linesearch(st, sc, part2, traces_blocks(n));
   // Eq. 16 and the footnote's updates of C, HC, SC; dHC, dSC; and their splits
@@ -380,7 +388,7 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   // refresh point), and its split for the next P G
   pf.begin(st);
   run_plan(ms, st, kPlanG);
-  pf.end(st, 8.0 * np * n * (double)n * m);
+  pf.end(st, 8.0 * np * n * (double)n * m, kPlanG);
 }
 
 }  // namespace omm

@@ -47,18 +47,25 @@ void Profiler::begin(cudaStream_t st) {
   }
   cudaEventRecord(pairs_[used_].a, st);
 }
-void Profiler::end(cudaStream_t st, double f) {
+void Profiler::end(cudaStream_t st, double f, int tag) {
   if (!on) return;
   cudaEventRecord(pairs_[used_].b, st);
   pairs_[used_].flop = f;
+  pairs_[used_].tag = tag;
   ++used_;
 }
 void Profiler::collect() {
   for (int i = 0; i < used_; ++i) {
     float t = 0.f;
-    if (cudaEventElapsedTime(&t, pairs_[i].a, pairs_[i].b) == cudaSuccess) ms += t;
+    if (cudaEventElapsedTime(&t, pairs_[i].a, pairs_[i].b) != cudaSuccess) t = 0.f;
+    ms += t;
     flop += pairs_[i].flop;
     ++launches;
+    const int g = pairs_[i].tag;
+    if (g >= 0 && g < kTags) {
+      ms_tag[g] += t;
+      flop_tag[g] += pairs_[i].flop;
+    }
   }
   cudaGetLastError();
   used_ = 0;
@@ -80,7 +87,7 @@ namespace omm {
 constexpr int kMixedRoundCap = 400;
 constexpr int kEmuSlices = 10;  // fixed-point slices of the float64-class refresh (about 50 bits)
 // slices of the mixed path's preconditioner inverse: P reaches the line searches only through its
-// bf16 hi/lo split (about 2^-16 of each element), and the minimum does not depend on P
+// bf16 rounding (the single-pass P G of the search direction), and the minimum does not depend on P
 constexpr int kPrecondSlices = 5;
 // Below these sizes the native float64 routines are cheaper than the sliced tensor-core ones,
 // whose many small launches are latency-bound there: the inverse (or factor) of an m x m matrix
@@ -640,6 +647,10 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
     inf.ms_main_gemm = c->prof.ms;
     inf.main_gemm_launches = (double)c->prof.launches;
     inf.main_gemm_flop = c->prof.flop;
+    for (int t = 0; t < 4; ++t) {
+      inf.ms_gemm_plan[t] = c->prof.ms_tag[t];
+      inf.flop_gemm_plan[t] = c->prof.flop_tag[t];
+    }
     if (c->prof_sliced.on) {
       c->prof_sliced.collect();
       inf.ms_sliced_gemm = c->sliced_setup[0] + c->prof_sliced.ms;

@@ -91,17 +91,22 @@ void alloc(T** p, size_t count, cudaStream_t st) {
 // synchronisation adds the elapsed times.
 class Profiler {
  public:
+  static constexpr int kTags = 4;  // launches may be tagged 0..3 (the line-search GEMMs) for per-tag sums
   bool on = false;
   double ms = 0.0, flop = 0.0;
   long launches = 0;
+  double ms_tag[kTags] = {}, flop_tag[kTags] = {};
   void begin(cudaStream_t st);
-  void end(cudaStream_t st, double flop_of_launch);
+  void end(cudaStream_t st, double flop_of_launch, int tag = -1);
   void collect();  // the stream must have been synchronised
-  void reset() { ms = 0.0; flop = 0.0; launches = 0; }
+  void reset() {
+    ms = 0.0; flop = 0.0; launches = 0;
+    for (int t = 0; t < kTags; ++t) ms_tag[t] = flop_tag[t] = 0.0;
+  }
   ~Profiler();
 
  private:
-  struct Pair { cudaEvent_t a, b; double flop; };
+  struct Pair { cudaEvent_t a, b; double flop; int tag; };
   Pair* pairs_ = nullptr;
   int used_ = 0, cap_ = 0;
 };

@@ -216,7 +216,7 @@ __device__ __forceinline__ void fused_element(const Epilogue& ep, float a, int r
   double out;
   if (ep.mode == kEpGrad) {
     const long ox = (long)row * ep.ldx + cb, of = (long)row * ep.ldf + cb;
-    out = fma(ep.alpha, widen(a), fma(ep.xs, dev::f64_of_f32(ep.x1f[of]), ep.x0[ox]));
+    out = ep.x0[ox] + widen(fmaf((float)ep.xs, ep.x1f[of], (float)ep.alpha * a));
   } else if (ep.mode == kEpReduce) {
     const long ox = (long)row * ep.ldx + cb, of = (long)row * ep.ldf + cb;
     const double pg = widen(a), g = ep.x0[ox];
@@ -330,20 +330,31 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
 #pragma unroll
             for (int k = 0; k < 4; ++k) d[k] = __ldg(reinterpret_cast<const float4*>(ep.x2f + offf + c16) + k);
           }
+          // the sums of these 16 products in float32 (g rounded to float32 on the integer pipe),
+          // then widened into the float64 running sums: 3 float64 adds per 16 elements instead of
+          // 3 float64 FMAs per element on this GPU's narrow float64 pipe. The sums steer the
+          // direction (Polak-Ribiere) and give the slope <G, Delta>; 16-term float32 sums carry
+          // about 2^-20 of their absolute terms, far below what either needs.
+          float s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
-            const double p0 = widen(o[2 * k]), p1 = widen(o[2 * k + 1]);
-            red.v0 = fma(g[k].x, p0, red.v0);
-            red.v0 = fma(g[k].y, p1, red.v0);
+            const float gx = dev::f32_rne_bits(g[k].x), gy = dev::f32_rne_bits(g[k].y);
+            s0 = fmaf(gx, o[2 * k], s0);
+            s0 = fmaf(gy, o[2 * k + 1], s0);
             red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g[k].x) & 0x7FFFFFFFFFFFFFFFull);
             red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g[k].y) & 0x7FFFFFFFFFFFFFFFull);
             if (red.have_dir) {
-              red.v1 = fma(go[k].x, p0, red.v1);
-              red.v1 = fma(go[k].y, p1, red.v1);
+              s1 = fmaf(dev::f32_rne_bits(go[k].x), o[2 * k], s1);
+              s1 = fmaf(dev::f32_rne_bits(go[k].y), o[2 * k + 1], s1);
               const float dx = (k & 1) ? d[k >> 1].z : d[k >> 1].x, dy = (k & 1) ? d[k >> 1].w : d[k >> 1].y;
-              red.v2 = fma(g[k].x, dev::f64_of_f32(dx), red.v2);
-              red.v2 = fma(g[k].y, dev::f64_of_f32(dy), red.v2);
+              s2 = fmaf(gx, dx, s2);
+              s2 = fmaf(gy, dy, s2);
             }
+          }
+          red.v0 += widen(s0);
+          if (red.have_dir) {
+            red.v1 += widen(s1);
+            red.v2 += widen(s2);
           }
 #pragma unroll
           for (int k = 0; k < 8; ++k) *(reinterpret_cast<double2*>(ep.xout + offx + c16) + k) = g[k];
@@ -372,11 +383,14 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
         for (int k = 0; k < 8; ++k) a0[k] = __ldg(reinterpret_cast<const double2*>(ep.x0 + offx + c16) + k);
 #pragma unroll
         for (int k = 0; k < 4; ++k) a1[k] = __ldg(reinterpret_cast<const float4*>(ep.x1f + offf + c16) + k);
+        // the increment xs x1f + alpha acc in float32 (one rounding, 2^-24 of it, far below the
+        // split product's own 2^-17), then one float64 add onto x0
+        const float alf = (float)ep.alpha, xsf = (float)ep.xs;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const float fx = (k & 1) ? a1[k >> 1].z : a1[k >> 1].x, fy = (k & 1) ? a1[k >> 1].w : a1[k >> 1].y;
-          out[2 * k] = fma(ep.alpha, widen(v[c16 + 2 * k]), fma(ep.xs, dev::f64_of_f32(fx), a0[k].x));
-          out[2 * k + 1] = fma(ep.alpha, widen(v[c16 + 2 * k + 1]), fma(ep.xs, dev::f64_of_f32(fy), a0[k].y));
+          out[2 * k] = a0[k].x + widen(fmaf(xsf, fx, alf * v[c16 + 2 * k]));
+          out[2 * k + 1] = a0[k].y + widen(fmaf(xsf, fy, alf * v[c16 + 2 * k + 1]));
         }
       } else if (unit) {
 #pragma unroll
@@ -928,12 +942,18 @@ __device__ __forceinline__ void umma_commit_pair_local(uint32_t bar) {
 constexpr uint32_t PAIR_TMEM_COLS = 512;  // two accumulator buffers, 256 columns apart
 constexpr uint64_t PAIR_ABORT_SETTLE_NS = 200000ull;
 
-template <int TBN>
+// SPLIT: the 3-term split form (stages hold A_hi, A_lo, B_hi, B_lo); otherwise the pair list pl
+// (stages hold one slice of A and one of B), chunk by chunk: every chunk of a tile is one
+// accumulator round whose FP32 sum the epilogue adds to C in chunk order (the first with the
+// Epilogue's beta, the later ones with beta = 1), as in the single-SM kernel.
+template <int TBN, bool SPLIT>
 __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, int ngroups, int total_units,
-                                          int* err) {
+                                          const PairList& pl, int* err) {
   constexpr int TBH = TBN / 2;  // B rows (or MN-major output columns) staged by each CTA
   constexpr int BH_BYTES = TBH * BK * 2;
-  constexpr int SB = 2 * (A_BYTES + BH_BYTES);  // one CTA's stage: A_hi, A_lo, B_hi, B_lo
+  constexpr int NSL = SPLIT ? 2 : 1;                  // slices of each operand in a stage
+  constexpr int SB = NSL * (A_BYTES + BH_BYTES);      // one CTA's stage
+  constexpr int B_OFF = NSL * A_BYTES;                // B_hi (B_0) inside a stage
   constexpr int NS = ring_stages(SB);
   constexpr uint32_t ACC_STRIDE = 256;
   static_assert(TBN % 32 == 0 && TBN >= 64 && TBN <= 256 && NS >= 2 && NS * SB <= RING_BYTES && 2 * NS + 5 <= 28,
@@ -949,6 +969,9 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
   const uint32_t rank = cluster_ctarank();
   const bool leader = rank == 0;
   const int cluster = (int)(blockIdx.x >> 1), nclusters = (int)(gridDim.x >> 1);
+  const int nchunk = (SPLIT || pl.nchunk <= 0) ? 1 : pl.nchunk;
+  auto chunk_begin = [&](int c) { return (c == 0 || pl.nchunk <= 0) ? 0 : (int)pl.chunk_end[c - 1]; };
+  auto chunk_end = [&](int c) { return pl.nchunk <= 0 ? pl.n : (int)pl.chunk_end[c]; };
 
   if (threadIdx.x == 0) {
     for (int q = 0; q < NS; ++q) {
@@ -996,7 +1019,9 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
       const int m0 = (local % tiles_m) * 2 * BM + (int)rank * BM;  // this CTA's rows of A
       const int n0 = (local / tiles_m) * TBN + (int)rank * TBH;     // this CTA's half of B
       const KBlocks kbs = tile_kblocks(g, local, tiles_m);
-      for (int t = 0; t < kbs.count; ++t, ++it) {
+      const int nkb = kbs.count;
+      const int total = SPLIT ? nkb : pl.n * nkb;  // every pair of every chunk of the tile
+      for (int t = 0; t < total; ++t, ++it) {
         const int q = it % NS;
         const uint32_t r = it / NS;
         if (!mbar_wait(smem_u32(&bars[NS + q]), (r & 1) ^ 1)) {
@@ -1007,19 +1032,21 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
         const uint32_t full = mapa_shared(smem_u32(&bars[q]), 0);
         if (leader) mbar_expect_tx(smem_u32(&bars[q]), 2 * SB);  // the bytes of both CTAs
         const uint32_t sa = smem_u32(smem + q * SB);
-        const int kb = kbs.at(t);
-        tma_load_2d_pair(sa, mA, full, kb * BK, g->offA + m0);
-        tma_load_2d_pair(sa + A_BYTES, mA, full, kb * BK, g->rowsA + g->offA + m0);
+        const int p = SPLIT ? 0 : t / nkb, kb = kbs.at(SPLIT ? t : t % nkb);
+        const int ra = SPLIT ? 0 : (int)pl.a[p] * g->rowsA, rb = SPLIT ? 0 : (int)pl.b[p] * g->rowsB;
+        tma_load_2d_pair(sa, mA, full, kb * BK, ra + g->offA + m0);
+        if (SPLIT) tma_load_2d_pair(sa + A_BYTES, mA, full, kb * BK, g->rowsA + g->offA + m0);
         if (g->b_mn) {
 #pragma unroll
           for (int h = 0; h < TBH / 64; ++h) {
-            tma_load_2d_pair(sa + 2 * A_BYTES + h * MN_BOX_BYTES, mB, full, n0 + 64 * h, g->offB + kb * BK);
-            tma_load_2d_pair(sa + 2 * A_BYTES + BH_BYTES + h * MN_BOX_BYTES, mB, full, n0 + 64 * h,
-                             g->rowsB + g->offB + kb * BK);
+            tma_load_2d_pair(sa + B_OFF + h * MN_BOX_BYTES, mB, full, n0 + 64 * h, rb + g->offB + kb * BK);
+            if (SPLIT)
+              tma_load_2d_pair(sa + B_OFF + BH_BYTES + h * MN_BOX_BYTES, mB, full, n0 + 64 * h,
+                               g->rowsB + g->offB + kb * BK);
           }
         } else {
-          tma_load_2d_pair(sa + 2 * A_BYTES, mB, full, kb * BK, g->offB + n0);
-          tma_load_2d_pair(sa + 2 * A_BYTES + BH_BYTES, mB, full, kb * BK, g->rowsB + g->offB + n0);
+          tma_load_2d_pair(sa + B_OFF, mB, full, kb * BK, rb + g->offB + n0);
+          if (SPLIT) tma_load_2d_pair(sa + B_OFF + BH_BYTES, mB, full, kb * BK, g->rowsB + g->offB + n0);
         }
       }
     }
@@ -1047,35 +1074,40 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
       auto bdesc = [bmn](uint32_t addr, int k) {
         return bmn ? smem_desc_mn(addr + (uint32_t)k * 2048u) : smem_desc(addr + (uint32_t)k * 32u);
       };
-      const uint32_t buf = lt & 1, use = lt >> 1;
-      if (!mbar_wait(smem_u32(&bars[2 * NS + 2 + buf]), (use & 1) ^ 1)) {
-        *abort_flag = 1;
-        atomicCAS(err, 0, 4);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t d = tmem + buf * ACC_STRIDE;
-      for (int t = 0; t < nkb; ++t, ++it) {
-        const int q = it % NS;
-        const uint32_t r = it / NS;
-        if (!mbar_wait(smem_u32(&bars[q]), r & 1)) {
+      for (int c = 0; c < nchunk && !*abort_flag; ++c) {
+        const uint32_t buf = lt & 1, use = lt >> 1;
+        if (!mbar_wait(smem_u32(&bars[2 * NS + 2 + buf]), (use & 1) ^ 1)) {
           *abort_flag = 1;
-          atomicCAS(err, 0, 2);
+          atomicCAS(err, 0, 4);
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t sa = smem_u32(smem + q * SB);
-        const uint32_t alo = sa + A_BYTES, bhi = sa + 2 * A_BYTES, blo = bhi + BH_BYTES;
+        const uint32_t d = tmem + buf * ACC_STRIDE;
+        const int total = SPLIT ? nkb : (chunk_end(c) - chunk_begin(c)) * nkb;
+        for (int t = 0; t < total; ++t, ++it) {
+          const int q = it % NS;
+          const uint32_t r = it / NS;
+          if (!mbar_wait(smem_u32(&bars[q]), r & 1)) {
+            *abort_flag = 1;
+            atomicCAS(err, 0, 2);
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(smem + q * SB);
+          const uint32_t alo = sa + A_BYTES, bhi = sa + B_OFF, blo = bhi + BH_BYTES;
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k) {
-          umma_bf16_pair(d, smem_desc(sa + k * 32), bdesc(bhi, k), idesc, (t > 0 || k > 0) ? 1u : 0u);
-          umma_bf16_pair(d, smem_desc(sa + k * 32), bdesc(blo, k), idesc, 1u);
-          umma_bf16_pair(d, smem_desc(alo + k * 32), bdesc(bhi, k), idesc, 1u);
+          for (int k = 0; k < BK / 16; ++k) {
+            umma_bf16_pair(d, smem_desc(sa + k * 32), bdesc(bhi, k), idesc, (t > 0 || k > 0) ? 1u : 0u);
+            if (SPLIT) {
+              umma_bf16_pair(d, smem_desc(sa + k * 32), bdesc(blo, k), idesc, 1u);
+              umma_bf16_pair(d, smem_desc(alo + k * 32), bdesc(bhi, k), idesc, 1u);
+            }
+          }
+          umma_commit_pair(smem_u32(&bars[NS + q]));  // stage q of both CTAs is free
         }
-        umma_commit_pair(smem_u32(&bars[NS + q]));  // stage q of both CTAs is free
+        umma_commit_pair(smem_u32(&bars[2 * NS + buf]));  // both halves of the accumulator are complete
+        ++lt;
       }
-      umma_commit_pair(smem_u32(&bars[2 * NS + buf]));  // both halves of the accumulator are complete
-      ++lt;
     }
     if (*abort_flag) {  // every MMA issued so far is complete before the tensor memory is freed
       umma_commit_pair_local(smem_u32(&bars[2 * NS + 4]));
@@ -1091,30 +1123,36 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
       const GroupDesc* g = groups + find_group(groups, ngroups, u);
       const int* skip = g->ep.skip;
       if (skip != nullptr && (skip[0] | skip[1])) continue;
-      const uint32_t buf = lt & 1, use = lt >> 1;
-      const bool ok = !*abort_flag && mbar_wait(smem_u32(&bars[2 * NS + buf]), use & 1);
-      if (!ok) {
-        atomicCAS(err, 0, 3);
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const Epilogue ep = g->ep;
-      const int local = u - g->tile_begin, tiles_m = (ep.M + 2 * BM - 1) / (2 * BM);
-      const int m0 = (local % tiles_m) * 2 * BM + (int)rank * BM, n0 = (local / tiles_m) * TBN;
-      const int row = m0 + lane_base + lane;
-      EpiRed red;
-      red.have_dir = ep.mode == kEpReduce && ep.sc != nullptr && ep.sc->have_dir;
+      bool failed = false;
+      for (int c = 0; c < nchunk; ++c) {
+        const uint32_t buf = lt & 1, use = lt >> 1;
+        const bool ok = !*abort_flag && mbar_wait(smem_u32(&bars[2 * NS + buf]), use & 1);
+        if (!ok) {
+          atomicCAS(err, 0, 3);
+          failed = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        Epilogue ep = g->ep;
+        if (c > 0) ep.beta = 1.0;
+        const int local = u - g->tile_begin, tiles_m = (ep.M + 2 * BM - 1) / (2 * BM);
+        const int m0 = (local % tiles_m) * 2 * BM + (int)rank * BM, n0 = (local / tiles_m) * TBN;
+        const int row = m0 + lane_base + lane;
+        EpiRed red;
+        red.have_dir = ep.mode == kEpReduce && ep.sc != nullptr && ep.sc->have_dir;
 #pragma unroll 1
-      for (int j = 0; j < TBN / 32; ++j) {
-        float v[32];
-        tmem_ld32(tmem + buf * ACC_STRIDE + ((uint32_t)lane_base << 16) + (uint32_t)(j * 32), v);
-        store_chunk(ep, row, n0 + j * 32, v, red);
+        for (int j = 0; j < TBN / 32; ++j) {
+          float v[32];
+          tmem_ld32(tmem + buf * ACC_STRIDE + ((uint32_t)lane_base << 16) + (uint32_t)(j * 32), v);
+          store_chunk(ep, row, n0 + j * 32, v, red);
+        }
+        flush_reduce(ep, local * 2 + (int)rank, warp & 3, red);  // slots of 128-row halves
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(buf ? acc_empty1 : acc_empty0);
+        ++lt;
       }
-      flush_reduce(ep, local * 2 + (int)rank, warp & 3, red);  // slots of 128-row halves
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive_cluster(buf ? acc_empty1 : acc_empty0);
-      ++lt;
+      if (failed) break;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1129,10 +1167,19 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
   }
 }
 
-template <int TBN>
+template <int TBN, bool SPLIT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
-gemm_pair_kernel(const GroupDesc* __restrict__ groups, int ngroups, int total_units, int* err) {
-  pair_body<TBN>(groups, ngroups, total_units, err);
+gemm_pair_kernel(const GroupDesc* __restrict__ groups, int ngroups, int total_units,
+                 const __grid_constant__ PairList pl, int* err) {
+  pair_body<TBN, SPLIT>(groups, ngroups, total_units, pl, err);
+}
+
+// one GEMM, its descriptor (tensor maps included) in the kernel's parameter space
+template <int TBN, bool SPLIT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+gemm_pair_one_kernel(const __grid_constant__ GroupDesc g, int total_units, const __grid_constant__ PairList pl,
+                     int* err) {
+  pair_body<TBN, SPLIT>(&g, 1, total_units, pl, err);
 }
 
 template <bool FUSED, int TBN>
@@ -1193,7 +1240,7 @@ int pair_clusters() {
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     int c = 0;
-    if (cudaOccupancyMaxActiveClusters(&c, gemm_pair_kernel<256>, &cfg) != cudaSuccess || c <= 0) {
+    if (cudaOccupancyMaxActiveClusters(&c, gemm_pair_kernel<256, true>, &cfg) != cudaSuccess || c <= 0) {
       cudaGetLastError();
       c = sm_count() / 2;
     }
@@ -1299,6 +1346,8 @@ void check_pairs(const PairList& pl, int slices_a, int slices_b) {
   if (pl.nchunk > 0 && pl.chunk_end[pl.nchunk - 1] != pl.n) throw CudaError{cudaErrorInvalidValue, "tc: chunk list"};
 }
 
+bool is_single(const PairList& pl) { return pl.n == 1 && pl.nchunk <= 1 && pl.a[0] == 0 && pl.b[0] == 0; }
+
 bool is_split3(const PairList& pl) {
   return pl.n == 3 && pl.nchunk <= 1 && pl.a[0] == 0 && pl.b[0] == 0 && pl.a[1] == 0 && pl.b[1] == 1 && pl.a[2] == 1 && pl.b[2] == 0;
 }
@@ -1383,9 +1432,11 @@ void prepare_persistent() {
                                       SMEM_BYTES));
     OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_persistent_one_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       SMEM_BYTES));
-    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_pair_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_pair_kernel<192>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    OMM_CUDA_TRY(cudaFuncSetAttribute(gemm_pair_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    for (const void* f : {(const void*)gemm_pair_kernel<128, true>, (const void*)gemm_pair_kernel<192, true>,
+                          (const void*)gemm_pair_kernel<256, true>, (const void*)gemm_pair_kernel<128, false>,
+                          (const void*)gemm_pair_kernel<192, false>, (const void*)gemm_pair_kernel<256, false>,
+                          (const void*)gemm_pair_one_kernel<256, true>, (const void*)gemm_pair_one_kernel<256, false>})
+      OMM_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     sm_count();
     pair_clusters();
     attr_set = true;
@@ -1399,15 +1450,15 @@ void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, 
   if (ngroups <= 0 || total_tiles <= 0) return;
   const bool fused = is_split3(pl);
   if (pair) {
-    if (!fused || (bn != 256 && bn != 192 && bn != 128))
-      throw CudaError{cudaErrorInvalidValue, "tc::gemm_persistent: SM pairs run the split form, 128/192/256 wide"};
+    if (bn != 256 && bn != 192 && bn != 128)
+      throw CudaError{cudaErrorInvalidValue, "tc::gemm_persistent: SM-pair tiles are 128, 192 or 256 wide"};
     const unsigned grid = 2u * (unsigned)std::min(total_tiles, pair_clusters());
-    if (bn == 256)
-      gemm_pair_kernel<256><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, err);
-    else if (bn == 192)
-      gemm_pair_kernel<192><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, err);
-    else
-      gemm_pair_kernel<128><<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, err);
+    auto go = [&](auto kernel) {
+      kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, pl, err);
+    };
+    if (bn == 256) fused ? go(gemm_pair_kernel<256, true>) : go(gemm_pair_kernel<256, false>);
+    else if (bn == 192) fused ? go(gemm_pair_kernel<192, true>) : go(gemm_pair_kernel<192, false>);
+    else fused ? go(gemm_pair_kernel<128, true>) : go(gemm_pair_kernel<128, false>);
     OMM_LAUNCH_CHECK();
     return;
   }
@@ -1436,6 +1487,18 @@ void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K,
   const int nchunk = pl.nchunk > 0 ? pl.nchunk : 1;
   const bool split = !fused && partial != nullptr && nchunk > 1 && 2 * tiles < sm_count() &&
                      (long)nchunk * ep.M * ep.N <= partial_capacity && ep.skip == nullptr;
+  // a product with at least a wave of 256-row tiles runs on SM pairs (half the B bytes per SM)
+  const int pair_units = tiles_of(ep, BN, true);
+  if (!split && ep.M >= 2 * BM && pair_units >= pair_clusters()) {
+    const GroupDesc gp = make_group(A, B, K, ep, 0, BN, sparse, true);
+    const unsigned pgrid = 2u * (unsigned)std::min(pair_units, pair_clusters());
+    if (fused)
+      gemm_pair_one_kernel<BN, true><<<pgrid, NTHREADS, SMEM_BYTES, st>>>(gp, pair_units, pl, ep.err);
+    else
+      gemm_pair_one_kernel<BN, false><<<pgrid, NTHREADS, SMEM_BYTES, st>>>(gp, pair_units, pl, ep.err);
+    OMM_LAUNCH_CHECK();
+    return;
+  }
   const int units = split ? tiles * nchunk : tiles;
   const unsigned grid = (unsigned)std::min(units, sm_count());
   if (fused)
@@ -1550,9 +1613,10 @@ TileShape choose_tile_shape(cudaStream_t st, const std::vector<GemmSpec>& specs,
   // candidates: one SM per 128-row tile, and (split form, every M >= 256) SM pairs; 192-wide pair
   // tiles need K-major B (an SM stages 96 rows) and, for a block-sparse B, lists for that width
   std::vector<TileShape> cands = {{256, false}, {128, false}};
-  bool pair_ok = allow_pair && is_split3(pl), w192 = true;
+  const bool split = is_split3(pl);
+  bool pair_ok = allow_pair && (split || is_single(pl)), w192 = true;
   for (const GemmSpec& g : specs) {
-    if (g.ep.M < 2 * BM || g.A->slices < 2 || g.B->slices < 2) pair_ok = false;
+    if (g.ep.M < 2 * BM || (split && (g.A->slices < 2 || g.B->slices < 2))) pair_ok = false;
     if (g.B->mn_major || (g.sparse[0] != nullptr && g.sparse[2] == nullptr)) w192 = false;
   }
   if (pair_ok) {

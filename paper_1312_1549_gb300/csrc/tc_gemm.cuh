@@ -62,9 +62,11 @@ PairList pairs_single();   // A_0 B_0
 // Fused forms (mode), all with split_cols = N unless stated:
 //   kEpPlain   the above; with c_f32 C is float32 and receives alpha * acc (beta is not used;
 //              split_cols and split_stride apply, in float elements).
-//   kEpGrad    C = alpha * acc + (x0 + xs * x1f)   (the incremental gradient about a refresh
-//              point: x0 = G_ref (float64), x1f = dHC (float32), xs = 8, alpha = -4)
-//   kEpReduce  C = acc as float32 (c_f32 = 1, alpha = 1), and with g = x0, g_old = x1 (float64),
+//   kEpGrad    C = x0 + (xs * x1f + alpha * acc)   (the incremental gradient about a refresh
+//              point: x0 = G_ref (float64), x1f = dHC (float32), xs = 8, alpha = -4; the
+//              increment is formed in float32 with one rounding, then added in float64)
+//   kEpReduce  C = acc as float32 (c_f32 = 1, alpha = 1), and with g = x0, g_old = x1 (float64,
+//              rounded to float32 for the sums, which run in float32 over 16 columns at a time),
 //              d = x2f (float32) the sums <g, C>, <g_old, C>, <g, d> (the last two only when
 //              sc->have_dir) and max|g| of each epilogue warp's rows of the tile go to
 //              part[(tile * 4 + warp) * 4 + 0..3]; then xout = g (xout may alias x1: every
@@ -118,7 +120,7 @@ inline void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, int
 }
 // Output tiles of a persistent launch: 128 x bn on one SM (bn = 128 or 256), or, with pair,
 // 256 x bn on a cluster of two SMs that share the MMA (tcgen05 cta_group::2; bn = 128, 192 or 256;
-// the split form only).
+// the split form or a single pass).
 struct TileShape {
   int bn = 256;
   bool pair = false;
@@ -182,7 +184,8 @@ void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K,
 
 // Tile-shape autotuner: times one persistent launch over these GEMMs (the operands as given,
 // the outputs redirected to scratch) with each candidate shape -- 128 x 256 and 128 x 128 on one
-// SM, and (split form, allow_pair, every M >= 256) 256 x 128, 256 x 192 and 256 x 256 on SM pairs
+// SM, and (split form or single pass, allow_pair, every M >= 256) 256 x 128, 256 x 192 and
+// 256 x 256 on SM pairs
 // -- returns the fastest, and remembers it per shape signature for the life of the process.
 // ms_spent receives the time spent timing (0 when the answer came from the cache).
 struct GemmSpec {

@@ -46,6 +46,30 @@ def test_pair_split_product(S, M, N, K, tile_n):
     assert np.abs(got - C1.cpu().numpy()).max() <= 2.0 ** -20 * scale.max()
 
 
+def bf16_round(x):
+    """float64 -> nearest bf16 (8 significant bits, ties to even), rounded once."""
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+@pytest.mark.parametrize("tile_n", [128, 192, 256])
+@pytest.mark.parametrize("M,N,K", [(256, 256, 64), (130, 257, 70), (1024, 1664, 1000), (1, 1, 1)])
+def test_pair_single_pass_is_exact_bf16_product(S, M, N, K, tile_n):
+    """npass = 1 (the search direction's P G): the product of the bf16-rounded operands up to FP32
+    accumulation (K 2^-23), and the single-SM kernel's value."""
+    rng = np.random.default_rng(M + 5 * N + K + tile_n)
+    A = rng.normal(size=(M, K)); B = rng.normal(size=(N, K))
+    C = dev(np.zeros((M, N)))
+    S.gemm_tc_pair(dev(A), dev(B), C, npass=1, tile_n=tile_n)
+    got = C.cpu().numpy()
+    ref = bf16_round(A) @ bf16_round(B).T
+    scale = np.abs(bf16_round(A)) @ np.abs(bf16_round(B)).T
+    assert np.all(np.abs(got - ref) <= K * 2.0 ** -23 * scale + 1e-30)
+    C1 = dev(np.zeros((M, N)))
+    S.gemm_tc(dev(A), dev(B), C1, npass=1, tile_n=128)
+    assert np.abs(got - C1.cpu().numpy()).max() <= 2.0 ** -20 * scale.max()
+
+
 @pytest.mark.parametrize("tile_n", [128, 256])
 @pytest.mark.parametrize("M,N,K", [(256, 256, 64), (1024, 640, 256), (200, 300, 72), (512, 6656 // 4, 4096 // 4)])
 def test_pair_mn_major_b(S, M, N, K, tile_n):
@@ -88,7 +112,8 @@ def test_pair_blocksparse_equals_dense(S, M, N, K, tile_n):
 def test_pair_rejects_bad_arguments(S):
     from paper_1312_1549_gb300 import _native as N
     A = dev(np.ones((256, 64))); B = dev(np.ones((64, 64))); C = dev(np.zeros((256, 64)))
-    for kw in ({"tile_n": 64}, {"tile_n": 192, "b_kn": True}, {"tile_n": 128, "b_kn": True, "block_sparse": True}):
+    for kw in ({"tile_n": 64}, {"tile_n": 192, "b_kn": True}, {"tile_n": 128, "b_kn": True, "block_sparse": True},
+               {"npass": 2}, {"npass": 1, "b_kn": True}):
         with pytest.raises(N.OMMError) as e:
             S.gemm_tc_pair(A, B, C, **kw)
         assert e.value.status == 1

@@ -114,9 +114,10 @@ def test_mixed_solve_without_preconditioner(S, si64):
 
 
 # few output tiles: every chunk on its own CTA and a reduction; (1024, 4096, 2048): 128 tiles, chunks in
-# order on one CTA per tile
+# order on one CTA per tile; (1024, 6144, 1000) and (2048, 5000, 333): at least a wave of 256-row tiles,
+# chunks in order on SM pairs
 @pytest.mark.parametrize("M,N,K", [(128, 256, 64), (200, 300, 1000), (64, 1000, 6656), (130, 70, 16384),
-                                   (1024, 4096, 2048)])
+                                   (1024, 4096, 2048), (1024, 6144, 1000), (2048, 5000, 333)])
 def test_gemm_emu_is_float64_class(S, M, N, K):
     """10 fixed-point slices: error within 2^-44 of |alpha||A||B|^T + |beta C| elementwise."""
     rng = np.random.default_rng(M * N + K)
@@ -186,7 +187,7 @@ def test_spd_inverse_sliced_preconditioner_matches_oracle(S):
 
 
 # The preconditioner-grade inverse (the mixed solver's default): fewer slices and float32 leaves.
-# P reaches the line searches only through its bf16 hi/lo split (about 2^-16 of each element);
+# P reaches the line searches only through its bf16 rounding (2^-9 of each element, the single-pass P G);
 # the residual bound below (5 slices, about 2^-24 of each row-scaled operand, condition numbers
 # near 10) keeps P well inside that.
 @pytest.mark.parametrize("m", [5, 65, 200, 1000, 2500])
