@@ -57,6 +57,25 @@ GOLDEN = os.path.join(ROOT, "tests", "golden")
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 float64 FMA rate, nominal (context; the roofline uses the probe)
 
 
+# DRAM bytes per launch of the four mixed line-search GEMMs of the Si512 workload (average of
+# dram__bytes_read.sum + dram__bytes_write.sum over the P G, [HD; SD], projection and gradient
+# launches of one ncu capture: profiles/traffic_si512_line_search.md). Valid only for the GEMM
+# source it was measured on: reported as null once tc_gemm.cu has changed.
+GEMM_TRAFFIC_BYTES = 304.9e6
+GEMM_TRAFFIC_SOURCE_SHA256 = "0623d445c5564f62aa213aa43acc608ea966e39123233097ec0d91fa4dd89654"
+
+
+def gemm_traffic():
+    import hashlib
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1312_1549_gb300", "csrc", "tc_gemm.cu")
+    try:
+        with open(src, "rb") as fh:
+            same = hashlib.sha256(fh.read()).hexdigest() == GEMM_TRAFFIC_SOURCE_SHA256
+    except OSError:
+        same = False
+    return GEMM_TRAFFIC_BYTES if same else None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -682,7 +701,11 @@ def main():
     achieved = main_flop / (main_ms * 1e-3) / 1e12 if main_ms > 0 else None
     peak = peaks["bf16_tflops_sustained"] if mixed else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+                "frac": (achieved / peak) if (achieved and peak) else None,
+                "traffic": gemm_traffic() if mixed else None,
+                "traffic_source": ("bytes per launch, mean over the four line-search GEMMs of one ncu capture "
+                                   "(dram__bytes_read.sum + dram__bytes_write.sum; algorithmic 277.5 MB); "
+                                   "null once the GEMM source differs from the one measured") if mixed else None,
                 "kernel": ("gemm_pair_kernel / gemm_persistent_kernel (tcgen05 on SM pairs or single SMs, "
                            "fused 3-term split; shapes as tile_width_autotuned)" if mixed
                            else "dgemm_kernel (DFMA)"),
