@@ -143,7 +143,8 @@ typedef struct {
   int tile_width[4];         /* mixed: output tile shape the autotuner chose for the P G, [H D; S D],
                                 projection and gradient GEMMs: 256 or 128 (columns of a 128-row
                                 tile on one SM), 1000 + 128, 192 or 256 (a 256-row tile on a pair
-                                of SMs), 0: not run */
+                                of SMs), 2000 + the width (the same on a cluster of two pairs that
+                                share the A operand), 0: not run */
   double ms_autotune;        /* time the autotuner spent timing candidates (0 when cached) */
   double ms_sliced_gemm;     /* with opts.profile: summed duration of the float64-class sliced
                                 products of omm_create (inverse) and this solve (refreshes,

@@ -113,11 +113,14 @@ omm_status omm_kernel_gemm_tc(int M, int N, int K, const double* A, const double
  * MN-major (as omm_kernel_gemm_tc_kn). tile_n: 128, 192 (b_kn = 0 only) or 256. block_sparse
  * (b_kn = 0 only): skip the zero 64-wide K blocks of B as omm_kernel_gemm_tc_blocksparse, with the
  * same result. The FP32 accumulation runs over the same products in the same K order as the
- * single-SM kernels. Scratch is allocated and freed inside the call. Errors: OMM_ERR_ARG,
- * OMM_ERR_OOM, OMM_ERR_TIMEOUT, OMM_ERR_CUDA. */
+ * single-SM kernels. cluster_pairs = 2 (block_sparse = 0 only): two such pairs per cluster of four
+ * CTAs, side by side along N (256 x 2 tile_n per cluster), share A: each SM loads half of its 128
+ * A rows and multicasts them to its counterpart in the other pair, so A leaves L2 once per two
+ * column tiles. Scratch is allocated and freed inside the call. Errors: OMM_ERR_ARG, OMM_ERR_OOM,
+ * OMM_ERR_TIMEOUT, OMM_ERR_CUDA. */
 omm_status omm_kernel_gemm_tc_pair(int M, int N, int K, const double* A, const double* B, double alpha,
                                    double beta, double* C, int npass, int tile_n, int b_kn, int block_sparse,
-                                   void* stream);
+                                   int cluster_pairs, void* stream);
 
 /* Float64-class contraction on the BF16 tensor cores, as the mixed path
  * refreshes its state (float64 emulation by error-free fixed-point slicing:

@@ -93,7 +93,7 @@ _SIGNATURES = {
     "omm_kernel_quartic_coefficients": (_I, [_I, _P, _P, _D, ct.POINTER(_D), _P]),
     "omm_kernel_gemm_tc": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _P]),
     "omm_kernel_gemm_tc_kn": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _P]),
-    "omm_kernel_gemm_tc_pair": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _I, _I, _I, _P]),
+    "omm_kernel_gemm_tc_pair": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _I, _I, _I, _I, _P]),
     "omm_kernel_gemm_emu": (_I, [_I, _I, _I, _P, _P, _D, _D, _P, _I, _P]),
     "omm_kernel_quartic_coefficients_noalloc": (_I, [_I, _P, _P, _D, ct.POINTER(_D), _P]),
 }

@@ -98,6 +98,7 @@ struct Grouped {
   int ngroups = 0, tiles = 0;
   int bn = 256;       // output tile shape chosen by the autotuner
   bool pair = false;
+  bool quad = false;
 };
 
 constexpr int kGroupedGemms = 4;
@@ -133,7 +134,8 @@ struct omm_batch {
   bool profile = false;
   Profiler prof;
   int tile_width[4] = {256, 256, 256, 256};  // autotuned shapes of the P G, [HD; SD], projection, G GEMMs
-                                             // (width, + 1000 for 256-row tiles on SM pairs)
+                                             // (width, + 1000 for 256-row tiles on SM pairs, + 2000 on
+                                             // clusters of two pairs sharing A)
   double ms_autotune = 0.0;
   // refreshes and certificates of different instances run concurrently on these
   cudaStream_t pool[kRefreshStreams] = {};
@@ -172,16 +174,17 @@ void batch_destroy(omm_batch* b) {
 void upload_groups(cudaStream_t st, Grouped* g, const std::vector<tc::GroupDesc>& v) {
   g->ngroups = (int)v.size();
   if (v.empty()) return;
-  g->tiles = v.back().tile_begin + tc::tiles_of(v.back().ep, v.back().bn, v.back().pair != 0);
+  g->tiles = v.back().tile_begin + tc::tiles_of(v.back().ep, v.back().bn, v.back().pair != 0, v.back().quad != 0);
   g->bn = v.back().bn;
   g->pair = v.back().pair != 0;
+  g->quad = v.back().quad != 0;
   alloc(&g->dev, v.size(), st);
   OMM_CUDA_TRY(cudaMemcpyAsync(g->dev, v.data(), v.size() * sizeof(tc::GroupDesc), cudaMemcpyHostToDevice, st));
 }
 
 void timed_gemm(omm_batch* b, const Grouped& g, const tc::PairList& pl) {
   b->prof.begin(b->st);
-  tc::gemm_persistent(b->st, g.dev, g.ngroups, g.tiles, pl, b->err, g.bn, g.pair);
+  tc::gemm_persistent(b->st, g.dev, g.ngroups, g.tiles, pl, b->err, g.bn, g.pair, g.quad);
   b->prof.end(b->st, 0.0);
 }
 
@@ -344,11 +347,11 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       const tc::TileShape ts =
           tc::choose_tile_shape(b->st, *specs[k], k == 0 ? tc::pairs_single() : tc::pairs_split3(), &ms_tune);
       b->ms_autotune += ms_tune;
-      b->tile_width[k] = ts.bn + (ts.pair ? 1000 : 0);
+      b->tile_width[k] = ts.code();
       for (size_t i = 0; i < specs[k]->size(); ++i) {
         const tc::GemmSpec& sp = (*specs[k])[i];
-        const tc::BlockLists* bl = sp.sparse[tc::sparse_slot(ts.bn)];
-        groups[k]->push_back(tc::make_group(*sp.A, *sp.B, sp.K, sp.ep, 0, ts.bn, bl, ts.pair));
+        const tc::BlockLists* bl = ts.quad ? nullptr : sp.sparse[tc::sparse_slot(ts.bn)];
+        groups[k]->push_back(tc::make_group(*sp.A, *sp.B, sp.K, sp.ep, 0, ts.bn, bl, ts.pair, ts.quad));
         if (bl && k == 1) b->gemm_flop[1][i] *= tc::block_density(bl);  // issued flops of the visited blocks
       }
       if (k == 0)  // partial sums each instance's P G epilogue leaves for its direction step
@@ -358,7 +361,7 @@ omm_status omm_create_batched(int count, const int* m, const int* n, const doubl
       int t = 0;
       for (tc::GroupDesc& g : *groups[k]) {
         g.tile_begin = t;
-        t += tc::tiles_of(g.ep, g.bn, g.pair != 0);
+        t += tc::tiles_of(g.ep, g.bn, g.pair != 0, g.quad != 0);
       }
     }
     for (cudaStream_t& q : b->pool) OMM_CUDA_TRY(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));

@@ -191,11 +191,11 @@ namespace {
 // K x N and read MN-major; pair: 256-row tiles on pairs of SMs
 omm_status gemm_tc_impl(const char* name, int M, int N, int K, const double* A, const double* B, double alpha,
                         double beta, double* C, int npass, int tile_n, bool block_sparse, bool b_kn, bool pair,
-                        void* stream) {
+                        void* stream, bool quad = false) {
   const bool width_ok = pair ? (tile_n == 128 || tile_n == 256 || (tile_n == 192 && !b_kn))
                              : (tile_n == 128 || tile_n == 256);
   if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || (npass != 1 && npass != 3) || !width_ok ||
-      (b_kn && (npass != 3 || block_sparse))) {
+      (b_kn && (npass != 3 || block_sparse)) || (quad && block_sparse)) {
     set_last_error(std::string(name) + ": invalid argument");
     return OMM_ERR_ARG;
   }
@@ -231,10 +231,10 @@ omm_status gemm_tc_impl(const char* name, int M, int N, int K, const double* A, 
     }
     if (block_sparse) tc::block_lists(st, B, N, K, K, tile_n, lists);
     const tc::Epilogue ep{C, N, N, 0, alpha, beta, M, N, nullptr, err};
-    const tc::GroupDesc g = tc::make_group(oa, ob, K, ep, 0, tile_n, block_sparse ? &lists : nullptr, pair);
+    const tc::GroupDesc g = tc::make_group(oa, ob, K, ep, 0, tile_n, block_sparse ? &lists : nullptr, pair, quad);
     OMM_CUDA_TRY(cudaMemcpyAsync(desc, &g, sizeof(g), cudaMemcpyHostToDevice, st));
-    tc::gemm_persistent(st, desc, 1, tc::tiles_of(ep, tile_n, pair),
-                        npass == 3 ? tc::pairs_split3() : tc::pairs_single(), err, tile_n, pair);
+    tc::gemm_persistent(st, desc, 1, tc::tiles_of(ep, tile_n, pair, quad),
+                        npass == 3 ? tc::pairs_split3() : tc::pairs_single(), err, tile_n, pair, quad);
     int h = 0;
     OMM_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -262,9 +262,14 @@ omm_status omm_kernel_gemm_tc_kn(int M, int N, int K, const double* A, const dou
 }
 
 omm_status omm_kernel_gemm_tc_pair(int M, int N, int K, const double* A, const double* B, double alpha, double beta,
-                                   double* C, int npass, int tile_n, int b_kn, int block_sparse, void* stream) {
+                                   double* C, int npass, int tile_n, int b_kn, int block_sparse, int cluster_pairs,
+                                   void* stream) {
+  if (cluster_pairs != 1 && cluster_pairs != 2) {
+    set_last_error("omm_kernel_gemm_tc_pair: invalid argument");
+    return OMM_ERR_ARG;
+  }
   return gemm_tc_impl("omm_kernel_gemm_tc_pair", M, N, K, A, B, alpha, beta, C, npass, tile_n, block_sparse != 0,
-                      b_kn != 0, true, stream);
+                      b_kn != 0, true, stream, cluster_pairs == 2);
 }
 
 omm_status omm_kernel_gemm_tc_tiled(int M, int N, int K, const double* A, const double* B, double alpha,

@@ -59,8 +59,8 @@ namespace {
 
 long round8(long x) { return (x + 7) / 8 * 8; }
 // output tiles of the P G product (n x m) counted as 128 x 128 tiles, rounded so that 256-row tiles
-// (two slots of four warps each) fit too
-long red_tiles(long n, long m) { return 2 * ((n + 255) / 256) * ((m + 127) / 128); }
+// (two slots of four warps each) and the odd column tile of a two-pair cluster fit too
+long red_tiles(long n, long m) { return 2 * ((n + 255) / 256) * ((m + 127) / 128 + 1); }
 
 template <typename T>
 void alloc(T** p, size_t count, cudaStream_t st) {
@@ -128,8 +128,8 @@ MixedState* mixed_create(cudaStream_t st, int m, int n, const double* HS, const 
 }
 
 void mixed_tuning(const MixedState* ms, int bn[4], double* ms_autotune) {
-  // the width of a 256-row (SM pair) tile is reported as 1000 + width
-  for (int k = 0; k < 4; ++k) bn[k] = ms->plans ? ms->plan_shape[k].bn + (ms->plan_shape[k].pair ? 1000 : 0) : 0;
+  // the width of a 256-row (SM pair) tile is reported as 1000 + width, of a two-pair cluster's 2000 + width
+  for (int k = 0; k < 4; ++k) bn[k] = ms->plans ? ms->plan_shape[k].code() : 0;
   if (!ms->precond) bn[0] = 0;
   *ms_autotune = ms->ms_autotune;
 }
@@ -327,8 +327,9 @@ void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double
     const tc::TileShape ts = tc::choose_tile_shape(st, {spec}, plan_pairs(k), &ms_tune);
     ms->plan_shape[k] = ts;
     ms->ms_autotune += ms_tune;
-    h[k] = tc::make_group(*opA[k], *opB[k], K[k], ep[k], 0, ts.bn, spec.sparse[tc::sparse_slot(ts.bn)], ts.pair);
-    ms->plan_tiles[k] = tc::tiles_of(ep[k], ts.bn, ts.pair);
+    h[k] = tc::make_group(*opA[k], *opB[k], K[k], ep[k], 0, ts.bn, ts.quad ? nullptr : spec.sparse[tc::sparse_slot(ts.bn)],
+                          ts.pair, ts.quad);
+    ms->plan_tiles[k] = tc::tiles_of(ep[k], ts.bn, ts.pair, ts.quad);
   }
   if (!ms->plans) alloc(&ms->plans, 4, st);
   OMM_CUDA_TRY(cudaMemcpyAsync(ms->plans, h, sizeof(h), cudaMemcpyHostToDevice, st));
@@ -338,14 +339,15 @@ void build_plans(MixedState* ms, cudaStream_t st, Scalars* sc, double* G, double
 
 void run_plan(MixedState* ms, cudaStream_t st, int k) {
   tc::gemm_persistent(st, ms->plans + k, 1, ms->plan_tiles[k], plan_pairs(k), ms->err, ms->plan_shape[k].bn,
-                      ms->plan_shape[k].pair);
+                      ms->plan_shape[k].pair, ms->plan_shape[k].quad);
 }
 
 }  // namespace
 
 int mixed_reduce_parts(const MixedState* ms) {
   // one slot of partial sums per epilogue warp of every P G output tile (eight on an SM pair's tile)
-  return 4 * ms->plan_tiles[kPlanPG] * (ms->plan_shape[kPlanPG].pair ? 2 : 1);
+  const tc::TileShape& ts = ms->plan_shape[kPlanPG];
+  return 4 * ms->plan_tiles[kPlanPG] * (ts.quad ? 4 : (ts.pair ? 2 : 1));
 }
 
 void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, double* Dir, double* G,

@@ -927,11 +927,22 @@ __device__ __forceinline__ void umma_bf16_pair(uint32_t tmem_d, uint64_t a, uint
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
-// arrive at the barrier at this shared offset in both CTAs once the MMAs issued so far are complete
-__device__ __forceinline__ void umma_commit_pair(uint32_t bar) {
+// the same load delivered to every CTA of ctaMask (the same shared offset in each); the bytes count
+// at the barrier at bar's offset in the even CTA of each destination's pair
+__device__ __forceinline__ void tma_load_2d_pair_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar_cluster,
+                                                    int c0, int c1, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(c0), "r"(c1), "h"(mask)
+      : "memory");
+}
+// arrive at the barrier at this shared offset in every CTA of mask once the MMAs issued so far
+// are complete
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar, uint16_t mask) {
   asm volatile(
       "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-      "h"((uint16_t)3)
+      "h"(mask)
       : "memory");
 }
 // the same, at this CTA's barrier only
@@ -946,7 +957,13 @@ constexpr uint64_t PAIR_ABORT_SETTLE_NS = 200000ull;
 // (stages hold one slice of A and one of B), chunk by chunk: every chunk of a tile is one
 // accumulator round whose FP32 sum the epilogue adds to C in chunk order (the first with the
 // Epilogue's beta, the later ones with beta = 1), as in the single-SM kernel.
-template <int TBN, bool SPLIT>
+// NP = 2: a cluster of two pairs side by side along N (a work unit is 256 x 2 TBN) that share A:
+// CTA r of pair p loads rows [64 p, 64 p + 64) of the 128 A rows its CTA position needs and
+// multicasts them to CTA r of both pairs, so every A byte leaves L2 once per two column tiles.
+// A stage of a CTA is then written by both pairs, so it is free only when both pairs' MMAs have
+// read it: the empty barriers count the commits of both pair leaders. Dense B only (both pairs
+// walk the same K blocks).
+template <int TBN, bool SPLIT, int NP>
 __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, int ngroups, int total_units,
                                           const PairList& pl, int* err) {
   constexpr int TBH = TBN / 2;  // B rows (or MN-major output columns) staged by each CTA
@@ -966,9 +983,15 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  static_assert(NP == 1 || NP == 2, "pairs per cluster");
   const uint32_t rank = cluster_ctarank();
-  const bool leader = rank == 0;
-  const int cluster = (int)(blockIdx.x >> 1), nclusters = (int)(gridDim.x >> 1);
+  const int pp = (int)(rank >> 1), rr = (int)(rank & 1);  // pair within the cluster, CTA within the pair
+  const uint32_t lead_rank = rank & ~1u;
+  const bool leader = rr == 0;
+  const int cluster = (int)(blockIdx.x / (2 * NP)), nclusters = (int)(gridDim.x / (2 * NP));
+  const uint16_t mask_all = (uint16_t)((1u << (2 * NP)) - 1u);      // every CTA of the cluster
+  const uint16_t mask_pair = (uint16_t)(3u << (2 * pp));            // the CTAs of this pair
+  const uint16_t mask_a = (uint16_t)((1u << rr) | (1u << (2 + rr)));  // CTA rr of both pairs (NP = 2)
   const int nchunk = (SPLIT || pl.nchunk <= 0) ? 1 : pl.nchunk;
   auto chunk_begin = [&](int c) { return (c == 0 || pl.nchunk <= 0) ? 0 : (int)pl.chunk_end[c - 1]; };
   auto chunk_end = [&](int c) { return pl.nchunk <= 0 ? pl.n : (int)pl.chunk_end[c]; };
@@ -976,7 +999,7 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
   if (threadIdx.x == 0) {
     for (int q = 0; q < NS; ++q) {
       mbar_init(smem_u32(&bars[q]), 1);
-      mbar_init(smem_u32(&bars[NS + q]), 1);
+      mbar_init(smem_u32(&bars[NS + q]), NP);  // one commit per pair that reads this CTA's stage
     }
     for (int q = 0; q < 2; ++q) {
       mbar_init(smem_u32(&bars[2 * NS + q]), 1);      // the even CTA's multicast commit
@@ -1016,8 +1039,8 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
       const CUtensorMap* mA = reinterpret_cast<const CUtensorMap*>(&g->a);
       const CUtensorMap* mB = reinterpret_cast<const CUtensorMap*>(&g->b);
       const int local = u - g->tile_begin, tiles_m = (g->ep.M + 2 * BM - 1) / (2 * BM);
-      const int m0 = (local % tiles_m) * 2 * BM + (int)rank * BM;  // this CTA's rows of A
-      const int n0 = (local / tiles_m) * TBN + (int)rank * TBH;     // this CTA's half of B
+      const int m0 = (local % tiles_m) * 2 * BM + rr * BM;                  // this CTA's rows of A
+      const int n0 = ((local / tiles_m) * NP + pp) * TBN + rr * TBH;        // this CTA's half of B
       const KBlocks kbs = tile_kblocks(g, local, tiles_m);
       const int nkb = kbs.count;
       const int total = SPLIT ? nkb : pl.n * nkb;  // every pair of every chunk of the tile
@@ -1029,13 +1052,20 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
           atomicCAS(err, 0, 1);
           break;
         }
-        const uint32_t full = mapa_shared(smem_u32(&bars[q]), 0);
-        if (leader) mbar_expect_tx(smem_u32(&bars[q]), 2 * SB);  // the bytes of both CTAs
+        const uint32_t full = mapa_shared(smem_u32(&bars[q]), lead_rank);
+        if (leader) mbar_expect_tx(smem_u32(&bars[q]), 2 * SB);  // the bytes landing in both CTAs
         const uint32_t sa = smem_u32(smem + q * SB);
         const int p = SPLIT ? 0 : t / nkb, kb = kbs.at(SPLIT ? t : t % nkb);
         const int ra = SPLIT ? 0 : (int)pl.a[p] * g->rowsA, rb = SPLIT ? 0 : (int)pl.b[p] * g->rowsB;
-        tma_load_2d_pair(sa, mA, full, kb * BK, ra + g->offA + m0);
-        if (SPLIT) tma_load_2d_pair(sa + A_BYTES, mA, full, kb * BK, g->rowsA + g->offA + m0);
+        if (NP == 1) {
+          tma_load_2d_pair(sa, mA, full, kb * BK, ra + g->offA + m0);
+          if (SPLIT) tma_load_2d_pair(sa + A_BYTES, mA, full, kb * BK, g->rowsA + g->offA + m0);
+        } else {  // this pair's 64-row half of the A tile, to CTA rr of both pairs (64-row boxes)
+          const uint32_t ah = (uint32_t)pp * (A_BYTES / 2);
+          tma_load_2d_pair_mc(sa + ah, mA, full, kb * BK, ra + g->offA + m0 + 64 * pp, mask_a);
+          if (SPLIT)
+            tma_load_2d_pair_mc(sa + A_BYTES + ah, mA, full, kb * BK, g->rowsA + g->offA + m0 + 64 * pp, mask_a);
+        }
         if (g->b_mn) {
 #pragma unroll
           for (int h = 0; h < TBH / 64; ++h) {
@@ -1054,7 +1084,8 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
       if (leader) {  // the copies of the stages issued last (both CTAs' bytes count here)
         for (uint32_t j = it > (uint32_t)NS ? it - NS : 0u; j < it; ++j)
           mbar_wait(smem_u32(&bars[j % NS]), (j / NS) & 1);
-      } else {  // the odd CTA's copies complete at the even CTA's barriers: give them time to land
+      }
+      if (!leader || NP > 1) {  // copies that complete at another CTA's barrier: give them time to land
         const uint64_t t0 = globaltimer();
         while (globaltimer() - t0 < PAIR_ABORT_SETTLE_NS) {
         }
@@ -1068,7 +1099,7 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
       const GroupDesc* g = groups + find_group(groups, ngroups, u);
       const int* skip = g->ep.skip;
       if (skip != nullptr && (skip[0] | skip[1])) continue;
-      const int nkb = tile_kblocks(g, u - g->tile_begin, (g->ep.M + 2 * BM - 1) / (2 * BM)).count;
+      const int nkb = tile_kblocks(g, u - g->tile_begin, (g->ep.M + 2 * BM - 1) / (2 * BM)).count;  // NP > 1: dense
       const bool bmn = g->b_mn != 0;
       const uint32_t idesc = idesc_k | (bmn ? kIdescBMN : 0u);
       auto bdesc = [bmn](uint32_t addr, int k) {
@@ -1103,9 +1134,9 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
               umma_bf16_pair(d, smem_desc(alo + k * 32), bdesc(bhi, k), idesc, 1u);
             }
           }
-          umma_commit_pair(smem_u32(&bars[NS + q]));  // stage q of both CTAs is free
+          umma_commit_pair(smem_u32(&bars[NS + q]), mask_all);  // this pair is done with stage q
         }
-        umma_commit_pair(smem_u32(&bars[2 * NS + buf]));  // both halves of the accumulator are complete
+        umma_commit_pair(smem_u32(&bars[2 * NS + buf]), mask_pair);  // both halves of the accumulator are complete
         ++lt;
       }
     }
@@ -1116,8 +1147,8 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
   } else if (warp >= 2) {
     // ---------------- epilogue (both CTAs: 128 rows each)
     const int lane_base = (warp & 3) * 32;
-    const uint32_t acc_empty0 = mapa_shared(smem_u32(&bars[2 * NS + 2]), 0);
-    const uint32_t acc_empty1 = mapa_shared(smem_u32(&bars[2 * NS + 3]), 0);
+    const uint32_t acc_empty0 = mapa_shared(smem_u32(&bars[2 * NS + 2]), lead_rank);
+    const uint32_t acc_empty1 = mapa_shared(smem_u32(&bars[2 * NS + 3]), lead_rank);
     uint32_t lt = 0;
     for (int u = cluster; u < total_units; u += nclusters) {
       const GroupDesc* g = groups + find_group(groups, ngroups, u);
@@ -1136,7 +1167,7 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
         Epilogue ep = g->ep;
         if (c > 0) ep.beta = 1.0;
         const int local = u - g->tile_begin, tiles_m = (ep.M + 2 * BM - 1) / (2 * BM);
-        const int m0 = (local % tiles_m) * 2 * BM + (int)rank * BM, n0 = (local / tiles_m) * TBN;
+        const int m0 = (local % tiles_m) * 2 * BM + rr * BM, n0 = ((local / tiles_m) * NP + pp) * TBN;
         const int row = m0 + lane_base + lane;
         EpiRed red;
         red.have_dir = ep.mode == kEpReduce && ep.sc != nullptr && ep.sc->have_dir;
@@ -1146,7 +1177,7 @@ __device__ __forceinline__ void pair_body(const GroupDesc* __restrict__ groups, 
           tmem_ld32(tmem + buf * ACC_STRIDE + ((uint32_t)lane_base << 16) + (uint32_t)(j * 32), v);
           store_chunk(ep, row, n0 + j * 32, v, red);
         }
-        flush_reduce(ep, local * 2 + (int)rank, warp & 3, red);  // slots of 128-row halves
+        flush_reduce(ep, (local * NP + pp) * 2 + rr, warp & 3, red);  // slots of 128 x TBN quarters
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive_cluster(buf ? acc_empty1 : acc_empty0);
@@ -1171,7 +1202,15 @@ template <int TBN, bool SPLIT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
 gemm_pair_kernel(const GroupDesc* __restrict__ groups, int ngroups, int total_units,
                  const __grid_constant__ PairList pl, int* err) {
-  pair_body<TBN, SPLIT>(groups, ngroups, total_units, pl, err);
+  pair_body<TBN, SPLIT, 1>(groups, ngroups, total_units, pl, err);
+}
+
+// two SM pairs per cluster, sharing A (NP = 2)
+template <int TBN, bool SPLIT>
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(NTHREADS, 1)
+gemm_quad_kernel(const GroupDesc* __restrict__ groups, int ngroups, int total_units,
+                 const __grid_constant__ PairList pl, int* err) {
+  pair_body<TBN, SPLIT, 2>(groups, ngroups, total_units, pl, err);
 }
 
 // one GEMM, its descriptor (tensor maps included) in the kernel's parameter space
@@ -1179,7 +1218,7 @@ template <int TBN, bool SPLIT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
 gemm_pair_one_kernel(const __grid_constant__ GroupDesc g, int total_units, const __grid_constant__ PairList pl,
                      int* err) {
-  pair_body<TBN, SPLIT>(&g, 1, total_units, pl, err);
+  pair_body<TBN, SPLIT, 1>(&g, 1, total_units, pl, err);
 }
 
 template <bool FUSED, int TBN>
@@ -1225,27 +1264,33 @@ int sm_count() {
   return n;
 }
 
-// clusters of two GEMM CTAs (one per SM) that the device holds at once
+// clusters of `size` GEMM CTAs (one per SM) that the device holds at once
+template <typename Kernel>
+int max_clusters(Kernel kernel, int size) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(size * sm_count()));
+  cfg.blockDim = dim3(NTHREADS);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = (unsigned)size;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int c = 0;
+  if (cudaOccupancyMaxActiveClusters(&c, kernel, &cfg) != cudaSuccess || c <= 0) {
+    cudaGetLastError();
+    c = sm_count() / size;
+  }
+  return c;
+}
 int pair_clusters() {
-  static const int n = [] {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * (unsigned)sm_count());
-    cfg.blockDim = dim3(NTHREADS);
-    cfg.dynamicSmemBytes = SMEM_BYTES;
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = 2;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    int c = 0;
-    if (cudaOccupancyMaxActiveClusters(&c, gemm_pair_kernel<256, true>, &cfg) != cudaSuccess || c <= 0) {
-      cudaGetLastError();
-      c = sm_count() / 2;
-    }
-    return c;
-  }();
+  static const int n = max_clusters(gemm_pair_kernel<256, true>, 2);
+  return n;
+}
+int quad_clusters() {
+  static const int n = max_clusters(gemm_quad_kernel<256, true>, 4);
   return n;
 }
 
@@ -1376,13 +1421,17 @@ void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, const Pair
   OMM_LAUNCH_CHECK();
 }
 
-int tiles_of(const Epilogue& ep, int bn, bool pair) {
-  const int bm = pair ? 2 * BM : BM;
-  return ((ep.M + bm - 1) / bm) * ((ep.N + bn - 1) / bn);
+int tiles_of(const Epilogue& ep, int bn, bool pair, bool quad) {
+  const int bm = (pair || quad) ? 2 * BM : BM;
+  const int tn = (ep.N + bn - 1) / bn;
+  return ((ep.M + bm - 1) / bm) * (quad ? (tn + 1) / 2 : tn);
 }
 
 GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin, int bn,
-                     const BlockLists* sparse, bool pair) {
+                     const BlockLists* sparse, bool pair, bool quad) {
+  if (quad) pair = true;
+  if (quad && sparse != nullptr)
+    throw CudaError{cudaErrorInvalidValue, "tc::make_group: clusters of two pairs need a dense B"};
   if (pair ? (bn != 256 && bn != 192 && bn != 128) : (bn != 256 && bn != 128))
     throw CudaError{cudaErrorInvalidValue, "tc::make_group: tile width"};
   // the TMA boxes must match the tile: A in 128-row boxes, B in boxes of the tile width (of half of
@@ -1393,7 +1442,8 @@ GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& 
   if (B.mn_major && (sparse != nullptr || K > B.rows))
     throw CudaError{cudaErrorInvalidValue, "tc::make_group: MN-major B: no block lists, K <= its rows"};
   GroupDesc g{};
-  g.a = A.map;
+  g.a = quad ? make_map(A.base, A.map_rows, A.cols, A.ld, BM / 2) : A.map;  // quad: 64-row halves
+  g.quad = quad ? 1 : 0;
   if (B.mn_major)
     g.b = B.map;
   else if (pair)
@@ -1435,20 +1485,37 @@ void prepare_persistent() {
     for (const void* f : {(const void*)gemm_pair_kernel<128, true>, (const void*)gemm_pair_kernel<192, true>,
                           (const void*)gemm_pair_kernel<256, true>, (const void*)gemm_pair_kernel<128, false>,
                           (const void*)gemm_pair_kernel<192, false>, (const void*)gemm_pair_kernel<256, false>,
-                          (const void*)gemm_pair_one_kernel<256, true>, (const void*)gemm_pair_one_kernel<256, false>})
+                          (const void*)gemm_pair_one_kernel<256, true>, (const void*)gemm_pair_one_kernel<256, false>,
+                          (const void*)gemm_quad_kernel<128, true>, (const void*)gemm_quad_kernel<192, true>,
+                          (const void*)gemm_quad_kernel<256, true>, (const void*)gemm_quad_kernel<128, false>,
+                          (const void*)gemm_quad_kernel<192, false>, (const void*)gemm_quad_kernel<256, false>})
       OMM_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     sm_count();
     pair_clusters();
+    quad_clusters();
     attr_set = true;
   }
 }
 
 void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl,
-                     int* err, int bn, bool pair) {
+                     int* err, int bn, bool pair, bool quad) {
   prepare_persistent();
   check_pairs(pl, kMaxPairs, kMaxPairs);  // slice counts are checked where the groups are made
   if (ngroups <= 0 || total_tiles <= 0) return;
   const bool fused = is_split3(pl);
+  if (quad) {
+    if (bn != 256 && bn != 192 && bn != 128)
+      throw CudaError{cudaErrorInvalidValue, "tc::gemm_persistent: SM-pair tiles are 128, 192 or 256 wide"};
+    const unsigned grid = 4u * (unsigned)std::min(total_tiles, quad_clusters());
+    auto go = [&](auto kernel) {
+      kernel<<<grid, NTHREADS, SMEM_BYTES, st>>>(groups_dev, ngroups, total_tiles, pl, err);
+    };
+    if (bn == 256) fused ? go(gemm_quad_kernel<256, true>) : go(gemm_quad_kernel<256, false>);
+    else if (bn == 192) fused ? go(gemm_quad_kernel<192, true>) : go(gemm_quad_kernel<192, false>);
+    else fused ? go(gemm_quad_kernel<128, true>) : go(gemm_quad_kernel<128, false>);
+    OMM_LAUNCH_CHECK();
+    return;
+  }
   if (pair) {
     if (bn != 256 && bn != 192 && bn != 128)
       throw CudaError{cudaErrorInvalidValue, "tc::gemm_persistent: SM-pair tiles are 128, 192 or 256 wide"};
@@ -1614,15 +1681,21 @@ TileShape choose_tile_shape(cudaStream_t st, const std::vector<GemmSpec>& specs,
   // tiles need K-major B (an SM stages 96 rows) and, for a block-sparse B, lists for that width
   std::vector<TileShape> cands = {{256, false}, {128, false}};
   const bool split = is_split3(pl);
-  bool pair_ok = allow_pair && (split || is_single(pl)), w192 = true;
+  bool pair_ok = allow_pair && (split || is_single(pl)), w192 = true, dense = true;
   for (const GemmSpec& g : specs) {
     if (g.ep.M < 2 * BM || (split && (g.A->slices < 2 || g.B->slices < 2))) pair_ok = false;
     if (g.B->mn_major || (g.sparse[0] != nullptr && g.sparse[2] == nullptr)) w192 = false;
+    if (g.sparse[0] != nullptr) dense = false;
   }
   if (pair_ok) {
     cands.push_back({256, true});
     cands.push_back({128, true});
     if (w192) cands.push_back({192, true});
+    if (dense) {  // pairs sharing A walk the same K blocks
+      cands.push_back({256, true, true});
+      cands.push_back({128, true, true});
+      if (w192) cands.push_back({192, true, true});
+    }
   }
   std::string key = std::to_string(pl.n) + (is_split3(pl) ? "s" : "g") + (pair_ok ? "p" : "");
   long out_elems = 0;
@@ -1666,15 +1739,16 @@ TileShape choose_tile_shape(cudaStream_t st, const std::vector<GemmSpec>& specs,
       int tiles = 0;
       for (const GemmSpec& g : specs) {
         Epilogue ep{scratch + off, g.ep.N, g.ep.N, 0, 1.0, 0.0, g.ep.M, g.ep.N, nullptr, err};
-        h.push_back(make_group(*g.A, *g.B, g.K, ep, tiles, ts.bn, g.sparse[sparse_slot(ts.bn)], ts.pair));
-        tiles += tiles_of(ep, ts.bn, ts.pair);
+        h.push_back(make_group(*g.A, *g.B, g.K, ep, tiles, ts.bn, ts.quad ? nullptr : g.sparse[sparse_slot(ts.bn)],
+                               ts.pair, ts.quad));
+        tiles += tiles_of(ep, ts.bn, ts.pair, ts.quad);
         off += (long)g.ep.M * g.ep.N;
       }
       OMM_CUDA_TRY(cudaMemcpyAsync(dev, h.data(), h.size() * sizeof(GroupDesc), cudaMemcpyHostToDevice, st));
-      gemm_persistent(st, dev, (int)h.size(), tiles, pl, err, ts.bn, ts.pair);  // warm-up
+      gemm_persistent(st, dev, (int)h.size(), tiles, pl, err, ts.bn, ts.pair, ts.quad);  // warm-up
       constexpr int kReps = 3;
       OMM_CUDA_TRY(cudaEventRecord(e0, st));
-      for (int r = 0; r < kReps; ++r) gemm_persistent(st, dev, (int)h.size(), tiles, pl, err, ts.bn, ts.pair);
+      for (int r = 0; r < kReps; ++r) gemm_persistent(st, dev, (int)h.size(), tiles, pl, err, ts.bn, ts.pair, ts.quad);
       OMM_CUDA_TRY(cudaEventRecord(e1, st));
       OMM_CUDA_TRY(cudaEventSynchronize(e1));  // h stays alive until the copy has been consumed
       float ms = 0.f;

@@ -121,14 +121,18 @@ inline void gemm(cudaStream_t st, const Operand& A, const Operand& B, int K, int
 // Output tiles of a persistent launch: 128 x bn on one SM (bn = 128 or 256), or, with pair,
 // 256 x bn on a cluster of two SMs that share the MMA (tcgen05 cta_group::2; bn = 128, 192 or 256;
 // the split form or a single pass).
+// With quad (pair set too), a cluster of two SM pairs side by side along N shares the A operand
+// through TMA multicast: a work unit is 256 x 2 bn (dense B only).
 struct TileShape {
   int bn = 256;
   bool pair = false;
+  bool quad = false;
+  int code() const { return bn + (quad ? 2000 : (pair ? 1000 : 0)); }  // as reported in omm_info
 };
-int tiles_of(const Epilogue& ep, int bn = 256, bool pair = false);  // work units of one GEMM
-// the partial-sum slots (one per epilogue warp and 128-row tile half) a kEpReduce GEMM writes
+int tiles_of(const Epilogue& ep, int bn = 256, bool pair = false, bool quad = false);  // work units of one GEMM
+// the partial-sum slots (one per epilogue warp and 128 x bn quarter) a kEpReduce GEMM writes
 inline int reduce_slots(const Epilogue& ep, const TileShape& ts) {
-  return 4 * tiles_of(ep, ts.bn, ts.pair) * (ts.pair ? 2 : 1);
+  return 4 * tiles_of(ep, ts.bn, ts.pair, ts.quad) * (ts.quad ? 4 : (ts.pair ? 2 : 1));
 }
 
 // One GEMM of a grouped launch (device array element; tensor maps in global memory).
@@ -162,19 +166,20 @@ struct alignas(64) GroupDesc {
   int K, rowsA, rowsB, tile_begin;  // rowsA, rowsB: rows between the slices of A and B
   int offA, offB;                   // first row of A and B inside each slice
   int b_mn;                         // B is MN-major (its rows are the contracted index)
-  int bn;    // output tile width (all groups of one launch share it and pair)
+  int bn;    // output tile width (all groups of one launch share it, pair and quad)
   int pair;  // 256-row tiles on a cluster of two SMs
+  int quad;  // two such pairs per cluster, sharing A
   const int* kb_off;  // block sparsity of B for row blocks of bn (null: dense)
   const int* kb_idx;
 };
 GroupDesc make_group(const Operand& A, const Operand& B, int K, const Epilogue& ep, int tile_begin, int bn = 256,
-                     const BlockLists* sparse = nullptr, bool pair = false);
+                     const BlockLists* sparse = nullptr, bool pair = false, bool quad = false);
 // groups_dev: ngroups descriptors in device memory, sorted by tile_begin; all share the pair list
 void prepare_persistent();  // kernel attributes (call before a stream capture)
 // persistent grouped launch: one CTA per SM, double-buffered TMEM accumulators; err receives a
 // nonzero code if a bounded wait expired
 void gemm_persistent(cudaStream_t st, const GroupDesc* groups_dev, int ngroups, int total_tiles, const PairList& pl,
-                     int* err, int bn = 256, bool pair = false);
+                     int* err, int bn = 256, bool pair = false, bool quad = false);
 // the same persistent kernel for one GEMM whose descriptor travels as a kernel parameter.
 // partial (optional, partial_capacity doubles): scratch that lets a GEMM of few output tiles run
 // each chunk of its pair list on its own CTA and add the chunks afterwards, in chunk order.
@@ -185,7 +190,7 @@ void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K,
 // Tile-shape autotuner: times one persistent launch over these GEMMs (the operands as given,
 // the outputs redirected to scratch) with each candidate shape -- 128 x 256 and 128 x 128 on one
 // SM, and (split form or single pass, allow_pair, every M >= 256) 256 x 128, 256 x 192 and
-// 256 x 256 on SM pairs
+// 256 x 256 on SM pairs, and (dense B) the same on clusters of two pairs sharing A
 // -- returns the fastest, and remembers it per shape signature for the life of the process.
 // ms_spent receives the time spent timing (0 when the answer came from the cache).
 struct GemmSpec {

@@ -197,16 +197,17 @@ def gemm_tc_kn(A, B, C, alpha=1.0, beta=0.0, tile_n=256, stream=None):
     return C
 
 
-def gemm_tc_pair(A, B, C, alpha=1.0, beta=0.0, tile_n=256, b_kn=False, block_sparse=False, npass=3, stream=None):
+def gemm_tc_pair(A, B, C, alpha=1.0, beta=0.0, tile_n=256, b_kn=False, block_sparse=False, npass=3, cluster_pairs=1,
+                 stream=None):
     """The tensor-core contraction on pairs of SMs (256-row tiles, tcgen05 cta_group::2): C = alpha A B^T
     + beta C (B N x K), or with b_kn C = alpha A B + beta C (B K x N, read MN-major); npass 3 (split
     form) or 1 (single bf16 pass); tile_n 128, 192 (K-major B only) or 256; block_sparse skips the K
-    blocks where B is zero."""
+    blocks where B is zero; cluster_pairs 2 runs two pairs per cluster that share A (dense B)."""
     M, K = A.shape
     Nn = B.shape[1] if b_kn else B.shape[0]
     N.check(N.lib().omm_kernel_gemm_tc_pair(M, Nn, K, _ptr(A), _ptr(B), float(alpha), float(beta), _ptr(C),
                                             int(npass), int(tile_n), int(bool(b_kn)), int(bool(block_sparse)),
-                                            _stream_handle(stream)), "omm_kernel_gemm_tc_pair")
+                                            int(cluster_pairs), _stream_handle(stream)), "omm_kernel_gemm_tc_pair")
     return C
 
 

@@ -28,14 +28,17 @@ def dev(a):
 SHAPES = [(256, 256, 64), (512, 384, 1000), (130, 257, 70), (1024, 1000, 333), (300, 700, 128), (1, 1, 1)]
 
 
+@pytest.mark.parametrize("cp", [1, 2])
 @pytest.mark.parametrize("tile_n", [128, 192, 256])
 @pytest.mark.parametrize("M,N,K", SHAPES)
-def test_pair_split_product(S, M, N, K, tile_n):
+def test_pair_split_product(S, M, N, K, tile_n, cp):
+    """cp = 2: two pairs per cluster sharing A by multicast (an odd number of column tiles leaves the
+    second pair of the last cluster without columns)."""
     rng = np.random.default_rng(11 * M + N + K + tile_n)
     A = rng.normal(size=(M, K)); B = rng.normal(size=(N, K))
     C0 = rng.normal(size=(M, N))
     C = dev(C0)
-    S.gemm_tc_pair(dev(A), dev(B), C, alpha=2.0, beta=-1.0, tile_n=tile_n)
+    S.gemm_tc_pair(dev(A), dev(B), C, alpha=2.0, beta=-1.0, tile_n=tile_n, cluster_pairs=cp)
     got = C.cpu().numpy()
     ref = 2.0 * A @ B.T - C0
     scale = 2.0 * np.abs(A) @ np.abs(B).T
@@ -52,15 +55,16 @@ def bf16_round(x):
     return np.ldexp(np.rint(m * 256.0) / 256.0, e)
 
 
+@pytest.mark.parametrize("cp", [1, 2])
 @pytest.mark.parametrize("tile_n", [128, 192, 256])
 @pytest.mark.parametrize("M,N,K", [(256, 256, 64), (130, 257, 70), (1024, 1664, 1000), (1, 1, 1)])
-def test_pair_single_pass_is_exact_bf16_product(S, M, N, K, tile_n):
+def test_pair_single_pass_is_exact_bf16_product(S, M, N, K, tile_n, cp):
     """npass = 1 (the search direction's P G): the product of the bf16-rounded operands up to FP32
     accumulation (K 2^-23), and the single-SM kernel's value."""
     rng = np.random.default_rng(M + 5 * N + K + tile_n)
     A = rng.normal(size=(M, K)); B = rng.normal(size=(N, K))
     C = dev(np.zeros((M, N)))
-    S.gemm_tc_pair(dev(A), dev(B), C, npass=1, tile_n=tile_n)
+    S.gemm_tc_pair(dev(A), dev(B), C, npass=1, tile_n=tile_n, cluster_pairs=cp)
     got = C.cpu().numpy()
     ref = bf16_round(A) @ bf16_round(B).T
     scale = np.abs(bf16_round(A)) @ np.abs(bf16_round(B)).T
@@ -70,15 +74,16 @@ def test_pair_single_pass_is_exact_bf16_product(S, M, N, K, tile_n):
     assert np.abs(got - C1.cpu().numpy()).max() <= 2.0 ** -20 * scale.max()
 
 
+@pytest.mark.parametrize("cp", [1, 2])
 @pytest.mark.parametrize("tile_n", [128, 256])
 @pytest.mark.parametrize("M,N,K", [(256, 256, 64), (1024, 640, 256), (200, 300, 72), (512, 6656 // 4, 4096 // 4)])
-def test_pair_mn_major_b(S, M, N, K, tile_n):
+def test_pair_mn_major_b(S, M, N, K, tile_n, cp):
     """B given K x N and read MN-major (the gradient product's layout)."""
     rng = np.random.default_rng(5 * M + N + K + tile_n)
     A = rng.normal(size=(M, K)); B = rng.normal(size=(K, N))
     C0 = rng.normal(size=(M, N))
     C = dev(C0)
-    S.gemm_tc_pair(dev(A), dev(B), C, alpha=-4.0, beta=1.0, tile_n=tile_n, b_kn=True)
+    S.gemm_tc_pair(dev(A), dev(B), C, alpha=-4.0, beta=1.0, tile_n=tile_n, b_kn=True, cluster_pairs=cp)
     got = C.cpu().numpy()
     ref = -4.0 * A @ B + C0
     scale = 4.0 * np.abs(A) @ np.abs(B)
@@ -113,7 +118,8 @@ def test_pair_rejects_bad_arguments(S):
     from paper_1312_1549_gb300 import _native as N
     A = dev(np.ones((256, 64))); B = dev(np.ones((64, 64))); C = dev(np.zeros((256, 64)))
     for kw in ({"tile_n": 64}, {"tile_n": 192, "b_kn": True}, {"tile_n": 128, "b_kn": True, "block_sparse": True},
-               {"npass": 2}, {"npass": 1, "b_kn": True}):
+               {"npass": 2}, {"npass": 1, "b_kn": True}, {"cluster_pairs": 3},
+               {"cluster_pairs": 2, "block_sparse": True}):
         with pytest.raises(N.OMMError) as e:
             S.gemm_tc_pair(A, B, C, **kw)
         assert e.value.status == 1
