@@ -19,9 +19,10 @@
 //     Y21 = -(Y22 L21) Y11                         (Y = L^-1)
 //   lauum(Y) = Y^T Y:  P22 = lauum(Y22);  P21 = Y22^T Y21;
 //     P11 = lauum(Y11) + Y21^T Y21
-// with 64 x 64 leaves factored and inverted in float64 by one CTA (which also writes the leaf's
-// block of Y^T Y). The P updates of a node run on a second stream as soon as its Y is final,
-// beside the factorisation of the blocks that follow.
+// with leaves factored and inverted by one CTA (which also writes the leaf's block of Y^T Y):
+// 64 x 64 in float64 for float64-class results, 128 x 128 in float32 for the preconditioner. The
+// P updates of a node run on a second stream as soon as its Y is final, beside the factorisation
+// of the blocks that follow.
 #include "emu.cuh"
 #include "omm_internal.cuh"
 #include "tc_gemm.cuh"
@@ -160,37 +161,72 @@ leaf_f32_kernel(const double* A, long lda, int b, double* Linv, int* info, int c
       X[i][j] = 0.f;
     }
   __syncthreads();
-  // Right-looking, one column per step and one barrier per step: step j reads the pivot and
-  // column j (final after step j - 1) and updates the trailing lower triangle with the column
-  // scaled on the fly, L_il -= (L_ij / sqrt(d)) (L_lj / sqrt(d)); column j itself is scaled in
-  // step j + 1, which neither reads nor writes it otherwise. Warp w takes rows j+1+w, j+1+w+16,
-  // ..., its lanes the columns of a row.
-  float s_prev = 1.f, r_prev = 1.f;  // sqrt(d) and 1 / sqrt(d) of the previous pivot
-  for (int j = 0; j <= b; ++j) {
-    if (j > 0) {  // finish column j - 1
-      const int c = j - 1;
-      if (tid == 0) {
-        L[c][c] = s_prev;
-        rdiag[c] = r_prev;
+  // Right-looking in panels of 16 columns. Warp 0 factors a panel with its rows in registers
+  // (lane l holds rows p0 + l + 32 t), pivots and column entries passed by shuffles, no block
+  // barrier; then all warps apply the panel's rank-16 update to the trailing lower triangle
+  // (warp w on rows q0 + w, q0 + w + 16, ..., lanes on columns), each element's 16 products
+  // from independent shared-memory loads. Two barriers per panel instead of one per column: a
+  // column at a time left every warp waiting on a chain of dependent shared-memory loads.
+  for (int p0 = 0; p0 < b; p0 += 16) {
+    const int pw = min(16, b - p0);
+    if (warp == 0) {
+      float r[4][16];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int i = p0 + lane + 32 * t;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) r[t][c] = (i < b && c < pw && p0 + c <= i) ? L[i][p0 + c] : 0.f;
       }
-      for (int i = c + 1 + tid; i < b; i += nt) L[i][c] *= r_prev;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        if (c < pw) {
+          float d = __shfl_sync(0xffffffffu, r[0][c], c);  // the pivot, row p0 + c
+          if (!(d > 0.f)) {
+            if (lane == 0) atomicCAS(info, 0, col_offset + p0 + c + 1);
+            d = 1.f;
+          }
+          const float sq = sqrtf(d), rs = 1.f / sq;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int i = p0 + lane + 32 * t;
+            if (i > p0 + c) r[t][c] *= rs;
+            else if (i == p0 + c) r[t][c] = sq;
+          }
+          if (lane == 0) rdiag[p0 + c] = rs;
+#pragma unroll
+          for (int l = 0; l < 16; ++l) {
+            if (l > c) {
+              const float lc = __shfl_sync(0xffffffffu, r[0][c], l);  // L[p0 + l][p0 + c], scaled
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                if (lane + 32 * t >= l) r[t][l] = fmaf(-r[t][c], lc, r[t][l]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int i = p0 + lane + 32 * t;
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (i < b && c < pw && p0 + c <= i) L[i][p0 + c] = r[t][c];
+      }
     }
-    if (j == b) break;
-    float d = L[j][j];
-    if (!(d > 0.f)) {
-      if (tid == 0) atomicCAS(info, 0, col_offset + j + 1);
-      d = 1.f;
+    __syncthreads();
+    const int q0 = p0 + pw;  // trailing block: rows and columns q0 .. b - 1 (empty after the last panel)
+    for (int i = q0 + warp; i < b; i += nwarps) {
+      float li[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) li[k] = L[i][p0 + k];
+      for (int l = q0 + lane; l <= i; l += 32) {
+        float acc = L[i][l];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc = fmaf(-li[k], L[l][p0 + k], acc);
+        L[i][l] = acc;
+      }
     }
-    const float sj = sqrtf(d), rj = 1.f / sj;
-    for (int i = j + 1 + warp; i < b; i += nwarps) {
-      const float ai = L[i][j] * rj;
-      for (int l = j + 1 + lane; l <= i; l += 32) L[i][l] = fmaf(-ai, L[l][j] * rj, L[i][l]);
-    }
-    s_prev = sj;
-    r_prev = rj;
     __syncthreads();
   }
-  __syncthreads();
   // 16 x 16 diagonal blocks: lane c of warp w solves column c of block w
   const int nb16 = (b + 15) / 16;
   if (warp < nb16 && lane < 16) {
@@ -212,9 +248,15 @@ leaf_f32_kernel(const double* A, long lda, int b, double* Linv, int* info, int c
       const int p = idx / (s * s), i = (idx / s) % s, j = idx % s;
       const int o = 2 * s * p, gi = o + s + i, gj = o + j;
       if (gi >= b) continue;
-      float acc = 0.f;
-      for (int k = j; k < s; ++k) acc = fmaf(L[gi][o + k], X[o + k][gj], acc);
-      T[gi][gj] = acc;
+      float acc0 = 0.f, acc1 = 0.f;  // two chains, loads of four terms in flight
+      int k = j;
+#pragma unroll 2
+      for (; k + 1 < s; k += 2) {
+        acc0 = fmaf(L[gi][o + k], X[o + k][gj], acc0);
+        acc1 = fmaf(L[gi][o + k + 1], X[o + k + 1][gj], acc1);
+      }
+      if (k < s) acc0 = fmaf(L[gi][o + k], X[o + k][gj], acc0);
+      T[gi][gj] = acc0 + acc1;
     }
     __syncthreads();
     // X21 = -X22 T (X22 lower: k <= i)
@@ -222,9 +264,15 @@ leaf_f32_kernel(const double* A, long lda, int b, double* Linv, int* info, int c
       const int p = idx / (s * s), i = (idx / s) % s, j = idx % s;
       const int o = 2 * s * p, gi = o + s + i, gj = o + j;
       if (gi >= b) continue;
-      float acc = 0.f;
-      for (int k = 0; k <= i; ++k) acc = fmaf(X[gi][o + s + k], T[o + s + k][gj], acc);
-      X[gi][gj] = -acc;
+      float acc0 = 0.f, acc1 = 0.f;
+      int k = 0;
+#pragma unroll 2
+      for (; k + 1 <= i; k += 2) {
+        acc0 = fmaf(X[gi][o + s + k], T[o + s + k][gj], acc0);
+        acc1 = fmaf(X[gi][o + s + k + 1], T[o + s + k + 1][gj], acc1);
+      }
+      if (k <= i) acc0 = fmaf(X[gi][o + s + k], T[o + s + k][gj], acc0);
+      X[gi][gj] = -(acc0 + acc1);
     }
     __syncthreads();
   }
@@ -233,28 +281,46 @@ leaf_f32_kernel(const double* A, long lda, int b, double* Linv, int* info, int c
     Linv[idx] = to_f64(X[i][j]);
   }
   if (Pblk != nullptr) {
-    // (X^T X)_ij = sum_{k >= i} X_ki X_kj for j <= i, mirrored. A warp takes whole rows i, its
-    // lanes the columns j = lane + 32 q (q <= i / 32); rows are dealt from both ends of the block
-    // (w, 2 nw - 1 - w, 2 nw + w, ...) so that the warps' work, (b - i)(i / 32 + 1), evens out
-    for (int t = 0;; ++t) {
-      const int i = (t & 1) ? (t + 1) * nwarps - 1 - warp : t * nwarps + warp;
-      if (t * nwarps >= b) break;
-      if (i >= b) continue;
-      const int nq = i / 32 + 1;
-      float acc[NL / 32] = {0.f, 0.f, 0.f, 0.f};
-      for (int k = i; k < b; ++k) {
-        const float xi = X[k][i];
+    // (X^T X)_ij = sum_{k >= i} X_ki X_kj for j <= i, mirrored (X is zero above its diagonal, so
+    // a sum may start below i). Warp w takes the row groups 4g .. 4g + 3 for g = w and g = 31 - w
+    // (long and short k ranges paired), its lanes the columns j = lane + 32 q; per k it loads the
+    // group's four entries of row k (broadcast) and its own columns, for up to 16 products: a
+    // quarter of the shared-memory loads per product of one row at a time.
+    static_assert(kLeafThreads == 512 && NL == 128, "32 row groups over 16 warps");
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      const int i0 = 4 * (h == 0 ? warp : NL / 4 - 1 - warp);
+      if (i0 >= b) continue;
+      const int nq = min(i0 + 3, b - 1) / 32 + 1;
+      float acc[4][NL / 32];
 #pragma unroll
-        for (int q = 0; q < NL / 32; ++q)
-          if (q < nq) acc[q] = fmaf(xi, X[k][lane + 32 * q], acc[q]);
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < NL / 32; ++q) acc[r][q] = 0.f;
+      for (int k = i0; k < b; ++k) {
+        float xi[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) xi[r] = X[k][i0 + r];
+#pragma unroll
+        for (int q = 0; q < NL / 32; ++q) {
+          if (q < nq) {
+            const float xj = X[k][lane + 32 * q];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[r][q] = fmaf(xi[r], xj, acc[r][q]);
+          }
+        }
       }
 #pragma unroll
-      for (int q = 0; q < NL / 32; ++q) {
-        const int j = lane + 32 * q;
-        if (q < nq && j <= i) {
-          const double v = to_f64(acc[q]);
-          Pblk[(long)i * ldp + j] = v;
-          Pblk[(long)j * ldp + i] = v;
+      for (int r = 0; r < 4; ++r) {
+        const int i = i0 + r;
+#pragma unroll
+        for (int q = 0; q < NL / 32; ++q) {
+          const int jj = lane + 32 * q;
+          if (i < b && q < nq && jj <= i) {
+            const double v = to_f64(acc[r][q]);
+            Pblk[(long)i * ldp + jj] = v;
+            Pblk[(long)jj * ldp + i] = v;
+          }
         }
       }
     }
