@@ -159,6 +159,7 @@ leaf_f32_kernel(const double* A, long lda, int b, double* Linv, int* info, int c
     for (int j = lane; j < NL; j += 32) {
       L[i][j] = (i < b && j <= i) ? to_f32(A[(long)i * lda + j]) : 0.f;
       X[i][j] = 0.f;
+      T[i][j] = 0.f;
     }
   __syncthreads();
   // Right-looking in panels of 16 columns. Warp 0 factors a panel with its rows in registers
@@ -241,40 +242,45 @@ leaf_f32_kernel(const double* A, long lda, int b, double* Linv, int* info, int c
     }
   }
   __syncthreads();
-  for (int s = 16; s < b; s *= 2) {  // join blocks of edge s into blocks of edge 2s
+  // Join blocks of edge s into blocks of edge 2s: T = L21 X11, then X21 = -X22 T, each a dense
+  // s x s x s product over the pair's blocks (the zeros above the diagonals of X11 and X22, and the
+  // zero rows of L, X and T at and beyond b, make the full sums exact). Warp w takes a group of four
+  // rows, its lanes the columns j = lane + 32 q, four products per loaded column entry.
+  for (int s = 16; s < b; s *= 2) {
     const int pairs = (b + 2 * s - 1) / (2 * s);
-    // T = L21 X11 for every pair (rows o+s .. o+2s, columns o .. o+s)
-    for (int idx = tid; idx < pairs * s * s; idx += nt) {
-      const int p = idx / (s * s), i = (idx / s) % s, j = idx % s;
-      const int o = 2 * s * p, gi = o + s + i, gj = o + j;
-      if (gi >= b) continue;
-      float acc0 = 0.f, acc1 = 0.f;  // two chains, loads of four terms in flight
-      int k = j;
-#pragma unroll 2
-      for (; k + 1 < s; k += 2) {
-        acc0 = fmaf(L[gi][o + k], X[o + k][gj], acc0);
-        acc1 = fmaf(L[gi][o + k + 1], X[o + k + 1][gj], acc1);
+    const int gps = s / 4, ngroups = pairs * gps, nq = (s + 31) / 32;
+    for (int pass = 0; pass < 2; ++pass) {  // 0: T = L21 X11; 1: X21 = -X22 T
+      for (int g = warp; g < ngroups; g += nwarps) {
+        const int o = 2 * s * (g / gps), r0 = o + s + (g % gps) * 4;
+        float acc[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        for (int k = 0; k < s; ++k) {
+          float a[4];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) a[r] = pass == 0 ? L[r0 + r][o + k] : X[r0 + r][o + s + k];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int j = lane + 32 * q;
+            if (q < nq && j < s) {
+              const float bv = pass == 0 ? X[o + k][o + j] : T[o + s + k][o + j];
+#pragma unroll
+              for (int r = 0; r < 4; ++r) acc[r][q] = fmaf(a[r], bv, acc[r][q]);
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int j = lane + 32 * q;
+            if (q < nq && j < s && r0 + r < b) {
+              if (pass == 0) T[r0 + r][o + j] = acc[r][q];
+              else X[r0 + r][o + j] = -acc[r][q];
+            }
+          }
+        }
       }
-      if (k < s) acc0 = fmaf(L[gi][o + k], X[o + k][gj], acc0);
-      T[gi][gj] = acc0 + acc1;
+      __syncthreads();
     }
-    __syncthreads();
-    // X21 = -X22 T (X22 lower: k <= i)
-    for (int idx = tid; idx < pairs * s * s; idx += nt) {
-      const int p = idx / (s * s), i = (idx / s) % s, j = idx % s;
-      const int o = 2 * s * p, gi = o + s + i, gj = o + j;
-      if (gi >= b) continue;
-      float acc0 = 0.f, acc1 = 0.f;
-      int k = 0;
-#pragma unroll 2
-      for (; k + 1 <= i; k += 2) {
-        acc0 = fmaf(X[gi][o + s + k], T[o + s + k][gj], acc0);
-        acc1 = fmaf(X[gi][o + s + k + 1], T[o + s + k + 1][gj], acc1);
-      }
-      if (k <= i) acc0 = fmaf(X[gi][o + s + k], T[o + s + k][gj], acc0);
-      X[gi][gj] = -(acc0 + acc1);
-    }
-    __syncthreads();
   }
   for (int idx = tid; idx < NL * NL; idx += nt) {
     const int i = idx / NL, j = idx % NL;

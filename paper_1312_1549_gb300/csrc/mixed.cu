@@ -17,6 +17,7 @@
 #include "omm_mixed.cuh"
 #include "tc_gemm.cuh"
 
+#include <algorithm>
 #include <new>
 
 namespace omm {
@@ -53,6 +54,11 @@ struct MixedState {
   tc::TileShape plan_shape[4];             // output tile shapes chosen by the autotuner
   double ms_autotune = 0.0;               // time the autotuner spent timing candidates
   const Scalars* plan_sc = nullptr;
+  // one line search as a CUDA graph, with the stream and buffers it was captured for
+  cudaGraphExec_t ls_exec = nullptr;
+  cudaStream_t ls_stream = nullptr;
+  const void* ls_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool ls_failed = false;
 };
 
 namespace {
@@ -134,9 +140,15 @@ void mixed_tuning(const MixedState* ms, int bn[4], double* ms_autotune) {
   *ms_autotune = ms->ms_autotune;
 }
 
+static void drop_graph(MixedState* ms) {
+  if (ms->ls_exec) cudaGraphExecDestroy(ms->ls_exec);
+  ms->ls_exec = nullptr;
+}
+
 void mixed_set_expire(MixedState* ms, int on) {
   ms->expire = on;
   ms->plan_sc = nullptr;  // rebuild the plans with the flag
+  drop_graph(ms);
 }
 
 void mixed_reset_error(MixedState* ms, cudaStream_t st) {
@@ -187,6 +199,7 @@ void mixed_destroy(MixedState* ms, cudaStream_t st) {
   mem::release(ms->err, st);
   mem::release(ms->plans, st);
   for (tc::BlockLists& bl : ms->hs_blocks) tc::free_block_lists(bl, st);
+  drop_graph(ms);
   delete ms;
 }
 
@@ -391,6 +404,43 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   pf.begin(st);
   run_plan(ms, st, kPlanG);
   pf.end(st, 8.0 * np * n * (double)n * m, kPlanG);
+}
+
+void mixed_iterate_replay(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, double* Dir, double* G,
+                          double* Gold, double* PG, double* Y4, double* SWHW, double* Proj, double* part,
+                          double* part2, const double* HS, const double* P, bool precond, Profiler& pf) {
+  const bool capturable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+  if (pf.on || !capturable || ms->ls_failed || ms->plan_sc != sc) {  // the first call builds the plans
+    mixed_iterate(ms, st, sc, C, Dir, G, Gold, PG, Y4, SWHW, Proj, part, part2, HS, P, precond, pf);
+    return;
+  }
+  const void* key[4] = {st, C, G, sc};
+  if (ms->ls_exec && std::equal(key, key + 4, ms->ls_key)) {
+    OMM_CUDA_TRY(cudaGraphLaunch(ms->ls_exec, st));
+    return;
+  }
+  drop_graph(ms);
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    try {
+      mixed_iterate(ms, st, sc, C, Dir, G, Gold, PG, Y4, SWHW, Proj, part, part2, HS, P, precond, pf);
+    } catch (...) {
+      ok = false;
+    }
+    ok = (cudaStreamEndCapture(st, &graph) == cudaSuccess) && ok && graph != nullptr;
+    ok = ok && cudaGraphInstantiate(&ms->ls_exec, graph, 0) == cudaSuccess;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {  // no graph on this stream: launch eagerly from now on
+    cudaGetLastError();
+    ms->ls_exec = nullptr;
+    ms->ls_failed = true;
+    mixed_iterate(ms, st, sc, C, Dir, G, Gold, PG, Y4, SWHW, Proj, part, part2, HS, P, precond, pf);
+    return;
+  }
+  std::copy(key, key + 4, ms->ls_key);
+  OMM_CUDA_TRY(cudaGraphLaunch(ms->ls_exec, st));
 }
 
 }  // namespace omm

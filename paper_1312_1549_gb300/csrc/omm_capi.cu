@@ -54,8 +54,9 @@ void Profiler::end(cudaStream_t st, double f, int tag) {
   pairs_[used_].tag = tag;
   ++used_;
 }
-void Profiler::collect() {
+void Profiler::collect(long keep) {
   for (int i = 0; i < used_; ++i) {
+    if (keep >= 0 && i >= keep) break;
     float t = 0.f;
     if (cudaEventElapsedTime(&t, pairs_[i].a, pairs_[i].b) != cudaSuccess) t = 0.f;
     ms += t;
@@ -555,14 +556,18 @@ omm_status omm_solve(omm_ctx* c, const double* C0, double* Cout, double* E, doub
       OMM_CUDA_TRY(cudaEventRecord(c->ev[2], c->st));
       int prev_iter = iter_total;
       for (;;) {
+        const int it_batch = h.iter;
         for (int k = 0; k < c->opts.check_every; ++k) {
-          if (mixed) mixed_iterate(c->mixed, c->st, c->sc, c->C, c->Dir, c->G, c->Gold, c->PG,
+          if (mixed) mixed_iterate_replay(c->mixed, c->st, c->sc, c->C, c->Dir, c->G, c->Gold, c->PG,
                                    c->Y4, c->SWHW, c->Proj, c->part, c->part2, c->HS, c->P,
                                    c->precond, c->prof);
           else iterate_fp64(c);
         }
         read_scalars(c);
-        c->prof.collect();
+        // the GEMMs of the line searches that ran: every completed one, and the P G product of the
+        // line search whose direction step stopped the round; the rest skipped on the stop flags
+        const long per_iter = c->precond ? 4 : 3;
+        c->prof.collect(per_iter * (h.iter - it_batch) + ((h.done || h.halt) && c->precond ? 1 : 0));
         if (h.done || h.halt) break;
         if (mixed && mixed_error(c->mixed, c->st) != 0) break;  // a bounded wait expired: stop at once
         // a mixed round that stalls above its refinement threshold is refreshed in float64

@@ -98,7 +98,9 @@ class Profiler {
   double ms_tag[kTags] = {}, flop_tag[kTags] = {};
   void begin(cudaStream_t st);
   void end(cudaStream_t st, double flop_of_launch, int tag = -1);
-  void collect();  // the stream must have been synchronised
+  // the stream must have been synchronised; keep >= 0: only the first `keep` launches recorded
+  // since the last collect are counted (the later ones were skipped by the solver's stop flags)
+  void collect(long keep = -1);
   void reset() {
     ms = 0.0; flop = 0.0; launches = 0;
     for (int t = 0; t < kTags; ++t) ms_tag[t] = flop_tag[t] = 0.0;

@@ -48,5 +48,11 @@ int mixed_error(MixedState* ms, cudaStream_t st);
 void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, double* Dir, double* G,
                    double* Gold, double* PG, double* Y4, double* SWHW, double* Proj, double* part,
                    double* part2, const double* HS, const double* P, bool precond, Profiler& prof);
+// the same line search replayed from a CUDA graph (captured on first use, after the plans exist,
+// for this stream and these buffers); launched eagerly when profiling, on the legacy default
+// stream or when a capture fails
+void mixed_iterate_replay(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, double* Dir, double* G,
+                          double* Gold, double* PG, double* Y4, double* SWHW, double* Proj, double* part,
+                          double* part2, const double* HS, const double* P, bool precond, Profiler& prof);
 
 }  // namespace omm

@@ -1679,13 +1679,15 @@ TileShape choose_tile_shape(cudaStream_t st, const std::vector<GemmSpec>& specs,
                             bool allow_pair) {
   if (ms_spent) *ms_spent = 0.0;
   if (specs.empty()) return TileShape{};
-  // candidates: one SM per 128-row tile, and (split form, every M >= 256) SM pairs; 192-wide pair
+  // candidates: one SM per 128-row tile, and (split form or single pass) SM pairs; 192-wide pair
   // tiles need K-major B (an SM stages 96 rows) and, for a block-sparse B, lists for that width
   std::vector<TileShape> cands = {{256, false}, {128, false}};
   const bool split = is_split3(pl);
   bool pair_ok = allow_pair && (split || is_single(pl)), w192 = true, dense = true;
   for (const GemmSpec& g : specs) {
-    if (g.ep.M < 2 * BM || (split && (g.A->slices < 2 || g.B->slices < 2))) pair_ok = false;
+    // (a GEMM of fewer than 256 rows runs on pairs too, its second CTA's rows past M; the timing
+    // decides whether that pays)
+    if (split && (g.A->slices < 2 || g.B->slices < 2)) pair_ok = false;
     if (g.B->mn_major || (g.sparse[0] != nullptr && g.sparse[2] == nullptr)) w192 = false;
     if (g.sparse[0] != nullptr) dense = false;
   }

@@ -189,8 +189,8 @@ void gemm_persistent(cudaStream_t st, const Operand& A, const Operand& B, int K,
 
 // Tile-shape autotuner: times one persistent launch over these GEMMs (the operands as given,
 // the outputs redirected to scratch) with each candidate shape -- 128 x 256 and 128 x 128 on one
-// SM, and (split form or single pass, allow_pair, every M >= 256) 256 x 128, 256 x 192 and
-// 256 x 256 on SM pairs, and (dense B) the same on clusters of two pairs sharing A
+// SM, and (split form or single pass, allow_pair) 256 x 128, 256 x 192 and 256 x 256 on SM pairs,
+// and (dense B) the same on clusters of two pairs sharing A
 // -- returns the fastest, and remembers it per shape signature for the life of the process.
 // ms_spent receives the time spent timing (0 when the answer came from the cache).
 struct GemmSpec {
