@@ -732,7 +732,7 @@ def main():
         a = sl_flop / (sl_ms * 1e-3) / 1e12
         roofline_sliced = {"bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
                            "traffic": None, "kernel": "gemm_persistent_one_kernel (tcgen05, sliced products: "
-                           "preconditioner inverse (5 slices), refreshes and certificate (10), D (8))", "launches": sl_n,
+                           "preconditioner inverse (3-term bf16 split), refreshes and certificate (10 slices), D (8))", "launches": sl_n,
                            "avg_launch_ms": sl_ms / max(sl_n, 1), "ms_per_solve": sl_ms}
     out = {"metric": METRIC, "value": ms * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",

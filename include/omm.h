@@ -102,12 +102,13 @@ typedef struct {
                            tol_grad and omm_info.gmax then refer to the gradient of the reduced
                            problem (Eq. 12 with S = I). Products as for the preconditioner:
                            float64, or float64-class slices on the mixed path. 0 (default) -> off */
-  int precond_slices;   /* mixed: 5-bit fixed-point slices of the sliced tensor-core products that
-                           invert S + T/tau (2..10; 0 -> 5, about 25 bits of each row-scaled
-                           operand). P enters the line searches only through its bf16 rounding (the
-                           single-pass P G of the search direction) and the converged point does
-                           not depend on P, so the float64-class 10 slices buy nothing there; the
-                           Cholesky flavour's factor always takes 10 */
+  int precond_slices;   /* mixed: products of the tensor-core inverse of S + T/tau: 1 (the default,
+                           0 -> 1) the 3-term bf16 split form (about 16 bits of each product),
+                           2..10 that many 5-bit fixed-point slices (about 5 bits each). P enters
+                           the line searches only through its bf16 rounding (the single-pass P G
+                           of the search direction) and the converged point does not depend on P,
+                           so the float64-class 10 slices buy nothing there; the Cholesky
+                           flavour's factor always takes 10 */
   int debug_expire_wait; /* tests of the timeout status only (0 = off, the default): 1 -> on the
                            mixed path the first tensor-core GEMM of every line search waits about
                            1 ms on a barrier that nothing arrives at, before it issues any copy or
@@ -165,8 +166,8 @@ typedef struct {
  * H~ = H - eta S (Eq. 9) and the preconditioner P = (S + T/tau)^-1 (Eq. 17), once per
  * geometry (Sec. 2.4): on the float64 path (and on the mixed path below m = 2048) by a
  * blocked float64 Cholesky factorisation and inverse; on the mixed path from m = 2048 by a
- * recursive Cholesky inverse whose products are fixed-point sliced tensor-core GEMMs at
- * preconditioner grade (opts->precond_slices, default 5 slices, float32 diagonal blocks).
+ * recursive Cholesky inverse whose products are tensor-core GEMMs at preconditioner grade
+ * (opts->precond_slices: by default the 3-term bf16 split form; float32 diagonal blocks).
  *   m      number of basis functions, n number of Wannier functions, 0 < n < m.
  *   H,S,T  m x m symmetric float64 (host or device). T may be NULL when
  *          opts->no_precondition == 1. They are copied; the caller keeps ownership.

@@ -46,12 +46,13 @@ omm_status omm_kernel_spd_inverse(int m, const double* A, double* P, int* info, 
  * Y^T Y updates beside the factorisation and is joined before the call returns. */
 omm_status omm_kernel_spd_inverse_sliced(int m, const double* A, double* P, int* info, void* stream);
 
-/* The preconditioner-grade variant the mixed solver uses by default (omm_opts.precond_slices):
- * the same recursion with `slices` fixed-point slices per operand (2..9, 5 bits each) and the
- * 64 x 64 diagonal blocks in float32. P enters the line searches only through its bf16 hi/lo
- * split (about 2^-16 of each element), so an inverse to a few parts in 10^6 serves as well as a
- * float64 one. Arguments and errors as for omm_kernel_spd_inverse_sliced; OMM_ERR_ARG for
- * slices outside 2..9. */
+/* The preconditioner-grade variant the mixed solver uses (omm_opts.precond_slices): the same
+ * recursion with `slices` fixed-point slices per operand (2..9, 5 bits each), or with slices = 1
+ * (the solver's default) every product in the 3-term bf16 split form (about 2^-16 of |A||B|), and
+ * the 128 x 128 diagonal blocks in float32. P enters the line searches only through its bf16
+ * rounding (the single-pass P G of the search direction, 2^-9 of each element), so an inverse to a
+ * few parts in 10^4 serves as well as a float64 one. Arguments and errors as for
+ * omm_kernel_spd_inverse_sliced; OMM_ERR_ARG for slices outside 1..9. */
 omm_status omm_kernel_spd_inverse_precond(int m, const double* A, double* P, int slices, int* info,
                                           void* stream);
 

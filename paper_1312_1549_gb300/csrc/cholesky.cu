@@ -443,7 +443,7 @@ long round8(long x) { return (x + 7) / 8 * 8; }
 // scratch of one stream's products
 struct Lane {
   cudaStream_t st = nullptr;
-  int slices = kInvSlices;   // fixed-point slices of every product on this lane
+  int slices = kInvSlices;   // fixed-point slices of every product on this lane (1: the 3-term bf16 split)
   double* tr0 = nullptr;     // float64 transposes
   double* tr1 = nullptr;
   __nv_bfloat16* sl0 = nullptr;  // slices of two operands
@@ -472,6 +472,18 @@ void sliced_nt(Lane& L, int* err, int M, int N, int K, double alpha, const doubl
                long ldb, double beta, double* C, long ldc) {
   const long ld = round8(K);
   const int s = L.slices;
+  if (s == 1) {  // preconditioner grade from bf16 hi/lo splits: three products, about 2^-16 of |A||B|
+    const tc::Epilogue ep{C, ldc, N, 0, alpha, beta, M, N, nullptr, err};
+    tc::split(L.st, A, M, K, lda, L.sl0, L.sl0 + (long)M * ld, ld, nullptr);
+    const tc::Operand oa = tc::make_operand(L.sl0, M, K, ld, 2, true);
+    if (B == A && ldb == lda && N == M) {
+      emu::gemm_split(L.st, oa, tc::make_operand(L.sl0, N, K, ld, 2, false), K, ep);
+    } else {
+      tc::split(L.st, B, N, K, ldb, L.sl1, L.sl1 + (long)N * ld, ld, nullptr);
+      emu::gemm_split(L.st, oa, tc::make_operand(L.sl1, N, K, ld, 2, false), K, ep);
+    }
+    return;
+  }
   emu::slice_rows(L.st, A, M, K, lda, s, L.sl0, ld, nullptr);
   const tc::Operand oa = tc::make_operand(L.sl0, M, K, ld, s, true);
   tc::Operand ob;
@@ -609,7 +621,7 @@ void sliced_impl(cudaStream_t st, int m, double* A, double* P, double* Y_out, vo
   w.side.sl0 = w.main.sl1 + sl;
   w.side.sl1 = w.side.sl0 + sl;
   w.main.st = st;
-  w.main.slices = w.side.slices = std::min(std::max(slices, 2), kInvSlices);
+  w.main.slices = w.side.slices = slices == 1 ? 1 : std::min(std::max(slices, 2), kInvSlices);
   if (w.nb == NL) {
     static bool attr = false;
     if (!attr) {

@@ -155,6 +155,12 @@ void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, in
   if (t_prof) t_prof->end(st, 2.0 * ep.M * (double)ep.N * K * pl.n * tc::block_density(sparse));
 }
 
+void gemm_split(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, const tc::Epilogue& ep) {
+  if (t_prof) t_prof->begin(st);
+  tc::gemm_persistent(st, A, B, K, tc::pairs_split3(), ep);
+  if (t_prof) t_prof->end(st, 2.0 * ep.M * (double)ep.N * K * 3.0);
+}
+
 }  // namespace emu
 
 struct EmuState {

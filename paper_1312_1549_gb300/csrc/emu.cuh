@@ -18,6 +18,8 @@ void set_profiler(Profiler* p);
 // C = alpha A B^T + beta C from s-slice operands (A, B made by slice_rows)
 void gemm(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, int s, const tc::Epilogue& ep,
           double* partial = nullptr, long partial_capacity = 0, const tc::BlockLists* sparse = nullptr);
+// C = alpha A B^T + beta C from bf16 hi/lo operands (the 3-term split form), timed like the sliced products
+void gemm_split(cudaStream_t st, const tc::Operand& A, const tc::Operand& B, int K, const tc::Epilogue& ep);
 }  // namespace emu
 
 struct EmuState;

@@ -119,8 +119,8 @@ omm_status omm_kernel_spd_inverse_sliced(int m, const double* A, double* P, int*
 }
 
 omm_status omm_kernel_spd_inverse_precond(int m, const double* A, double* P, int slices, int* info, void* stream) {
-  if (slices < 2 || slices > 9) {
-    set_last_error("omm_kernel_spd_inverse_precond: slices must be in 2..9");
+  if (slices < 1 || slices > 9) {
+    set_last_error("omm_kernel_spd_inverse_precond: slices must be in 1..9");
     return OMM_ERR_ARG;
   }
   return spd_inverse_sliced_impl("omm_kernel_spd_inverse_precond", m, A, P, slices, info, stream);

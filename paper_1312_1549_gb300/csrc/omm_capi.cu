@@ -87,9 +87,10 @@ namespace omm {
 
 constexpr int kMixedRoundCap = 400;
 constexpr int kEmuSlices = 10;  // fixed-point slices of the float64-class refresh (about 50 bits)
-// slices of the mixed path's preconditioner inverse: P reaches the line searches only through its
+// products of the mixed path's preconditioner inverse: 1 = the 3-term bf16 split form (about 2^-16
+// of each product; 2..10 would be fixed-point slices). P reaches the line searches only through its
 // bf16 rounding (the single-pass P G of the search direction), and the minimum does not depend on P
-constexpr int kPrecondSlices = 5;
+constexpr int kPrecondSlices = 1;
 // Below these sizes the native float64 routines are cheaper than the sliced tensor-core ones,
 // whose many small launches are latency-bound there: the inverse (or factor) of an m x m matrix
 // with m < kSlicedInverseMin, and the state recompute (refresh, certificate, D) of a problem with
@@ -305,8 +306,8 @@ omm_status omm_create(int m, int n, const double* H, const double* S, const doub
   if (!(o.e_tol >= 0.0)) o.e_tol = 0.0;
   if (!(o.refine_ratio > 0.0)) o.refine_ratio = 1e-3;
   if (o.precond_slices <= 0) o.precond_slices = kPrecondSlices;
-  if (o.precond_slices < 2 || o.precond_slices > 10)
-    return fail(OMM_ERR_ARG, "omm_create: precond_slices must be in 2..10");
+  if (o.precond_slices < 1 || o.precond_slices > 10)
+    return fail(OMM_ERR_ARG, "omm_create: precond_slices must be in 1..10");
   if (o.precision != OMM_PREC_FP64 && o.precision != OMM_PREC_MIXED)
     return fail(OMM_ERR_ARG, "omm_create: unknown precision");
   const bool chol = o.cholesky != 0;

@@ -190,15 +190,18 @@ def test_spd_inverse_sliced_preconditioner_matches_oracle(S):
 # P reaches the line searches only through its bf16 rounding (2^-9 of each element, the single-pass P G);
 # the residual bound below (5 slices, about 2^-24 of each row-scaled operand, condition numbers
 # near 10) keeps P well inside that.
+# slices = 1: every product of the recursion in the 3-term bf16 split form (about 2^-16 of |A||B|),
+# still far inside the bf16 rounding (2^-9) through which P enters the search direction.
 @pytest.mark.parametrize("m", [5, 65, 200, 1000, 2500])
-@pytest.mark.parametrize("slices", [5, 7])
+@pytest.mark.parametrize("slices", [1, 5, 7])
 def test_spd_inverse_precond(S, m, slices):
     rng = np.random.default_rng(m)
     X = rng.normal(size=(m, m))
     A = X @ X.T / m + 0.5 * np.eye(m)
     P = S.spd_inverse(dev(A), slices=slices).cpu().numpy()
     assert np.array_equal(P, P.T)
-    assert np.abs(P @ A - np.eye(m)).max() <= 1e-5
+    assert np.abs(P @ A - np.eye(m)).max() <= (1e-3 if slices == 1 else 1e-5)
+    assert np.linalg.eigvalsh(P).min() > 0.0
 
 
 def test_spd_inverse_precond_rejects_bad_arguments(S):
