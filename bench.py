@@ -61,8 +61,8 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 float64 FMA rate, nominal (context; the roof
 # dram__bytes_read.sum + dram__bytes_write.sum over the P G, [HD; SD], projection and gradient
 # launches of one ncu capture: profiles/traffic_si512_line_search.md). Valid only for the GEMM
 # source it was measured on: reported as null once tc_gemm.cu has changed.
-GEMM_TRAFFIC_BYTES = 304.9e6
-GEMM_TRAFFIC_SOURCE_SHA256 = "0623d445c5564f62aa213aa43acc608ea966e39123233097ec0d91fa4dd89654"
+GEMM_TRAFFIC_BYTES = 283.5e6
+GEMM_TRAFFIC_SOURCE_SHA256 = "c265b6b483b8fb484f357985f7525766ef5acbaa8bef3cb77e07d4b1139c73e8"
 
 
 def gemm_traffic():
@@ -330,6 +330,7 @@ def batch_record(args, probs, device, stream, with_fp64=True, profile_roofline=T
            "s_create_wall": statistics.mean(x[0] for x in timed),
            "s_solve_wall": statistics.mean(x[1] for x in timed),
            "ms_line_search_graphs": infos[0]["ms_iterate"],
+           "ms_refresh_wall": infos[0]["ms_batch_refresh"],
            "ms_refresh_sum": sum(i["ms_refine"] - i["ms_certify"] for i in infos),
            "ms_certify_sum": sum(i["ms_certify"] for i in infos),
            "tile_width_autotuned": infos[0]["tile_width"], "gpu_launches": launches, "clocks": clk.summary()}
@@ -551,6 +552,7 @@ def run_kpoints(args):
                 "s_create_wall": statistics.mean(t[0] for t in timed),
                 "s_solve_wall": statistics.mean(t[1] for t in timed),
                 "ms_line_search_graphs": infos[0]["ms_iterate"],
+           "ms_refresh_wall": infos[0]["ms_batch_refresh"],
                 "gpu_launches": launches, "clocks": clk.summary(),
                 "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": (achieved / peak) if achieved else None, "traffic": None,

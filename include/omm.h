@@ -160,6 +160,9 @@ typedef struct {
   double ms_gemm_plan[4];    /* mixed single solve with opts.profile: ms_main_gemm split over the
                                 P G, [H D; S D], projection and gradient GEMMs */
   double flop_gemm_plan[4];  /* the same for main_gemm_flop */
+  double ms_batch_refresh;   /* omm_solve_batched only: host wall time of its refresh and
+                                certificate passes (the stopped instances' recomputes, overlapped
+                                on several streams, and the read-back that follows) */
 } omm_info;
 
 /* Create a solver context for one (H, S, T) and do the per-geometry setup:

@@ -40,7 +40,7 @@ class OmmInfo(ct.Structure):
                 ("ms_sliced_gemm", ct.c_double), ("sliced_gemm_flop", ct.c_double),
                 ("sliced_gemm_launches", ct.c_double), ("ms_batch", ct.c_double),
                 ("ms_transform", ct.c_double), ("ms_gemm_plan", ct.c_double * 4),
-                ("flop_gemm_plan", ct.c_double * 4)]
+                ("flop_gemm_plan", ct.c_double * 4), ("ms_batch_refresh", ct.c_double)]
 
     def as_dict(self):
         out = {}

@@ -18,6 +18,7 @@
 #include "split_device.cuh"
 #include "tc_gemm.cuh"
 
+#include <chrono>
 #include <algorithm>
 #include <atomic>
 #include <thread>
@@ -102,7 +103,7 @@ struct Grouped {
 };
 
 constexpr int kGroupedGemms = 4;
-constexpr int kRefreshStreams = 8;
+constexpr int kRefreshStreams = 32;  // the stopped instances' refreshes and certificates overlap on these
 
 template <typename T>
 void alloc(T** p, size_t count, cudaStream_t st) {
@@ -434,7 +435,7 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
   omm_status worst = OMM_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr, g0 = nullptr, g1 = nullptr;
   float ms_total = 0.f;
-  double ms_graph = 0.0, gemm_flop = 0.0;
+  double ms_graph = 0.0, gemm_flop = 0.0, ms_refresh_wall = 0.0;
   const bool profile = b->opts.profile != 0;
   try {
     OMM_CUDA_TRY(cudaEventCreate(&e0));
@@ -507,6 +508,7 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
       // pass 1: instances that stopped get their refresh (float64-class) or certificate
       // (float64-class, or native float64 on request) enqueued, spread over the pool
       // streams so that the small instances' products overlap on the GPU
+      const auto t_pass = std::chrono::steady_clock::now();
       std::vector<int> todo;
       for (int i = 0; i < cnt; ++i) {
         if (finished[i]) continue;
@@ -580,6 +582,7 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
         round_start[i] = h.iter;
         begin_round(b, i, h.gmax, h.iter);
       }
+      ms_refresh_wall += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_pass).count();
     }
     OMM_CUDA_TRY(cudaEventRecord(e1, b->st));
     OMM_CUDA_TRY(cudaEventSynchronize(e1));
@@ -623,6 +626,7 @@ omm_status omm_solve_batched(omm_batch* b, const double* const* C0, double* cons
         // opts.profile, the grouped tensor-core GEMMs inside them
         inf.ms_iterate = ms_graph;
         inf.ms_batch = ms_total;
+        inf.ms_batch_refresh = ms_refresh_wall;
         inf.ms_main_gemm = b->prof.ms;
         inf.main_gemm_launches = (double)b->prof.launches;
         inf.main_gemm_flop = gemm_flop;
