@@ -348,7 +348,8 @@ def batch_record(args, probs, device, stream, with_fp64=True, profile_roofline=T
         peak = load_peaks()[0]["bf16_tflops_sustained"]
         rec["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                            "frac": (achieved / peak) if achieved else None, "traffic": None,
-                           "kernel": "gemm_persistent_kernel (grouped over the batch, tcgen05, fused 3-term split)",
+                           "kernel": "gemm_pair_kernel / gemm_persistent_kernel (grouped over the batch, tcgen05; "
+                                     "split form, single-pass P G; shapes as tile_width_autotuned)",
                            "peak_source": "bf16_tflops_sustained of measured MEASURED_PEAKS",
                            "launches": b0["main_gemm_launches"],
                            "avg_launch_ms": b0["ms_main_gemm"] / max(b0["main_gemm_launches"], 1),
@@ -426,7 +427,7 @@ def sequence_record(args, p, device, stream):
            "ms_outputs": [i["ms_outputs"] for _, i in infos],
            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                         "frac": (achieved / peak) if achieved else None, "traffic": None,
-                        "kernel": "gemm_persistent_kernel (tcgen05, fused 3-term split)",
+                        "kernel": "line-search GEMMs (tcgen05 on SM pairs or single SMs; split form, single-pass P G)",
                         "peak_source": "bf16_tflops_sustained of measured MEASURED_PEAKS",
                         "launches": sum(i["main_gemm_launches"] for _, i in infos)},
            "gpu_launches": launches, "clocks": clk.summary()}
@@ -556,7 +557,7 @@ def run_kpoints(args):
                 "gpu_launches": launches, "clocks": clk.summary(),
                 "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                              "frac": (achieved / peak) if achieved else None, "traffic": None,
-                             "kernel": "gemm_persistent_kernel (grouped over the k points, tcgen05, fused 3-term "
+                             "kernel": "gemm_pair_kernel / gemm_persistent_kernel (grouped over the k points, tcgen05, fused 3-term "
                                        "split; real forms 2m x 2m, 2n)",
                              "peak_source": "bf16_tflops_sustained of measured MEASURED_PEAKS",
                              "launches": b0["main_gemm_launches"],
