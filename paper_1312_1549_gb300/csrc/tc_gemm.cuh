@@ -203,10 +203,6 @@ struct GemmSpec {
 inline int sparse_slot(int bn) { return bn == 256 ? 0 : (bn == 128 ? 1 : 2); }
 TileShape choose_tile_shape(cudaStream_t st, const std::vector<GemmSpec>& specs, const PairList& pl,
                             double* ms_spent = nullptr, bool allow_pair = true);
-inline int choose_tile_width(cudaStream_t st, const std::vector<GemmSpec>& specs, const PairList& pl,
-                             double* ms_spent = nullptr) {
-  return choose_tile_shape(st, specs, pl, ms_spent, false).bn;
-}
 
 // x (float64, rows x cols, ld_src) -> hi = bf16(x), lo = bf16(x - hi) (ld_dst);
 // transposed variants write dst[j][i]. Skipped when sc's done/halt is set.

@@ -186,12 +186,11 @@ def test_spd_inverse_sliced_preconditioner_matches_oracle(S):
     assert np.abs(P - P_ref).max() <= 1e-11 * np.abs(P_ref).max()
 
 
-# The preconditioner-grade inverse (the mixed solver's default): fewer slices and float32 leaves.
-# P reaches the line searches only through its bf16 rounding (2^-9 of each element, the single-pass P G);
-# the residual bound below (5 slices, about 2^-24 of each row-scaled operand, condition numbers
-# near 10) keeps P well inside that.
-# slices = 1: every product of the recursion in the 3-term bf16 split form (about 2^-16 of |A||B|),
-# still far inside the bf16 rounding (2^-9) through which P enters the search direction.
+# The preconditioner-grade inverses: float32 leaves and, for slices = 1 (the mixed solver's default),
+# every product of the recursion in the 3-term bf16 split form (about 2^-16 of |A||B|), else that many
+# 5-bit fixed-point slices (5 slices: about 2^-24 of each row-scaled operand). P reaches the line
+# searches only through its bf16 rounding (2^-9 of each element, the single-pass P G); the residual
+# bounds below (condition numbers near 10) keep P well inside that.
 @pytest.mark.parametrize("m", [5, 65, 200, 1000, 2500])
 @pytest.mark.parametrize("slices", [1, 5, 7])
 def test_spd_inverse_precond(S, m, slices):
