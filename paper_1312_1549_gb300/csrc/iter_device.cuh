@@ -253,67 +253,73 @@ __device__ __forceinline__ float f32_trunc(double x) {
 //   t4 Tr(S'' H_W)  t5 Tr(S_W H'')  t6 Tr(S' H')    t7 Tr(S'^T H')
 //   t8 Tr(S'' H')   t9 Tr(S' H'')   t10 Tr(S'' H'')
 // F32: the nine product traces multiply float32 copies of the elements (truncated on the integer
-// pipe) and sum each thread's four products in float32 before the float64 block sums: about 2^-22
-// of each term, far below the error of the tensor-core projections they come from (mixed path).
+// pipe) and sum each thread's products (four per tile) in float32 before the float64 block sums:
+// about 2^-20 of each term, far below the error of the tensor-core projections they come from
+// (mixed path).
 template <bool F32>
 __device__ __forceinline__ void traces_body(int n, const double* __restrict__ SWHW, const double* __restrict__ Proj,
               double* part, const Scalars* sc, int bx_, int nbx_) {
   if (stopped(sc)) return;
   const int tiles = (n + 31) / 32;
-  const int I = bx_ / tiles, J = bx_ % tiles;
   __shared__ double tHW[32][33], tH1[32][33], tH2[32][33];
   const long l2 = 2L * n, l4 = 4L * n;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  // load Y^T tiles: element (i, j) of tile (I, J) needs Y[j][i] from tile (J, I)
-  for (int r = ty; r < 32; r += 8) {
-    const int gi = J * 32 + r, gj = I * 32 + tx;  // row gi of Y, col gj
-    const bool ok = gi < n && gj < n;
-    tHW[r][tx] = ok ? SWHW[(long)gi * l2 + n + gj] : 0.0;
-    tH1[r][tx] = ok ? Proj[(long)gi * l4 + gj] : 0.0;
-    tH2[r][tx] = ok ? Proj[(long)gi * l4 + 2L * n + gj] : 0.0;
-  }
-  __syncthreads();
   double t[kNumTraces];
 #pragma unroll
   for (int q = 0; q < kNumTraces; ++q) t[q] = 0.0;
   float f[kNumTraces];
 #pragma unroll
   for (int q = 0; q < kNumTraces; ++q) f[q] = 0.0f;
-  for (int r = ty; r < 32; r += 8) {
-    const int gi = I * 32 + r, gj = J * 32 + tx;
-    if (gi >= n || gj >= n) continue;
-    const double sw = SWHW[(long)gi * l2 + gj];
-    const double h1 = Proj[(long)gi * l4 + gj];
-    const double s1 = Proj[(long)gi * l4 + n + gj];
-    const double s2 = Proj[(long)gi * l4 + 3L * n + gj];
-    // Y_ji from the staged transposed tiles: Y[gj][gi] = tile(J,I)[tx][r]
-    const double hwT = tHW[tx][r], h1T = tH1[tx][r], h2T = tH2[tx][r];
-    if (gi == gj) {
-      t[0] += h1;
-      t[3] += Proj[(long)gi * l4 + 2L * n + gj];
+  // 32 x 32 tiles bx_, bx_ + nbx_, ... of the n x n blocks (one per block of the batched launch,
+  // several per block of the single launch, whose partial sums then number fewer)
+  for (int tile = bx_; tile < tiles * tiles; tile += nbx_) {
+    const int I = tile / tiles, J = tile % tiles;
+    __syncthreads();  // the previous tile's staged transposes have been read
+    // load Y^T tiles: element (i, j) of tile (I, J) needs Y[j][i] from tile (J, I)
+    for (int r = ty; r < 32; r += 8) {
+      const int gi = J * 32 + r, gj = I * 32 + tx;  // row gi of Y, col gj
+      const bool ok = gi < n && gj < n;
+      tHW[r][tx] = ok ? SWHW[(long)gi * l2 + n + gj] : 0.0;
+      tH1[r][tx] = ok ? Proj[(long)gi * l4 + gj] : 0.0;
+      tH2[r][tx] = ok ? Proj[(long)gi * l4 + 2L * n + gj] : 0.0;
     }
-    if (F32) {
-      const float fs1 = f32_trunc(s1), fsw = f32_trunc(sw), fs2 = f32_trunc(s2), fh1 = f32_trunc(h1);
-      const float fhwT = f32_trunc(hwT), fh1T = f32_trunc(h1T), fh2T = f32_trunc(h2T);
-      f[1] = fmaf(fs1, fhwT, f[1]);
-      f[2] = fmaf(fsw, fh1T, f[2]);
-      f[4] = fmaf(fs2, fhwT, f[4]);
-      f[5] = fmaf(fsw, fh2T, f[5]);
-      f[6] = fmaf(fs1, fh1T, f[6]);
-      f[7] = fmaf(fs1, fh1, f[7]);
-      f[8] = fmaf(fs2, fh1T, f[8]);
-      f[9] = fmaf(fs1, fh2T, f[9]);
-      f[10] = fmaf(fs2, fh2T, f[10]);
-    } else {
-      t[1] = fma(s1, hwT, t[1]);
-      t[2] = fma(sw, h1T, t[2]);
-      t[4] = fma(s2, hwT, t[4]);
-      t[5] = fma(sw, h2T, t[5]);
-      t[6] = fma(s1, h1T, t[6]);
-      t[7] = fma(s1, h1, t[7]);   // Tr(S'^T H') = sum_ij S'_ij H'_ij
-      t[8] = fma(s2, h1T, t[8]);
-      t[9] = fma(s1, h2T, t[9]);
-      t[10] = fma(s2, h2T, t[10]);
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int gi = I * 32 + r, gj = J * 32 + tx;
+      if (gi >= n || gj >= n) continue;
+      const double sw = SWHW[(long)gi * l2 + gj];
+      const double h1 = Proj[(long)gi * l4 + gj];
+      const double s1 = Proj[(long)gi * l4 + n + gj];
+      const double s2 = Proj[(long)gi * l4 + 3L * n + gj];
+      // Y_ji from the staged transposed tiles: Y[gj][gi] = tile(J,I)[tx][r]
+      const double hwT = tHW[tx][r], h1T = tH1[tx][r], h2T = tH2[tx][r];
+      if (gi == gj) {
+        t[0] += h1;
+        t[3] += Proj[(long)gi * l4 + 2L * n + gj];
+      }
+      if (F32) {
+        const float fs1 = f32_trunc(s1), fsw = f32_trunc(sw), fs2 = f32_trunc(s2), fh1 = f32_trunc(h1);
+        const float fhwT = f32_trunc(hwT), fh1T = f32_trunc(h1T), fh2T = f32_trunc(h2T);
+        f[1] = fmaf(fs1, fhwT, f[1]);
+        f[2] = fmaf(fsw, fh1T, f[2]);
+        f[4] = fmaf(fs2, fhwT, f[4]);
+        f[5] = fmaf(fsw, fh2T, f[5]);
+        f[6] = fmaf(fs1, fh1T, f[6]);
+        f[7] = fmaf(fs1, fh1, f[7]);
+        f[8] = fmaf(fs2, fh1T, f[8]);
+        f[9] = fmaf(fs1, fh2T, f[9]);
+        f[10] = fmaf(fs2, fh2T, f[10]);
+      } else {
+        t[1] = fma(s1, hwT, t[1]);
+        t[2] = fma(sw, h1T, t[2]);
+        t[4] = fma(s2, hwT, t[4]);
+        t[5] = fma(sw, h2T, t[5]);
+        t[6] = fma(s1, h1T, t[6]);
+        t[7] = fma(s1, h1, t[7]);   // Tr(S'^T H') = sum_ij S'_ij H'_ij
+        t[8] = fma(s2, h1T, t[8]);
+        t[9] = fma(s1, h2T, t[9]);
+        t[10] = fma(s2, h2T, t[10]);
+      }
     }
   }
   __shared__ double sh[kNumTraces][TB / 32];

@@ -265,10 +265,11 @@ int traces_blocks(int n) {
   const int t = (n + 31) / 32;
   return t * t;
 }
+int traces_partials(int n) { return (traces_blocks(n) + 3) / 4; }
 void launch_traces(cudaStream_t st, int n, const double* SWHW, const double* Proj, double* part,
                    const Scalars* sc, bool fp32_products) {
-  if (fp32_products) traces_kernel<true><<<traces_blocks(n), TB, 0, st>>>(n, SWHW, Proj, part, sc);
-  else traces_kernel<false><<<traces_blocks(n), TB, 0, st>>>(n, SWHW, Proj, part, sc);
+  if (fp32_products) traces_kernel<true><<<traces_partials(n), TB, 0, st>>>(n, SWHW, Proj, part, sc);
+  else traces_kernel<false><<<traces_partials(n), TB, 0, st>>>(n, SWHW, Proj, part, sc);
   OMM_LAUNCH_CHECK();
 }
 void launch_control_linesearch(cudaStream_t st, Scalars* sc, const double* part, int nblocks) {

@@ -170,7 +170,7 @@ omm_status omm_kernel_quartic_coefficients(int n, const double* SWHW, const doub
     h.max_iter = 1;
     OMM_CUDA_TRY(cudaMemcpyAsync(sc, &h, sizeof(h), cudaMemcpyHostToDevice, st));
     launch_traces(st, n, SWHW, Proj, part, sc);
-    launch_control_linesearch(st, sc, part, traces_blocks(n));
+    launch_control_linesearch(st, sc, part, traces_partials(n));
     OMM_CUDA_TRY(cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, st));
     OMM_CUDA_TRY(cudaStreamSynchronize(st));
     for (int q = 0; q < 5; ++q) alpha[q] = h.alpha[q];

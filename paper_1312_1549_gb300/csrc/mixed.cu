@@ -394,7 +394,7 @@ void mixed_iterate(MixedState* ms, cudaStream_t st, Scalars* sc, double* C, doub
   run_plan(ms, st, kPlanProj);
   pf.end(st, 8.0 * np * n * (double)n * m, kPlanProj);
   launch_traces(st, n, SWHW, Proj, part2, sc, /*fp32_products=*/true);
-  launch_control_linesearch(st, sc, part2, traces_blocks(n));
+  launch_control_linesearch(st, sc, part2, traces_partials(n));
   // Eq. 16 and the footnote's updates of C, HC, SC; dHC, dSC; and their splits
   launch_update_state_split32(st, n, m, C, Y4, ms->Dir32, ms->HD32, ms->dY32, ms->Y_hi, ms->Y_lo, ms->ldm, sc);
   // H_W, S_W (Eq. 16) and the split of [dS_W | dH_W] into W

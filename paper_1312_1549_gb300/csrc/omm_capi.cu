@@ -179,7 +179,7 @@ void iterate_fp64(omm_ctx* c) {
   dgemm(c->st, 0, 1, n, 4 * n, m, 1.0, c->Dir, m, 0, c->Y4, m, 0, 0.0, c->Proj, 4L * n, 0, 1, 0, skip);
   pf.end(c->st, fPr);
   launch_traces(c->st, n, c->SWHW, c->Proj, c->part2, c->sc);
-  launch_control_linesearch(c->st, c->sc, c->part2, traces_blocks(n));
+  launch_control_linesearch(c->st, c->sc, c->part2, traces_partials(n));
   launch_update_state(c->st, n, m, c->C, c->Y4, c->Dir, c->G, c->Gold, c->sc);
   launch_update_subspace(c->st, n, c->SWHW, c->Proj, c->sc);
   pf.begin(c->st);

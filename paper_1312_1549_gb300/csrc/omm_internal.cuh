@@ -184,7 +184,8 @@ void launch_reduce_unpreconditioned(cudaStream_t st, long n, long m, const doubl
 // fp32_products: the mixed path's traces (float32 products of the tensor-core projections)
 void launch_traces(cudaStream_t st, int n, const double* SWHW, const double* Proj, double* part,
                    const Scalars* sc, bool fp32_products = false);
-int traces_blocks(int n);
+int traces_blocks(int n);    // 32 x 32 tiles of an n x n matrix (one CTA each in the n x n kernels)
+int traces_partials(int n);  // partial-sum slots launch_traces writes (about four tiles per CTA)
 void launch_control_linesearch(cudaStream_t st, Scalars* sc, const double* part, int nblocks);
 void launch_update_state(cudaStream_t st, int n, long m, double* C, double* Y4, const double* Dir,
                          double* G, double* Gold, const Scalars* sc);
