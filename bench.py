@@ -61,8 +61,8 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 float64 FMA rate, nominal (context; the roof
 # dram__bytes_read.sum + dram__bytes_write.sum over the P G, [HD; SD], projection and gradient
 # launches of one ncu capture: profiles/traffic_si512_line_search.md). Valid only for the GEMM
 # source it was measured on: reported as null once tc_gemm.cu has changed.
-GEMM_TRAFFIC_BYTES = 283.5e6
-GEMM_TRAFFIC_SOURCE_SHA256 = "c265b6b483b8fb484f357985f7525766ef5acbaa8bef3cb77e07d4b1139c73e8"
+GEMM_TRAFFIC_BYTES = 299.1e6
+GEMM_TRAFFIC_SOURCE_SHA256 = "a82f4112cd47d88477669b6c07d71553209b5c3cd8544153bf7443c62f1d46a0"
 
 
 def gemm_traffic():

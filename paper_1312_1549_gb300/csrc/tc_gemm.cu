@@ -259,6 +259,100 @@ __device__ __forceinline__ void store_bf8(__nv_bfloat16* p, const unsigned short
                                             h[4] | ((uint32_t)h[5] << 16), h[6] | ((uint32_t)h[7] << 16));
 }
 
+// The fused forms, float32 outputs and split outputs for the 32 accumulator columns of a row whose
+// float64 data (C unless c_f32, x0, x1, xout) starts on an 8-byte but not a 16-byte boundary (a
+// row of an odd leading dimension): eight columns at a time, 8-byte accesses to those arrays and
+// the usual vector accesses to the float32 and split arrays. offc, offx, offf, bf0: the row's first
+// element in C, in x0/x1/xout, in x1f/x2f and in the split outputs.
+__device__ __forceinline__ float f4_at(const float4& q, int i) { return i == 0 ? q.x : (i == 1 ? q.y : (i == 2 ? q.z : q.w)); }
+
+__device__ __forceinline__ void store_chunk_odd(const Epilogue& ep, long offc, long offx, long offf, long bf0,
+                                                const float (&v)[32], EpiRed& red) {
+  const bool unit = ep.alpha == 1.0 && ep.beta == 0.0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c8 = 8 * q;
+    if (ep.c_f32) {
+      float o[8];
+      const float al = (float)ep.alpha;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o[k] = (ep.mode == kEpReduce || unit) ? v[c8 + k] : al * v[c8 + k];
+      if (ep.mode == kEpReduce) {
+        double g[8], go[8];
+        float4 d[2];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) g[k] = __ldg(ep.x0 + offx + c8 + k);
+        if (red.have_dir) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) go[k] = ep.x1[offx + c8 + k];  // x1 may alias xout
+#pragma unroll
+          for (int k = 0; k < 2; ++k) d[k] = __ldg(reinterpret_cast<const float4*>(ep.x2f + offf + c8) + k);
+        }
+        // float32 sums of these 8 products, widened into the float64 running sums (as in the
+        // 16-column form)
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float gk = dev::f32_rne_bits(g[k]);
+          s0 = fmaf(gk, o[k], s0);
+          red.mb = max(red.mb, (unsigned long long)__double_as_longlong(g[k]) & 0x7FFFFFFFFFFFFFFFull);
+          if (red.have_dir) {
+            s1 = fmaf(dev::f32_rne_bits(go[k]), o[k], s1);
+            s2 = fmaf(gk, f4_at(d[k >> 2], k & 3), s2);
+          }
+        }
+        red.v0 += widen(s0);
+        if (red.have_dir) {
+          red.v1 += widen(s1);
+          red.v2 += widen(s2);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) ep.xout[offx + c8 + k] = g[k];
+      }
+      float4* c4 = reinterpret_cast<float4*>(reinterpret_cast<float*>(ep.C) + offc + c8);
+      c4[0] = make_float4(o[0], o[1], o[2], o[3]);
+      c4[1] = make_float4(o[4], o[5], o[6], o[7]);
+      if (ep.bf_hi != nullptr) {
+        unsigned short h[8], l[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dev::split_bits_f32(o[k], h[k], l[k]);
+        __nv_bfloat16* hp = ep.bf_hi + bf0 + c8;
+        store_bf8(hp, h);
+        store_bf8(hp + ep.bf_lo, l);
+      }
+      continue;
+    }
+    double out[8];
+    if (ep.mode == kEpGrad) {
+      double a0[8];
+      float4 a1[2];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a0[k] = __ldg(ep.x0 + offx + c8 + k);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) a1[k] = __ldg(reinterpret_cast<const float4*>(ep.x1f + offf + c8) + k);
+      const float alf = (float)ep.alpha, xsf = (float)ep.xs;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) out[k] = a0[k] + widen(fmaf(xsf, f4_at(a1[k >> 2], k & 3), alf * v[c8 + k]));
+    } else if (unit) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) out[k] = widen(v[c8 + k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) out[k] = combine(ep, widen(v[c8 + k]), ep.C + offc + c8 + k);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ep.C[offc + c8 + k] = out[k];
+    if (ep.bf_hi != nullptr) {
+      unsigned short h[8], l[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dev::split_bits_fast(out[k], h[k], l[k]);
+      __nv_bfloat16* hp = ep.bf_hi + bf0 + c8;
+      store_bf8(hp, h);
+      store_bf8(hp + ep.bf_lo, l);
+    }
+  }
+}
+
 // C = alpha * v + beta * C (or a fused form) for the 32 accumulator columns [col0, col0 + 32) of one row.
 __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col0, const float (&v)[32], EpiRed& red) {
   if (row >= ep.M || col0 >= ep.N) return;
@@ -307,9 +401,14 @@ __device__ __forceinline__ void store_chunk(const Epilogue& ep, int row, int col
   const long offx = (long)row * ep.ldx + cb0, offf = (long)row * ep.ldf + cb0;
   const long bf0 = blk0 * ep.bf_blk + (long)row * ep.bf_ld + cb0;
   const bool fused = ep.mode != kEpPlain;
-  const bool vec = blk0 == blk1 && nvalid == 32 && ((offc & (ep.c_f32 ? 3 : 1)) == 0) &&
-                   (!fused || ((offx & 1) == 0 && (offf & 3) == 0)) &&
-                   (ep.bf_hi == nullptr || ((bf0 & 7) == 0 && (ep.bf_lo & 7) == 0));
+  const bool vec8 = blk0 == blk1 && nvalid == 32 && (!ep.c_f32 || (offc & 3) == 0) && (!fused || (offf & 3) == 0) &&
+                    (ep.bf_hi == nullptr || ((bf0 & 7) == 0 && (ep.bf_lo & 7) == 0));
+  // the float64 rows on 16-byte boundaries too (an even leading dimension)
+  const bool vec = vec8 && (ep.c_f32 || (offc & 1) == 0) && (!fused || (offx & 1) == 0);
+  if (vec8 && !vec) {
+    store_chunk_odd(ep, offc, offx, offf, bf0, v, red);
+    return;
+  }
   if (vec) {
     const bool unit = ep.alpha == 1.0 && ep.beta == 0.0;  // plain store of the accumulator
 #pragma unroll
