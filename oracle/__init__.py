@@ -19,7 +19,8 @@ Contents (all plain float64 CPU code, written from the paper):
   conjugates, as the paper writes them (Secs. 2.1-2.3), for k-point problems.
 
 Parity status: every function here is pinned by a test in
-tests/test_oracle_pins.py and tests/test_oracle_hermitian.py against brute force, closed forms, finite
-differences or invariants; none is "parity unpinned" except the CG iteration
-count, which the paper does not fix.
+tests/test_oracle_pins.py, tests/test_oracle_hermitian.py and tests/test_oracle_cg_pins.py (the
+Polak-Ribiere coefficient, through its equality with the Hestenes-Stiefel one under exact line
+searches) against brute force, closed forms, finite differences or invariants; none is "parity
+unpinned" except the CG iteration count, which the paper does not fix.
 """
